@@ -1,0 +1,192 @@
+"""Python view of the plain FP64 CPU oracle (``hn_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may use this package; the product library never does.  Each function is a thin
+ctypes call into the C++ oracle, which restates the mathematics of the HONEI paper's Poisson
+client (Sec. 2.1 discretisation, Sec. 6.2 multigrid and mixed-precision defect correction).
+
+Vectors are numpy float64 arrays of length N = (2^L+1)^2, node i = iy*n + ix.  Bands are a
+(9, N) float64 array, band k holding A[i, i + dy*n + dx] with (dy, dx) = (k//3 - 1, k%3 - 1).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+PREC_FP64, PREC_FP32_DC, PREC_FP16BAND_DC, PREC_FP32_ONLY = 0, 1, 2, 3
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("inner_cycles", ctypes.c_int), ("converged", ctypes.c_int),
+                ("relres", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        fp = ctypes.POINTER(ctypes.c_float)
+        up = ctypes.POINTER(ctypes.c_uint16)
+        L.or_n.restype = ctypes.c_long
+        L.or_N.restype = ctypes.c_long
+        L.or_norm2.restype = ctypes.c_double
+        L.or_norm2.argtypes = [ctypes.c_long, dp]
+        L.or_fp16_rne.restype = ctypes.c_uint16
+        L.or_fp16_rne.argtypes = [ctypes.c_double]
+        L.or_fp16_to_float.restype = ctypes.c_float
+        L.or_fp16_to_float.argtypes = [ctypes.c_uint16]
+        L.or_element_stiffness.argtypes = [ctypes.c_double, dp]
+        L.or_assemble.argtypes = [ctypes.c_int, dp, dp]
+        L.or_coarsen_coef.argtypes = [ctypes.c_int, dp, dp]
+        L.or_spmv.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.or_defect.argtypes = [ctypes.c_int, dp, dp, dp, dp]
+        L.or_jacobi.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, dp]
+        L.or_restrict.argtypes = [ctypes.c_int, dp, dp]
+        L.or_prolong_add.argtypes = [ctypes.c_int, dp, dp]
+        L.or_coarse_solve.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.or_coarse_solve.restype = ctypes.c_int
+        L.or_quantize_fp16.argtypes = [ctypes.c_int, dp, fp, up]
+        L.or_mg_solve.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp,
+                                  ctypes.POINTER(Stats)]
+        L.or_mg_solve.restype = ctypes.c_int
+        L.or_load_sinsin.argtypes = [ctypes.c_int, dp]
+        L.or_l2_error_sinsin.argtypes = [ctypes.c_int, dp]
+        L.or_l2_error_sinsin.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def _p(a, ctype=ctypes.c_double):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def n_of(L):
+    return (1 << L) + 1
+
+
+def N_of(L):
+    return n_of(L) ** 2
+
+
+def element_stiffness(h=1.0):
+    K = np.zeros(16)
+    lib().or_element_stiffness(h, _p(K))
+    return K.reshape(4, 4)
+
+
+def assemble(L, coef=None):
+    """Q1 stiffness matrix of -div(a grad u) as 9 bands, Dirichlet rows/columns eliminated."""
+    bands = np.zeros((9, N_of(L)))
+    c = None if coef is None else _f64(coef)
+    lib().or_assemble(L, _p(c), _p(bands))
+    return bands
+
+
+def coarsen_coef(Lf, coef):
+    nc = n_of(Lf - 1) - 1
+    out = np.zeros(nc * nc)
+    lib().or_coarsen_coef(Lf, _p(_f64(coef)), _p(out))
+    return out
+
+
+def spmv(L, bands, x):
+    y = np.zeros(N_of(L))
+    lib().or_spmv(L, _p(_f64(bands)), _p(_f64(x)), _p(y))
+    return y
+
+
+def defect(L, bands, b, x):
+    r = np.zeros(N_of(L))
+    lib().or_defect(L, _p(_f64(bands)), _p(_f64(b)), _p(_f64(x)), _p(r))
+    return r
+
+
+def norm2(v):
+    v = _f64(v)
+    return lib().or_norm2(v.size, _p(v))
+
+
+def jacobi(L, bands, omega, b, x):
+    out = np.zeros(N_of(L))
+    lib().or_jacobi(L, _p(_f64(bands)), omega, _p(_f64(b)), _p(_f64(x)), _p(out))
+    return out
+
+
+def restrict(Lf, rf):
+    rc = np.zeros(N_of(Lf - 1))
+    lib().or_restrict(Lf, _p(_f64(rf)), _p(rc))
+    return rc
+
+
+def prolong_add(Lf, ec, xf):
+    out = _f64(xf).copy()
+    lib().or_prolong_add(Lf, _p(_f64(ec)), _p(out))
+    return out
+
+
+def coarse_solve(Lc, bands, b):
+    x = np.zeros(N_of(Lc))
+    rc = lib().or_coarse_solve(Lc, _p(_f64(bands)), _p(_f64(b)), _p(x))
+    if rc != 0:
+        raise ValueError("coarse matrix not positive definite")
+    return x
+
+
+def fp16_rne(v):
+    """IEEE binary16 round-to-nearest-even codes (uint16) of float64 values."""
+    v = np.asarray(v, dtype=np.float64)
+    f = lib().or_fp16_rne
+    return np.array([f(float(t)) for t in v.ravel()], dtype=np.uint16).reshape(v.shape)
+
+
+def quantize_fp16(L, bands):
+    s = np.zeros(9, dtype=np.float32)
+    codes = np.zeros((9, N_of(L)), dtype=np.uint16)
+    lib().or_quantize_fp16(L, _p(_f64(bands)), _p(s, ctypes.c_float), _p(codes, ctypes.c_uint16))
+    return s, codes
+
+
+def mg_solve(L, b, coef=None, x0=None, prec=PREC_FP64, pre=2, post=2, omega=0.7, tol=1e-8,
+             max_cycles=100, max_outer=50, inner_tol=1e-2, inner_max=10, coarse_L=2,
+             history=False):
+    """Multigrid solve; returns (x, stats dict[, relres history])."""
+    N = N_of(L)
+    x = np.zeros(N) if x0 is None else _f64(x0).copy()
+    c = None if coef is None else _f64(coef)
+    hlen = max(max_cycles, max_outer) + 2
+    hist = np.full(hlen, np.nan) if history else None
+    st = Stats()
+    rc = lib().or_mg_solve(L, _p(c), _p(_f64(b)), _p(x), prec, pre, post, omega, tol,
+                           max_cycles, max_outer, inner_tol, inner_max, coarse_L, _p(hist),
+                           ctypes.byref(st))
+    if rc < 0:
+        raise ValueError("bad arguments to the oracle solve")
+    stats = dict(cycles=st.cycles, outer_iters=st.outer_iters, inner_cycles=st.inner_cycles,
+                 converged=bool(st.converged), relres=st.relres)
+    if history:
+        return x, stats, hist[~np.isnan(hist)]
+    return x, stats
+
+
+def load_sinsin(L):
+    """Load vector of f = 2 pi^2 sin(pi x) sin(pi y), exact solution sin(pi x) sin(pi y)."""
+    b = np.zeros(N_of(L))
+    lib().or_load_sinsin(L, _p(b))
+    return b
+
+
+def l2_error_sinsin(L, x):
+    return lib().or_l2_error_sinsin(L, _p(_f64(x)))

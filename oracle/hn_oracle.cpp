@@ -1,0 +1,560 @@
+// Plain CPU oracle for the Q1-FEM multigrid Poisson solver of the HONEI paper.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the tests, __graft_entry__.smoke() and the CPU-baseline leg of
+// bench.py may load or call this library.  The product (the CUDA library under
+// paper_0904_4152_gb300/) never links, loads or calls it, and this file shares no code, header,
+// table or constant with it.
+//
+// Every routine is a slow, direct transcription of the mathematics, written for reading against
+// the paper (Sec. 2.1: Poisson problem, Q1 conforming elements, tensor-product numbering, band
+// structure, (2^L+1)^2 unknowns; Sec. 6.2: V cycle, two damped Jacobi pre/post smoothing steps,
+// mixed-precision defect correction).  No blocking, fusion or reordering.  Floating point is
+// FP64 unless the method itself prescribes a lower inner precision (the FP32 / FP16-band inner
+// multigrid of the defect-correction scheme, Sec. 6.2).  Compile with -ffp-contract=off so that
+// every operation rounds as written.
+//
+// Readings where the paper is silent (each also listed in the design notes):
+//  * boundary: zero Dirichlet on all four sides, eliminated symmetrically (row and column zeroed,
+//    diagonal 1, right-hand side 0);
+//  * coarse operators by re-discretisation, coarse cell coefficient = mean of its 4 children;
+//  * transfers: bilinear interpolation P (boundary rows/columns zeroed) and restriction R = P^T;
+//  * coarsest level solved exactly (dense Cholesky) instead of the paper's unpreconditioned CG;
+//  * stopping test ||b - A x||_2 / ||b||_2 <= tol after a complete cycle, x0 given (0 default);
+//  * defect correction: the FP64 defect is scaled by 1/||d|| before the cast to the inner
+//    precision, the inner cycles stop at a relative inner residual <= inner_tol (cap inner_max);
+//  * FP16 band storage: per band k, s_k = (float)max_i |band_k[i]|, code h = fp16_rne(band/s_k)
+//    with the quotient formed in FP64; the inner operator uses (float)(s_k * (float)h) per entry.
+//
+// Parity is pinned by the tests (closed-form stencil and eigenvalues, independent dense assembly,
+// dense LU, O(h^2) convergence, transfer identities, numpy's float16 rounding).  Nothing here is
+// "parity unpinned" except the absolute Table 1 values of the paper, which are not reproducible
+// because the paper does not name its test polynomial.
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------- grid and numbering (Sec. 2.1)
+inline long n_of(int L) { return (1L << L) + 1; }     // nodes per side
+inline long N_of(int L) { long n = n_of(L); return n * n; }
+inline bool is_boundary(long ix, long iy, long n) {
+  return ix == 0 || iy == 0 || ix == n - 1 || iy == n - 1;
+}
+// band k <-> neighbour offset (dy, dx), dy, dx in {-1, 0, 1}; band_k[i] = A[i, i + dy*n + dx]
+inline int band_dy(int k) { return k / 3 - 1; }
+inline int band_dx(int k) { return k % 3 - 1; }
+inline int band_of(int dy, int dx) { return (dy + 1) * 3 + (dx + 1); }
+
+// ------------------------------------------------- Q1 element stiffness from its definition
+// K_e[a][b] = integral over the cell of grad(phi_a) . grad(phi_b), bilinear basis on the square
+// cell of side h, local nodes (0,0), (1,0), (1,1), (0,1).  The integrand is a polynomial of
+// degree <= 2 in each variable, so 2-point Gauss-Legendre per direction integrates it exactly.
+void element_stiffness(double h, double K[4][4]) {
+  const double g = 0.5 / std::sqrt(3.0);
+  const double pts[2] = {0.5 - g, 0.5 + g};
+  const double wts[2] = {0.5, 0.5};
+  const int lx[4] = {0, 1, 1, 0}, ly[4] = {0, 0, 1, 1};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) K[a][b] = 0.0;
+  for (int qy = 0; qy < 2; ++qy)
+    for (int qx = 0; qx < 2; ++qx) {
+      const double xi = pts[qx], eta = pts[qy];
+      double gx[4], gy[4];  // physical gradients of the 4 local basis functions
+      for (int a = 0; a < 4; ++a) {
+        const double fx = lx[a] ? xi : 1.0 - xi;      // 1D factor in x
+        const double fy = ly[a] ? eta : 1.0 - eta;    // 1D factor in y
+        const double dfx = lx[a] ? 1.0 : -1.0;        // d/dxi of fx
+        const double dfy = ly[a] ? 1.0 : -1.0;        // d/deta of fy
+        gx[a] = dfx * fy / h;
+        gy[a] = fx * dfy / h;
+      }
+      const double w = wts[qx] * wts[qy] * h * h;     // |Jacobian| = h^2
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) K[a][b] += w * (gx[a] * gx[b] + gy[a] * gy[b]);
+    }
+}
+
+// --------------------------------------------------------------- global assembly (Sec. 2.1)
+// Full assembly of the 9-band matrix of -div(a grad u) with piecewise-constant cell coefficient,
+// element by element, followed by symmetric elimination of the Dirichlet nodes.
+void assemble(int L, const double* coef, double* bands) {
+  const long n = n_of(L), N = N_of(L), nc = n - 1;
+  const double h = 1.0 / (double)(n - 1);
+  std::memset(bands, 0, sizeof(double) * 9 * N);
+  double K[4][4];
+  element_stiffness(h, K);
+  const int lx[4] = {0, 1, 1, 0}, ly[4] = {0, 0, 1, 1};
+  for (long ey = 0; ey < nc; ++ey)
+    for (long ex = 0; ex < nc; ++ex) {
+      const double a = coef ? coef[ey * nc + ex] : 1.0;
+      for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q) {
+          const long ix = ex + lx[p], iy = ey + ly[p];
+          const long jx = ex + lx[q], jy = ey + ly[q];
+          const int k = band_of((int)(jy - iy), (int)(jx - ix));
+          bands[k * N + iy * n + ix] += a * K[p][q];
+        }
+    }
+  for (long iy = 0; iy < n; ++iy)
+    for (long ix = 0; ix < n; ++ix) {
+      const long i = iy * n + ix;
+      if (is_boundary(ix, iy, n)) {
+        for (int k = 0; k < 9; ++k) bands[k * N + i] = 0.0;
+        bands[4 * N + i] = 1.0;
+        continue;
+      }
+      for (int k = 0; k < 9; ++k)
+        if (is_boundary(ix + band_dx(k), iy + band_dy(k), n)) bands[k * N + i] = 0.0;
+    }
+}
+
+// coarse cell coefficient = arithmetic mean of the 4 child cells
+void coarsen_coef(int Lf, const double* af, double* ac) {
+  const long ncf = n_of(Lf) - 1, ncc = n_of(Lf - 1) - 1;
+  for (long Ey = 0; Ey < ncc; ++Ey)
+    for (long Ex = 0; Ex < ncc; ++Ex) {
+      const long y = 2 * Ey, x = 2 * Ex;
+      ac[Ey * ncc + Ex] = (af[y * ncf + x] + af[y * ncf + x + 1] + af[(y + 1) * ncf + x] +
+                           af[(y + 1) * ncf + x + 1]) * 0.25;
+    }
+}
+
+// ---------------------------------------------------------------- banded matrix-vector product
+// y_i = sum over on-grid neighbours j = i + off_k of band_k[i] * x_j
+template <typename T>
+void spmv(int L, const T* bands, const T* x, T* y) {
+  const long n = n_of(L), N = N_of(L);
+  for (long iy = 0; iy < n; ++iy)
+    for (long ix = 0; ix < n; ++ix) {
+      const long i = iy * n + ix;
+      T s = 0;
+      for (int k = 0; k < 9; ++k) {
+        const long jx = ix + band_dx(k), jy = iy + band_dy(k);
+        if (jx < 0 || jy < 0 || jx >= n || jy >= n) continue;
+        s += bands[k * N + i] * x[jy * n + jx];
+      }
+      y[i] = s;
+    }
+}
+
+// r = b - A x
+template <typename T>
+void defect(int L, const T* bands, const T* b, const T* x, T* r) {
+  const long N = N_of(L);
+  std::vector<T> ax(N);
+  spmv<T>(L, bands, x, ax.data());
+  for (long i = 0; i < N; ++i) r[i] = b[i] - ax[i];
+}
+
+// Euclidean norm, plain sequential sum of squares in FP64
+template <typename T>
+double norm2(long N, const T* v) {
+  double s = 0.0;
+  for (long i = 0; i < N; ++i) s += (double)v[i] * (double)v[i];
+  return std::sqrt(s);
+}
+
+// one damped Jacobi step: x_out = x_in + omega * (b - A x_in) / diag(A)   (Sec. 6.2)
+template <typename T>
+void jacobi(int L, const T* bands, T omega, const T* b, const T* x_in, T* x_out) {
+  const long N = N_of(L);
+  std::vector<T> r(N);
+  defect<T>(L, bands, b, x_in, r.data());
+  for (long i = 0; i < N; ++i) x_out[i] = x_in[i] + omega * r[i] / bands[4 * N + i];
+}
+
+// ------------------------------------------------------------------ grid transfers
+// Bilinear interpolation weight of coarse index C for fine index f along one axis.
+inline double w1d(long f, long C) {
+  if (f % 2 == 0) return (f / 2 == C) ? 1.0 : 0.0;
+  return (C == (f - 1) / 2 || C == (f + 1) / 2) ? 0.5 : 0.0;
+}
+
+// x_f += P e_c (bilinear interpolation, boundary rows and columns of P zeroed)
+template <typename T>
+void prolong_add(int Lf, const T* ec, T* xf) {
+  const long nf = n_of(Lf), nc = n_of(Lf - 1);
+  for (long fy = 0; fy < nf; ++fy)
+    for (long fx = 0; fx < nf; ++fx) {
+      if (is_boundary(fx, fy, nf)) continue;
+      T s = 0;
+      for (long Cy = (fy - 1) / 2; Cy <= (fy + 1) / 2; ++Cy)
+        for (long Cx = (fx - 1) / 2; Cx <= (fx + 1) / 2; ++Cx) {
+          if (Cx < 0 || Cy < 0 || Cx >= nc || Cy >= nc || is_boundary(Cx, Cy, nc)) continue;
+          const double w = w1d(fx, Cx) * w1d(fy, Cy);
+          if (w != 0.0) s += (T)w * ec[Cy * nc + Cx];
+        }
+      xf[fy * nf + fx] += s;
+    }
+}
+
+// r_c = P^T r_f : every fine node scatters its value with the interpolation weights
+template <typename T>
+void restrict_(int Lf, const T* rf, T* rc) {
+  const long nf = n_of(Lf), nc = n_of(Lf - 1);
+  for (long i = 0; i < nc * nc; ++i) rc[i] = 0;
+  for (long fy = 0; fy < nf; ++fy)
+    for (long fx = 0; fx < nf; ++fx) {
+      if (is_boundary(fx, fy, nf)) continue;
+      for (long Cy = (fy - 1) / 2; Cy <= (fy + 1) / 2; ++Cy)
+        for (long Cx = (fx - 1) / 2; Cx <= (fx + 1) / 2; ++Cx) {
+          if (Cx < 0 || Cy < 0 || Cx >= nc || Cy >= nc || is_boundary(Cx, Cy, nc)) continue;
+          const double w = w1d(fx, Cx) * w1d(fy, Cy);
+          if (w != 0.0) rc[Cy * nc + Cx] += (T)w * rf[fy * nf + fx];
+        }
+    }
+}
+
+// ------------------------------------------------------------------- exact coarse solve
+// Dense Cholesky of the interior block of the coarsest matrix (the paper uses unpreconditioned
+// CG there; on this tiny SPD system both give the exact solution up to rounding).
+struct CoarseSolver {
+  int L = 0;
+  long n = 0, m = 0;              // nodes per side, interior unknowns
+  std::vector<double> chol;       // lower factor, m*m row-major
+  bool ok = false;
+  void factor(int Lc, const double* bands) {
+    L = Lc; n = n_of(Lc); const long N = N_of(Lc); const long ni = n - 2; m = ni * ni;
+    std::vector<double> A(m * m, 0.0);
+    for (long iy = 1; iy < n - 1; ++iy)
+      for (long ix = 1; ix < n - 1; ++ix) {
+        const long I = (iy - 1) * ni + (ix - 1);
+        for (int k = 0; k < 9; ++k) {
+          const long jx = ix + band_dx(k), jy = iy + band_dy(k);
+          if (is_boundary(jx, jy, n)) continue;
+          const long J = (jy - 1) * ni + (jx - 1);
+          A[I * m + J] = bands[k * N + iy * n + ix];
+        }
+      }
+    chol.assign(m * m, 0.0);
+    ok = true;
+    for (long j = 0; j < m; ++j) {
+      double d = A[j * m + j];
+      for (long k = 0; k < j; ++k) d -= chol[j * m + k] * chol[j * m + k];
+      if (!(d > 0.0)) { ok = false; return; }
+      chol[j * m + j] = std::sqrt(d);
+      for (long i = j + 1; i < m; ++i) {
+        double s = A[i * m + j];
+        for (long k = 0; k < j; ++k) s -= chol[i * m + k] * chol[j * m + k];
+        chol[i * m + j] = s / chol[j * m + j];
+      }
+    }
+  }
+  // x = A^{-1} b on interior nodes, 0 on the boundary.  Solved in FP64, then stored as T.
+  template <typename T>
+  void solve(const T* b, T* x) const {
+    const long ni = n - 2;
+    std::vector<double> y(m);
+    for (long i = 0; i < m; ++i) {
+      const long iy = i / ni + 1, ix = i % ni + 1;
+      double s = (double)b[iy * n + ix];
+      for (long k = 0; k < i; ++k) s -= chol[i * m + k] * y[k];
+      y[i] = s / chol[i * m + i];
+    }
+    for (long i = m - 1; i >= 0; --i) {
+      double s = y[i];
+      for (long k = i + 1; k < m; ++k) s -= chol[k * m + i] * y[k];
+      y[i] = s / chol[i * m + i];
+    }
+    for (long i = 0; i < n * n; ++i) x[i] = 0;
+    for (long i = 0; i < m; ++i) x[(i / ni + 1) * n + (i % ni + 1)] = (T)y[i];
+  }
+};
+
+// -------------------------------------------------------------------- FP16 band storage
+// IEEE 754 binary16 round-to-nearest-even of an FP64 value, from the format's definition:
+// 1 sign bit, 5 exponent bits (bias 15), 10 fraction bits, subnormal quantum 2^-24.
+uint16_t fp16_rne(double v) {
+  uint16_t sign = std::signbit(v) ? 0x8000u : 0u;
+  double a = std::fabs(v);
+  if (std::isnan(v)) return (uint16_t)(sign | 0x7e00u);
+  if (a >= 65520.0) return (uint16_t)(sign | 0x7c00u);   // rounds to infinity
+  if (a < std::ldexp(1.0, -14)) {                        // subnormal range (or zero)
+    const double m = std::nearbyint(std::ldexp(a, 24));  // multiple of 2^-24, ties to even
+    return (uint16_t)(sign | (uint16_t)m);               // m == 1024 encodes 2^-14 correctly
+  }
+  int e;
+  std::frexp(a, &e);                                     // a = f * 2^e, f in [0.5, 1)
+  e -= 1;                                                // 2^e <= a < 2^(e+1)
+  double m = std::nearbyint(std::ldexp(a, 10 - e));      // in [1024, 2048]
+  if (m == 2048.0) { m = 1024.0; e += 1; }
+  if (e > 15) return (uint16_t)(sign | 0x7c00u);
+  return (uint16_t)(sign | (uint16_t)((e + 15) << 10) | (uint16_t)(m - 1024.0));
+}
+
+float fp16_to_float(uint16_t h) {
+  const int s = (h >> 15) & 1, e = (h >> 10) & 31, f = h & 1023;
+  double v;
+  if (e == 0) v = std::ldexp((double)f, -24);
+  else if (e == 31) v = f ? NAN : INFINITY;
+  else v = std::ldexp(1024.0 + f, e - 25);
+  return (float)(s ? -v : v);
+}
+
+// quantise the 9 bands: scales[k] (float), codes[k*N + i]
+void quantize_fp16(int L, const double* bands, float* scales, uint16_t* codes) {
+  const long N = N_of(L);
+  for (int k = 0; k < 9; ++k) {
+    double mx = 0.0;
+    for (long i = 0; i < N; ++i) mx = std::fmax(mx, std::fabs(bands[k * N + i]));
+    float s = (float)mx;
+    if (s == 0.0f) s = 1.0f;
+    scales[k] = s;
+    for (long i = 0; i < N; ++i) codes[k * N + i] = fp16_rne(bands[k * N + i] / (double)s);
+  }
+}
+
+// ------------------------------------------------------------------------ the hierarchy
+struct Level {
+  int L;
+  long N;
+  std::vector<double> a64;   // bands FP64
+  std::vector<float> a32;    // bands of the inner precision (FP32 cast, or FP16 dequantised)
+};
+
+struct Hierarchy {
+  std::vector<Level> lev;    // lev[0] = finest
+  CoarseSolver cs;
+  int coarse_L;
+  void build(int L, const double* coef, int coarse, int inner_prec) {
+    coarse_L = coarse;
+    std::vector<double> a;
+    if (coef) a.assign(coef, coef + (n_of(L) - 1) * (n_of(L) - 1));
+    for (int l = L; l >= coarse; --l) {
+      Level v; v.L = l; v.N = N_of(l);
+      v.a64.resize(9 * v.N);
+      assemble(l, coef ? a.data() : nullptr, v.a64.data());
+      if (inner_prec == 1 || inner_prec == 3) {
+        v.a32.resize(9 * v.N);
+        for (long i = 0; i < 9 * v.N; ++i) v.a32[i] = (float)v.a64[i];
+      } else if (inner_prec == 2) {
+        std::vector<float> s(9);
+        std::vector<uint16_t> c(9 * v.N);
+        quantize_fp16(l, v.a64.data(), s.data(), c.data());
+        v.a32.resize(9 * v.N);
+        for (int k = 0; k < 9; ++k)
+          for (long i = 0; i < v.N; ++i)
+            v.a32[k * v.N + i] = s[k] * fp16_to_float(c[k * v.N + i]);
+      }
+      lev.push_back(std::move(v));
+      if (coef && l > coarse) {
+        std::vector<double> ac((n_of(l - 1) - 1) * (n_of(l - 1) - 1));
+        coarsen_coef(l, a.data(), ac.data());
+        a.swap(ac);
+      }
+    }
+    cs.factor(coarse, lev.back().a64.data());
+  }
+  template <typename T> const T* bands(size_t d) const;
+};
+template <> const double* Hierarchy::bands<double>(size_t d) const { return lev[d].a64.data(); }
+template <> const float* Hierarchy::bands<float>(size_t d) const { return lev[d].a32.data(); }
+
+// one V(pre, post) cycle on level depth d (Sec. 6.2); x is updated in place
+template <typename T>
+void vcycle(const Hierarchy& H, size_t d, T* x, const T* b, int pre, int post, T omega) {
+  const Level& lv = H.lev[d];
+  if (lv.L == H.coarse_L) { H.cs.solve<T>(b, x); return; }
+  const long N = lv.N;
+  const T* A = H.bands<T>(d);
+  std::vector<T> t(N);
+  for (int s = 0; s < pre; ++s) { jacobi<T>(lv.L, A, omega, b, x, t.data()); std::copy(t.begin(), t.end(), x); }
+  std::vector<T> r(N);
+  defect<T>(lv.L, A, b, x, r.data());
+  const long Nc = H.lev[d + 1].N;
+  std::vector<T> bc(Nc), ec(Nc, (T)0);
+  restrict_<T>(lv.L, r.data(), bc.data());
+  vcycle<T>(H, d + 1, ec.data(), bc.data(), pre, post, omega);
+  prolong_add<T>(lv.L, ec.data(), x);
+  for (int s = 0; s < post; ++s) { jacobi<T>(lv.L, A, omega, b, x, t.data()); std::copy(t.begin(), t.end(), x); }
+}
+
+}  // namespace
+
+// =============================================================================== C interface
+extern "C" {
+
+typedef struct {
+  int cycles;        // V cycles in the precision that drives convergence (FP64 mode) or inner cycles
+  int outer_iters;   // defect-correction updates applied (0 in FP64 mode)
+  int inner_cycles;  // inner-precision V cycles (0 in FP64 mode)
+  int converged;     // 1 if relres <= tol was reached
+  double relres;     // final ||b - A x|| / ||b|| in FP64 with the FP64 operator
+} or_stats;
+
+long or_n(int L) { return n_of(L); }
+long or_N(int L) { return N_of(L); }
+
+void or_element_stiffness(double h, double* K16) {
+  double K[4][4];
+  element_stiffness(h, K);
+  for (int a = 0; a < 4; ++a) for (int b = 0; b < 4; ++b) K16[a * 4 + b] = K[a][b];
+}
+void or_assemble(int L, const double* coef, double* bands) { assemble(L, coef, bands); }
+void or_coarsen_coef(int Lf, const double* af, double* ac) { coarsen_coef(Lf, af, ac); }
+void or_spmv(int L, const double* bands, const double* x, double* y) { spmv<double>(L, bands, x, y); }
+void or_defect(int L, const double* bands, const double* b, const double* x, double* r) {
+  defect<double>(L, bands, b, x, r);
+}
+double or_norm2(long N, const double* v) { return norm2<double>(N, v); }
+void or_jacobi(int L, const double* bands, double omega, const double* b, const double* x_in, double* x_out) {
+  jacobi<double>(L, bands, omega, b, x_in, x_out);
+}
+void or_restrict(int Lf, const double* rf, double* rc) { restrict_<double>(Lf, rf, rc); }
+void or_prolong_add(int Lf, const double* ec, double* xf) { prolong_add<double>(Lf, ec, xf); }
+int or_coarse_solve(int Lc, const double* bands, const double* b, double* x) {
+  CoarseSolver cs;
+  cs.factor(Lc, bands);
+  if (!cs.ok) return -1;
+  cs.solve<double>(b, x);
+  return 0;
+}
+uint16_t or_fp16_rne(double v) { return fp16_rne(v); }
+float or_fp16_to_float(uint16_t h) { return fp16_to_float(h); }
+void or_quantize_fp16(int L, const double* bands, float* scales, uint16_t* codes) {
+  quantize_fp16(L, bands, scales, codes);
+}
+
+// Multigrid solve.  prec: 0 = FP64 V cycles; 1 = FP64 defect correction with FP32 inner MG;
+// 2 = the same with FP16-band-storage inner MG; 3 = FP32-only MG (the paper's failing
+// single-precision column, Table 1): b and x cast to FP32, FP32 cycles, FP32 convergence test.
+// relres_hist (optional, length >= max_cycles + 1 for prec 0/3, max_outer + 1 for prec 1/2)
+// receives the FP64 relative residual before the first and after every cycle / outer step.
+// Returns 0 on convergence, 1 if the cycle cap was hit, -1 on bad arguments.
+int or_mg_solve(int L, const double* coef, const double* b, double* x, int prec, int pre, int post,
+                double omega, double tol, int max_cycles, int max_outer, double inner_tol,
+                int inner_max, int coarse_L, double* relres_hist, or_stats* st) {
+  if (L < coarse_L || coarse_L < 2 || prec < 0 || prec > 3) return -1;
+  Hierarchy H;
+  H.build(L, coef, coarse_L, prec);
+  if (!H.cs.ok) return -1;
+  const long N = N_of(L);
+  const double* A = H.lev[0].a64.data();
+  const double bnorm = norm2<double>(N, b);
+  or_stats s = {0, 0, 0, 0, 0.0};
+  std::vector<double> r(N);
+  int hist = 0;
+  auto relres_now = [&]() {
+    defect<double>(L, A, b, x, r.data());
+    return bnorm > 0.0 ? norm2<double>(N, r.data()) / bnorm : 0.0;
+  };
+  if (bnorm == 0.0) {
+    for (long i = 0; i < N; ++i) x[i] = 0.0;
+    s.converged = 1;
+    if (relres_hist) relres_hist[0] = 0.0;
+    if (st) *st = s;
+    return 0;
+  }
+  if (prec == 0) {
+    double rr = relres_now();
+    if (relres_hist) relres_hist[hist++] = rr;
+    while (rr > tol && s.cycles < max_cycles) {
+      vcycle<double>(H, 0, x, b, pre, post, omega);
+      ++s.cycles;
+      rr = relres_now();
+      if (relres_hist) relres_hist[hist++] = rr;
+    }
+    s.relres = rr;
+    s.converged = rr <= tol;
+  } else if (prec == 3) {
+    std::vector<float> bf(N), xf(N), rf(N);
+    for (long i = 0; i < N; ++i) { bf[i] = (float)b[i]; xf[i] = (float)x[i]; }
+    const float* A32 = H.lev[0].a32.data();
+    const double bn32 = norm2<float>(N, bf.data());
+    auto rr32 = [&]() { defect<float>(L, A32, bf.data(), xf.data(), rf.data()); return norm2<float>(N, rf.data()) / bn32; };
+    double rr = rr32();
+    if (relres_hist) { for (long i = 0; i < N; ++i) x[i] = xf[i]; relres_hist[hist++] = relres_now(); }
+    while (rr > tol && s.cycles < max_cycles) {
+      vcycle<float>(H, 0, xf.data(), bf.data(), pre, post, (float)omega);
+      ++s.cycles;
+      rr = rr32();
+      if (relres_hist) { for (long i = 0; i < N; ++i) x[i] = xf[i]; relres_hist[hist++] = relres_now(); }
+    }
+    for (long i = 0; i < N; ++i) x[i] = xf[i];
+    s.relres = relres_now();
+    s.converged = rr <= tol;
+  } else {
+    // mixed-precision defect correction (Sec. 6.2): FP64 outer loop, inner-precision MG
+    std::vector<double> d(N);
+    std::vector<float> dh(N), c(N), t(N);
+    const float* A32 = H.lev[0].a32.data();
+    for (;;) {
+      defect<double>(L, A, b, x, d.data());
+      const double dn = norm2<double>(N, d.data());
+      const double rr = dn / bnorm;
+      if (relres_hist) relres_hist[hist++] = rr;
+      s.relres = rr;
+      if (rr <= tol) { s.converged = 1; break; }
+      if (s.outer_iters >= max_outer) break;
+      for (long i = 0; i < N; ++i) { dh[i] = (float)(d[i] / dn); c[i] = 0.0f; }
+      const double dhn = norm2<float>(N, dh.data());
+      for (int k = 0; k < inner_max; ++k) {
+        vcycle<float>(H, 0, c.data(), dh.data(), pre, post, (float)omega);
+        ++s.inner_cycles;
+        ++s.cycles;
+        defect<float>(L, A32, dh.data(), c.data(), t.data());
+        if (norm2<float>(N, t.data()) <= inner_tol * dhn) break;
+      }
+      for (long i = 0; i < N; ++i) x[i] += dn * (double)c[i];
+      ++s.outer_iters;
+    }
+  }
+  if (st) *st = s;
+  return s.converged ? 0 : 1;
+}
+
+// Load vector b_i = integral of f phi_i for f = 2 pi^2 sin(pi x) sin(pi y) (so that
+// u = sin(pi x) sin(pi y) solves -Laplace(u) = f), 3x3 Gauss-Legendre per cell; Dirichlet entries 0.
+void or_load_sinsin(int L, double* b) {
+  const long n = n_of(L), N = N_of(L);
+  const double h = 1.0 / (double)(n - 1);
+  const double g = 0.5 * std::sqrt(0.6);
+  const double pts[3] = {0.5 - g, 0.5, 0.5 + g};
+  const double wts[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  const int lx[4] = {0, 1, 1, 0}, ly[4] = {0, 0, 1, 1};
+  for (long i = 0; i < N; ++i) b[i] = 0.0;
+  for (long ey = 0; ey < n - 1; ++ey)
+    for (long ex = 0; ex < n - 1; ++ex)
+      for (int qy = 0; qy < 3; ++qy)
+        for (int qx = 0; qx < 3; ++qx) {
+          const double xi = pts[qx], eta = pts[qy];
+          const double px = (ex + xi) * h, py = (ey + eta) * h;
+          const double f = 2.0 * M_PI * M_PI * std::sin(M_PI * px) * std::sin(M_PI * py);
+          const double w = wts[qx] * wts[qy] * h * h;
+          for (int a = 0; a < 4; ++a) {
+            const double phi = (lx[a] ? xi : 1.0 - xi) * (ly[a] ? eta : 1.0 - eta);
+            b[(ey + ly[a]) * n + ex + lx[a]] += w * f * phi;
+          }
+        }
+  for (long iy = 0; iy < n; ++iy)
+    for (long ix = 0; ix < n; ++ix)
+      if (is_boundary(ix, iy, n)) b[iy * n + ix] = 0.0;
+}
+
+// Integral L2 error || u_h - sin(pi x) sin(pi y) ||, u_h the bilinear interpolant of the nodal
+// values, 3x3 Gauss per cell, in FP64 (Sec. 6.2.1).
+double or_l2_error_sinsin(int L, const double* x) {
+  const long n = n_of(L);
+  const double h = 1.0 / (double)(n - 1);
+  const double g = 0.5 * std::sqrt(0.6);
+  const double pts[3] = {0.5 - g, 0.5, 0.5 + g};
+  const double wts[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  double s = 0.0;
+  for (long ey = 0; ey < n - 1; ++ey)
+    for (long ex = 0; ex < n - 1; ++ex)
+      for (int qy = 0; qy < 3; ++qy)
+        for (int qx = 0; qx < 3; ++qx) {
+          const double xi = pts[qx], eta = pts[qy];
+          const double uh = (1 - xi) * (1 - eta) * x[ey * n + ex] + xi * (1 - eta) * x[ey * n + ex + 1] +
+                            xi * eta * x[(ey + 1) * n + ex + 1] + (1 - xi) * eta * x[(ey + 1) * n + ex];
+          const double u = std::sin(M_PI * (ex + xi) * h) * std::sin(M_PI * (ey + eta) * h);
+          s += wts[qx] * wts[qy] * h * h * (uh - u) * (uh - u);
+        }
+  return std::sqrt(s);
+}
+
+}  // extern "C"

@@ -1,0 +1,410 @@
+"""Pins of the CPU oracle against what the mathematics and the paper fix (no GPU needed).
+
+Each test checks the oracle against something other than itself: closed forms (Q1 element
+matrix, eigenpairs of the constant-coefficient operator, transfer identities), an independent
+dense assembly, dense LU, the O(h^2) error reduction printed in the paper's Table 1 (Sec. 6.2.1),
+and numpy's IEEE float16 rounding.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0904_4152_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------- helpers (tests)
+def offsets(n):
+    return [(k // 3 - 1) * n + (k % 3 - 1) for k in range(9)]
+
+
+def dense_from_bands(L, bands):
+    n = O.n_of(L)
+    N = n * n
+    A = np.zeros((N, N))
+    for iy in range(n):
+        for ix in range(n):
+            i = iy * n + ix
+            for k in range(9):
+                jy, jx = iy + k // 3 - 1, ix + k % 3 - 1
+                if 0 <= jx < n and 0 <= jy < n:
+                    A[i, jy * n + jx] = bands[k, i]
+    return A
+
+
+def interior_idx(L):
+    return np.flatnonzero(I.interior_mask(L))
+
+
+def sin_mode(L, p, q):
+    n = O.n_of(L)
+    h = 1.0 / (n - 1)
+    ix = np.arange(n)
+    return np.outer(np.sin(q * np.pi * ix * h), np.sin(p * np.pi * ix * h)).ravel()  # [iy, ix]
+
+
+def q1_eigenvalue(L, p, q):
+    """Eigenvalue of the a=1 Q1 operator for sin mode (p, q): A = K1 x M1 + M1 x K1 (1D
+    stiffness K1 = tridiag(-1, 2, -1)/h, mass M1 = tridiag(1, 4, 1) h/6)."""
+    h = 1.0 / (O.n_of(L) - 1)
+    k = lambda m: (2.0 / h) * (1.0 - math.cos(m * math.pi * h))
+    mm = lambda m: (h / 3.0) * (2.0 + math.cos(m * math.pi * h))
+    return k(p) * mm(q) + mm(p) * k(q)
+
+
+# ------------------------------------------------------------------------ element / assembly
+@pytest.mark.parametrize("h", [1.0, 1.0 / 8, 1.0 / 1024])
+def test_element_stiffness_closed_form(h):
+    # Q1 stiffness on a square, local nodes counter-clockwise: (1/6)[[4,-1,-2,-1], ...], no h in 2D
+    ref = np.array([[4, -1, -2, -1], [-1, 4, -1, -2], [-2, -1, 4, -1], [-1, -2, -1, 4]]) / 6.0
+    np.testing.assert_allclose(O.element_stiffness(h), ref, rtol=0, atol=4e-16)
+
+
+def test_interior_stencil_closed_form():
+    L = 5
+    A = O.assemble(L)
+    n = O.n_of(L)
+    N = n * n
+    for iy in range(2, n - 2):
+        for ix in range(2, n - 2):
+            i = iy * n + ix
+            np.testing.assert_allclose(A[4, i], 8.0 / 3.0, rtol=0, atol=1e-15)
+            for k in (0, 1, 2, 3, 5, 6, 7, 8):
+                np.testing.assert_allclose(A[k, i], -1.0 / 3.0, rtol=0, atol=1e-15)
+    # rows with no Dirichlet neighbour have row sum 0 (constants are in the kernel of -Laplace)
+    inner = [iy * n + ix for iy in range(2, n - 2) for ix in range(2, n - 2)]
+    assert np.max(np.abs(A[:, inner].sum(axis=0))) < 1e-14
+    assert A.shape == (9, N)
+
+
+def test_band_layout_exact():
+    # structurally nonzero iff row and column are interior nodes (boundary rows: identity)
+    for L in (2, 3, 5):
+        a = I.lognormal_coef(L, 3)
+        A = O.assemble(L, a)
+        n = O.n_of(L)
+        inner = I.interior_mask(L).reshape(n, n)
+        for iy in range(n):
+            for ix in range(n):
+                i = iy * n + ix
+                for k in range(9):
+                    jy, jx = iy + k // 3 - 1, ix + k % 3 - 1
+                    on = 0 <= jx < n and 0 <= jy < n
+                    expect = inner[iy, ix] and on and inner[jy, jx]
+                    if not inner[iy, ix]:
+                        assert A[k, i] == (1.0 if k == 4 else 0.0)
+                    else:
+                        assert (A[k, i] != 0.0) == expect, (L, ix, iy, k)
+
+
+def test_constant_coefficient_matches_kronecker_form():
+    # independent dense construction: interior block = M1 (x) K1 + K1 (x) M1
+    for L in (2, 3, 4):
+        n = O.n_of(L)
+        h = 1.0 / (n - 1)
+        m = n - 2
+        K1 = (2 * np.eye(m) - np.eye(m, k=1) - np.eye(m, k=-1)) / h
+        M1 = (4 * np.eye(m) + np.eye(m, k=1) + np.eye(m, k=-1)) * h / 6
+        ref = np.kron(M1, K1) + np.kron(K1, M1)
+        idx = interior_idx(L)
+        got = dense_from_bands(L, O.assemble(L))[np.ix_(idx, idx)]
+        np.testing.assert_allclose(got, ref, rtol=0, atol=2e-15)
+
+
+def test_variable_coefficient_matches_independent_quadrature():
+    # independent assembly: hat-function gradients at 3x3 Gauss points of every cell
+    L = 3
+    n = O.n_of(L)
+    h = 1.0 / (n - 1)
+    a = I.lognormal_coef(L, 11)
+    N = n * n
+    ref = np.zeros((N, N))
+    g = np.array([0.5 - 0.5 * math.sqrt(0.6), 0.5, 0.5 + 0.5 * math.sqrt(0.6)])
+    w = np.array([5, 8, 5]) / 18.0
+    for ey in range(n - 1):
+        for ex in range(n - 1):
+            nodes = [(ex + dx, ey + dy) for dy in (0, 1) for dx in (0, 1)]
+            for qy in range(3):
+                for qx in range(3):
+                    x = (ex + g[qx]) * h
+                    y = (ey + g[qy]) * h
+                    grads = []
+                    for (jx, jy) in nodes:
+                        tx, ty = x - jx * h, y - jy * h
+                        hx, hy = 1 - abs(tx) / h, 1 - abs(ty) / h
+                        grads.append((-np.sign(tx) / h * hy, -np.sign(ty) / h * hx))
+                    for p, (ix, iy) in enumerate(nodes):
+                        for q, (jx, jy) in enumerate(nodes):
+                            ref[iy * n + ix, jy * n + jx] += (w[qx] * w[qy] * h * h * a[ey * (n - 1) + ex]
+                                                              * (grads[p][0] * grads[q][0] + grads[p][1] * grads[q][1]))
+    idx = interior_idx(L)
+    got = dense_from_bands(L, O.assemble(L, a))[np.ix_(idx, idx)]
+    np.testing.assert_allclose(got, ref[np.ix_(idx, idx)], rtol=1e-13, atol=1e-14)
+
+
+def test_coefficient_scaling():
+    L = 4
+    c = 3.25
+    N1 = O.assemble(L)
+    Nc = O.assemble(L, np.full((O.n_of(L) - 1) ** 2, c))
+    idx = interior_idx(L)
+    np.testing.assert_allclose(Nc[:, idx], c * N1[:, idx], rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 5])
+def test_symmetric_positive_definite(L):
+    a = I.lognormal_coef(L, 5)
+    A = O.assemble(L, a)
+    n = O.n_of(L)
+    N = n * n
+    offs = offsets(n)
+    for k in range(9):
+        for i in range(N):
+            j = i + offs[k]
+            if 0 <= j < N and A[k, i] != 0.0:
+                assert A[k, i] == A[8 - k, j]          # bit-exact symmetry
+    D = dense_from_bands(L, A)
+    np.linalg.cholesky(D)                              # raises if not SPD
+    assert np.linalg.eigvalsh(D).min() > 0
+
+
+def test_coarsen_coef_linear_field():
+    # mean of 4 children of a linear field sampled at cell centres = value at the coarse centre
+    Lf = 5
+    nf = 1 << Lf
+    c = (np.arange(nf) + 0.5) / nf
+    X, Y = np.meshgrid(c, c)
+    af = (2.0 + 0.7 * X - 0.3 * Y).ravel()
+    nc = nf // 2
+    cc = (np.arange(nc) + 0.5) / nc
+    Xc, Yc = np.meshgrid(cc, cc)
+    np.testing.assert_allclose(O.coarsen_coef(Lf, af), (2.0 + 0.7 * Xc - 0.3 * Yc).ravel(),
+                               rtol=0, atol=1e-14)
+
+
+# -------------------------------------------------------------- band operators (a = 1 modes)
+@pytest.mark.parametrize("L,p,q", [(4, 1, 1), (4, 3, 7), (5, 2, 13), (5, 31, 1)])
+def test_spmv_eigenpairs(L, p, q):
+    A = O.assemble(L)
+    v = sin_mode(L, p, q)
+    lam = q1_eigenvalue(L, p, q)
+    tol = 1e-14 * max(1.0, lam)
+    np.testing.assert_allclose(O.spmv(L, A, v), lam * v, rtol=0, atol=tol)
+    # defect of the exact eigen-solution vanishes; defect of 0 is b
+    np.testing.assert_allclose(O.defect(L, A, lam * v, v), 0.0, atol=tol)
+    np.testing.assert_array_equal(O.defect(L, A, v, np.zeros_like(v)), v)
+
+
+@pytest.mark.parametrize("omega", [0.7, 0.5])
+def test_jacobi_error_propagation(omega):
+    # with b = 0 one damped Jacobi step multiplies mode (p,q) by 1 - omega * lambda / (8/3)
+    L = 5
+    A = O.assemble(L)
+    for p, q in [(1, 1), (5, 9), (30, 30)]:
+        v = sin_mode(L, p, q)
+        x1 = O.jacobi(L, A, omega, np.zeros_like(v), v)
+        fac = 1.0 - omega * q1_eigenvalue(L, p, q) * 3.0 / 8.0
+        np.testing.assert_allclose(x1, fac * v, rtol=0, atol=1e-14)
+
+
+def test_jacobi_fixed_point():
+    L = 4
+    a = I.lognormal_coef(L, 2)
+    A = O.assemble(L, a)
+    idx = interior_idx(L)
+    D = dense_from_bands(L, A)
+    b = I.rhs_uniform(L, 4)
+    xs = np.zeros_like(b)
+    xs[idx] = np.linalg.solve(D[np.ix_(idx, idx)], b[idx])
+    np.testing.assert_allclose(O.jacobi(L, A, 0.7, b, xs), xs, rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------------------------------------ transfers
+@pytest.mark.parametrize("Lf,p,q", [(4, 1, 1), (4, 3, 5), (6, 7, 30)])
+def test_restriction_of_modes(Lf, p, q):
+    # full weighting of a fine sin mode = (1+cos(p pi h))(1+cos(q pi h)) x the coarse mode
+    hf = 1.0 / (O.n_of(Lf) - 1)
+    fac = (1 + math.cos(p * math.pi * hf)) * (1 + math.cos(q * math.pi * hf))
+    rc = O.restrict(Lf, sin_mode(Lf, p, q))
+    np.testing.assert_allclose(rc, fac * sin_mode(Lf - 1, p, q), rtol=0, atol=1e-13)
+
+
+def test_restriction_of_constant():
+    Lf = 5
+    rc = O.restrict(Lf, I.interior_mask(Lf).astype(float)).reshape(O.n_of(Lf - 1), -1)
+    np.testing.assert_array_equal(rc[2:-2, 2:-2], 4.0)     # 1 + 4 * 1/2 + 4 * 1/4
+    assert np.all(rc[0, :] == 0) and np.all(rc[:, -1] == 0)
+
+
+def test_prolongation_reproduces_bilinear():
+    Lf = 5
+    nf, nc = O.n_of(Lf), O.n_of(Lf - 1)
+    f = lambda x, y: 0.3 + 1.7 * x - 0.4 * y + 2.2 * x * y
+    Xc, Yc = np.meshgrid(np.linspace(0, 1, nc), np.linspace(0, 1, nc))
+    ec = (f(Xc, Yc) * I.interior_mask(Lf - 1).reshape(nc, nc)).ravel()
+    xf = O.prolong_add(Lf, ec, np.zeros(nf * nf)).reshape(nf, nf)
+    Xf, Yf = np.meshgrid(np.linspace(0, 1, nf), np.linspace(0, 1, nf))
+    np.testing.assert_allclose(xf[2:-2, 2:-2], f(Xf, Yf)[2:-2, 2:-2], rtol=0, atol=1e-14)
+    assert np.all(xf[0, :] == 0) and np.all(xf[:, 0] == 0)
+
+
+def test_restriction_is_adjoint_of_prolongation():
+    Lf = 6
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal(O.N_of(Lf)) * I.interior_mask(Lf)
+    e = rng.standard_normal(O.N_of(Lf - 1)) * I.interior_mask(Lf - 1)
+    lhs = O.restrict(Lf, r) @ e
+    rhs = r @ O.prolong_add(Lf, e, np.zeros(O.N_of(Lf)))
+    assert abs(lhs - rhs) <= 1e-12 * (np.abs(r).sum() + 1)
+
+
+@pytest.mark.parametrize("Lf", [3, 4])
+def test_galerkin_equals_rediscretisation(Lf):
+    # for a = 1, P^T A_f P equals the re-assembled coarse operator
+    Nc = O.N_of(Lf - 1)
+    ic = interior_idx(Lf - 1)
+    P = np.zeros((O.N_of(Lf), ic.size))
+    for c, C in enumerate(ic):
+        e = np.zeros(Nc)
+        e[C] = 1.0
+        P[:, c] = O.prolong_add(Lf, e, np.zeros(O.N_of(Lf)))
+    Af = dense_from_bands(Lf, O.assemble(Lf))
+    Ac = dense_from_bands(Lf - 1, O.assemble(Lf - 1))[np.ix_(ic, ic)]
+    np.testing.assert_allclose(P.T @ Af @ P, Ac, rtol=0, atol=2e-15)
+
+
+def test_coarse_solve_matches_dense():
+    L = 2
+    a = I.lognormal_coef(L, 9)
+    A = O.assemble(L, a)
+    b = I.rhs_uniform(L, 1)
+    idx = interior_idx(L)
+    ref = np.zeros_like(b)
+    ref[idx] = np.linalg.solve(dense_from_bands(L, A)[np.ix_(idx, idx)], b[idx])
+    np.testing.assert_allclose(O.coarse_solve(L, A, b), ref, rtol=1e-14, atol=1e-15)
+
+
+# ------------------------------------------------------------------------------- multigrid
+@pytest.mark.parametrize("L,lognormal", [(3, False), (4, False), (4, True)])
+def test_mg_matches_dense_lu(L, lognormal):
+    a = I.lognormal_coef(L, 21) if lognormal else None
+    A = O.assemble(L, a)
+    b = I.rhs_uniform(L, 22)
+    idx = interior_idx(L)
+    xs = np.zeros_like(b)
+    xs[idx] = np.linalg.solve(dense_from_bands(L, A)[np.ix_(idx, idx)], b[idx])
+    x, st = O.mg_solve(L, b, coef=a, tol=1e-13)
+    assert st["converged"] and st["relres"] <= 1e-13
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-11
+
+
+def test_mg_contraction_level_independent():
+    # Sec. 6.2: two V(2,2) cycles gain (at least) one digit; the rate does not grow with L
+    rates = []
+    for L in (4, 6, 8):
+        _, st, h = O.mg_solve(L, O.load_sinsin(L), tol=1e-12, history=True)
+        r = h[2:6] / h[1:5]
+        rates.append(r.max())
+        assert st["converged"]
+    assert max(rates) < 10 ** -0.5
+    assert max(rates) / min(rates) < 1.5
+
+
+def _golden(name):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, name)) if not l.startswith("#")]
+    return {int(r[0]): float(r[2]) for r in rows}
+
+
+@pytest.mark.slow
+def test_l2_error_reduction_matches_table1():
+    # Table 1: the L2 error falls by 4.00 (+-0.02) per level for L >= 5 in double and mixed
+    # precision.  Our manufactured solution is sin(pi x) sin(pi y) (the paper's polynomial is
+    # unnamed), so only the reduction factors are compared.
+    gd, gm = _golden("table1_double_reduction.txt"), _golden("table1_mixed_reduction.txt")
+    err64, err32 = {}, {}
+    for L in range(4, 10):
+        b = O.load_sinsin(L)
+        x, st = O.mg_solve(L, b, tol=1e-11)
+        err64[L] = O.l2_error_sinsin(L, x)
+        x, st = O.mg_solve(L, b, prec=O.PREC_FP32_DC, tol=1e-11)
+        assert st["converged"]
+        err32[L] = O.l2_error_sinsin(L, x)
+    for L in range(5, 10):
+        assert abs(err64[L - 1] / err64[L] - gd[L]) < 0.05, (L, err64[L - 1] / err64[L])
+        assert abs(err32[L - 1] / err32[L] - gm[L]) < 0.05
+        assert abs(err32[L] / err64[L] - 1) < 0.01        # mixed = double accuracy
+
+
+def test_l2_error_of_zero_and_of_interpolant():
+    # ||sin(pi x) sin(pi y)||_L2 = 1/2; the nodal interpolant's error falls like h^2
+    assert abs(O.l2_error_sinsin(5, np.zeros(O.N_of(5))) - 0.5) < 1e-10
+    e = [O.l2_error_sinsin(L, sin_mode(L, 1, 1)) for L in (4, 5, 6)]
+    assert 3.9 < e[0] / e[1] < 4.1 and 3.9 < e[1] / e[2] < 4.1
+
+
+def test_load_vector_consistent_with_point_values():
+    # b_i / (h^2 f(x_i)) -> 1 at interior nodes (f smooth, basis integrates to h^2)
+    L = 7
+    n = O.n_of(L)
+    h = 1.0 / (n - 1)
+    b = O.load_sinsin(L).reshape(n, n)
+    f = 2 * np.pi ** 2 * sin_mode(L, 1, 1).reshape(n, n)
+    ratio = b[1:-1, 1:-1] / (h * h * f[1:-1, 1:-1])
+    assert np.max(np.abs(ratio - 1)) < 1e-3
+    assert np.all(b[0, :] == 0) and np.all(b[:, -1] == 0)
+
+
+@pytest.mark.parametrize("prec", [O.PREC_FP32_DC, O.PREC_FP16BAND_DC])
+def test_mixed_precision_reaches_fp64_tolerance(prec):
+    L = 7
+    a = I.lognormal_coef(L, 0)
+    b = I.rhs_uniform(L, 1)
+    x, st = O.mg_solve(L, b, coef=a, prec=prec)
+    assert st["converged"] and st["relres"] <= 1e-8
+    r = O.defect(L, O.assemble(L, a), b, x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-8
+    assert st["outer_iters"] >= 2 and st["inner_cycles"] >= st["outer_iters"]
+
+
+def test_fp32_only_loses_accuracy():
+    # Table 1 single-precision column: pure FP32 multigrid stops improving; the error grows again
+    # with the level and falls behind FP64 by more than an order of magnitude
+    errs = {}
+    for L in (7, 9):
+        b = O.load_sinsin(L)
+        x, _ = O.mg_solve(L, b, prec=O.PREC_FP32_ONLY, max_cycles=30)
+        x64, _ = O.mg_solve(L, b)
+        errs[L] = (O.l2_error_sinsin(L, x), O.l2_error_sinsin(L, x64))
+    assert errs[9][0] > errs[7][0]
+    assert errs[9][0] > 10 * errs[9][1]
+
+
+# ------------------------------------------------------------------------- FP16 band storage
+def test_fp16_rne_matches_ieee():
+    rng = np.random.default_rng(1)
+    vals = np.concatenate([
+        rng.standard_normal(2000),
+        rng.standard_normal(500) * 2.0 ** -16,                     # subnormal range
+        rng.uniform(-1, 1, 500) * 60000.0,
+        (1 + np.arange(0, 64) * 2.0 ** -11),                       # exact ties at 1
+        -(2.0 ** -14) * (1 + np.arange(0, 64) * 2.0 ** -11),
+        np.arange(0, 40) * 2.0 ** -25,                              # subnormal ties
+        [0.0, -0.0, 1.0, -1.0, 65504.0, 2.0 ** -24],
+    ])
+    ref = vals.astype(np.float16).view(np.uint16)
+    np.testing.assert_array_equal(O.fp16_rne(vals), ref)
+
+
+def test_quantize_fp16_bands():
+    L = 5
+    A = O.assemble(L, I.lognormal_coef(L, 3))
+    s, codes = O.quantize_fp16(L, A)
+    np.testing.assert_array_equal(s, np.abs(A).max(axis=1).astype(np.float32))
+    dec = codes.view(np.float16).astype(np.float64) * s[:, None].astype(np.float64)
+    np.testing.assert_array_equal(codes, (A / s[:, None].astype(np.float64)).astype(np.float16).view(np.uint16))
+    big = np.abs(A) > 2.0 ** -14 * s[:, None]
+    assert np.all(np.abs(dec - A)[big] <= 2.0 ** -11 * np.abs(A)[big] * (1 + 1e-7))
