@@ -53,6 +53,9 @@ def lib():
         L.or_coarse_solve.argtypes = [ctypes.c_int, dp, dp, dp]
         L.or_coarse_solve.restype = ctypes.c_int
         L.or_quantize_fp16.argtypes = [ctypes.c_int, dp, fp, up]
+        L.or_spmv_rowsum.argtypes = [ctypes.c_int, fp, fp, fp]
+        L.or_defect_f32.argtypes = [ctypes.c_int, fp, fp, fp, fp, ctypes.c_int]
+        L.or_jacobi_f32.argtypes = [ctypes.c_int, fp, ctypes.c_float, fp, fp, fp, ctypes.c_int]
         L.or_mg_solve.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp,
@@ -157,6 +160,42 @@ def quantize_fp16(L, bands):
     codes = np.zeros((9, N_of(L)), dtype=np.uint16)
     lib().or_quantize_fp16(L, _p(_f64(bands)), _p(s, ctypes.c_float), _p(codes, ctypes.c_uint16))
     return s, codes
+
+
+def dequantize_fp16(scales, codes):
+    """Float32 values s_k * float(h) of quantized band arrays."""
+    return codes.view(np.float16).astype(np.float32) * np.asarray(scales, dtype=np.float32)[:, None]
+
+
+def spmv_rowsum(L, deq_bands, x):
+    """FP16-band inner operator in row-sum form on dequantized float32 bands (float arithmetic)."""
+    y = np.zeros(N_of(L), dtype=np.float32)
+    b = np.ascontiguousarray(deq_bands, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    lib().or_spmv_rowsum(L, _p(b, ctypes.c_float), _p(xx, ctypes.c_float), _p(y, ctypes.c_float))
+    return y
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def defect_f32(L, bands, b, x, rowsum):
+    """Float-arithmetic defect b - A x of an inner operator (rowsum: FP16 row-sum form)."""
+    r = np.zeros(N_of(L), dtype=np.float32)
+    fp = ctypes.c_float
+    lib().or_defect_f32(L, _p(_f32(bands), fp), _p(_f32(b), fp), _p(_f32(x), fp), _p(r, fp),
+                        1 if rowsum else 0)
+    return r
+
+
+def jacobi_f32(L, bands, omega, b, x, rowsum):
+    """Float-arithmetic damped Jacobi step of an inner operator."""
+    out = np.zeros(N_of(L), dtype=np.float32)
+    fp = ctypes.c_float
+    lib().or_jacobi_f32(L, _p(_f32(bands), fp), omega, _p(_f32(b), fp), _p(_f32(x), fp),
+                        _p(out, fp), 1 if rowsum else 0)
+    return out
 
 
 def mg_solve(L, b, coef=None, x0=None, prec=PREC_FP64, pre=2, post=2, omega=0.7, tol=1e-8,

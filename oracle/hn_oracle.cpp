@@ -22,8 +22,10 @@
 //  * stopping test ||b - A x||_2 / ||b||_2 <= tol after a complete cycle, x0 given (0 default);
 //  * defect correction: the FP64 defect is scaled by 1/||d|| before the cast to the inner
 //    precision, the inner cycles stop at a relative inner residual <= inner_tol (cap inner_max);
-//  * FP16 band storage: per band k, s_k = (float)max_i |band_k[i]|, code h = fp16_rne(band/s_k)
-//    with the quotient formed in FP64; the inner operator uses (float)(s_k * (float)h) per entry.
+//  * FP16 band storage (row-sum form): the 8 coupling bands and, in slot 4, the row sums
+//    rho_i = sum_k band_k[i]; per array k, s_k = (float)max_i |v_k[i]|, code h = fp16_rne(v/s_k)
+//    with the quotient formed in FP64; entries dequantize to (float)(s_k * (float)h) and the
+//    operator is applied as rho_i x_i + sum_{k != 4} a_k (x_j - x_i) in float arithmetic.
 //
 // Parity is pinned by the tests (closed-form stencil and eigenvalues, independent dense assembly,
 // dense LU, O(h^2) convergence, transfer identities, numpy's float16 rounding).  Nothing here is
@@ -141,12 +143,33 @@ void spmv(int L, const T* bands, const T* x, T* y) {
     }
 }
 
+void spmv_rowsum(int L, const float* bands, const float* x, float* y);
+float rowsum_diag(const float* bands, long N, long i);
+extern thread_local bool g_rowsum_form;
+
+// the inner operator: 9-band product, or the row-sum form for FP16-band storage
+template <typename T>
+void apply_op(int L, const T* bands, const T* x, T* y) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (g_rowsum_form) { spmv_rowsum(L, bands, x, y); return; }
+  }
+  spmv<T>(L, bands, x, y);
+}
+
+template <typename T>
+T diag_of(const T* bands, long N, long i) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (g_rowsum_form) return rowsum_diag(bands, N, i);
+  }
+  return bands[4 * N + i];
+}
+
 // r = b - A x
 template <typename T>
 void defect(int L, const T* bands, const T* b, const T* x, T* r) {
   const long N = N_of(L);
   std::vector<T> ax(N);
-  spmv<T>(L, bands, x, ax.data());
+  apply_op<T>(L, bands, x, ax.data());
   for (long i = 0; i < N; ++i) r[i] = b[i] - ax[i];
 }
 
@@ -164,7 +187,7 @@ void jacobi(int L, const T* bands, T omega, const T* b, const T* x_in, T* x_out)
   const long N = N_of(L);
   std::vector<T> r(N);
   defect<T>(L, bands, b, x_in, r.data());
-  for (long i = 0; i < N; ++i) x_out[i] = x_in[i] + omega * r[i] / bands[4 * N + i];
+  for (long i = 0; i < N; ++i) x_out[i] = x_in[i] + omega * r[i] / diag_of<T>(bands, N, i);
 }
 
 // ------------------------------------------------------------------ grid transfers
@@ -295,17 +318,52 @@ float fp16_to_float(uint16_t h) {
   return (float)(s ? -v : v);
 }
 
-// quantise the 9 bands: scales[k] (float), codes[k*N + i]
+// FP16 band storage in row-sum form.  Bands k != 4 (the 8 couplings) are stored as they are; slot
+// 4 holds the row sum rho_i = sum_k band_k[i] (k = 0..8 in order, FP64) instead of the diagonal.
+// Each of the 9 arrays gets its own scale s_k = float(max_i |v_k[i]|) (1 if all zero) and codes
+// fp16_rne(v_k[i] / s_k), the quotient formed in FP64.
 void quantize_fp16(int L, const double* bands, float* scales, uint16_t* codes) {
   const long N = N_of(L);
+  std::vector<double> rho(N, 0.0);
+  for (long i = 0; i < N; ++i)
+    for (int k = 0; k < 9; ++k) rho[i] += bands[k * N + i];
   for (int k = 0; k < 9; ++k) {
+    const double* v = k == 4 ? rho.data() : bands + k * N;
     double mx = 0.0;
-    for (long i = 0; i < N; ++i) mx = std::fmax(mx, std::fabs(bands[k * N + i]));
+    for (long i = 0; i < N; ++i) mx = std::fmax(mx, std::fabs(v[i]));
     float s = (float)mx;
     if (s == 0.0f) s = 1.0f;
     scales[k] = s;
-    for (long i = 0; i < N; ++i) codes[k * N + i] = fp16_rne(bands[k * N + i] / (double)s);
+    for (long i = 0; i < N; ++i) codes[k * N + i] = fp16_rne(v[i] / (double)s);
   }
+}
+
+// The FP16-band inner operator in row-sum form, float arithmetic (bands: 8 dequantized couplings,
+// slot 4 the dequantized row sum):  (A x)_i = rho_i x_i + sum_{k != 4} a_k[i] (x_j - x_i).  In
+// exact arithmetic with unquantized values this equals the 9-band product; quantization errors
+// of the couplings multiply differences x_j - x_i, so constants stay in the kernel of every row
+// with rho_i = 0.  Its diagonal is rho_i - sum_{k != 4} a_k[i].
+void spmv_rowsum(int L, const float* bands, const float* x, float* y) {
+  const long n = n_of(L), N = N_of(L);
+  for (long iy = 0; iy < n; ++iy)
+    for (long ix = 0; ix < n; ++ix) {
+      const long i = iy * n + ix;
+      float s = bands[4 * N + i] * x[i];
+      for (int k = 0; k < 9; ++k) {
+        if (k == 4) continue;
+        const long jx = ix + band_dx(k), jy = iy + band_dy(k);
+        if (jx < 0 || jy < 0 || jx >= n || jy >= n) continue;
+        s += bands[k * N + i] * (x[jy * n + jx] - x[i]);
+      }
+      y[i] = s;
+    }
+}
+
+float rowsum_diag(const float* bands, long N, long i) {
+  float d = bands[4 * N + i];
+  for (int k = 0; k < 9; ++k)
+    if (k != 4) d -= bands[k * N + i];
+  return d;
 }
 
 // ------------------------------------------------------------------------ the hierarchy
@@ -315,6 +373,10 @@ struct Level {
   std::vector<double> a64;   // bands FP64
   std::vector<float> a32;    // bands of the inner precision (FP32 cast, or FP16 dequantised)
 };
+
+// inner operator form: the FP32 cast bands are applied as 9-band products; the FP16 bands are
+// in row-sum form (set when the hierarchy is built)
+thread_local bool g_rowsum_form = false;
 
 struct Hierarchy {
   std::vector<Level> lev;    // lev[0] = finest
@@ -339,6 +401,7 @@ struct Hierarchy {
         for (int k = 0; k < 9; ++k)
           for (long i = 0; i < v.N; ++i)
             v.a32[k * v.N + i] = s[k] * fp16_to_float(c[k * v.N + i]);
+        g_rowsum_form = true;
       }
       lev.push_back(std::move(v));
       if (coef && l > coarse) {
@@ -418,6 +481,21 @@ float or_fp16_to_float(uint16_t h) { return fp16_to_float(h); }
 void or_quantize_fp16(int L, const double* bands, float* scales, uint16_t* codes) {
   quantize_fp16(L, bands, scales, codes);
 }
+// the FP16-band inner operator (row-sum form) on dequantized float bands
+void or_spmv_rowsum(int L, const float* bands, const float* x, float* y) { spmv_rowsum(L, bands, x, y); }
+// float-arithmetic defect and Jacobi step of an inner operator: rowsum = 1 selects the row-sum
+// form (FP16-band storage), 0 the 9-band product (FP32 bands)
+void or_defect_f32(int L, const float* bands, const float* b, const float* x, float* r, int rowsum) {
+  g_rowsum_form = rowsum != 0;
+  defect<float>(L, bands, b, x, r);
+  g_rowsum_form = false;
+}
+void or_jacobi_f32(int L, const float* bands, float omega, const float* b, const float* x_in,
+                   float* x_out, int rowsum) {
+  g_rowsum_form = rowsum != 0;
+  jacobi<float>(L, bands, omega, b, x_in, x_out);
+  g_rowsum_form = false;
+}
 
 // Multigrid solve.  prec: 0 = FP64 V cycles; 1 = FP64 defect correction with FP32 inner MG;
 // 2 = the same with FP16-band-storage inner MG; 3 = FP32-only MG (the paper's failing
@@ -429,6 +507,7 @@ int or_mg_solve(int L, const double* coef, const double* b, double* x, int prec,
                 double omega, double tol, int max_cycles, int max_outer, double inner_tol,
                 int inner_max, int coarse_L, double* relres_hist, or_stats* st) {
   if (L < coarse_L || coarse_L < 2 || prec < 0 || prec > 3) return -1;
+  g_rowsum_form = false;
   Hierarchy H;
   H.build(L, coef, coarse_L, prec);
   if (!H.cs.ok) return -1;
