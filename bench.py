@@ -1,0 +1,339 @@
+"""Benchmark of the GPU multigrid Poisson solver (one JSON line on rank 0).
+
+Workload: Q1 FEM Poisson on the unit square at level L=10 (1025^2 = 1,050,625 nodes), a = 1, zero
+Dirichlet boundary, b ~ U[-1,1] on interior nodes (seeded), V(2,2) damped Jacobi (omega 0.7),
+coarsest level 2 solved exactly, relative residual 1e-8.  The headline is FP32-inner multigrid
+under FP64 defect correction (inner reduction 1e-2); plain FP64 multigrid is measured on the same
+GPU beside it.  A step is one complete solve to 1e-8 from x = 0 (setup excluded, reported apart).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: per-step CUDA events on the solve stream after W warm-up solves; a 512 MiB buffer is
+written between timed steps (outside the events) to flush the 129 MB L2.  `e2e` repeats the
+measurement through the same C call with host buffers (host->device copy of b and device->host
+copy of x inside the timed region).  `roofline` times the dominant kernel of the headline solve
+with events around each of its launches (a separate profiled pass over K solves), against the
+measured HBM copy bandwidth.  `cpu_baseline` times the FP64 CPU oracle on one full solve of the
+same problem on one host core.  With N > 1 (torchrun) every rank solves its own independent
+problem (weak scaling, no collective on the data path); value = all ranks' DOF / slowest rank.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_BENCH = 10
+TOL = 1e-8
+WORKLOAD = "poisson-q1-L10-const-coef-uniform-rhs"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--level", type=int, default=L_BENCH,
+                    help="refinement level (default 10, the benchmark workload; others for profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed solves only (no e2e, profiled pass or CPU baseline): for ncu captures")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("HN_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def max_over_ranks(v, pg, device=None):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        import torch
+        t = torch.zeros(1, device=device)
+        pg.all_reduce(t)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(L, seed, prec):
+    """The oracle, as it stands, on one host core: one full solve of the bench problem."""
+    import numpy as np
+    import oracle as O
+    from paper_0904_4152_gb300 import inputs as I
+    b = I.rhs_uniform(L, seed)
+    O.lib()
+    t0 = time.perf_counter()
+    x, st = O.mg_solve(L, b, prec=prec, tol=TOL)
+    dt = time.perf_counter() - t0
+    N = ((1 << L) + 1) ** 2
+    return {"value": N / dt, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": "one full %s solve to 1e-8 at L=%d (%d DOF), %.2f s, %d cycles"
+                      % ("FP32-inner DC" if prec == 1 else "FP64 MG", L, N, dt, st["cycles"]),
+            "seconds": dt}
+
+
+def run_reference(args, rank, world, pg):
+    if rank != 0:
+        return
+    import oracle as O
+    O.lib()
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(L_BENCH, 0, 1)
+        if i >= args.warmup:
+            times.append(r["seconds"])
+    N = ((1 << L_BENCH) + 1) ** 2
+    total = sum(times)
+    value = N * len(times) / total
+    line = {"impl": "reference", "metric": "MG Poisson DOF/s to 1e-8 (mixed vs FP64)",
+            "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "L": L_BENCH, "dof": N,
+                                            "prec": "fp32-inner defect correction",
+                                            "solver": "CPU oracle (plain C++), 1 core"},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d full FP32-inner DC solves at L=%d" % (len(times), L_BENCH)},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local, pg):
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    from paper_0904_4152_gb300 import hn, inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        g.build()
+    barrier(pg, dev)
+    hn.lib()
+    L = args.level
+    N = ((1 << L) + 1) ** 2
+    stream = torch.cuda.current_stream(dev)
+    b_host = I.rhs_uniform(L, rank)                       # rank r solves its own problem
+    b = torch.from_numpy(b_host).to(dev)
+    x = torch.zeros(N, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    t0 = time.perf_counter()
+    A = hn.hn_band_create(L)
+    setup_band_s = time.perf_counter() - t0
+    mgs = {}
+    for name, prec in (("mixed", hn.HN_PREC_FP32_DC), ("fp64", hn.HN_PREC_FP64)):
+        mgs[name] = hn.hn_mg_setup(A, prec=prec, stream=stream.cuda_stream)
+    hn.hn_band_destroy(A)
+
+    def timed(mg, steps, warmup):
+        for _ in range(warmup):
+            hn.hn_mg_solve(mg, L, b, x)
+        torch.cuda.synchronize(dev)
+        barrier(pg, dev)
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        stats = None
+        launches = 0
+        for s, e in ev:
+            flush.fill_(1)                                 # evict the L2 between steps
+            s.record(stream)
+            _, stats, status = hn.hn_mg_solve(mg, L, b, x)
+            e.record(stream)
+            assert status == hn.HN_OK, stats
+            launches += hn.hn_mg_last_launches(mg)
+        torch.cuda.synchronize(dev)
+        barrier(pg, dev)
+        torch.cuda.synchronize(dev)
+        ms = [s.elapsed_time(e) for s, e in ev]
+        return ms, stats, launches
+
+    with ClockSampler(local) as clk:
+        ms_mixed, st_mixed, launches = timed(mgs["mixed"], args.steps, args.warmup)
+    ms_fp64, st_fp64, _ = timed(mgs["fp64"], args.steps, args.warmup)
+
+    total_mixed = max_over_ranks(sum(ms_mixed), pg, dev)
+    total_fp64 = max_over_ranks(sum(ms_fp64), pg, dev)
+    value = world * N * args.steps / (total_mixed * 1e-3)
+    fp64_value = world * N * args.steps / (total_fp64 * 1e-3)
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "L": L, "mixed_dof_per_s": value,
+                              "fp64_dof_per_s": fp64_value, "mixed_ms": total_mixed / args.steps,
+                              "fp64_ms": total_fp64 / args.steps, "mixed_cycles": st_mixed["cycles"],
+                              "fp64_cycles": st_fp64["cycles"]}), flush=True)
+        return
+
+    # end to end through the same call with host buffers (pinned)
+    bh = torch.from_numpy(b_host).pin_memory().numpy()
+    xh = torch.zeros(N, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(args.warmup):
+        hn.hn_mg_solve(mgs["mixed"], L, bh, xh)
+    barrier(pg, dev)
+    e2e = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        _, _, status = hn.hn_mg_solve(mgs["mixed"], L, bh, xh)
+        e2e.append(time.perf_counter() - t)
+        assert status == hn.HN_OK
+    e2e_total = max_over_ranks(sum(e2e), pg, dev)
+    e2e_value = world * N * args.steps / e2e_total
+
+    # roofline: events around every launch of the headline solve's kernels (profiled pass)
+    mg = mgs["mixed"]
+    hn.hn_mg_set_profiling(mg, True)
+    for _ in range(args.steps):
+        flush.fill_(1)
+        hn.hn_mg_solve(mg, L, b, x)
+    times = hn.hn_mg_kernel_times(mg)
+    hn.hn_mg_set_profiling(mg, False)
+    tops = [t for t in times if t["bytes_per_launch"] > 0]
+    dom = max(tops, key=lambda t: t["total_ms"])
+    avg_s = dom["total_ms"] / dom["launches"] * 1e-3
+    achieved = dom["bytes_per_launch"] / avg_s / 1e9
+    peak, peak_kind = measured_peak_gbs()
+    by_class = {}
+    for t in times:
+        by_class.setdefault(t["name"], 0.0)
+        by_class[t["name"]] += t["total_ms"]
+    prof_total = sum(by_class.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and L <= 11:
+        cpu = cpu_baseline(L, 0, 1)
+        cpu.pop("seconds")
+
+    if rank == 0:
+        line = {
+            "metric": "MG Poisson DOF/s to 1e-8 (mixed vs FP64)",
+            "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_mixed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if L == L_BENCH else "poisson-q1-L%d-const-coef-uniform-rhs" % L,
+                       "L": L, "dof": N, "coef": "a=1",
+                       "rhs": "U[-1,1] interior, seed=rank", "cycle": "V(2,2) jacobi omega=0.7",
+                       "coarse_L": 2, "tol": TOL, "prec": "fp32-inner defect correction, inner 1e-2",
+                       "l2_between_steps": "flushed (512 MiB write)",
+                       "setup_ms": {"band": 1e3 * setup_band_s,
+                                    "hierarchy_mixed": st_mixed["setup_ns"] / 1e6,
+                                    "hierarchy_fp64": st_fp64["setup_ns"] / 1e6}},
+            "mixed": {"dof_per_s": value, "ms_per_solve": total_mixed / args.steps,
+                      "cycles": st_mixed["cycles"], "outer_iters": st_mixed["outer_iters"],
+                      "relres": st_mixed["relres"]},
+            "fp64": {"dof_per_s": fp64_value, "ms_per_solve": total_fp64 / args.steps,
+                     "cycles": st_fp64["cycles"], "relres": st_fp64["relres"]},
+            "mixed_over_fp64": value / fp64_value,
+            "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": N * 8,
+                    "d2h_bytes_per_step": N * 8},
+            "roofline": {"bound": "hbm", "kernel": "%s L%d" % (dom["name"], dom["level"]),
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "bytes_per_launch": dom["bytes_per_launch"],
+                         "avg_launch_us": avg_s * 1e6, "launches": dom["launches"],
+                         "share_of_profiled": dom["total_ms"] / prof_total if prof_total else None},
+            "kernel_share": {k: v / prof_total for k, v in sorted(by_class.items())} if prof_total else {},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local, pg = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world, pg)
+    else:
+        run_ours(args, rank, world, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/* hn.h -- C ABI of the GB300 multigrid Poisson solver (HONEI paper, arXiv 0904.4152).
+ *
+ * The library solves the Q1 (bilinear, conforming) finite-element discretisation of
+ *     -div(a grad u) = f   on the unit square, zero Dirichlet boundary       (Sec. 2.1)
+ * on a regular grid of refinement level L, i.e. n = 2^L + 1 nodes per side and N = n^2 unknowns
+ * numbered in tensor-product order, node i = iy*n + ix with ix fastest (Sec. 2.1).  The matrix is
+ * assembled fully into 9 bands at fixed positions (Sec. 2.1, Sec. 4.1) and solved by a geometric
+ * multigrid V cycle with damped Jacobi pre/post smoothing and an exact coarse solve, optionally as
+ * the single-precision preconditioner of an FP64 defect-correction loop (Sec. 6.2).  Everything
+ * runs on one GB300 GPU (sm_103a); data crosses the host-device boundary only at these calls.
+ *
+ * Conventions shared by every call:
+ *  - Every function returning hn_status returns HN_OK (0) on success and never exits or aborts,
+ *    also not when device memory runs out (cf. Sec. 4.2, "exits cleanly").  hn_last_error()
+ *    returns a message for the calling thread's last failure.
+ *  - Explicit copy (Sec. 4.1): the library copies every input at call time and never keeps or
+ *    aliases a caller pointer; outputs are written into caller buffers.  Handles are opaque and
+ *    owned by the caller until passed to the matching *_destroy.
+ *  - Vectors have length N over all (2^L+1)^2 nodes including the boundary.  Right-hand-side
+ *    entries on boundary nodes must be 0 (HN_ERR_ARG otherwise); solutions are 0 there.
+ *  - Band layout: 9 bands, k = 0..8 <-> neighbour offset (dy, dx) = (k/3 - 1, k%3 - 1), band-major
+ *    (band k occupies elements [k*N, (k+1)*N)), band_k[i] = A[i, i + dy*n + dx].  An entry is exactly
+ *    0.0 where the neighbour is off the grid or either node lies on the Dirichlet boundary; boundary
+ *    rows are identity rows (diagonal 1.0).
+ *  - Thread safety: a handle is used by one thread at a time; different handles may be used from
+ *    different threads.  hn_mg_solve_batch requires distinct handles.  The server is internally
+ *    synchronised.
+ */
+#ifndef HN_H
+#define HN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HN_OK = 0,
+  HN_ERR_ARG = 1,            /* invalid argument (null pointer, level out of range, bad option) */
+  HN_ERR_OOM = 2,            /* device or host allocation failed */
+  HN_ERR_BUDGET = 3,         /* request exceeds the server's device-memory budget */
+  HN_ERR_CUDA = 4,           /* a CUDA runtime call failed (message in hn_last_error) */
+  HN_ERR_NOT_CONVERGED = 5,  /* cycle / outer-iteration cap reached before the tolerance */
+  HN_ERR_NONFINITE = 6,      /* a norm became NaN or infinite (e.g. non-finite right-hand side) */
+  HN_PENDING = 7,            /* server request accepted but not finished */
+  HN_ERR_TIMEOUT = 8,        /* poll deadline passed */
+  HN_ERR_STATE = 9           /* call not valid in the handle's current state */
+} hn_status;
+
+/* Precision of the solve (Sec. 6.2).  FP64: FP64 V cycles to the tolerance.  FP32_DC: FP64 defect
+ * correction (defect b - A x, update and convergence norm in FP64 on the GPU) preconditioned by
+ * FP32 V cycles (FP32 bands and vectors).  FP16BAND_DC: the same with the inner bands stored in
+ * FP16 with one FP32 scale per band and level (FP32 arithmetic and vectors). */
+typedef enum { HN_PREC_FP64 = 0, HN_PREC_FP32_DC = 1, HN_PREC_FP16BAND_DC = 2 } hn_precision;
+
+typedef struct hn_band hn_band;      /* an assembled fine-level operator (device resident) */
+typedef struct hn_mg hn_mg;          /* a multigrid hierarchy built from an hn_band (device) */
+typedef struct hn_server hn_server;  /* continuous-batching solve server */
+
+#define HN_MIN_LEVEL 2
+#define HN_MAX_LEVEL 14
+
+/* Assemble the Q1 stiffness matrix of -div(a grad u) at level L (HN_MIN_LEVEL..HN_MAX_LEVEL) on
+ * the GPU (Sec. 2.1: full assembly, fixed band positions).  cell_coef: host array of (2^L)^2
+ * per-cell coefficients a > 0, row-major by cell (ey, ex), cell (ex, ey) = [ex h, (ex+1) h] x
+ * [ey h, (ey+1) h]; NULL means a = 1.  Dirichlet nodes are eliminated symmetrically (rows and
+ * columns zeroed, diagonal 1).  *out receives a new handle.  Errors: HN_ERR_ARG (L out of range,
+ * out NULL, a coefficient not finite or <= 0), HN_ERR_OOM, HN_ERR_CUDA. */
+hn_status hn_band_create(int L, const double* cell_coef, hn_band** out);
+
+/* Copy the 9 assembled FP64 bands to host memory: bands_out holds 9*N doubles in the band layout
+ * above.  Errors: HN_ERR_ARG, HN_ERR_CUDA. */
+hn_status hn_band_get(const hn_band* A, double* bands_out);
+
+/* Level L and node count N of an operator (0 for a NULL handle). */
+int hn_band_level(const hn_band* A);
+long long hn_band_nodes(const hn_band* A);
+
+void hn_band_destroy(hn_band* A);
+
+typedef struct {
+  int coarse_L;      /* coarsest level, solved exactly (2; the paper uses CG there, Sec. 6.2) */
+  int pre, post;     /* damped Jacobi steps before / after the coarse correction (2, 2).  pre >= 1,
+                        pre + post even */
+  int max_cycles;    /* cap on V cycles (FP64) or inner cycles in total (DC) (100) */
+  int max_outer;     /* cap on defect-correction updates (50) */
+  int inner_max;     /* cap on inner V cycles per defect-correction step (10) */
+  double omega;      /* Jacobi damping (0.7) */
+  double tol;        /* stop when ||b - A x||_2 / ||b||_2 <= tol, FP64 operator (1e-8) */
+  double inner_tol;  /* inner cycles stop at relative inner residual <= inner_tol (1e-2) */
+  hn_precision prec; /* HN_PREC_FP64 */
+  void* stream;      /* cudaStream_t the solves run on; NULL = the library's own stream */
+} hn_mg_opts;
+
+typedef struct {
+  int cycles;        /* V cycles run (inner cycles in DC modes) */
+  int outer_iters;   /* defect-correction updates applied (0 in FP64 mode) */
+  int inner_cycles;  /* inner V cycles (0 in FP64 mode) */
+  int status;        /* hn_status of this solve */
+  double relres;     /* final ||b - A x|| / ||b|| with the FP64 operator, FP64 arithmetic */
+  long long setup_ns;/* time spent in hn_mg_setup for this hierarchy */
+  long long solve_ns;/* wall time of the solve call (host clock, includes copies) */
+} hn_mg_stats;
+
+void hn_mg_opts_default(hn_mg_opts* opts);
+
+/* Build the multigrid hierarchy of A on the device: coarse operators by re-discretisation with the
+ * coarse cell coefficient equal to the mean of its 4 child cells, inner-precision copies of the
+ * bands (FP32 cast, or FP16 codes with per-band scales), the exact coarse-level solver, and all
+ * work vectors.  A may be destroyed afterwards (its data are copied).  Errors: HN_ERR_ARG (bad
+ * options, A NULL, coarse_L > level of A), HN_ERR_OOM, HN_ERR_CUDA. */
+hn_status hn_mg_setup(const hn_band* A, const hn_mg_opts* opts, hn_mg** out);
+
+/* Solve A x = b to the tolerance (Sec. 6.2).  b: N doubles.  x: N doubles; on entry the initial
+ * guess (ignored and taken as 0 if x_is_guess is 0), on exit the solution.  device_ptrs = 1: b and
+ * x are device pointers (16-byte aligned); 0: host pointers.  stats may be NULL.  Returns HN_OK,
+ * HN_ERR_NOT_CONVERGED (x holds the last iterate), HN_ERR_NONFINITE, HN_ERR_ARG, HN_ERR_CUDA. */
+hn_status hn_mg_solve(hn_mg* mg, const double* b, double* x, int x_is_guess, int device_ptrs,
+                      hn_mg_stats* stats);
+
+/* Solve count independent systems together: one launch per V-cycle phase covers every problem
+ * (persistent kernels over a device work list), the per-iteration launch sequence is a CUDA
+ * graph, and each problem stops on its own.  All handles must share precision, pre, post, omega,
+ * coarse_L and may differ in level and coefficients.  b[j], x[j] as in hn_mg_solve (x zero guess).
+ * stats: count entries or NULL.  Each problem's result is bit-identical to solving it alone.
+ * Returns the first non-OK per-problem status, HN_OK if all converged. */
+hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b,
+                            double* const* x, int device_ptrs, hn_mg_stats* stats);
+
+/* Device bytes held by a hierarchy (bands, vectors, scratch). */
+size_t hn_mg_device_bytes(const hn_mg* mg);
+
+void hn_mg_destroy(hn_mg* mg);
+
+/* ---------------------------------------------------------------- single-kernel entry points
+ * Run one kernel of the solver on one level of a hierarchy, for testing and measurement.  Vectors
+ * are host arrays of N_l elements of the level's storage type: double for the FP64 hierarchy and
+ * for the FP64 fine level of a DC hierarchy (inner = 0), float for the inner levels of a DC
+ * hierarchy (inner = 1).  level is the refinement level l (coarse_L..L).
+ *   HN_OP_SPMV        out = A_l in1
+ *   HN_OP_DEFECT      out = in2 - A_l in1; *norm_out = ||out||_2 (FP64 accumulation)
+ *   HN_OP_JACOBI      out = in1 + omega D^-1 (in2 - A_l in1)     (in1 = x, in2 = rhs)
+ *   HN_OP_JACOBI_ZERO out = omega D^-1 in2                         (the step from x = 0)
+ *   HN_OP_RESTRICT    out (level l-1) = R in1 (level l), R = P^T full weighting
+ *   HN_OP_PROLONG_ADD out (level l) = in2 (level l) + P in1 (level l-1), bilinear
+ *   HN_OP_COARSE      out = A_c^-1 in2 (level = coarse_L)
+ * Errors: HN_ERR_ARG, HN_ERR_STATE (op not available for that precision/level), HN_ERR_CUDA. */
+typedef enum {
+  HN_OP_SPMV = 0, HN_OP_DEFECT = 1, HN_OP_JACOBI = 2, HN_OP_JACOBI_ZERO = 3,
+  HN_OP_RESTRICT = 4, HN_OP_PROLONG_ADD = 5, HN_OP_COARSE = 6
+} hn_op;
+hn_status hn_mg_apply(hn_mg* mg, hn_op op, int level, int inner, const void* in1,
+                      const void* in2, void* out, double* norm_out);
+
+/* Copy the inner-precision bands of one level to the host: FP32 values (9*N_l floats) for an
+ * FP32_DC hierarchy, or FP16 codes (9*N_l uint16) plus the 9 FP32 scales for FP16BAND_DC. */
+hn_status hn_mg_get_inner_bands(const hn_mg* mg, int level, void* bands_out, float* scales_out);
+
+/* -------------------------------------------------------------------------------- serving
+ * A server owns a worker thread and a device-memory budget.  Submitted requests wait in a FIFO
+ * queue; a request is admitted once a slot (max_active) and budget room for its hierarchy are
+ * free.  Admitted requests are solved together: every scheduler iteration runs one V-cycle phase
+ * sequence over all active requests (continuous batching); finished requests leave, free their
+ * memory and let queued requests in.  All requests of a server share precision, pre, post, omega
+ * and coarse_L (taken from the first submit). */
+hn_status hn_server_create(size_t budget_bytes, int max_active, hn_server** out);
+
+/* Queue a solve of level L with cell coefficients (NULL = 1) and right-hand side b (host, N
+ * doubles); both are copied.  *ticket identifies the request.  HN_ERR_BUDGET if the request
+ * alone exceeds the budget; HN_ERR_ARG on bad input. */
+hn_status hn_mg_submit(hn_server* srv, int L, const double* cell_coef, const double* b,
+                       const hn_mg_opts* opts, unsigned long long* ticket);
+
+/* Wait up to timeout_ns (0 = do not wait, < 0 = wait forever) for a request.  HN_PENDING if not
+ * finished (timeout_ns == 0), HN_ERR_TIMEOUT if the deadline passed; otherwise the request's final
+ * status, with x_out (host, N doubles, may be NULL) and stats filled and the request forgotten. */
+hn_status hn_mg_poll(hn_server* srv, unsigned long long ticket, long long timeout_ns,
+                     double* x_out, hn_mg_stats* stats);
+
+typedef struct {
+  long long submitted, completed, active, queued;
+  long long iterations;        /* scheduler iterations run */
+  size_t bytes_in_use, budget;
+} hn_server_info;
+hn_status hn_server_query(hn_server* srv, hn_server_info* info);
+
+/* Stop the worker after finishing active requests; queued requests are dropped. */
+void hn_server_destroy(hn_server* srv);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* hn_last_error(void);
+
+/* Library version string. */
+const char* hn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HN_H */

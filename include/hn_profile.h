@@ -1,0 +1,39 @@
+/* hn_profile.h -- per-kernel timing of the hn solver (measurement support, not part of the
+ * method).  With profiling on, a hierarchy's solves run the V-cycle schedule one iteration per
+ * graph launch with a CUDA event recorded on the solve stream before and after every kernel
+ * launch; elapsed times accumulate per kernel class and level.  Profiling adds a host
+ * synchronisation per iteration and the event nodes, so headline timings are taken with it off.
+ */
+#ifndef HN_PROFILE_H
+#define HN_PROFILE_H
+
+#include "hn.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  char name[24];          /* kernel class: jacobi, jacobi_first, defect, restrict, prolong, coarse,
+                             check, outer_defect, update, control */
+  int level;              /* refinement level the launches worked on (-1: per-problem finest) */
+  long long launches;     /* launches timed */
+  double total_ms;        /* summed event-to-event time */
+  double bytes_per_launch;/* algorithmic DRAM bytes of one launch (unit counts x bytes per node of
+                             the kernel and precision; 0 for control kernels) */
+} hn_kernel_time;
+
+/* Turn per-kernel event timing on (1) or off (0) for later solves of mg; clears the totals. */
+hn_status hn_mg_set_profiling(hn_mg* mg, int enable);
+
+/* Copy up to max accumulated entries (classes x levels with launches > 0); returns the count. */
+int hn_mg_kernel_times(const hn_mg* mg, hn_kernel_time* out, int max);
+
+/* Kernel launches of mg's last single solve (hn_mg_solve): the graph's init kernels plus the
+ * kernels of every loop iteration that ran.  0 before the first solve. */
+long long hn_mg_last_launches(const hn_mg* mg);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HN_PROFILE_H */

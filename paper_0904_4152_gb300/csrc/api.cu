@@ -1,0 +1,378 @@
+// C ABI of the hn library (include/hn.h, include/hn_profile.h): argument checking, explicit copies
+// at the boundary (Sec. 4.1 explicit-copy containers), and dispatch to the engine.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+
+#include "engine.h"
+
+using namespace hn;
+
+namespace {
+
+struct OwnedStream {
+  cudaStream_t s = nullptr;
+  ~OwnedStream() { if (s) cudaStreamDestroy(s); }
+};
+
+// work-list capacities of a single hierarchy
+void exact_caps(const std::vector<hn_mg*>& mgs, std::vector<long long>& caps, long long& fine) {
+  caps.assign(kMaxLevel + 1, 0);
+  fine = 0;
+  for (hn_mg* mg : mgs) {
+    for (int l = mg->coarse; l <= mg->L; ++l) caps[l] += pitch_of(l) / kTile;
+    fine += pitch_of(mg->L) / kTile;
+  }
+}
+
+hn_status ensure_solo(hn_mg* mg) {
+  if (mg->solo) return HN_OK;
+  std::vector<long long> caps;
+  long long fine;
+  exact_caps({mg}, caps, fine);
+  std::unique_ptr<Engine> e(new Engine());
+  HN_TRY(e->create(mg->prm, 1, mg->L, caps, fine, mg->stream));
+  HN_TRY(e->set_members({mg}));
+  mg->solo = e.release();
+  return HN_OK;
+}
+
+// cache of the last batch engine (same hierarchy list -> same work lists and graphs)
+std::mutex g_batch_mu;
+std::vector<hn_mg*> g_batch_key;
+std::unique_ptr<Engine> g_batch_engine;
+
+void forget_batch(hn_mg* mg) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (std::find(g_batch_key.begin(), g_batch_key.end(), mg) != g_batch_key.end()) {
+    g_batch_engine.reset();
+    g_batch_key.clear();
+  }
+}
+
+hn_status copy_in(double* dst, const double* src, long long N, int device_ptrs, cudaStream_t s) {
+  HN_CUDA(cudaMemcpyAsync(dst, src, (size_t)N * 8,
+                          device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  return HN_OK;
+}
+
+hn_status copy_out(double* dst, const double* src, long long N, int device_ptrs, cudaStream_t s) {
+  HN_CUDA(cudaMemcpyAsync(dst, src, (size_t)N * 8,
+                          device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  return HN_OK;
+}
+
+hn_status check_ptr(const void* p, int device_ptrs) {
+  if (!p) return set_error(HN_ERR_ARG, "null vector pointer");
+  if (device_ptrs && (reinterpret_cast<uintptr_t>(p) & 15))
+    return set_error(HN_ERR_ARG, "device vectors must be 16-byte aligned");
+  return HN_OK;
+}
+
+void fill_stats(const hn_mg* mg, const ProbState& st, long long t0, hn_mg_stats* out) {
+  if (!out) return;
+  out->cycles = st.cycles;
+  out->outer_iters = st.outer_iters;
+  out->inner_cycles = st.inner_cycles;
+  out->status = st.status;
+  out->relres = st.relres;
+  out->setup_ns = mg->setup_ns;
+  out->solve_ns = now_ns() - t0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hn_last_error(void) { return hn::last_error(); }
+const char* hn_version(void) { return "hn 0.1 (sm_103a)"; }
+
+hn_status hn_band_create(int L, const double* cell_coef, hn_band** out) {
+  clear_error();
+  if (!out) return set_error(HN_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (L < HN_MIN_LEVEL || L > HN_MAX_LEVEL)
+    return set_error(HN_ERR_ARG, "level %d outside [%d, %d]", L, HN_MIN_LEVEL, HN_MAX_LEVEL);
+  const long long cells = (1LL << L) * (1LL << L);
+  if (cell_coef)
+    for (long long i = 0; i < cells; ++i)
+      if (!(std::isfinite(cell_coef[i]) && cell_coef[i] > 0.0))
+        return set_error(HN_ERR_ARG, "cell coefficient %lld is not a positive finite number", i);
+  std::unique_ptr<hn_band> A(new hn_band());
+  A->L = L;
+  A->n = n_of(L);
+  A->N = N_of(L);
+  A->pitch = pitch_of(L);
+  size_t bytes = 0;
+  auto take = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
+  for (int k = 0; k < 9; ++k) take((size_t)A->pitch * 8);
+  if (cell_coef) take((size_t)cells * 8);
+  bytes += 256;
+  OwnedStream os;
+  HN_CUDA(cudaStreamCreateWithFlags(&os.s, cudaStreamNonBlocking));
+  HN_CUDA(cudaMalloc(&A->mem, bytes));
+  Bump b{static_cast<char*>(A->mem), 0};
+  BandPtrs64 bp{};
+  for (int k = 0; k < 9; ++k) bp.p[k] = A->band[k] = b.take<double>(A->pitch);
+  if (cell_coef) {
+    A->coef = b.take<double>((size_t)cells);
+    HN_CUDA(cudaMemcpyAsync(A->coef, cell_coef, (size_t)cells * 8, cudaMemcpyHostToDevice, os.s));
+  }
+  HN_CUDA(launch_assemble(L, A->coef, bp, nullptr, 1.0, os.s));
+  HN_CUDA(cudaStreamSynchronize(os.s));
+  *out = A.release();
+  return HN_OK;
+}
+
+hn_status hn_band_get(const hn_band* A, double* bands_out) {
+  clear_error();
+  if (!A || !bands_out) return set_error(HN_ERR_ARG, "null argument");
+  for (int k = 0; k < 9; ++k)
+    HN_CUDA(cudaMemcpy(bands_out + (size_t)k * A->N, A->band[k], (size_t)A->N * 8, cudaMemcpyDeviceToHost));
+  return HN_OK;
+}
+
+int hn_band_level(const hn_band* A) { return A ? A->L : 0; }
+long long hn_band_nodes(const hn_band* A) { return A ? A->N : 0; }
+void hn_band_destroy(hn_band* A) { delete A; }
+
+void hn_mg_opts_default(hn_mg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->coarse_L = 2;
+  o->pre = 2;
+  o->post = 2;
+  o->max_cycles = 100;
+  o->max_outer = 50;
+  o->inner_max = 10;
+  o->omega = 0.7;
+  o->tol = 1e-8;
+  o->inner_tol = 1e-2;
+  o->prec = HN_PREC_FP64;
+  o->stream = nullptr;
+}
+
+hn_status hn_mg_setup(const hn_band* A, const hn_mg_opts* opts, hn_mg** out) {
+  clear_error();
+  if (!A || !out) return set_error(HN_ERR_ARG, "null argument");
+  *out = nullptr;
+  hn_mg_opts o;
+  if (opts) o = *opts; else hn_mg_opts_default(&o);
+  HN_TRY(validate_opts(o, A->L));
+  const long long t0 = now_ns();
+  std::unique_ptr<hn_mg> mg(new hn_mg());
+  if (o.stream) {
+    mg->stream = static_cast<cudaStream_t>(o.stream);
+  } else {
+    HN_CUDA(cudaStreamCreateWithFlags(&mg->stream, cudaStreamNonBlocking));
+    mg->own_stream = true;
+  }
+  HN_TRY(build_hierarchy(A, o, mg->stream, mg.get()));
+  mg->setup_ns = now_ns() - t0;
+  *out = mg.release();
+  return HN_OK;
+}
+
+size_t hn_mg_device_bytes(const hn_mg* mg) { return mg ? mg->bytes : 0; }
+
+void hn_mg_destroy(hn_mg* mg) {
+  if (!mg) return;
+  forget_batch(mg);
+  if (mg->stream) cudaStreamSynchronize(mg->stream);
+  delete mg;
+}
+
+hn_status hn_mg_solve(hn_mg* mg, const double* b, double* x, int x_is_guess, int device_ptrs,
+                      hn_mg_stats* stats) {
+  clear_error();
+  if (!mg) return set_error(HN_ERR_ARG, "null hierarchy");
+  HN_TRY(check_ptr(b, device_ptrs));
+  HN_TRY(check_ptr(x, device_ptrs));
+  const long long t0 = now_ns();
+  HN_TRY(ensure_solo(mg));
+  Engine& e = *mg->solo;
+  cudaStream_t s = e.stream();
+  const long long N = N_of(mg->L);
+  ProblemDev& P = mg->host;
+  HN_TRY(copy_in(P.b64, b, N, device_ptrs, s));
+  if (x_is_guess) HN_TRY(copy_in(P.x64, x, N, device_ptrs, s));
+  else HN_CUDA(cudaMemsetAsync(P.x64, 0, (size_t)N * 8, s));
+  HN_TRY(e.start({0}, {x_is_guess ? 1 : 0}));
+  HN_TRY(e.run_to_completion());
+  std::vector<ProbState> st;
+  HN_TRY(e.read_states(st));
+  if (st[0].status != HN_ERR_ARG) {
+    if (st[0].status == HN_OK && st[0].bnorm == 0.0) HN_CUDA(cudaMemsetAsync(P.x64, 0, (size_t)N * 8, s));
+    HN_TRY(copy_out(x, P.x64, N, device_ptrs, s));
+    HN_CUDA(cudaStreamSynchronize(s));
+  }
+  fill_stats(mg, st[0], t0, stats);
+  if (st[0].status == HN_ERR_ARG) return set_error(HN_ERR_ARG, "right-hand side is nonzero on the boundary");
+  if (st[0].status == HN_ERR_NONFINITE) return set_error(HN_ERR_NONFINITE, "non-finite residual norm");
+  if (st[0].status == HN_ERR_NOT_CONVERGED)
+    return set_error(HN_ERR_NOT_CONVERGED, "not converged: relres %.3e after %d cycles", st[0].relres, st[0].cycles);
+  return (hn_status)st[0].status;
+}
+
+hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b, double* const* x,
+                            int device_ptrs, hn_mg_stats* stats) {
+  clear_error();
+  if (!mgs || !b || !x || count < 1) return set_error(HN_ERR_ARG, "bad batch arguments");
+  const long long t0 = now_ns();
+  std::vector<hn_mg*> list(mgs, mgs + count);
+  for (int j = 0; j < count; ++j) {
+    if (!list[j]) return set_error(HN_ERR_ARG, "null hierarchy %d", j);
+    HN_TRY(check_ptr(b[j], device_ptrs));
+    HN_TRY(check_ptr(x[j], device_ptrs));
+    const Params& a = list[0]->prm;
+    const Params& c = list[j]->prm;
+    if (a.prec != c.prec || a.pre != c.pre || a.post != c.post || a.omega != c.omega ||
+        a.coarse != c.coarse)
+      return set_error(HN_ERR_ARG, "batch members must share precision, pre, post, omega, coarse_L");
+    for (int i = 0; i < j; ++i)
+      if (list[i] == list[j]) return set_error(HN_ERR_ARG, "batch members must be distinct");
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (!g_batch_engine || g_batch_key != list) {
+    g_batch_engine.reset();
+    g_batch_key.clear();
+    std::vector<long long> caps;
+    long long fine;
+    exact_caps(list, caps, fine);
+    int Lmax = 0;
+    for (hn_mg* mg : list) Lmax = std::max(Lmax, mg->L);
+    // batch-wide iteration caps: the most generous member's (each problem keeps its own state)
+    Params prm = list[0]->prm;
+    for (hn_mg* mg : list) {
+      prm.max_cycles = std::max(prm.max_cycles, mg->prm.max_cycles);
+      prm.max_outer = std::max(prm.max_outer, mg->prm.max_outer);
+    }
+    std::unique_ptr<Engine> e(new Engine());
+    HN_TRY(e->create(prm, count, Lmax, caps, fine, list[0]->stream));
+    HN_TRY(e->set_members(list));
+    g_batch_engine = std::move(e);
+    g_batch_key = list;
+  }
+  Engine& e = *g_batch_engine;
+  cudaStream_t s = e.stream();
+  std::vector<int> slots(count), guess(count, 0);
+  for (int j = 0; j < count; ++j) {
+    slots[j] = j;
+    ProblemDev& P = list[j]->host;
+    const long long N = N_of(list[j]->L);
+    HN_TRY(copy_in(P.b64, b[j], N, device_ptrs, s));
+    HN_CUDA(cudaMemsetAsync(P.x64, 0, (size_t)N * 8, s));
+  }
+  HN_TRY(e.start(slots, guess));
+  HN_TRY(e.run_to_completion());
+  std::vector<ProbState> st;
+  HN_TRY(e.read_states(st));
+  hn_status first_bad = HN_OK;
+  for (int j = 0; j < count; ++j) {
+    ProblemDev& P = list[j]->host;
+    const long long N = N_of(list[j]->L);
+    if (st[j].status != HN_ERR_ARG) {
+      if (st[j].status == HN_OK && st[j].bnorm == 0.0) HN_CUDA(cudaMemsetAsync(P.x64, 0, (size_t)N * 8, s));
+      HN_TRY(copy_out(x[j], P.x64, N, device_ptrs, s));
+    }
+    if (st[j].status != HN_OK && first_bad == HN_OK) first_bad = (hn_status)st[j].status;
+  }
+  HN_CUDA(cudaStreamSynchronize(s));
+  for (int j = 0; j < count; ++j) fill_stats(list[j], st[j], t0, stats ? stats + j : nullptr);
+  if (first_bad != HN_OK) return set_error(first_bad, "at least one batch member did not converge cleanly");
+  return HN_OK;
+}
+
+hn_status hn_mg_apply(hn_mg* mg, hn_op op, int level, int inner, const void* in1, const void* in2,
+                      void* out, double* norm_out) {
+  clear_error();
+  if (!mg || !out) return set_error(HN_ERR_ARG, "null argument");
+  if (level < mg->coarse || level > mg->L) return set_error(HN_ERR_ARG, "level out of range");
+  const bool p64 = mg->prm.prec == P64;
+  if ((inner != 0) == p64)
+    return set_error(HN_ERR_STATE, "inner=%d does not match the hierarchy precision", inner);
+  if ((op == HN_OP_RESTRICT || op == HN_OP_PROLONG_ADD) && level <= mg->coarse)
+    return set_error(HN_ERR_ARG, "transfer needs a coarser level");
+  if (op == HN_OP_COARSE && level != mg->coarse) return set_error(HN_ERR_ARG, "coarse op on the coarsest level only");
+  if (norm_out && (op != HN_OP_DEFECT || level != mg->L))
+    return set_error(HN_ERR_STATE, "norm only for the defect on the finest level");
+  HN_TRY(ensure_solo(mg));
+  Engine& e = *mg->solo;
+  cudaStream_t s = e.stream();
+  const size_t vs = p64 ? 8 : 4;
+  const LevelDev& d = mg->host.lev[level];
+  const size_t N = (size_t)N_of(level);
+  auto put = [&](void* dst, const void* src, size_t n) -> hn_status {
+    if (!src) return set_error(HN_ERR_ARG, "missing input vector");
+    HN_CUDA(cudaMemcpyAsync(dst, src, n * vs, cudaMemcpyHostToDevice, s));
+    return HN_OK;
+  };
+  const void* result = nullptr;
+  size_t nres = N;
+  HN_TRY(e.set_phase(0, PH_CYCLE, op == HN_OP_JACOBI_ZERO ? 1 : 0));
+  switch (op) {
+    case HN_OP_SPMV: HN_TRY(put(d.x[0], in1, N)); result = d.r; break;
+    case HN_OP_DEFECT: HN_TRY(put(d.x[0], in1, N)); HN_TRY(put(d.rhs, in2, N)); result = d.r; break;
+    case HN_OP_JACOBI: HN_TRY(put(d.x[0], in1, N)); HN_TRY(put(d.rhs, in2, N)); result = d.x[1]; break;
+    case HN_OP_JACOBI_ZERO: HN_TRY(put(d.rhs, in2, N)); result = d.x[1]; break;
+    case HN_OP_RESTRICT: {
+      HN_TRY(put(d.r, in1, N));
+      result = mg->host.lev[level - 1].rhs;
+      nres = (size_t)N_of(level - 1);
+      break;
+    }
+    case HN_OP_PROLONG_ADD:
+      HN_TRY(put(mg->host.lev[level - 1].x[0], in1, (size_t)N_of(level - 1)));
+      HN_TRY(put(d.x[0], in2, N));
+      result = d.x[0];
+      break;
+    case HN_OP_COARSE: HN_TRY(put(d.rhs, in2, N)); result = d.x[0]; break;
+    default: return set_error(HN_ERR_ARG, "unknown op %d", (int)op);
+  }
+  HN_TRY(e.apply(op, level, PH_CYCLE, s));
+  HN_CUDA(cudaMemcpyAsync(out, result, nres * vs, cudaMemcpyDeviceToHost, s));
+  HN_CUDA(cudaStreamSynchronize(s));
+  if (norm_out) {
+    std::vector<ProbState> st;
+    HN_TRY(e.set_phase(0, PH_CHECK, 0));
+    HN_TRY(e.apply_check_norm(s));
+    HN_TRY(e.read_states(st));
+    *norm_out = st[0].dnorm;
+  }
+  return HN_OK;
+}
+
+hn_status hn_mg_get_inner_bands(const hn_mg* mg, int level, void* bands_out, float* scales_out) {
+  clear_error();
+  if (!mg || !bands_out) return set_error(HN_ERR_ARG, "null argument");
+  if (mg->prm.prec == P64) return set_error(HN_ERR_STATE, "FP64 hierarchy has no inner bands");
+  if (level < mg->coarse || level > mg->L) return set_error(HN_ERR_ARG, "level out of range");
+  const LevelDev& d = mg->host.lev[level];
+  const size_t N = (size_t)N_of(level), es = mg->prm.prec == P32 ? 4 : 2;
+  for (int k = 0; k < 9; ++k)
+    HN_CUDA(cudaMemcpy(static_cast<char*>(bands_out) + k * N * es, d.band[k], N * es, cudaMemcpyDeviceToHost));
+  if (scales_out)
+    for (int k = 0; k < 9; ++k) scales_out[k] = d.scale[k];
+  return HN_OK;
+}
+
+hn_status hn_mg_set_profiling(hn_mg* mg, int enable) {
+  clear_error();
+  if (!mg) return set_error(HN_ERR_ARG, "null hierarchy");
+  HN_TRY(ensure_solo(mg));
+  mg->solo->set_profiling(enable != 0);
+  return HN_OK;
+}
+
+long long hn_mg_last_launches(const hn_mg* mg) {
+  return (mg && mg->solo) ? mg->solo->last_launches() : 0;
+}
+
+int hn_mg_kernel_times(const hn_mg* mg, hn_kernel_time* out, int max) {
+  if (!mg || !mg->solo) return 0;
+  return mg->solo->kernel_times(out, max);
+}
+
+}  // extern "C"

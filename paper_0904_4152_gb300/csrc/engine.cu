@@ -1,0 +1,758 @@
+// Host-side engine: hierarchy construction (Sec. 2.1 assembly per level, Sec. 6.2 multigrid
+// hierarchy) and the batch engine that runs the V-cycle schedule of Sec. 6.2 over any set of
+// hierarchies as CUDA graphs.
+//
+// Schedule.  Problems of different finest levels are aligned by absolute level: the launch for
+// "level l" covers every problem that has a level l, problems whose finest level is l start their
+// cycle there.  One iteration of the schedule is: [FP64 outer defect -> control] -> V cycle over
+// levels Lmax..coarse..Lmax -> fine-level residual norm -> control [-> update -> control].  A
+// per-problem state machine on the device decides, from the deterministic per-problem norms, what
+// each problem does next, so the host never waits inside a solve: a closed-world solve is one
+// graph launch whose body is a device-side while loop (graph conditional node) that ends when
+// every problem is done.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "engine.h"
+
+namespace hn {
+
+// ---------------------------------------------------------------------------- error messages
+namespace {
+thread_local std::string t_err;
+}
+
+hn_status set_error(hn_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return st;
+}
+void clear_error() { t_err.clear(); }
+const char* last_error() { return t_err.c_str(); }
+
+int sm_count() {
+  static int cached = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      cached = v;
+    if (cached <= 0) cached = 1;
+  });
+  return cached;
+}
+
+// ----------------------------------------------------------------------------- hierarchy
+namespace {
+
+struct LevelLayout {
+  long long pitch, halo;
+};
+
+size_t vec_elems(int l) { return (size_t)(pitch_of(l) + 2 * halo_of(l)); }
+
+template <class F>
+void walk_layout(int L, int coarse, int prec, F&& take) {
+  // take(bytes) is called for every piece in construction order
+  const size_t vs = prec == P64 ? 8 : 4;
+  const size_t bs = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
+  for (int l = L; l >= coarse; --l) {
+    for (int v = 0; v < 4; ++v) take(vec_elems(l) * vs);
+    for (int k = 0; k < 9; ++k) take((size_t)pitch_of(l) * bs);
+    if (prec == P64) take((size_t)pitch_of(l) * 8);
+  }
+  if (prec != P64) {
+    for (int k = 0; k < 9; ++k) take((size_t)pitch_of(L) * 8);
+    take(vec_elems(L) * 8);
+    take(vec_elems(L) * 8);
+  }
+  const long long m = ((1LL << coarse) - 1) * ((1LL << coarse) - 1);
+  take((size_t)(m * m) * 8);
+}
+
+// dense inverse of an SPD matrix by Gauss-Jordan elimination with partial pivoting (FP64)
+bool invert(std::vector<double>& a, int m) {
+  std::vector<double> inv((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) inv[(size_t)i * m + i] = 1.0;
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(a[(size_t)r * m + c]) > std::fabs(a[(size_t)piv * m + c])) piv = r;
+    if (!(std::fabs(a[(size_t)piv * m + c]) > 0.0)) return false;
+    if (piv != c)
+      for (int k = 0; k < m; ++k) {
+        std::swap(a[(size_t)c * m + k], a[(size_t)piv * m + k]);
+        std::swap(inv[(size_t)c * m + k], inv[(size_t)piv * m + k]);
+      }
+    const double d = a[(size_t)c * m + c];
+    for (int k = 0; k < m; ++k) { a[(size_t)c * m + k] /= d; inv[(size_t)c * m + k] /= d; }
+    for (int r = 0; r < m; ++r) {
+      if (r == c) continue;
+      const double f = a[(size_t)r * m + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < m; ++k) {
+        a[(size_t)r * m + k] -= f * a[(size_t)c * m + k];
+        inv[(size_t)r * m + k] -= f * inv[(size_t)c * m + k];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
+struct TempDev {
+  void* p = nullptr;
+  ~TempDev() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+size_t hierarchy_bytes(int L, int coarse, int prec) {
+  size_t off = 0;
+  walk_layout(L, coarse, prec, [&](size_t b) { off = ((off + 255) & ~size_t(255)) + b; });
+  return off + 256;
+}
+
+Params params_from(const hn_mg_opts& o) {
+  Params p{};
+  p.prec = o.prec == HN_PREC_FP64 ? P64 : (o.prec == HN_PREC_FP32_DC ? P32 : P16);
+  p.pre = o.pre;
+  p.post = o.post;
+  p.coarse = o.coarse_L;
+  p.max_cycles = o.max_cycles;
+  p.max_outer = o.max_outer;
+  p.inner_max = o.inner_max;
+  p.omega = o.omega;
+  p.tol = o.tol;
+  p.inner_tol = o.inner_tol;
+  return p;
+}
+
+hn_status validate_opts(const hn_mg_opts& o, int L) {
+  if (o.prec != HN_PREC_FP64 && o.prec != HN_PREC_FP32_DC && o.prec != HN_PREC_FP16BAND_DC)
+    return set_error(HN_ERR_ARG, "unknown precision %d", (int)o.prec);
+  if (o.coarse_L < HN_MIN_LEVEL || o.coarse_L > kMaxCoarse)
+    return set_error(HN_ERR_ARG, "coarse_L must be in [%d, %d]", HN_MIN_LEVEL, kMaxCoarse);
+  if (L >= 0 && o.coarse_L > L) return set_error(HN_ERR_ARG, "coarse_L %d > level %d", o.coarse_L, L);
+  if (o.pre < 1 || o.post < 0 || ((o.pre + o.post) & 1) || o.pre + o.post > 64)
+    return set_error(HN_ERR_ARG, "need pre >= 1, post >= 0, pre + post even and <= 64");
+  if (!(o.omega > 0.0 && o.omega < 2.0)) return set_error(HN_ERR_ARG, "omega must be in (0, 2)");
+  if (!(o.tol >= 0.0) || !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
+    return set_error(HN_ERR_ARG, "need tol >= 0 and 0 < inner_tol < 1");
+  if (o.max_cycles < 1 || o.max_outer < 1 || o.inner_max < 1 || o.max_cycles > 100000 ||
+      o.max_outer > 100000 || o.inner_max > 100000)
+    return set_error(HN_ERR_ARG, "iteration caps must be in [1, 100000]");
+  return HN_OK;
+}
+
+hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s, hn_mg* mg) {
+  const int L = A->L, c = o.coarse_L;
+  const Params prm = params_from(o);
+  const int prec = prm.prec;
+  mg->L = L;
+  mg->coarse = c;
+  mg->opts = o;
+  mg->prm = prm;
+  const long long ni = (1LL << c) - 1;
+  mg->m = (int)(ni * ni);
+  mg->bytes = hierarchy_bytes(L, c, prec);
+  HN_CUDA(cudaMalloc(&mg->mem, mg->bytes));
+  HN_CUDA(cudaMemsetAsync(mg->mem, 0, mg->bytes, s));
+
+  ProblemDev& P = mg->host;
+  std::memset(&P, 0, sizeof P);
+  P.L = L;
+  P.coarse = c;
+  P.m = mg->m;
+  Bump b{static_cast<char*>(mg->mem), 0};
+  const size_t vsz = prec == P64 ? 8 : 4;
+  for (int l = L; l >= c; --l) {
+    LevelDev& d = P.lev[l];
+    d.L = l;
+    d.n = (int)n_of(l);
+    d.pitch = (int)pitch_of(l);
+    const long long H = halo_of(l);
+    void* vecs[4];
+    for (int v = 0; v < 4; ++v) {
+      char* base = b.take<char>(vec_elems(l) * vsz);
+      vecs[v] = base + H * vsz;
+    }
+    d.x[0] = vecs[0];
+    d.x[1] = vecs[1];
+    d.rhs = vecs[2];
+    d.r = vecs[3];
+    for (int k = 0; k < 9; ++k) {
+      if (prec == P64) d.band[k] = b.take<double>(d.pitch);
+      else if (prec == P32) d.band[k] = b.take<float>(d.pitch);
+      else d.band[k] = b.take<__half>(d.pitch);
+    }
+    for (int k = 0; k < 9; ++k) d.scale[k] = 1.0f;
+    if (prec == P64) d.wdinv = b.take<double>(d.pitch);
+  }
+  if (prec != P64) {
+    for (int k = 0; k < 9; ++k) P.band64[k] = b.take<double>(pitch_of(L));
+    P.x64 = b.take<double>(vec_elems(L)) + halo_of(L);
+    P.b64 = b.take<double>(vec_elems(L)) + halo_of(L);
+  } else {
+    for (int k = 0; k < 9; ++k) P.band64[k] = static_cast<const double*>(P.lev[L].band[k]);
+    P.x64 = static_cast<double*>(P.lev[L].x[0]);
+    P.b64 = static_cast<double*>(P.lev[L].rhs);
+  }
+  double* cinv = b.take<double>((size_t)mg->m * mg->m);
+  P.cinv = cinv;
+  if (b.off > mg->bytes) return set_error(HN_ERR_STATE, "hierarchy layout overflow");
+
+  // temporaries: coefficients of two consecutive levels, FP64 bands of one coarse level,
+  // FP16 scale reduction words
+  const long long cells_L = (1LL << L) * (1LL << L);
+  const size_t coef_bytes = A->coef ? (size_t)(cells_L + cells_L / 4 + 64) * 8 : 0;
+  const size_t tmpband_bytes = (prec != P64 && L > c) ? (size_t)9 * pitch_of(L - 1) * 8 + 9 * 256 : 0;
+  TempDev tmp;
+  const size_t tmp_bytes = coef_bytes + tmpband_bytes + 1024;
+  HN_CUDA(cudaMalloc(&tmp.p, tmp_bytes));
+  Bump tb{static_cast<char*>(tmp.p), 0};
+  double* coef_a = A->coef ? tb.take<double>((size_t)cells_L) : nullptr;
+  double* coef_b = A->coef ? tb.take<double>((size_t)(cells_L / 4 + 1)) : nullptr;
+  double* tband[9] = {};
+  if (tmpband_bytes)
+    for (int k = 0; k < 9; ++k) tband[k] = tb.take<double>(pitch_of(L - 1));
+  unsigned long long* absmax = tb.take<unsigned long long>(9);
+  float* dscales = tb.take<float>(9);
+
+  if (A->coef) HN_CUDA(cudaMemcpyAsync(coef_a, A->coef, (size_t)cells_L * 8, cudaMemcpyDeviceToDevice, s));
+  const double* coef_cur = A->coef ? coef_a : nullptr;
+  std::vector<double> coarse64((size_t)9 * pitch_of(c));
+  for (int l = L; l >= c; --l) {
+    LevelDev& d = P.lev[l];
+    // FP64 bands of level l
+    BandPtrs64 b64{};
+    if (l == L) {
+      double* dst[9];
+      for (int k = 0; k < 9; ++k) dst[k] = const_cast<double*>(P.band64[k]);
+      for (int k = 0; k < 9; ++k)
+        HN_CUDA(cudaMemcpyAsync(dst[k], A->band[k], (size_t)pitch_of(L) * 8, cudaMemcpyDeviceToDevice, s));
+      for (int k = 0; k < 9; ++k) b64.p[k] = dst[k];
+      if (prec == P64) {
+        // the fine level also needs omega / diag: reassemble writes identical bands plus it
+        HN_CUDA(launch_assemble(l, coef_cur, b64, const_cast<double*>(d.wdinv), o.omega, s));
+      }
+    } else if (prec == P64) {
+      for (int k = 0; k < 9; ++k) b64.p[k] = static_cast<double*>(const_cast<void*>(d.band[k]));
+      HN_CUDA(launch_assemble(l, coef_cur, b64, const_cast<double*>(d.wdinv), o.omega, s));
+    } else {
+      for (int k = 0; k < 9; ++k) b64.p[k] = tband[k];
+      HN_CUDA(launch_assemble(l, coef_cur, b64, nullptr, o.omega, s));
+    }
+    BandPtrs64c src{};
+    for (int k = 0; k < 9; ++k) src.p[k] = b64.p[k];
+    if (prec == P32) {
+      BandPtrs32 dst{};
+      for (int k = 0; k < 9; ++k) dst.p[k] = static_cast<float*>(const_cast<void*>(d.band[k]));
+      HN_CUDA(launch_band_to_f32(l, src, dst, s));
+    } else if (prec == P16) {
+      BandPtrs16 dst{};
+      for (int k = 0; k < 9; ++k) dst.p[k] = static_cast<__half*>(const_cast<void*>(d.band[k]));
+      HN_CUDA(launch_band_to_f16(l, src, absmax, dst, dscales, s));
+      float hs[9];
+      HN_CUDA(cudaMemcpyAsync(hs, dscales, sizeof hs, cudaMemcpyDeviceToHost, s));
+      HN_CUDA(cudaStreamSynchronize(s));
+      for (int k = 0; k < 9; ++k) d.scale[k] = hs[k];
+    }
+    if (l == c) {
+      for (int k = 0; k < 9; ++k)
+        HN_CUDA(cudaMemcpyAsync(coarse64.data() + (size_t)k * pitch_of(c), src.p[k],
+                                (size_t)pitch_of(c) * 8, cudaMemcpyDeviceToHost, s));
+    }
+    if (l > c && coef_cur) {
+      double* next = (coef_cur == coef_a) ? coef_b : coef_a;
+      HN_CUDA(launch_coarsen_coef(l, coef_cur, next, s));
+      coef_cur = next;
+    }
+  }
+  HN_CUDA(cudaStreamSynchronize(s));
+  // exact coarse solver: inverse of the interior block of the coarsest operator
+  {
+    const long long n = n_of(c), pc = pitch_of(c);
+    const int m = mg->m;
+    std::vector<double> a((size_t)m * m, 0.0);
+    for (long long iy = 1; iy < n - 1; ++iy)
+      for (long long ix = 1; ix < n - 1; ++ix) {
+        const long long I = (iy - 1) * ni + (ix - 1);
+        for (int k = 0; k < 9; ++k) {
+          const long long jx = ix + (k % 3 - 1), jy = iy + (k / 3 - 1);
+          if (jx <= 0 || jy <= 0 || jx >= n - 1 || jy >= n - 1) continue;
+          const long long J = (jy - 1) * ni + (jx - 1);
+          a[(size_t)(I * m + J)] = coarse64[(size_t)k * pc + iy * n + ix];
+        }
+      }
+    if (!invert(a, m)) return set_error(HN_ERR_STATE, "coarse matrix is singular");
+    HN_CUDA(cudaMemcpyAsync(cinv, a.data(), a.size() * 8, cudaMemcpyHostToDevice, s));
+    HN_CUDA(cudaStreamSynchronize(s));
+  }
+  return HN_OK;
+}
+
+// ------------------------------------------------------------------------------- engine
+Engine::~Engine() {
+  destroy_graphs();
+  for (auto& m : marks_) { cudaEventDestroy(m.b); cudaEventDestroy(m.e); }
+  if (mem_) cudaFree(mem_);
+  if (hActive_) cudaFreeHost(hActive_);
+}
+
+void Engine::destroy_graphs() {
+  if (gSolve_) cudaGraphExecDestroy(gSolve_);
+  if (gInit_) cudaGraphExecDestroy(gInit_);
+  if (gIter_) cudaGraphExecDestroy(gIter_);
+  gSolve_ = gInit_ = gIter_ = nullptr;
+  graphsValid_ = false;
+}
+
+int Engine::grid_for(long long tiles) const {
+  const long long warps_per_cta = 8;
+  long long g = (tiles + warps_per_cta - 1) / warps_per_cta;
+  if (g < 1) g = 1;
+  if (g > maxGrid_) g = maxGrid_;
+  return (int)g;
+}
+
+hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector<long long>& tiles_cap,
+                         long long fine_cap, cudaStream_t s) {
+  prm_ = prm;
+  cap_ = cap;
+  Lmax_ = Lmax;
+  s_ = s;
+  maxGrid_ = sm_count() * 4;
+  size_t bytes = 0;
+  auto take = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
+  take(sizeof(ProblemDev) * cap);
+  take(sizeof(ProbState) * cap);
+  take(sizeof(int) * cap);
+  take(sizeof(int) * (kMaxLevel + 2));
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    itemCap_[l] = l < (int)tiles_cap.size() ? tiles_cap[l] : 0;
+    take(sizeof(int2) * (size_t)std::max<long long>(itemCap_[l], 1));
+  }
+  fineCap_ = fine_cap;
+  take(sizeof(int2) * (size_t)std::max<long long>(fine_cap, 1));
+  take(sizeof(double) * (size_t)std::max<long long>(fine_cap, 1));
+  take(sizeof(double) * (size_t)std::max<long long>(fine_cap, 1));
+  take(sizeof(unsigned));
+  bytes += 256;
+  HN_CUDA(cudaMalloc(&mem_, bytes));
+  HN_CUDA(cudaMemsetAsync(mem_, 0, bytes, s_));
+  Bump b{static_cast<char*>(mem_), 0};
+  dP_ = b.take<ProblemDev>(cap);
+  dS_ = b.take<ProbState>(cap);
+  dFineOff_ = b.take<int>(cap);
+  dCounts_ = b.take<int>(kMaxLevel + 2);
+  for (int l = 0; l <= kMaxLevel; ++l) dItems_[l] = b.take<int2>((size_t)std::max<long long>(itemCap_[l], 1));
+  dFine_ = b.take<int2>((size_t)std::max<long long>(fine_cap, 1));
+  double* part = b.take<double>((size_t)std::max<long long>(fine_cap, 1));
+  double* part2 = b.take<double>((size_t)std::max<long long>(fine_cap, 1));
+  unsigned* iter = b.take<unsigned>(1);
+  HN_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&hActive_), sizeof(unsigned), cudaHostAllocMapped));
+  *hActive_ = 0;
+  unsigned* dActive = nullptr;
+  HN_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dActive), hActive_, 0));
+  E_.P = dP_;
+  E_.S = dS_;
+  E_.fine_off = dFineOff_;
+  E_.partial = part;
+  E_.partial2 = part2;
+  E_.nprob = cap;
+  E_.prm = prm;
+  E_.active_host = dActive;
+  E_.iter = iter;
+  E_.iter_limit = (unsigned)(prm.max_cycles + prm.max_outer + 8);
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    lists_[l] = TileList{dItems_[l], dCounts_ + l};
+    grid_[l] = grid_for(itemCap_[l]);
+  }
+  fine_ = TileList{dFine_, dCounts_ + kMaxLevel + 1};
+  fineGrid_ = grid_for(fine_cap);
+  hCounts_.assign(kMaxLevel + 2, 0);
+  members_.assign(cap, nullptr);
+  return HN_OK;
+}
+
+hn_status Engine::set_members(const std::vector<hn_mg*>& slots) {
+  if ((int)slots.size() > cap_) return set_error(HN_ERR_ARG, "too many problems for the engine");
+  std::vector<std::vector<int2>> items(kMaxLevel + 1);
+  std::vector<int2> fine;
+  std::vector<int> fine_off(cap_, 0);
+  std::vector<ProblemDev> probs(cap_);
+  std::memset(probs.data(), 0, sizeof(ProblemDev) * cap_);
+  for (int p = 0; p < (int)slots.size(); ++p) {
+    hn_mg* mg = slots[p];
+    if (!mg) continue;
+    if (mg->L > Lmax_) return set_error(HN_ERR_ARG, "level %d above the engine's %d", mg->L, Lmax_);
+    probs[p] = mg->host;
+    for (int l = mg->coarse; l <= mg->L; ++l) {
+      const int nt = (int)(pitch_of(l) / kTile);
+      for (int t = 0; t < nt; ++t) items[l].push_back(make_int2(p, t));
+    }
+    fine_off[p] = (int)fine.size();
+    const int nt = (int)(pitch_of(mg->L) / kTile);
+    for (int t = 0; t < nt; ++t) fine.push_back(make_int2(p, t));
+  }
+  for (int l = 0; l <= kMaxLevel; ++l)
+    if ((long long)items[l].size() > itemCap_[l])
+      return set_error(HN_ERR_ARG, "work list of level %d exceeds the engine capacity", l);
+  if ((long long)fine.size() > fineCap_) return set_error(HN_ERR_ARG, "fine work list exceeds capacity");
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    hCounts_[l] = (int)items[l].size();
+    if (!items[l].empty())
+      HN_CUDA(cudaMemcpyAsync(dItems_[l], items[l].data(), items[l].size() * sizeof(int2),
+                              cudaMemcpyHostToDevice, s_));
+  }
+  hCounts_[kMaxLevel + 1] = (int)fine.size();
+  if (!fine.empty())
+    HN_CUDA(cudaMemcpyAsync(dFine_, fine.data(), fine.size() * sizeof(int2), cudaMemcpyHostToDevice, s_));
+  HN_CUDA(cudaMemcpyAsync(dCounts_, hCounts_.data(), hCounts_.size() * sizeof(int), cudaMemcpyHostToDevice, s_));
+  HN_CUDA(cudaMemcpyAsync(dFineOff_, fine_off.data(), fine_off.size() * sizeof(int), cudaMemcpyHostToDevice, s_));
+  HN_CUDA(cudaMemcpyAsync(dP_, probs.data(), sizeof(ProblemDev) * cap_, cudaMemcpyHostToDevice, s_));
+  members_ = slots;
+  members_.resize(cap_, nullptr);
+  return HN_OK;
+}
+
+hn_status Engine::start(const std::vector<int>& slots, const std::vector<int>& have_guess) {
+  for (size_t q = 0; q < slots.size(); ++q) {
+    ProbState st;
+    std::memset(&st, 0, sizeof st);
+    st.phase = PH_INIT;
+    st.status = HN_PENDING;
+    const int g = q < have_guess.size() ? have_guess[q] : 0;
+    st.zero_top = g ? 0 : 1;
+    st.x_zero = g ? 0 : 1;
+    st.s = 1.0;
+    HN_CUDA(cudaMemcpyAsync(dS_ + slots[q], &st, sizeof st, cudaMemcpyHostToDevice, s_));
+  }
+  // the iteration counter restarts with every closed-world solve (serving keeps counting and
+  // relies on per-problem caps; its limit is set out of reach)
+  HN_CUDA(cudaMemsetAsync(E_.iter, 0, sizeof(unsigned), s_));
+  return HN_OK;
+}
+
+hn_status Engine::set_phase(int slot, int phase, int zero_top) {
+  ProbState st;
+  std::memset(&st, 0, sizeof st);
+  st.phase = phase;
+  st.status = HN_PENDING;
+  st.zero_top = zero_top;
+  st.x_zero = zero_top;
+  st.s = 1.0;
+  HN_CUDA(cudaMemcpyAsync(dS_ + slot, &st, sizeof st, cudaMemcpyHostToDevice, s_));
+  return HN_OK;
+}
+
+long long Engine::launch_bytes(int cls, int level) const {
+  // algorithmic DRAM bytes of one launch: nodes of the level summed over members x bytes per node
+  long long nodes = 0;
+  for (hn_mg* mg : members_) {
+    if (!mg) continue;
+    const int lv = level < 0 ? mg->L : level;
+    if (lv < mg->coarse || lv > mg->L) continue;
+    nodes += N_of(lv);
+  }
+  const int prec = prm_.prec;
+  const double vb = prec == P64 ? 8 : 4;
+  const double bb = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
+  const double wd = prec == P64 ? 8 : 0;   // stored omega/diag (FP64 hierarchy only)
+  double per = 0;
+  switch (cls) {
+    case KC_JACOBI: per = 9 * bb + 3 * vb + wd; break;
+    case KC_JACOBI_FIRST: per = 9 * bb + 3 * vb + wd; break;   // top level with a nonzero iterate
+    case KC_DEFECT: per = 9 * bb + 3 * vb; break;
+    case KC_CHECK: per = 9 * bb + 2 * vb; break;
+    case KC_RESTRICT: per = 1.25 * vb; break;                   // per fine node
+    case KC_PROLONG: per = 2.25 * vb; break;                    // per fine node
+    case KC_OUTER_DEFECT: per = 72 + 8 + 8 + 4; break;
+    case KC_UPDATE: per = 4 + 8 + 8; break;
+    default: per = 0; break;
+  }
+  return (long long)(per * (double)nodes);
+}
+
+hn_status Engine::mark(cudaStream_t s, int cls, int level, bool begin) {
+  if (!profiling_) return HN_OK;
+  if (begin) {
+    cudaEvent_t e;
+    HN_CUDA(cudaEventCreate(&e));
+    HN_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    openBegin_.push_back(e);
+  } else {
+    cudaEvent_t e;
+    HN_CUDA(cudaEventCreate(&e));
+    HN_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    Mark m{openBegin_.back(), e, cls, level, launch_bytes(cls, level)};
+    openBegin_.pop_back();
+    marks_.push_back(m);
+  }
+  return HN_OK;
+}
+
+#define HN_LAUNCH(cls, level, call)        \
+  do {                                     \
+    HN_TRY(mark(s, cls, level, true));     \
+    HN_CUDA(call);                         \
+    ++counting_;                           \
+    HN_TRY(mark(s, cls, level, false));    \
+  } while (0)
+#define HN_LAUNCH0(call) \
+  do {                   \
+    HN_CUDA(call);       \
+    ++counting_;         \
+  } while (0)
+
+hn_status Engine::issue_vcycle(cudaStream_t s, int want) {
+  const int c = prm_.coarse, pre = prm_.pre, post = prm_.post;
+  for (int l = Lmax_; l > c; --l) {
+    HN_LAUNCH(KC_JACOBI_FIRST, l, launch_jacobi(E_, lists_[l], l, want, 0, 1, grid_[l], s));
+    for (int sw = 2; sw <= pre; ++sw)
+      HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (sw - 1) & 1, 0, grid_[l], s));
+    HN_LAUNCH(KC_DEFECT, l, launch_defect(E_, lists_[l], l, want, pre & 1, grid_[l], s));
+    HN_LAUNCH(KC_RESTRICT, l, launch_restrict(E_, lists_[l - 1], l, want, grid_[l - 1], s));
+  }
+  HN_LAUNCH(KC_COARSE, c, launch_coarse(E_, lists_[c], want, grid_[c], s));
+  for (int l = c + 1; l <= Lmax_; ++l) {
+    HN_LAUNCH(KC_PROLONG, l, launch_prolong(E_, lists_[l], l, want, pre & 1, grid_[l], s));
+    for (int sw = 1; sw <= post; ++sw)
+      HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (pre + sw - 1) & 1, 0, grid_[l], s));
+  }
+  return HN_OK;
+}
+
+hn_status Engine::issue_init(cudaStream_t s, cudaGraphConditionalHandle h, int use_h) {
+  HN_LAUNCH0(launch_boundary_check(E_, s));
+  HN_LAUNCH0(launch_norm_b(E_, fine_, fineGrid_, s));
+  HN_LAUNCH0(launch_control(E_, CTRL_INIT, s));
+  if (prm_.prec == P64) {
+    HN_LAUNCH0(launch_check(E_, fine_, PH_CHECK, 0, fineGrid_, s));
+    HN_LAUNCH0(launch_control(E_, CTRL_CHECK0, s));
+  }
+  HN_LAUNCH0(launch_summary(E_, h, use_h, s));
+  return HN_OK;
+}
+
+hn_status Engine::issue_iteration(cudaStream_t s, cudaGraphConditionalHandle h, int use_h) {
+  if (prm_.prec == P64) {
+    HN_TRY(issue_vcycle(s, PH_CYCLE));
+    HN_LAUNCH(KC_CHECK, -1, launch_check(E_, fine_, PH_CYCLE, 0, fineGrid_, s));
+    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_CHECK, s));
+  } else {
+    HN_LAUNCH(KC_OUTER_DEFECT, -1, launch_outer_defect(E_, fine_, fineGrid_, s));
+    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_OUTER, s));
+    HN_TRY(issue_vcycle(s, PH_INNER));
+    HN_LAUNCH(KC_CHECK, -1, launch_check(E_, fine_, PH_INNER, 0, fineGrid_, s));
+    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_INNER, s));
+    HN_LAUNCH(KC_UPDATE, -1, launch_update(E_, fine_, fineGrid_, s));
+    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_POST, s));
+  }
+  HN_LAUNCH0(launch_summary(E_, h, use_h, s));
+  return HN_OK;
+}
+
+hn_status Engine::capture_graphs() {
+  destroy_graphs();
+  for (auto& m : marks_) { cudaEventDestroy(m.b); cudaEventDestroy(m.e); }
+  marks_.clear();
+  cudaStream_t cs;
+  HN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } guard{cs};
+  const cudaGraphConditionalHandle none = 0;
+  // host-driven pieces: init and one iteration (events only in the iteration graph)
+  {
+    const bool prof = profiling_;
+    profiling_ = false;
+    cudaGraph_t g;
+    HN_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    counting_ = 0;
+    hn_status st = issue_init(cs, none, 0);
+    initLaunches_ = counting_;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    profiling_ = prof;
+    HN_TRY(st);
+    HN_CUDA(e);
+    e = cudaGraphInstantiate(&gInit_, g, 0);
+    cudaGraphDestroy(g);
+    HN_CUDA(e);
+  }
+  {
+    cudaGraph_t g;
+    HN_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    counting_ = 0;
+    hn_status st = issue_iteration(cs, none, 0);
+    iterLaunches_ = counting_;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    HN_TRY(st);
+    HN_CUDA(e);
+    e = cudaGraphInstantiate(&gIter_, g, 0);
+    cudaGraphDestroy(g);
+    HN_CUDA(e);
+  }
+  // closed-world solve: init, then while (any problem running) { iteration }
+  if (!profiling_) {
+    cudaGraph_t main;
+    HN_CUDA(cudaGraphCreate(&main, 0));
+    struct GraphGuard { cudaGraph_t g; ~GraphGuard() { cudaGraphDestroy(g); } } gg{main};
+    cudaGraphConditionalHandle h;
+    HN_CUDA(cudaGraphConditionalHandleCreate(&h, main, 1, cudaGraphCondAssignDefault));
+    cudaGraph_t init;
+    HN_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    hn_status st = issue_init(cs, none, 0);
+    cudaError_t e = cudaStreamEndCapture(cs, &init);
+    HN_TRY(st);
+    HN_CUDA(e);
+    cudaGraphNode_t nInit;
+    e = cudaGraphAddChildGraphNode(&nInit, main, nullptr, 0, init);
+    cudaGraphDestroy(init);
+    HN_CUDA(e);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t nCond;
+    HN_CUDA(cudaGraphAddNode(&nCond, main, &nInit, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    HN_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    st = issue_iteration(cs, h, 1);
+    e = cudaStreamEndCapture(cs, &body);
+    HN_TRY(st);
+    HN_CUDA(e);
+    HN_CUDA(cudaGraphInstantiate(&gSolve_, main, 0));
+  }
+  graphsValid_ = true;
+  return HN_OK;
+}
+
+hn_status Engine::run_to_completion() {
+  if (!graphsValid_) HN_TRY(capture_graphs());
+  if (profiling_) {
+    HN_TRY(run_init());
+    lastLaunches_ = initLaunches_;
+    const int limit = prm_.max_cycles + prm_.max_outer + 8;
+    for (int it = 0; it < limit; ++it) {
+      unsigned active = 0;
+      HN_TRY(run_iteration(&active));
+      lastLaunches_ += iterLaunches_;
+      if (active == 0) break;
+    }
+    return HN_OK;
+  }
+  HN_CUDA(cudaGraphLaunch(gSolve_, s_));
+  unsigned iters = 0;
+  HN_CUDA(cudaMemcpyAsync(&iters, E_.iter, sizeof iters, cudaMemcpyDeviceToHost, s_));
+  HN_CUDA(cudaStreamSynchronize(s_));
+  // the init graph's summary also counts one; each body iteration runs iterLaunches_ kernels
+  lastLaunches_ = initLaunches_ + (long long)(iters > 0 ? iters - 1 : 0) * iterLaunches_;
+  return HN_OK;
+}
+
+hn_status Engine::run_init() {
+  if (!graphsValid_) HN_TRY(capture_graphs());
+  HN_CUDA(cudaGraphLaunch(gInit_, s_));
+  return HN_OK;
+}
+
+hn_status Engine::run_iteration(unsigned* active_out) {
+  if (!graphsValid_) HN_TRY(capture_graphs());
+  HN_CUDA(cudaGraphLaunch(gIter_, s_));
+  HN_CUDA(cudaStreamSynchronize(s_));
+  if (profiling_) HN_TRY(accumulate_marks());
+  if (active_out) *active_out = *reinterpret_cast<volatile unsigned*>(hActive_);
+  return HN_OK;
+}
+
+hn_status Engine::accumulate_marks() {
+  for (const Mark& m : marks_) {
+    float ms = 0.0f;
+    HN_CUDA(cudaEventElapsedTime(&ms, m.b, m.e));
+    const int lv = m.level < 0 ? 0 : m.level;
+    Acc& a = acc_[m.cls][lv];
+    a.ms += ms;
+    a.launches += 1;
+    a.bytes = m.bytes;
+  }
+  return HN_OK;
+}
+
+void Engine::set_profiling(bool on) {
+  profiling_ = on;
+  graphsValid_ = false;
+  for (auto& row : acc_)
+    for (auto& a : row) a = Acc{};
+}
+
+int Engine::kernel_times(hn_kernel_time* out, int max) const {
+  static const char* names[KC_COUNT] = {"jacobi", "jacobi_first", "defect", "restrict", "prolong",
+                                        "coarse", "check", "outer_defect", "update", "control"};
+  int n = 0;
+  for (int c = 0; c < KC_COUNT; ++c)
+    for (int l = 0; l <= kMaxLevel; ++l) {
+      const Acc& a = acc_[c][l];
+      if (a.launches == 0) continue;
+      if (n < max && out) {
+        hn_kernel_time& t = out[n];
+        std::memset(&t, 0, sizeof t);
+        std::snprintf(t.name, sizeof t.name, "%s", names[c]);
+        t.level = (c == KC_CHECK || c == KC_OUTER_DEFECT || c == KC_UPDATE || c == KC_CONTROL) ? -1 : l;
+        t.launches = a.launches;
+        t.total_ms = a.ms;
+        t.bytes_per_launch = (double)a.bytes;
+      }
+      ++n;
+    }
+  return n < max ? n : max;
+}
+
+hn_status Engine::read_states(std::vector<ProbState>& out) {
+  out.resize(cap_);
+  HN_CUDA(cudaMemcpyAsync(out.data(), dS_, sizeof(ProbState) * cap_, cudaMemcpyDeviceToHost, s_));
+  HN_CUDA(cudaStreamSynchronize(s_));
+  return HN_OK;
+}
+
+hn_status Engine::apply_check_norm(cudaStream_t s) {
+  HN_CUDA(launch_check(E_, fine_, PH_CHECK, 0, fineGrid_, s));
+  HN_CUDA(launch_control(E_, CTRL_CHECK0, s));
+  return HN_OK;
+}
+
+hn_status Engine::apply(int op, int level, int want, cudaStream_t s) {
+  switch (op) {
+    case HN_OP_SPMV: HN_CUDA(launch_spmv(E_, lists_[level], level, want, 0, grid_[level], s)); break;
+    case HN_OP_DEFECT: HN_CUDA(launch_defect(E_, lists_[level], level, want, 0, grid_[level], s)); break;
+    case HN_OP_JACOBI: HN_CUDA(launch_jacobi(E_, lists_[level], level, want, 0, 0, grid_[level], s)); break;
+    case HN_OP_JACOBI_ZERO: HN_CUDA(launch_jacobi(E_, lists_[level], level, want, 0, 1, grid_[level], s)); break;
+    case HN_OP_RESTRICT:
+      HN_CUDA(launch_restrict(E_, lists_[level - 1], level, want, grid_[level - 1], s));
+      break;
+    case HN_OP_PROLONG_ADD: HN_CUDA(launch_prolong(E_, lists_[level], level, want, 0, grid_[level], s)); break;
+    case HN_OP_COARSE: HN_CUDA(launch_coarse(E_, lists_[level], want, grid_[level], s)); break;
+    default: return set_error(HN_ERR_ARG, "unknown op %d", op);
+  }
+  return HN_OK;
+}
+
+}  // namespace hn
+
+hn_band::~hn_band() {
+  if (mem) cudaFree(mem);
+}
+
+hn_mg::~hn_mg() {
+  delete solo;
+  if (mem) cudaFree(mem);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}

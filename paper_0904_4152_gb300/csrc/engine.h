@@ -1,0 +1,174 @@
+// Host-side engine of the hn library (internal): operators, hierarchies, and the batch engine
+// that runs the V-cycle schedule over a set of hierarchies as CUDA graphs.
+#pragma once
+
+#include <chrono>
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "hn_internal.h"
+#include "../../include/hn_profile.h"
+
+namespace hn {
+
+// thread-local error message + status helpers
+hn_status set_error(hn_status st, const char* fmt, ...);
+void clear_error();
+const char* last_error();
+
+#define HN_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return ::hn::set_error(e_ == cudaErrorMemoryAllocation ? HN_ERR_OOM : HN_ERR_CUDA, \
+                             "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
+                             __LINE__);                                                  \
+  } while (0)
+
+#define HN_TRY(expr)                      \
+  do {                                    \
+    hn_status s_ = (expr);                \
+    if (s_ != HN_OK) return s_;           \
+  } while (0)
+
+inline long long now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// bump allocator over one device allocation (256-byte aligned pieces)
+struct Bump {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* r = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return r;
+  }
+};
+
+// device bytes a hierarchy of fine level L needs (same arithmetic as its construction)
+size_t hierarchy_bytes(int L, int coarse, int prec);
+
+// kernel classes timed in profiling mode
+enum KClass {
+  KC_JACOBI = 0, KC_JACOBI_FIRST, KC_DEFECT, KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_CHECK,
+  KC_OUTER_DEFECT, KC_UPDATE, KC_CONTROL, KC_COUNT
+};
+
+class Engine;
+
+}  // namespace hn
+
+struct hn_band {
+  int L = 0;
+  long long n = 0, N = 0, pitch = 0;
+  void* mem = nullptr;
+  double* band[9] = {};
+  double* coef = nullptr;   // device cell coefficients, nullptr for a = 1
+  ~hn_band();
+};
+
+struct hn_mg {
+  int L = 0, coarse = 2, m = 0;
+  hn_mg_opts opts{};
+  hn::Params prm{};
+  void* mem = nullptr;
+  size_t bytes = 0;
+  hn::ProblemDev host{};     // descriptor (device pointers)
+  long long setup_ns = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  hn::Engine* solo = nullptr;
+  ~hn_mg();
+};
+
+namespace hn {
+
+hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t stream, hn_mg* mg);
+hn_status validate_opts(const hn_mg_opts& o, int L);
+Params params_from(const hn_mg_opts& o);
+
+// A batch engine: up to `cap` problem slots solved together.
+class Engine {
+ public:
+  Engine() = default;
+  ~Engine();
+  // cap: slots; Lmax: highest level the schedule covers; tiles_cap[l]: work-list capacity per
+  // level (l = 0..kMaxLevel), fine_cap: fine-list capacity
+  hn_status create(const Params& prm, int cap, int Lmax, const std::vector<long long>& tiles_cap,
+                   long long fine_cap, cudaStream_t s);
+  // assign hierarchies to slots (nullptr = empty slot) and rewrite the device work lists
+  hn_status set_members(const std::vector<hn_mg*>& slots);
+  // reset the state of the given slots for a new solve
+  hn_status start(const std::vector<int>& slots, const std::vector<int>& have_guess);
+  // closed-world solve of all members: device-side loop in one graph launch
+  hn_status run_to_completion();
+  // host-driven steps (serving / profiling)
+  hn_status run_init();
+  hn_status run_iteration(unsigned* active_out);
+  hn_status read_states(std::vector<ProbState>& out);
+  hn_status read_states_async(ProbState* host_dst);
+  // single-kernel execution on slot 0 (hn_mg_apply)
+  hn_status apply(int op, int level, int want, cudaStream_t s);
+  hn_status apply_check_norm(cudaStream_t s);
+  hn_status set_phase(int slot, int phase, int zero_top);
+
+  void set_profiling(bool on);
+  void set_iter_limit(unsigned lim) { E_.iter_limit = lim; graphsValid_ = false; }
+  int kernel_times(hn_kernel_time* out, int max) const;
+
+  long long last_launches() const { return lastLaunches_; }
+  int cap() const { return cap_; }
+  const Params& params() const { return prm_; }
+  cudaStream_t stream() const { return s_; }
+
+ private:
+  hn_status capture_graphs();
+  hn_status issue_init(cudaStream_t s, cudaGraphConditionalHandle h, int use_h);
+  hn_status issue_iteration(cudaStream_t s, cudaGraphConditionalHandle h, int use_h);
+  hn_status issue_vcycle(cudaStream_t s, int want);
+  int grid_for(long long tiles) const;
+  hn_status mark(cudaStream_t s, int cls, int level, bool begin);
+  void destroy_graphs();
+
+  Params prm_{};
+  int cap_ = 0, Lmax_ = 0;
+  cudaStream_t s_ = nullptr;
+  void* mem_ = nullptr;
+  unsigned* hActive_ = nullptr;  // mapped pinned
+  EngineDev E_{};
+  ProblemDev* dP_ = nullptr;
+  ProbState* dS_ = nullptr;
+  int* dFineOff_ = nullptr;
+  int* dCounts_ = nullptr;          // [kMaxLevel + 2]: per level, then the fine list
+  int2* dItems_[kMaxLevel + 1] = {};
+  int2* dFine_ = nullptr;
+  long long itemCap_[kMaxLevel + 1] = {};
+  long long fineCap_ = 0;
+  TileList lists_[kMaxLevel + 1] = {};
+  TileList fine_{};
+  int grid_[kMaxLevel + 1] = {};
+  int fineGrid_ = 1;
+  int maxGrid_ = 1;
+  std::vector<hn_mg*> members_;
+  std::vector<int> hCounts_;
+  cudaGraphExec_t gSolve_ = nullptr, gInit_ = nullptr, gIter_ = nullptr;
+  bool graphsValid_ = false;
+  int initLaunches_ = 0, iterLaunches_ = 0, counting_ = 0;
+  long long lastLaunches_ = 0;
+  // profiling
+  bool profiling_ = false;
+  struct Mark { cudaEvent_t b, e; int cls, level; long long bytes; };
+  std::vector<Mark> marks_;
+  std::vector<cudaEvent_t> openBegin_;
+  struct Acc { double ms = 0; long long launches = 0; long long bytes = 0; };
+  Acc acc_[KC_COUNT][kMaxLevel + 1];
+  long long launch_bytes(int cls, int level) const;
+  hn_status accumulate_marks();
+};
+
+}  // namespace hn

@@ -1,0 +1,158 @@
+// Internal declarations of the hn library: device-side descriptors, the per-problem solver state
+// machine, and the kernel launch wrappers.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/hn.h"
+
+namespace hn {
+
+// ------------------------------------------------------------------------------ geometry
+// A warp-tile is 128 consecutive nodes of the flat (padded) index range; each lane owns 4.
+constexpr int kTile = 128;
+constexpr int kLaneNodes = 4;
+constexpr int kMaxLevel = HN_MAX_LEVEL;
+constexpr int kMaxCoarse = 4;                       // coarse_L <= 4: at most 225 interior unknowns
+constexpr int kMaxCoarseM = 225;
+
+__host__ __device__ inline long long n_of_dev(int L) { return (1LL << L) + 1; }
+inline long long n_of(int L) { return (1LL << L) + 1; }
+inline long long N_of(int L) { return n_of(L) * n_of(L); }
+inline long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+// padded length of a level: multiple of the tile, and every row/tile index is in range
+inline long long pitch_of(int L) { return round_up(N_of(L), kTile); }
+// zero halo in front of / behind every vector, covers the +-(n+1) stencil reach of the padded
+// range (multiple of 32 elements keeps every vector 256-byte aligned)
+inline long long halo_of(int L) { return round_up(n_of(L) + 8, 32); }
+
+enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+
+// ------------------------------------------------------------------- device descriptors
+// One level of one problem.  Vectors point at element 0 (a zero halo of halo_of(L) elements sits
+// on either side); bands are 9 arrays of pitch elements of the level's storage type.
+struct LevelDev {
+  const void* band[9];   // double (FP64 hierarchy), float (FP32), __half (FP16 codes)
+  const double* wdinv;   // FP64 hierarchy only: omega / diag, pitch doubles
+  void* x[2];            // iterate and its Jacobi ping-pong partner (double or float)
+  void* rhs;             // right-hand side of this level (restricted defect, or the top rhs)
+  void* r;               // defect of this level
+  float scale[9];        // FP16 band scales
+  int L, n, pitch, pad;
+};
+
+struct ProblemDev {
+  int L;                 // finest level
+  int coarse;            // coarsest level
+  int m;                 // interior unknowns of the coarsest level
+  int pad0;
+  const double* cinv;    // m*m inverse of the coarsest interior block, row-major
+  // FP64 fine-level data of the outer loop (aliases of the top level in FP64 mode)
+  const double* band64[9];
+  double* x64;           // solution
+  double* b64;           // right-hand side
+  LevelDev lev[kMaxLevel + 1];   // indexed by level l in [coarse, L]
+};
+
+// per-problem state machine of a solve (device)
+enum Phase {
+  PH_DONE = 0,    // finished (status holds the outcome)
+  PH_OUTER = 1,   // defect correction: needs the FP64 outer defect
+  PH_INNER = 2,   // defect correction: running inner V cycles
+  PH_UPDATE = 3,  // defect correction: inner solve finished, apply x += c / s
+  PH_CYCLE = 4,   // FP64 multigrid: run a V cycle, then check
+  PH_CHECK = 5,   // FP64 multigrid: check the initial guess before cycling
+  PH_INIT = 6     // starting: boundary check and ||b||
+};
+
+struct ProbState {
+  int phase;             // Phase
+  int status;            // hn_status once done; HN_PENDING while running
+  int cycles, outer_iters, inner_cycles, inner_k;
+  int zero_top;          // the top-level iterate is zero (first sweep skips reading it)
+  int x_zero;            // the FP64 solution is still zero (outer defect = b)
+  double bnorm;          // ||b||
+  double dnorm;          // ||b - A x|| at the last outer defect / FP64 check
+  double relres;         // dnorm / bnorm
+  double s;              // scale applied to the defect before the cast to the inner precision
+  double inner_ref;      // ||scaled defect|| (reference of the inner relative residual)
+  double inner_res;      // last inner residual norm
+};
+
+// solver parameters shared by every problem of an engine
+struct Params {
+  int prec, pre, post, coarse;
+  int max_cycles, max_outer, inner_max, pad;
+  double omega, tol, inner_tol;
+};
+
+// tile work list of one level: items[g] = (problem, tile of that problem's level).  The count is
+// read from device memory so that a captured graph stays valid when the list is rewritten.
+struct TileList {
+  const int2* items;
+  const int* count;
+};
+
+// ------------------------------------------------------------------------ launch wrappers
+// setup kernels (k_setup.cu); band pointer sets are passed by value
+struct BandPtrs64 { double* p[9]; };
+struct BandPtrs64c { const double* p[9]; };
+struct BandPtrs32 { float* p[9]; };
+struct BandPtrs16 { __half* p[9]; };
+cudaError_t launch_assemble(int L, const double* coef, const BandPtrs64& band, double* wdinv,
+                            double omega, cudaStream_t s);
+cudaError_t launch_coarsen_coef(int Lf, const double* af, double* ac, cudaStream_t s);
+cudaError_t launch_band_to_f32(int L, const BandPtrs64c& src, const BandPtrs32& dst,
+                               cudaStream_t s);
+cudaError_t launch_band_to_f16(int L, const BandPtrs64c& src, unsigned long long* absmax9,
+                               const BandPtrs16& dst, float* scales_dev, cudaStream_t s);
+
+// solver kernels (k_cycle.cu).  All take the engine's device arrays.
+struct EngineDev {
+  const ProblemDev* P;   // problems
+  ProbState* S;          // states
+  const int* fine_off;   // first partial slot of each problem (fine-level tile list order)
+  double* partial;       // one slot per fine-level tile
+  double* partial2;      // second set (||b|| at start)
+  int nprob;
+  int pad;
+  Params prm;
+  unsigned int* active_host;   // mapped host word: problems not done after the iteration
+  unsigned int* iter;          // iterations since the solve started (device)
+  unsigned int iter_limit;     // beyond it every running problem stops as not converged
+  unsigned int pad2;
+};
+
+// Launch wrappers for one step of the schedule; grid = CTAs of 256 threads.  level < 0 means
+// "each problem's own finest level" (used with the fine work list).
+cudaError_t launch_jacobi(const EngineDev& E, TileList tl, int level, int want, int in_sel,
+                          int first, int grid, cudaStream_t s);
+cudaError_t launch_defect(const EngineDev& E, TileList tl, int level, int want, int in_sel,
+                          int grid, cudaStream_t s);
+cudaError_t launch_spmv(const EngineDev& E, TileList tl, int level, int want, int in_sel, int grid,
+                        cudaStream_t s);
+cudaError_t launch_check(const EngineDev& E, TileList fine, int want, int x_sel, int grid,
+                         cudaStream_t s);
+cudaError_t launch_restrict(const EngineDev& E, TileList tl_coarse, int fine_level, int want,
+                            int grid, cudaStream_t s);
+cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want, int x_sel,
+                           int grid, cudaStream_t s);
+cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, cudaStream_t s);
+cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+cudaError_t launch_norm_b(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+cudaError_t launch_control(const EngineDev& E, int kind, cudaStream_t s);
+cudaError_t launch_summary(const EngineDev& E, cudaGraphConditionalHandle h, int use_handle,
+                           cudaStream_t s);
+cudaError_t launch_boundary_check(const EngineDev& E, cudaStream_t s);
+
+enum ControlKind {
+  CTRL_INIT = 0, CTRL_CHECK = 1, CTRL_OUTER = 2, CTRL_INNER = 3, CTRL_POST = 4, CTRL_CHECK0 = 5
+};
+
+int sm_count();
+
+}  // namespace hn

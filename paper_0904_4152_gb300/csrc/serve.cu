@@ -1,0 +1,352 @@
+// Continuous-batching solve server.  Requests queue FIFO; a request is admitted when a slot is free
+// and its hierarchy fits the device-memory budget.  Every scheduler iteration runs one launch
+// sequence of the V-cycle schedule (engine.cu) over all active requests at once; requests that
+// finish leave between iterations, free their memory and let queued requests in.  The hierarchy
+// of a request stays resident on the device from admission to completion.
+#include <algorithm>
+#include <climits>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+
+#include "engine.h"
+
+using namespace hn;
+
+namespace {
+
+struct Request {
+  unsigned long long ticket = 0;
+  int L = 0;
+  std::vector<double> coef, b, x;
+  hn_mg* mg = nullptr;
+  int slot = -1;
+  size_t bytes = 0;
+  bool done = false;
+  int status = HN_PENDING;
+  hn_mg_stats stats{};
+  long long t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct hn_server {
+  size_t budget = 0;
+  int max_active = 0;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::map<unsigned long long, std::unique_ptr<Request>> all;
+  unsigned long long next_ticket = 1;
+  bool stop = false;
+  bool have_opts = false;
+  hn_mg_opts opts{};
+  size_t in_use = 0;
+  long long submitted = 0, completed = 0, iterations = 0;
+  std::vector<Request*> slots;
+  std::thread worker;
+  std::string worker_error;
+  void run();
+};
+
+namespace {
+
+size_t request_bytes(int L, const hn_mg_opts& o) {
+  const Params p = params_from(o);
+  // resident hierarchy + the transient fine operator built during admission
+  return hierarchy_bytes(L, o.coarse_L, p.prec) + (size_t)9 * pitch_of(L) * 8 +
+         (size_t)(1LL << L) * (1LL << L) * 8 + 4096;
+}
+
+}  // namespace
+
+void hn_server::run() {
+  cudaSetDevice(device);
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    worker_error = "stream creation failed";
+    stop = true;
+    cv_done.notify_all();
+    return;
+  }
+  std::unique_ptr<Engine> engine;
+  int engine_lmax = 0;
+  bool members_dirty = false;
+  std::vector<int> fresh;
+  auto fail_all = [&](const char* why) {
+    std::lock_guard<std::mutex> lk(mu);
+    worker_error = why;
+    for (Request*& r : slots)
+      if (r) { r->status = HN_ERR_CUDA; r->done = true; r = nullptr; }
+    for (Request* r : queue) { r->status = HN_ERR_CUDA; r->done = true; }
+    queue.clear();
+    stop = true;
+    cv_done.notify_all();
+  };
+  for (;;) {
+    std::vector<Request*> admitted;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      auto active = [&] { return std::count_if(slots.begin(), slots.end(), [](Request* r) { return r != nullptr; }); };
+      cv_work.wait(lk, [&] { return stop || !queue.empty() || active() > 0; });
+      if (stop && active() == 0) break;
+      if (!stop) {
+        while (!queue.empty()) {
+          auto free_slot = std::find(slots.begin(), slots.end(), nullptr);
+          if (free_slot == slots.end()) break;
+          Request* r = queue.front();
+          if (in_use + r->bytes > budget) break;    // FIFO: the head waits for memory
+          queue.pop_front();
+          in_use += r->bytes;
+          r->slot = (int)(free_slot - slots.begin());
+          *free_slot = r;
+          r->t_admit = now_ns();
+          admitted.push_back(r);
+        }
+      }
+    }
+    // build the hierarchies of the admitted requests (explicit copies of their inputs)
+    for (Request* r : admitted) {
+      hn_band* A = nullptr;
+      hn_status st = hn_band_create(r->L, r->coef.empty() ? nullptr : r->coef.data(), &A);
+      hn_mg* mg = nullptr;
+      if (st == HN_OK) {
+        hn_mg_opts o = opts;
+        o.stream = s;
+        st = hn_mg_setup(A, &o, &mg);
+      }
+      hn_band_destroy(A);
+      if (st == HN_OK) {
+        const long long N = N_of(r->L);
+        if (cudaMemcpyAsync(mg->host.b64, r->b.data(), (size_t)N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(mg->host.x64, 0, (size_t)N * 8, s) != cudaSuccess)
+          st = HN_ERR_CUDA;
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      if (st != HN_OK) {
+        hn_mg_destroy(mg);
+        r->status = st;
+        r->done = true;
+        r->t_done = now_ns();
+        in_use -= r->bytes;
+        slots[r->slot] = nullptr;
+        cv_done.notify_all();
+        continue;
+      }
+      r->mg = mg;
+      r->stats.setup_ns = mg->setup_ns;
+      fresh.push_back(r->slot);
+      members_dirty = true;
+    }
+    // (re)build the engine for the current highest level, then refresh its work lists
+    int lmax = 0;
+    std::vector<hn_mg*> members(max_active, nullptr);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (int q = 0; q < max_active; ++q)
+        if (slots[q] && slots[q]->mg) { members[q] = slots[q]->mg; lmax = std::max(lmax, slots[q]->L); }
+    }
+    if (lmax == 0) continue;
+    if (!engine || lmax > engine_lmax) {
+      // a larger level than the schedule covers: wait until the running requests drain
+      bool running_old = false;
+      if (engine) {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int q = 0; q < max_active; ++q)
+          if (slots[q] && slots[q]->mg && std::find(fresh.begin(), fresh.end(), q) == fresh.end())
+            running_old = true;
+      }
+      if (!engine || !running_old) {
+        const int Lcap = std::max(lmax, 8);
+        std::vector<long long> caps(kMaxLevel + 1, 0);
+        const long long budget_tiles = (long long)(budget / (64 * kTile)) + max_active;
+        for (int l = opts.coarse_L; l <= Lcap; ++l)
+          caps[l] = std::min<long long>((long long)max_active * (pitch_of(l) / kTile), budget_tiles);
+        const long long fine_cap = std::min<long long>((long long)max_active * (pitch_of(Lcap) / kTile), budget_tiles);
+        engine.reset(new Engine());
+        if (engine->create(params_from(opts), max_active, Lcap, caps, fine_cap, s) != HN_OK) {
+          fail_all(hn_last_error());
+          break;
+        }
+        engine->set_iter_limit(UINT_MAX - 1);
+        engine_lmax = Lcap;
+        members_dirty = true;
+        // every admitted request (re)starts on the new engine
+        fresh.clear();
+        for (int q = 0; q < max_active; ++q) if (members[q]) fresh.push_back(q);
+      } else {
+        // keep the too-large requests out of this iteration
+        for (int q = 0; q < max_active; ++q)
+          if (members[q] && members[q]->L > engine_lmax) members[q] = nullptr;
+      }
+    }
+    if (members_dirty) {
+      if (engine->set_members(members) != HN_OK) { fail_all(hn_last_error()); break; }
+      members_dirty = false;
+    }
+    std::vector<int> start_now;
+    for (int q : fresh) if (members[q]) start_now.push_back(q);
+    if (!start_now.empty()) {
+      if (engine->start(start_now, std::vector<int>(start_now.size(), 0)) != HN_OK ||
+          engine->run_init() != HN_OK) { fail_all(hn_last_error()); break; }
+      fresh.erase(std::remove_if(fresh.begin(), fresh.end(), [&](int q) { return members[q] != nullptr; }), fresh.end());
+    }
+    unsigned active = 0;
+    if (engine->run_iteration(&active) != HN_OK) { fail_all(hn_last_error()); break; }
+    std::vector<ProbState> st;
+    if (engine->read_states(st) != HN_OK) { fail_all(hn_last_error()); break; }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      ++iterations;
+    }
+    // retire finished requests
+    for (int q = 0; q < max_active; ++q) {
+      if (!members[q] || st[q].phase != PH_DONE) continue;
+      Request* r;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        r = slots[q];
+      }
+      const long long N = N_of(r->L);
+      r->x.resize((size_t)N);
+      if (st[q].status == HN_OK && st[q].bnorm == 0.0) std::fill(r->x.begin(), r->x.end(), 0.0);
+      else if (cudaMemcpyAsync(r->x.data(), r->mg->host.x64, (size_t)N * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+               cudaStreamSynchronize(s) != cudaSuccess) { fail_all("result copy failed"); break; }
+      hn_mg_destroy(r->mg);
+      std::lock_guard<std::mutex> lk(mu);
+      r->mg = nullptr;
+      r->status = st[q].status;
+      r->stats.cycles = st[q].cycles;
+      r->stats.outer_iters = st[q].outer_iters;
+      r->stats.inner_cycles = st[q].inner_cycles;
+      r->stats.status = st[q].status;
+      r->stats.relres = st[q].relres;
+      r->t_done = now_ns();
+      r->stats.solve_ns = r->t_done - r->t_submit;
+      r->done = true;
+      in_use -= r->bytes;
+      slots[q] = nullptr;
+      ++completed;
+      members_dirty = true;
+      cv_done.notify_all();
+    }
+    if (stop && worker_error.size()) break;
+  }
+  engine.reset();
+  cudaStreamDestroy(s);
+}
+
+extern "C" {
+
+hn_status hn_server_create(size_t budget_bytes, int max_active, hn_server** out) {
+  clear_error();
+  if (!out || budget_bytes == 0 || max_active < 1 || max_active > 4096)
+    return set_error(HN_ERR_ARG, "bad server arguments");
+  std::unique_ptr<hn_server> srv(new hn_server());
+  srv->budget = budget_bytes;
+  srv->max_active = max_active;
+  srv->slots.assign(max_active, nullptr);
+  HN_CUDA(cudaGetDevice(&srv->device));
+  hn_server* raw = srv.get();
+  srv->worker = std::thread([raw] { raw->run(); });
+  *out = srv.release();
+  return HN_OK;
+}
+
+hn_status hn_mg_submit(hn_server* srv, int L, const double* cell_coef, const double* b,
+                       const hn_mg_opts* opts, unsigned long long* ticket) {
+  clear_error();
+  if (!srv || !b || !ticket) return set_error(HN_ERR_ARG, "null argument");
+  if (L < HN_MIN_LEVEL || L > HN_MAX_LEVEL) return set_error(HN_ERR_ARG, "level %d out of range", L);
+  hn_mg_opts o;
+  if (opts) o = *opts; else hn_mg_opts_default(&o);
+  HN_TRY(validate_opts(o, L));
+  std::unique_ptr<Request> r(new Request());
+  r->L = L;
+  const long long N = N_of(L), cells = (1LL << L) * (1LL << L);
+  if (cell_coef) r->coef.assign(cell_coef, cell_coef + cells);
+  r->b.assign(b, b + N);
+  r->bytes = request_bytes(L, o);
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->stop) return set_error(HN_ERR_STATE, "server stopped: %s", srv->worker_error.c_str());
+  if (!srv->have_opts) {
+    srv->opts = o;
+    srv->have_opts = true;
+  } else {
+    const hn_mg_opts& a = srv->opts;
+    if (a.prec != o.prec || a.pre != o.pre || a.post != o.post || a.omega != o.omega ||
+        a.coarse_L != o.coarse_L || a.tol != o.tol || a.inner_tol != o.inner_tol ||
+        a.max_cycles != o.max_cycles || a.max_outer != o.max_outer || a.inner_max != o.inner_max)
+      return set_error(HN_ERR_ARG, "options differ from the server's (first submit)");
+  }
+  if (r->bytes > srv->budget) return set_error(HN_ERR_BUDGET, "request needs %zu bytes, budget %zu", r->bytes, srv->budget);
+  r->ticket = srv->next_ticket++;
+  r->t_submit = now_ns();
+  *ticket = r->ticket;
+  srv->queue.push_back(r.get());
+  srv->all[r->ticket] = std::move(r);
+  ++srv->submitted;
+  srv->cv_work.notify_one();
+  return HN_OK;
+}
+
+hn_status hn_mg_poll(hn_server* srv, unsigned long long ticket, long long timeout_ns, double* x_out,
+                     hn_mg_stats* stats) {
+  clear_error();
+  if (!srv) return set_error(HN_ERR_ARG, "null server");
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto it = srv->all.find(ticket);
+  if (it == srv->all.end()) return set_error(HN_ERR_ARG, "unknown ticket %llu", ticket);
+  Request* r = it->second.get();
+  if (!r->done) {
+    if (timeout_ns == 0) return HN_PENDING;
+    if (timeout_ns < 0) {
+      srv->cv_done.wait(lk, [&] { return r->done; });
+    } else {
+      const auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns);
+      if (!srv->cv_done.wait_until(lk, deadline, [&] { return r->done; }))
+        return set_error(HN_ERR_TIMEOUT, "request %llu not finished before the deadline", ticket);
+    }
+  }
+  if (x_out && !r->x.empty()) std::memcpy(x_out, r->x.data(), r->x.size() * 8);
+  if (stats) *stats = r->stats;
+  const hn_status st = (hn_status)r->status;
+  srv->all.erase(it);
+  if (st != HN_OK) set_error(st, "request %llu finished with status %d", ticket, (int)st);
+  return st;
+}
+
+hn_status hn_server_query(hn_server* srv, hn_server_info* info) {
+  clear_error();
+  if (!srv || !info) return set_error(HN_ERR_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  info->submitted = srv->submitted;
+  info->completed = srv->completed;
+  info->active = std::count_if(srv->slots.begin(), srv->slots.end(), [](Request* r) { return r != nullptr; });
+  info->queued = (long long)srv->queue.size();
+  info->iterations = srv->iterations;
+  info->bytes_in_use = srv->in_use;
+  info->budget = srv->budget;
+  return HN_OK;
+}
+
+void hn_server_destroy(hn_server* srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+    for (Request* r : srv->queue) { r->status = HN_ERR_STATE; r->done = true; }
+    srv->queue.clear();
+    srv->cv_work.notify_all();
+  }
+  if (srv->worker.joinable()) srv->worker.join();
+  delete srv;
+}
+
+}  // extern "C"

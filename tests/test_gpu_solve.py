@@ -1,0 +1,241 @@
+"""End-to-end parity of the GPU multigrid solves with the oracle, through the C ABI.
+
+Gates (the method iterates, so two independently stopped solves differ by about the tolerance):
+  G1  FP64 V cycles in lockstep with the oracle (same cycle count): ||dx|| / ||x|| <= 1e-9.
+  G2  every GPU result, checked with the oracle's FP64 operator: ||b - A x|| / ||b|| <= 1e-8.
+  G3  mixed-precision results against the oracle solved to 1e-13: <= 1e-9 when the GPU side is
+      also run to a tighter stop (1e-11)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0904_4152_gb300 import inputs as I
+from gpu_util import oracle_relres, require_gpu, solve
+
+pytestmark = pytest.mark.gpu
+RELRES = 1.0001e-8
+
+
+@pytest.fixture(scope="module")
+def hn():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("L,lognormal", [(3, False), (6, False), (6, True), (9, True)])
+def test_g1_fp64_lockstep(hn, L, lognormal):
+    coef = I.lognormal_coef(L, 300 + L) if lognormal else None
+    b = I.rhs_uniform(L, 301)
+    k = 4
+    x, st, status = solve(hn, L, b, coef, tol=0.0, max_cycles=k)
+    assert status == hn.HN_ERR_NOT_CONVERGED and st["cycles"] == k
+    xr, sr = O.mg_solve(L, b, coef=coef, tol=0.0, max_cycles=k)
+    assert sr["cycles"] == k
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-9
+    assert abs(st["relres"] - sr["relres"]) <= 1e-6 * sr["relres"]
+
+
+def test_g2_config_small_sinsin(hn):
+    # L=6, a=1, f = 2 pi^2 sin(pi x) sin(pi y), V(2,2), omega 0.7, coarse L=2, tol 1e-8
+    L = 6
+    b = O.load_sinsin(L)
+    x, st, status = solve(hn, L, b)
+    xr, sr = O.mg_solve(L, b)
+    assert status == hn.HN_OK and st["relres"] <= 1e-8
+    assert oracle_relres(L, None, b, x) <= RELRES
+    assert st["cycles"] == sr["cycles"]
+    e_gpu, e_or = O.l2_error_sinsin(L, x), O.l2_error_sinsin(L, xr)
+    assert abs(e_gpu / e_or - 1) < 1e-6
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_g2_g3_mixed_precision(hn, prec):
+    L = 7
+    coef = I.lognormal_coef(L, 0)
+    b = I.rhs_uniform(L, 1)
+    x, st, status = solve(hn, L, b, coef, prec=prec)
+    assert status == hn.HN_OK
+    assert oracle_relres(L, coef, b, x) <= RELRES
+    assert st["outer_iters"] >= 2 and st["inner_cycles"] >= st["outer_iters"]
+    xs, _ = O.mg_solve(L, b, coef=coef, tol=1e-13)
+    # the oracle's own DC takes the same number of outer steps (+-1)
+    _, so = O.mg_solve(L, b, coef=coef, prec=prec)
+    assert abs(so["outer_iters"] - st["outer_iters"]) <= 1
+    x2, st2, status2 = solve(hn, L, b, coef, prec=prec, tol=1e-11)
+    assert status2 == hn.HN_OK
+    assert np.linalg.norm(x2 - xs) / np.linalg.norm(xs) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_g2_config_L10(hn, prec):
+    # L=10 (1025^2 nodes), a=1, b ~ U[-1,1] seed 0: FP64 MG and FP32-inner defect correction
+    L = 10
+    b = I.rhs_uniform(L, 0)
+    x, st, status = solve(hn, L, b, prec=prec)
+    assert status == hn.HN_OK
+    assert oracle_relres(L, None, b, x) <= RELRES
+
+
+def test_g2_config_L12_fp16(hn):
+    # the largest configuration: L=12 lognormal field, FP16-band inner multigrid
+    L = 12
+    coef = I.lognormal_coef(L, 0)
+    b = I.rhs_uniform(L, 1)
+    x, st, status = solve(hn, L, b, coef, prec=2)
+    assert status == hn.HN_OK
+    assert oracle_relres(L, coef, b, x) <= RELRES
+
+
+def test_device_and_host_pointers_agree(hn):
+    torch = pytest.importorskip("torch")
+    L = 7
+    b = I.rhs_uniform(L, 9)
+    A = hn.hn_band_create(L)
+    mg = hn.hn_mg_setup(A, prec=1)
+    hn.hn_band_destroy(A)
+    try:
+        xh, _, _ = hn.hn_mg_solve(mg, L, b)
+        bd = torch.from_numpy(b).cuda()
+        xd, _, _ = hn.hn_mg_solve(mg, L, bd)
+        np.testing.assert_array_equal(xd.cpu().numpy(), xh)
+        # a converged initial guess: no cycle is needed
+        x0 = xh.copy()
+        x1, st, status = hn.hn_mg_solve(mg, L, b, x=x0, x_is_guess=True)
+        assert status == hn.HN_OK and st["cycles"] == 0
+    finally:
+        hn.hn_mg_destroy(mg)
+
+
+def test_fp64_converged_guess_and_zero_rhs(hn):
+    L = 5
+    b = I.rhs_uniform(L, 3)
+    A = hn.hn_band_create(L)
+    mg = hn.hn_mg_setup(A)
+    hn.hn_band_destroy(A)
+    try:
+        x, st, _ = hn.hn_mg_solve(mg, L, b)
+        x1, st1, status = hn.hn_mg_solve(mg, L, b, x=x.copy(), x_is_guess=True)
+        assert status == hn.HN_OK and st1["cycles"] == 0
+        np.testing.assert_array_equal(x1, x)
+        z, stz, status = hn.hn_mg_solve(mg, L, np.zeros_like(b), x=np.ones_like(b), x_is_guess=True)
+        assert status == hn.HN_OK and np.all(z == 0) and stz["cycles"] == 0
+    finally:
+        hn.hn_mg_destroy(mg)
+
+
+def test_invalid_inputs_fail_cleanly(hn):
+    L = 4
+    A = hn.hn_band_create(L)
+    mg = hn.hn_mg_setup(A, prec=1)
+    hn.hn_band_destroy(A)
+    try:
+        b = I.rhs_uniform(L, 1)
+        bad = b.copy()
+        bad[3] = 1.0                                    # boundary node
+        with pytest.raises(hn.HnError) as e:
+            hn.hn_mg_solve(mg, L, bad)
+        assert e.value.status == hn.HN_ERR_ARG
+        nan = b.copy()
+        nan[40] = np.nan
+        with pytest.raises(hn.HnError) as e:
+            hn.hn_mg_solve(mg, L, nan)
+        assert e.value.status == hn.HN_ERR_NONFINITE
+        x, st, status = hn.hn_mg_solve(mg, L, b)          # the handle still works
+        assert status == hn.HN_OK
+    finally:
+        hn.hn_mg_destroy(mg)
+    A = hn.hn_band_create(L)
+    mg = hn.hn_mg_setup(A, max_cycles=2, tol=1e-14)
+    hn.hn_band_destroy(A)
+    try:
+        x, st, status = hn.hn_mg_solve(mg, L, I.rhs_uniform(L, 1))
+        assert status == hn.HN_ERR_NOT_CONVERGED and st["cycles"] == 2
+    finally:
+        hn.hn_mg_destroy(mg)
+    A = hn.hn_band_create(L)
+    try:
+        for bad in (dict(pre=0), dict(pre=2, post=1), dict(omega=2.5), dict(coarse_L=5),
+                    dict(inner_tol=1.5)):
+            with pytest.raises(hn.HnError) as e:
+                hn.hn_mg_setup(A, **bad)
+            assert e.value.status == hn.HN_ERR_ARG
+    finally:
+        hn.hn_band_destroy(A)
+
+
+@pytest.mark.parametrize("L", [2, 3])
+def test_degenerate_levels(hn, L):
+    # L = coarse level: the exact coarse solve is the whole cycle
+    b = I.rhs_uniform(L, 4)
+    for prec in (0, 1, 2):
+        x, st, status = solve(hn, L, b, prec=prec)
+        assert status == hn.HN_OK and oracle_relres(L, None, b, x) <= RELRES
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_batch_alone_equals_in_mix(hn, prec):
+    levels = [2, 5, 7, 3, 6, 8, 5]
+    mgs, bs, coefs = [], [], []
+    for j, L in enumerate(levels):
+        coef, b = I.batch_problem(j, L)
+        A = hn.hn_band_create(L, coef)
+        mgs.append(hn.hn_mg_setup(A, prec=prec))
+        hn.hn_band_destroy(A)
+        bs.append(b)
+        coefs.append(coef)
+    try:
+        xs, stats, status = hn.hn_mg_solve_batch(mgs, levels, bs)
+        assert status == hn.HN_OK
+        for j, L in enumerate(levels):
+            xa, sa, _ = hn.hn_mg_solve(mgs[j], L, bs[j])
+            np.testing.assert_array_equal(xs[j], xa)              # bit-identical alone / in mix
+            assert stats[j]["cycles"] == sa["cycles"]
+            assert oracle_relres(L, coefs[j], bs[j], xs[j]) <= RELRES
+        xs2, _, _ = hn.hn_mg_solve_batch(mgs, levels, bs)        # cached engine, same result
+        for a, c in zip(xs, xs2):
+            np.testing.assert_array_equal(a, c)
+    finally:
+        for m in mgs:
+            hn.hn_mg_destroy(m)
+
+
+def test_server_results_match_alone(hn):
+    srv = hn.hn_server_create(2 << 30, 4)
+    try:
+        reqs = []
+        for j, L in enumerate([6, 8, 5, 7, 6, 9, 4]):
+            coef, b = I.batch_problem(j, L)
+            t = hn.hn_mg_submit(srv, L, b, coef, prec=1)
+            reqs.append((t, L, coef, b))
+        for t, L, coef, b in reqs:
+            status, x, st = hn.hn_mg_poll(srv, t, L, timeout_ns=60_000_000_000)
+            assert status == hn.HN_OK
+            xa, sa, _ = solve(hn, L, b, coef, prec=1)
+            np.testing.assert_array_equal(x, xa)
+            assert st["cycles"] == sa["cycles"]
+        info = hn.hn_server_query(srv)
+        assert info["completed"] == len(reqs) and info["active"] == 0
+        status, _, _ = hn.hn_mg_poll(srv, reqs[0][0], 6, timeout_ns=0)   # forgotten ticket
+    except hn.HnError as e:
+        assert e.status == hn.HN_ERR_ARG
+    finally:
+        hn.hn_server_destroy(srv)
+
+
+def test_profiling_times_kernels_without_changing_results(hn):
+    L = 8
+    b = I.rhs_uniform(L, 21)
+    A = hn.hn_band_create(L)
+    mg = hn.hn_mg_setup(A, prec=1)
+    hn.hn_band_destroy(A)
+    try:
+        x0, _, _ = hn.hn_mg_solve(mg, L, b)
+        hn.hn_mg_set_profiling(mg, True)
+        x1, _, _ = hn.hn_mg_solve(mg, L, b)
+        times = hn.hn_mg_kernel_times(mg)
+        names = {t["name"] for t in times}
+        assert {"jacobi", "defect", "restrict", "prolong", "coarse", "outer_defect"} <= names
+        assert all(t["total_ms"] > 0 for t in times)
+        np.testing.assert_array_equal(x0, x1)
+        hn.hn_mg_set_profiling(mg, False)
+    finally:
+        hn.hn_mg_destroy(mg)
