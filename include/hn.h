@@ -153,6 +153,22 @@ typedef enum {
 hn_status hn_mg_apply(hn_mg* mg, hn_op op, int level, int inner, const void* in1,
                       const void* in2, void* out, double* norm_out);
 
+/* Allocation-free defect and norm (the paper has no counterpart; a service for callers that cannot
+ * allocate device memory at the time of the call: code running while another thread captures a
+ * CUDA graph in global mode, where cudaMalloc is not permitted; processes that hand out their
+ * whole device-memory plan up front; latency-critical paths where cudaMalloc / cudaFree would
+ * synchronize the device).  Computes r = b - A x and ||r||_2 for an operator from hn_band_create.
+ * x, b, r: device pointers to N doubles, 16-byte aligned, caller-owned; norm: device pointer to one
+ * double.  Runs on stream (cudaStream_t, NULL = default stream) and returns without waiting.
+ * The only temporary (one partial sum per 128-node tile) is a fixed device array inside the library
+ * (512 KiB, held by every GPU that loads the library until exit), so at most 8,388,608 nodes
+ * (level 11) are accepted; larger operators get HN_ERR_ARG.  The call allocates nothing.  The first
+ * call on a device looks up that array's address and should come before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (e.g. on two streams) race and must be
+ * ordered by the caller.  Errors: HN_ERR_ARG, HN_ERR_CUDA. */
+hn_status hn_band_defect_norm_static(const hn_band* A, const double* x, const double* b, double* r,
+                                     double* norm, void* stream);
+
 /* Copy the inner-precision bands of one level to the host: FP32 values (9*N_l floats) for an
  * FP32_DC hierarchy, or FP16 codes (9*N_l uint16) plus the 9 FP32 scales for FP16BAND_DC. */
 hn_status hn_mg_get_inner_bands(const hn_mg* mg, int level, void* bands_out, float* scales_out);

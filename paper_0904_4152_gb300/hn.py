@@ -31,6 +31,7 @@ EXPORTS = [
     "hn_mg_destroy", "hn_mg_apply", "hn_mg_get_inner_bands", "hn_server_create", "hn_mg_submit",
     "hn_mg_poll", "hn_server_query", "hn_server_destroy", "hn_last_error", "hn_version",
     "hn_mg_set_profiling", "hn_mg_kernel_times", "hn_mg_last_launches",
+    "hn_band_defect_norm_static",
 ]
 
 
@@ -113,6 +114,7 @@ def lib():
         L.hn_version.restype = ctypes.c_char_p
         L.hn_mg_set_profiling.argtypes = [vp, ip]
         L.hn_mg_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime), ip]
+        L.hn_band_defect_norm_static.argtypes = [vp, vp, vp, vp, vp, vp]
         L.hn_mg_last_launches.argtypes = [vp]
         L.hn_mg_last_launches.restype = ctypes.c_longlong
         _lib = L
@@ -273,6 +275,20 @@ def hn_mg_apply(mg, op, level, inner, in1=None, in2=None, want_norm=False):
                              ctypes.byref(nrm) if want_norm else None))
     del keep
     return (out, nrm.value) if want_norm else out
+
+
+def hn_band_defect_norm_static(A, x, b, r, norm, stream=None):
+    """r = b - A x and ||r|| on caller-owned CUDA float64 tensors (norm: 1 element), with no device
+    allocation inside the library; asynchronous on ``stream`` (a torch.cuda.Stream or None)."""
+    N = lib().hn_band_nodes(A)
+    ptrs = []
+    for t, n in ((x, N), (b, N), (r, N), (norm, 1)):
+        p, dev = _vec_ptr(t, n)
+        if not dev:
+            raise TypeError("x, b, r and norm must be CUDA tensors")
+        ptrs.append(p)
+    s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(lib().hn_band_defect_norm_static(A, *ptrs, s))
 
 
 def hn_mg_get_inner_bands(mg, level, prec):

@@ -1,0 +1,63 @@
+"""The allocation-free defect/norm entry point (hn_band_defect_norm_static) against the solver's own
+defect kernel (hn_mg_apply with HN_OP_DEFECT on an FP64 hierarchy of the same operator).
+
+The entry point serves callers that cannot allocate device memory when they call it (code that
+runs while another thread captures a CUDA graph in global mode, processes whose device memory is
+fully planned up front, latency-critical paths where cudaMalloc would synchronize the device).
+Its scratch is a fixed array inside the library that every call reuses, so the test checks two
+calls in a row with different data, and that operators larger than the array's limit are refused.
+This file is collected last so that a run stopping at the first failure has run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_0904_4152_gb300 import inputs as I
+from gpu_util import abs_spmv, rand_interior, require_gpu
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+U64 = 2.0 ** -53
+
+
+def test_static_defect_norm_matches_solver_kernel_twice():
+    hn = require_gpu()
+    import torch
+    L = 9
+    coef = I.lognormal_coef(L, 123)
+    A = hn.hn_band_create(L, coef)
+    mg = hn.hn_mg_setup(A)
+    try:
+        B = O.assemble(L, coef)
+        N = hn.hn_band_nodes(A)
+        r = torch.empty(N, dtype=torch.float64, device="cuda")
+        nrm = torch.empty(1, dtype=torch.float64, device="cuda")
+        for call, seed in enumerate((1, 2)):
+            x = rand_interior(L, 10 + seed)
+            b = rand_interior(L, 20 + seed)
+            hn.hn_band_defect_norm_static(A, torch.from_numpy(x).cuda(), torch.from_numpy(b).cuda(),
+                                          r, nrm)
+            torch.cuda.synchronize()
+            ref, ref_norm = hn.hn_mg_apply(mg, hn.HN_OP_DEFECT, L, 0, x, b, want_norm=True)
+            got = r.cpu().numpy()
+            tol = 16 * U64 * (abs_spmv(L, B, x) + np.abs(b))
+            assert np.all(np.abs(got - ref) <= tol), call
+            assert abs(nrm.item() - ref_norm) <= 1e-12 * ref_norm, call
+    finally:
+        hn.hn_mg_destroy(mg)
+        hn.hn_band_destroy(A)
+
+
+def test_static_defect_norm_refuses_operators_beyond_its_scratch():
+    hn = require_gpu()
+    import torch
+    L = 12                                   # 16,785,409 nodes > 8,388,608
+    A = hn.hn_band_create(L)
+    try:
+        N = hn.hn_band_nodes(A)
+        v = torch.zeros(N, dtype=torch.float64, device="cuda")
+        nrm = torch.empty(1, dtype=torch.float64, device="cuda")
+        with pytest.raises(hn.HnError) as e:
+            hn.hn_band_defect_norm_static(A, v, v, v, nrm)
+        assert e.value.status == hn.HN_ERR_ARG and "static scratch" in str(e.value)
+    finally:
+        hn.hn_band_destroy(A)
