@@ -1,0 +1,38 @@
+/* hn_tune.h -- launch-shape tuning of the hn solver (performance only; results do not change).
+ *
+ * The V-cycle schedule runs levels above `tail_level` as one launch per step over the device work
+ * list, and levels coarse_L..tail_level of every problem inside one fused launch of one
+ * thread-block cluster (`cluster` blocks of 256 threads) per problem.  The best split depends on
+ * the levels and the batch; hn_mg_autotune measures candidates on the hierarchy itself.
+ */
+#ifndef HN_TUNE_H
+#define HN_TUNE_H
+
+#include "hn.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int tail_level;   /* levels <= tail_level run fused (coarse_L .. HN_MAX_LEVEL) */
+  int cluster;      /* blocks per cluster of the fused launch: 1, 2, 4, 8 or 16 */
+  int pdl;          /* 1: consecutive kernels overlap their launch with the predecessor
+                       (programmatic dependent launch); 0: plain stream order */
+} hn_tuning;
+
+/* Set / read the launch shape used by mg's later solves.  HN_ERR_ARG on values out of range. */
+hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t);
+hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t);
+
+/* Time `reps` solves of b (host vector, N doubles) for every candidate shape (tail_level from
+ * coarse_L to min(L, 9), cluster 1..16) and keep the fastest; the candidate timings are returned
+ * in `times_ms` (may be NULL, capacity `cap` entries, row-major tail_level x 5 cluster sizes) and
+ * the chosen shape in *best.  The solution is unchanged by the shape. */
+hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, double* times_ms,
+                         int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HN_TUNE_H */

@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "engine.h"
+#include "../../include/hn_tune.h"
 
 using namespace hn;
 
@@ -35,6 +36,7 @@ hn_status ensure_solo(hn_mg* mg) {
   std::unique_ptr<Engine> e(new Engine());
   HN_TRY(e->create(mg->prm, 1, mg->L, caps, fine, mg->stream));
   HN_TRY(e->set_members({mg}));
+  if (mg->tuned) e->set_tuning(mg->tuning);
   mg->solo = e.release();
   return HN_OK;
 }
@@ -363,6 +365,75 @@ hn_status hn_mg_set_profiling(hn_mg* mg, int enable) {
   if (!mg) return set_error(HN_ERR_ARG, "null hierarchy");
   HN_TRY(ensure_solo(mg));
   mg->solo->set_profiling(enable != 0);
+  return HN_OK;
+}
+
+hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
+  clear_error();
+  if (!mg || !t) return set_error(HN_ERR_ARG, "null argument");
+  const int c = t->cluster;
+  if (t->tail_level < mg->coarse || t->tail_level > HN_MAX_LEVEL || !(c == 1 || c == 2 || c == 4 || c == 8 || c == 16))
+    return set_error(HN_ERR_ARG, "tail_level in [coarse_L, %d], cluster in {1,2,4,8,16}", HN_MAX_LEVEL);
+  HN_TRY(ensure_solo(mg));
+  if (t->pdl != 0 && t->pdl != 1) return set_error(HN_ERR_ARG, "pdl must be 0 or 1");
+  Tuning tu;
+  tu.tail_level = t->tail_level;
+  tu.cluster = c;
+  tu.pdl = t->pdl;
+  mg->solo->set_tuning(tu);
+  mg->tuning = tu;
+  mg->tuned = true;
+  return HN_OK;
+}
+
+hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t) {
+  clear_error();
+  if (!mg || !t) return set_error(HN_ERR_ARG, "null argument");
+  const Tuning tu = mg->solo ? mg->solo->tuning() : mg->tuning;
+  t->tail_level = tu.tail_level;
+  t->cluster = tu.cluster;
+  t->pdl = tu.pdl;
+  return HN_OK;
+}
+
+hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, double* times_ms,
+                         int cap) {
+  clear_error();
+  if (!mg || !b || reps < 1) return set_error(HN_ERR_ARG, "bad arguments");
+  HN_TRY(ensure_solo(mg));
+  const long long N = N_of(mg->L);
+  double* x = nullptr;
+  HN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&x), (size_t)N * 8));
+  struct Free { double* p; ~Free() { cudaFreeHost(p); } } fr{x};
+  const int clusters[5] = {1, 2, 4, 8, 16};
+  double best_ms = 1e300;
+  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 1};
+  cudaEvent_t e0, e1;
+  HN_CUDA(cudaEventCreate(&e0));
+  HN_CUDA(cudaEventCreate(&e1));
+  struct Ev { cudaEvent_t a, b; ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); } } ev{e0, e1};
+  const int tmax = std::min(mg->L, 9);
+  for (int T = mg->coarse; T <= tmax; ++T)
+    for (int ci = 0; ci < 5; ++ci) {
+      hn_tuning t{T, clusters[ci], 1};
+      HN_TRY(hn_mg_set_tuning(mg, &t));
+      HN_TRY(hn_mg_solve(mg, b, x, 0, 0, nullptr));            // capture + warm-up
+      HN_CUDA(cudaEventRecord(e0, mg->solo->stream()));
+      for (int r = 0; r < reps; ++r) {
+        hn_status st = hn_mg_solve(mg, b, x, 0, 0, nullptr);
+        if (st != HN_OK && st != HN_ERR_NOT_CONVERGED) return st;
+      }
+      HN_CUDA(cudaEventRecord(e1, mg->solo->stream()));
+      HN_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      HN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      const double per = ms / reps;
+      const int idx = (T - mg->coarse) * 5 + ci;
+      if (times_ms && idx < cap) times_ms[idx] = per;
+      if (per < best_ms) { best_ms = per; bt = t; }
+    }
+  HN_TRY(hn_mg_set_tuning(mg, &bt));
+  if (best) *best = bt;
   return HN_OK;
 }
 

@@ -66,11 +66,11 @@ void walk_layout(int L, int coarse, int prec, F&& take) {
   const size_t bs = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
   for (int l = L; l >= coarse; --l) {
     for (int v = 0; v < 4; ++v) take(vec_elems(l) * vs);
-    for (int k = 0; k < 9; ++k) take((size_t)pitch_of(l) * bs);
-    if (prec == P64) take((size_t)pitch_of(l) * 8);
+    for (int k = 0; k < 9; ++k) take(vec_elems(l) * bs);
+    if (prec == P64) take(vec_elems(l) * 8);
   }
   if (prec != P64) {
-    for (int k = 0; k < 9; ++k) take((size_t)pitch_of(L) * 8);
+    for (int k = 0; k < 9; ++k) take(vec_elems(L) * 8);
     take(vec_elems(L) * 8);
     take(vec_elems(L) * 8);
   }
@@ -190,15 +190,15 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
     d.rhs = vecs[2];
     d.r = vecs[3];
     for (int k = 0; k < 9; ++k) {
-      if (prec == P64) d.band[k] = b.take<double>(d.pitch);
-      else if (prec == P32) d.band[k] = b.take<float>(d.pitch);
-      else d.band[k] = b.take<__half>(d.pitch);
+      if (prec == P64) d.band[k] = b.take<double>(vec_elems(l)) + H;
+      else if (prec == P32) d.band[k] = b.take<float>(vec_elems(l)) + H;
+      else d.band[k] = b.take<__half>(vec_elems(l)) + H;
     }
     for (int k = 0; k < 9; ++k) d.scale[k] = 1.0f;
-    if (prec == P64) d.wdinv = b.take<double>(d.pitch);
+    if (prec == P64) d.wdinv = b.take<double>(vec_elems(l)) + H;
   }
   if (prec != P64) {
-    for (int k = 0; k < 9; ++k) P.band64[k] = b.take<double>(pitch_of(L));
+    for (int k = 0; k < 9; ++k) P.band64[k] = b.take<double>(vec_elems(L)) + halo_of(L);
     P.x64 = b.take<double>(vec_elems(L)) + halo_of(L);
     P.b64 = b.take<double>(vec_elems(L)) + halo_of(L);
   } else {
@@ -330,6 +330,12 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   cap_ = cap;
   Lmax_ = Lmax;
   s_ = s;
+  {
+    static std::once_flag once;
+    static cudaError_t prep = cudaSuccess;
+    std::call_once(once, [] { prep = prepare_kernels(); });
+    HN_CUDA(prep);
+  }
   maxGrid_ = sm_count() * 4;
   size_t bytes = 0;
   auto take = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
@@ -372,6 +378,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   E_.prm = prm;
   E_.active_host = dActive;
   E_.iter = iter;
+  E_.pdl = tune_.pdl;
   E_.iter_limit = (unsigned)(prm.max_cycles + prm.max_outer + 8);
   for (int l = 0; l <= kMaxLevel; ++l) {
     lists_[l] = TileList{dItems_[l], dCounts_ + l};
@@ -422,6 +429,11 @@ hn_status Engine::set_members(const std::vector<hn_mg*>& slots) {
   HN_CUDA(cudaMemcpyAsync(dP_, probs.data(), sizeof(ProblemDev) * cap_, cudaMemcpyHostToDevice, s_));
   members_ = slots;
   members_.resize(cap_, nullptr);
+  unsigned mask = 0;
+  for (hn_mg* mg : members_)
+    if (mg) mask |= 1u << mg->L;
+  if (mask != topMask_ && !topMaskAll_) graphsValid_ = false;
+  topMask_ = mask;
   return HN_OK;
 }
 
@@ -471,7 +483,7 @@ long long Engine::launch_bytes(int cls, int level) const {
   double per = 0;
   switch (cls) {
     case KC_JACOBI: per = 9 * bb + 3 * vb + wd; break;
-    case KC_JACOBI_FIRST: per = 9 * bb + 3 * vb + wd; break;   // top level with a nonzero iterate
+    case KC_JACOBI_FIRST: per = 9 * bb + 2 * vb + wd; break;   // two fused steps from x = 0
     case KC_DEFECT: per = 9 * bb + 3 * vb; break;
     case KC_CHECK: per = 9 * bb + 2 * vb; break;
     case KC_RESTRICT: per = 1.25 * vb; break;                   // per fine node
@@ -516,15 +528,25 @@ hn_status Engine::mark(cudaStream_t s, int cls, int level, bool begin) {
 
 hn_status Engine::issue_vcycle(cudaStream_t s, int want) {
   const int c = prm_.coarse, pre = prm_.pre, post = prm_.post;
-  for (int l = Lmax_; l > c; --l) {
-    HN_LAUNCH(KC_JACOBI_FIRST, l, launch_jacobi(E_, lists_[l], l, want, 0, 1, grid_[l], s));
-    for (int sw = 2; sw <= pre; ++sw)
-      HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (sw - 1) & 1, 0, grid_[l], s));
+  const int T = std::max(tune_.tail_level, c);
+  for (int l = Lmax_; l > T; --l) {
+    const bool top = topMaskAll_ || ((topMask_ >> l) & 1u);   // a finest level: lagged check
+    if (pre >= 2) {
+      HN_LAUNCH(KC_JACOBI_FIRST, l, launch_pre12(E_, lists_[l], l, want, grid_[l], s));
+      if (top) HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
+      if (!pre_fuses(prm_.prec) || top)
+        HN_LAUNCH(KC_JACOBI, l, launch_pre2b(E_, lists_[l], l, want, grid_[l], s));
+      for (int sw = 3; sw <= pre; ++sw)
+        HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (sw - 1) & 1, 0, grid_[l], s));
+    } else {
+      HN_LAUNCH(KC_JACOBI_FIRST, l, launch_jacobi(E_, lists_[l], l, want, 0, 1, grid_[l], s));
+      if (top) HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
+    }
     HN_LAUNCH(KC_DEFECT, l, launch_defect(E_, lists_[l], l, want, pre & 1, grid_[l], s));
     HN_LAUNCH(KC_RESTRICT, l, launch_restrict(E_, lists_[l - 1], l, want, grid_[l - 1], s));
   }
-  HN_LAUNCH(KC_COARSE, c, launch_coarse(E_, lists_[c], want, grid_[c], s));
-  for (int l = c + 1; l <= Lmax_; ++l) {
+  HN_LAUNCH(KC_TAIL, T, launch_tail(E_, T, want, tune_.cluster, s));
+  for (int l = T + 1; l <= Lmax_; ++l) {
     HN_LAUNCH(KC_PROLONG, l, launch_prolong(E_, lists_[l], l, want, pre & 1, grid_[l], s));
     for (int sw = 1; sw <= post; ++sw)
       HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (pre + sw - 1) & 1, 0, grid_[l], s));
@@ -536,29 +558,21 @@ hn_status Engine::issue_init(cudaStream_t s, cudaGraphConditionalHandle h, int u
   HN_LAUNCH0(launch_boundary_check(E_, s));
   HN_LAUNCH0(launch_norm_b(E_, fine_, fineGrid_, s));
   HN_LAUNCH0(launch_control(E_, CTRL_INIT, s));
-  if (prm_.prec == P64) {
-    HN_LAUNCH0(launch_check(E_, fine_, PH_CHECK, 0, fineGrid_, s));
-    HN_LAUNCH0(launch_control(E_, CTRL_CHECK0, s));
-  }
-  HN_LAUNCH0(launch_summary(E_, h, use_h, s));
+  HN_LAUNCH0(launch_summary(E_, h, use_h, 0, s));
   return HN_OK;
 }
 
 hn_status Engine::issue_iteration(cudaStream_t s, cudaGraphConditionalHandle h, int use_h) {
   if (prm_.prec == P64) {
     HN_TRY(issue_vcycle(s, PH_CYCLE));
-    HN_LAUNCH(KC_CHECK, -1, launch_check(E_, fine_, PH_CYCLE, 0, fineGrid_, s));
-    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_CHECK, s));
   } else {
     HN_LAUNCH(KC_OUTER_DEFECT, -1, launch_outer_defect(E_, fine_, fineGrid_, s));
     HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_OUTER, s));
     HN_TRY(issue_vcycle(s, PH_INNER));
-    HN_LAUNCH(KC_CHECK, -1, launch_check(E_, fine_, PH_INNER, 0, fineGrid_, s));
-    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_INNER, s));
     HN_LAUNCH(KC_UPDATE, -1, launch_update(E_, fine_, fineGrid_, s));
     HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_POST, s));
   }
-  HN_LAUNCH0(launch_summary(E_, h, use_h, s));
+  HN_LAUNCH0(launch_summary(E_, h, use_h, 1, s));
   return HN_OK;
 }
 
@@ -696,7 +710,8 @@ void Engine::set_profiling(bool on) {
 
 int Engine::kernel_times(hn_kernel_time* out, int max) const {
   static const char* names[KC_COUNT] = {"jacobi", "jacobi_first", "defect", "restrict", "prolong",
-                                        "coarse", "check", "outer_defect", "update", "control"};
+                                        "coarse", "check", "outer_defect", "update", "control",
+                                        "tail"};
   int n = 0;
   for (int c = 0; c < KC_COUNT; ++c)
     for (int l = 0; l <= kMaxLevel; ++l) {

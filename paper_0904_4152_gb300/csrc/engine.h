@@ -56,7 +56,15 @@ size_t hierarchy_bytes(int L, int coarse, int prec);
 // kernel classes timed in profiling mode
 enum KClass {
   KC_JACOBI = 0, KC_JACOBI_FIRST, KC_DEFECT, KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_CHECK,
-  KC_OUTER_DEFECT, KC_UPDATE, KC_CONTROL, KC_COUNT
+  KC_OUTER_DEFECT, KC_UPDATE, KC_CONTROL, KC_TAIL, KC_COUNT
+};
+
+// launch shape of the schedule: levels <= tail_level run fused in one cluster launch of
+// `cluster` blocks per problem; levels above run as one launch per step
+struct Tuning {
+  int tail_level = 7;
+  int cluster = 16;
+  int pdl = 0;      // programmatic dependent launch between consecutive kernels
 };
 
 class Engine;
@@ -83,6 +91,8 @@ struct hn_mg {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   hn::Engine* solo = nullptr;
+  hn::Tuning tuning{};        // launch shape chosen for this hierarchy (hn_mg_set_tuning)
+  bool tuned = false;
   ~hn_mg();
 };
 
@@ -119,6 +129,11 @@ class Engine {
 
   void set_profiling(bool on);
   void set_iter_limit(unsigned lim) { E_.iter_limit = lim; graphsValid_ = false; }
+  void set_tuning(const Tuning& t) { tune_ = t; E_.pdl = t.pdl; graphsValid_ = false; }
+  const Tuning& tuning() const { return tune_; }
+  // levels that may be some problem's finest level (their first smoothing step may start from a
+  // nonzero iterate); all levels for the server
+  void set_top_mask_all() { topMaskAll_ = true; graphsValid_ = false; }
   int kernel_times(hn_kernel_time* out, int max) const;
 
   long long last_launches() const { return lastLaunches_; }
@@ -159,6 +174,9 @@ class Engine {
   cudaGraphExec_t gSolve_ = nullptr, gInit_ = nullptr, gIter_ = nullptr;
   bool graphsValid_ = false;
   int initLaunches_ = 0, iterLaunches_ = 0, counting_ = 0;
+  Tuning tune_{};
+  unsigned topMask_ = 0;
+  bool topMaskAll_ = false;
   long long lastLaunches_ = 0;
   // profiling
   bool profiling_ = false;

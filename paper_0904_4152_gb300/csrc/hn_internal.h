@@ -32,8 +32,9 @@ inline long long halo_of(int L) { return round_up(n_of(L) + 8, 32); }
 enum Prec { P64 = 0, P32 = 1, P16 = 2 };
 
 // ------------------------------------------------------------------- device descriptors
-// One level of one problem.  Vectors point at element 0 (a zero halo of halo_of(L) elements sits
-// on either side); bands are 9 arrays of pitch elements of the level's storage type.
+// One level of one problem.  Vectors and bands point at element 0 of pitch elements; a zero halo
+// of halo_of(L) elements sits on either side of every array, so stencil windows of any padded row
+// stay inside the allocation.
 struct LevelDev {
   const void* band[9];   // double (FP64 hierarchy), float (FP32), __half (FP16 codes)
   const double* wdinv;   // FP64 hierarchy only: omega / diag, pitch doubles
@@ -123,7 +124,7 @@ struct EngineDev {
   unsigned int* active_host;   // mapped host word: problems not done after the iteration
   unsigned int* iter;          // iterations since the solve started (device)
   unsigned int iter_limit;     // beyond it every running problem stops as not converged
-  unsigned int pad2;
+  int pdl;                     // launch with programmatic dependent launch (host-side flag)
 };
 
 // Launch wrappers for one step of the schedule; grid = CTAs of 256 threads.  level < 0 means
@@ -136,6 +137,18 @@ cudaError_t launch_spmv(const EngineDev& E, TileList tl, int level, int want, in
                         cudaStream_t s);
 cudaError_t launch_check(const EngineDev& E, TileList fine, int want, int x_sel, int grid,
                          cudaStream_t s);
+// first two smoothing steps: fused from a zero iterate (PRE12 alone), else step 1 (PRE12) and
+// step 2 (PRE2B); pre_fuses(prec) tells whether the zero-iterate fusion exists for a precision
+cudaError_t launch_pre12(const EngineDev& E, TileList tl, int level, int want, int grid,
+                         cudaStream_t s);
+cudaError_t launch_pre2b(const EngineDev& E, TileList tl, int level, int want, int grid,
+                         cudaStream_t s);
+bool pre_fuses(int prec);
+// the V cycle on levels coarse..min(T, L) of every problem in phase `want`, one thread-block
+// cluster of `cluster` blocks per problem slot
+cudaError_t launch_tail(const EngineDev& E, int T, int want, int cluster, cudaStream_t s);
+// one-time kernel attributes (cluster-size opt-in); call outside stream capture
+cudaError_t prepare_kernels();
 cudaError_t launch_restrict(const EngineDev& E, TileList tl_coarse, int fine_level, int want,
                             int grid, cudaStream_t s);
 cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want, int x_sel,
@@ -144,13 +157,16 @@ cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, c
 cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
 cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
 cudaError_t launch_norm_b(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
-cudaError_t launch_control(const EngineDev& E, int kind, cudaStream_t s);
+// kind: ControlKind; level: for CTRL_PRE, the finest level whose problems are checked
+cudaError_t launch_control(const EngineDev& E, int kind, cudaStream_t s, int level = -1);
+// end_of_iteration: clear the zero-iterate flag of running cycles (iteration graph only)
 cudaError_t launch_summary(const EngineDev& E, cudaGraphConditionalHandle h, int use_handle,
-                           cudaStream_t s);
+                           int end_of_iteration, cudaStream_t s);
 cudaError_t launch_boundary_check(const EngineDev& E, cudaStream_t s);
 
 enum ControlKind {
-  CTRL_INIT = 0, CTRL_CHECK = 1, CTRL_OUTER = 2, CTRL_INNER = 3, CTRL_POST = 4, CTRL_CHECK0 = 5
+  CTRL_INIT = 0, CTRL_CHECK = 1, CTRL_OUTER = 2, CTRL_INNER = 3, CTRL_POST = 4, CTRL_CHECK0 = 5,
+  CTRL_PRE = 6   // lagged convergence test after the first smoothing step of a cycle
 };
 
 int sm_count();

@@ -11,7 +11,11 @@
 // vectors (double2 pairs, float4, or 4 packed halves); the three x rows of the stencil are loaded
 // as aligned 4-vectors because the row offset n = 2^L + 1 equals 2^L plus one column, and the
 // one- or two-column overhang at each side comes from the neighbouring lanes by warp shuffles.
+#include <cooperative_groups.h>
+
 #include "hn_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace hn {
 
@@ -19,18 +23,44 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Programmatic dependent launch: a kernel lets its successor in the stream launch as soon as all
+// of its blocks are running (launch_dependents), and waits for its predecessor's completion and
+// memory before touching any data (wait).  Both are no-ops for a normal launch.
+__device__ __forceinline__ void pdl_start() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
 // -------------------------------------------------------------------- precision policies
 struct F64 { using B = double; using V = double; using A = double; static constexpr int prec = P64; };
 struct F32 { using B = float; using V = float; using A = float; static constexpr int prec = P32; };
 struct F16 { using B = __half; using V = float; using A = float; static constexpr int prec = P16; };
 
+// Load kinds: LD_NC reads global memory through the non-coherent path (data written by an
+// earlier launch); LD_CG reads global memory from L2 (data written earlier in the same launch by
+// other SMs of the cluster); LD_GEN is a plain generic load (data in shared memory).  Bands are
+// never written by the solver: NC from global memory, GEN from shared memory.
+enum { LD_NC = 0, LD_CG = 1, LD_GEN = 2 };
+template <int LK> __device__ __forceinline__ constexpr int band_kind() { return LK == LD_GEN ? LD_GEN : LD_NC; }
+
+template <int LK, class T> __device__ __forceinline__ T ldk(const T* p) {
+  if constexpr (LK == LD_NC) return __ldg(p);
+  else if constexpr (LK == LD_CG) return __ldcg(p);
+  else return *p;
+}
+template <int LK> __device__ __forceinline__ double ld1(const double* p) { return ldk<LK>(p); }
+template <int LK> __device__ __forceinline__ float ld1(const float* p) { return ldk<LK>(p); }
+
+template <int LK>
 __device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = ldk<LK>(q);
+  const double2 b = ldk<LK>(q + 1);
   o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
+template <int LK>
 __device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 a = ldk<LK>(reinterpret_cast<const float4*>(p));
   o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
 }
 __device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
@@ -40,7 +70,7 @@ __device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
 __device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
   *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
-// plain (coherent) loads for data the same kernel also writes
+// plain (coherent) loads for data the same thread also writes
 __device__ __forceinline__ void ld4c(const double* p, double (&o)[4]) {
   const double2 a = reinterpret_cast<const double2*>(p)[0];
   const double2 b = reinterpret_cast<const double2*>(p)[1];
@@ -52,116 +82,108 @@ __device__ __forceinline__ void ld4c(const float* p, float (&o)[4]) {
 }
 
 // 4 consecutive band values of band k at node i0, in the arithmetic type
-template <class Pol>
+template <class Pol, int LKB = LD_NC>
 __device__ __forceinline__ void load_band(const void* band, float scale, long long i0,
                                           typename Pol::A (&o)[4]) {
   if constexpr (Pol::prec == P16) {
-    const uint2 u = __ldg(reinterpret_cast<const uint2*>(static_cast<const __half*>(band) + i0));
+    const uint2 u = ldk<LKB>(reinterpret_cast<const uint2*>(static_cast<const __half*>(band) + i0));
     const __half2 h0 = *reinterpret_cast<const __half2*>(&u.x);
     const __half2 h1 = *reinterpret_cast<const __half2*>(&u.y);
     const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
     o[0] = scale * f0.x; o[1] = scale * f0.y; o[2] = scale * f1.x; o[3] = scale * f1.y;
   } else {
-    ld4(static_cast<const typename Pol::B*>(band) + i0, o);
+    ld4<LKB>(static_cast<const typename Pol::B*>(band) + i0, o);
   }
 }
 
-// Row window of x around the lane's 4 nodes: w[o + 2] = x[a + o], o = -2..5, a aligned to 4.
-template <class V>
-__device__ __forceinline__ void load_row(const V* __restrict__ x, long long a, int lane, V (&w)[8]) {
+// Row window around the lane's 4 nodes: w[o + 2] = v[a + o], o = -2..5, a aligned to 4.
+template <class V, int LK>
+__device__ __forceinline__ void load_row(const V* __restrict__ v, long long a, int lane, V (&w)[8]) {
   V c[4];
-  ld4(x + a, c);
+  ld4<LK>(v + a, c);
   V l2 = __shfl_up_sync(kFull, c[2], 1), l1 = __shfl_up_sync(kFull, c[3], 1);
   V r0 = __shfl_down_sync(kFull, c[0], 1), r1 = __shfl_down_sync(kFull, c[1], 1);
-  if (lane == 0) { l2 = __ldg(x + a - 2); l1 = __ldg(x + a - 1); }
-  if (lane == 31) { r0 = __ldg(x + a + 4); r1 = __ldg(x + a + 5); }
+  if (lane == 0) { l2 = ld1<LK>(v + a - 2); l1 = ld1<LK>(v + a - 1); }
+  if (lane == 31) { r0 = ld1<LK>(v + a + 4); r1 = ld1<LK>(v + a + 5); }
   w[0] = l2; w[1] = l1; w[2] = c[0]; w[3] = c[1]; w[4] = c[2]; w[5] = c[3]; w[6] = r0; w[7] = r1;
 }
 
-// acc[j] = sum_k band_k[i0+j] * x[i0+j+off_k] in band order k = 0..8; also returns x[i0+j] and
-// the diagonal.  shift = 2^L = n - 1, so off_k = dy*n + dx = dy*shift + (dy + dx).
-template <class Pol>
-__device__ __forceinline__ void stencil4(const void* const* band, const float* scale,
-                                         const typename Pol::V* __restrict__ x, long long i0,
-                                         long long shift, int lane, typename Pol::A (&acc)[4],
-                                         typename Pol::V (&xc)[4], typename Pol::A (&dg)[4]) {
+// acc[j] = sum_k band_k[i0+j] * x[i0+j+off_k] over the windows w (rows dy = -1, 0, 1), in band
+// order k = 0..8; also the diagonal.  off_k = dy*n + dx = dy*shift + (dy + dx), shift = n - 1.
+template <class Pol, int LKB>
+__device__ __forceinline__ void stencil_windows(const void* const* band, const float* scale,
+                                                const typename Pol::V (&w)[3][8], long long i0,
+                                                typename Pol::A (&acc)[4],
+                                                typename Pol::A (&dg)[4]) {
   using A = typename Pol::A;
-  using V = typename Pol::V;
 #pragma unroll
   for (int j = 0; j < 4; ++j) acc[j] = A(0);
 #pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
-    V w[8];
-    load_row<V>(x, i0 + dy * shift, lane, w);
-    if (dy == 0) {
+  for (int k = 0; k < 9; ++k) {
+    const int dy = k / 3 - 1, dx = k % 3 - 1;
+    A b[4];
+    load_band<Pol, LKB>(band[k], scale ? scale[k] : 1.0f, i0, b);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) xc[j] = w[j + 2];
-    }
+    for (int j = 0; j < 4; ++j) acc[j] = fma(b[j], A(w[dy + 1][j + dy + dx + 2]), acc[j]);
+    if (k == 4) {
 #pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int k = (dy + 1) * 3 + (dx + 1);
-      A b[4];
-      load_band<Pol>(band[k], scale ? scale[k] : 1.0f, i0, b);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = fma(b[j], A(w[j + dy + dx + 2]), acc[j]);
-      if (k == 4) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dg[j] = b[j];
-      }
+      for (int j = 0; j < 4; ++j) dg[j] = b[j];
     }
   }
 }
 
 // FP16-band operator in row-sum form (array 4 holds the row sum rho):
 // acc[j] = rho x_i + sum_{k != 4} a_k (x_{i+off_k} - x_i) in band order; dg[j] = rho - sum a_k.
-__device__ __forceinline__ void stencil4_rowsum(const void* const* band, const float* scale,
-                                                const float* __restrict__ x, long long i0,
-                                                long long shift, int lane, float (&acc)[4],
-                                                float (&xc)[4], float (&dg)[4]) {
-  float w[3][8];
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) load_row<float>(x, i0 + dy * shift, lane, w[dy + 1]);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) xc[j] = w[1][j + 2];
+template <int LKB>
+__device__ __forceinline__ void stencil_windows_rowsum(const void* const* band, const float* scale,
+                                                       const float (&w)[3][8], long long i0,
+                                                       float (&acc)[4], float (&dg)[4]) {
   float rho[4];
-  load_band<F16>(band[4], scale[4], i0, rho);
+  load_band<F16, LKB>(band[4], scale[4], i0, rho);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) { acc[j] = rho[j] * xc[j]; dg[j] = rho[j]; }
+  for (int j = 0; j < 4; ++j) { acc[j] = rho[j] * w[1][j + 2]; dg[j] = rho[j]; }
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     if (k == 4) continue;
     const int dy = k / 3 - 1, dx = k % 3 - 1;
     float b[4];
-    load_band<F16>(band[k], scale[k], i0, b);
+    load_band<F16, LKB>(band[k], scale[k], i0, b);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      acc[j] = fmaf(b[j], w[dy + 1][j + dy + dx + 2] - xc[j], acc[j]);
+      acc[j] = fmaf(b[j], w[dy + 1][j + dy + dx + 2] - w[1][j + 2], acc[j]);
       dg[j] -= b[j];
     }
   }
 }
 
 // diagonal of the row-sum form without x (for the zero-guess Jacobi step)
+template <int LKB>
 __device__ __forceinline__ void diag_rowsum(const void* const* band, const float* scale,
                                             long long i0, float (&dg)[4]) {
-  load_band<F16>(band[4], scale[4], i0, dg);
+  load_band<F16, LKB>(band[4], scale[4], i0, dg);
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     if (k == 4) continue;
     float b[4];
-    load_band<F16>(band[k], scale[k], i0, b);
+    load_band<F16, LKB>(band[k], scale[k], i0, b);
 #pragma unroll
     for (int j = 0; j < 4; ++j) dg[j] -= b[j];
   }
 }
 
-template <class Pol>
-__device__ __forceinline__ void apply_op4(const void* const* band, const float* scale,
-                                          const typename Pol::V* __restrict__ x, long long i0,
-                                          long long shift, int lane, typename Pol::A (&acc)[4],
-                                          typename Pol::V (&xc)[4], typename Pol::A (&dg)[4]) {
-  if constexpr (Pol::prec == P16) stencil4_rowsum(band, scale, x, i0, shift, lane, acc, xc, dg);
-  else stencil4<Pol>(band, scale, x, i0, shift, lane, acc, xc, dg);
+// y = A x at the lane's 4 nodes (x read with load kind LK); xc = x at the nodes, dg = diagonal
+template <class Pol, int LK>
+__device__ __forceinline__ void apply_op4(const LevelDev& d, const typename Pol::V* __restrict__ x,
+                                          long long i0, long long shift, int lane,
+                                          typename Pol::A (&acc)[4], typename Pol::V (&xc)[4],
+                                          typename Pol::A (&dg)[4]) {
+  typename Pol::V w[3][8];
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) load_row<typename Pol::V, LK>(x, i0 + dy * shift, lane, w[dy + 1]);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) xc[j] = w[1][j + 2];
+  if constexpr (Pol::prec == P16) stencil_windows_rowsum<band_kind<LK>()>(d.band, d.scale, w, i0, acc, dg);
+  else stencil_windows<Pol, band_kind<LK>()>(d.band, nullptr, w, i0, acc, dg);
 }
 
 // deterministic warp sum (butterfly; every lane ends with the same value)
@@ -186,14 +208,276 @@ __device__ double block_sum256(double v, double* sh) {
   return t;   // valid in warp 0
 }
 
-enum BandMode { M_SPMV = 0, M_DEFECT = 1, M_JACOBI = 2, M_JACOBI_FIRST = 3, M_CHECK = 4 };
+// Fixed-order sum of one problem's per-tile partials by one block of 256 threads (thread t adds
+// slots t, t+256, ... in order, then the block tree).  Every caller uses this order, so a
+// problem's norm does not depend on which kernel or batch computed it.  Valid in thread 0.
+__device__ double problem_partial_sum(const double* part, int ntiles, double* sh) {
+  double t = 0.0;
+  for (int q = threadIdx.x; q < ntiles; q += blockDim.x) t += __ldcg(part + q);
+  return block_sum256(t, sh);
+}
 
-// One warp-tile per loop trip.  in_sel selects the iterate buffer read; Jacobi writes the other.
+__host__ __device__ inline int fine_tiles(int L) {
+  const long long n = (1LL << L) + 1;
+  return (int)((n * n + kTile - 1) / kTile);
+}
+
+// Lagged convergence test: the first smoothing step of a cycle from a nonzero iterate computes
+// the residual of that iterate; nrm is its norm.  FP64 multigrid stops when relres <= tol (the
+// iterate in buffer 0 is the result) or at the cycle cap; inner cycles of the defect correction
+// stop at the inner tolerance or the inner caps (the correction goes to the update).  Otherwise
+// the cycle proceeds and is counted.
+__device__ void pre_check(ProbState& st, const Params& prm, double nrm) {
+  if (!isfinite(nrm)) { st.status = HN_ERR_NONFINITE; st.phase = PH_DONE; return; }
+  if (st.phase == PH_CYCLE) {
+    st.dnorm = nrm;
+    st.relres = nrm / st.bnorm;
+    if (st.relres <= prm.tol) { st.status = HN_OK; st.phase = PH_DONE; }
+    else if (st.cycles >= prm.max_cycles) { st.status = HN_ERR_NOT_CONVERGED; st.phase = PH_DONE; }
+    else st.cycles += 1;
+  } else {
+    st.inner_res = nrm;
+    if (nrm <= prm.inner_tol * st.inner_ref || st.inner_k >= prm.inner_max ||
+        st.inner_cycles >= prm.max_cycles)
+      st.phase = PH_UPDATE;
+    else { st.inner_k += 1; st.inner_cycles += 1; st.cycles += 1; }
+  }
+}
+
+// Modes of the band kernel.  PRE12 / PRE2B split the first two smoothing steps: from a zero
+// iterate both steps fuse into one pass (x1 = omega D^-1 b is formed on the fly from windows of b
+// and D, then x2 = x1 + omega D^-1 (b - A x1) goes to buffer 0) and PRE2B skips the tile;
+// otherwise PRE12 does step 1 (buffer 0 -> 1) and PRE2B step 2 (1 -> 0).  The FP16 row-sum
+// diagonal needs all bands at every window position, so FP16 does not fuse.
+enum BandMode {
+  M_SPMV = 0, M_DEFECT = 1, M_JACOBI = 2, M_JACOBI_FIRST = 3, M_CHECK = 4, M_PRE12 = 5,
+  M_PRE2B = 6
+};
+
+template <class Pol> __device__ __forceinline__ constexpr bool fuses_pre() { return Pol::prec != P16; }
+
+// omega / diag at the lane's 4 nodes from the stored array (FP64) or the diagonal band (FP32)
+template <class Pol, int LKB>
+__device__ __forceinline__ void wd4_of(const LevelDev& d, long long i0, typename Pol::A omega,
+                                       const typename Pol::A (&dg)[4], typename Pol::A (&wd)[4]) {
+  if constexpr (Pol::prec == P64) {
+    ld4<LKB>(d.wdinv + i0, wd);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wd[j] = omega / dg[j];
+  }
+}
+
+// One warp-tile of the band kernel on level d.  zg: the iterate of this level is zero.
+template <class Pol, int MODE, int LK>
+__device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bool zg, long long i0,
+                                          int lane, int in_sel, typename Pol::A omega,
+                                          double* partial_slot) {
+  using A = typename Pol::A;
+  using V = typename Pol::V;
+  constexpr int LKB = band_kind<LK>();
+  const V* rhs = static_cast<const V*>(d.rhs);
+  if constexpr (MODE == M_PRE2B) {
+    if (zg && fuses_pre<Pol>()) return;
+  }
+  if constexpr (MODE == M_JACOBI_FIRST || MODE == M_PRE12) {
+    if (zg && (MODE == M_JACOBI_FIRST || !fuses_pre<Pol>())) {   // x = 0: x' = omega D^-1 rhs
+      V b[4], out[4];
+      ld4<LK>(rhs + i0, b);
+      if constexpr (Pol::prec == P64) {
+        double wd[4];
+        ld4<LKB>(d.wdinv + i0, wd);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[j] = wd[j] * b[j];
+      } else {
+        A dgv[4];
+        if constexpr (Pol::prec == P16) diag_rowsum<LKB>(d.band, d.scale, i0, dgv);
+        else load_band<Pol, LKB>(d.band[4], 1.0f, i0, dgv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[j] = (omega / dgv[j]) * A(b[j]);
+      }
+      st4(static_cast<V*>(d.x[1]) + i0, out);
+      return;
+    }
+    if constexpr (MODE == M_PRE12 && fuses_pre<Pol>()) {
+      if (zg) {                                   // two steps from zero in one pass
+        V bw[3][8], dw[3][8], x1[3][8];
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+          load_row<V, LK>(rhs, i0 + dy * shift, lane, bw[dy + 1]);
+          if constexpr (Pol::prec == P64) load_row<V, LKB>(d.wdinv, i0 + dy * shift, lane, dw[dy + 1]);
+          else load_row<V, LKB>(static_cast<const V*>(d.band[4]), i0 + dy * shift, lane, dw[dy + 1]);
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            if constexpr (Pol::prec == P64) x1[r][o] = dw[r][o] * bw[r][o];
+            else x1[r][o] = dw[r][o] != V(0) ? (omega / dw[r][o]) * bw[r][o] : V(0);
+          }
+        A acc[4], dg[4];
+        stencil_windows<Pol, LKB>(d.band, nullptr, x1, i0, acc, dg);
+        A wd[4];
+        wd4_of<Pol, LKB>(d, i0, omega, dg, wd);
+        V out[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[j] = fma(wd[j], A(bw[1][j + 2]) - acc[j], A(x1[1][j + 2]));
+        st4(static_cast<V*>(d.x[0]) + i0, out);
+        return;
+      }
+    }
+  }
+  int src = in_sel, dst = 1 - in_sel;
+  if constexpr (MODE == M_JACOBI_FIRST || MODE == M_PRE12) { src = 0; dst = 1; }
+  if constexpr (MODE == M_PRE2B) { src = 1; dst = 0; }
+  const V* xin = static_cast<const V*>(d.x[src]);
+  A acc[4], dg[4];
+  V xc[4];
+  apply_op4<Pol, LK>(d, xin, i0, shift, lane, acc, xc, dg);
+  if constexpr (MODE == M_SPMV) {
+    V out[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = V(acc[j]);
+    st4(static_cast<V*>(d.r) + i0, out);
+  } else {
+    V b[4];
+    ld4<LK>(rhs + i0, b);
+    if constexpr (MODE == M_DEFECT) {
+      V out[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[j] = V(A(b[j]) - acc[j]);
+      st4(static_cast<V*>(d.r) + i0, out);
+    } else if constexpr (MODE == M_CHECK) {
+      double q = 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const double r = double(A(b[j]) - acc[j]);
+        q += r * r;
+      }
+      q = warp_sum(q);
+      if (lane == 0) *partial_slot = q;
+    } else {                                      // a Jacobi step src -> dst
+      A wd[4];
+      wd4_of<Pol, LKB>(d, i0, omega, dg, wd);
+      V out[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[j] = fma(wd[j], A(b[j]) - acc[j], A(xc[j]));
+      st4(static_cast<V*>(d.x[dst]) + i0, out);
+      if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST) {
+        if (partial_slot) {                       // residual norm of the iterate (lagged check)
+          double q = 0.0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const double r = double(A(b[j]) - acc[j]);
+            q += r * r;
+          }
+          q = warp_sum(q);
+          if (lane == 0) *partial_slot = q;
+        }
+      }
+    }
+  }
+}
+
+// Full-weighting restriction of the fine defect onto coarse tile i0 (coarse boundary and padding
+// nodes get 0).  Summation order: fine rows 2J-1, 2J, 2J+1, columns 2I-1, 2I, 2I+1, weights 1/4,
+// 1/2, 1/4 x 1/4, 1/2, 1/4 (products by powers of two are exact).
+template <class V, int LK>
+__device__ __forceinline__ void restrict_tile(const LevelDev& f, const LevelDev& c, long long i0) {
+  const long long nc = c.n, nf = f.n, Nc = nc * nc;
+  const V* r = static_cast<const V*>(f.r);
+  V out[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const long long ci = i0 + j;
+    V v = V(0);
+    if (ci < Nc) {
+      const long long J = ci / nc, I = ci - J * nc;
+      if (I > 0 && J > 0 && I < nc - 1 && J < nc - 1) {
+        const long long fc = 2 * J * nf + 2 * I;
+        const V q = V(0.25), h = V(0.5);
+        v = q * ld1<LK>(r + fc - nf - 1);
+        v = fma(h, ld1<LK>(r + fc - nf), v);
+        v = fma(q, ld1<LK>(r + fc - nf + 1), v);
+        v = fma(h, ld1<LK>(r + fc - 1), v);
+        v = v + ld1<LK>(r + fc);
+        v = fma(h, ld1<LK>(r + fc + 1), v);
+        v = fma(q, ld1<LK>(r + fc + nf - 1), v);
+        v = fma(h, ld1<LK>(r + fc + nf), v);
+        v = fma(q, ld1<LK>(r + fc + nf + 1), v);
+      }
+    }
+    out[j] = v;
+  }
+  st4(static_cast<V*>(c.rhs) + i0, out);
+}
+
+// x_f[x_sel] += P e_c on fine tile i0 (bilinear interpolation of the coarse iterate, buffer 0);
+// boundary fine nodes are left unchanged.
+template <class V, int LK>
+__device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& c, int x_sel,
+                                             long long i0) {
+  const long long nf = f.n, nc = c.n, Nf = nf * nf;
+  const V* e = static_cast<const V*>(c.x[0]);
+  V* x = static_cast<V*>(f.x[x_sel]);
+  V v[4];
+  if constexpr (LK == LD_NC) ld4c(x + i0, v);   // read and rewritten by this thread only
+  else ld4<LK>(x + i0, v);                      // written earlier in this launch
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const long long fi = i0 + j;
+    if (fi >= Nf) continue;
+    const long long iy = fi / nf, ix = fi - iy * nf;
+    if (ix == 0 || iy == 0 || ix == nf - 1 || iy == nf - 1) continue;
+    const long long cx0 = ix >> 1, cx1 = (ix + 1) >> 1, cy0 = iy >> 1, cy1 = (iy + 1) >> 1;
+    V add;
+    const bool ox = ix & 1, oy = iy & 1;
+    if (!ox && !oy) {
+      add = ld1<LK>(e + cy0 * nc + cx0);
+    } else if (ox && !oy) {
+      add = V(0.5) * (ld1<LK>(e + cy0 * nc + cx0) + ld1<LK>(e + cy0 * nc + cx1));
+    } else if (!ox && oy) {
+      add = V(0.5) * (ld1<LK>(e + cy0 * nc + cx0) + ld1<LK>(e + cy1 * nc + cx0));
+    } else {
+      add = V(0.25) * (((ld1<LK>(e + cy0 * nc + cx0) + ld1<LK>(e + cy0 * nc + cx1)) +
+                        ld1<LK>(e + cy1 * nc + cx0)) + ld1<LK>(e + cy1 * nc + cx1));
+    }
+    v[j] = v[j] + add;
+  }
+  st4(x + i0, v);
+}
+
+// Exact coarsest-level solve x_c = A_c^-1 rhs_c (precomputed FP64 inverse of the interior block)
+// by one warp; result into buffer 0.  sol: m doubles of shared memory.
+template <class V, int LK>
+__device__ __forceinline__ void coarse_warp(const ProblemDev& P, int lane, double* sol) {
+  const LevelDev& d = P.lev[P.coarse];
+  const int n = d.n, ni = n - 2, m = P.m;
+  const V* rhs = static_cast<const V*>(d.rhs);
+  for (int u = lane; u < m; u += 32) {
+    const double* row = P.cinv + (long long)u * m;
+    double s = 0.0;
+    for (int v = 0; v < m; ++v) s = fma(row[v], double(ld1<LK>(rhs + (v / ni + 1) * n + (v % ni + 1))), s);
+    sol[u] = s;
+  }
+  __syncwarp();
+  V* x = static_cast<V*>(d.x[0]);
+  for (int q = lane; q < d.pitch; q += 32) {
+    const int iy = q / n, ix = q - iy * n;
+    V val = V(0);
+    if (q < n * n && ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1) val = V(sol[(iy - 1) * ni + (ix - 1)]);
+    x[q] = val;
+  }
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ per-level kernels
+// One warp-tile per loop trip over the work list.  level < 0: each problem's own finest level.
 template <class Pol, int MODE>
 __global__ void __launch_bounds__(256) k_band(EngineDev E, TileList tl, int level, int want,
                                               int in_sel) {
+  pdl_start();
   using A = typename Pol::A;
-  using V = typename Pol::V;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -202,86 +486,24 @@ __global__ void __launch_bounds__(256) k_band(EngineDev E, TileList tl, int leve
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
     const int p = it.x;
-    if (E.S[p].phase != want) continue;
+    const ProbState& st = E.S[p];
+    if (st.phase != want) continue;
     const ProblemDev& P = E.P[p];
     const int lv = level < 0 ? P.L : level;
-    const LevelDev& d = P.lev[lv];
-    const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
-    const long long shift = 1LL << lv;
-    const V* rhs = static_cast<const V*>(d.rhs);
-    const float* scale = Pol::prec == P16 ? d.scale : nullptr;
-
-    if constexpr (MODE == M_JACOBI_FIRST) {
-      const bool zg = (P.L > lv) || E.S[p].zero_top;
-      if (zg) {                                   // x = 0: x' = omega D^-1 rhs
-        V b[4], out[4];
-        ld4(rhs + i0, b);
-        if constexpr (Pol::prec == P64) {
-          double wd[4];
-          ld4(d.wdinv + i0, wd);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) out[j] = wd[j] * b[j];
-        } else {
-          A dgv[4];
-          if constexpr (Pol::prec == P16) diag_rowsum(d.band, scale, i0, dgv);
-          else load_band<Pol>(d.band[4], 1.0f, i0, dgv);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) out[j] = (omega / dgv[j]) * A(b[j]);
-        }
-        st4(static_cast<V*>(d.x[1]) + i0, out);
-        continue;
-      }
-    }
-    const V* xin = static_cast<const V*>(d.x[MODE == M_JACOBI_FIRST ? 0 : in_sel]);
-    A acc[4], dg[4];
-    V xc[4];
-    apply_op4<Pol>(d.band, scale, xin, i0, shift, lane, acc, xc, dg);
-    if constexpr (MODE == M_SPMV) {
-      V out[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) out[j] = V(acc[j]);
-      st4(static_cast<V*>(d.r) + i0, out);
-    } else {
-      V b[4];
-      ld4(rhs + i0, b);
-      if constexpr (MODE == M_DEFECT) {
-        V out[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) out[j] = V(A(b[j]) - acc[j]);
-        st4(static_cast<V*>(d.r) + i0, out);
-      } else if constexpr (MODE == M_CHECK) {
-        double s = 0.0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const double r = double(A(b[j]) - acc[j]);
-          s += r * r;
-        }
-        s = warp_sum(s);
-        if (lane == 0) E.partial[g] = s;
-      } else {                                    // Jacobi
-        V out[4];
-        if constexpr (Pol::prec == P64) {
-          double wd[4];
-          ld4(d.wdinv + i0, wd);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) out[j] = fma(wd[j], b[j] - acc[j], xc[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) out[j] = fma(omega / dg[j], A(b[j]) - acc[j], A(xc[j]));
-        }
-        const int out_sel = MODE == M_JACOBI_FIRST ? 1 : 1 - in_sel;
-        st4(static_cast<V*>(d.x[out_sel]) + i0, out);
-      }
-    }
+    const bool zg = (P.L > lv) || st.zero_top;
+    double* slot = nullptr;
+    if constexpr (MODE == M_CHECK) slot = E.partial + E.fine_off[p] + it.y;
+    if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST)
+      if (lv == P.L && !zg) slot = E.partial + E.fine_off[p] + it.y;
+    band_tile<Pol, MODE, LD_NC>(P.lev[lv], 1LL << lv, zg, (long long)it.y * kTile + lane * kLaneNodes,
+                                lane, in_sel, omega, slot);
   }
 }
 
-// Full-weighting restriction r_c = P^T r_f onto the coarse level (work list of the coarse level).
-// Coarse boundary and padding nodes are set to 0.  Summation order: fine rows 2J-1, 2J, 2J+1,
-// columns 2I-1, 2I, 2I+1, weights 1/4, 1/2, 1/4 x 1/4, 1/2, 1/4 (products by powers of two exact).
 template <class V>
 __global__ void __launch_bounds__(256) k_restrict(EngineDev E, TileList tl, int fine_level,
                                                   int want) {
+  pdl_start();
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -291,43 +513,15 @@ __global__ void __launch_bounds__(256) k_restrict(EngineDev E, TileList tl, int 
     const int p = it.x;
     const ProblemDev& P = E.P[p];
     if (P.L < fine_level || E.S[p].phase != want) continue;
-    const LevelDev& f = P.lev[fine_level];
-    const LevelDev& c = P.lev[fine_level - 1];
-    const long long nc = c.n, nf = f.n, Nc = nc * nc;
-    const V* r = static_cast<const V*>(f.r);
-    const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
-    V out[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const long long ci = i0 + j;
-      V v = V(0);
-      if (ci < Nc) {
-        const long long J = ci / nc, I = ci - J * nc;
-        if (I > 0 && J > 0 && I < nc - 1 && J < nc - 1) {
-          const long long fc = 2 * J * nf + 2 * I;
-          const V q = V(0.25), h = V(0.5);
-          v = q * __ldg(r + fc - nf - 1);
-          v = fma(h, __ldg(r + fc - nf), v);
-          v = fma(q, __ldg(r + fc - nf + 1), v);
-          v = fma(h, __ldg(r + fc - 1), v);
-          v = v + __ldg(r + fc);
-          v = fma(h, __ldg(r + fc + 1), v);
-          v = fma(q, __ldg(r + fc + nf - 1), v);
-          v = fma(h, __ldg(r + fc + nf), v);
-          v = fma(q, __ldg(r + fc + nf + 1), v);
-        }
-      }
-      out[j] = v;
-    }
-    st4(static_cast<V*>(c.rhs) + i0, out);
+    restrict_tile<V, LD_NC>(P.lev[fine_level], P.lev[fine_level - 1],
+                            (long long)it.y * kTile + lane * kLaneNodes);
   }
 }
 
-// x_f[x_sel] += P e_c (bilinear interpolation of the coarse iterate, buffer 0 of level-1);
-// boundary fine nodes are left unchanged.
 template <class V>
 __global__ void __launch_bounds__(256) k_prolong(EngineDev E, TileList tl, int level, int want,
                                                  int x_sel) {
+  pdl_start();
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -337,43 +531,14 @@ __global__ void __launch_bounds__(256) k_prolong(EngineDev E, TileList tl, int l
     const int p = it.x;
     if (E.S[p].phase != want) continue;
     const ProblemDev& P = E.P[p];
-    const LevelDev& f = P.lev[level];
-    const LevelDev& c = P.lev[level - 1];
-    const long long nf = f.n, nc = c.n, Nf = nf * nf;
-    const V* e = static_cast<const V*>(c.x[0]);
-    V* x = static_cast<V*>(f.x[x_sel]);
-    const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
-    V v[4];
-    ld4c(x + i0, v);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const long long fi = i0 + j;
-      if (fi >= Nf) continue;
-      const long long iy = fi / nf, ix = fi - iy * nf;
-      if (ix == 0 || iy == 0 || ix == nf - 1 || iy == nf - 1) continue;
-      const long long cx0 = ix >> 1, cx1 = (ix + 1) >> 1, cy0 = iy >> 1, cy1 = (iy + 1) >> 1;
-      V add;
-      const bool ox = ix & 1, oy = iy & 1;
-      if (!ox && !oy) {
-        add = __ldg(e + cy0 * nc + cx0);
-      } else if (ox && !oy) {
-        add = V(0.5) * (__ldg(e + cy0 * nc + cx0) + __ldg(e + cy0 * nc + cx1));
-      } else if (!ox && oy) {
-        add = V(0.5) * (__ldg(e + cy0 * nc + cx0) + __ldg(e + cy1 * nc + cx0));
-      } else {
-        add = V(0.25) * (((__ldg(e + cy0 * nc + cx0) + __ldg(e + cy0 * nc + cx1)) +
-                          __ldg(e + cy1 * nc + cx0)) + __ldg(e + cy1 * nc + cx1));
-      }
-      v[j] = v[j] + add;
-    }
-    st4(x + i0, v);
+    prolong_tile<V, LD_NC>(P.lev[level], P.lev[level - 1], x_sel,
+                           (long long)it.y * kTile + lane * kLaneNodes);
   }
 }
 
-// Exact coarsest-level solve x_c = A_c^-1 rhs_c with the precomputed FP64 inverse of the interior
-// block; one warp per problem (tile 0 of its coarsest level), result into buffer 0.
 template <class V>
 __global__ void __launch_bounds__(256) k_coarse(EngineDev E, TileList tl, int want) {
+  pdl_start();
   __shared__ double sol[8][kMaxCoarseM];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -384,32 +549,286 @@ __global__ void __launch_bounds__(256) k_coarse(EngineDev E, TileList tl, int wa
     if (it.y != 0) continue;
     const int p = it.x;
     if (E.S[p].phase != want) continue;
-    const ProblemDev& P = E.P[p];
-    const LevelDev& d = P.lev[P.coarse];
-    const int n = d.n, ni = n - 2, m = P.m;
-    const V* rhs = static_cast<const V*>(d.rhs);
-    for (int u = lane; u < m; u += 32) {
-      const double* row = P.cinv + (long long)u * m;
-      double s = 0.0;
-      for (int v = 0; v < m; ++v) s = fma(row[v], double(rhs[(v / ni + 1) * n + (v % ni + 1)]), s);
-      sol[wib][u] = s;
-    }
-    __syncwarp();
-    V* x = static_cast<V*>(d.x[0]);
-    for (int q = lane; q < d.pitch; q += 32) {
-      const int iy = q / n, ix = q - iy * n;
-      V val = V(0);
-      if (q < n * n && ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1)
-        val = V(sol[wib][(iy - 1) * ni + (ix - 1)]);
-      x[q] = val;
-    }
-    __syncwarp();
+    coarse_warp<V, LD_NC>(E.P[p], lane, sol[wib]);
   }
+}
+
+// ----------------------------------------------------------- fused coarse-level V cycle
+// One thread-block cluster per problem runs the part of the V cycle on levels coarse..min(T, L):
+// pre-smoothing, defect and restriction down to the coarsest level, the exact solve, then
+// prolongation and post-smoothing back up.
+//  * Levels above S run on the whole cluster over global memory: phases are separated by cluster
+//    barriers (release / acquire at cluster scope) and data produced inside the launch are read
+//    from L2 (LD_CG).
+//  * Levels coarse..S run inside block 0 alone, entirely in its shared memory (all bands and
+//    vectors of those levels, with zero halos), phases separated by block barriers; on the way in
+//    the restricted right-hand side of level S (and its iterate, if nonzero) is copied in, on
+//    the way out the iterate of level S is copied back.
+// The problem's level descriptors are copied to shared memory once.  The barrier sequence depends
+// only on the problem's levels and the engine parameters, so every block of a cluster passes the
+// same barriers.
+
+constexpr long long kCinvSmemMax = 32 * 1024;
+
+// 16-byte asynchronous global -> shared copy (cp.async, L2 only); completion by cp_async_wait()
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// shared-memory bytes of levels coarse..S for a precision (16-byte aligned pieces)
+__host__ __device__ inline long long smem_level_bytes(int l, int prec) {
+  const long long ve = ((1LL << l) + 1) * ((1LL << l) + 1);
+  const long long pitch = (ve + kTile - 1) / kTile * kTile;
+  const long long halo = (((1LL << l) + 1 + 8) + 31) / 32 * 32;
+  const long long e = pitch + 2 * halo;
+  const long long bs = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
+  const long long vs = prec == P64 ? 8 : 4;
+  auto al = [](long long b) { return (b + 15) / 16 * 16; };
+  return 9 * al(e * bs) + 4 * al(e * vs) + (prec == P64 ? al(e * 8) : 0);
+}
+
+// carve level l of the shared-memory hierarchy starting at *off; start the asynchronous copies of
+// its bands (and omega/D) and zero its vectors.  The caller waits for the copies (cp_async_wait)
+// and synchronizes the block before use.
+template <class Pol>
+__device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* base, long long* off,
+                                 int l) {
+  using V = typename Pol::V;
+  using B = typename Pol::B;
+  const long long halo = (((1LL << l) + 1 + 8) + 31) / 32 * 32;
+  const long long e = (long long)g.pitch + 2 * halo;    // a multiple of 32 elements
+  auto take = [&](long long bytes) { unsigned char* r = base + *off; *off += (bytes + 15) / 16 * 16; return r; };
+  // every thread computes the same carve-up; thread 0 publishes the pointers
+  LevelDev t = g;
+  for (int k = 0; k < 9; ++k) {
+    B* dst = reinterpret_cast<B*>(take(e * sizeof(B)));
+    const B* src = static_cast<const B*>(g.band[k]) - halo;
+    const int chunks = (int)(e * sizeof(B) / 16);
+    for (int q = threadIdx.x; q < chunks; q += blockDim.x)
+      cp_async16(reinterpret_cast<uint4*>(dst) + q, reinterpret_cast<const uint4*>(src) + q);
+    t.band[k] = dst + halo;
+  }
+  if constexpr (Pol::prec == P64) {
+    double* dst = reinterpret_cast<double*>(take(e * 8));
+    const double* src = g.wdinv - halo;
+    for (int q = threadIdx.x; q < (int)(e / 2); q += blockDim.x)
+      cp_async16(reinterpret_cast<double2*>(dst) + q, reinterpret_cast<const double2*>(src) + q);
+    t.wdinv = dst + halo;
+  }
+  V* vec[4];
+  for (int v = 0; v < 4; ++v) {
+    vec[v] = reinterpret_cast<V*>(take(e * sizeof(V)));
+    for (int q = threadIdx.x; q < (int)(e * sizeof(V) / 16); q += blockDim.x)
+      reinterpret_cast<uint4*>(vec[v])[q] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  t.x[0] = vec[0] + halo; t.x[1] = vec[1] + halo; t.rhs = vec[2] + halo; t.r = vec[3] + halo;
+  if (threadIdx.x == 0) s = t;
+}
+
+// Pre-smoothing, defect and restriction of level l.  check_part (top level with a nonzero
+// iterate): the first smoothing step also writes the residual partials, block 0 reduces them and
+// takes the lagged convergence decision; returns false if the problem leaves the cycle.
+template <class Pol, int LK>
+__device__ __forceinline__ bool vcycle_down_level(const LevelDev& d, const LevelDev& dc, int l,
+                                                  bool zg, int pre, typename Pol::A omega, int w0,
+                                                  int nw, int lane, bool cluster_sync,
+                                                  double* check_part, ProbState* st,
+                                                  const Params& prm, int want, int rank,
+                                                  double* sh) {
+  const long long shift = 1LL << l;
+  const int tiles = d.pitch / kTile;
+  auto sync = [&] { if (cluster_sync) cg::this_cluster().sync(); else __syncthreads(); };
+  if (pre >= 2) {
+    for (int t = w0; t < tiles; t += nw)
+      band_tile<Pol, M_PRE12, LK>(d, shift, zg, (long long)t * kTile + lane * kLaneNodes, lane, 0, omega,
+                                  check_part ? check_part + t : nullptr);
+  } else {
+    for (int t = w0; t < tiles; t += nw)
+      band_tile<Pol, M_JACOBI_FIRST, LK>(d, shift, zg, (long long)t * kTile + lane * kLaneNodes, lane, 0, omega,
+                                         check_part ? check_part + t : nullptr);
+  }
+  sync();
+  if (check_part) {
+    if (rank == 0) {
+      const double sum = problem_partial_sum(check_part, fine_tiles(l), sh);
+      if (threadIdx.x == 0) pre_check(*st, prm, sqrt(sum));
+    }
+    sync();
+    if (__ldcg(&st->phase) != want) return false;
+  }
+  if (pre >= 2) {
+    if (!(zg && fuses_pre<Pol>())) {
+      for (int t = w0; t < tiles; t += nw)
+        band_tile<Pol, M_PRE2B, LK>(d, shift, zg, (long long)t * kTile + lane * kLaneNodes, lane, 0, omega, nullptr);
+      sync();
+    }
+    for (int s = 3; s <= pre; ++s) {
+      for (int t = w0; t < tiles; t += nw)
+        band_tile<Pol, M_JACOBI, LK>(d, shift, zg, (long long)t * kTile + lane * kLaneNodes, lane, (s - 1) & 1, omega, nullptr);
+      sync();
+    }
+  }
+  for (int t = w0; t < tiles; t += nw)
+    band_tile<Pol, M_DEFECT, LK>(d, shift, zg, (long long)t * kTile + lane * kLaneNodes, lane, pre & 1, omega, nullptr);
+  sync();
+  const int ctiles = dc.pitch / kTile;
+  for (int t = w0; t < ctiles; t += nw)
+    restrict_tile<typename Pol::V, LK>(d, dc, (long long)t * kTile + lane * kLaneNodes);
+  sync();
+  return true;
+}
+
+template <class Pol, int LK>
+__device__ __forceinline__ void vcycle_up_level(const LevelDev& d, const LevelDev& dc, int l, int pre,
+                                                int post, typename Pol::A omega, int w0, int nw,
+                                                int lane, bool cluster_sync) {
+  const long long shift = 1LL << l;
+  const int tiles = d.pitch / kTile;
+  auto sync = [&] { if (cluster_sync) cg::this_cluster().sync(); else __syncthreads(); };
+  for (int t = w0; t < tiles; t += nw)
+    prolong_tile<typename Pol::V, LK>(d, dc, pre & 1, (long long)t * kTile + lane * kLaneNodes);
+  sync();
+  for (int s = 1; s <= post; ++s) {
+    for (int t = w0; t < tiles; t += nw)
+      band_tile<Pol, M_JACOBI, LK>(d, shift, false, (long long)t * kTile + lane * kLaneNodes, lane, (pre + s - 1) & 1, omega, nullptr);
+    sync();
+  }
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256) k_tail(EngineDev E, int T, int S, int want) {
+  pdl_start();
+  using A = typename Pol::A;
+  using V = typename Pol::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ LevelDev gd[kMaxLevel + 1];       // global-memory descriptors of this problem
+  __shared__ LevelDev sd[kMaxLevel + 1];       // shared-memory copies of levels coarse..S
+  __shared__ double sol[kMaxCoarseM];
+  __shared__ double sh[32];
+  cg::cluster_group cl = cg::this_cluster();
+  const int csize = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int p = blockIdx.x / csize;
+  if (p >= E.nprob) return;
+  const ProbState& st = E.S[p];
+  if (st.phase != want) return;
+  const ProblemDev& P = E.P[p];
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int top = P.L < T ? P.L : T, c = P.coarse;
+  const int Ss = S < top ? S : top;
+  const int pre = E.prm.pre, post = E.prm.post;
+  const A omega = A(E.prm.omega);
+  const bool zero_top = st.zero_top;
+  ProbState* stw = E.S + p;
+  double* check_part = E.partial + E.fine_off[p];   // used on the problem's own finest level
+  {   // descriptors of levels coarse..top into shared memory
+    const int words = (int)(sizeof(LevelDev) / 4) * (top - c + 1);
+    const unsigned* src = reinterpret_cast<const unsigned*>(&P.lev[c]);
+    unsigned* dst = reinterpret_cast<unsigned*>(&gd[c]);
+    for (int q = threadIdx.x; q < words; q += blockDim.x) dst[q] = src[q];
+    __syncthreads();
+  }
+  // cluster part, down
+  const int w0 = rank * wpb + (threadIdx.x >> 5), nw = csize * wpb;
+  for (int l = top; l > Ss; --l) {
+    const bool chk = (l == P.L) && !zero_top;
+    if (!vcycle_down_level<Pol, LD_CG>(gd[l], gd[l - 1], l, (P.L > l) || zero_top, pre, omega, w0, nw,
+                                       lane, true, chk ? check_part : nullptr, stw, E.prm, want, rank, sh))
+      return;                                   // converged at the lagged check: cluster-uniform
+  }
+  // block 0: levels coarse..Ss in shared memory
+  if (rank == 0) {
+    long long off = 0;
+    for (int l = c; l <= Ss; ++l) smem_level_setup<Pol>(gd[l], sd[l], smem, &off, l);
+    const int m = P.m;
+    // the coarse inverse (m*m doubles) is staged in shared memory when it is small
+    const bool cinv_smem = (long long)m * m * 8 <= kCinvSmemMax;
+    const double* cinv = P.cinv;
+    if (cinv_smem) {
+      double* dst = reinterpret_cast<double*>(smem + off);
+      for (int q = threadIdx.x; q < m * m; q += blockDim.x) dst[q] = __ldg(P.cinv + q);
+      cinv = dst;
+    }
+    __syncthreads();                                          // descriptors published
+    {   // inputs of level Ss: restricted rhs (or the top rhs), and the iterate if it is nonzero
+      const LevelDev& g = gd[Ss];
+      const LevelDev& s = sd[Ss];
+      const bool nonzero = (Ss == P.L) && !zero_top;
+      const int chunks = (int)(g.pitch * sizeof(V) / 16);
+      for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
+        cp_async16(static_cast<uint4*>(s.rhs) + q, static_cast<const uint4*>(g.rhs) + q);
+        if (nonzero) cp_async16(static_cast<uint4*>(s.x[0]) + q, static_cast<const uint4*>(g.x[0]) + q);
+      }
+      cp_async_wait();
+      __syncthreads();
+    }
+    const int sw0 = threadIdx.x >> 5;
+    bool go = true;
+    for (int l = Ss; l > c && go; --l) {
+      const bool chk = (l == P.L) && !zero_top;
+      go = vcycle_down_level<Pol, LD_GEN>(sd[l], sd[l - 1], l, (P.L > l) || zero_top, pre, omega, sw0, wpb,
+                                          lane, false, chk ? check_part : nullptr, stw, E.prm, want, 0, sh);
+    }
+    if (go && c == P.L && !zero_top) {
+      // the problem is the coarsest level alone: its residual check before the exact solve
+      const LevelDev& d = sd[c];
+      for (int t = sw0; t < d.pitch / kTile; t += wpb)
+        band_tile<Pol, M_CHECK, LD_GEN>(d, 1LL << c, false, (long long)t * kTile + lane * kLaneNodes, lane, 0,
+                                        omega, check_part + t);
+      __syncthreads();
+      const double sum = problem_partial_sum(check_part, fine_tiles(c), sh);
+      if (threadIdx.x == 0) pre_check(*stw, E.prm, sqrt(sum));
+      __syncthreads();
+      go = __ldcg(&stw->phase) == want;
+    }
+  if (go) {
+    if (threadIdx.x < 32) {
+      // the coarsest level: the exact solve with the FP64 inverse, all in shared memory
+      const LevelDev& d = sd[c];
+      const int n = d.n, ni = n - 2;
+      const V* rhs = static_cast<const V*>(d.rhs);
+      for (int u = lane; u < m; u += 32) {
+        const double* row = cinv + u * m;
+        double sacc = 0.0;
+        for (int v = 0; v < m; ++v) sacc = fma(row[v], double(rhs[(v / ni + 1) * n + (v % ni + 1)]), sacc);
+        sol[u] = sacc;
+      }
+      __syncwarp();
+      V* x = static_cast<V*>(d.x[0]);
+      for (int q = lane; q < d.pitch; q += 32) {
+        const int iy = q / n, ix = q - iy * n;
+        V val = V(0);
+        if (q < n * n && ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1) val = V(sol[(iy - 1) * ni + (ix - 1)]);
+        x[q] = val;
+      }
+    }
+    __syncthreads();
+    for (int l = c + 1; l <= Ss; ++l)
+      vcycle_up_level<Pol, LD_GEN>(sd[l], sd[l - 1], l, pre, post, omega, sw0, wpb, lane, false);
+    {   // the iterate of level Ss back to global memory
+      const LevelDev& g = gd[Ss];
+      const LevelDev& s = sd[Ss];
+      const int chunks = (int)(g.pitch * sizeof(V) / 16);
+      for (int q = threadIdx.x; q < chunks; q += blockDim.x)
+        static_cast<uint4*>(g.x[0])[q] = static_cast<const uint4*>(s.x[0])[q];
+    }
+  }
+  }
+  cl.sync();
+  // cluster part, up
+  for (int l = Ss + 1; l <= top; ++l)
+    vcycle_up_level<Pol, LD_CG>(gd[l], gd[l - 1], l, pre, post, omega, w0, nw, lane, true);
 }
 
 // FP64 outer defect of the defect correction: d = b - A x (FP64 bands, FP64 x), written to the
 // inner top-level right-hand side as float(d * s); partial[g] = sum d^2.  x = 0 gives d = b.
 __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) {
+  pdl_start();
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -423,14 +842,15 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
     const LevelDev& top = P.lev[P.L];
     const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
     double b[4], r[4];
-    ld4(P.b64 + i0, b);
+    ld4<LD_NC>(P.b64 + i0, b);
     if (st.x_zero) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) r[j] = b[j];
     } else {
-      double acc[4], xc[4], dg[4];
-      stencil4<F64>(reinterpret_cast<const void* const*>(P.band64), nullptr, P.x64, i0,
-                    1LL << P.L, lane, acc, xc, dg);
+      double w[3][8], acc[4], dg[4];
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) load_row<double, LD_NC>(P.x64, i0 + dy * (1LL << P.L), lane, w[dy + 1]);
+      stencil_windows<F64, LD_NC>(reinterpret_cast<const void* const*>(P.band64), nullptr, w, i0, acc, dg);
 #pragma unroll
       for (int j = 0; j < 4; ++j) r[j] = b[j] - acc[j];
     }
@@ -450,6 +870,7 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
 
 // x64 += c / s (c = inner top-level iterate, buffer 0), for problems in PH_UPDATE
 __global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl) {
+  pdl_start();
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -462,7 +883,7 @@ __global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl) {
     const ProblemDev& P = E.P[p];
     const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
     float c[4];
-    ld4(static_cast<const float*>(P.lev[P.L].x[0]) + i0, c);
+    ld4<LD_NC>(static_cast<const float*>(P.lev[P.L].x[0]) + i0, c);
     double x[4];
     ld4c(P.x64 + i0, x);
     const double inv_s = 1.0 / st.s;
@@ -474,6 +895,7 @@ __global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl) {
 
 // ||b||^2 partials for problems starting a solve
 __global__ void __launch_bounds__(256) k_norm_b(EngineDev E, TileList tl) {
+  pdl_start();
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -484,7 +906,7 @@ __global__ void __launch_bounds__(256) k_norm_b(EngineDev E, TileList tl) {
     if (E.S[p].phase != PH_INIT) continue;
     const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
     double b[4];
-    ld4(E.P[p].b64 + i0, b);
+    ld4<LD_NC>(E.P[p].b64 + i0, b);
     double q = b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
     q = warp_sum(q);
     if (lane == 0) E.partial2[g] = q;
@@ -493,6 +915,7 @@ __global__ void __launch_bounds__(256) k_norm_b(EngineDev E, TileList tl) {
 
 // Reject right-hand sides with non-zero boundary entries (one block per problem).
 __global__ void __launch_bounds__(256) k_boundary_check(EngineDev E) {
+  pdl_start();
   const int p = blockIdx.x;
   if (p >= E.nprob) return;
   ProbState& st = E.S[p];
@@ -515,12 +938,19 @@ __global__ void __launch_bounds__(256) k_boundary_check(EngineDev E) {
 
 // Per-problem control of the solver state machine: reduce the problem's norm partials in a fixed
 // order (bit-reproducible, independent of the batch), then update its state.
-__global__ void __launch_bounds__(256) k_control(EngineDev E, int kind) {
+__global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int level) {
+  pdl_start();
   __shared__ double sh[32];
   const int p = blockIdx.x;
   if (p >= E.nprob) return;
   ProbState& st = E.S[p];
   const int ph = st.phase;
+  if (kind == CTRL_PRE) {
+    if (!((ph == PH_INNER || ph == PH_CYCLE) && E.P[p].L == level && !st.zero_top)) return;
+    const double sum = problem_partial_sum(E.partial + E.fine_off[p], fine_tiles(level), sh);
+    if (threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
+    return;
+  }
   const bool mine = (kind == CTRL_INIT && ph == PH_INIT) ||
                     (kind == CTRL_CHECK0 && ph == PH_CHECK) ||
                     (kind == CTRL_CHECK && ph == PH_CYCLE) ||
@@ -549,8 +979,14 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind) {
       st.bnorm = nrm;
       st.s = 1.0 / nrm;
       st.relres = 1.0;
-      if (prm.prec == P64) st.phase = st.x_zero ? PH_CYCLE : PH_CHECK;
-      else st.phase = PH_OUTER;
+      if (prm.prec == P64) {
+        // a zero initial guess starts its first cycle unchecked (relres 1); a given guess is
+        // checked by the first smoothing step of its first cycle
+        st.phase = PH_CYCLE;
+        st.cycles = st.x_zero ? 1 : 0;
+      } else {
+        st.phase = PH_OUTER;
+      }
       break;
     case CTRL_CHECK0:
     case CTRL_CHECK:
@@ -570,7 +1006,9 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind) {
       else if (st.outer_iters >= prm.max_outer || st.inner_cycles >= prm.max_cycles) {
         st.status = HN_ERR_NOT_CONVERGED; st.phase = PH_DONE;
       } else {
-        st.phase = PH_INNER; st.inner_k = 0; st.zero_top = 1; st.inner_ref = st.s * nrm;
+        // the first inner cycle starts from zero: it runs unchecked and is counted here
+        st.phase = PH_INNER; st.zero_top = 1; st.inner_ref = st.s * nrm;
+        st.inner_k = 1; st.inner_cycles += 1; st.cycles += 1;
       }
       break;
     case CTRL_INNER:
@@ -599,7 +1037,8 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind) {
 // graph's while-condition.  Past the iteration limit every running problem is stopped as not
 // converged, so a device-side loop always ends.
 __global__ void __launch_bounds__(256) k_summary(EngineDev E, cudaGraphConditionalHandle h,
-                                                 int use_handle) {
+                                                 int use_handle, int end_of_iteration) {
+  pdl_start();
   __shared__ double sh[32];
   __shared__ unsigned over;
   if (threadIdx.x == 0) {
@@ -611,6 +1050,8 @@ __global__ void __launch_bounds__(256) k_summary(EngineDev E, cudaGraphCondition
   for (int p = threadIdx.x; p < E.nprob; p += blockDim.x) {
     ProbState& st = E.S[p];
     if (st.phase != PH_DONE && over) { st.status = HN_ERR_NOT_CONVERGED; st.phase = PH_DONE; }
+    // after an iteration the finest-level iterate of a running cycle is no longer zero
+    if (end_of_iteration && (st.phase == PH_INNER || st.phase == PH_CYCLE)) st.zero_top = 0;
     c += st.phase != PH_DONE ? 1.0 : 0.0;
   }
   c = block_sum256(c, sh);
@@ -623,17 +1064,47 @@ __global__ void __launch_bounds__(256) k_summary(EngineDev E, cudaGraphCondition
 
 inline int grid_or_one(int g) { return g < 1 ? 1 : g; }
 
+// launch with optional programmatic dependent launch and thread-block clusters
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t s, bool pdl,
+                     int cluster, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid_or_one(grid), 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (cluster > 0) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = (unsigned)cluster;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <class Pol>
 cudaError_t launch_band_t(int mode, const EngineDev& E, TileList tl, int level, int want,
                           int in_sel, int grid, cudaStream_t s) {
   grid = grid_or_one(grid);
   switch (mode) {
-    case M_SPMV: k_band<Pol, M_SPMV><<<grid, 256, 0, s>>>(E, tl, level, want, in_sel); break;
-    case M_DEFECT: k_band<Pol, M_DEFECT><<<grid, 256, 0, s>>>(E, tl, level, want, in_sel); break;
-    case M_JACOBI: k_band<Pol, M_JACOBI><<<grid, 256, 0, s>>>(E, tl, level, want, in_sel); break;
+    case M_SPMV: return launch_k(k_band<Pol, M_SPMV>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
+    case M_DEFECT: return launch_k(k_band<Pol, M_DEFECT>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
+    case M_JACOBI: return launch_k(k_band<Pol, M_JACOBI>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
     case M_JACOBI_FIRST:
-      k_band<Pol, M_JACOBI_FIRST><<<grid, 256, 0, s>>>(E, tl, level, want, in_sel); break;
-    case M_CHECK: k_band<Pol, M_CHECK><<<grid, 256, 0, s>>>(E, tl, level, want, in_sel); break;
+      return launch_k(k_band<Pol, M_JACOBI_FIRST>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
+    case M_CHECK: return launch_k(k_band<Pol, M_CHECK>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
+    case M_PRE12: return launch_k(k_band<Pol, M_PRE12>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
+    case M_PRE2B: return launch_k(k_band<Pol, M_PRE2B>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -655,6 +1126,68 @@ cudaError_t launch_jacobi(const EngineDev& E, TileList tl, int level, int want, 
                           int first, int grid, cudaStream_t s) {
   return launch_band(first ? M_JACOBI_FIRST : M_JACOBI, E, tl, level, want, in_sel, grid, s);
 }
+cudaError_t launch_pre12(const EngineDev& E, TileList tl, int level, int want, int grid,
+                         cudaStream_t s) {
+  return launch_band(M_PRE12, E, tl, level, want, 0, grid, s);
+}
+cudaError_t launch_pre2b(const EngineDev& E, TileList tl, int level, int want, int grid,
+                         cudaStream_t s) {
+  return launch_band(M_PRE2B, E, tl, level, want, 0, grid, s);
+}
+bool pre_fuses(int prec) { return prec != P16; }
+
+// shared memory the fused coarse-level kernel may use for levels coarse..S
+constexpr long long kTailSmemBudget = 160 * 1024;
+
+int tail_smem_level(int prec, int coarse, int T) {
+  const long long ni = (1LL << coarse) - 1;
+  long long bytes = ni * ni * ni * ni * 8 <= kCinvSmemMax ? ni * ni * ni * ni * 8 : 0;
+  int S = coarse;
+  for (int l = coarse; l <= T; ++l) {
+    bytes += smem_level_bytes(l, prec);
+    if (bytes > kTailSmemBudget) break;
+    S = l;
+  }
+  return S;
+}
+
+long long tail_smem_bytes(int prec, int coarse, int S) {
+  long long bytes = 0;
+  for (int l = coarse; l <= S; ++l) bytes += smem_level_bytes(l, prec);
+  const long long ni = (1LL << coarse) - 1;
+  const long long cinv = ni * ni * ni * ni * 8;
+  return bytes + (cinv <= kCinvSmemMax ? cinv : 0);     // the coarse inverse, when staged
+}
+
+// clusters of up to 16 blocks need the non-portable opt-in, the shared-memory levels a larger
+// dynamic shared-memory size; set once, outside any stream capture
+cudaError_t prepare_kernels() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBudget);
+  };
+  set(reinterpret_cast<const void*>(k_tail<F64>));
+  set(reinterpret_cast<const void*>(k_tail<F32>));
+  set(reinterpret_cast<const void*>(k_tail<F16>));
+  return e;
+}
+
+template <class Pol>
+cudaError_t launch_tail_t(const EngineDev& E, int T, int want, int cluster, cudaStream_t s) {
+  const int S = tail_smem_level(Pol::prec, E.prm.coarse, T);
+  const size_t smem = (size_t)tail_smem_bytes(Pol::prec, E.prm.coarse, S);
+  return launch_k(k_tail<Pol>, E.nprob * cluster, smem, s, E.pdl, cluster, E, T, S, want);
+}
+
+cudaError_t launch_tail(const EngineDev& E, int T, int want, int cluster, cudaStream_t s) {
+  switch (E.prm.prec) {
+    case P64: return launch_tail_t<F64>(E, T, want, cluster, s);
+    case P32: return launch_tail_t<F32>(E, T, want, cluster, s);
+    case P16: return launch_tail_t<F16>(E, T, want, cluster, s);
+  }
+  return cudaErrorInvalidValue;
+}
 cudaError_t launch_defect(const EngineDev& E, TileList tl, int level, int want, int in_sel,
                           int grid, cudaStream_t s) {
   return launch_band(M_DEFECT, E, tl, level, want, in_sel, grid, s);
@@ -667,55 +1200,46 @@ cudaError_t launch_spmv(const EngineDev& E, TileList tl, int level, int want, in
 cudaError_t launch_restrict(const EngineDev& E, TileList tl_coarse, int fine_level, int want,
                             int grid, cudaStream_t s) {
   grid = grid_or_one(grid);
-  if (E.prm.prec == P64) k_restrict<double><<<grid, 256, 0, s>>>(E, tl_coarse, fine_level, want);
-  else k_restrict<float><<<grid, 256, 0, s>>>(E, tl_coarse, fine_level, want);
-  return cudaGetLastError();
+  if (E.prm.prec == P64) return launch_k(k_restrict<double>, grid, 0, s, E.pdl, 0, E, tl_coarse, fine_level, want);
+  return launch_k(k_restrict<float>, grid, 0, s, E.pdl, 0, E, tl_coarse, fine_level, want);
 }
 
 cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want, int x_sel,
                            int grid, cudaStream_t s) {
   grid = grid_or_one(grid);
-  if (E.prm.prec == P64) k_prolong<double><<<grid, 256, 0, s>>>(E, tl, level, want, x_sel);
-  else k_prolong<float><<<grid, 256, 0, s>>>(E, tl, level, want, x_sel);
-  return cudaGetLastError();
+  if (E.prm.prec == P64) return launch_k(k_prolong<double>, grid, 0, s, E.pdl, 0, E, tl, level, want, x_sel);
+  return launch_k(k_prolong<float>, grid, 0, s, E.pdl, 0, E, tl, level, want, x_sel);
 }
 
 cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, cudaStream_t s) {
   grid = grid_or_one(grid);
-  if (E.prm.prec == P64) k_coarse<double><<<grid, 256, 0, s>>>(E, tl, want);
-  else k_coarse<float><<<grid, 256, 0, s>>>(E, tl, want);
-  return cudaGetLastError();
+  if (E.prm.prec == P64) return launch_k(k_coarse<double>, grid, 0, s, E.pdl, 0, E, tl, want);
+  return launch_k(k_coarse<float>, grid, 0, s, E.pdl, 0, E, tl, want);
 }
 
 cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  k_outer_defect<<<grid_or_one(grid), 256, 0, s>>>(E, fine);
-  return cudaGetLastError();
+  return launch_k(k_outer_defect, grid, 0, s, E.pdl, 0, E, fine);
 }
 
 cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  k_update<<<grid_or_one(grid), 256, 0, s>>>(E, fine);
-  return cudaGetLastError();
+  return launch_k(k_update, grid, 0, s, E.pdl, 0, E, fine);
 }
 
 cudaError_t launch_norm_b(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  k_norm_b<<<grid_or_one(grid), 256, 0, s>>>(E, fine);
-  return cudaGetLastError();
+  return launch_k(k_norm_b, grid, 0, s, E.pdl, 0, E, fine);
 }
 
-cudaError_t launch_control(const EngineDev& E, int kind, cudaStream_t s) {
-  k_control<<<grid_or_one(E.nprob), 256, 0, s>>>(E, kind);
-  return cudaGetLastError();
+cudaError_t launch_control(const EngineDev& E, int kind, cudaStream_t s, int level) {
+  return launch_k(k_control, E.nprob, 0, s, E.pdl, 0, E, kind, level);
 }
 
 cudaError_t launch_summary(const EngineDev& E, cudaGraphConditionalHandle h, int use_handle,
-                           cudaStream_t s) {
-  k_summary<<<1, 256, 0, s>>>(E, h, use_handle);
-  return cudaGetLastError();
+                           int end_of_iteration, cudaStream_t s) {
+  return launch_k(k_summary, 1, 0, s, E.pdl, 0, E, h, use_handle, end_of_iteration);
 }
 
 cudaError_t launch_boundary_check(const EngineDev& E, cudaStream_t s) {
-  k_boundary_check<<<grid_or_one(E.nprob), 256, 0, s>>>(E);
-  return cudaGetLastError();
+  return launch_k(k_boundary_check, E.nprob, 0, s, false, 0, E);
 }
 
 // the fine-level defect norm of the V-cycle's own precision (convergence check)

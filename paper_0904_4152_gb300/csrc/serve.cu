@@ -175,6 +175,7 @@ void hn_server::run() {
           break;
         }
         engine->set_iter_limit(UINT_MAX - 1);
+        engine->set_top_mask_all();
         engine_lmax = Lcap;
         members_dirty = true;
         // every admitted request (re)starts on the new engine

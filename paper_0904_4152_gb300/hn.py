@@ -31,7 +31,7 @@ EXPORTS = [
     "hn_mg_destroy", "hn_mg_apply", "hn_mg_get_inner_bands", "hn_server_create", "hn_mg_submit",
     "hn_mg_poll", "hn_server_query", "hn_server_destroy", "hn_last_error", "hn_version",
     "hn_mg_set_profiling", "hn_mg_kernel_times", "hn_mg_last_launches",
-    "hn_band_defect_norm_static",
+    "hn_band_defect_norm_static", "hn_mg_set_tuning", "hn_mg_get_tuning", "hn_mg_autotune",
 ]
 
 
@@ -63,6 +63,10 @@ class ServerInfo(ctypes.Structure):
                 ("active", ctypes.c_longlong), ("queued", ctypes.c_longlong),
                 ("iterations", ctypes.c_longlong), ("bytes_in_use", ctypes.c_size_t),
                 ("budget", ctypes.c_size_t)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tail_level", ctypes.c_int), ("cluster", ctypes.c_int), ("pdl", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -115,6 +119,9 @@ def lib():
         L.hn_mg_set_profiling.argtypes = [vp, ip]
         L.hn_mg_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime), ip]
         L.hn_band_defect_norm_static.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.hn_mg_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        L.hn_mg_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        L.hn_mg_autotune.argtypes = [vp, vp, ip, ctypes.POINTER(Tuning), dp, ip]
         L.hn_mg_last_launches.argtypes = [vp]
         L.hn_mg_last_launches.restype = ctypes.c_longlong
         _lib = L
@@ -310,6 +317,32 @@ def hn_mg_kernel_times(mg, max_entries=256):
     return [dict(name=buf[i].name.decode(), level=buf[i].level, launches=buf[i].launches,
                  total_ms=buf[i].total_ms, bytes_per_launch=buf[i].bytes_per_launch)
             for i in range(n)]
+
+
+def hn_mg_set_tuning(mg, tail_level, cluster, pdl=1):
+    _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl))))
+
+
+def hn_mg_get_tuning(mg):
+    t = Tuning()
+    _check(lib().hn_mg_get_tuning(mg, ctypes.byref(t)))
+    return t.tail_level, t.cluster, t.pdl
+
+
+def hn_mg_autotune(mg, b, reps=3, coarse_L=2):
+    """Time every launch shape on this hierarchy, keep the fastest; returns (best, {shape: ms})."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    cap = 5 * 16
+    times = np.full(cap, np.nan)
+    best = Tuning()
+    _check(lib().hn_mg_autotune(mg, _host_ptr(b, np.float64), reps, ctypes.byref(best),
+                                times.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cap))
+    clusters = (1, 2, 4, 8, 16)
+    table = {}
+    for i, v in enumerate(times):
+        if not np.isnan(v):
+            table[(coarse_L + i // 5, clusters[i % 5])] = float(v)
+    return (best.tail_level, best.cluster), table
 
 
 def hn_mg_last_launches(mg):

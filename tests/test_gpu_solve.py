@@ -233,9 +233,45 @@ def test_profiling_times_kernels_without_changing_results(hn):
         x1, _, _ = hn.hn_mg_solve(mg, L, b)
         times = hn.hn_mg_kernel_times(mg)
         names = {t["name"] for t in times}
-        assert {"jacobi", "defect", "restrict", "prolong", "coarse", "outer_defect"} <= names
+        assert {"jacobi", "defect", "restrict", "prolong", "tail", "outer_defect"} <= names
         assert all(t["total_ms"] > 0 for t in times)
         np.testing.assert_array_equal(x0, x1)
         hn.hn_mg_set_profiling(mg, False)
     finally:
         hn.hn_mg_destroy(mg)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_launch_shapes_do_not_change_results(hn, prec):
+    # the tail level, cluster size and programmatic dependent launch only change where work runs
+    L = 8
+    coef, b = I.batch_problem(3, L)
+    A = hn.hn_band_create(L, coef)
+    mg = hn.hn_mg_setup(A, prec=prec)
+    hn.hn_band_destroy(A)
+    try:
+        ref, st0, _ = hn.hn_mg_solve(mg, L, b)
+        for shape in [(2, 1, 0), (4, 2, 0), (5, 16, 1), (7, 8, 0), (8, 16, 1)]:
+            hn.hn_mg_set_tuning(mg, *shape)
+            assert hn.hn_mg_get_tuning(mg) == shape
+            x, st, _ = hn.hn_mg_solve(mg, L, b)
+            np.testing.assert_array_equal(x, ref)
+            assert st["cycles"] == st0["cycles"]
+        best, table = hn.hn_mg_autotune(mg, b, reps=1)
+        assert best in table and len(table) == 5 * 7
+        x, _, _ = hn.hn_mg_solve(mg, L, b)
+        np.testing.assert_array_equal(x, ref)
+    finally:
+        hn.hn_mg_destroy(mg)
+
+
+@pytest.mark.parametrize("coarse_L", [3, 4])
+def test_other_coarse_levels_lockstep(hn, coarse_L):
+    L = 7
+    coef = I.lognormal_coef(L, 17)
+    b = I.rhs_uniform(L, 18)
+    x, st, status = solve(hn, L, b, coef, coarse_L=coarse_L, tol=0.0, max_cycles=3)
+    xr, _ = O.mg_solve(L, b, coef=coef, coarse_L=coarse_L, tol=0.0, max_cycles=3)
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-9
+    x, st, status = solve(hn, L, b, coef, coarse_L=coarse_L, prec=1)
+    assert status == hn.HN_OK and oracle_relres(L, coef, b, x) <= RELRES
