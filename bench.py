@@ -43,6 +43,16 @@ def parse():
                     help="refinement level (default 10, the benchmark workload; others for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="timed solves only (no e2e, profiled pass or CPU baseline): for ncu captures")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run solves as one graph launch per iteration (ncu cannot profile kernels "
+                         "inside the device-side loop)")
+    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve"],
+                    help="solve: the L=10 benchmark (default); batch: 256 uneven problems in one "
+                         "batched solve; serve: Poisson-arrival requests through the solve server")
+    ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
+    ap.add_argument("--load", type=float, default=0.7, help="serve: offered load / capacity")
+    ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: device memory budget")
+    ap.add_argument("--slots", type=int, default=64, help="serve: concurrently active requests")
     return ap.parse_args()
 
 
@@ -205,6 +215,8 @@ def run_ours(args, rank, world, local, pg):
     mgs = {}
     for name, prec in (("mixed", hn.HN_PREC_FP32_DC), ("fp64", hn.HN_PREC_FP64)):
         mgs[name] = hn.hn_mg_setup(A, prec=prec, stream=stream.cuda_stream)
+        if args.host_loop:
+            hn.hn_mg_set_profiling(mgs[name], True)
     hn.hn_band_destroy(A)
 
     def timed(mg, steps, warmup):
@@ -324,11 +336,198 @@ def run_ours(args, rank, world, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world, local, pg):
+    """256 independent problems, L_j ~ U{5..9}, lognormal coefficients, U[-1,1] right-hand sides,
+    FP32-inner defect correction: one batched solve (persistent work-list kernels, one CUDA graph
+    with a device-side loop) against solving the same problems one after the other."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    from paper_0904_4152_gb300 import hn, inputs as I
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        g.build()
+    barrier(pg, dev)
+    count = 256
+    levels = [int(v) for v in I.batch_levels(count, seed=rank)]
+    mgs, bs, xs, coefs, bh = [], [], [], [], []
+    for j, L in enumerate(levels):
+        coef, b = I.batch_problem(j + rank * count, L)
+        A = hn.hn_band_create(L, coef)
+        mgs.append(hn.hn_mg_setup(A, prec=hn.HN_PREC_FP32_DC))
+        hn.hn_band_destroy(A)
+        coefs.append(coef)
+        bh.append(b)
+        bs.append(torch.from_numpy(b).to(dev))
+        xs.append(torch.zeros_like(bs[-1]))
+    dofs = sum(((1 << L) + 1) ** 2 for L in levels)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    best = hn.hn_mg_autotune_batch(mgs, bh, reps=2)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier(pg, dev)
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        barrier(pg, dev)
+        return ms
+
+    stats = {}
+
+    def batched():
+        _, st, status = hn.hn_mg_solve_batch(mgs, levels, bs, xs)
+        assert status == hn.HN_OK
+        stats["b"] = st
+
+    def looped():
+        for mg, L, b, x in zip(mgs, levels, bs, xs):
+            _, st, status = hn.hn_mg_solve(mg, L, b, x)
+            assert status == hn.HN_OK
+
+    with ClockSampler(local) as clk:
+        ms_b = timed(batched, args.steps, args.warmup)
+    ms_l = timed(looped, max(1, args.steps // 10), 1)
+    tb = max_over_ranks(sum(ms_b), pg, dev)
+    value = world * dofs * len(ms_b) / (tb * 1e-3)
+    loop_value = world * dofs * len(ms_l) / (max_over_ranks(sum(ms_l), pg, dev) * 1e-3)
+    # parity sample: the oracle's FP64 operator evaluates a few batched results
+    import oracle as O
+    worst = 0.0
+    for j in range(0, count, 32):
+        x = xs[j].cpu().numpy()
+        A64 = O.assemble(levels[j], coefs[j])
+        worst = max(worst, np.linalg.norm(O.defect(levels[j], A64, bh[j], x)) / np.linalg.norm(bh[j]))
+    if rank == 0:
+        cyc = [s["cycles"] for s in stats["b"]]
+        print(json.dumps({
+            "metric": "batched MG Poisson DOF/s to 1e-8 (256 problems, L 5..9, FP32-inner DC)",
+            "value": value, "unit": "DOF/s", "n_gpus": world, "steps": len(ms_b),
+            "warmup": args.warmup, "ms_per_step": tb / len(ms_b), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": "batch-256-L5to9-lognormal", "problems": count, "dof": dofs,
+                       "levels": {str(L): levels.count(L) for L in sorted(set(levels))},
+                       "tuning": {"tail_level": best[0], "cluster": best[1]},
+                       "l2_between_steps": "flushed (512 MiB write)"},
+            "per_problem_loop_dof_per_s": loop_value, "batched_over_loop": value / loop_value,
+            "inner_cycles": {"min": min(cyc), "max": max(cyc)},
+            "oracle_relres_max_sampled": worst, "clocks": clk.summary()}), flush=True)
+    for mg in mgs:
+        hn.hn_mg_destroy(mg)
+
+
+def run_serve(args, rank, world, local, pg):
+    """Continuous-batching server: Poisson arrivals, L uniform over {6..11}, seeded lognormal
+    coefficients and U[-1,1] right-hand sides (drawn from pools of 4 per level, scaled per
+    request: host-side generation would otherwise dominate), FP32-inner DC to 1e-8 under a
+    device-memory budget; reports throughput and p50/p99 latency (submit to completion)."""
+    import threading
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    from paper_0904_4152_gb300 import hn, inputs as I
+    torch.cuda.set_device(local)
+    if rank == 0:
+        g.build()
+    barrier(pg)
+    hn.lib()
+    pools = {}
+    for L in range(6, 12):
+        pools[L] = [(I.lognormal_coef(L, 500 + 10 * L + k), I.rhs_uniform(L, 600 + 10 * L + k))
+                    for k in range(4)]
+    opts = hn.hn_mg_opts_default(prec=hn.HN_PREC_FP32_DC)
+
+    def request(seed, L):
+        coef, b = pools[L][seed % 4]
+        scale = 0.5 + (seed % 97) / 97.0
+        return coef, b * scale
+
+    srv = hn.hn_server_create(int(args.budget_gb * (1 << 30)), args.slots)
+    try:
+        # capacity: a burst of requests with the same level mix, all submitted at once
+        calib = 120
+        _, lv, sd = I.serve_requests(calib, 1.0, seed=11 + rank)
+        t0 = time.perf_counter()
+        tickets = []
+        for L, seed in zip(lv, sd):
+            coef, b = request(int(seed), int(L))
+            tickets.append((hn.hn_mg_submit(srv, int(L), b, coef, opts=opts), int(L)))
+        for t, L in tickets:
+            status, _, _ = hn.hn_mg_poll(srv, t, L)
+            assert status == hn.HN_OK
+        capacity = calib / (time.perf_counter() - t0)
+        rate = args.load * capacity
+        arrivals, levels, seeds = I.serve_requests(args.requests, rate, seed=7 + rank)
+        sub = [None] * args.requests
+        res = [None] * args.requests
+        err = []
+
+        def submitter():
+            start = time.perf_counter()
+            for i in range(args.requests):
+                dt = start + arrivals[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                coef, b = request(int(seeds[i]), int(levels[i]))
+                try:
+                    sub[i] = hn.hn_mg_submit(srv, int(levels[i]), b, coef, opts=opts)
+                except hn.HnError as e:
+                    err.append(str(e))
+                    return
+
+        th = threading.Thread(target=submitter)
+        t_start = time.perf_counter()
+        th.start()
+        for i in range(args.requests):
+            while sub[i] is None and th.is_alive():
+                time.sleep(0.0005)
+            if sub[i] is None:
+                break
+            status, x, st = hn.hn_mg_poll(srv, sub[i], int(levels[i]))
+            res[i] = (status, st["solve_ns"] * 1e-6 if st else None, st["relres"] if st else None)
+        th.join()
+        t_end = time.perf_counter()
+        info = hn.hn_server_query(srv)
+    finally:
+        hn.hn_server_destroy(srv)
+    done = [r for r in res if r is not None]
+    lat = np.array([r[1] for r in done if r[0] == hn.HN_OK])
+    ok = len(lat)
+    dofs = sum(((1 << int(L)) + 1) ** 2 for L, r in zip(levels, res) if r is not None and r[0] == hn.HN_OK)
+    wall = t_end - t_start
+    if rank == 0:
+        print(json.dumps({
+            "metric": "serve p50/p99 latency and throughput (Poisson arrivals, L 6..11, FP32-inner DC)",
+            "value": ok / wall, "unit": "requests/s", "n_gpus": world, "requests": args.requests,
+            "completed_ok": ok, "errors": err[:3], "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "serve-poisson-L6to11-lognormal", "offered_load": args.load,
+                       "arrival_rate_per_s": rate, "capacity_per_s": capacity,
+                       "budget_gb": args.budget_gb, "slots": args.slots},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "dof_per_s": dofs / wall, "scheduler_iterations": info["iterations"],
+            "relres_max": max(r[2] for r in done if r[0] == hn.HN_OK)}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local, pg = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world, pg)
+    elif args.workload == "batch":
+        run_batch(args, rank, world, local, pg)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local, pg)
     else:
         run_ours(args, rank, world, local, pg)
     if pg is not None:

@@ -32,6 +32,12 @@ hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t);
 hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, double* times_ms,
                          int cap);
 
+/* The same for a batch (hn_mg_solve_batch over mgs[0..count)): candidates tail_level coarse_L..8,
+ * cluster 1, 2, 4; the fastest shape is stored in every member and used by later batch solves of
+ * the same members (a batch whose members carry no common tuned shape picks one by its size). */
+hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const* b, int reps,
+                               hn_tuning* best);
+
 #ifdef __cplusplus
 }
 #endif

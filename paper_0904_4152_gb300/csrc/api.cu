@@ -54,6 +54,21 @@ void forget_batch(hn_mg* mg) {
   }
 }
 
+// launch shape of a batch: the members' common tuned shape, else by batch size (many problems:
+// one block per problem and a tail that fits in shared memory; few problems: the solo default)
+Tuning batch_tuning(const std::vector<hn_mg*>& list) {
+  bool same = list[0]->tuned;
+  for (hn_mg* mg : list)
+    same = same && mg->tuned && mg->tuning.tail_level == list[0]->tuning.tail_level &&
+           mg->tuning.cluster == list[0]->tuning.cluster && mg->tuning.pdl == list[0]->tuning.pdl;
+  if (same) return list[0]->tuning;
+  Tuning t;
+  const int n = (int)list.size();
+  if (n >= 32) { t.tail_level = 5; t.cluster = 1; }
+  else if (n >= 8) { t.tail_level = 6; t.cluster = 4; }
+  return t;
+}
+
 hn_status copy_in(double* dst, const double* src, long long N, int device_ptrs, cudaStream_t s) {
   HN_CUDA(cudaMemcpyAsync(dst, src, (size_t)N * 8,
                           device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -254,10 +269,16 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
     std::unique_ptr<Engine> e(new Engine());
     HN_TRY(e->create(prm, count, Lmax, caps, fine, list[0]->stream));
     HN_TRY(e->set_members(list));
+    e->set_tuning(batch_tuning(list));
     g_batch_engine = std::move(e);
     g_batch_key = list;
   }
   Engine& e = *g_batch_engine;
+  {
+    const Tuning t = batch_tuning(list);
+    const Tuning& c = e.tuning();
+    if (t.tail_level != c.tail_level || t.cluster != c.cluster || t.pdl != c.pdl) e.set_tuning(t);
+  }
   cudaStream_t s = e.stream();
   std::vector<int> slots(count), guess(count, 0);
   for (int j = 0; j < count; ++j) {
@@ -433,6 +454,50 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
       if (per < best_ms) { best_ms = per; bt = t; }
     }
   HN_TRY(hn_mg_set_tuning(mg, &bt));
+  if (best) *best = bt;
+  return HN_OK;
+}
+
+hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const* b, int reps,
+                               hn_tuning* best) {
+  clear_error();
+  if (!mgs || !b || count < 1 || reps < 1) return set_error(HN_ERR_ARG, "bad arguments");
+  std::vector<double*> xs(count, nullptr);
+  struct FreeAll { std::vector<double*>& v; ~FreeAll() { for (double* p : v) if (p) cudaFreeHost(p); } } fa{xs};
+  for (int j = 0; j < count; ++j)
+    HN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&xs[j]), (size_t)N_of(mgs[j]->L) * 8));
+  const int clusters[3] = {1, 2, 4};
+  int Lmax = 0;
+  for (int j = 0; j < count; ++j) Lmax = std::max(Lmax, mgs[j]->L);
+  double best_ms = 1e300;
+  hn_tuning bt{5, 1, 0};
+  for (int T = mgs[0]->coarse; T <= std::min(Lmax, 8); ++T)
+    for (int ci = 0; ci < 3; ++ci) {
+      hn_tuning t{T, clusters[ci], 0};
+      for (int j = 0; j < count; ++j) {
+        Tuning tu; tu.tail_level = T; tu.cluster = clusters[ci]; tu.pdl = 0;
+        mgs[j]->tuning = tu;
+        mgs[j]->tuned = true;
+      }
+      HN_TRY(hn_mg_solve_batch(mgs, count, b, xs.data(), 0, nullptr));   // capture + warm-up
+      const long long t0 = now_ns();
+      for (int r = 0; r < reps; ++r) {
+        hn_status st = hn_mg_solve_batch(mgs, count, b, xs.data(), 0, nullptr);
+        if (st != HN_OK && st != HN_ERR_NOT_CONVERGED) return st;
+      }
+      const double ms = (now_ns() - t0) * 1e-6 / reps;
+      if (ms < best_ms) { best_ms = ms; bt = t; }
+    }
+  for (int j = 0; j < count; ++j) {
+    Tuning tu; tu.tail_level = bt.tail_level; tu.cluster = bt.cluster; tu.pdl = 0;
+    mgs[j]->tuning = tu;
+    mgs[j]->tuned = true;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_batch_engine.reset();
+    g_batch_key.clear();
+  }
   if (best) *best = bt;
   return HN_OK;
 }

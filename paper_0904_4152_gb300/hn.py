@@ -32,6 +32,7 @@ EXPORTS = [
     "hn_mg_poll", "hn_server_query", "hn_server_destroy", "hn_last_error", "hn_version",
     "hn_mg_set_profiling", "hn_mg_kernel_times", "hn_mg_last_launches",
     "hn_band_defect_norm_static", "hn_mg_set_tuning", "hn_mg_get_tuning", "hn_mg_autotune",
+    "hn_mg_autotune_batch",
 ]
 
 
@@ -122,6 +123,8 @@ def lib():
         L.hn_mg_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
         L.hn_mg_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
         L.hn_mg_autotune.argtypes = [vp, vp, ip, ctypes.POINTER(Tuning), dp, ip]
+        L.hn_mg_autotune_batch.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ip,
+                                           ctypes.POINTER(Tuning)]
         L.hn_mg_last_launches.argtypes = [vp]
         L.hn_mg_last_launches.restype = ctypes.c_longlong
         _lib = L
@@ -343,6 +346,17 @@ def hn_mg_autotune(mg, b, reps=3, coarse_L=2):
         if not np.isnan(v):
             table[(coarse_L + i // 5, clusters[i % 5])] = float(v)
     return (best.tail_level, best.cluster), table
+
+
+def hn_mg_autotune_batch(mgs, bs, reps=2):
+    """Time launch shapes on a batch (host right-hand sides), keep the fastest in every member."""
+    n = len(mgs)
+    bs = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
+    arr = lambda v: (ctypes.c_void_p * n)(*v)
+    best = Tuning()
+    _check(lib().hn_mg_autotune_batch(arr([m.value for m in mgs]), n, arr([b.ctypes.data for b in bs]),
+                                      reps, ctypes.byref(best)))
+    return best.tail_level, best.cluster, best.pdl
 
 
 def hn_mg_last_launches(mg):
