@@ -17,8 +17,9 @@ extern "C" {
 typedef struct {
   int tail_level;   /* levels <= tail_level run fused (coarse_L .. HN_MAX_LEVEL) */
   int cluster;      /* blocks per cluster of the fused launch: 1, 2, 4, 8 or 16 */
-  int pdl;          /* 1: consecutive kernels overlap their launch with the predecessor
-                       (programmatic dependent launch); 0: plain stream order */
+  int pdl;          /* programmatic dependent launch (a kernel launches while its predecessor
+                       runs and waits for its results): 0 off, 1 every kernel, 2 kernels of
+                       fewer blocks than SMs only */
 } hn_tuning;
 
 /* Set / read the launch shape used by mg's later solves.  HN_ERR_ARG on values out of range. */

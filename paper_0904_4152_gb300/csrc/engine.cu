@@ -336,7 +336,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
     std::call_once(once, [] { prep = prepare_kernels(); });
     HN_CUDA(prep);
   }
-  maxGrid_ = sm_count() * 4;
+  maxGrid_ = sm_count() * 8;     // each launch is clamped to its kernel's resident blocks
   size_t bytes = 0;
   auto take = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
   take(sizeof(ProblemDev) * cap);

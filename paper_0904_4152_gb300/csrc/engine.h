@@ -64,7 +64,7 @@ enum KClass {
 struct Tuning {
   int tail_level = 7;
   int cluster = 16;
-  int pdl = 0;      // programmatic dependent launch between consecutive kernels
+  int pdl = 2;      // programmatic dependent launch for launches of fewer blocks than SMs
 };
 
 class Engine;

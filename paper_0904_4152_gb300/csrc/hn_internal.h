@@ -149,6 +149,7 @@ bool pre_fuses(int prec);
 cudaError_t launch_tail(const EngineDev& E, int T, int want, int cluster, cudaStream_t s);
 // one-time kernel attributes (cluster-size opt-in); call outside stream capture
 cudaError_t prepare_kernels();
+
 cudaError_t launch_restrict(const EngineDev& E, TileList tl_coarse, int fine_level, int want,
                             int grid, cudaStream_t s);
 cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want, int x_sel,

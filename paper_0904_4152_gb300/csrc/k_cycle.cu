@@ -11,6 +11,9 @@
 // vectors (double2 pairs, float4, or 4 packed halves); the three x rows of the stencil are loaded
 // as aligned 4-vectors because the row offset n = 2^L + 1 equals 2^L plus one column, and the
 // one- or two-column overhang at each side comes from the neighbouring lanes by warp shuffles.
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
 #include <cooperative_groups.h>
 
 #include "hn_internal.h"
@@ -1064,10 +1067,25 @@ __global__ void __launch_bounds__(256) k_summary(EngineDev E, cudaGraphCondition
 
 inline int grid_or_one(int g) { return g < 1 ? 1 : g; }
 
-// launch with optional programmatic dependent launch and thread-block clusters
+// resident 256-thread blocks per SM of a kernel (cached per kernel)
+int resident_blocks(const void* f, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(f);
+  if (it != cache.end()) return it->second;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, 256, smem) != cudaSuccess || b < 1) b = 1;
+  cache[f] = b;
+  return b;
+}
+
+// launch with optional programmatic dependent launch and thread-block clusters.  Grid-stride
+// kernels (cluster == 0) get at most one wave of resident blocks.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_k(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t s, bool pdl,
+cudaError_t launch_k(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t s, int pdl,
                      int cluster, Args... args) {
+  if (cluster == 0) grid = std::min(grid, resident_blocks(reinterpret_cast<const void*>(kern), smem) * sm_count());
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid_or_one(grid), 1, 1);
   cfg.blockDim = dim3(256, 1, 1);
@@ -1075,7 +1093,9 @@ cudaError_t launch_k(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
   int na = 0;
-  if (pdl) {
+  // pdl: 1 = every launch; 2 = launches of fewer blocks than SMs (their waiting blocks do not
+  // take occupancy from a bandwidth-bound predecessor)
+  if (pdl == 1 || (pdl == 2 && grid_or_one(grid) < sm_count())) {
     attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[na].val.programmaticStreamSerializationAllowed = 1;
     ++na;
@@ -1239,7 +1259,7 @@ cudaError_t launch_summary(const EngineDev& E, cudaGraphConditionalHandle h, int
 }
 
 cudaError_t launch_boundary_check(const EngineDev& E, cudaStream_t s) {
-  return launch_k(k_boundary_check, E.nprob, 0, s, false, 0, E);
+  return launch_k(k_boundary_check, E.nprob, 0, s, 0, 0, E);
 }
 
 // the fine-level defect norm of the V-cycle's own precision (convergence check)
