@@ -46,9 +46,10 @@ def parse():
     ap.add_argument("--host-loop", action="store_true",
                     help="run solves as one graph launch per iteration (ncu cannot profile kernels "
                          "inside the device-side loop)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve"],
+    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve", "kernels"],
                     help="solve: the L=10 benchmark (default); batch: 256 uneven problems in one "
-                         "batched solve; serve: Poisson-arrival requests through the solve server")
+                         "batched solve; serve: Poisson-arrival requests through the solve server; "
+                         "kernels: band-SpMV / defect / Jacobi alone at L=12 in FP64, FP32, FP16-band")
     ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load / capacity")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: device memory budget")
@@ -189,6 +190,39 @@ def run_reference(args, rank, world, pg):
     print(json.dumps(line), flush=True)
 
 
+def band_kernels(hn, stream, peak, L=12, reps=20):
+    """Band-SpMV, defect and Jacobi launched alone on level L (FP64, FP32, FP16-band storage):
+    mean launch time by CUDA events and algorithmic bytes -> GB/s and fraction of `peak`."""
+    band = {}
+    A = hn.hn_band_create(L)
+    for pname, prec in (("fp64", hn.HN_PREC_FP64), ("fp32", hn.HN_PREC_FP32_DC),
+                        ("fp16band", hn.HN_PREC_FP16BAND_DC)):
+        mg = hn.hn_mg_setup(A, prec=prec, stream=stream.cuda_stream)
+        row = {}
+        for oname, op in (("spmv", hn.HN_OP_SPMV), ("defect", hn.HN_OP_DEFECT),
+                          ("jacobi", hn.HN_OP_JACOBI)):
+            ms, by = hn.hn_mg_time_kernel(mg, op, L, reps=reps)
+            row[oname] = {"gb_per_s": by / (ms * 1e-3) / 1e9, "frac": by / (ms * 1e-3) / 1e9 / peak,
+                          "us": ms * 1e3, "bytes": by}
+        band[pname] = row
+        hn.hn_mg_destroy(mg)
+    hn.hn_band_destroy(A)
+    return band
+
+
+def run_kernels(args, rank, local):
+    import torch
+    import __graft_entry__ as g
+    from paper_0904_4152_gb300 import hn
+    torch.cuda.set_device(local)
+    g.build()
+    peak, kind = measured_peak_gbs()
+    band = band_kernels(hn, torch.cuda.current_stream(), peak, L=args.level if args.level != L_BENCH else 12)
+    if rank == 0:
+        print(json.dumps({"metric": "band kernels alone, HBM GB/s", "peak": peak, "peak_kind": kind,
+                          "kernels": band}), flush=True)
+
+
 def run_ours(args, rank, world, local, pg):
     import numpy as np
     import torch
@@ -294,6 +328,9 @@ def run_ours(args, rank, world, local, pg):
         by_class[t["name"]] += t["total_ms"]
     prof_total = sum(by_class.values())
 
+    # band kernels alone at L=12 (data >> L2): band-SpMV, defect and Jacobi HBM GB/s per precision
+    band = band_kernels(hn, stream, peak) if rank == 0 else {}
+
     cpu = None
     if rank == 0 and world == 1 and L <= 11:
         cpu = cpu_baseline(L, 0, 1)
@@ -329,6 +366,7 @@ def run_ours(args, rank, world, local, pg):
                          "avg_launch_us": avg_s * 1e6, "launches": dom["launches"],
                          "share_of_profiled": dom["total_ms"] / prof_total if prof_total else None},
             "kernel_share": {k: v / prof_total for k, v in sorted(by_class.items())} if prof_total else {},
+            "band_kernels_L12": band,
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
@@ -528,6 +566,8 @@ def main():
         run_batch(args, rank, world, local, pg)
     elif args.workload == "serve":
         run_serve(args, rank, world, local, pg)
+    elif args.workload == "kernels":
+        run_kernels(args, rank, local)
     else:
         run_ours(args, rank, world, local, pg)
     if pg is not None:

@@ -29,6 +29,13 @@ hn_status hn_mg_set_profiling(hn_mg* mg, int enable);
 /* Copy up to max accumulated entries (classes x levels with launches > 0); returns the count. */
 int hn_mg_kernel_times(const hn_mg* mg, hn_kernel_time* out, int max);
 
+/* Time one kernel of the solver on its own: `reps` back-to-back launches of op (HN_OP_SPMV,
+ * HN_OP_DEFECT or HN_OP_JACOBI) on `level` of mg's hierarchy (the inner hierarchy of a DC
+ * hierarchy), on whatever the level's vectors hold, timed with CUDA events on mg's stream after
+ * one warm-up launch.  *avg_ms receives the mean launch time, *bytes the algorithmic DRAM bytes of
+ * one launch (N_l x bytes per node of the kernel and precision). */
+hn_status hn_mg_time_kernel(hn_mg* mg, int op, int level, int reps, double* avg_ms, double* bytes);
+
 /* Kernel launches of mg's last single solve (hn_mg_solve): the graph's init kernels plus the
  * kernels of every loop iteration that ran.  0 before the first solve. */
 long long hn_mg_last_launches(const hn_mg* mg);

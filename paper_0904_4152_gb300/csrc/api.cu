@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "engine.h"
+#include "../../include/hn_profile.h"
 #include "../../include/hn_tune.h"
 
 using namespace hn;
@@ -499,6 +500,39 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
     g_batch_key.clear();
   }
   if (best) *best = bt;
+  return HN_OK;
+}
+
+hn_status hn_mg_time_kernel(hn_mg* mg, int op, int level, int reps, double* avg_ms, double* bytes) {
+  clear_error();
+  if (!mg || !avg_ms || reps < 1) return set_error(HN_ERR_ARG, "bad arguments");
+  if (op != HN_OP_SPMV && op != HN_OP_DEFECT && op != HN_OP_JACOBI)
+    return set_error(HN_ERR_ARG, "op must be SPMV, DEFECT or JACOBI");
+  if (level < mg->coarse || level > mg->L) return set_error(HN_ERR_ARG, "level out of range");
+  HN_TRY(ensure_solo(mg));
+  Engine& e = *mg->solo;
+  cudaStream_t s = e.stream();
+  HN_TRY(e.set_phase(0, PH_CYCLE, 0));
+  HN_TRY(e.apply(op, level, PH_CYCLE, s));                   // warm-up
+  cudaEvent_t e0, e1;
+  HN_CUDA(cudaEventCreate(&e0));
+  HN_CUDA(cudaEventCreate(&e1));
+  struct Ev { cudaEvent_t a, b; ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); } } ev{e0, e1};
+  HN_CUDA(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) HN_TRY(e.apply(op, level, PH_CYCLE, s));
+  HN_CUDA(cudaEventRecord(e1, s));
+  HN_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.0f;
+  HN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  *avg_ms = ms / reps;
+  if (bytes) {
+    const int prec = mg->prm.prec;
+    const double vb = prec == P64 ? 8 : 4, bb = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
+    const double per = op == HN_OP_SPMV ? 9 * bb + 2 * vb
+                     : op == HN_OP_DEFECT ? 9 * bb + 3 * vb
+                     : 9 * bb + 3 * vb + (prec == P64 ? 8 : 0);
+    *bytes = per * (double)N_of(level);
+  }
   return HN_OK;
 }
 

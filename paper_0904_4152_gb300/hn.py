@@ -32,7 +32,7 @@ EXPORTS = [
     "hn_mg_poll", "hn_server_query", "hn_server_destroy", "hn_last_error", "hn_version",
     "hn_mg_set_profiling", "hn_mg_kernel_times", "hn_mg_last_launches",
     "hn_band_defect_norm_static", "hn_mg_set_tuning", "hn_mg_get_tuning", "hn_mg_autotune",
-    "hn_mg_autotune_batch",
+    "hn_mg_autotune_batch", "hn_mg_time_kernel",
 ]
 
 
@@ -125,6 +125,7 @@ def lib():
         L.hn_mg_autotune.argtypes = [vp, vp, ip, ctypes.POINTER(Tuning), dp, ip]
         L.hn_mg_autotune_batch.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ip,
                                            ctypes.POINTER(Tuning)]
+        L.hn_mg_time_kernel.argtypes = [vp, ip, ip, ip, dp, dp]
         L.hn_mg_last_launches.argtypes = [vp]
         L.hn_mg_last_launches.restype = ctypes.c_longlong
         _lib = L
@@ -357,6 +358,13 @@ def hn_mg_autotune_batch(mgs, bs, reps=2):
     _check(lib().hn_mg_autotune_batch(arr([m.value for m in mgs]), n, arr([b.ctypes.data for b in bs]),
                                       reps, ctypes.byref(best)))
     return best.tail_level, best.cluster, best.pdl
+
+
+def hn_mg_time_kernel(mg, op, level, reps=20):
+    """(mean ms per launch, algorithmic bytes per launch) of one solver kernel on one level."""
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    _check(lib().hn_mg_time_kernel(mg, op, level, reps, ctypes.byref(ms), ctypes.byref(by)))
+    return ms.value, by.value
 
 
 def hn_mg_last_launches(mg):
