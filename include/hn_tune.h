@@ -20,6 +20,8 @@ typedef struct {
   int pdl;          /* programmatic dependent launch (a kernel launches while its predecessor
                        runs and waits for its results): 0 off, 1 every kernel, 2 kernels of
                        fewer blocks than SMs only */
+  int staged;       /* 1: the band kernels of large FP32 / FP16 levels stream the bands through
+                       shared memory with bulk copies (TMA engine) on mbarriers; 0: register path */
 } hn_tuning;
 
 /* Set / read the launch shape used by mg's later solves.  HN_ERR_ARG on values out of range. */

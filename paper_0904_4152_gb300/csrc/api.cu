@@ -61,7 +61,8 @@ Tuning batch_tuning(const std::vector<hn_mg*>& list) {
   bool same = list[0]->tuned;
   for (hn_mg* mg : list)
     same = same && mg->tuned && mg->tuning.tail_level == list[0]->tuning.tail_level &&
-           mg->tuning.cluster == list[0]->tuning.cluster && mg->tuning.pdl == list[0]->tuning.pdl;
+           mg->tuning.cluster == list[0]->tuning.cluster && mg->tuning.pdl == list[0]->tuning.pdl &&
+           mg->tuning.staged == list[0]->tuning.staged;
   if (same) return list[0]->tuning;
   Tuning t;
   const int n = (int)list.size();
@@ -221,6 +222,9 @@ hn_status hn_mg_solve(hn_mg* mg, const double* b, double* x, int x_is_guess, int
   HN_TRY(e.run_to_completion());
   std::vector<ProbState> st;
   HN_TRY(e.read_states(st));
+  int derr = 0;
+  HN_TRY(e.read_error(&derr));
+  if (derr) return set_error(HN_ERR_CUDA, "a bounded device wait for a bulk copy gave up");
   if (st[0].status != HN_ERR_ARG) {
     if (st[0].status == HN_OK && st[0].bnorm == 0.0) HN_CUDA(cudaMemsetAsync(P.x64, 0, (size_t)N * 8, s));
     HN_TRY(copy_out(x, P.x64, N, device_ptrs, s));
@@ -278,7 +282,8 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
   {
     const Tuning t = batch_tuning(list);
     const Tuning& c = e.tuning();
-    if (t.tail_level != c.tail_level || t.cluster != c.cluster || t.pdl != c.pdl) e.set_tuning(t);
+    if (t.tail_level != c.tail_level || t.cluster != c.cluster || t.pdl != c.pdl || t.staged != c.staged)
+      e.set_tuning(t);
   }
   cudaStream_t s = e.stream();
   std::vector<int> slots(count), guess(count, 0);
@@ -293,6 +298,9 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
   HN_TRY(e.run_to_completion());
   std::vector<ProbState> st;
   HN_TRY(e.read_states(st));
+  int derr = 0;
+  HN_TRY(e.read_error(&derr));
+  if (derr) return set_error(HN_ERR_CUDA, "a bounded device wait for a bulk copy gave up");
   hn_status first_bad = HN_OK;
   for (int j = 0; j < count; ++j) {
     ProblemDev& P = list[j]->host;
@@ -398,10 +406,12 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
     return set_error(HN_ERR_ARG, "tail_level in [coarse_L, %d], cluster in {1,2,4,8,16}", HN_MAX_LEVEL);
   HN_TRY(ensure_solo(mg));
   if (t->pdl < 0 || t->pdl > 2) return set_error(HN_ERR_ARG, "pdl must be 0, 1 or 2");
+  if (t->staged != 0 && t->staged != 1) return set_error(HN_ERR_ARG, "staged must be 0 or 1");
   Tuning tu;
   tu.tail_level = t->tail_level;
   tu.cluster = c;
   tu.pdl = t->pdl;
+  tu.staged = t->staged;
   mg->solo->set_tuning(tu);
   mg->tuning = tu;
   mg->tuned = true;
@@ -415,6 +425,7 @@ hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t) {
   t->tail_level = tu.tail_level;
   t->cluster = tu.cluster;
   t->pdl = tu.pdl;
+  t->staged = tu.staged;
   return HN_OK;
 }
 
@@ -429,7 +440,7 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
   struct Free { double* p; ~Free() { cudaFreeHost(p); } } fr{x};
   const int clusters[5] = {1, 2, 4, 8, 16};
   double best_ms = 1e300;
-  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 1};
+  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 2, 0};
   cudaEvent_t e0, e1;
   HN_CUDA(cudaEventCreate(&e0));
   HN_CUDA(cudaEventCreate(&e1));
@@ -437,7 +448,7 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
   const int tmax = std::min(mg->L, 9);
   for (int T = mg->coarse; T <= tmax; ++T)
     for (int ci = 0; ci < 5; ++ci) {
-      hn_tuning t{T, clusters[ci], 1};
+      hn_tuning t{T, clusters[ci], 2, 0};
       HN_TRY(hn_mg_set_tuning(mg, &t));
       HN_TRY(hn_mg_solve(mg, b, x, 0, 0, nullptr));            // capture + warm-up
       HN_CUDA(cudaEventRecord(e0, mg->solo->stream()));
@@ -471,12 +482,12 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
   int Lmax = 0;
   for (int j = 0; j < count; ++j) Lmax = std::max(Lmax, mgs[j]->L);
   double best_ms = 1e300;
-  hn_tuning bt{5, 1, 0};
+  hn_tuning bt{5, 1, 2, 0};
   for (int T = mgs[0]->coarse; T <= std::min(Lmax, 8); ++T)
     for (int ci = 0; ci < 3; ++ci) {
-      hn_tuning t{T, clusters[ci], 0};
+      hn_tuning t{T, clusters[ci], 2, 0};
       for (int j = 0; j < count; ++j) {
-        Tuning tu; tu.tail_level = T; tu.cluster = clusters[ci]; tu.pdl = 0;
+        Tuning tu; tu.tail_level = T; tu.cluster = clusters[ci]; tu.pdl = 2;
         mgs[j]->tuning = tu;
         mgs[j]->tuned = true;
       }
@@ -490,7 +501,7 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
       if (ms < best_ms) { best_ms = ms; bt = t; }
     }
   for (int j = 0; j < count; ++j) {
-    Tuning tu; tu.tail_level = bt.tail_level; tu.cluster = bt.cluster; tu.pdl = 0;
+    Tuning tu; tu.tail_level = bt.tail_level; tu.cluster = bt.cluster; tu.pdl = bt.pdl;
     mgs[j]->tuning = tu;
     mgs[j]->tuned = true;
   }

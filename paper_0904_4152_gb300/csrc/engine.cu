@@ -346,7 +346,11 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   for (int l = 0; l <= kMaxLevel; ++l) {
     itemCap_[l] = l < (int)tiles_cap.size() ? tiles_cap[l] : 0;
     take(sizeof(int2) * (size_t)std::max<long long>(itemCap_[l], 1));
+    chunkCap_[l] = itemCap_[l] > 0 ? itemCap_[l] / kChunkTiles + cap + 1 : 0;
+    take(sizeof(int4) * (size_t)std::max<long long>(chunkCap_[l], 1));
   }
+  take(sizeof(int) * (kMaxLevel + 1));
+  take(sizeof(int));
   fineCap_ = fine_cap;
   take(sizeof(int2) * (size_t)std::max<long long>(fine_cap, 1));
   take(sizeof(double) * (size_t)std::max<long long>(fine_cap, 1));
@@ -360,7 +364,12 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   dS_ = b.take<ProbState>(cap);
   dFineOff_ = b.take<int>(cap);
   dCounts_ = b.take<int>(kMaxLevel + 2);
-  for (int l = 0; l <= kMaxLevel; ++l) dItems_[l] = b.take<int2>((size_t)std::max<long long>(itemCap_[l], 1));
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    dItems_[l] = b.take<int2>((size_t)std::max<long long>(itemCap_[l], 1));
+    dChunks_[l] = b.take<int4>((size_t)std::max<long long>(chunkCap_[l], 1));
+  }
+  dChunkCounts_ = b.take<int>(kMaxLevel + 1);
+  dErr_ = b.take<int>(1);
   dFine_ = b.take<int2>((size_t)std::max<long long>(fine_cap, 1));
   double* part = b.take<double>((size_t)std::max<long long>(fine_cap, 1));
   double* part2 = b.take<double>((size_t)std::max<long long>(fine_cap, 1));
@@ -379,9 +388,11 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   E_.active_host = dActive;
   E_.iter = iter;
   E_.pdl = tune_.pdl;
+  E_.err = dErr_;
+  E_.staged = tune_.staged;
   E_.iter_limit = (unsigned)(prm.max_cycles + prm.max_outer + 8);
   for (int l = 0; l <= kMaxLevel; ++l) {
-    lists_[l] = TileList{dItems_[l], dCounts_ + l};
+    lists_[l] = TileList{dItems_[l], dCounts_ + l, dChunks_[l], dChunkCounts_ + l, (int)chunkCap_[l]};
     grid_[l] = grid_for(itemCap_[l]);
   }
   fine_ = TileList{dFine_, dCounts_ + kMaxLevel + 1};
@@ -394,6 +405,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
 hn_status Engine::set_members(const std::vector<hn_mg*>& slots) {
   if ((int)slots.size() > cap_) return set_error(HN_ERR_ARG, "too many problems for the engine");
   std::vector<std::vector<int2>> items(kMaxLevel + 1);
+  std::vector<std::vector<int4>> chunks(kMaxLevel + 1);
   std::vector<int2> fine;
   std::vector<int> fine_off(cap_, 0);
   std::vector<ProblemDev> probs(cap_);
@@ -406,21 +418,30 @@ hn_status Engine::set_members(const std::vector<hn_mg*>& slots) {
     for (int l = mg->coarse; l <= mg->L; ++l) {
       const int nt = (int)(pitch_of(l) / kTile);
       for (int t = 0; t < nt; ++t) items[l].push_back(make_int2(p, t));
+      for (int t = 0; t < nt; t += kChunkTiles)
+        chunks[l].push_back(make_int4(p, t, std::min(kChunkTiles, nt - t), 0));
     }
     fine_off[p] = (int)fine.size();
     const int nt = (int)(pitch_of(mg->L) / kTile);
     for (int t = 0; t < nt; ++t) fine.push_back(make_int2(p, t));
   }
   for (int l = 0; l <= kMaxLevel; ++l)
-    if ((long long)items[l].size() > itemCap_[l])
+    if ((long long)items[l].size() > itemCap_[l] || (long long)chunks[l].size() > chunkCap_[l])
       return set_error(HN_ERR_ARG, "work list of level %d exceeds the engine capacity", l);
   if ((long long)fine.size() > fineCap_) return set_error(HN_ERR_ARG, "fine work list exceeds capacity");
+  std::vector<int> chunkCounts(kMaxLevel + 1, 0);
   for (int l = 0; l <= kMaxLevel; ++l) {
     hCounts_[l] = (int)items[l].size();
+    chunkCounts[l] = (int)chunks[l].size();
     if (!items[l].empty())
       HN_CUDA(cudaMemcpyAsync(dItems_[l], items[l].data(), items[l].size() * sizeof(int2),
                               cudaMemcpyHostToDevice, s_));
+    if (!chunks[l].empty())
+      HN_CUDA(cudaMemcpyAsync(dChunks_[l], chunks[l].data(), chunks[l].size() * sizeof(int4),
+                              cudaMemcpyHostToDevice, s_));
   }
+  HN_CUDA(cudaMemcpyAsync(dChunkCounts_, chunkCounts.data(), chunkCounts.size() * sizeof(int),
+                          cudaMemcpyHostToDevice, s_));
   hCounts_[kMaxLevel + 1] = (int)fine.size();
   if (!fine.empty())
     HN_CUDA(cudaMemcpyAsync(dFine_, fine.data(), fine.size() * sizeof(int2), cudaMemcpyHostToDevice, s_));
@@ -452,6 +473,7 @@ hn_status Engine::start(const std::vector<int>& slots, const std::vector<int>& h
   // the iteration counter restarts with every closed-world solve (serving keeps counting and
   // relies on per-problem caps; its limit is set out of reach)
   HN_CUDA(cudaMemsetAsync(E_.iter, 0, sizeof(unsigned), s_));
+  HN_CUDA(cudaMemsetAsync(dErr_, 0, sizeof(int), s_));
   return HN_OK;
 }
 
@@ -734,6 +756,12 @@ int Engine::kernel_times(hn_kernel_time* out, int max) const {
 hn_status Engine::read_states(std::vector<ProbState>& out) {
   out.resize(cap_);
   HN_CUDA(cudaMemcpyAsync(out.data(), dS_, sizeof(ProbState) * cap_, cudaMemcpyDeviceToHost, s_));
+  HN_CUDA(cudaStreamSynchronize(s_));
+  return HN_OK;
+}
+
+hn_status Engine::read_error(int* err) {
+  HN_CUDA(cudaMemcpyAsync(err, dErr_, sizeof(int), cudaMemcpyDeviceToHost, s_));
   HN_CUDA(cudaStreamSynchronize(s_));
   return HN_OK;
 }

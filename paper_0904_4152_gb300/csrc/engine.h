@@ -65,6 +65,8 @@ struct Tuning {
   int tail_level = 7;
   int cluster = 16;
   int pdl = 2;      // programmatic dependent launch for launches of fewer blocks than SMs
+  int staged = 0;   // stream the bands of large FP32/FP16 levels through shared memory by bulk
+                    // copies (measured slower than the register path at L=12; off)
 };
 
 class Engine;
@@ -121,6 +123,8 @@ class Engine {
   hn_status run_init();
   hn_status run_iteration(unsigned* active_out);
   hn_status read_states(std::vector<ProbState>& out);
+  // the device error word (a bounded wait gave up); reset by start()
+  hn_status read_error(int* err);
   hn_status read_states_async(ProbState* host_dst);
   // single-kernel execution on slot 0 (hn_mg_apply)
   hn_status apply(int op, int level, int want, cudaStream_t s);
@@ -129,7 +133,7 @@ class Engine {
 
   void set_profiling(bool on);
   void set_iter_limit(unsigned lim) { E_.iter_limit = lim; graphsValid_ = false; }
-  void set_tuning(const Tuning& t) { tune_ = t; E_.pdl = t.pdl; graphsValid_ = false; }
+  void set_tuning(const Tuning& t) { tune_ = t; E_.pdl = t.pdl; E_.staged = t.staged; graphsValid_ = false; }
   const Tuning& tuning() const { return tune_; }
   // levels that may be some problem's finest level (their first smoothing step may start from a
   // nonzero iterate); all levels for the server
@@ -161,6 +165,10 @@ class Engine {
   int* dFineOff_ = nullptr;
   int* dCounts_ = nullptr;          // [kMaxLevel + 2]: per level, then the fine list
   int2* dItems_[kMaxLevel + 1] = {};
+  int4* dChunks_[kMaxLevel + 1] = {};
+  int* dChunkCounts_ = nullptr;
+  long long chunkCap_[kMaxLevel + 1] = {};
+  int* dErr_ = nullptr;
   int2* dFine_ = nullptr;
   long long itemCap_[kMaxLevel + 1] = {};
   long long fineCap_ = 0;

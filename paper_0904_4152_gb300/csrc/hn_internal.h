@@ -95,7 +95,13 @@ struct Params {
 struct TileList {
   const int2* items;
   const int* count;
+  // the same tiles grouped in chunks of up to kChunkTiles consecutive tiles of one problem,
+  // items (problem, first tile, tiles, 0); used by the kernels that stage bands in shared memory
+  const int4* chunks = nullptr;
+  const int* chunk_count = nullptr;
+  int chunk_cap = 0;        // host side: capacity of the chunk list
 };
+constexpr int kChunkTiles = 8;
 
 // ------------------------------------------------------------------------ launch wrappers
 // setup kernels (k_setup.cu); band pointer sets are passed by value
@@ -125,6 +131,8 @@ struct EngineDev {
   unsigned int* iter;          // iterations since the solve started (device)
   unsigned int iter_limit;     // beyond it every running problem stops as not converged
   int pdl;                     // launch with programmatic dependent launch (host-side flag)
+  int* err;                    // device word: nonzero after a bounded wait gave up
+  int staged;                  // host-side flag: large FP32/FP16 levels use the bulk-copy kernels
 };
 
 // Launch wrappers for one step of the schedule; grid = CTAs of 256 threads.  level < 0 means

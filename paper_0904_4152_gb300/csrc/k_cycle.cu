@@ -177,7 +177,7 @@ __device__ __forceinline__ void diag_rowsum(const void* const* band, const float
 // y = A x at the lane's 4 nodes (x read with load kind LK); xc = x at the nodes, dg = diagonal
 template <class Pol, int LK>
 __device__ __forceinline__ void apply_op4(const LevelDev& d, const typename Pol::V* __restrict__ x,
-                                          long long i0, long long shift, int lane,
+                                          long long i0, long long ib, long long shift, int lane,
                                           typename Pol::A (&acc)[4], typename Pol::V (&xc)[4],
                                           typename Pol::A (&dg)[4]) {
   typename Pol::V w[3][8];
@@ -185,8 +185,8 @@ __device__ __forceinline__ void apply_op4(const LevelDev& d, const typename Pol:
   for (int dy = -1; dy <= 1; ++dy) load_row<typename Pol::V, LK>(x, i0 + dy * shift, lane, w[dy + 1]);
 #pragma unroll
   for (int j = 0; j < 4; ++j) xc[j] = w[1][j + 2];
-  if constexpr (Pol::prec == P16) stencil_windows_rowsum<band_kind<LK>()>(d.band, d.scale, w, i0, acc, dg);
-  else stencil_windows<Pol, band_kind<LK>()>(d.band, nullptr, w, i0, acc, dg);
+  if constexpr (Pol::prec == P16) stencil_windows_rowsum<band_kind<LK>()>(d.band, d.scale, w, ib, acc, dg);
+  else stencil_windows<Pol, band_kind<LK>()>(d.band, nullptr, w, ib, acc, dg);
 }
 
 // deterministic warp sum (butterfly; every lane ends with the same value)
@@ -272,13 +272,16 @@ __device__ __forceinline__ void wd4_of(const LevelDev& d, long long i0, typename
 }
 
 // One warp-tile of the band kernel on level d.  zg: the iterate of this level is zero.
-template <class Pol, int MODE, int LK>
+// boff: bands are indexed at i0 - boff (a chunk of bands staged in shared memory); LKB_ is the
+// load kind of the bands (shared memory: LD_GEN).
+template <class Pol, int MODE, int LK, int LKB_ = band_kind<LK>()>
 __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bool zg, long long i0,
                                           int lane, int in_sel, typename Pol::A omega,
-                                          double* partial_slot) {
+                                          double* partial_slot, long long boff = 0) {
   using A = typename Pol::A;
   using V = typename Pol::V;
-  constexpr int LKB = band_kind<LK>();
+  constexpr int LKB = LKB_;
+  const long long ib = i0 - boff;
   const V* rhs = static_cast<const V*>(d.rhs);
   if constexpr (MODE == M_PRE2B) {
     if (zg && fuses_pre<Pol>()) return;
@@ -294,8 +297,8 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
         for (int j = 0; j < 4; ++j) out[j] = wd[j] * b[j];
       } else {
         A dgv[4];
-        if constexpr (Pol::prec == P16) diag_rowsum<LKB>(d.band, d.scale, i0, dgv);
-        else load_band<Pol, LKB>(d.band[4], 1.0f, i0, dgv);
+        if constexpr (Pol::prec == P16) diag_rowsum<LKB>(d.band, d.scale, ib, dgv);
+        else load_band<Pol, LKB>(d.band[4], 1.0f, ib, dgv);
 #pragma unroll
         for (int j = 0; j < 4; ++j) out[j] = (omega / dgv[j]) * A(b[j]);
       }
@@ -336,7 +339,16 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
   const V* xin = static_cast<const V*>(d.x[src]);
   A acc[4], dg[4];
   V xc[4];
-  apply_op4<Pol, LK>(d, xin, i0, shift, lane, acc, xc, dg);
+  if constexpr (LKB == band_kind<LK>()) apply_op4<Pol, LK>(d, xin, i0, ib, shift, lane, acc, xc, dg);
+  else {                                          // bands from a shared-memory stage
+    V w[3][8];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) load_row<V, LK>(xin, i0 + dy * shift, lane, w[dy + 1]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) xc[j] = w[1][j + 2];
+    if constexpr (Pol::prec == P16) stencil_windows_rowsum<LKB>(d.band, d.scale, w, ib, acc, dg);
+    else stencil_windows<Pol, LKB>(d.band, nullptr, w, ib, acc, dg);
+  }
   if constexpr (MODE == M_SPMV) {
     V out[4];
 #pragma unroll
@@ -474,6 +486,45 @@ __device__ __forceinline__ void coarse_warp(const ProblemDev& P, int lane, doubl
   __syncwarp();
 }
 
+// mbarrier and bulk-copy (TMA engine, 1D) helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for phase `parity` of an mbarrier; false if it did not complete in time
+constexpr int kWaitTries = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (int i = 0; i < kWaitTries; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // ------------------------------------------------------------------ per-level kernels
 // One warp-tile per loop trip over the work list.  level < 0: each problem's own finest level.
 template <class Pol, int MODE>
@@ -500,6 +551,107 @@ __global__ void __launch_bounds__(256) k_band(EngineDev E, TileList tl, int leve
       if (lv == P.L && !zg) slot = E.partial + E.fine_off[p] + it.y;
     band_tile<Pol, MODE, LD_NC>(P.lev[lv], 1LL << lv, zg, (long long)it.y * kTile + lane * kLaneNodes,
                                 lane, in_sel, omega, slot);
+  }
+}
+
+// Band kernel with the bands streamed through shared memory by the bulk-copy engine.  A block
+// walks chunks of up to 8 consecutive warp-tiles of one problem-level (one warp per tile); for
+// each chunk one thread issues 9 bulk copies (one per band) into one of two stages, signalled on
+// that stage's mbarrier, two chunks ahead of the warps, which compute from shared memory with the
+// vectors read as in k_band.  Chunks of problems not in phase `want` are skipped; chunks whose
+// first two smoothing steps fuse from a zero iterate run the register path (their stencil reads
+// diagonal windows beyond the chunk).  A wait that does not complete in time sets E.err, stops
+// further copies and the block drains its outstanding copies (bounded) before returning.
+template <class Pol, int MODE>
+__global__ void __launch_bounds__(256) k_band_staged(EngineDev E, TileList tl, int level, int want,
+                                                     int in_sel) {
+  using A = typename Pol::A;
+  using B = typename Pol::B;
+  extern __shared__ __align__(128) unsigned char sbuf[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ LevelDev sdesc[2];
+  __shared__ int sinfo[2][4];        // problem, first tile, tiles, kind (-1 end, 0 skip, 1 staged, 2 register path)
+  __shared__ int s_abort;
+  pdl_start();
+  constexpr size_t kBandBytes = (size_t)kChunkTiles * kTile * sizeof(B);
+  constexpr size_t kStage = 9 * kBandBytes;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int count = *tl.chunk_count;
+  const int G = gridDim.x;
+  const A omega = A(E.prm.omega);
+  const long long shift = 1LL << level;
+  bool pending[2] = {false, false};   // thread 0: a fill of the stage is outstanding
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  auto prepare = [&](int k) {         // thread 0: chunk k of this block into stage k & 1
+    const int st = k & 1;
+    const int c = blockIdx.x + k * G;
+    if (c >= count || s_abort) { sinfo[st][3] = -1; return; }
+    const int4 ch = tl.chunks[c];
+    const ProblemDev& P = E.P[ch.x];
+    const ProbState& S = E.S[ch.x];
+    int kind = 1;
+    if (S.phase != want) kind = 0;
+    else if ((MODE == M_PRE12 || MODE == M_PRE2B) && fuses_pre<Pol>() && ((P.L > level) || S.zero_top))
+      kind = MODE == M_PRE12 ? 2 : 0;
+    sinfo[st][0] = ch.x; sinfo[st][1] = ch.y; sinfo[st][2] = ch.z; sinfo[st][3] = kind;
+    if (kind != 1) return;
+    const LevelDev& g = P.lev[level];
+    LevelDev& sd = sdesc[st];
+    sd = g;
+    unsigned char* base = sbuf + st * kStage;
+    const long long start = (long long)ch.y * kTile;
+    const unsigned bytes = (unsigned)(ch.z * kTile * sizeof(B));
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], 9 * bytes);
+    for (int q = 0; q < 9; ++q) {
+      B* dst = reinterpret_cast<B*>(base + q * kBandBytes);
+      bulk_g2s(dst, static_cast<const B*>(g.band[q]) + start, bytes, &bar[st]);
+      sd.band[q] = dst;
+    }
+    pending[st] = true;
+  };
+  if (threadIdx.x == 0) { prepare(0); prepare(1); }
+  __syncthreads();
+  unsigned phase[2] = {0u, 0u};
+  for (int k = 0;; ++k) {
+    const int st = k & 1;
+    const int kind = sinfo[st][3];
+    if (kind < 0) break;
+    bool ok = true;
+    if (kind == 1) {
+      ok = mbar_wait(&bar[st], phase[st]);
+      phase[st] ^= 1u;
+      if (threadIdx.x == 0) pending[st] = false;
+      if (!ok) { s_abort = 1; if (lane == 0) atomicExch(E.err, 1); }
+    }
+    if (ok && kind != 0 && warp < sinfo[st][2]) {
+      const int p = sinfo[st][0], t = sinfo[st][1] + warp;
+      const ProblemDev& P = E.P[p];
+      const ProbState& S = E.S[p];
+      const bool zg = (P.L > level) || S.zero_top;
+      double* slot = nullptr;
+      if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST)
+        if (level == P.L && !zg) slot = E.partial + E.fine_off[p] + t;
+      const long long i0 = (long long)t * kTile + lane * kLaneNodes;
+      if (kind == 1)
+        band_tile<Pol, MODE, LD_NC, LD_GEN>(sdesc[st], shift, zg, i0, lane, in_sel, omega, slot,
+                                            (long long)sinfo[st][1] * kTile);
+      else
+        band_tile<Pol, MODE, LD_NC>(P.lev[level], shift, zg, i0, lane, in_sel, omega, slot);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) prepare(k + 2);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {            // after an abort: let outstanding copies land (bounded)
+    for (int st = 0; st < 2; ++st)
+      if (pending[st]) (void)mbar_wait(&bar[st], phase[st]);
   }
 }
 
@@ -1112,10 +1264,29 @@ cudaError_t launch_k(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// shared memory of the staged band kernels: two stages of 9 band slices of 8 tiles
+template <class Pol>
+constexpr size_t staged_smem() { return 2 * 9 * (size_t)kChunkTiles * kTile * sizeof(typename Pol::B); }
+
 template <class Pol>
 cudaError_t launch_band_t(int mode, const EngineDev& E, TileList tl, int level, int want,
                           int in_sel, int grid, cudaStream_t s) {
   grid = grid_or_one(grid);
+  // large levels of the FP32 / FP16 hierarchies may stream their bands through shared memory
+  if (E.staged && Pol::prec != P64 && level >= 0 && tl.chunks && tl.chunk_cap >= sm_count() &&
+      (mode == M_SPMV || mode == M_DEFECT || mode == M_JACOBI || mode == M_JACOBI_FIRST ||
+       mode == M_PRE12 || mode == M_PRE2B)) {
+    const size_t sm = staged_smem<Pol>();
+    const int g = tl.chunk_cap;
+    switch (mode) {
+      case M_SPMV: return launch_k(k_band_staged<Pol, M_SPMV>, g, sm, s, E.pdl, 0, E, tl, level, want, in_sel);
+      case M_DEFECT: return launch_k(k_band_staged<Pol, M_DEFECT>, g, sm, s, E.pdl, 0, E, tl, level, want, in_sel);
+      case M_JACOBI: return launch_k(k_band_staged<Pol, M_JACOBI>, g, sm, s, E.pdl, 0, E, tl, level, want, in_sel);
+      case M_JACOBI_FIRST: return launch_k(k_band_staged<Pol, M_JACOBI_FIRST>, g, sm, s, E.pdl, 0, E, tl, level, want, in_sel);
+      case M_PRE12: return launch_k(k_band_staged<Pol, M_PRE12>, g, sm, s, E.pdl, 0, E, tl, level, want, in_sel);
+      default: return launch_k(k_band_staged<Pol, M_PRE2B>, g, sm, s, E.pdl, 0, E, tl, level, want, in_sel);
+    }
+  }
   switch (mode) {
     case M_SPMV: return launch_k(k_band<Pol, M_SPMV>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
     case M_DEFECT: return launch_k(k_band<Pol, M_DEFECT>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
@@ -1190,6 +1361,21 @@ cudaError_t prepare_kernels() {
   set(reinterpret_cast<const void*>(k_tail<F64>));
   set(reinterpret_cast<const void*>(k_tail<F32>));
   set(reinterpret_cast<const void*>(k_tail<F16>));
+  auto staged = [&](const void* f, size_t bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  staged((const void*)k_band_staged<F32, M_SPMV>, staged_smem<F32>());
+  staged((const void*)k_band_staged<F32, M_DEFECT>, staged_smem<F32>());
+  staged((const void*)k_band_staged<F32, M_JACOBI>, staged_smem<F32>());
+  staged((const void*)k_band_staged<F32, M_JACOBI_FIRST>, staged_smem<F32>());
+  staged((const void*)k_band_staged<F32, M_PRE12>, staged_smem<F32>());
+  staged((const void*)k_band_staged<F32, M_PRE2B>, staged_smem<F32>());
+  staged((const void*)k_band_staged<F16, M_SPMV>, staged_smem<F16>());
+  staged((const void*)k_band_staged<F16, M_DEFECT>, staged_smem<F16>());
+  staged((const void*)k_band_staged<F16, M_JACOBI>, staged_smem<F16>());
+  staged((const void*)k_band_staged<F16, M_JACOBI_FIRST>, staged_smem<F16>());
+  staged((const void*)k_band_staged<F16, M_PRE12>, staged_smem<F16>());
+  staged((const void*)k_band_staged<F16, M_PRE2B>, staged_smem<F16>());
   return e;
 }
 

@@ -130,15 +130,19 @@ def _inner_reference_bands(prec, l, cl):
     return O.dequantize_fp16(s, codes)
 
 
+@pytest.mark.parametrize("staged", [0, 1])
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
-@pytest.mark.parametrize("L", [4, 8])
-def test_inner_level_kernels(hn, prec, L):
+@pytest.mark.parametrize("L", [4, 8, 10])    # staged: levels 9, 10 stream their bands by bulk copies
+def test_inner_level_kernels(hn, prec, L, staged):
+    if staged and L < 10:
+        pytest.skip("the bulk-copy kernels serve levels with at least one chunk per SM")
     coef = I.lognormal_coef(L, 55)
     p = hn.HN_PREC_FP32_DC if prec == "fp32" else hn.HN_PREC_FP16BAND_DC
     rowsum = prec == "fp16"
     A = hn.hn_band_create(L, coef)
     mg = hn.hn_mg_setup(A, prec=p)
     hn.hn_band_destroy(A)
+    hn.hn_mg_set_tuning(mg, 7, 16, 2, staged)
     omega = 0.7
     try:
         for l, cl in coef_levels(L, coef).items():

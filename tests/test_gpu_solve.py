@@ -244,21 +244,21 @@ def test_profiling_times_kernels_without_changing_results(hn):
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_launch_shapes_do_not_change_results(hn, prec):
     # the tail level, cluster size and programmatic dependent launch only change where work runs
-    L = 8
+    L = 10                 # levels 9 and 10 are large enough for the bulk-copy kernels
     coef, b = I.batch_problem(3, L)
     A = hn.hn_band_create(L, coef)
     mg = hn.hn_mg_setup(A, prec=prec)
     hn.hn_band_destroy(A)
     try:
         ref, st0, _ = hn.hn_mg_solve(mg, L, b)
-        for shape in [(2, 1, 0), (4, 2, 0), (5, 16, 1), (7, 8, 0), (8, 16, 1)]:
+        for shape in [(2, 1, 0, 0), (4, 2, 0, 1), (5, 16, 1, 0), (7, 8, 2, 1), (8, 16, 1, 1)]:
             hn.hn_mg_set_tuning(mg, *shape)
             assert hn.hn_mg_get_tuning(mg) == shape
             x, st, _ = hn.hn_mg_solve(mg, L, b)
             np.testing.assert_array_equal(x, ref)
             assert st["cycles"] == st0["cycles"]
         best, table = hn.hn_mg_autotune(mg, b, reps=1)
-        assert best in table and len(table) == 5 * 7
+        assert best in table and len(table) == 5 * 8
         x, _, _ = hn.hn_mg_solve(mg, L, b)
         np.testing.assert_array_equal(x, ref)
     finally:
