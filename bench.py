@@ -138,6 +138,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def ncu_traffic_per_node(kernel):
+    """DRAM bytes per node of `kernel` from the committed ncu summary (profiles/), or None."""
+    path = os.path.join(ROOT, "profiles", "jacobi_f32_L12_ncu.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_node") and kernel in line:
+                return float(line.split("=")[1].split()[0])
+    except OSError:
+        pass
+    return None
+
+
 def measured_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -200,7 +212,8 @@ def band_kernels(hn, stream, peak, L=12, reps=20):
         mg = hn.hn_mg_setup(A, prec=prec, stream=stream.cuda_stream)
         row = {}
         for oname, op in (("spmv", hn.HN_OP_SPMV), ("defect", hn.HN_OP_DEFECT),
-                          ("jacobi", hn.HN_OP_JACOBI)):
+                          ("jacobi", hn.HN_OP_JACOBI), ("restrict", hn.HN_OP_RESTRICT),
+                          ("prolong", hn.HN_OP_PROLONG_ADD)):
             ms, by = hn.hn_mg_time_kernel(mg, op, L, reps=reps)
             row[oname] = {"gb_per_s": by / (ms * 1e-3) / 1e9, "frac": by / (ms * 1e-3) / 1e9 / peak,
                           "us": ms * 1e3, "bytes": by}
@@ -247,7 +260,8 @@ def run_ours(args, rank, world, local, pg):
     A = hn.hn_band_create(L)
     setup_band_s = time.perf_counter() - t0
     mgs = {}
-    for name, prec in (("mixed", hn.HN_PREC_FP32_DC), ("fp64", hn.HN_PREC_FP64)):
+    for name, prec in (("mixed", hn.HN_PREC_FP32_DC), ("fp64", hn.HN_PREC_FP64),
+                       ("fp16band", hn.HN_PREC_FP16BAND_DC)):
         mgs[name] = hn.hn_mg_setup(A, prec=prec, stream=stream.cuda_stream)
         if args.host_loop:
             hn.hn_mg_set_profiling(mgs[name], True)
@@ -279,11 +293,14 @@ def run_ours(args, rank, world, local, pg):
     with ClockSampler(local) as clk:
         ms_mixed, st_mixed, launches = timed(mgs["mixed"], args.steps, args.warmup)
     ms_fp64, st_fp64, _ = timed(mgs["fp64"], args.steps, args.warmup)
+    ms_fp16, st_fp16, _ = timed(mgs["fp16band"], args.steps, args.warmup)
 
     total_mixed = max_over_ranks(sum(ms_mixed), pg, dev)
     total_fp64 = max_over_ranks(sum(ms_fp64), pg, dev)
+    total_fp16 = max_over_ranks(sum(ms_fp16), pg, dev)
     value = world * N * args.steps / (total_mixed * 1e-3)
     fp64_value = world * N * args.steps / (total_fp64 * 1e-3)
+    fp16_value = world * N * args.steps / (total_fp16 * 1e-3)
     if args.quick:
         if rank == 0:
             print(json.dumps({"quick": True, "L": L, "mixed_dof_per_s": value,
@@ -321,6 +338,9 @@ def run_ours(args, rank, world, local, pg):
     dom = max(tops, key=lambda t: t["total_ms"])
     avg_s = dom["total_ms"] / dom["launches"] * 1e-3
     achieved = dom["bytes_per_launch"] / avg_s / 1e9
+    nodes = ((1 << dom["level"]) + 1) ** 2 if dom["level"] >= 0 else N
+    tpn = ncu_traffic_per_node("%s-fp32" % dom["name"])
+    traffic = tpn * nodes if tpn is not None else None
     peak, peak_kind = measured_peak_gbs()
     by_class = {}
     for t in times:
@@ -356,12 +376,17 @@ def run_ours(args, rank, world, local, pg):
                       "relres": st_mixed["relres"]},
             "fp64": {"dof_per_s": fp64_value, "ms_per_solve": total_fp64 / args.steps,
                      "cycles": st_fp64["cycles"], "relres": st_fp64["relres"]},
+            "fp16band": {"dof_per_s": fp16_value, "ms_per_solve": total_fp16 / args.steps,
+                         "cycles": st_fp16["cycles"], "outer_iters": st_fp16["outer_iters"],
+                         "relres": st_fp16["relres"]},
             "mixed_over_fp64": value / fp64_value,
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": N * 8,
                     "d2h_bytes_per_step": N * 8},
             "roofline": {"bound": "hbm", "kernel": "%s L%d" % (dom["name"], dom["level"]),
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "traffic_note": "ncu DRAM read+write per node of this kernel at L=12 "
+                                         "(data >> L2) x nodes of one launch",
                          "bytes_per_launch": dom["bytes_per_launch"],
                          "avg_launch_us": avg_s * 1e6, "launches": dom["launches"],
                          "share_of_profiled": dom["total_ms"] / prof_total if prof_total else None},

@@ -30,7 +30,7 @@ hn_status hn_mg_set_profiling(hn_mg* mg, int enable);
 int hn_mg_kernel_times(const hn_mg* mg, hn_kernel_time* out, int max);
 
 /* Time one kernel of the solver on its own: `reps` back-to-back launches of op (HN_OP_SPMV,
- * HN_OP_DEFECT or HN_OP_JACOBI) on `level` of mg's hierarchy (the inner hierarchy of a DC
+ * HN_OP_DEFECT, HN_OP_JACOBI, HN_OP_RESTRICT or HN_OP_PROLONG_ADD) on `level` of mg's hierarchy (the inner hierarchy of a DC
  * hierarchy), on whatever the level's vectors hold, timed with CUDA events on mg's stream after
  * one warm-up launch.  *avg_ms receives the mean launch time, *bytes the algorithmic DRAM bytes of
  * one launch (N_l x bytes per node of the kernel and precision). */

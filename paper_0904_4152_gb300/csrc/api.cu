@@ -517,8 +517,11 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
 hn_status hn_mg_time_kernel(hn_mg* mg, int op, int level, int reps, double* avg_ms, double* bytes) {
   clear_error();
   if (!mg || !avg_ms || reps < 1) return set_error(HN_ERR_ARG, "bad arguments");
-  if (op != HN_OP_SPMV && op != HN_OP_DEFECT && op != HN_OP_JACOBI)
-    return set_error(HN_ERR_ARG, "op must be SPMV, DEFECT or JACOBI");
+  if (op != HN_OP_SPMV && op != HN_OP_DEFECT && op != HN_OP_JACOBI && op != HN_OP_RESTRICT &&
+      op != HN_OP_PROLONG_ADD)
+    return set_error(HN_ERR_ARG, "op must be SPMV, DEFECT, JACOBI, RESTRICT or PROLONG_ADD");
+  if (level <= mg->coarse && (op == HN_OP_RESTRICT || op == HN_OP_PROLONG_ADD))
+    return set_error(HN_ERR_ARG, "transfers need a coarser level");
   if (level < mg->coarse || level > mg->L) return set_error(HN_ERR_ARG, "level out of range");
   HN_TRY(ensure_solo(mg));
   Engine& e = *mg->solo;
@@ -539,8 +542,12 @@ hn_status hn_mg_time_kernel(hn_mg* mg, int op, int level, int reps, double* avg_
   if (bytes) {
     const int prec = mg->prm.prec;
     const double vb = prec == P64 ? 8 : 4, bb = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
+    // restriction / prolongation per fine node: read r (1) + write coarse (1/4); read coarse
+    // (1/4) + read and write x (2)
     const double per = op == HN_OP_SPMV ? 9 * bb + 2 * vb
                      : op == HN_OP_DEFECT ? 9 * bb + 3 * vb
+                     : op == HN_OP_RESTRICT ? 1.25 * vb
+                     : op == HN_OP_PROLONG_ADD ? 2.25 * vb
                      : 9 * bb + 3 * vb + (prec == P64 ? 8 : 0);
     *bytes = per * (double)N_of(level);
   }

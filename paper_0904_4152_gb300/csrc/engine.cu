@@ -356,6 +356,8 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   take(sizeof(double) * (size_t)std::max<long long>(fine_cap, 1));
   take(sizeof(double) * (size_t)std::max<long long>(fine_cap, 1));
   take(sizeof(unsigned));
+  take(sizeof(unsigned) * 4);
+  take(sizeof(unsigned long long));
   bytes += 256;
   HN_CUDA(cudaMalloc(&mem_, bytes));
   HN_CUDA(cudaMemsetAsync(mem_, 0, bytes, s_));
@@ -374,6 +376,8 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   double* part = b.take<double>((size_t)std::max<long long>(fine_cap, 1));
   double* part2 = b.take<double>((size_t)std::max<long long>(fine_cap, 1));
   unsigned* iter = b.take<unsigned>(1);
+  dTaken_ = b.take<unsigned>(4);
+  dLaunches_ = b.take<unsigned long long>(1);
   HN_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&hActive_), sizeof(unsigned), cudaHostAllocMapped));
   *hActive_ = 0;
   unsigned* dActive = nullptr;
@@ -474,6 +478,10 @@ hn_status Engine::start(const std::vector<int>& slots, const std::vector<int>& h
   // relies on per-problem caps; its limit is set out of reach)
   HN_CUDA(cudaMemsetAsync(E_.iter, 0, sizeof(unsigned), s_));
   HN_CUDA(cudaMemsetAsync(dErr_, 0, sizeof(int), s_));
+  // mirrors of the IF values as the closed-world graph sets them at its launch
+  static const unsigned taken0[4] = {0u, 1u, 0u, 0u};
+  HN_CUDA(cudaMemcpyAsync(dTaken_, taken0, sizeof taken0, cudaMemcpyHostToDevice, s_));
+  HN_CUDA(cudaMemsetAsync(dLaunches_, 0, sizeof(unsigned long long), s_));
   return HN_OK;
 }
 
@@ -535,34 +543,94 @@ hn_status Engine::mark(cudaStream_t s, int cls, int level, bool begin) {
   return HN_OK;
 }
 
-#define HN_LAUNCH(cls, level, call)        \
-  do {                                     \
-    HN_TRY(mark(s, cls, level, true));     \
-    HN_CUDA(call);                         \
-    ++counting_;                           \
-    HN_TRY(mark(s, cls, level, false));    \
+// A launch right after an IF node, or first in an IF body, has no kernel before it to overlap
+// with: it goes without programmatic dependent launch.
+#define HN_LAUNCH(cls, level, call)                 \
+  do {                                              \
+    HN_TRY(mark(s, cls, level, true));              \
+    const int pdl_saved = E_.pdl;                   \
+    if (pdlBarrier_) E_.pdl = 0;                    \
+    const cudaError_t launch_err = (call);          \
+    E_.pdl = pdl_saved;                             \
+    pdlBarrier_ = false;                            \
+    HN_CUDA(launch_err);                            \
+    ++counting_;                                    \
+    HN_TRY(mark(s, cls, level, false));             \
   } while (0)
-#define HN_LAUNCH0(call) \
-  do {                   \
-    HN_CUDA(call);       \
-    ++counting_;         \
+#define HN_LAUNCH0(call)                            \
+  do {                                              \
+    const int pdl_saved = E_.pdl;                   \
+    if (pdlBarrier_) E_.pdl = 0;                    \
+    const cudaError_t launch_err = (call);          \
+    E_.pdl = pdl_saved;                             \
+    pdlBarrier_ = false;                            \
+    HN_CUDA(launch_err);                            \
+    ++counting_;                                    \
   } while (0)
 
-hn_status Engine::issue_vcycle(cudaStream_t s, int want) {
+hn_status Engine::open_if(cudaStream_t& s, int which) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  HN_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &ed, &nd));
+  if (cst != cudaStreamCaptureStatusActive) return set_error(HN_ERR_STATE, "IF node outside a capture");
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hCond_[which];
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  HN_CUDA(cudaGraphAddNode(&node, g, deps, ed, nd, &cp));
+  HN_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  HN_CUDA(cudaStreamBeginCaptureToGraph(aux_, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  s = aux_;
+  pdlBarrier_ = true;
+  return HN_OK;
+}
+
+hn_status Engine::close_if(cudaStream_t& s, cudaStream_t outer) {
+  cudaGraph_t body = nullptr;
+  HN_CUDA(cudaStreamEndCapture(aux_, &body));
+  s = outer;
+  pdlBarrier_ = true;
+  return HN_OK;
+}
+
+hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
   const int c = prm_.coarse, pre = prm_.pre, post = prm_.post;
   const int T = std::max(tune_.tail_level, c);
+  cudaStream_t s = s0;
+  bool opened = false;
+  int c0 = 0;
+  // inside the closed-world loop the rest of the cycle after the first lagged check is an IF body
+  auto after_check = [&]() -> hn_status {
+    if (!condCapture_ || opened) return HN_OK;
+    HN_TRY(open_if(s, 0));
+    opened = true;
+    c0 = counting_;
+    return HN_OK;
+  };
   for (int l = Lmax_; l > T; --l) {
     const bool top = topMaskAll_ || ((topMask_ >> l) & 1u);   // a finest level: lagged check
     if (pre >= 2) {
       HN_LAUNCH(KC_JACOBI_FIRST, l, launch_pre12(E_, lists_[l], l, want, grid_[l], s));
-      if (top) HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
+      if (top) {
+        HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
+        HN_TRY(after_check());
+      }
       if (!pre_fuses(prm_.prec) || top)
         HN_LAUNCH(KC_JACOBI, l, launch_pre2b(E_, lists_[l], l, want, grid_[l], s));
       for (int sw = 3; sw <= pre; ++sw)
         HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (sw - 1) & 1, 0, grid_[l], s));
     } else {
       HN_LAUNCH(KC_JACOBI_FIRST, l, launch_jacobi(E_, lists_[l], l, want, 0, 1, grid_[l], s));
-      if (top) HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
+      if (top) {
+        HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
+        HN_TRY(after_check());
+      }
     }
     HN_LAUNCH(KC_DEFECT, l, launch_defect(E_, lists_[l], l, want, pre & 1, grid_[l], s));
     HN_LAUNCH(KC_RESTRICT, l, launch_restrict(E_, lists_[l - 1], l, want, grid_[l - 1], s));
@@ -572,6 +640,10 @@ hn_status Engine::issue_vcycle(cudaStream_t s, int want) {
     HN_LAUNCH(KC_PROLONG, l, launch_prolong(E_, lists_[l], l, want, pre & 1, grid_[l], s));
     for (int sw = 1; sw <= post; ++sw)
       HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (pre + sw - 1) & 1, 0, grid_[l], s));
+  }
+  if (opened) {
+    E_.prm.cond.n_cycle = (unsigned)(counting_ - c0);
+    HN_TRY(close_if(s, s0));
   }
   return HN_OK;
 }
@@ -584,15 +656,33 @@ hn_status Engine::issue_init(cudaStream_t s, cudaGraphConditionalHandle h, int u
   return HN_OK;
 }
 
-hn_status Engine::issue_iteration(cudaStream_t s, cudaGraphConditionalHandle h, int use_h) {
+hn_status Engine::issue_iteration(cudaStream_t s0, cudaGraphConditionalHandle h, int use_h) {
+  cudaStream_t s = s0;
+  const int start = counting_;
   if (prm_.prec == P64) {
     HN_TRY(issue_vcycle(s, PH_CYCLE));
   } else {
+    if (condCapture_) HN_TRY(open_if(s, 1));
+    int c0 = counting_;
     HN_LAUNCH(KC_OUTER_DEFECT, -1, launch_outer_defect(E_, fine_, fineGrid_, s));
     HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_OUTER, s));
+    if (condCapture_) {
+      E_.prm.cond.n_outer = (unsigned)(counting_ - c0);
+      HN_TRY(close_if(s, s0));
+    }
     HN_TRY(issue_vcycle(s, PH_INNER));
+    if (condCapture_) HN_TRY(open_if(s, 2));
+    c0 = counting_;
     HN_LAUNCH(KC_UPDATE, -1, launch_update(E_, fine_, fineGrid_, s));
     HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_POST, s));
+    if (condCapture_) {
+      E_.prm.cond.n_update = (unsigned)(counting_ - c0);
+      HN_TRY(close_if(s, s0));
+    }
+  }
+  if (condCapture_) {
+    const CondDev& cd = E_.prm.cond;
+    E_.prm.cond.n_base = (unsigned)(counting_ + 1 - start) - cd.n_cycle - cd.n_outer - cd.n_update;
   }
   HN_LAUNCH0(launch_summary(E_, h, use_h, 1, s));
   return HN_OK;
@@ -636,39 +726,97 @@ hn_status Engine::capture_graphs() {
     cudaGraphDestroy(g);
     HN_CUDA(e);
   }
-  // closed-world solve: init, then while (any problem running) { iteration }
+  // closed-world solve: init, then while (any problem running) { iteration }, with IF nodes
+  // that skip the parts of an iteration no problem is in; the flat loop if those do not build
   if (!profiling_) {
-    cudaGraph_t main;
-    HN_CUDA(cudaGraphCreate(&main, 0));
-    struct GraphGuard { cudaGraph_t g; ~GraphGuard() { cudaGraphDestroy(g); } } gg{main};
-    cudaGraphConditionalHandle h;
-    HN_CUDA(cudaGraphConditionalHandleCreate(&h, main, 1, cudaGraphCondAssignDefault));
-    cudaGraph_t init;
-    HN_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    hn_status st = issue_init(cs, none, 0);
-    cudaError_t e = cudaStreamEndCapture(cs, &init);
-    HN_TRY(st);
-    HN_CUDA(e);
-    cudaGraphNode_t nInit;
-    e = cudaGraphAddChildGraphNode(&nInit, main, nullptr, 0, init);
-    cudaGraphDestroy(init);
-    HN_CUDA(e);
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t nCond;
-    HN_CUDA(cudaGraphAddNode(&nCond, main, &nInit, nullptr, 1, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    HN_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    st = issue_iteration(cs, h, 1);
-    e = cudaStreamEndCapture(cs, &body);
-    HN_TRY(st);
-    HN_CUDA(e);
-    HN_CUDA(cudaGraphInstantiate(&gSolve_, main, 0));
+    hn_status st = capture_solve(true);
+    if (st != HN_OK) {
+      cudaGetLastError();
+      HN_TRY(capture_solve(false));
+    }
   }
   graphsValid_ = true;
+  return HN_OK;
+}
+
+hn_status Engine::capture_solve(bool cond) {
+  cudaStream_t cs;
+  HN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  HN_CUDA(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
+  struct Guard {
+    Engine* e;
+    cudaStream_t cs;
+    cudaGraph_t main = nullptr;
+    ~Guard() {
+      for (cudaStream_t q : {cs, e->aux_}) {
+        cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(q, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+          cudaGraph_t g = nullptr;
+          if (cudaStreamEndCapture(q, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+        }
+        cudaStreamDestroy(q);
+      }
+      e->aux_ = nullptr;
+      e->condCapture_ = false;
+      e->pdlBarrier_ = false;
+      e->E_.prm.cond = CondDev{};
+      if (main) cudaGraphDestroy(main);
+    }
+  } guard{this, cs};
+  HN_CUDA(cudaGraphCreate(&guard.main, 0));
+  cudaGraph_t main = guard.main;
+  const cudaGraphConditionalHandle none = 0;
+  cudaGraphConditionalHandle h;
+  HN_CUDA(cudaGraphConditionalHandleCreate(&h, main, 1, cudaGraphCondAssignDefault));
+  CondDev cd{};
+  if (cond) {
+    // IF handles: the cycle's rest (only when a lagged check precedes it), outer defect and
+    // update (defect correction); the outer defect runs in the first iteration
+    const int T = std::max(tune_.tail_level, prm_.coarse);
+    if (Lmax_ > T) cd.mask |= 1u;
+    if (prm_.prec != P64) cd.mask |= 6u;
+    const unsigned defaults[3] = {0u, 1u, 0u};
+    for (int w = 0; w < 3; ++w)
+      if ((cd.mask >> w) & 1u)
+        HN_CUDA(cudaGraphConditionalHandleCreate(&hCond_[w], main, defaults[w], cudaGraphCondAssignDefault));
+    cd.h_cycle = hCond_[0];
+    cd.h_outer = hCond_[1];
+    cd.h_update = hCond_[2];
+    cd.taken = dTaken_;
+    cd.launches = dLaunches_;
+  }
+  cudaGraph_t init;
+  HN_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  hn_status st = issue_init(cs, none, 0);
+  cudaError_t e = cudaStreamEndCapture(cs, &init);
+  HN_TRY(st);
+  HN_CUDA(e);
+  cudaGraphNode_t nInit;
+  e = cudaGraphAddChildGraphNode(&nInit, main, nullptr, 0, init);
+  cudaGraphDestroy(init);
+  HN_CUDA(e);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t nCond;
+  HN_CUDA(cudaGraphAddNode(&nCond, main, &nInit, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  HN_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  E_.prm.cond = cd;
+  condCapture_ = cd.mask != 0;
+  counting_ = 0;
+  st = issue_iteration(cs, h, 1);
+  condCapture_ = false;
+  e = cudaStreamEndCapture(cs, &body);
+  HN_TRY(st);
+  HN_CUDA(e);
+  cudaGraphExec_t exec = nullptr;
+  HN_CUDA(cudaGraphInstantiate(&exec, main, 0));
+  if (gSolve_) cudaGraphExecDestroy(gSolve_);
+  gSolve_ = exec;
+  condUsed_ = cd.mask != 0;
   return HN_OK;
 }
 
@@ -688,10 +836,14 @@ hn_status Engine::run_to_completion() {
   }
   HN_CUDA(cudaGraphLaunch(gSolve_, s_));
   unsigned iters = 0;
+  unsigned long long body = 0;
   HN_CUDA(cudaMemcpyAsync(&iters, E_.iter, sizeof iters, cudaMemcpyDeviceToHost, s_));
+  HN_CUDA(cudaMemcpyAsync(&body, dLaunches_, sizeof body, cudaMemcpyDeviceToHost, s_));
   HN_CUDA(cudaStreamSynchronize(s_));
-  // the init graph's summary also counts one; each body iteration runs iterLaunches_ kernels
-  lastLaunches_ = initLaunches_ + (long long)(iters > 0 ? iters - 1 : 0) * iterLaunches_;
+  // the init graph's summary also counts one iteration; with IF nodes the loop counts the
+  // kernels it ran, otherwise each body iteration runs iterLaunches_ kernels
+  lastLaunches_ = initLaunches_ + (condUsed_ ? (long long)body
+                                             : (long long)(iters > 0 ? iters - 1 : 0) * iterLaunches_);
   return HN_OK;
 }
 

@@ -150,6 +150,10 @@ class Engine {
   hn_status issue_init(cudaStream_t s, cudaGraphConditionalHandle h, int use_h);
   hn_status issue_iteration(cudaStream_t s, cudaGraphConditionalHandle h, int use_h);
   hn_status issue_vcycle(cudaStream_t s, int want);
+  // IF node at the current end of stream s's capture; further launches go to its body (on aux_)
+  hn_status open_if(cudaStream_t& s, int which);
+  hn_status close_if(cudaStream_t& s, cudaStream_t outer);
+  hn_status capture_solve(bool cond);
   int grid_for(long long tiles) const;
   hn_status mark(cudaStream_t s, int cls, int level, bool begin);
   void destroy_graphs();
@@ -186,6 +190,12 @@ class Engine {
   unsigned topMask_ = 0;
   bool topMaskAll_ = false;
   long long lastLaunches_ = 0;
+  // IF nodes inside the closed-world loop (see CondDev)
+  cudaStream_t aux_ = nullptr;
+  bool condCapture_ = false, condUsed_ = false, pdlBarrier_ = false;
+  cudaGraphConditionalHandle hCond_[3] = {};
+  unsigned* dTaken_ = nullptr;
+  unsigned long long* dLaunches_ = nullptr;
   // profiling
   bool profiling_ = false;
   struct Mark { cudaEvent_t b, e; int cls, level; long long bytes; };

@@ -84,10 +84,24 @@ struct ProbState {
 };
 
 // solver parameters shared by every problem of an engine
+// IF nodes of the device-side solve loop (closed-world graph only).  One iteration of the loop
+// runs [IF outer: outer defect, control] [top-level first smoothing step, check] [IF cycle: rest
+// of the V cycle] [IF update: update, control] summary.  The kernel that takes a phase decision
+// sets the matching value (and its mirror in `taken`); the summary counts the launches the
+// iteration ran and resets the values for the next one.
+struct CondDev {
+  unsigned long long h_cycle = 0, h_outer = 0, h_update = 0;   // cudaGraphConditionalHandle
+  unsigned* taken = nullptr;              // [0] cycle, [1] outer, [2] update
+  unsigned long long* launches = nullptr; // kernels launched by the loop's iterations
+  unsigned n_base = 0, n_cycle = 0, n_outer = 0, n_update = 0;
+  unsigned mask = 0;                      // handles that exist: bit w for taken[w]
+};
+
 struct Params {
   int prec, pre, post, coarse;
   int max_cycles, max_outer, inner_max, pad;
   double omega, tol, inner_tol;
+  CondDev cond;
 };
 
 // tile work list of one level: items[g] = (problem, tile of that problem's level).  The count is

@@ -29,9 +29,15 @@ constexpr unsigned kFull = 0xffffffffu;
 // Programmatic dependent launch: a kernel lets its successor in the stream launch as soon as all
 // of its blocks are running (launch_dependents), and waits for its predecessor's completion and
 // memory before touching any data (wait).  Both are no-ops for a normal launch.
-__device__ __forceinline__ void pdl_start() {
+__device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_start() {
+  pdl_trigger();
+  pdl_wait();
 }
 
 // -------------------------------------------------------------------- precision policies
@@ -216,7 +222,8 @@ __device__ double block_sum256(double v, double* sh) {
 // problem's norm does not depend on which kernel or batch computed it.  Valid in thread 0.
 __device__ double problem_partial_sum(const double* part, int ntiles, double* sh) {
   double t = 0.0;
-  for (int q = threadIdx.x; q < ntiles; q += blockDim.x) t += __ldcg(part + q);
+  if (threadIdx.x < 256)                      // larger blocks: the other threads add +0.0
+    for (int q = threadIdx.x; q < ntiles; q += 256) t += __ldcg(part + q);
   return block_sum256(t, sh);
 }
 
@@ -230,6 +237,12 @@ __host__ __device__ inline int fine_tiles(int L) {
 // iterate in buffer 0 is the result) or at the cycle cap; inner cycles of the defect correction
 // stop at the inner tolerance or the inner caps (the correction goes to the update).  Otherwise
 // the cycle proceeds and is counted.
+__device__ __forceinline__ void cond_set(const CondDev& c, int which, unsigned v) {
+  if (!((c.mask >> which) & 1u)) return;
+  cudaGraphSetConditional(which == 0 ? c.h_cycle : (which == 1 ? c.h_outer : c.h_update), v);
+  c.taken[which] = v;
+}
+
 __device__ void pre_check(ProbState& st, const Params& prm, double nrm) {
   if (!isfinite(nrm)) { st.status = HN_ERR_NONFINITE; st.phase = PH_DONE; return; }
   if (st.phase == PH_CYCLE) {
@@ -241,9 +254,10 @@ __device__ void pre_check(ProbState& st, const Params& prm, double nrm) {
   } else {
     st.inner_res = nrm;
     if (nrm <= prm.inner_tol * st.inner_ref || st.inner_k >= prm.inner_max ||
-        st.inner_cycles >= prm.max_cycles)
+        st.inner_cycles >= prm.max_cycles) {
       st.phase = PH_UPDATE;
-    else { st.inner_k += 1; st.inner_cycles += 1; st.cycles += 1; }
+      cond_set(prm.cond, 2, 1u);
+    } else { st.inner_k += 1; st.inner_cycles += 1; st.cycles += 1; }
   }
 }
 
@@ -399,30 +413,29 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
 // 1/2, 1/4 x 1/4, 1/2, 1/4 (products by powers of two are exact).
 template <class V, int LK>
 __device__ __forceinline__ void restrict_tile(const LevelDev& f, const LevelDev& c, long long i0) {
-  const long long nc = c.n, nf = f.n, Nc = nc * nc;
+  const int nc = c.n, nf = f.n, Nc = nc * nc;
   const V* r = static_cast<const V*>(f.r);
+  // coarse coordinates of the lane's first node, then step along the row (one wrap at most)
+  int J = (int)((unsigned)i0 / (unsigned)nc), I = (int)i0 - J * nc;
   V out[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const long long ci = i0 + j;
     V v = V(0);
-    if (ci < Nc) {
-      const long long J = ci / nc, I = ci - J * nc;
-      if (I > 0 && J > 0 && I < nc - 1 && J < nc - 1) {
-        const long long fc = 2 * J * nf + 2 * I;
-        const V q = V(0.25), h = V(0.5);
-        v = q * ld1<LK>(r + fc - nf - 1);
-        v = fma(h, ld1<LK>(r + fc - nf), v);
-        v = fma(q, ld1<LK>(r + fc - nf + 1), v);
-        v = fma(h, ld1<LK>(r + fc - 1), v);
-        v = v + ld1<LK>(r + fc);
-        v = fma(h, ld1<LK>(r + fc + 1), v);
-        v = fma(q, ld1<LK>(r + fc + nf - 1), v);
-        v = fma(h, ld1<LK>(r + fc + nf), v);
-        v = fma(q, ld1<LK>(r + fc + nf + 1), v);
-      }
+    if ((int)i0 + j < Nc && I > 0 && J > 0 && I < nc - 1 && J < nc - 1) {
+      const long long fc = 2LL * J * nf + 2 * I;
+      const V q = V(0.25), h = V(0.5);
+      v = q * ld1<LK>(r + fc - nf - 1);
+      v = fma(h, ld1<LK>(r + fc - nf), v);
+      v = fma(q, ld1<LK>(r + fc - nf + 1), v);
+      v = fma(h, ld1<LK>(r + fc - 1), v);
+      v = v + ld1<LK>(r + fc);
+      v = fma(h, ld1<LK>(r + fc + 1), v);
+      v = fma(q, ld1<LK>(r + fc + nf - 1), v);
+      v = fma(h, ld1<LK>(r + fc + nf), v);
+      v = fma(q, ld1<LK>(r + fc + nf + 1), v);
     }
     out[j] = v;
+    if (++I == nc) { I = 0; ++J; }
   }
   st4(static_cast<V*>(c.rhs) + i0, out);
 }
@@ -432,32 +445,34 @@ __device__ __forceinline__ void restrict_tile(const LevelDev& f, const LevelDev&
 template <class V, int LK>
 __device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& c, int x_sel,
                                              long long i0) {
-  const long long nf = f.n, nc = c.n, Nf = nf * nf;
+  const int nf = f.n, nc = c.n, Nf = nf * nf;
   const V* e = static_cast<const V*>(c.x[0]);
   V* x = static_cast<V*>(f.x[x_sel]);
   V v[4];
   if constexpr (LK == LD_NC) ld4c(x + i0, v);   // read and rewritten by this thread only
   else ld4<LK>(x + i0, v);                      // written earlier in this launch
+  // fine coordinates of the lane's first node, then step along the row (one wrap at most)
+  int iy = (int)((unsigned)i0 / (unsigned)nf), ix = (int)i0 - iy * nf;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const long long fi = i0 + j;
-    if (fi >= Nf) continue;
-    const long long iy = fi / nf, ix = fi - iy * nf;
-    if (ix == 0 || iy == 0 || ix == nf - 1 || iy == nf - 1) continue;
-    const long long cx0 = ix >> 1, cx1 = (ix + 1) >> 1, cy0 = iy >> 1, cy1 = (iy + 1) >> 1;
-    V add;
-    const bool ox = ix & 1, oy = iy & 1;
-    if (!ox && !oy) {
-      add = ld1<LK>(e + cy0 * nc + cx0);
-    } else if (ox && !oy) {
-      add = V(0.5) * (ld1<LK>(e + cy0 * nc + cx0) + ld1<LK>(e + cy0 * nc + cx1));
-    } else if (!ox && oy) {
-      add = V(0.5) * (ld1<LK>(e + cy0 * nc + cx0) + ld1<LK>(e + cy1 * nc + cx0));
-    } else {
-      add = V(0.25) * (((ld1<LK>(e + cy0 * nc + cx0) + ld1<LK>(e + cy0 * nc + cx1)) +
-                        ld1<LK>(e + cy1 * nc + cx0)) + ld1<LK>(e + cy1 * nc + cx1));
+    if ((int)i0 + j < Nf && ix > 0 && iy > 0 && ix < nf - 1 && iy < nf - 1) {
+      const int cx0 = ix >> 1, cx1 = (ix + 1) >> 1, cy0 = iy >> 1, cy1 = (iy + 1) >> 1;
+      const V* e0 = e + (long long)cy0 * nc;
+      const V* e1 = e + (long long)cy1 * nc;
+      V add;
+      const bool ox = ix & 1, oy = iy & 1;
+      if (!ox && !oy) {
+        add = ld1<LK>(e0 + cx0);
+      } else if (ox && !oy) {
+        add = V(0.5) * (ld1<LK>(e0 + cx0) + ld1<LK>(e0 + cx1));
+      } else if (!ox && oy) {
+        add = V(0.5) * (ld1<LK>(e0 + cx0) + ld1<LK>(e1 + cx0));
+      } else {
+        add = V(0.25) * (((ld1<LK>(e0 + cx0) + ld1<LK>(e0 + cx1)) + ld1<LK>(e1 + cx0)) + ld1<LK>(e1 + cx1));
+      }
+      v[j] = v[j] + add;
     }
-    v[j] = v[j] + add;
+    if (++ix == nf) { ix = 0; ++iy; }
   }
   st4(x + i0, v);
 }
@@ -527,9 +542,20 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 
 // ------------------------------------------------------------------ per-level kernels
 // One warp-tile per loop trip over the work list.  level < 0: each problem's own finest level.
+// Resident blocks per SM asked of the register allocator.  The streaming modes keep 5 blocks
+// (40 warps) of FP32 (FP16 for SpMV/defect) loads in flight, enough to saturate HBM; the fused
+// pre-smoothing and check modes run once per cycle and get more registers per thread.
+template <class Pol, int MODE> constexpr int band_min_blocks() {
+  if (MODE == M_CHECK || MODE == M_PRE12) return Pol::prec == P64 ? 2 : 3;
+  if (Pol::prec == P32) return 5;
+  if (Pol::prec == P16) return (MODE == M_SPMV || MODE == M_DEFECT) ? 5 : 4;
+  return 4;
+}
+
 template <class Pol, int MODE>
-__global__ void __launch_bounds__(256) k_band(EngineDev E, TileList tl, int level, int want,
-                                              int in_sel) {
+__global__ void __launch_bounds__(256, band_min_blocks<Pol, MODE>()) k_band(EngineDev E, TileList tl,
+                                                                     int level, int want,
+                                                                     int in_sel) {
   pdl_start();
   using A = typename Pol::A;
   const int lane = threadIdx.x & 31;
@@ -784,6 +810,224 @@ __device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* 
   if (threadIdx.x == 0) s = t;
 }
 
+// ---------------------------------------------- node-wise steps on shared-memory levels
+// One thread per node on the small levels that the fused tail holds in shared memory: at most a
+// few thousand nodes, where one warp per 128-node tile would leave most of the block idle.  Each
+// function computes exactly the arithmetic of the corresponding tile step for that node (same
+// operands, same order of operations), so the results do not depend on which path ran.
+
+// acc = sum_k a_k[i] x[i + off_k] in band order (FP16: the row-sum form), dg = the diagonal
+template <class Pol>
+__device__ __forceinline__ void stencil_node(const LevelDev& d, const typename Pol::V* x, int i,
+                                             typename Pol::A& acc, typename Pol::A& dg) {
+  using A = typename Pol::A;
+  using B = typename Pol::B;
+  const int n = d.n;
+  if constexpr (Pol::prec == P16) {
+    const float xi = x[i];
+    const float rho = d.scale[4] * __half2float(static_cast<const B*>(d.band[4])[i]);
+    acc = rho * xi;
+    dg = rho;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      if (k == 4) continue;
+      const int off = (k / 3 - 1) * n + (k % 3 - 1);
+      const float b = d.scale[k] * __half2float(static_cast<const B*>(d.band[k])[i]);
+      acc = fmaf(b, x[i + off] - xi, acc);
+      dg -= b;
+    }
+  } else {
+    acc = A(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int off = (k / 3 - 1) * n + (k % 3 - 1);
+      const A b = static_cast<const B*>(d.band[k])[i];
+      acc = fma(b, A(x[i + off]), acc);
+      if (k == 4) dg = b;
+    }
+  }
+}
+
+// omega / diag at node i (FP64: the stored array)
+template <class Pol>
+__device__ __forceinline__ typename Pol::A wd_node(const LevelDev& d, int i, typename Pol::A omega,
+                                                   typename Pol::A dg) {
+  if constexpr (Pol::prec == P64) return d.wdinv[i];
+  else return omega / dg;
+}
+
+// diagonal of the row-sum form without x
+__device__ __forceinline__ float diag_rowsum_node(const LevelDev& d, int i) {
+  float dg = d.scale[4] * __half2float(static_cast<const __half*>(d.band[4])[i]);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    if (k == 4) continue;
+    dg -= d.scale[k] * __half2float(static_cast<const __half*>(d.band[k])[i]);
+  }
+  return dg;
+}
+
+template <class Pol, int MODE>
+__device__ __forceinline__ void band_node(const LevelDev& d, int i, bool zg, int in_sel,
+                                          typename Pol::A omega) {
+  using A = typename Pol::A;
+  using V = typename Pol::V;
+  const V* rhs = static_cast<const V*>(d.rhs);
+  if constexpr (MODE == M_PRE2B) {
+    if (zg && fuses_pre<Pol>()) return;
+  }
+  if constexpr (MODE == M_JACOBI_FIRST || MODE == M_PRE12) {
+    if (zg && (MODE == M_JACOBI_FIRST || !fuses_pre<Pol>())) {   // x = 0: x' = omega D^-1 rhs
+      V out;
+      if constexpr (Pol::prec == P64) out = d.wdinv[i] * rhs[i];
+      else {
+        A dg;
+        if constexpr (Pol::prec == P16) dg = diag_rowsum_node(d, i);
+        else dg = static_cast<const typename Pol::B*>(d.band[4])[i];
+        out = (omega / dg) * A(rhs[i]);
+      }
+      static_cast<V*>(d.x[1])[i] = out;
+      return;
+    }
+    if constexpr (MODE == M_PRE12 && fuses_pre<Pol>()) {
+      if (zg) {                                   // two steps from zero in one pass
+        const int n = d.n;
+        A acc = A(0), dg = A(0);
+        V x1c = V(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const int j = i + (k / 3 - 1) * n + (k % 3 - 1);
+          V x1;
+          if constexpr (Pol::prec == P64) x1 = d.wdinv[j] * rhs[j];
+          else {
+            const V dw = static_cast<const typename Pol::B*>(d.band[4])[j];
+            x1 = dw != V(0) ? (omega / dw) * rhs[j] : V(0);
+          }
+          const A b = static_cast<const typename Pol::B*>(d.band[k])[i];
+          acc = fma(b, A(x1), acc);
+          if (k == 4) { dg = b; x1c = x1; }
+        }
+        const A wd = wd_node<Pol>(d, i, omega, dg);
+        static_cast<V*>(d.x[0])[i] = fma(wd, A(rhs[i]) - acc, A(x1c));
+        return;
+      }
+    }
+  }
+  int src = in_sel, dst = 1 - in_sel;
+  if constexpr (MODE == M_JACOBI_FIRST || MODE == M_PRE12) { src = 0; dst = 1; }
+  if constexpr (MODE == M_PRE2B) { src = 1; dst = 0; }
+  const V* xin = static_cast<const V*>(d.x[src]);
+  A acc, dg;
+  stencil_node<Pol>(d, xin, i, acc, dg);
+  if constexpr (MODE == M_DEFECT) {
+    static_cast<V*>(d.r)[i] = V(A(rhs[i]) - acc);
+  } else {                                        // a Jacobi step src -> dst
+    const A wd = wd_node<Pol>(d, i, omega, dg);
+    static_cast<V*>(d.x[dst])[i] = fma(wd, A(rhs[i]) - acc, A(xin[i]));
+  }
+}
+
+// full-weighting restriction onto coarse node i (the tile step's formula)
+template <class V>
+__device__ __forceinline__ void restrict_node(const LevelDev& f, const LevelDev& c, int i) {
+  const int nc = c.n, nf = f.n;
+  const int J = i / nc, I = i - J * nc;
+  V v = V(0);
+  if (i < nc * nc && I > 0 && J > 0 && I < nc - 1 && J < nc - 1) {
+    const V* r = static_cast<const V*>(f.r) + (2 * J * nf + 2 * I);
+    const V q = V(0.25), h = V(0.5);
+    v = q * r[-nf - 1];
+    v = fma(h, r[-nf], v);
+    v = fma(q, r[-nf + 1], v);
+    v = fma(h, r[-1], v);
+    v = v + r[0];
+    v = fma(h, r[1], v);
+    v = fma(q, r[nf - 1], v);
+    v = fma(h, r[nf], v);
+    v = fma(q, r[nf + 1], v);
+  }
+  static_cast<V*>(c.rhs)[i] = v;
+}
+
+// x_f[x_sel] += P e_c at fine node i (the tile step's formula)
+template <class V>
+__device__ __forceinline__ void prolong_node(const LevelDev& f, const LevelDev& c, int x_sel, int i) {
+  const int nf = f.n, nc = c.n;
+  const int iy = i / nf, ix = i - iy * nf;
+  if (!(i < nf * nf && ix > 0 && iy > 0 && ix < nf - 1 && iy < nf - 1)) return;
+  const V* e = static_cast<const V*>(c.x[0]);
+  const V* e0 = e + (iy >> 1) * nc;
+  const V* e1 = e + ((iy + 1) >> 1) * nc;
+  const int cx0 = ix >> 1, cx1 = (ix + 1) >> 1;
+  V add;
+  const bool ox = ix & 1, oy = iy & 1;
+  if (!ox && !oy) add = e0[cx0];
+  else if (ox && !oy) add = V(0.5) * (e0[cx0] + e0[cx1]);
+  else if (!ox && oy) add = V(0.5) * (e0[cx0] + e1[cx0]);
+  else add = V(0.25) * (((e0[cx0] + e0[cx1]) + e1[cx0]) + e1[cx1]);
+  V* x = static_cast<V*>(f.x[x_sel]);
+  x[i] = x[i] + add;
+}
+
+// Down part of the cycle on shared-memory level l (block-wide, node-wise).  The first smoothing
+// step of a problem's own finest level from a nonzero iterate takes the tile path, which also
+// writes the residual partials of the lagged check; returns false if the problem leaves.
+template <class Pol>
+__device__ bool vcycle_down_smem(const LevelDev& d, const LevelDev& dc, int l, bool zg, int pre,
+                                 typename Pol::A omega, int lane, double* check_part,
+                                 ProbState* st, const Params& prm, int want, double* sh) {
+  const int tid = threadIdx.x, nt = blockDim.x, np = d.pitch;
+  if (check_part) {
+    const int tiles = np / kTile, warp = tid >> 5, nwarp = nt >> 5;
+    for (int t = warp; t < tiles; t += nwarp) {
+      if (pre >= 2)
+        band_tile<Pol, M_PRE12, LD_GEN>(d, 1LL << l, zg, (long long)t * kTile + lane * kLaneNodes,
+                                        lane, 0, omega, check_part + t);
+      else
+        band_tile<Pol, M_JACOBI_FIRST, LD_GEN>(d, 1LL << l, zg, (long long)t * kTile + lane * kLaneNodes,
+                                               lane, 0, omega, check_part + t);
+    }
+    __syncthreads();
+    const double sum = problem_partial_sum(check_part, fine_tiles(l), sh);
+    if (tid == 0) pre_check(*st, prm, sqrt(sum));
+    __syncthreads();
+    if (__ldcg(&st->phase) != want) return false;
+  } else {
+    for (int i = tid; i < np; i += nt) {
+      if (pre >= 2) band_node<Pol, M_PRE12>(d, i, zg, 0, omega);
+      else band_node<Pol, M_JACOBI_FIRST>(d, i, zg, 0, omega);
+    }
+    __syncthreads();
+  }
+  if (pre >= 2) {
+    if (!(zg && fuses_pre<Pol>())) {
+      for (int i = tid; i < np; i += nt) band_node<Pol, M_PRE2B>(d, i, zg, 0, omega);
+      __syncthreads();
+    }
+    for (int s = 3; s <= pre; ++s) {
+      for (int i = tid; i < np; i += nt) band_node<Pol, M_JACOBI>(d, i, zg, (s - 1) & 1, omega);
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < np; i += nt) band_node<Pol, M_DEFECT>(d, i, zg, pre & 1, omega);
+  __syncthreads();
+  for (int i = tid; i < dc.pitch; i += nt) restrict_node<typename Pol::V>(d, dc, i);
+  __syncthreads();
+  return true;
+}
+
+template <class Pol>
+__device__ void vcycle_up_smem(const LevelDev& d, const LevelDev& dc, int pre, int post,
+                               typename Pol::A omega) {
+  const int tid = threadIdx.x, nt = blockDim.x, np = d.pitch;
+  for (int i = tid; i < np; i += nt) prolong_node<typename Pol::V>(d, dc, pre & 1, i);
+  __syncthreads();
+  for (int s = 1; s <= post; ++s) {
+    for (int i = tid; i < np; i += nt) band_node<Pol, M_JACOBI>(d, i, false, (pre + s - 1) & 1, omega);
+    __syncthreads();
+  }
+}
+
 // Pre-smoothing, defect and restriction of level l.  check_part (top level with a nonzero
 // iterate): the first smoothing step also writes the residual partials, block 0 reduces them and
 // takes the lagged convergence decision; returns false if the problem leaves the cycle.
@@ -854,9 +1098,10 @@ __device__ __forceinline__ void vcycle_up_level(const LevelDev& d, const LevelDe
   }
 }
 
+constexpr int kTailThreads = 512;
+
 template <class Pol>
-__global__ void __launch_bounds__(256) k_tail(EngineDev E, int T, int S, int want) {
-  pdl_start();
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, int S, int want) {
   using A = typename Pol::A;
   using V = typename Pol::V;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -864,52 +1109,70 @@ __global__ void __launch_bounds__(256) k_tail(EngineDev E, int T, int S, int wan
   __shared__ LevelDev sd[kMaxLevel + 1];       // shared-memory copies of levels coarse..S
   __shared__ double sol[kMaxCoarseM];
   __shared__ double sh[32];
+  __shared__ const double* s_cinv;
   cg::cluster_group cl = cg::this_cluster();
   const int csize = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int p = blockIdx.x / csize;
+  pdl_trigger();
   if (p >= E.nprob) return;
-  const ProbState& st = E.S[p];
-  if (st.phase != want) return;
+  // constant data before the wait for the preceding launch: the level descriptors and, in block 0,
+  // the bands of the shared-memory levels (asynchronous copies, completed before first use).
+  // Descriptors change only between launches (host copies); an empty slot's is all zero.
   const ProblemDev& P = E.P[p];
+  if (P.L < HN_MIN_LEVEL) return;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const int top = P.L < T ? P.L : T, c = P.coarse;
   const int Ss = S < top ? S : top;
-  const int pre = E.prm.pre, post = E.prm.post;
-  const A omega = A(E.prm.omega);
-  const bool zero_top = st.zero_top;
-  ProbState* stw = E.S + p;
-  double* check_part = E.partial + E.fine_off[p];   // used on the problem's own finest level
-  {   // descriptors of levels coarse..top into shared memory
+  const int m = P.m;
+  {
     const int words = (int)(sizeof(LevelDev) / 4) * (top - c + 1);
     const unsigned* src = reinterpret_cast<const unsigned*>(&P.lev[c]);
     unsigned* dst = reinterpret_cast<unsigned*>(&gd[c]);
     for (int q = threadIdx.x; q < words; q += blockDim.x) dst[q] = src[q];
     __syncthreads();
   }
+  if (rank == 0) {
+    long long off = 0;
+    for (int l = c; l <= Ss; ++l) smem_level_setup<Pol>(gd[l], sd[l], smem, &off, l);
+    // the coarse inverse (m*m doubles) is staged in shared memory when it is small
+    if ((long long)m * m * 8 <= kCinvSmemMax) {
+      double* dst = reinterpret_cast<double*>(smem + off);
+      for (int q = threadIdx.x; q < m * m / 2; q += blockDim.x)
+        cp_async16(reinterpret_cast<double2*>(dst) + q, reinterpret_cast<const double2*>(P.cinv) + q);
+      if ((m * m) & 1) {
+        if (threadIdx.x == 0) dst[m * m - 1] = __ldg(P.cinv + m * m - 1);
+      }
+      if (threadIdx.x == 0) s_cinv = dst;
+    } else if (threadIdx.x == 0) {
+      s_cinv = P.cinv;
+    }
+    __syncthreads();                            // shared-memory descriptors published
+  }
+  pdl_wait();
+  const ProbState& st = E.S[p];
+  if (st.phase != want) {
+    if (rank == 0) cp_async_wait();               // no copy outlives the block
+    return;
+  }
+  const int pre = E.prm.pre, post = E.prm.post;
+  const A omega = A(E.prm.omega);
+  const bool zero_top = st.zero_top;
+  ProbState* stw = E.S + p;
+  double* check_part = E.partial + E.fine_off[p];   // used on the problem's own finest level
   // cluster part, down
   const int w0 = rank * wpb + (threadIdx.x >> 5), nw = csize * wpb;
   for (int l = top; l > Ss; --l) {
     const bool chk = (l == P.L) && !zero_top;
     if (!vcycle_down_level<Pol, LD_CG>(gd[l], gd[l - 1], l, (P.L > l) || zero_top, pre, omega, w0, nw,
-                                       lane, true, chk ? check_part : nullptr, stw, E.prm, want, rank, sh))
+                                       lane, true, chk ? check_part : nullptr, stw, E.prm, want, rank, sh)) {
+      if (rank == 0) cp_async_wait();
       return;                                   // converged at the lagged check: cluster-uniform
-  }
-  // block 0: levels coarse..Ss in shared memory
-  if (rank == 0) {
-    long long off = 0;
-    for (int l = c; l <= Ss; ++l) smem_level_setup<Pol>(gd[l], sd[l], smem, &off, l);
-    const int m = P.m;
-    // the coarse inverse (m*m doubles) is staged in shared memory when it is small
-    const bool cinv_smem = (long long)m * m * 8 <= kCinvSmemMax;
-    const double* cinv = P.cinv;
-    if (cinv_smem) {
-      double* dst = reinterpret_cast<double*>(smem + off);
-      for (int q = threadIdx.x; q < m * m; q += blockDim.x) dst[q] = __ldg(P.cinv + q);
-      cinv = dst;
     }
-    __syncthreads();                                          // descriptors published
+  }
+  // block 0: levels coarse..Ss in shared memory, one thread per node
+  if (rank == 0) {
     {   // inputs of level Ss: restricted rhs (or the top rhs), and the iterate if it is nonzero
       const LevelDev& g = gd[Ss];
       const LevelDev& s = sd[Ss];
@@ -922,16 +1185,16 @@ __global__ void __launch_bounds__(256) k_tail(EngineDev E, int T, int S, int wan
       cp_async_wait();
       __syncthreads();
     }
-    const int sw0 = threadIdx.x >> 5;
     bool go = true;
     for (int l = Ss; l > c && go; --l) {
       const bool chk = (l == P.L) && !zero_top;
-      go = vcycle_down_level<Pol, LD_GEN>(sd[l], sd[l - 1], l, (P.L > l) || zero_top, pre, omega, sw0, wpb,
-                                          lane, false, chk ? check_part : nullptr, stw, E.prm, want, 0, sh);
+      go = vcycle_down_smem<Pol>(sd[l], sd[l - 1], l, (P.L > l) || zero_top, pre, omega, lane,
+                                 chk ? check_part : nullptr, stw, E.prm, want, sh);
     }
     if (go && c == P.L && !zero_top) {
       // the problem is the coarsest level alone: its residual check before the exact solve
       const LevelDev& d = sd[c];
+      const int sw0 = threadIdx.x >> 5;
       for (int t = sw0; t < d.pitch / kTile; t += wpb)
         band_tile<Pol, M_CHECK, LD_GEN>(d, 1LL << c, false, (long long)t * kTile + lane * kLaneNodes, lane, 0,
                                         omega, check_part + t);
@@ -941,38 +1204,36 @@ __global__ void __launch_bounds__(256) k_tail(EngineDev E, int T, int S, int wan
       __syncthreads();
       go = __ldcg(&stw->phase) == want;
     }
-  if (go) {
-    if (threadIdx.x < 32) {
-      // the coarsest level: the exact solve with the FP64 inverse, all in shared memory
+    if (go) {
+      // the coarsest level: the exact solve with the FP64 inverse, one thread per unknown
       const LevelDev& d = sd[c];
       const int n = d.n, ni = n - 2;
       const V* rhs = static_cast<const V*>(d.rhs);
-      for (int u = lane; u < m; u += 32) {
+      const double* cinv = s_cinv;
+      for (int u = threadIdx.x; u < m; u += blockDim.x) {
         const double* row = cinv + u * m;
         double sacc = 0.0;
         for (int v = 0; v < m; ++v) sacc = fma(row[v], double(rhs[(v / ni + 1) * n + (v % ni + 1)]), sacc);
         sol[u] = sacc;
       }
-      __syncwarp();
+      __syncthreads();
       V* x = static_cast<V*>(d.x[0]);
-      for (int q = lane; q < d.pitch; q += 32) {
+      for (int q = threadIdx.x; q < d.pitch; q += blockDim.x) {
         const int iy = q / n, ix = q - iy * n;
         V val = V(0);
         if (q < n * n && ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1) val = V(sol[(iy - 1) * ni + (ix - 1)]);
         x[q] = val;
       }
+      __syncthreads();
+      for (int l = c + 1; l <= Ss; ++l) vcycle_up_smem<Pol>(sd[l], sd[l - 1], pre, post, omega);
+      {   // the iterate of level Ss back to global memory
+        const LevelDev& g = gd[Ss];
+        const LevelDev& s = sd[Ss];
+        const int chunks = (int)(g.pitch * sizeof(V) / 16);
+        for (int q = threadIdx.x; q < chunks; q += blockDim.x)
+          static_cast<uint4*>(g.x[0])[q] = static_cast<const uint4*>(s.x[0])[q];
+      }
     }
-    __syncthreads();
-    for (int l = c + 1; l <= Ss; ++l)
-      vcycle_up_level<Pol, LD_GEN>(sd[l], sd[l - 1], l, pre, post, omega, sw0, wpb, lane, false);
-    {   // the iterate of level Ss back to global memory
-      const LevelDev& g = gd[Ss];
-      const LevelDev& s = sd[Ss];
-      const int chunks = (int)(g.pitch * sizeof(V) / 16);
-      for (int q = threadIdx.x; q < chunks; q += blockDim.x)
-        static_cast<uint4*>(g.x[0])[q] = static_cast<const uint4*>(s.x[0])[q];
-    }
-  }
   }
   cl.sync();
   // cluster part, up
@@ -1101,9 +1362,13 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
   ProbState& st = E.S[p];
   const int ph = st.phase;
   if (kind == CTRL_PRE) {
-    if (!((ph == PH_INNER || ph == PH_CYCLE) && E.P[p].L == level && !st.zero_top)) return;
-    const double sum = problem_partial_sum(E.partial + E.fine_off[p], fine_tiles(level), sh);
-    if (threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
+    if ((ph == PH_INNER || ph == PH_CYCLE) && E.P[p].L == level && !st.zero_top) {
+      const double sum = problem_partial_sum(E.partial + E.fine_off[p], fine_tiles(level), sh);
+      if (threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
+    }
+    // the rest of the V cycle runs if any problem is still in it
+    if (threadIdx.x == 0 && (st.phase == PH_INNER || st.phase == PH_CYCLE))
+      cond_set(E.prm.cond, 0, 1u);
     return;
   }
   const bool mine = (kind == CTRL_INIT && ph == PH_INIT) ||
@@ -1201,33 +1466,43 @@ __global__ void __launch_bounds__(256) k_summary(EngineDev E, cudaGraphCondition
     over = (E.iter && it > E.iter_limit) ? 1u : 0u;
   }
   __syncthreads();
-  double c = 0.0;
+  double c = 0.0, o = 0.0;
   for (int p = threadIdx.x; p < E.nprob; p += blockDim.x) {
     ProbState& st = E.S[p];
     if (st.phase != PH_DONE && over) { st.status = HN_ERR_NOT_CONVERGED; st.phase = PH_DONE; }
     // after an iteration the finest-level iterate of a running cycle is no longer zero
     if (end_of_iteration && (st.phase == PH_INNER || st.phase == PH_CYCLE)) st.zero_top = 0;
     c += st.phase != PH_DONE ? 1.0 : 0.0;
+    o += st.phase == PH_OUTER ? 1.0 : 0.0;
   }
   c = block_sum256(c, sh);
+  o = block_sum256(o, sh);
   if (threadIdx.x == 0) {
     const unsigned active = (unsigned)c;
     if (E.active_host) *E.active_host = active;
     if (use_handle) cudaGraphSetConditional(h, active > 0 ? 1u : 0u);
+    const CondDev& cd = E.prm.cond;
+    if (cd.mask) {
+      *cd.launches += cd.n_base + (cd.taken[0] ? cd.n_cycle : 0u) + (cd.taken[1] ? cd.n_outer : 0u) +
+                      (cd.taken[2] ? cd.n_update : 0u);
+      cond_set(cd, 0, 0u);
+      cond_set(cd, 2, 0u);
+      cond_set(cd, 1, o > 0.0 ? 1u : 0u);
+    }
   }
 }
 
 inline int grid_or_one(int g) { return g < 1 ? 1 : g; }
 
-// resident 256-thread blocks per SM of a kernel (cached per kernel)
-int resident_blocks(const void* f, size_t smem) {
+// resident blocks per SM of a kernel at a block size (cached per kernel)
+int resident_blocks(const void* f, int threads, size_t smem) {
   static std::mutex mu;
   static std::unordered_map<const void*, int> cache;
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(f);
   if (it != cache.end()) return it->second;
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, 256, smem) != cudaSuccess || b < 1) b = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, threads, smem) != cudaSuccess || b < 1) b = 1;
   cache[f] = b;
   return b;
 }
@@ -1235,12 +1510,12 @@ int resident_blocks(const void* f, size_t smem) {
 // launch with optional programmatic dependent launch and thread-block clusters.  Grid-stride
 // kernels (cluster == 0) get at most one wave of resident blocks.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_k(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t s, int pdl,
-                     int cluster, Args... args) {
-  if (cluster == 0) grid = std::min(grid, resident_blocks(reinterpret_cast<const void*>(kern), smem) * sm_count());
+cudaError_t launch_kt(void (*kern)(KArgs...), int grid, int threads, size_t smem, cudaStream_t s,
+                      int pdl, int cluster, Args... args) {
+  if (cluster == 0) grid = std::min(grid, resident_blocks(reinterpret_cast<const void*>(kern), threads, smem) * sm_count());
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid_or_one(grid), 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
@@ -1262,6 +1537,12 @@ cudaError_t launch_k(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t
   cfg.attrs = attr;
   cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t s, int pdl,
+                     int cluster, Args... args) {
+  return launch_kt(kern, grid, 256, smem, s, pdl, cluster, args...);
 }
 
 // shared memory of the staged band kernels: two stages of 9 band slices of 8 tiles
@@ -1383,7 +1664,7 @@ template <class Pol>
 cudaError_t launch_tail_t(const EngineDev& E, int T, int want, int cluster, cudaStream_t s) {
   const int S = tail_smem_level(Pol::prec, E.prm.coarse, T);
   const size_t smem = (size_t)tail_smem_bytes(Pol::prec, E.prm.coarse, S);
-  return launch_k(k_tail<Pol>, E.nprob * cluster, smem, s, E.pdl, cluster, E, T, S, want);
+  return launch_kt(k_tail<Pol>, E.nprob * cluster, kTailThreads, smem, s, E.pdl, cluster, E, T, S, want);
 }
 
 cudaError_t launch_tail(const EngineDev& E, int T, int want, int cluster, cudaStream_t s) {

@@ -242,6 +242,37 @@ def test_profiling_times_kernels_without_changing_results(hn):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("L", [6, 9])
+def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L):
+    # the one-launch solve skips, through IF nodes, the parts of an iteration no problem is in
+    # (outer defect, update, the rest of a cycle after a converged lagged check); the host-driven
+    # iterations (profiling) run every kernel of every iteration
+    coef, b = I.batch_problem(5, L)
+    A = hn.hn_band_create(L, coef)
+    mg = hn.hn_mg_setup(A, prec=prec)
+    hn.hn_band_destroy(A)
+    try:
+        x0, st0, s0 = hn.hn_mg_solve(mg, L, b)
+        n_loop = hn.hn_mg_last_launches(mg)
+        hn.hn_mg_set_profiling(mg, True)
+        x1, st1, s1 = hn.hn_mg_solve(mg, L, b)
+        n_host = hn.hn_mg_last_launches(mg)
+        hn.hn_mg_set_profiling(mg, False)
+        assert s0 == s1 == hn.HN_OK
+        np.testing.assert_array_equal(x0, x1)
+        for k in ("cycles", "outer_iters", "inner_cycles", "relres"):
+            assert st0[k] == st1[k], k
+        assert 0 < n_loop <= n_host
+        if prec != 0:
+            assert n_loop < n_host
+        # a second solve counts its own launches again
+        hn.hn_mg_solve(mg, L, b)
+        assert hn.hn_mg_last_launches(mg) == n_loop
+    finally:
+        hn.hn_mg_destroy(mg)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_launch_shapes_do_not_change_results(hn, prec):
     # the tail level, cluster size and programmatic dependent launch only change where work runs
     L = 10                 # levels 9 and 10 are large enough for the bulk-copy kernels
