@@ -67,7 +67,7 @@ void walk_layout(int L, int coarse, int prec, F&& take) {
   for (int l = L; l >= coarse; --l) {
     for (int v = 0; v < 4; ++v) take(vec_elems(l) * vs);
     for (int k = 0; k < 9; ++k) take(vec_elems(l) * bs);
-    if (prec == P64) take(vec_elems(l) * 8);
+    take(vec_elems(l) * (prec == P64 ? 8 : 4));    // omega / diag
   }
   if (prec != P64) {
     for (int k = 0; k < 9; ++k) take(vec_elems(L) * 8);
@@ -196,6 +196,7 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
     }
     for (int k = 0; k < 9; ++k) d.scale[k] = 1.0f;
     if (prec == P64) d.wdinv = b.take<double>(vec_elems(l)) + H;
+    else d.wdf = b.take<float>(vec_elems(l)) + H;
   }
   if (prec != P64) {
     for (int k = 0; k < 9; ++k) P.band64[k] = b.take<double>(vec_elems(L)) + halo_of(L);
@@ -266,6 +267,7 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
       HN_CUDA(cudaStreamSynchronize(s));
       for (int k = 0; k < 9; ++k) d.scale[k] = hs[k];
     }
+    if (prec != P64) HN_CUDA(launch_wdf(l, prec, d.band, d.scale, o.omega, const_cast<float*>(d.wdf), s));
     if (l == c) {
       for (int k = 0; k < 9; ++k)
         HN_CUDA(cudaMemcpyAsync(coarse64.data() + (size_t)k * pitch_of(c), src.p[k],

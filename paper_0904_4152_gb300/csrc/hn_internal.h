@@ -38,6 +38,8 @@ enum Prec { P64 = 0, P32 = 1, P16 = 2 };
 struct LevelDev {
   const void* band[9];   // double (FP64 hierarchy), float (FP32), __half (FP16 codes)
   const double* wdinv;   // FP64 hierarchy only: omega / diag, pitch doubles
+  const float* wdf;      // FP32 / FP16 hierarchies: omega / diag in FP32, rounded as the band
+                         // kernels round it (FP16: diag of the row-sum form), pitch floats
   void* x[2];            // iterate and its Jacobi ping-pong partner (double or float)
   void* rhs;             // right-hand side of this level (restricted defect, or the top rhs)
   void* r;               // defect of this level
@@ -123,6 +125,9 @@ struct BandPtrs64 { double* p[9]; };
 struct BandPtrs64c { const double* p[9]; };
 struct BandPtrs32 { float* p[9]; };
 struct BandPtrs16 { __half* p[9]; };
+// omega / diag of an FP32 or FP16 level into wdf (pitch floats)
+cudaError_t launch_wdf(int L, int prec, const void* const* band, const float* scale, double omega,
+                       float* wdf, cudaStream_t s);
 cudaError_t launch_assemble(int L, const double* coef, const BandPtrs64& band, double* wdinv,
                             double omega, cudaStream_t s);
 cudaError_t launch_coarsen_coef(int Lf, const double* af, double* ac, cudaStream_t s);

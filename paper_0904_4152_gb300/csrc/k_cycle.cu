@@ -90,6 +90,10 @@ __device__ __forceinline__ void ld4c(const float* p, float (&o)[4]) {
   o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
 }
 
+// products rounded on their own (never contracted into a following add or subtract)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // 4 consecutive band values of band k at node i0, in the arithmetic type
 template <class Pol, int LKB = LD_NC>
 __device__ __forceinline__ void load_band(const void* band, float scale, long long i0,
@@ -99,7 +103,9 @@ __device__ __forceinline__ void load_band(const void* band, float scale, long lo
     const __half2 h0 = *reinterpret_cast<const __half2*>(&u.x);
     const __half2 h1 = *reinterpret_cast<const __half2*>(&u.y);
     const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
-    o[0] = scale * f0.x; o[1] = scale * f0.y; o[2] = scale * f1.x; o[3] = scale * f1.y;
+    // each value rounded on its own (never contracted into a following add)
+    o[0] = __fmul_rn(scale, f0.x); o[1] = __fmul_rn(scale, f0.y);
+    o[2] = __fmul_rn(scale, f1.x); o[3] = __fmul_rn(scale, f1.y);
   } else {
     ld4<LKB>(static_cast<const typename Pol::B*>(band) + i0, o);
   }
@@ -263,15 +269,14 @@ __device__ void pre_check(ProbState& st, const Params& prm, double nrm) {
 
 // Modes of the band kernel.  PRE12 / PRE2B split the first two smoothing steps: from a zero
 // iterate both steps fuse into one pass (x1 = omega D^-1 b is formed on the fly from windows of b
-// and D, then x2 = x1 + omega D^-1 (b - A x1) goes to buffer 0) and PRE2B skips the tile;
-// otherwise PRE12 does step 1 (buffer 0 -> 1) and PRE2B step 2 (1 -> 0).  The FP16 row-sum
-// diagonal needs all bands at every window position, so FP16 does not fuse.
+// and of the stored omega / D, then x2 = x1 + omega D^-1 (b - A x1) goes to buffer 0) and PRE2B
+// skips the tile; otherwise PRE12 does step 1 (buffer 0 -> 1) and PRE2B step 2 (1 -> 0).
 enum BandMode {
   M_SPMV = 0, M_DEFECT = 1, M_JACOBI = 2, M_JACOBI_FIRST = 3, M_CHECK = 4, M_PRE12 = 5,
   M_PRE2B = 6
 };
 
-template <class Pol> __device__ __forceinline__ constexpr bool fuses_pre() { return Pol::prec != P16; }
+template <class Pol> __device__ __forceinline__ constexpr bool fuses_pre() { return true; }
 
 // omega / diag at the lane's 4 nodes from the stored array (FP64) or the diagonal band (FP32)
 template <class Pol, int LKB>
@@ -310,38 +315,36 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
 #pragma unroll
         for (int j = 0; j < 4; ++j) out[j] = wd[j] * b[j];
       } else {
-        A dgv[4];
-        if constexpr (Pol::prec == P16) diag_rowsum<LKB>(d.band, d.scale, ib, dgv);
-        else load_band<Pol, LKB>(d.band[4], 1.0f, ib, dgv);
+        float wd[4];                              // omega / D, stored (never staged)
+        ld4<band_kind<LK>()>(d.wdf + i0, wd);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) out[j] = (omega / dgv[j]) * A(b[j]);
+        for (int j = 0; j < 4; ++j) out[j] = wd[j] * A(b[j]);
       }
       st4(static_cast<V*>(d.x[1]) + i0, out);
       return;
     }
     if constexpr (MODE == M_PRE12 && fuses_pre<Pol>()) {
       if (zg) {                                   // two steps from zero in one pass
+        // windows of b and of omega / D (zero in the halos, so x1 is zero there)
         V bw[3][8], dw[3][8], x1[3][8];
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
           load_row<V, LK>(rhs, i0 + dy * shift, lane, bw[dy + 1]);
           if constexpr (Pol::prec == P64) load_row<V, LKB>(d.wdinv, i0 + dy * shift, lane, dw[dy + 1]);
-          else load_row<V, LKB>(static_cast<const V*>(d.band[4]), i0 + dy * shift, lane, dw[dy + 1]);
+          else load_row<V, band_kind<LK>()>(d.wdf, i0 + dy * shift, lane, dw[dy + 1]);
         }
+        // x1 rounded on its own: the FP16 form subtracts x1 values, where a contracted product
+        // would round differently from one path to another
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-          for (int o = 0; o < 8; ++o) {
-            if constexpr (Pol::prec == P64) x1[r][o] = dw[r][o] * bw[r][o];
-            else x1[r][o] = dw[r][o] != V(0) ? (omega / dw[r][o]) * bw[r][o] : V(0);
-          }
+          for (int o = 0; o < 8; ++o) x1[r][o] = mul_rn(dw[r][o], bw[r][o]);
         A acc[4], dg[4];
-        stencil_windows<Pol, LKB>(d.band, nullptr, x1, i0, acc, dg);
-        A wd[4];
-        wd4_of<Pol, LKB>(d, i0, omega, dg, wd);
+        if constexpr (Pol::prec == P16) stencil_windows_rowsum<LKB>(d.band, d.scale, x1, ib, acc, dg);
+        else stencil_windows<Pol, LKB>(d.band, nullptr, x1, ib, acc, dg);
         V out[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) out[j] = fma(wd[j], A(bw[1][j + 2]) - acc[j], A(x1[1][j + 2]));
+        for (int j = 0; j < 4; ++j) out[j] = fma(A(dw[1][j + 2]), A(bw[1][j + 2]) - acc[j], A(x1[1][j + 2]));
         st4(static_cast<V*>(d.x[0]) + i0, out);
         return;
       }
@@ -769,7 +772,7 @@ __host__ __device__ inline long long smem_level_bytes(int l, int prec) {
   const long long bs = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
   const long long vs = prec == P64 ? 8 : 4;
   auto al = [](long long b) { return (b + 15) / 16 * 16; };
-  return 9 * al(e * bs) + 4 * al(e * vs) + (prec == P64 ? al(e * 8) : 0);
+  return 9 * al(e * bs) + 4 * al(e * vs) + al(e * (prec == P64 ? 8 : 4));
 }
 
 // carve level l of the shared-memory hierarchy starting at *off; start the asynchronous copies of
@@ -799,6 +802,12 @@ __device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* 
     for (int q = threadIdx.x; q < (int)(e / 2); q += blockDim.x)
       cp_async16(reinterpret_cast<double2*>(dst) + q, reinterpret_cast<const double2*>(src) + q);
     t.wdinv = dst + halo;
+  } else {
+    float* dst = reinterpret_cast<float*>(take(e * 4));
+    const float* src = g.wdf - halo;
+    for (int q = threadIdx.x; q < (int)(e / 4); q += blockDim.x)
+      cp_async16(reinterpret_cast<float4*>(dst) + q, reinterpret_cast<const float4*>(src) + q);
+    t.wdf = dst + halo;
   }
   V* vec[4];
   for (int v = 0; v < 4; ++v) {
@@ -825,14 +834,14 @@ __device__ __forceinline__ void stencil_node(const LevelDev& d, const typename P
   const int n = d.n;
   if constexpr (Pol::prec == P16) {
     const float xi = x[i];
-    const float rho = d.scale[4] * __half2float(static_cast<const B*>(d.band[4])[i]);
+    const float rho = __fmul_rn(d.scale[4], __half2float(static_cast<const B*>(d.band[4])[i]));
     acc = rho * xi;
     dg = rho;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       if (k == 4) continue;
       const int off = (k / 3 - 1) * n + (k % 3 - 1);
-      const float b = d.scale[k] * __half2float(static_cast<const B*>(d.band[k])[i]);
+      const float b = __fmul_rn(d.scale[k], __half2float(static_cast<const B*>(d.band[k])[i]));
       acc = fmaf(b, x[i + off] - xi, acc);
       dg -= b;
     }
@@ -856,17 +865,6 @@ __device__ __forceinline__ typename Pol::A wd_node(const LevelDev& d, int i, typ
   else return omega / dg;
 }
 
-// diagonal of the row-sum form without x
-__device__ __forceinline__ float diag_rowsum_node(const LevelDev& d, int i) {
-  float dg = d.scale[4] * __half2float(static_cast<const __half*>(d.band[4])[i]);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    if (k == 4) continue;
-    dg -= d.scale[k] * __half2float(static_cast<const __half*>(d.band[k])[i]);
-  }
-  return dg;
-}
-
 template <class Pol, int MODE>
 __device__ __forceinline__ void band_node(const LevelDev& d, int i, bool zg, int in_sel,
                                           typename Pol::A omega) {
@@ -880,35 +878,40 @@ __device__ __forceinline__ void band_node(const LevelDev& d, int i, bool zg, int
     if (zg && (MODE == M_JACOBI_FIRST || !fuses_pre<Pol>())) {   // x = 0: x' = omega D^-1 rhs
       V out;
       if constexpr (Pol::prec == P64) out = d.wdinv[i] * rhs[i];
-      else {
-        A dg;
-        if constexpr (Pol::prec == P16) dg = diag_rowsum_node(d, i);
-        else dg = static_cast<const typename Pol::B*>(d.band[4])[i];
-        out = (omega / dg) * A(rhs[i]);
-      }
+      else out = d.wdf[i] * A(rhs[i]);
       static_cast<V*>(d.x[1])[i] = out;
       return;
     }
     if constexpr (MODE == M_PRE12 && fuses_pre<Pol>()) {
       if (zg) {                                   // two steps from zero in one pass
         const int n = d.n;
-        A acc = A(0), dg = A(0);
-        V x1c = V(0);
+        V x1[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
           const int j = i + (k / 3 - 1) * n + (k % 3 - 1);
-          V x1;
-          if constexpr (Pol::prec == P64) x1 = d.wdinv[j] * rhs[j];
-          else {
-            const V dw = static_cast<const typename Pol::B*>(d.band[4])[j];
-            x1 = dw != V(0) ? (omega / dw) * rhs[j] : V(0);
-          }
-          const A b = static_cast<const typename Pol::B*>(d.band[k])[i];
-          acc = fma(b, A(x1), acc);
-          if (k == 4) { dg = b; x1c = x1; }
+          if constexpr (Pol::prec == P64) x1[k] = mul_rn(d.wdinv[j], rhs[j]);
+          else x1[k] = mul_rn(d.wdf[j], rhs[j]);
         }
-        const A wd = wd_node<Pol>(d, i, omega, dg);
-        static_cast<V*>(d.x[0])[i] = fma(wd, A(rhs[i]) - acc, A(x1c));
+        A acc;
+        if constexpr (Pol::prec == P16) {
+          const float rho = __fmul_rn(d.scale[4], __half2float(static_cast<const __half*>(d.band[4])[i]));
+          acc = rho * x1[4];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            if (k == 4) continue;
+            const float b = __fmul_rn(d.scale[k], __half2float(static_cast<const __half*>(d.band[k])[i]));
+            acc = fmaf(b, x1[k] - x1[4], acc);
+          }
+        } else {
+          acc = A(0);
+#pragma unroll
+          for (int k = 0; k < 9; ++k)
+            acc = fma(A(static_cast<const typename Pol::B*>(d.band[k])[i]), A(x1[k]), acc);
+        }
+        A wd;
+        if constexpr (Pol::prec == P64) wd = d.wdinv[i];
+        else wd = d.wdf[i];
+        static_cast<V*>(d.x[0])[i] = fma(wd, A(rhs[i]) - acc, A(x1[4]));
         return;
       }
     }
@@ -1606,7 +1609,7 @@ cudaError_t launch_pre2b(const EngineDev& E, TileList tl, int level, int want, i
                          cudaStream_t s) {
   return launch_band(M_PRE2B, E, tl, level, want, 0, grid, s);
 }
-bool pre_fuses(int prec) { return prec != P16; }
+bool pre_fuses(int) { return true; }
 
 // shared memory the fused coarse-level kernel may use for levels coarse..S
 constexpr long long kTailSmemBudget = 160 * 1024;

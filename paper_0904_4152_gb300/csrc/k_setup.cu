@@ -127,6 +127,28 @@ __global__ void k_to_f16(long long pitch, BandPtrs64c src, const unsigned long l
   for (int k = 0; k < 9; ++k) dst.p[k][i] = __double2half(rowsum_value(src, k, i) / (double)sk[k]);
 }
 
+// omega / diag in FP32: FP32 bands divide by array 4; FP16 bands by the row-sum diagonal
+// rho - sum_{k != 4} a_k with every a_k = scale_k * code rounded on its own (band order)
+struct BandPtrsAny { const void* p[9]; };
+struct Scales9 { float s[9]; };
+__global__ void k_wdf(long long pitch, int prec, BandPtrsAny band, Scales9 sc, float omega,
+                      float* __restrict__ wdf) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pitch) return;
+  float dg;
+  if (prec == P32) {
+    dg = static_cast<const float*>(band.p[4])[i];
+  } else {
+    dg = __fmul_rn(sc.s[4], __half2float(static_cast<const __half*>(band.p[4])[i]));
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      if (k == 4) continue;
+      dg -= __fmul_rn(sc.s[k], __half2float(static_cast<const __half*>(band.p[k])[i]));
+    }
+  }
+  wdf[i] = omega / dg;
+}
+
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -158,6 +180,16 @@ cudaError_t launch_band_to_f16(int L, const BandPtrs64c& src, unsigned long long
   if (e != cudaSuccess) return e;
   k_absmax<<<blocks_for(pitch, 256), 256, 0, s>>>(pitch, src, absmax9);
   k_to_f16<<<blocks_for(pitch, 256), 256, 0, s>>>(pitch, src, absmax9, dst, scales_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wdf(int L, int prec, const void* const* band, const float* scale, double omega,
+                       float* wdf, cudaStream_t s) {
+  const long long pitch = pitch_of(L);
+  BandPtrsAny b{};
+  Scales9 sc{};
+  for (int k = 0; k < 9; ++k) { b.p[k] = band[k]; sc.s[k] = scale[k]; }
+  k_wdf<<<blocks_for(pitch, 256), 256, 0, s>>>(pitch, prec, b, sc, (float)omega, wdf);
   return cudaGetLastError();
 }
 
