@@ -2,8 +2,11 @@
  *
  * The V-cycle schedule runs levels above `tail_level` as one launch per step over the device work
  * list, and levels coarse_L..tail_level of every problem inside one fused launch of one
- * thread-block cluster (`cluster` blocks of 256 threads) per problem.  The best split depends on
- * the levels and the batch; hn_mg_autotune measures candidates on the hierarchy itself.
+ * thread-block cluster (`cluster` blocks of 512 threads) per problem.  Inside that launch the
+ * smallest levels live in the shared memory of the cluster's first block; the levels between
+ * them and tail_level either live in the distributed shared memory of the whole cluster (`dsm`,
+ * when they fit) or are read through L2.  The best split depends on the levels and the batch;
+ * hn_mg_autotune measures candidates on the hierarchy itself.
  */
 #ifndef HN_TUNE_H
 #define HN_TUNE_H
@@ -22,6 +25,8 @@ typedef struct {
                        fewer blocks than SMs only */
   int staged;       /* 1: the band kernels of large FP32 / FP16 levels stream the bands through
                        shared memory with bulk copies (TMA engine) on mbarriers; 0: register path */
+  int dsm;          /* 1: the fused launch keeps its cluster levels in distributed shared memory
+                       when they fit (else, and with 0, they run through L2) */
 } hn_tuning;
 
 /* Set / read the launch shape used by mg's later solves.  HN_ERR_ARG on values out of range. */

@@ -29,6 +29,15 @@ void exact_caps(const std::vector<hn_mg*>& mgs, std::vector<long long>& caps, lo
   }
 }
 
+// default launch shape of one problem: FP64 arithmetic is slow enough on this part that the
+// fused tail pays from level 6 down (its levels then fit in distributed shared memory); the
+// FP32/FP16 inner cycles fuse from level 7 down (measured at L=10)
+Tuning default_tuning(const Params& prm) {
+  Tuning t;
+  t.tail_level = prm.prec == P64 ? 6 : 7;
+  return t;
+}
+
 hn_status ensure_solo(hn_mg* mg) {
   if (mg->solo) return HN_OK;
   std::vector<long long> caps;
@@ -37,7 +46,7 @@ hn_status ensure_solo(hn_mg* mg) {
   std::unique_ptr<Engine> e(new Engine());
   HN_TRY(e->create(mg->prm, 1, mg->L, caps, fine, mg->stream));
   HN_TRY(e->set_members({mg}));
-  if (mg->tuned) e->set_tuning(mg->tuning);
+  e->set_tuning(mg->tuned ? mg->tuning : default_tuning(mg->prm));
   mg->solo = e.release();
   return HN_OK;
 }
@@ -62,7 +71,7 @@ Tuning batch_tuning(const std::vector<hn_mg*>& list) {
   for (hn_mg* mg : list)
     same = same && mg->tuned && mg->tuning.tail_level == list[0]->tuning.tail_level &&
            mg->tuning.cluster == list[0]->tuning.cluster && mg->tuning.pdl == list[0]->tuning.pdl &&
-           mg->tuning.staged == list[0]->tuning.staged;
+           mg->tuning.staged == list[0]->tuning.staged && mg->tuning.dsm == list[0]->tuning.dsm;
   if (same) return list[0]->tuning;
   Tuning t;
   const int n = (int)list.size();
@@ -282,7 +291,8 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
   {
     const Tuning t = batch_tuning(list);
     const Tuning& c = e.tuning();
-    if (t.tail_level != c.tail_level || t.cluster != c.cluster || t.pdl != c.pdl || t.staged != c.staged)
+    if (t.tail_level != c.tail_level || t.cluster != c.cluster || t.pdl != c.pdl || t.staged != c.staged ||
+        t.dsm != c.dsm)
       e.set_tuning(t);
   }
   cudaStream_t s = e.stream();
@@ -407,11 +417,13 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
   HN_TRY(ensure_solo(mg));
   if (t->pdl < 0 || t->pdl > 2) return set_error(HN_ERR_ARG, "pdl must be 0, 1 or 2");
   if (t->staged != 0 && t->staged != 1) return set_error(HN_ERR_ARG, "staged must be 0 or 1");
+  if (t->dsm != 0 && t->dsm != 1) return set_error(HN_ERR_ARG, "dsm must be 0 or 1");
   Tuning tu;
   tu.tail_level = t->tail_level;
   tu.cluster = c;
   tu.pdl = t->pdl;
   tu.staged = t->staged;
+  tu.dsm = t->dsm;
   mg->solo->set_tuning(tu);
   mg->tuning = tu;
   mg->tuned = true;
@@ -421,11 +433,12 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
 hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t) {
   clear_error();
   if (!mg || !t) return set_error(HN_ERR_ARG, "null argument");
-  const Tuning tu = mg->solo ? mg->solo->tuning() : mg->tuning;
+  const Tuning tu = mg->solo ? mg->solo->tuning() : (mg->tuned ? mg->tuning : default_tuning(mg->prm));
   t->tail_level = tu.tail_level;
   t->cluster = tu.cluster;
   t->pdl = tu.pdl;
   t->staged = tu.staged;
+  t->dsm = tu.dsm;
   return HN_OK;
 }
 
@@ -440,7 +453,7 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
   struct Free { double* p; ~Free() { cudaFreeHost(p); } } fr{x};
   const int clusters[5] = {1, 2, 4, 8, 16};
   double best_ms = 1e300;
-  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 2, 0};
+  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 2, 0, 1};
   cudaEvent_t e0, e1;
   HN_CUDA(cudaEventCreate(&e0));
   HN_CUDA(cudaEventCreate(&e1));
@@ -448,7 +461,7 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
   const int tmax = std::min(mg->L, 9);
   for (int T = mg->coarse; T <= tmax; ++T)
     for (int ci = 0; ci < 5; ++ci) {
-      hn_tuning t{T, clusters[ci], 2, 0};
+      hn_tuning t{T, clusters[ci], 2, 0, 1};
       HN_TRY(hn_mg_set_tuning(mg, &t));
       HN_TRY(hn_mg_solve(mg, b, x, 0, 0, nullptr));            // capture + warm-up
       HN_CUDA(cudaEventRecord(e0, mg->solo->stream()));
@@ -482,10 +495,10 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
   int Lmax = 0;
   for (int j = 0; j < count; ++j) Lmax = std::max(Lmax, mgs[j]->L);
   double best_ms = 1e300;
-  hn_tuning bt{5, 1, 2, 0};
+  hn_tuning bt{5, 1, 2, 0, 1};
   for (int T = mgs[0]->coarse; T <= std::min(Lmax, 8); ++T)
     for (int ci = 0; ci < 3; ++ci) {
-      hn_tuning t{T, clusters[ci], 2, 0};
+      hn_tuning t{T, clusters[ci], 2, 0, 1};
       for (int j = 0; j < count; ++j) {
         Tuning tu; tu.tail_level = T; tu.cluster = clusters[ci]; tu.pdl = 2;
         mgs[j]->tuning = tu;

@@ -396,6 +396,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   E_.pdl = tune_.pdl;
   E_.err = dErr_;
   E_.staged = tune_.staged;
+  E_.dsm = tune_.dsm;
   E_.iter_limit = (unsigned)(prm.max_cycles + prm.max_outer + 8);
   for (int l = 0; l <= kMaxLevel; ++l) {
     lists_[l] = TileList{dItems_[l], dCounts_ + l, dChunks_[l], dChunkCounts_ + l, (int)chunkCap_[l]};

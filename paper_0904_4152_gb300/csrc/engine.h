@@ -67,6 +67,7 @@ struct Tuning {
   int pdl = 2;      // programmatic dependent launch for launches of fewer blocks than SMs
   int staged = 0;   // stream the bands of large FP32/FP16 levels through shared memory by bulk
                     // copies (measured slower than the register path at L=12; off)
+  int dsm = 1;      // fused tail: cluster levels in distributed shared memory when they fit
 };
 
 class Engine;
@@ -133,7 +134,9 @@ class Engine {
 
   void set_profiling(bool on);
   void set_iter_limit(unsigned lim) { E_.iter_limit = lim; graphsValid_ = false; }
-  void set_tuning(const Tuning& t) { tune_ = t; E_.pdl = t.pdl; E_.staged = t.staged; graphsValid_ = false; }
+  void set_tuning(const Tuning& t) {
+    tune_ = t; E_.pdl = t.pdl; E_.staged = t.staged; E_.dsm = t.dsm; graphsValid_ = false;
+  }
   const Tuning& tuning() const { return tune_; }
   // levels that may be some problem's finest level (their first smoothing step may start from a
   // nonzero iterate); all levels for the server

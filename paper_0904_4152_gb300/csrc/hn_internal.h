@@ -152,6 +152,8 @@ struct EngineDev {
   int pdl;                     // launch with programmatic dependent launch (host-side flag)
   int* err;                    // device word: nonzero after a bounded wait gave up
   int staged;                  // host-side flag: large FP32/FP16 levels use the bulk-copy kernels
+  int dsm;                     // host-side flag: the fused tail keeps its cluster levels in
+                               // distributed shared memory when they fit
 };
 
 // Launch wrappers for one step of the schedule; grid = CTAs of 256 threads.  level < 0 means

@@ -523,6 +523,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// one bulk copy global -> this block's shared memory, accounted on bar (16-byte aligned, size a
+// multiple of 16); issued by one thread, which arrives on bar once all its copies are issued
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+  if (bytes == 0) return;
+  mbar_expect(bar, bytes);
+  bulk_g2s(dst, src, bytes, bar);
+}
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
@@ -775,12 +790,13 @@ __host__ __device__ inline long long smem_level_bytes(int l, int prec) {
   return 9 * al(e * bs) + 4 * al(e * vs) + al(e * (prec == P64 ? 8 : 4));
 }
 
-// carve level l of the shared-memory hierarchy starting at *off; start the asynchronous copies of
-// its bands (and omega/D) and zero its vectors.  The caller waits for the copies (cp_async_wait)
-// and synchronizes the block before use.
+// carve level l of the shared-memory hierarchy starting at *off; with `fill`, start the bulk
+// copies of its bands (and omega/D, thread 0, accounted on bar) and zero its vectors.  The caller
+// arrives on bar, waits for its phase and synchronizes the block before use.  Every block of a cluster carves
+// the same layout, so a block can address block 0's copy through distributed shared memory.
 template <class Pol>
 __device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* base, long long* off,
-                                 int l) {
+                                 int l, bool fill, unsigned long long* bar) {
   using V = typename Pol::V;
   using B = typename Pol::B;
   const long long halo = (((1LL << l) + 1 + 8) + 31) / 32 * 32;
@@ -791,28 +807,22 @@ __device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* 
   for (int k = 0; k < 9; ++k) {
     B* dst = reinterpret_cast<B*>(take(e * sizeof(B)));
     const B* src = static_cast<const B*>(g.band[k]) - halo;
-    const int chunks = (int)(e * sizeof(B) / 16);
-    for (int q = threadIdx.x; q < chunks; q += blockDim.x)
-      cp_async16(reinterpret_cast<uint4*>(dst) + q, reinterpret_cast<const uint4*>(src) + q);
+    if (fill && threadIdx.x == 0) bulk_copy(dst, src, (unsigned)(e * sizeof(B)), bar);
     t.band[k] = dst + halo;
   }
   if constexpr (Pol::prec == P64) {
     double* dst = reinterpret_cast<double*>(take(e * 8));
-    const double* src = g.wdinv - halo;
-    for (int q = threadIdx.x; q < (int)(e / 2); q += blockDim.x)
-      cp_async16(reinterpret_cast<double2*>(dst) + q, reinterpret_cast<const double2*>(src) + q);
+    if (fill && threadIdx.x == 0) bulk_copy(dst, g.wdinv - halo, (unsigned)(e * 8), bar);
     t.wdinv = dst + halo;
   } else {
     float* dst = reinterpret_cast<float*>(take(e * 4));
-    const float* src = g.wdf - halo;
-    for (int q = threadIdx.x; q < (int)(e / 4); q += blockDim.x)
-      cp_async16(reinterpret_cast<float4*>(dst) + q, reinterpret_cast<const float4*>(src) + q);
+    if (fill && threadIdx.x == 0) bulk_copy(dst, g.wdf - halo, (unsigned)(e * 4), bar);
     t.wdf = dst + halo;
   }
   V* vec[4];
   for (int v = 0; v < 4; ++v) {
     vec[v] = reinterpret_cast<V*>(take(e * sizeof(V)));
-    for (int q = threadIdx.x; q < (int)(e * sizeof(V) / 16); q += blockDim.x)
+    for (int q = threadIdx.x; fill && q < (int)(e * sizeof(V) / 16); q += blockDim.x)
       reinterpret_cast<uint4*>(vec[v])[q] = make_uint4(0u, 0u, 0u, 0u);
   }
   t.x[0] = vec[0] + halo; t.x[1] = vec[1] + halo; t.rhs = vec[2] + halo; t.r = vec[3] + halo;
@@ -1031,6 +1041,194 @@ __device__ void vcycle_up_smem(const LevelDev& d, const LevelDev& dc, int pre, i
   }
 }
 
+// ------------------------------------------ cluster levels in distributed shared memory
+// The levels between the shared-memory levels of block 0 (coarse..S) and the top of the fused
+// tail live in the shared memory of the whole cluster: block r holds rows
+// [part_row(l, r), part_row(l, r + 1)) of level l (its bands, and its vectors with one ghost row
+// on each side).  The partition of level l + 1 is that of level l with every row doubled, so a
+// block restricts to, and prolongs from, its own rows of the next coarser level (plus a ghost row).
+// After each step a block stores its first and last own rows of the vector it wrote into the ghost
+// rows of its neighbours (distributed shared memory), then the cluster synchronizes.
+
+// C is a power of two no larger than 2^(S+1), so block r's first row r * 2^l / C is exact and
+// doubles from one level to the next; the last block also takes the last row
+__host__ __device__ inline int log2_pow2(int C) { int k = 0; while ((1 << k) < C) ++k; return k; }
+__host__ __device__ inline int part_row(int l, int r, int C, int S) {
+  (void)S;
+  if (r >= C) return (1 << l) + 1;
+  return (r << l) >> log2_pow2(C);
+}
+__host__ __device__ inline int part_maxrows(int l, int C, int S) {
+  (void)S;
+  return ((1 << l) >> log2_pow2(C)) + 1;
+}
+__host__ __device__ inline long long align_down(long long x, int a) {   // a: a power of two
+  return x & ~(long long)(a - 1);
+}
+// elements of one block's vector array (own rows, a ghost row and a node on each side, 16-byte
+// aligned start) and band array (own rows) of cluster level l
+__host__ __device__ inline long long dsm_vec_elems(int l, int C, int S, int esize) {
+  const long long n = (1LL << l) + 1;
+  const int a = 16 / esize;
+  return ((long long)(part_maxrows(l, C, S) + 2) * n + 2 + 3 * a) / a * a;
+}
+__host__ __device__ inline long long dsm_band_elems(int l, int C, int S, int esize) {
+  const long long n = (1LL << l) + 1;
+  const int a = 16 / esize;
+  return ((long long)part_maxrows(l, C, S) * n + 3 * a) / a * a;
+}
+__host__ __device__ inline long long dsm_level_bytes(int l, int C, int S, int prec) {
+  const int vs = prec == P64 ? 8 : 4, bs = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
+  return 9 * dsm_band_elems(l, C, S, bs) * bs + 5 * dsm_vec_elems(l, C, S, vs) * vs;
+}
+
+// first global node index of block r's vector arrays of level l
+template <class V>
+__device__ __forceinline__ long long dsm_vec_start(int l, int r, int C, int S) {
+  const long long n = (1LL << l) + 1;
+  return align_down((long long)part_row(l, r, C, S) * n - n - 1, 16 / (int)sizeof(V));
+}
+
+// carve block r's arrays of cluster level l at *off, bulk-copy its bands (own rows) and omega/D
+// (own and ghost rows; thread 0, accounted on bar), zero its vectors; v gets views indexed by
+// global node index
+template <class Pol>
+__device__ void dsm_level_setup(const LevelDev& g, LevelDev& v, unsigned char* base, long long* off,
+                                int l, int r, int C, int S, unsigned long long* bar) {
+  using V = typename Pol::V;
+  using B = typename Pol::B;
+  const long long n = (1LL << l) + 1;
+  const long long R0n = (long long)part_row(l, r, C, S) * n, R1n = (long long)part_row(l, r + 1, C, S) * n;
+  constexpr int av = 16 / (int)sizeof(V), ab = 16 / (int)sizeof(B);
+  const long long g0v = dsm_vec_start<V>(l, r, C, S), g0b = align_down(R0n, ab);
+  const long long nv = dsm_vec_elems(l, C, S, sizeof(V)), nb = dsm_band_elems(l, C, S, sizeof(B));
+  auto take = [&](long long bytes) { unsigned char* p = base + *off; *off += (bytes + 15) / 16 * 16; return p; };
+  LevelDev t = g;
+  const int bchunks = (int)((R1n - g0b + ab - 1) / ab);
+  for (int k = 0; k < 9; ++k) {
+    B* dst = reinterpret_cast<B*>(take(nb * sizeof(B)));
+    const B* src = static_cast<const B*>(g.band[k]) + g0b;
+    if (threadIdx.x == 0) bulk_copy(dst, src, (unsigned)bchunks * 16u, bar);
+    t.band[k] = dst - g0b;
+  }
+  const int vchunks = (int)((R1n + n + 1 - g0v + av - 1) / av);
+  {
+    V* dst = reinterpret_cast<V*>(take(nv * sizeof(V)));
+    const V* src;
+    if constexpr (Pol::prec == P64) src = g.wdinv + g0v;
+    else src = g.wdf + g0v;
+    if (threadIdx.x == 0) bulk_copy(dst, src, (unsigned)vchunks * 16u, bar);
+    if constexpr (Pol::prec == P64) t.wdinv = dst - g0v;
+    else t.wdf = dst - g0v;
+  }
+  V* vec[4];
+  for (int k = 0; k < 4; ++k) {
+    vec[k] = reinterpret_cast<V*>(take(nv * sizeof(V)));
+    for (int q = threadIdx.x; q < (int)(nv / av); q += blockDim.x)
+      reinterpret_cast<uint4*>(vec[k])[q] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  t.x[0] = vec[0] - g0v; t.x[1] = vec[1] - g0v; t.rhs = vec[2] - g0v; t.r = vec[3] - g0v;
+  if (threadIdx.x == 0) v = t;
+}
+
+// copy block r's first and last own rows of `view` (level l, indexed by global node index) into
+// the ghost rows of blocks r - 1 and r + 1
+template <class V>
+__device__ void dsm_push(V* view, int l, int r, int C, int S) {
+  cg::cluster_group cl = cg::this_cluster();
+  const long long n = (1LL << l) + 1;
+  V* start = view + dsm_vec_start<V>(l, r, C, S);
+  if (r > 0) {
+    const long long R0n = (long long)part_row(l, r, C, S) * n;
+    V* rv = cl.map_shared_rank(start, r - 1) - dsm_vec_start<V>(l, r - 1, C, S);
+    for (int q = threadIdx.x; q < (int)n; q += blockDim.x) rv[R0n + q] = view[R0n + q];
+  }
+  if (r < C - 1) {
+    const long long L1n = (long long)(part_row(l, r + 1, C, S) - 1) * n;
+    V* rv = cl.map_shared_rank(start, r + 1) - dsm_vec_start<V>(l, r + 1, C, S);
+    for (int q = threadIdx.x; q < (int)n; q += blockDim.x) rv[L1n + q] = view[L1n + q];
+  }
+}
+
+// one node-wise step on block r's own rows of cluster level l, then the ghost exchange of the
+// vector it wrote (dst: 0, 1 = x[0], x[1]; 2 = r; -1 = nothing written)
+template <class Pol, int MODE>
+__device__ __forceinline__ void dsm_step(const LevelDev& d, int l, int r, int C, int S, bool zg, int in_sel,
+                                         typename Pol::A omega, int dst) {
+  using V = typename Pol::V;
+  const long long n = (1LL << l) + 1;
+  const long long R0n = (long long)part_row(l, r, C, S) * n, R1n = (long long)part_row(l, r + 1, C, S) * n;
+  for (long long i = R0n + threadIdx.x; i < R1n; i += blockDim.x) band_node<Pol, MODE>(d, (int)i, zg, in_sel, omega);
+  __syncthreads();
+  if (dst >= 0) dsm_push<V>(static_cast<V*>(dst == 2 ? d.r : d.x[dst]), l, r, C, S);
+  cg::this_cluster().sync();
+}
+
+// down part of the cycle on cluster level l; the next coarser level is cluster level l - 1, or
+// block 0's shared-memory level S (c0: block 0's view of it, addressed through the cluster)
+template <class Pol>
+__device__ void dsm_down(const LevelDev* cv, const LevelDev& c0, int l, int r, int C, int S, bool zg,
+                         int pre, typename Pol::A omega) {
+  using V = typename Pol::V;
+  const LevelDev& d = cv[l];
+  if (pre >= 2) {
+    const bool fused = zg && fuses_pre<Pol>();
+    dsm_step<Pol, M_PRE12>(d, l, r, C, S, zg, 0, omega, fused ? 0 : 1);
+    if (!fused) dsm_step<Pol, M_PRE2B>(d, l, r, C, S, zg, 0, omega, 0);
+    for (int s = 3; s <= pre; ++s)
+      dsm_step<Pol, M_JACOBI>(d, l, r, C, S, zg, (s - 1) & 1, omega, 1 - ((s - 1) & 1));
+  } else {
+    dsm_step<Pol, M_JACOBI_FIRST>(d, l, r, C, S, zg, 0, omega, 1);
+  }
+  dsm_step<Pol, M_DEFECT>(d, l, r, C, S, zg, pre & 1, omega, 2);
+  const long long nc = (1LL << (l - 1)) + 1;
+  if (l - 1 > S) {
+    const LevelDev& dc = cv[l - 1];
+    const long long c0n = (long long)part_row(l - 1, r, C, S) * nc, c1n = (long long)part_row(l - 1, r + 1, C, S) * nc;
+    for (long long i = c0n + threadIdx.x; i < c1n; i += blockDim.x) restrict_node<V>(d, dc, (int)i);
+    __syncthreads();
+    dsm_push<V>(static_cast<V*>(dc.rhs), l - 1, r, C, S);
+  } else {
+    // coarse rows whose centre fine row is one of this block's rows, into block 0
+    const int J0 = (part_row(l, r, C, S) + 1) / 2, J1 = (part_row(l, r + 1, C, S) + 1) / 2;
+    for (long long i = (long long)J0 * nc + threadIdx.x; i < (long long)J1 * nc; i += blockDim.x)
+      restrict_node<V>(d, c0, (int)i);
+  }
+  cg::this_cluster().sync();
+}
+
+// up part on cluster level l.  From block 0's level S, the coarse rows this block interpolates
+// from are first copied (one read each through the cluster) into this block's own, otherwise
+// unused, copy of level S (buffer x[1], which block 0 no longer needs either).
+template <class Pol>
+__device__ void dsm_up(const LevelDev* cv, const LevelDev& c0, const LevelDev& s_own, int l, int r,
+                       int C, int S, int pre, int post, typename Pol::A omega) {
+  using V = typename Pol::V;
+  const LevelDev& d = cv[l];
+  const long long n = (1LL << l) + 1;
+  const long long R0n = (long long)part_row(l, r, C, S) * n, R1n = (long long)part_row(l, r + 1, C, S) * n;
+  LevelDev local = s_own;
+  if (l - 1 == S) {
+    const int nc = (1 << S) + 1;
+    const int J0 = part_row(l, r, C, S) >> 1;
+    const int J1 = min(part_row(l, r + 1, C, S) >> 1, nc - 1);
+    const V* src = static_cast<const V*>(c0.x[0]);
+    V* dst = static_cast<V*>(s_own.x[1]);
+    for (int i = J0 * nc + threadIdx.x; i < (J1 + 1) * nc; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    local.x[0] = s_own.x[1];
+  }
+  const LevelDev& dc = l - 1 > S ? cv[l - 1] : local;
+  for (long long i = R0n + threadIdx.x; i < R1n; i += blockDim.x) prolong_node<V>(d, dc, pre & 1, (int)i);
+  __syncthreads();
+  dsm_push<V>(static_cast<V*>(d.x[pre & 1]), l, r, C, S);
+  cg::this_cluster().sync();
+  for (int s = 1; s <= post; ++s) {
+    const int in_sel = (pre + s - 1) & 1;
+    dsm_step<Pol, M_JACOBI>(d, l, r, C, S, false, in_sel, omega, 1 - in_sel);
+  }
+}
+
 // Pre-smoothing, defect and restriction of level l.  check_part (top level with a nonzero
 // iterate): the first smoothing step also writes the residual partials, block 0 reduces them and
 // takes the lagged convergence decision; returns false if the problem leaves the cycle.
@@ -1103,25 +1301,30 @@ __device__ __forceinline__ void vcycle_up_level(const LevelDev& d, const LevelDe
 
 constexpr int kTailThreads = 512;
 
+// dsm: the cluster levels (S, T] live in distributed shared memory (the launch reserved room for
+// them); otherwise they run over global memory through L2
 template <class Pol>
-__global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, int S, int want) {
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, int S, int want, int dsm) {
   using A = typename Pol::A;
   using V = typename Pol::V;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LevelDev gd[kMaxLevel + 1];       // global-memory descriptors of this problem
-  __shared__ LevelDev sd[kMaxLevel + 1];       // shared-memory copies of levels coarse..S
+  __shared__ LevelDev sd[kMaxLevel + 1];       // shared-memory levels coarse..S (block 0's data)
+  __shared__ LevelDev cv[kMaxLevel + 1];       // this block's rows of the cluster levels
   __shared__ double sol[kMaxCoarseM];
   __shared__ double sh[32];
   __shared__ const double* s_cinv;
+  __shared__ __align__(8) unsigned long long s_bar;   // bulk copies: phase 0 constant data, 1 inputs
   cg::cluster_group cl = cg::this_cluster();
   const int csize = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int p = blockIdx.x / csize;
   pdl_trigger();
   if (p >= E.nprob) return;
-  // constant data before the wait for the preceding launch: the level descriptors and, in block 0,
-  // the bands of the shared-memory levels (asynchronous copies, completed before first use).
-  // Descriptors change only between launches (host copies); an empty slot's is all zero.
+  // constant data before the wait for the preceding launch: the level descriptors, the bands of
+  // block 0's shared-memory levels and of this block's rows of the cluster levels (asynchronous
+  // copies, completed before first use).  Descriptors change only between launches (host
+  // copies); an empty slot's is all zero.
   const ProblemDev& P = E.P[p];
   if (P.L < HN_MIN_LEVEL) return;
   const int lane = threadIdx.x & 31;
@@ -1129,34 +1332,49 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
   const int top = P.L < T ? P.L : T, c = P.coarse;
   const int Ss = S < top ? S : top;
   const int m = P.m;
+  const bool use_dsm = dsm && top > Ss;
   {
     const int words = (int)(sizeof(LevelDev) / 4) * (top - c + 1);
     const unsigned* src = reinterpret_cast<const unsigned*>(&P.lev[c]);
     unsigned* dst = reinterpret_cast<unsigned*>(&gd[c]);
     for (int q = threadIdx.x; q < words; q += blockDim.x) dst[q] = src[q];
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar, 1);
+      mbar_fence_init();
+    }
     __syncthreads();
   }
-  if (rank == 0) {
-    long long off = 0;
-    for (int l = c; l <= Ss; ++l) smem_level_setup<Pol>(gd[l], sd[l], smem, &off, l);
-    // the coarse inverse (m*m doubles) is staged in shared memory when it is small
-    if ((long long)m * m * 8 <= kCinvSmemMax) {
-      double* dst = reinterpret_cast<double*>(smem + off);
-      for (int q = threadIdx.x; q < m * m / 2; q += blockDim.x)
-        cp_async16(reinterpret_cast<double2*>(dst) + q, reinterpret_cast<const double2*>(P.cinv) + q);
-      if ((m * m) & 1) {
-        if (threadIdx.x == 0) dst[m * m - 1] = __ldg(P.cinv + m * m - 1);
+  long long off = 0;
+  for (int l = c; l <= Ss; ++l) smem_level_setup<Pol>(gd[l], sd[l], smem, &off, l, rank == 0, &s_bar);
+  {   // the coarse inverse (m*m doubles) is staged in shared memory when it is small
+    const bool staged = (long long)m * m * 8 <= kCinvSmemMax;
+    double* dst = reinterpret_cast<double*>(smem + off);
+    if (staged) off += ((long long)m * m * 8 + 15) / 16 * 16;
+    if (rank == 0 && threadIdx.x == 0) {
+      if (staged) {
+        bulk_copy(dst, P.cinv, (unsigned)(m * m / 2) * 16u, &s_bar);
+        if ((m * m) & 1) dst[m * m - 1] = __ldg(P.cinv + m * m - 1);
       }
-      if (threadIdx.x == 0) s_cinv = dst;
-    } else if (threadIdx.x == 0) {
-      s_cinv = P.cinv;
+      s_cinv = staged ? dst : P.cinv;
     }
-    __syncthreads();                            // shared-memory descriptors published
   }
+  if (use_dsm)
+    for (int l = Ss + 1; l <= top; ++l) dsm_level_setup<Pol>(gd[l], cv[l], smem, &off, l, rank, csize, Ss, &s_bar);
+  if (threadIdx.x == 0) mbar_arrive(&s_bar);   // all constant-data copies issued
+  fence_proxy_async();                          // the zeroed vectors before later bulk copies into them
+  __syncthreads();                              // shared-memory descriptors published
   pdl_wait();
+  // a copy that does not land in time (it always does) sets the error word; the block still
+  // waits, bounded, before it reads the data or exits
+  auto wait_copies = [&](unsigned parity) {
+    if (!mbar_wait(&s_bar, parity)) {
+      if (threadIdx.x == 0) atomicExch(E.err, 1);
+      (void)mbar_wait(&s_bar, parity);
+    }
+  };
   const ProbState& st = E.S[p];
   if (st.phase != want) {
-    if (rank == 0) cp_async_wait();               // no copy outlives the block
+    wait_copies(0);                             // no copy outlives the block
     return;
   }
   const int pre = E.prm.pre, post = E.prm.post;
@@ -1164,19 +1382,48 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
   const bool zero_top = st.zero_top;
   ProbState* stw = E.S + p;
   double* check_part = E.partial + E.fine_off[p];   // used on the problem's own finest level
-  // cluster part, down
+  // the distributed path needs no residual check on a cluster level (only the top one can be the
+  // problem's own finest level); otherwise the cluster levels run over L2
+  const bool dsm_ok = use_dsm && !(top == P.L && !zero_top);
+  // block 0's level Ss as seen from any block of the cluster
+  LevelDev c0 = sd[Ss];
+  c0.rhs = cl.map_shared_rank(static_cast<V*>(sd[Ss].rhs), 0);
+  c0.x[0] = cl.map_shared_rank(static_cast<V*>(sd[Ss].x[0]), 0);
   const int w0 = rank * wpb + (threadIdx.x >> 5), nw = csize * wpb;
-  for (int l = top; l > Ss; --l) {
-    const bool chk = (l == P.L) && !zero_top;
-    if (!vcycle_down_level<Pol, LD_CG>(gd[l], gd[l - 1], l, (P.L > l) || zero_top, pre, omega, w0, nw,
-                                       lane, true, chk ? check_part : nullptr, stw, E.prm, want, rank, sh)) {
-      if (rank == 0) cp_async_wait();
-      return;                                   // converged at the lagged check: cluster-uniform
+  if (dsm_ok) {
+    wait_copies(0);                             // the next phase of bar may start only now
+    {   // right-hand side of the top level: own and ghost rows
+      const LevelDev& g = gd[top];
+      const long long n = (1LL << top) + 1;
+      const long long g0 = dsm_vec_start<V>(top, rank, csize, Ss);
+      const long long R1n = (long long)part_row(top, rank + 1, csize, Ss) * n;
+      constexpr int av = 16 / (int)sizeof(V);
+      const int chunks = (int)((R1n + n + 1 - g0 + av - 1) / av);
+      V* dst = static_cast<V*>(cv[top].rhs) + g0;
+      const V* src = static_cast<const V*>(g.rhs) + g0;
+      if (threadIdx.x == 0) {
+        bulk_copy(dst, src, (unsigned)chunks * 16u, &s_bar);
+        mbar_arrive(&s_bar);
+      }
+    }
+    wait_copies(1);
+    __syncthreads();
+    cl.sync();                                  // every block's arrays are ready for its neighbours
+    for (int l = top; l > Ss; --l) dsm_down<Pol>(cv, c0, l, rank, csize, Ss, true, pre, omega);
+  } else {
+    wait_copies(0);
+    // cluster part over L2, down
+    for (int l = top; l > Ss; --l) {
+      const bool chk = (l == P.L) && !zero_top;
+      if (!vcycle_down_level<Pol, LD_CG>(gd[l], gd[l - 1], l, (P.L > l) || zero_top, pre, omega, w0, nw,
+                                         lane, true, chk ? check_part : nullptr, stw, E.prm, want, rank, sh))
+        return;                                 // converged at the lagged check: cluster-uniform
     }
   }
   // block 0: levels coarse..Ss in shared memory, one thread per node
   if (rank == 0) {
-    {   // inputs of level Ss: restricted rhs (or the top rhs), and the iterate if it is nonzero
+    if (!(dsm_ok && top > Ss)) {
+      // inputs of level Ss: restricted rhs (or the top rhs), and the iterate if it is nonzero
       const LevelDev& g = gd[Ss];
       const LevelDev& s = sd[Ss];
       const bool nonzero = (Ss == P.L) && !zero_top;
@@ -1186,8 +1433,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
         if (nonzero) cp_async16(static_cast<uint4*>(s.x[0]) + q, static_cast<const uint4*>(g.x[0]) + q);
       }
       cp_async_wait();
-      __syncthreads();
     }
+    __syncthreads();
     bool go = true;
     for (int l = Ss; l > c && go; --l) {
       const bool chk = (l == P.L) && !zero_top;
@@ -1229,7 +1476,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
       }
       __syncthreads();
       for (int l = c + 1; l <= Ss; ++l) vcycle_up_smem<Pol>(sd[l], sd[l - 1], pre, post, omega);
-      {   // the iterate of level Ss back to global memory
+      if (!dsm_ok) {   // the iterate of level Ss back to global memory
         const LevelDev& g = gd[Ss];
         const LevelDev& s = sd[Ss];
         const int chunks = (int)(g.pitch * sizeof(V) / 16);
@@ -1239,9 +1486,20 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
     }
   }
   cl.sync();
-  // cluster part, up
-  for (int l = Ss + 1; l <= top; ++l)
-    vcycle_up_level<Pol, LD_CG>(gd[l], gd[l - 1], l, pre, post, omega, w0, nw, lane, true);
+  if (dsm_ok) {
+    for (int l = Ss + 1; l <= top; ++l) dsm_up<Pol>(cv, c0, sd[Ss], l, rank, csize, Ss, pre, post, omega);
+    // the top level's iterate (own rows) back to global memory
+    const long long n = (1LL << top) + 1;
+    const long long R0n = (long long)part_row(top, rank, csize, Ss) * n;
+    const long long R1n = (long long)part_row(top, rank + 1, csize, Ss) * n;
+    const V* xs = static_cast<const V*>(cv[top].x[0]);
+    V* xg = static_cast<V*>(gd[top].x[0]);
+    for (long long i = R0n + threadIdx.x; i < R1n; i += blockDim.x) xg[i] = xs[i];
+  } else {
+    // cluster part over L2, up
+    for (int l = Ss + 1; l <= top; ++l)
+      vcycle_up_level<Pol, LD_CG>(gd[l], gd[l - 1], l, pre, post, omega, w0, nw, lane, true);
+  }
 }
 
 // FP64 outer defect of the defect correction: d = b - A x (FP64 bands, FP64 x), written to the
@@ -1612,7 +1870,8 @@ cudaError_t launch_pre2b(const EngineDev& E, TileList tl, int level, int want, i
 bool pre_fuses(int) { return true; }
 
 // shared memory the fused coarse-level kernel may use for levels coarse..S
-constexpr long long kTailSmemBudget = 160 * 1024;
+constexpr long long kTailSmemBudget = 160 * 1024;   // block 0's shared-memory levels
+constexpr long long kTailSmemMax = 212 * 1024;      // with the cluster levels (dynamic part)
 
 int tail_smem_level(int prec, int coarse, int T) {
   const long long ni = (1LL << coarse) - 1;
@@ -1631,7 +1890,16 @@ long long tail_smem_bytes(int prec, int coarse, int S) {
   for (int l = coarse; l <= S; ++l) bytes += smem_level_bytes(l, prec);
   const long long ni = (1LL << coarse) - 1;
   const long long cinv = ni * ni * ni * ni * 8;
-  return bytes + (cinv <= kCinvSmemMax ? cinv : 0);     // the coarse inverse, when staged
+  return bytes + (cinv <= kCinvSmemMax ? (cinv + 15) / 16 * 16 : 0);   // the coarse inverse, when staged
+}
+
+// shared memory of the cluster levels (S, T] in distributed shared memory, or -1 if they do not
+// fit (or the partition would leave a block without rows; C must be a power of two)
+long long tail_dsm_bytes(int prec, int coarse, int S, int T, int C) {
+  if (T <= S || (1 << (S + 1)) < C || (C & (C - 1)) != 0) return -1;
+  long long bytes = tail_smem_bytes(prec, coarse, S);
+  for (int l = S + 1; l <= T; ++l) bytes += dsm_level_bytes(l, C, S, prec);
+  return bytes <= kTailSmemMax ? bytes : -1;
 }
 
 // clusters of up to 16 blocks need the non-portable opt-in, the shared-memory levels a larger
@@ -1640,7 +1908,7 @@ cudaError_t prepare_kernels() {
   cudaError_t e = cudaSuccess;
   auto set = [&](const void* f) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBudget);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
   };
   set(reinterpret_cast<const void*>(k_tail<F64>));
   set(reinterpret_cast<const void*>(k_tail<F32>));
@@ -1666,8 +1934,10 @@ cudaError_t prepare_kernels() {
 template <class Pol>
 cudaError_t launch_tail_t(const EngineDev& E, int T, int want, int cluster, cudaStream_t s) {
   const int S = tail_smem_level(Pol::prec, E.prm.coarse, T);
-  const size_t smem = (size_t)tail_smem_bytes(Pol::prec, E.prm.coarse, S);
-  return launch_kt(k_tail<Pol>, E.nprob * cluster, kTailThreads, smem, s, E.pdl, cluster, E, T, S, want);
+  const long long dsm = E.dsm ? tail_dsm_bytes(Pol::prec, E.prm.coarse, S, T, cluster) : -1;
+  const size_t smem = (size_t)(dsm > 0 ? dsm : tail_smem_bytes(Pol::prec, E.prm.coarse, S));
+  return launch_kt(k_tail<Pol>, E.nprob * cluster, kTailThreads, smem, s, E.pdl, cluster, E, T, S, want,
+                   dsm > 0 ? 1 : 0);
 }
 
 cudaError_t launch_tail(const EngineDev& E, int T, int want, int cluster, cudaStream_t s) {

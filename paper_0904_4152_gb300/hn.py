@@ -68,7 +68,7 @@ class ServerInfo(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tail_level", ctypes.c_int), ("cluster", ctypes.c_int), ("pdl", ctypes.c_int),
-                ("staged", ctypes.c_int)]
+                ("staged", ctypes.c_int), ("dsm", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -324,14 +324,14 @@ def hn_mg_kernel_times(mg, max_entries=256):
             for i in range(n)]
 
 
-def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0):
-    _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl, staged))))
+def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0, dsm=1):
+    _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl, staged, dsm))))
 
 
 def hn_mg_get_tuning(mg):
     t = Tuning()
     _check(lib().hn_mg_get_tuning(mg, ctypes.byref(t)))
-    return t.tail_level, t.cluster, t.pdl, t.staged
+    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm
 
 
 def hn_mg_autotune(mg, b, reps=3, coarse_L=2):
