@@ -22,7 +22,7 @@ typedef struct {
   int cluster;      /* blocks per cluster of the fused launch: 1, 2, 4, 8 or 16 */
   int pdl;          /* programmatic dependent launch (a kernel launches while its predecessor
                        runs and waits for its results): 0 off, 1 every kernel, 2 kernels of
-                       fewer blocks than SMs only */
+                       fewer blocks than SMs only, 3 fewer blocks than twice the SMs */
   int staged;       /* 1: the band kernels of large FP32 / FP16 levels stream the bands through
                        shared memory with bulk copies (TMA engine) on mbarriers; 0: register path */
   int dsm;          /* 1: the fused launch keeps its cluster levels in distributed shared memory

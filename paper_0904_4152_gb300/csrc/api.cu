@@ -415,7 +415,7 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
   if (t->tail_level < mg->coarse || t->tail_level > HN_MAX_LEVEL || !(c == 1 || c == 2 || c == 4 || c == 8 || c == 16))
     return set_error(HN_ERR_ARG, "tail_level in [coarse_L, %d], cluster in {1,2,4,8,16}", HN_MAX_LEVEL);
   HN_TRY(ensure_solo(mg));
-  if (t->pdl < 0 || t->pdl > 2) return set_error(HN_ERR_ARG, "pdl must be 0, 1 or 2");
+  if (t->pdl < 0 || t->pdl > 3) return set_error(HN_ERR_ARG, "pdl must be 0, 1, 2 or 3");
   if (t->staged != 0 && t->staged != 1) return set_error(HN_ERR_ARG, "staged must be 0 or 1");
   if (t->dsm != 0 && t->dsm != 1) return set_error(HN_ERR_ARG, "dsm must be 0 or 1");
   Tuning tu;

@@ -610,7 +610,7 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
   int c0 = 0;
   // inside the closed-world loop the rest of the cycle after the first lagged check is an IF body
   auto after_check = [&]() -> hn_status {
-    if (!condCapture_ || opened) return HN_OK;
+    if (!cond_on(0) || opened) return HN_OK;
     HN_TRY(open_if(s, 0));
     opened = true;
     c0 = counting_;
@@ -665,20 +665,20 @@ hn_status Engine::issue_iteration(cudaStream_t s0, cudaGraphConditionalHandle h,
   if (prm_.prec == P64) {
     HN_TRY(issue_vcycle(s, PH_CYCLE));
   } else {
-    if (condCapture_) HN_TRY(open_if(s, 1));
+    if (cond_on(1)) HN_TRY(open_if(s, 1));
     int c0 = counting_;
     HN_LAUNCH(KC_OUTER_DEFECT, -1, launch_outer_defect(E_, fine_, fineGrid_, s));
     HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_OUTER, s));
-    if (condCapture_) {
+    if (cond_on(1)) {
       E_.prm.cond.n_outer = (unsigned)(counting_ - c0);
       HN_TRY(close_if(s, s0));
     }
     HN_TRY(issue_vcycle(s, PH_INNER));
-    if (condCapture_) HN_TRY(open_if(s, 2));
+    if (cond_on(2)) HN_TRY(open_if(s, 2));
     c0 = counting_;
     HN_LAUNCH(KC_UPDATE, -1, launch_update(E_, fine_, fineGrid_, s));
     HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_POST, s));
-    if (condCapture_) {
+    if (cond_on(2)) {
       E_.prm.cond.n_update = (unsigned)(counting_ - c0);
       HN_TRY(close_if(s, s0));
     }
@@ -773,11 +773,12 @@ hn_status Engine::capture_solve(bool cond) {
   HN_CUDA(cudaGraphConditionalHandleCreate(&h, main, 1, cudaGraphCondAssignDefault));
   CondDev cd{};
   if (cond) {
-    // IF handles: the cycle's rest (only when a lagged check precedes it), outer defect and
-    // update (defect correction); the outer defect runs in the first iteration
+    // An IF node costs about as much as several launches (measured: ~2 us skipped, ~5 us
+    // taken), so only the rest of a V cycle after the lagged check gets one, and only in the
+    // defect correction, where every outer step ends with one cycle that its check stops.  (The
+    // outer defect and the update would each skip two small launches: not worth an IF node.)
     const int T = std::max(tune_.tail_level, prm_.coarse);
-    if (Lmax_ > T) cd.mask |= 1u;
-    if (prm_.prec != P64) cd.mask |= 6u;
+    if (Lmax_ > T && prm_.prec != P64) cd.mask |= 1u;
     const unsigned defaults[3] = {0u, 1u, 0u};
     for (int w = 0; w < 3; ++w)
       if ((cd.mask >> w) & 1u)

@@ -157,6 +157,7 @@ class Engine {
   hn_status open_if(cudaStream_t& s, int which);
   hn_status close_if(cudaStream_t& s, cudaStream_t outer);
   hn_status capture_solve(bool cond);
+  bool cond_on(int which) const { return condCapture_ && ((E_.prm.cond.mask >> which) & 1u); }
   int grid_for(long long tiles) const;
   hn_status mark(cudaStream_t s, int cls, int level, bool begin);
   void destroy_graphs();

@@ -562,9 +562,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // One warp-tile per loop trip over the work list.  level < 0: each problem's own finest level.
 // Resident blocks per SM asked of the register allocator.  The streaming modes keep 5 blocks
 // (40 warps) of FP32 (FP16 for SpMV/defect) loads in flight, enough to saturate HBM; the fused
-// pre-smoothing and check modes run once per cycle and get more registers per thread.
+// pre-smoothing (4 blocks) and check modes run once per cycle and get more registers per thread.
 template <class Pol, int MODE> constexpr int band_min_blocks() {
-  if (MODE == M_CHECK || MODE == M_PRE12) return Pol::prec == P64 ? 2 : 3;
+  if (MODE == M_CHECK) return Pol::prec == P64 ? 2 : 3;
+  if (MODE == M_PRE12) return Pol::prec == P64 ? 2 : 4;
   if (Pol::prec == P32) return 5;
   if (Pol::prec == P16) return (MODE == M_SPMV || MODE == M_DEFECT) ? 5 : 4;
   return 4;
@@ -1782,8 +1783,9 @@ cudaError_t launch_kt(void (*kern)(KArgs...), int grid, int threads, size_t smem
   cudaLaunchAttribute attr[2];
   int na = 0;
   // pdl: 1 = every launch; 2 = launches of fewer blocks than SMs (their waiting blocks do not
-  // take occupancy from a bandwidth-bound predecessor)
-  if (pdl == 1 || (pdl == 2 && grid_or_one(grid) < sm_count())) {
+  // take occupancy from a bandwidth-bound predecessor); 3 = fewer blocks than twice the SMs
+  if (pdl == 1 || (pdl == 2 && grid_or_one(grid) < sm_count()) ||
+      (pdl == 3 && grid_or_one(grid) < 2 * sm_count())) {
     attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[na].val.programmaticStreamSerializationAllowed = 1;
     ++na;

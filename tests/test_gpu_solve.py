@@ -244,9 +244,9 @@ def test_profiling_times_kernels_without_changing_results(hn):
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("L", [6, 9])
 def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L):
-    # the one-launch solve skips, through IF nodes, the parts of an iteration no problem is in
-    # (outer defect, update, the rest of a cycle after a converged lagged check); the host-driven
-    # iterations (profiling) run every kernel of every iteration
+    # the one-launch solve of the defect correction skips, through an IF node, the rest of a V
+    # cycle after a lagged check that ends the inner solve (levels above the fused tail only);
+    # the host-driven iterations (profiling) run every kernel of every iteration
     coef, b = I.batch_problem(5, L)
     A = hn.hn_band_create(L, coef)
     mg = hn.hn_mg_setup(A, prec=prec)
@@ -263,7 +263,7 @@ def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L):
         for k in ("cycles", "outer_iters", "inner_cycles", "relres"):
             assert st0[k] == st1[k], k
         assert 0 < n_loop <= n_host
-        if prec != 0:
+        if prec != 0 and L > hn.hn_mg_get_tuning(mg)[0]:
             assert n_loop < n_host
         # a second solve counts its own launches again
         hn.hn_mg_solve(mg, L, b)
