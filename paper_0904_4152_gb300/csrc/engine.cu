@@ -528,17 +528,18 @@ long long Engine::launch_bytes(int cls, int level) const {
   return (long long)(per * (double)nodes);
 }
 
+// events around one launch of a profiled (directly issued) iteration
 hn_status Engine::mark(cudaStream_t s, int cls, int level, bool begin) {
   if (!profiling_) return HN_OK;
   if (begin) {
     cudaEvent_t e;
     HN_CUDA(cudaEventCreate(&e));
-    HN_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    HN_CUDA(cudaEventRecord(e, s));
     openBegin_.push_back(e);
   } else {
     cudaEvent_t e;
     HN_CUDA(cudaEventCreate(&e));
-    HN_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    HN_CUDA(cudaEventRecord(e, s));
     Mark m{openBegin_.back(), e, cls, level, launch_bytes(cls, level)};
     openBegin_.pop_back();
     marks_.push_back(m);
@@ -693,23 +694,24 @@ hn_status Engine::issue_iteration(cudaStream_t s0, cudaGraphConditionalHandle h,
 
 hn_status Engine::capture_graphs() {
   destroy_graphs();
-  for (auto& m : marks_) { cudaEventDestroy(m.b); cudaEventDestroy(m.e); }
-  marks_.clear();
+  clear_marks();
   cudaStream_t cs;
   HN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } guard{cs};
+  // graphs carry no profiling events (profiled iterations are issued directly)
+  struct Guard {
+    cudaStream_t s; bool& prof; bool saved;
+    ~Guard() { cudaStreamDestroy(s); prof = saved; }
+  } guard{cs, profiling_, profiling_};
+  profiling_ = false;
   const cudaGraphConditionalHandle none = 0;
-  // host-driven pieces: init and one iteration (events only in the iteration graph)
+  // host-driven pieces: init and one iteration
   {
-    const bool prof = profiling_;
-    profiling_ = false;
     cudaGraph_t g;
     HN_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     counting_ = 0;
     hn_status st = issue_init(cs, none, 0);
     initLaunches_ = counting_;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
-    profiling_ = prof;
     HN_TRY(st);
     HN_CUDA(e);
     e = cudaGraphInstantiate(&gInit_, g, 0);
@@ -729,9 +731,9 @@ hn_status Engine::capture_graphs() {
     cudaGraphDestroy(g);
     HN_CUDA(e);
   }
-  // closed-world solve: init, then while (any problem running) { iteration }, with IF nodes
-  // that skip the parts of an iteration no problem is in; the flat loop if those do not build
-  if (!profiling_) {
+  // closed-world solve: init, then while (any problem running) { iteration }, with the IF node
+  // that skips the rest of a cycle no problem is in; the flat loop if that does not build
+  {
     hn_status st = capture_solve(true);
     if (st != HN_OK) {
       cudaGetLastError();
@@ -825,7 +827,6 @@ hn_status Engine::capture_solve(bool cond) {
 }
 
 hn_status Engine::run_to_completion() {
-  if (!graphsValid_) HN_TRY(capture_graphs());
   if (profiling_) {
     HN_TRY(run_init());
     lastLaunches_ = initLaunches_;
@@ -838,6 +839,7 @@ hn_status Engine::run_to_completion() {
     }
     return HN_OK;
   }
+  if (!graphsValid_) HN_TRY(capture_graphs());
   HN_CUDA(cudaGraphLaunch(gSolve_, s_));
   unsigned iters = 0;
   unsigned long long body = 0;
@@ -851,19 +853,44 @@ hn_status Engine::run_to_completion() {
   return HN_OK;
 }
 
+// With profiling on, iterations are issued directly to the stream (every kernel between its
+// own events, and visible to a profiler, which does not profile graph kernels that may set a
+// conditional value); otherwise the captured init / iteration graphs run.
 hn_status Engine::run_init() {
+  if (profiling_) {
+    counting_ = 0;
+    HN_TRY(issue_init(s_, 0, 0));
+    initLaunches_ = counting_;
+    return HN_OK;
+  }
   if (!graphsValid_) HN_TRY(capture_graphs());
   HN_CUDA(cudaGraphLaunch(gInit_, s_));
   return HN_OK;
 }
 
 hn_status Engine::run_iteration(unsigned* active_out) {
-  if (!graphsValid_) HN_TRY(capture_graphs());
-  HN_CUDA(cudaGraphLaunch(gIter_, s_));
-  HN_CUDA(cudaStreamSynchronize(s_));
-  if (profiling_) HN_TRY(accumulate_marks());
+  if (profiling_) {
+    clear_marks();
+    counting_ = 0;
+    HN_TRY(issue_iteration(s_, 0, 0));
+    iterLaunches_ = counting_;
+    HN_CUDA(cudaStreamSynchronize(s_));
+    HN_TRY(accumulate_marks());
+    clear_marks();
+  } else {
+    if (!graphsValid_) HN_TRY(capture_graphs());
+    HN_CUDA(cudaGraphLaunch(gIter_, s_));
+    HN_CUDA(cudaStreamSynchronize(s_));
+  }
   if (active_out) *active_out = *reinterpret_cast<volatile unsigned*>(hActive_);
   return HN_OK;
+}
+
+void Engine::clear_marks() {
+  for (auto& m : marks_) { cudaEventDestroy(m.b); cudaEventDestroy(m.e); }
+  marks_.clear();
+  for (auto& e : openBegin_) cudaEventDestroy(e);
+  openBegin_.clear();
 }
 
 hn_status Engine::accumulate_marks() {

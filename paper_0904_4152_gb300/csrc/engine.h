@@ -26,10 +26,10 @@ const char* last_error();
                              __LINE__);                                                  \
   } while (0)
 
-#define HN_TRY(expr)                      \
-  do {                                    \
-    hn_status s_ = (expr);                \
-    if (s_ != HN_OK) return s_;           \
+#define HN_TRY(expr)                                    \
+  do {                                                  \
+    const hn_status hn_try_status_ = (expr);            \
+    if (hn_try_status_ != HN_OK) return hn_try_status_; \
   } while (0)
 
 inline long long now_ns() {
@@ -157,6 +157,7 @@ class Engine {
   hn_status open_if(cudaStream_t& s, int which);
   hn_status close_if(cudaStream_t& s, cudaStream_t outer);
   hn_status capture_solve(bool cond);
+  void clear_marks();
   bool cond_on(int which) const { return condCapture_ && ((E_.prm.cond.mask >> which) & 1u); }
   int grid_for(long long tiles) const;
   hn_status mark(cudaStream_t s, int cls, int level, bool begin);
