@@ -455,6 +455,23 @@ hn_status Engine::set_members(const std::vector<hn_mg*>& slots) {
   HN_CUDA(cudaMemcpyAsync(dCounts_, hCounts_.data(), hCounts_.size() * sizeof(int), cudaMemcpyHostToDevice, s_));
   HN_CUDA(cudaMemcpyAsync(dFineOff_, fine_off.data(), fine_off.size() * sizeof(int), cudaMemcpyHostToDevice, s_));
   HN_CUDA(cudaMemcpyAsync(dP_, probs.data(), sizeof(ProblemDev) * cap_, cudaMemcpyHostToDevice, s_));
+  // an engine of one problem passes its descriptors to the kernels by value (captured into its
+  // graphs, which therefore must be captured again when its member changes)
+  if (cap_ == 1) graphsValid_ = false;
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    TileList& t = lists_[l];
+    t.solo_tiles = 0;
+    t.solo_L = 0;
+    t.solo_d = t.solo_c = t.solo_f = LevelDev{};
+    if (cap_ != 1 || slots.empty() || !slots[0]) continue;
+    const ProblemDev& P = slots[0]->host;
+    if (l < P.coarse || l > P.L) continue;
+    t.solo_tiles = (int)(pitch_of(l) / kTile);
+    t.solo_L = P.L;
+    t.solo_d = P.lev[l];
+    if (l > P.coarse) t.solo_c = P.lev[l - 1];
+    if (l < P.L) t.solo_f = P.lev[l + 1];
+  }
   members_ = slots;
   members_.resize(cap_, nullptr);
   unsigned mask = 0;

@@ -116,6 +116,13 @@ struct TileList {
   const int4* chunks = nullptr;
   const int* chunk_count = nullptr;
   int chunk_cap = 0;        // host side: capacity of the chunk list
+  // an engine of one problem also passes that problem's descriptors by value, so its kernels
+  // start on the data without first loading the work list and the descriptor: solo_tiles > 0
+  // tiles of level solo_d.L (solo_c: the next coarser level, solo_f: the next finer one), the
+  // problem's finest level solo_L, problem slot 0
+  int solo_tiles = 0;
+  int solo_L = 0;
+  LevelDev solo_d{}, solo_c{}, solo_f{};
 };
 constexpr int kChunkTiles = 8;
 

@@ -580,8 +580,22 @@ __global__ void __launch_bounds__(256, band_min_blocks<Pol, MODE>()) k_band(Engi
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-  const int count = *tl.count;
   const A omega = A(E.prm.omega);
+  if (tl.solo_tiles > 0 && level >= 0) {          // one problem: descriptors by value
+    const ProbState& st = E.S[0];
+    if (st.phase != want) return;
+    const bool zg = (tl.solo_L > level) || st.zero_top;
+    for (int t = gw; t < tl.solo_tiles; t += nw) {
+      double* slot = nullptr;
+      if constexpr (MODE == M_CHECK) slot = E.partial + t;
+      if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST)
+        if (level == tl.solo_L && !zg) slot = E.partial + t;
+      band_tile<Pol, MODE, LD_NC>(tl.solo_d, 1LL << level, zg, (long long)t * kTile + lane * kLaneNodes,
+                                  lane, in_sel, omega, slot);
+    }
+    return;
+  }
+  const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
     const int p = it.x;
@@ -707,6 +721,12 @@ __global__ void __launch_bounds__(256) k_restrict(EngineDev E, TileList tl, int 
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  if (tl.solo_tiles > 0) {                        // one problem: tl is the coarse level's list
+    if (tl.solo_L < fine_level || E.S[0].phase != want) return;   // (no finer level: no descriptor)
+    for (int t = gw; t < tl.solo_tiles; t += nw)
+      restrict_tile<V, LD_NC>(tl.solo_f, tl.solo_d, (long long)t * kTile + lane * kLaneNodes);
+    return;
+  }
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
@@ -725,6 +745,12 @@ __global__ void __launch_bounds__(256) k_prolong(EngineDev E, TileList tl, int l
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  if (tl.solo_tiles > 0) {                        // one problem: descriptors by value
+    if (tl.solo_c.n == 0 || E.S[0].phase != want) return;   // (no coarser level: nothing to add)
+    for (int t = gw; t < tl.solo_tiles; t += nw)
+      prolong_tile<V, LD_NC>(tl.solo_d, tl.solo_c, x_sel, (long long)t * kTile + lane * kLaneNodes);
+    return;
+  }
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];

@@ -198,8 +198,11 @@ def test_batch_alone_equals_in_mix(hn, prec):
             hn.hn_mg_destroy(m)
 
 
-def test_server_results_match_alone(hn):
-    srv = hn.hn_server_create(2 << 30, 4)
+@pytest.mark.parametrize("slots", [4, 1])
+def test_server_results_match_alone(hn, slots):
+    # one slot: the engine of one problem passes descriptors by value and recaptures its graphs
+    # whenever the member changes
+    srv = hn.hn_server_create(2 << 30, slots)
     try:
         reqs = []
         for j, L in enumerate([6, 8, 5, 7, 6, 9, 4]):
