@@ -223,14 +223,26 @@ __device__ double block_sum256(double v, double* sh) {
   return t;   // valid in warp 0
 }
 
-// Fixed-order sum of one problem's per-tile partials by one block of 256 threads (thread t adds
-// slots t, t+256, ... in order, then the block tree).  Every caller uses this order, so a
-// problem's norm does not depend on which kernel or batch computed it.  Valid in thread 0.
+// Fixed-order sum of one problem's per-tile partials by one block of 256 threads: thread t adds
+// slots t + 256 (4j + c) into chain c = 0..3 (in order of j), then (c0 + c1) + (c2 + c3), then
+// the block tree.  Every caller uses this order, so a problem's norm does not depend on which
+// kernel or batch computed it.  (Four chains: a dependent FP64 add costs ~64 cycles here.)
+// Valid in thread 0.
 __device__ double problem_partial_sum(const double* part, int ntiles, double* sh) {
-  double t = 0.0;
-  if (threadIdx.x < 256)                      // larger blocks: the other threads add +0.0
-    for (int q = threadIdx.x; q < ntiles; q += 256) t += __ldcg(part + q);
-  return block_sum256(t, sh);
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+  if (threadIdx.x < 256) {                    // larger blocks: the other threads add +0.0
+    int q = threadIdx.x;
+    for (; q + 3 * 256 < ntiles; q += 4 * 256) {
+      c0 += __ldcg(part + q);
+      c1 += __ldcg(part + q + 256);
+      c2 += __ldcg(part + q + 512);
+      c3 += __ldcg(part + q + 768);
+    }
+    if (q < ntiles) c0 += __ldcg(part + q);
+    if (q + 256 < ntiles) c1 += __ldcg(part + q + 256);
+    if (q + 512 < ntiles) c2 += __ldcg(part + q + 512);
+  }
+  return block_sum256((c0 + c1) + (c2 + c3), sh);
 }
 
 __host__ __device__ inline int fine_tiles(int L) {
@@ -480,6 +492,25 @@ __device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& 
   st4(x + i0, v);
 }
 
+// One row of the coarse inverse times the coarse right-hand side: four interleaved FP64 chains
+// (v mod 4), then (a0 + a1) + (a2 + a3); a dependent FP64 operation costs ~64 cycles on this part,
+// so one chain of m would dominate the coarse solve.  rd(v) gives the v-th interior rhs in FP64.
+template <class F>
+__device__ __forceinline__ double coarse_dot(const double* row, int m, F rd) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int v = 0;
+  for (; v + 3 < m; v += 4) {
+    a0 = fma(row[v], rd(v), a0);
+    a1 = fma(row[v + 1], rd(v + 1), a1);
+    a2 = fma(row[v + 2], rd(v + 2), a2);
+    a3 = fma(row[v + 3], rd(v + 3), a3);
+  }
+  if (v < m) a0 = fma(row[v], rd(v), a0);
+  if (v + 1 < m) a1 = fma(row[v + 1], rd(v + 1), a1);
+  if (v + 2 < m) a2 = fma(row[v + 2], rd(v + 2), a2);
+  return (a0 + a1) + (a2 + a3);
+}
+
 // Exact coarsest-level solve x_c = A_c^-1 rhs_c (precomputed FP64 inverse of the interior block)
 // by one warp; result into buffer 0.  sol: m doubles of shared memory.
 template <class V, int LK>
@@ -489,9 +520,7 @@ __device__ __forceinline__ void coarse_warp(const ProblemDev& P, int lane, doubl
   const V* rhs = static_cast<const V*>(d.rhs);
   for (int u = lane; u < m; u += 32) {
     const double* row = P.cinv + (long long)u * m;
-    double s = 0.0;
-    for (int v = 0; v < m; ++v) s = fma(row[v], double(ld1<LK>(rhs + (v / ni + 1) * n + (v % ni + 1))), s);
-    sol[u] = s;
+    sol[u] = coarse_dot(row, m, [&](int v) { return double(ld1<LK>(rhs + (v / ni + 1) * n + (v % ni + 1))); });
   }
   __syncwarp();
   V* x = static_cast<V*>(d.x[0]);
@@ -1339,6 +1368,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
   __shared__ LevelDev sd[kMaxLevel + 1];       // shared-memory levels coarse..S (block 0's data)
   __shared__ LevelDev cv[kMaxLevel + 1];       // this block's rows of the cluster levels
   __shared__ double sol[kMaxCoarseM];
+  __shared__ double rd[kMaxCoarseM];          // coarse right-hand side in FP64
   __shared__ double sh[32];
   __shared__ const double* s_cinv;
   __shared__ __align__(8) unsigned long long s_bar;   // bulk copies: phase 0 constant data, 1 inputs
@@ -1487,12 +1517,10 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
       const int n = d.n, ni = n - 2;
       const V* rhs = static_cast<const V*>(d.rhs);
       const double* cinv = s_cinv;
-      for (int u = threadIdx.x; u < m; u += blockDim.x) {
-        const double* row = cinv + u * m;
-        double sacc = 0.0;
-        for (int v = 0; v < m; ++v) sacc = fma(row[v], double(rhs[(v / ni + 1) * n + (v % ni + 1)]), sacc);
-        sol[u] = sacc;
-      }
+      for (int v = threadIdx.x; v < m; v += blockDim.x) rd[v] = double(rhs[(v / ni + 1) * n + (v % ni + 1)]);
+      __syncthreads();
+      for (int u = threadIdx.x; u < m; u += blockDim.x)
+        sol[u] = coarse_dot(cinv + u * m, m, [&](int v) { return rd[v]; });
       __syncthreads();
       V* x = static_cast<V*>(d.x[0]);
       for (int q = threadIdx.x; q < d.pitch; q += blockDim.x) {
@@ -1672,9 +1700,7 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
     const int L = E.P[p].L;
     const int ntiles = (int)(((n_of_dev(L) * n_of_dev(L)) + kTile - 1) / kTile);
     const int off = E.fine_off[p];
-    double t = 0.0;
-    for (int q = threadIdx.x; q < ntiles; q += blockDim.x) t += part[off + q];
-    sum = block_sum256(t, sh);
+    sum = problem_partial_sum(part + off, ntiles, sh);
   }
   if (threadIdx.x != 0) return;
   const Params& prm = E.prm;
