@@ -225,7 +225,7 @@ def test_server_results_match_alone(hn, slots):
 
 
 def test_profiling_times_kernels_without_changing_results(hn):
-    L = 8
+    L = 9                  # levels 9 and 8 above the tail: separate restriction and prolongation
     b = I.rhs_uniform(L, 21)
     A = hn.hn_band_create(L)
     mg = hn.hn_mg_setup(A, prec=1)
