@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--host-loop", action="store_true",
                     help="run solves as one graph launch per iteration (ncu cannot profile kernels "
                          "inside the device-side loop)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve", "kernels"],
+    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve", "kernels", "blas1"],
                     help="solve: the L=10 benchmark (default); batch: 256 uneven problems in one "
                          "batched solve; serve: Poisson-arrival requests through the solve server; "
                          "kernels: band-SpMV / defect / Jacobi alone at L=12 in FP64, FP32, FP16-band")
@@ -234,6 +234,46 @@ def run_kernels(args, rank, local):
     if rank == 0:
         print(json.dumps({"metric": "band kernels alone, HBM GB/s", "peak": peak, "peak_kind": kind,
                           "kernels": band}), flush=True)
+
+
+def run_blas1(args, rank, local):
+    """BLAS level-1 kernels (Sec. 6.1, Fig. 2): axpy / dot rate against vector length."""
+    import torch
+    import __graft_entry__ as g
+    from paper_0904_4152_gb300 import hn
+    torch.cuda.set_device(local)
+    g.build()
+    peak, kind = measured_peak_gbs()
+    stream = torch.cuda.current_stream()
+    rows = []
+    for dtype, name in ((torch.float32, "f32"), (torch.float64, "f64")):
+        esize = 4 if dtype == torch.float32 else 8
+        for lg in range(10, 29, 2):
+            n = 1 << lg
+            x = torch.rand(n, dtype=dtype, device="cuda")
+            y = torch.rand(n, dtype=dtype, device="cuda")
+            r = torch.zeros(1, dtype=torch.float64, device="cuda")
+            for op in ("axpy", "dot"):
+                call = (lambda: hn.hn_axpy(1e-9, x, y, stream)) if op == "axpy" else (lambda: hn.hn_dot(x, y, r, stream))
+                for _ in range(3):
+                    call()
+                reps = max(5, min(2000, int(2e8 / (n * esize))))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(reps):
+                    call()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                us = e0.elapsed_time(e1) * 1e3 / reps
+                nbytes = (3 if op == "axpy" else 2) * n * esize
+                rows.append({"op": op, "type": name, "n": n, "us": us, "gb_per_s": nbytes / us / 1e3,
+                             "mflop_per_s": 2 * n / us, "in_l2": nbytes < 120e6,
+                             "frac_hbm": nbytes / us / 1e3 / peak})
+            del x, y
+    if rank == 0:
+        print(json.dumps({"metric": "BLAS-1 axpy / dot rate vs length (HBM GB/s, MFLOP/s)", "peak": peak,
+                          "peak_kind": kind, "rows": rows}), flush=True)
 
 
 def run_ours(args, rank, world, local, pg):
@@ -591,6 +631,8 @@ def main():
         run_batch(args, rank, world, local, pg)
     elif args.workload == "serve":
         run_serve(args, rank, world, local, pg)
+    elif args.workload == "blas1":
+        run_blas1(args, rank, local)
     elif args.workload == "kernels":
         run_kernels(args, rank, local)
     else:

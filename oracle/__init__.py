@@ -37,6 +37,12 @@ def lib():
         L.or_n.restype = ctypes.c_long
         L.or_N.restype = ctypes.c_long
         L.or_norm2.restype = ctypes.c_double
+        L.or_axpy_f32.argtypes = [ctypes.c_long, ctypes.c_float, fp, fp]
+        L.or_axpy_f64.argtypes = [ctypes.c_long, ctypes.c_double, dp, dp]
+        L.or_dot_f32.argtypes = [ctypes.c_long, fp, fp]
+        L.or_dot_f32.restype = ctypes.c_double
+        L.or_dot_f64.argtypes = [ctypes.c_long, dp, dp]
+        L.or_dot_f64.restype = ctypes.c_double
         L.or_norm2.argtypes = [ctypes.c_long, dp]
         L.or_fp16_rne.restype = ctypes.c_uint16
         L.or_fp16_rne.argtypes = [ctypes.c_double]
@@ -229,3 +235,29 @@ def load_sinsin(L):
 
 def l2_error_sinsin(L, x):
     return lib().or_l2_error_sinsin(L, _p(_f64(x)))
+
+
+def axpy(alpha, x, y):
+    """y + alpha*x with one rounding per element (x, y: float32 or float64 numpy arrays; new array)."""
+    out = np.array(y, copy=True)
+    if x.dtype == np.float32:
+        xs = np.ascontiguousarray(x, dtype=np.float32)
+        lib().or_axpy_f32(len(xs), float(np.float32(alpha)),
+                          xs.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    else:
+        xs = np.ascontiguousarray(x, dtype=np.float64)
+        lib().or_axpy_f64(len(xs), float(alpha), xs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def dot(x, y):
+    """x . y summed in long double (float32 or float64 arrays of one type)."""
+    if x.dtype == np.float32:
+        xs, ys = np.ascontiguousarray(x, np.float32), np.ascontiguousarray(y, np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        return lib().or_dot_f32(len(xs), xs.ctypes.data_as(fp), ys.ctypes.data_as(fp))
+    xs, ys = np.ascontiguousarray(x, np.float64), np.ascontiguousarray(y, np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    return lib().or_dot_f64(len(xs), xs.ctypes.data_as(dp), ys.ctypes.data_as(dp))

@@ -636,4 +636,24 @@ double or_l2_error_sinsin(int L, const double* x) {
   return std::sqrt(s);
 }
 
+// ---- BLAS level 1 (Sec. 6.1, Fig. 2): axpy with one rounding per element (std::fma),
+// and dot products summed in long double, against which the device's fixed-order sums are
+// compared within their rounding bound
+void or_axpy_f32(long n, float a, const float* x, float* y) {
+  for (long i = 0; i < n; ++i) y[i] = std::fma(a, x[i], y[i]);
+}
+void or_axpy_f64(long n, double a, const double* x, double* y) {
+  for (long i = 0; i < n; ++i) y[i] = std::fma(a, x[i], y[i]);
+}
+double or_dot_f32(long n, const float* x, const float* y) {
+  long double s = 0.0L;
+  for (long i = 0; i < n; ++i) s += (long double)x[i] * (long double)y[i];
+  return (double)s;
+}
+double or_dot_f64(long n, const double* x, const double* y) {
+  long double s = 0.0L;
+  for (long i = 0; i < n; ++i) s += (long double)x[i] * (long double)y[i];
+  return (double)s;
+}
+
 }  // extern "C"

@@ -32,7 +32,7 @@ EXPORTS = [
     "hn_mg_poll", "hn_server_query", "hn_server_destroy", "hn_last_error", "hn_version",
     "hn_mg_set_profiling", "hn_mg_kernel_times", "hn_mg_last_launches",
     "hn_band_defect_norm_static", "hn_mg_set_tuning", "hn_mg_get_tuning", "hn_mg_autotune",
-    "hn_mg_autotune_batch", "hn_mg_time_kernel",
+    "hn_mg_autotune_batch", "hn_mg_time_kernel", "hn_axpy", "hn_dot", "hn_nrm2",
 ]
 
 
@@ -129,6 +129,9 @@ def lib():
         L.hn_mg_time_kernel.argtypes = [vp, ip, ip, ip, dp, dp]
         L.hn_mg_last_launches.argtypes = [vp]
         L.hn_mg_last_launches.restype = ctypes.c_longlong
+        L.hn_axpy.argtypes = [ip, ctypes.c_longlong, ctypes.c_double, vp, vp, vp]
+        L.hn_dot.argtypes = [ip, ctypes.c_longlong, vp, vp, vp, vp]
+        L.hn_nrm2.argtypes = [ip, ctypes.c_longlong, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -407,3 +410,47 @@ def hn_server_query(srv):
 
 def hn_server_destroy(srv):
     lib().hn_server_destroy(srv)
+
+
+# ------------------------------------------------------------------ BLAS level 1 (hn_blas1.h)
+HN_F32, HN_F64 = 0, 1
+
+
+def _blas_vec(v):
+    """(type, n, device pointer) of a contiguous CUDA float32/float64 torch tensor."""
+    import torch
+    if not (isinstance(v, torch.Tensor) and v.is_cuda and v.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor")
+    if v.dtype == torch.float32:
+        return HN_F32, v.numel(), ctypes.c_void_p(v.data_ptr())
+    if v.dtype == torch.float64:
+        return HN_F64, v.numel(), ctypes.c_void_p(v.data_ptr())
+    raise TypeError("expected float32 or float64")
+
+
+def _stream_ptr(stream):
+    return ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+
+
+def hn_axpy(alpha, x, y, stream=None):
+    """y = alpha * x + y on the device (x, y: CUDA tensors of the same type and length)."""
+    t, n, px = _blas_vec(x)
+    t2, n2, py = _blas_vec(y)
+    if (t, n) != (t2, n2):
+        raise ValueError("x and y differ in type or length")
+    _check(lib().hn_axpy(t, n, alpha, px, py, _stream_ptr(stream)))
+
+
+def hn_dot(x, y, result, stream=None):
+    """result[0] = x . y (result: a CUDA float64 tensor of at least one element)."""
+    t, n, px = _blas_vec(x)
+    t2, n2, py = _blas_vec(y)
+    if (t, n) != (t2, n2):
+        raise ValueError("x and y differ in type or length")
+    _check(lib().hn_dot(t, n, px, py, ctypes.c_void_p(result.data_ptr()), _stream_ptr(stream)))
+
+
+def hn_nrm2(x, result, stream=None):
+    """result[0] = ||x||_2 (result: a CUDA float64 tensor of at least one element)."""
+    t, n, px = _blas_vec(x)
+    _check(lib().hn_nrm2(t, n, px, ctypes.c_void_p(result.data_ptr()), _stream_ptr(stream)))

@@ -443,3 +443,30 @@ def test_fp16_defect_correction_converges_at_large_level():
     b = I.rhs_uniform(L, 1)
     x, st = O.mg_solve(L, b, coef=a, prec=O.PREC_FP16BAND_DC)
     assert st["converged"] and st["outer_iters"] <= 12
+
+
+# ------------------------------------------------------------------ BLAS level 1 (Sec. 6.1)
+def test_oracle_dot_closed_form_and_exact_sum():
+    import math
+    n = 1_000_000
+    x = np.arange(n, dtype=np.float64)
+    assert O.dot(x, np.ones(n)) == n * (n - 1) / 2                    # exact integer sum
+    rng = np.random.default_rng(3)
+    a, b = rng.uniform(-1, 1, 4099).astype(np.float32), rng.uniform(-1, 1, 4099).astype(np.float32)
+    prods = a.astype(np.float64) * b.astype(np.float64)              # exact for float32 inputs
+    exact = math.fsum(prods.tolist())                                # correctly rounded sum
+    assert abs(O.dot(a, b) - exact) <= 2.0 ** -52 * abs(exact)
+
+
+def test_oracle_axpy_single_rounding():
+    rng = np.random.default_rng(4)
+    x, y = rng.uniform(-1, 1, 5000).astype(np.float32), rng.uniform(-1, 1, 5000).astype(np.float32)
+    a = np.float32(-0.37)
+    # a*x + y exactly in extended precision, rounded once to float32
+    ref = (np.longdouble(a) * x.astype(np.longdouble) + y.astype(np.longdouble)).astype(np.float32)
+    if np.finfo(np.longdouble).nmant < 60:
+        pytest.skip("no extended precision long double on this host")
+    np.testing.assert_array_equal(O.axpy(a, x, y), ref)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    assert np.array_equal(O.axpy(2.0, np.ones(3), np.ones(3)), np.full(3, 3.0))
+    assert np.all(np.abs(O.axpy(0.5, xd, yd) - (0.5 * xd + yd)) <= 2.0 ** -53 * (np.abs(0.5 * xd) + np.abs(yd)))
