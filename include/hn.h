@@ -1,7 +1,8 @@
 /* hn.h -- C ABI of the GB300 multigrid Poisson solver (HONEI paper, arXiv 0904.4152).
  *
  * The library solves the Q1 (bilinear, conforming) finite-element discretisation of
- *     -div(a grad u) = f   on the unit square, zero Dirichlet boundary       (Sec. 2.1)
+ *     -div(a grad u) = f   on the unit square, zero Dirichlet boundary on all or some
+ *                          sides and free Neumann on the others          (Sec. 2.1, 6.2)
  * on a regular grid of refinement level L, i.e. n = 2^L + 1 nodes per side and N = n^2 unknowns
  * numbered in tensor-product order, node i = iy*n + ix with ix fastest (Sec. 2.1).  The matrix is
  * assembled fully into 9 bands at fixed positions (Sec. 2.1, Sec. 4.1) and solved by a geometric
@@ -17,7 +18,8 @@
  *    aliases a caller pointer; outputs are written into caller buffers.  Handles are opaque and
  *    owned by the caller until passed to the matching *_destroy.
  *  - Vectors have length N over all (2^L+1)^2 nodes including the boundary.  Right-hand-side
- *    entries on boundary nodes must be 0 (HN_ERR_ARG otherwise); solutions are 0 there.
+ *    entries on Dirichlet nodes must be 0 (HN_ERR_ARG otherwise); solutions are 0 there.  Nodes
+ *    on free Neumann sides (hn_band_create_bc) are unknowns like interior nodes.
  *  - Band layout: 9 bands, k = 0..8 <-> neighbour offset (dy, dx) = (k/3 - 1, k%3 - 1), band-major
  *    (band k occupies elements [k*N, (k+1)*N)), band_k[i] = A[i, i + dy*n + dx].  An entry is exactly
  *    0.0 where the neighbour is off the grid or either node lies on the Dirichlet boundary; boundary
@@ -61,12 +63,28 @@ typedef struct hn_server hn_server;  /* continuous-batching solve server */
 #define HN_MIN_LEVEL 2
 #define HN_MAX_LEVEL 14
 
+/* Boundary conditions per side of the square: a side in the mask is zero Dirichlet (its nodes
+ * are eliminated), a side not in it is free Neumann (zero flux; its nodes are unknowns with the
+ * rows of their 1 or 2 cells, the natural boundary condition).  The paper's accuracy test uses
+ * Dirichlet on all sides (Sec. 6.2.1), its performance test mixes free Neumann and Dirichlet
+ * sides (Sec. 6.2.2).  A corner is Dirichlet if either of its sides is. */
+#define HN_DIRICHLET_BOTTOM 1u   /* y = 0 */
+#define HN_DIRICHLET_RIGHT 2u    /* x = 1 */
+#define HN_DIRICHLET_TOP 4u      /* y = 1 */
+#define HN_DIRICHLET_LEFT 8u     /* x = 0 */
+#define HN_DIRICHLET_ALL 15u
+
 /* Assemble the Q1 stiffness matrix of -div(a grad u) at level L (HN_MIN_LEVEL..HN_MAX_LEVEL) on
  * the GPU (Sec. 2.1: full assembly, fixed band positions).  cell_coef: host array of (2^L)^2
  * per-cell coefficients a > 0, row-major by cell (ey, ex), cell (ex, ey) = [ex h, (ex+1) h] x
- * [ey h, (ey+1) h]; NULL means a = 1.  Dirichlet nodes are eliminated symmetrically (rows and
- * columns zeroed, diagonal 1).  *out receives a new handle.  Errors: HN_ERR_ARG (L out of range,
- * out NULL, a coefficient not finite or <= 0), HN_ERR_OOM, HN_ERR_CUDA. */
+ * [ey h, (ey+1) h]; NULL means a = 1.  dirichlet_sides: a nonzero mask of HN_DIRICHLET_* sides
+ * (at least one, so that the operator is definite).  Dirichlet nodes are eliminated symmetrically
+ * (rows and columns zeroed, diagonal 1).  *out receives a new handle.  Errors: HN_ERR_ARG (L out
+ * of range, out NULL, a coefficient not finite or <= 0, a mask outside 1..15), HN_ERR_OOM,
+ * HN_ERR_CUDA. */
+hn_status hn_band_create_bc(int L, const double* cell_coef, unsigned dirichlet_sides, hn_band** out);
+
+/* hn_band_create_bc with all four sides Dirichlet. */
 hn_status hn_band_create(int L, const double* cell_coef, hn_band** out);
 
 /* Copy the 9 assembled FP64 bands to host memory: bands_out holds 9*N doubles in the band layout
@@ -91,6 +109,8 @@ typedef struct {
   double inner_tol;  /* inner cycles stop at relative inner residual <= inner_tol (1e-2) */
   hn_precision prec; /* HN_PREC_FP64 */
   void* stream;      /* cudaStream_t the solves run on; NULL = the library's own stream */
+  unsigned dirichlet_sides;  /* boundary of the operators hn_mg_submit assembles
+                                (HN_DIRICHLET_ALL); hn_mg_setup takes it from its operator */
 } hn_mg_opts;
 
 typedef struct {

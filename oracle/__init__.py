@@ -18,6 +18,15 @@ from . import build as _build
 _lib = None
 
 PREC_FP64, PREC_FP32_DC, PREC_FP16BAND_DC, PREC_FP32_ONLY = 0, 1, 2, 3
+# Dirichlet sides: bits 1 bottom (y = 0), 2 right (x = 1), 4 top (y = 1), 8 left (x = 0); the
+# other sides are free Neumann
+ALL_DIRICHLET, DIRICHLET_LEFT_RIGHT = 15, 10
+
+
+def _sides(bc):
+    if not (0 < bc <= 15):
+        raise ValueError("at least one Dirichlet side (bits 1, 2, 4, 8)")
+    lib().or_set_dirichlet(bc)
 
 
 class Stats(ctypes.Structure):
@@ -70,6 +79,11 @@ def lib():
         L.or_load_sinsin.argtypes = [ctypes.c_int, dp]
         L.or_l2_error_sinsin.argtypes = [ctypes.c_int, dp]
         L.or_l2_error_sinsin.restype = ctypes.c_double
+        L.or_load_sincos.argtypes = [ctypes.c_int, dp]
+        L.or_l2_error_sincos.argtypes = [ctypes.c_int, dp]
+        L.or_l2_error_sincos.restype = ctypes.c_double
+        L.or_set_dirichlet.argtypes = [ctypes.c_uint]
+        L.or_set_dirichlet.restype = None
         _lib = L
     return _lib
 
@@ -96,10 +110,11 @@ def element_stiffness(h=1.0):
     return K.reshape(4, 4)
 
 
-def assemble(L, coef=None):
+def assemble(L, coef=None, bc=ALL_DIRICHLET):
     """Q1 stiffness matrix of -div(a grad u) as 9 bands, Dirichlet rows/columns eliminated."""
     bands = np.zeros((9, N_of(L)))
     c = None if coef is None else _f64(coef)
+    _sides(bc)
     lib().or_assemble(L, _p(c), _p(bands))
     return bands
 
@@ -134,20 +149,23 @@ def jacobi(L, bands, omega, b, x):
     return out
 
 
-def restrict(Lf, rf):
+def restrict(Lf, rf, bc=ALL_DIRICHLET):
     rc = np.zeros(N_of(Lf - 1))
+    _sides(bc)
     lib().or_restrict(Lf, _p(_f64(rf)), _p(rc))
     return rc
 
 
-def prolong_add(Lf, ec, xf):
+def prolong_add(Lf, ec, xf, bc=ALL_DIRICHLET):
     out = _f64(xf).copy()
+    _sides(bc)
     lib().or_prolong_add(Lf, _p(_f64(ec)), _p(out))
     return out
 
 
-def coarse_solve(Lc, bands, b):
+def coarse_solve(Lc, bands, b, bc=ALL_DIRICHLET):
     x = np.zeros(N_of(Lc))
+    _sides(bc)
     rc = lib().or_coarse_solve(Lc, _p(_f64(bands)), _p(_f64(b)), _p(x))
     if rc != 0:
         raise ValueError("coarse matrix not positive definite")
@@ -206,8 +224,9 @@ def jacobi_f32(L, bands, omega, b, x, rowsum):
 
 def mg_solve(L, b, coef=None, x0=None, prec=PREC_FP64, pre=2, post=2, omega=0.7, tol=1e-8,
              max_cycles=100, max_outer=50, inner_tol=1e-2, inner_max=10, coarse_L=2,
-             history=False):
+             history=False, bc=ALL_DIRICHLET):
     """Multigrid solve; returns (x, stats dict[, relres history])."""
+    _sides(bc)
     N = N_of(L)
     x = np.zeros(N) if x0 is None else _f64(x0).copy()
     c = None if coef is None else _f64(coef)
@@ -226,9 +245,23 @@ def mg_solve(L, b, coef=None, x0=None, prec=PREC_FP64, pre=2, post=2, omega=0.7,
     return x, stats
 
 
+def load_sincos(L):
+    """Load vector of f = 2 pi^2 sin(pi x) cos(pi y), exact solution sin(pi x) cos(pi y):
+    Dirichlet on the left and right sides (DIRICHLET_LEFT_RIGHT), free Neumann on the others."""
+    b = np.zeros(N_of(L))
+    _sides(DIRICHLET_LEFT_RIGHT)
+    lib().or_load_sincos(L, _p(b))
+    return b
+
+
+def l2_error_sincos(L, x):
+    return lib().or_l2_error_sincos(L, _p(_f64(x)))
+
+
 def load_sinsin(L):
     """Load vector of f = 2 pi^2 sin(pi x) sin(pi y), exact solution sin(pi x) sin(pi y)."""
     b = np.zeros(N_of(L))
+    _sides(ALL_DIRICHLET)
     lib().or_load_sinsin(L, _p(b))
     return b
 

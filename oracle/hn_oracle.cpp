@@ -43,9 +43,17 @@ namespace {
 // ---------------------------------------------------------------- grid and numbering (Sec. 2.1)
 inline long n_of(int L) { return (1L << L) + 1; }     // nodes per side
 inline long N_of(int L) { long n = n_of(L); return n * n; }
-inline bool is_boundary(long ix, long iy, long n) {
-  return ix == 0 || iy == 0 || ix == n - 1 || iy == n - 1;
+// Boundary conditions: each side of the square is Dirichlet (zero value, eliminated) or free
+// Neumann (zero flux, natural).  Sides as bits: 1 bottom (y = 0), 2 right (x = 1), 4 top (y = 1),
+// 8 left (x = 0); the paper's accuracy test has all four Dirichlet (Sec. 6.2.1), its performance
+// test mixes Dirichlet and free Neumann sides (Sec. 6.2.2).  Set per call from the C interface.
+thread_local unsigned g_dirichlet = 15u;
+inline bool is_boundary(long ix, long iy, long n) {   // a Dirichlet node
+  const unsigned m = g_dirichlet;
+  return (iy == 0 && (m & 1u)) || (ix == n - 1 && (m & 2u)) || (iy == n - 1 && (m & 4u)) ||
+         (ix == 0 && (m & 8u));
 }
+inline bool on_grid(long ix, long iy, long n) { return ix >= 0 && iy >= 0 && ix < n && iy < n; }
 // band k <-> neighbour offset (dy, dx), dy, dx in {-1, 0, 1}; band_k[i] = A[i, i + dy*n + dx]
 inline int band_dy(int k) { return k / 3 - 1; }
 inline int band_dx(int k) { return k % 3 - 1; }
@@ -82,7 +90,8 @@ void element_stiffness(double h, double K[4][4]) {
 
 // --------------------------------------------------------------- global assembly (Sec. 2.1)
 // Full assembly of the 9-band matrix of -div(a grad u) with piecewise-constant cell coefficient,
-// element by element, followed by symmetric elimination of the Dirichlet nodes.
+// element by element (a node on a free Neumann side keeps the rows of its 1 or 2 cells: the
+// natural boundary condition), followed by symmetric elimination of the Dirichlet nodes.
 void assemble(int L, const double* coef, double* bands) {
   const long n = n_of(L), N = N_of(L), nc = n - 1;
   const double h = 1.0 / (double)(n - 1);
@@ -109,8 +118,10 @@ void assemble(int L, const double* coef, double* bands) {
         bands[4 * N + i] = 1.0;
         continue;
       }
-      for (int k = 0; k < 9; ++k)
-        if (is_boundary(ix + band_dx(k), iy + band_dy(k), n)) bands[k * N + i] = 0.0;
+      for (int k = 0; k < 9; ++k) {
+        const long jx = ix + band_dx(k), jy = iy + band_dy(k);
+        if (!on_grid(jx, jy, n) || is_boundary(jx, jy, n)) bands[k * N + i] = 0.0;
+      }
     }
 }
 
@@ -197,7 +208,7 @@ inline double w1d(long f, long C) {
   return (C == (f - 1) / 2 || C == (f + 1) / 2) ? 0.5 : 0.0;
 }
 
-// x_f += P e_c (bilinear interpolation, boundary rows and columns of P zeroed)
+// x_f += P e_c (bilinear interpolation; rows and columns of Dirichlet nodes of P zeroed)
 template <typename T>
 void prolong_add(int Lf, const T* ec, T* xf) {
   const long nf = n_of(Lf), nc = n_of(Lf - 1);
@@ -233,26 +244,31 @@ void restrict_(int Lf, const T* rf, T* rc) {
 }
 
 // ------------------------------------------------------------------- exact coarse solve
-// Dense Cholesky of the interior block of the coarsest matrix (the paper uses unpreconditioned
-// CG there; on this tiny SPD system both give the exact solution up to rounding).
+// Dense Cholesky of the coarsest matrix restricted to its unknowns (the paper uses
+// unpreconditioned CG there; on this tiny SPD system both give the exact solution up to rounding).
 struct CoarseSolver {
   int L = 0;
-  long n = 0, m = 0;              // nodes per side, interior unknowns
+  long n = 0, m = 0;              // nodes per side, unknowns (nodes that are not Dirichlet)
+  std::vector<long> node;         // node of unknown u, row-major order
   std::vector<double> chol;       // lower factor, m*m row-major
   bool ok = false;
   void factor(int Lc, const double* bands) {
-    L = Lc; n = n_of(Lc); const long N = N_of(Lc); const long ni = n - 2; m = ni * ni;
+    L = Lc; n = n_of(Lc); const long N = N_of(Lc);
+    node.clear();
+    std::vector<long> unk(N, -1);
+    for (long iy = 0; iy < n; ++iy)
+      for (long ix = 0; ix < n; ++ix)
+        if (!is_boundary(ix, iy, n)) { unk[iy * n + ix] = (long)node.size(); node.push_back(iy * n + ix); }
+    m = (long)node.size();
     std::vector<double> A(m * m, 0.0);
-    for (long iy = 1; iy < n - 1; ++iy)
-      for (long ix = 1; ix < n - 1; ++ix) {
-        const long I = (iy - 1) * ni + (ix - 1);
-        for (int k = 0; k < 9; ++k) {
-          const long jx = ix + band_dx(k), jy = iy + band_dy(k);
-          if (is_boundary(jx, jy, n)) continue;
-          const long J = (jy - 1) * ni + (jx - 1);
-          A[I * m + J] = bands[k * N + iy * n + ix];
-        }
+    for (long I = 0; I < m; ++I) {
+      const long i = node[I], iy = i / n, ix = i % n;
+      for (int k = 0; k < 9; ++k) {
+        const long jx = ix + band_dx(k), jy = iy + band_dy(k);
+        if (!on_grid(jx, jy, n) || is_boundary(jx, jy, n)) continue;
+        A[I * m + unk[jy * n + jx]] = bands[k * N + i];
       }
+    }
     chol.assign(m * m, 0.0);
     ok = true;
     for (long j = 0; j < m; ++j) {
@@ -267,14 +283,12 @@ struct CoarseSolver {
       }
     }
   }
-  // x = A^{-1} b on interior nodes, 0 on the boundary.  Solved in FP64, then stored as T.
+  // x = A^{-1} b on the unknowns, 0 on Dirichlet nodes.  Solved in FP64, then stored as T.
   template <typename T>
   void solve(const T* b, T* x) const {
-    const long ni = n - 2;
     std::vector<double> y(m);
     for (long i = 0; i < m; ++i) {
-      const long iy = i / ni + 1, ix = i % ni + 1;
-      double s = (double)b[iy * n + ix];
+      double s = (double)b[node[i]];
       for (long k = 0; k < i; ++k) s -= chol[i * m + k] * y[k];
       y[i] = s / chol[i * m + i];
     }
@@ -284,7 +298,7 @@ struct CoarseSolver {
       y[i] = s / chol[i * m + i];
     }
     for (long i = 0; i < n * n; ++i) x[i] = 0;
-    for (long i = 0; i < m; ++i) x[(i / ni + 1) * n + (i % ni + 1)] = (T)y[i];
+    for (long i = 0; i < m; ++i) x[node[i]] = (T)y[i];
   }
 };
 
@@ -449,6 +463,8 @@ typedef struct {
   double relres;     // final ||b - A x|| / ||b|| in FP64 with the FP64 operator
 } or_stats;
 
+// Dirichlet sides (bits: 1 bottom, 2 right, 4 top, 8 left) for the following calls of this thread
+void or_set_dirichlet(unsigned sides) { g_dirichlet = sides; }
 long or_n(int L) { return n_of(L); }
 long or_N(int L) { return N_of(L); }
 
@@ -586,9 +602,15 @@ int or_mg_solve(int L, const double* coef, const double* b, double* x, int prec,
   return s.converged ? 0 : 1;
 }
 
-// Load vector b_i = integral of f phi_i for f = 2 pi^2 sin(pi x) sin(pi y) (so that
-// u = sin(pi x) sin(pi y) solves -Laplace(u) = f), 3x3 Gauss-Legendre per cell; Dirichlet entries 0.
-void or_load_sinsin(int L, double* b) {
+// Manufactured solutions (Sec. 6.2.1): u = sin(pi x) sin(pi y) (zero on all four sides) and
+// u = sin(pi x) cos(pi y) (zero at x = 0, 1; zero normal derivative at y = 0, 1, i.e. Dirichlet
+// left/right and free Neumann bottom/top), both with -Laplace(u) = f = 2 pi^2 u.
+static double u_sinsin(double x, double y) { return std::sin(M_PI * x) * std::sin(M_PI * y); }
+static double u_sincos(double x, double y) { return std::sin(M_PI * x) * std::cos(M_PI * y); }
+
+// Load vector b_i = integral of f phi_i, 3x3 Gauss-Legendre per cell; Dirichlet entries 0 (the
+// Neumann sides are homogeneous, so no boundary integral is added).
+static void load_vector(int L, double (*u)(double, double), double* b) {
   const long n = n_of(L), N = N_of(L);
   const double h = 1.0 / (double)(n - 1);
   const double g = 0.5 * std::sqrt(0.6);
@@ -602,7 +624,7 @@ void or_load_sinsin(int L, double* b) {
         for (int qx = 0; qx < 3; ++qx) {
           const double xi = pts[qx], eta = pts[qy];
           const double px = (ex + xi) * h, py = (ey + eta) * h;
-          const double f = 2.0 * M_PI * M_PI * std::sin(M_PI * px) * std::sin(M_PI * py);
+          const double f = 2.0 * M_PI * M_PI * u(px, py);
           const double w = wts[qx] * wts[qy] * h * h;
           for (int a = 0; a < 4; ++a) {
             const double phi = (lx[a] ? xi : 1.0 - xi) * (ly[a] ? eta : 1.0 - eta);
@@ -614,9 +636,9 @@ void or_load_sinsin(int L, double* b) {
       if (is_boundary(ix, iy, n)) b[iy * n + ix] = 0.0;
 }
 
-// Integral L2 error || u_h - sin(pi x) sin(pi y) ||, u_h the bilinear interpolant of the nodal
-// values, 3x3 Gauss per cell, in FP64 (Sec. 6.2.1).
-double or_l2_error_sinsin(int L, const double* x) {
+// Integral L2 error || u_h - u ||, u_h the bilinear interpolant of the nodal values, 3x3 Gauss per
+// cell, in FP64 (Sec. 6.2.1).
+static double l2_error(int L, double (*u)(double, double), const double* x) {
   const long n = n_of(L);
   const double h = 1.0 / (double)(n - 1);
   const double g = 0.5 * std::sqrt(0.6);
@@ -630,11 +652,16 @@ double or_l2_error_sinsin(int L, const double* x) {
           const double xi = pts[qx], eta = pts[qy];
           const double uh = (1 - xi) * (1 - eta) * x[ey * n + ex] + xi * (1 - eta) * x[ey * n + ex + 1] +
                             xi * eta * x[(ey + 1) * n + ex + 1] + (1 - xi) * eta * x[(ey + 1) * n + ex];
-          const double u = std::sin(M_PI * (ex + xi) * h) * std::sin(M_PI * (ey + eta) * h);
-          s += wts[qx] * wts[qy] * h * h * (uh - u) * (uh - u);
+          const double d = uh - u((ex + xi) * h, (ey + eta) * h);
+          s += wts[qx] * wts[qy] * h * h * d * d;
         }
   return std::sqrt(s);
 }
+
+void or_load_sinsin(int L, double* b) { load_vector(L, u_sinsin, b); }
+void or_load_sincos(int L, double* b) { load_vector(L, u_sincos, b); }
+double or_l2_error_sinsin(int L, const double* x) { return l2_error(L, u_sinsin, x); }
+double or_l2_error_sincos(int L, const double* x) { return l2_error(L, u_sincos, x); }
 
 // ---- BLAS level 1 (Sec. 6.1, Fig. 2): axpy with one rounding per element (std::fma),
 // and dot products summed in long double, against which the device's fixed-order sums are

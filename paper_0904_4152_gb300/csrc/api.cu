@@ -118,9 +118,15 @@ const char* hn_last_error(void) { return hn::last_error(); }
 const char* hn_version(void) { return "hn 0.1 (sm_103a)"; }
 
 hn_status hn_band_create(int L, const double* cell_coef, hn_band** out) {
+  return hn_band_create_bc(L, cell_coef, HN_DIRICHLET_ALL, out);
+}
+
+hn_status hn_band_create_bc(int L, const double* cell_coef, unsigned dirichlet_sides, hn_band** out) {
   clear_error();
   if (!out) return set_error(HN_ERR_ARG, "out is NULL");
   *out = nullptr;
+  if (dirichlet_sides < 1u || dirichlet_sides > 15u)
+    return set_error(HN_ERR_ARG, "dirichlet_sides %u: need a nonzero mask of the 4 sides", dirichlet_sides);
   if (L < HN_MIN_LEVEL || L > HN_MAX_LEVEL)
     return set_error(HN_ERR_ARG, "level %d outside [%d, %d]", L, HN_MIN_LEVEL, HN_MAX_LEVEL);
   const long long cells = (1LL << L) * (1LL << L);
@@ -130,6 +136,7 @@ hn_status hn_band_create(int L, const double* cell_coef, hn_band** out) {
         return set_error(HN_ERR_ARG, "cell coefficient %lld is not a positive finite number", i);
   std::unique_ptr<hn_band> A(new hn_band());
   A->L = L;
+  A->bc = dirichlet_sides;
   A->n = n_of(L);
   A->N = N_of(L);
   A->pitch = pitch_of(L);
@@ -148,7 +155,7 @@ hn_status hn_band_create(int L, const double* cell_coef, hn_band** out) {
     A->coef = b.take<double>((size_t)cells);
     HN_CUDA(cudaMemcpyAsync(A->coef, cell_coef, (size_t)cells * 8, cudaMemcpyHostToDevice, os.s));
   }
-  HN_CUDA(launch_assemble(L, A->coef, bp, nullptr, 1.0, os.s));
+  HN_CUDA(launch_assemble(L, A->coef, bp, nullptr, 1.0, (int)A->bc, os.s));
   HN_CUDA(cudaStreamSynchronize(os.s));
   *out = A.release();
   return HN_OK;
@@ -180,6 +187,7 @@ void hn_mg_opts_default(hn_mg_opts* o) {
   o->inner_tol = 1e-2;
   o->prec = HN_PREC_FP64;
   o->stream = nullptr;
+  o->dirichlet_sides = HN_DIRICHLET_ALL;
 }
 
 hn_status hn_mg_setup(const hn_band* A, const hn_mg_opts* opts, hn_mg** out) {

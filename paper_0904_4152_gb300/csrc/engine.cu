@@ -74,7 +74,7 @@ void walk_layout(int L, int coarse, int prec, F&& take) {
     take(vec_elems(L) * 8);
     take(vec_elems(L) * 8);
   }
-  const long long m = ((1LL << coarse) - 1) * ((1LL << coarse) - 1);
+  const long long m = n_of(coarse) * n_of(coarse);   // unknowns of the coarsest level, at most
   take((size_t)(m * m) * 8);
 }
 
@@ -145,6 +145,8 @@ hn_status validate_opts(const hn_mg_opts& o, int L) {
   if (o.pre < 1 || o.post < 0 || ((o.pre + o.post) & 1) || o.pre + o.post > 64)
     return set_error(HN_ERR_ARG, "need pre >= 1, post >= 0, pre + post even and <= 64");
   if (!(o.omega > 0.0 && o.omega < 2.0)) return set_error(HN_ERR_ARG, "omega must be in (0, 2)");
+  if (o.dirichlet_sides < 1u || o.dirichlet_sides > 15u)
+    return set_error(HN_ERR_ARG, "dirichlet_sides must be a nonzero mask of the 4 sides");
   if (!(o.tol >= 0.0) || !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
     return set_error(HN_ERR_ARG, "need tol >= 0 and 0 < inner_tol < 1");
   if (o.max_cycles < 1 || o.max_outer < 1 || o.inner_max < 1 || o.max_cycles > 100000 ||
@@ -161,8 +163,8 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
   mg->coarse = c;
   mg->opts = o;
   mg->prm = prm;
-  const long long ni = (1LL << c) - 1;
-  mg->m = (int)(ni * ni);
+  const UnknownRect ur = unknown_rect((int)n_of(c), (int)A->bc);
+  mg->m = ur.nx * ur.ny;
   mg->bytes = hierarchy_bytes(L, c, prec);
   HN_CUDA(cudaMalloc(&mg->mem, mg->bytes));
   HN_CUDA(cudaMemsetAsync(mg->mem, 0, mg->bytes, s));
@@ -179,6 +181,7 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
     d.L = l;
     d.n = (int)n_of(l);
     d.pitch = (int)pitch_of(l);
+    d.bc = (int)A->bc;
     const long long H = halo_of(l);
     void* vecs[4];
     for (int v = 0; v < 4; ++v) {
@@ -243,14 +246,14 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
       for (int k = 0; k < 9; ++k) b64.p[k] = dst[k];
       if (prec == P64) {
         // the fine level also needs omega / diag: reassemble writes identical bands plus it
-        HN_CUDA(launch_assemble(l, coef_cur, b64, const_cast<double*>(d.wdinv), o.omega, s));
+        HN_CUDA(launch_assemble(l, coef_cur, b64, const_cast<double*>(d.wdinv), o.omega, (int)A->bc, s));
       }
     } else if (prec == P64) {
       for (int k = 0; k < 9; ++k) b64.p[k] = static_cast<double*>(const_cast<void*>(d.band[k]));
-      HN_CUDA(launch_assemble(l, coef_cur, b64, const_cast<double*>(d.wdinv), o.omega, s));
+      HN_CUDA(launch_assemble(l, coef_cur, b64, const_cast<double*>(d.wdinv), o.omega, (int)A->bc, s));
     } else {
       for (int k = 0; k < 9; ++k) b64.p[k] = tband[k];
-      HN_CUDA(launch_assemble(l, coef_cur, b64, nullptr, o.omega, s));
+      HN_CUDA(launch_assemble(l, coef_cur, b64, nullptr, o.omega, (int)A->bc, s));
     }
     BandPtrs64c src{};
     for (int k = 0; k < 9; ++k) src.p[k] = b64.p[k];
@@ -280,18 +283,19 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
     }
   }
   HN_CUDA(cudaStreamSynchronize(s));
-  // exact coarse solver: inverse of the interior block of the coarsest operator
+  // exact coarse solver: inverse of the coarsest operator restricted to its unknowns (the
+  // rectangle of nodes that are not Dirichlet), row-major
   {
     const long long n = n_of(c), pc = pitch_of(c);
     const int m = mg->m;
     std::vector<double> a((size_t)m * m, 0.0);
-    for (long long iy = 1; iy < n - 1; ++iy)
-      for (long long ix = 1; ix < n - 1; ++ix) {
-        const long long I = (iy - 1) * ni + (ix - 1);
+    for (long long iy = ur.y0; iy < ur.y0 + ur.ny; ++iy)
+      for (long long ix = ur.x0; ix < ur.x0 + ur.nx; ++ix) {
+        const long long I = (iy - ur.y0) * ur.nx + (ix - ur.x0);
         for (int k = 0; k < 9; ++k) {
           const long long jx = ix + (k % 3 - 1), jy = iy + (k / 3 - 1);
-          if (jx <= 0 || jy <= 0 || jx >= n - 1 || jy >= n - 1) continue;
-          const long long J = (jy - 1) * ni + (jx - 1);
+          if (jx < ur.x0 || jy < ur.y0 || jx >= ur.x0 + ur.nx || jy >= ur.y0 + ur.ny) continue;
+          const long long J = (jy - ur.y0) * ur.nx + (jx - ur.x0);
           a[(size_t)(I * m + J)] = coarse64[(size_t)k * pc + iy * n + ix];
         }
       }

@@ -80,6 +80,7 @@ struct hn_band {
   void* mem = nullptr;
   double* band[9] = {};
   double* coef = nullptr;   // device cell coefficients, nullptr for a = 1
+  unsigned bc = 15u;        // Dirichlet sides (HN_DIRICHLET_*); the others are free Neumann
   ~hn_band();
 };
 

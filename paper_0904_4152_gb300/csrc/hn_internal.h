@@ -17,7 +17,7 @@ constexpr int kTile = 128;
 constexpr int kLaneNodes = 4;
 constexpr int kMaxLevel = HN_MAX_LEVEL;
 constexpr int kMaxCoarse = 4;                       // coarse_L <= 4: at most 225 interior unknowns
-constexpr int kMaxCoarseM = 225;
+constexpr int kMaxCoarseM = 289;   // unknowns of the coarsest level (17 x 17 at level 4)
 
 __host__ __device__ inline long long n_of_dev(int L) { return (1LL << L) + 1; }
 inline long long n_of(int L) { return (1LL << L) + 1; }
@@ -44,8 +44,26 @@ struct LevelDev {
   void* rhs;             // right-hand side of this level (restricted defect, or the top rhs)
   void* r;               // defect of this level
   float scale[9];        // FP16 band scales
-  int L, n, pitch, pad;
+  int L, n, pitch;
+  int bc;                // Dirichlet sides (HN_DIRICHLET_*), the same on every level
 };
+
+// node classes under the boundary mask bc: Dirichlet nodes are eliminated, all others (interior
+// and free-Neumann boundary nodes) are unknowns
+__host__ __device__ inline bool is_dirichlet(long long ix, long long iy, long long n, int bc) {
+  return (iy == 0 && (bc & 1)) || (ix == n - 1 && (bc & 2)) || (iy == n - 1 && (bc & 4)) ||
+         (ix == 0 && (bc & 8));
+}
+// the unknowns of a level form the rectangle of nodes x0..x0+nx-1, y0..y0+ny-1 (row-major)
+struct UnknownRect { int x0, y0, nx, ny; };
+__host__ __device__ inline UnknownRect unknown_rect(int n, int bc) {
+  UnknownRect r;
+  r.x0 = (bc & 8) ? 1 : 0;
+  r.y0 = (bc & 1) ? 1 : 0;
+  r.nx = ((bc & 2) ? n - 2 : n - 1) - r.x0 + 1;
+  r.ny = ((bc & 4) ? n - 2 : n - 1) - r.y0 + 1;
+  return r;
+}
 
 struct ProblemDev {
   int L;                 // finest level
@@ -136,7 +154,7 @@ struct BandPtrs16 { __half* p[9]; };
 cudaError_t launch_wdf(int L, int prec, const void* const* band, const float* scale, double omega,
                        float* wdf, cudaStream_t s);
 cudaError_t launch_assemble(int L, const double* coef, const BandPtrs64& band, double* wdinv,
-                            double omega, cudaStream_t s);
+                            double omega, int bc, cudaStream_t s);
 cudaError_t launch_coarsen_coef(int Lf, const double* af, double* ac, cudaStream_t s);
 cudaError_t launch_band_to_f32(int L, const BandPtrs64c& src, const BandPtrs32& dst,
                                cudaStream_t s);

@@ -423,9 +423,31 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
   }
 }
 
-// Full-weighting restriction of the fine defect onto coarse tile i0 (coarse boundary and padding
+// Full-weighting restriction of the fine defect onto coarse node (I, J) (Dirichlet and padding
 // nodes get 0).  Summation order: fine rows 2J-1, 2J, 2J+1, columns 2I-1, 2I, 2I+1, weights 1/4,
-// 1/2, 1/4 x 1/4, 1/2, 1/4 (products by powers of two are exact).
+// 1/2, 1/4 x 1/4, 1/2, 1/4 (products by powers of two are exact); a fine node off the grid (next
+// to a free Neumann side) contributes 0.  rd(i) reads fine node i.
+template <class V, class F>
+__device__ __forceinline__ V restrict_value(int I, int J, int nc, int nf, int bc, F rd) {
+  if (I < 0 || J >= nc || is_dirichlet(I, J, nc, bc)) return V(0);
+  const int fx = 2 * I, fy = 2 * J;
+  auto R = [&](int dy, int dx) -> V {
+    const int x = fx + dx, y = fy + dy;
+    return (x >= 0 && y >= 0 && x < nf && y < nf) ? rd((long long)y * nf + x) : V(0);
+  };
+  const V q = V(0.25), h = V(0.5);
+  V v = q * R(-1, -1);
+  v = fma(h, R(-1, 0), v);
+  v = fma(q, R(-1, 1), v);
+  v = fma(h, R(0, -1), v);
+  v = v + R(0, 0);
+  v = fma(h, R(0, 1), v);
+  v = fma(q, R(1, -1), v);
+  v = fma(h, R(1, 0), v);
+  v = fma(q, R(1, 1), v);
+  return v;
+}
+
 template <class V, int LK>
 __device__ __forceinline__ void restrict_tile(const LevelDev& f, const LevelDev& c, long long i0) {
   const int nc = c.n, nf = f.n, Nc = nc * nc;
@@ -435,28 +457,29 @@ __device__ __forceinline__ void restrict_tile(const LevelDev& f, const LevelDev&
   V out[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    V v = V(0);
-    if ((int)i0 + j < Nc && I > 0 && J > 0 && I < nc - 1 && J < nc - 1) {
-      const long long fc = 2LL * J * nf + 2 * I;
-      const V q = V(0.25), h = V(0.5);
-      v = q * ld1<LK>(r + fc - nf - 1);
-      v = fma(h, ld1<LK>(r + fc - nf), v);
-      v = fma(q, ld1<LK>(r + fc - nf + 1), v);
-      v = fma(h, ld1<LK>(r + fc - 1), v);
-      v = v + ld1<LK>(r + fc);
-      v = fma(h, ld1<LK>(r + fc + 1), v);
-      v = fma(q, ld1<LK>(r + fc + nf - 1), v);
-      v = fma(h, ld1<LK>(r + fc + nf), v);
-      v = fma(q, ld1<LK>(r + fc + nf + 1), v);
-    }
-    out[j] = v;
+    out[j] = (int)i0 + j < Nc ? restrict_value<V>(I, J, nc, nf, c.bc, [&](long long k) { return ld1<LK>(r + k); })
+                              : V(0);
     if (++I == nc) { I = 0; ++J; }
   }
   st4(static_cast<V*>(c.rhs) + i0, out);
 }
 
-// x_f[x_sel] += P e_c on fine tile i0 (bilinear interpolation of the coarse iterate, buffer 0);
-// boundary fine nodes are left unchanged.
+// x_f[x_sel] += P e_c at fine node (ix, iy): bilinear interpolation of the coarse iterate
+// (buffer 0); Dirichlet fine nodes are left unchanged (their coarse neighbours on the same side
+// are Dirichlet too and hold 0).  Returns the value added (0 for Dirichlet nodes).
+template <class V, class F>
+__device__ __forceinline__ bool prolong_value(int ix, int iy, int nf, int nc, int bc, F ec, V* add) {
+  if (is_dirichlet(ix, iy, nf, bc)) return false;
+  const int cx0 = ix >> 1, cx1 = (ix + 1) >> 1, cy0 = iy >> 1, cy1 = (iy + 1) >> 1;
+  const bool ox = ix & 1, oy = iy & 1;
+  if (!ox && !oy) *add = ec(cy0 * nc + cx0);
+  else if (ox && !oy) *add = V(0.5) * (ec(cy0 * nc + cx0) + ec(cy0 * nc + cx1));
+  else if (!ox && oy) *add = V(0.5) * (ec(cy0 * nc + cx0) + ec(cy1 * nc + cx0));
+  else *add = V(0.25) * (((ec(cy0 * nc + cx0) + ec(cy0 * nc + cx1)) + ec(cy1 * nc + cx0)) + ec(cy1 * nc + cx1));
+  return true;
+}
+
+// x_f[x_sel] += P e_c on fine tile i0
 template <class V, int LK>
 __device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& c, int x_sel,
                                              long long i0) {
@@ -470,23 +493,9 @@ __device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& 
   int iy = (int)((unsigned)i0 / (unsigned)nf), ix = (int)i0 - iy * nf;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    if ((int)i0 + j < Nf && ix > 0 && iy > 0 && ix < nf - 1 && iy < nf - 1) {
-      const int cx0 = ix >> 1, cx1 = (ix + 1) >> 1, cy0 = iy >> 1, cy1 = (iy + 1) >> 1;
-      const V* e0 = e + (long long)cy0 * nc;
-      const V* e1 = e + (long long)cy1 * nc;
-      V add;
-      const bool ox = ix & 1, oy = iy & 1;
-      if (!ox && !oy) {
-        add = ld1<LK>(e0 + cx0);
-      } else if (ox && !oy) {
-        add = V(0.5) * (ld1<LK>(e0 + cx0) + ld1<LK>(e0 + cx1));
-      } else if (!ox && oy) {
-        add = V(0.5) * (ld1<LK>(e0 + cx0) + ld1<LK>(e1 + cx0));
-      } else {
-        add = V(0.25) * (((ld1<LK>(e0 + cx0) + ld1<LK>(e0 + cx1)) + ld1<LK>(e1 + cx0)) + ld1<LK>(e1 + cx1));
-      }
+    V add;
+    if ((int)i0 + j < Nf && prolong_value<V>(ix, iy, nf, nc, f.bc, [&](int k) { return ld1<LK>(e + k); }, &add))
       v[j] = v[j] + add;
-    }
     if (++ix == nf) { ix = 0; ++iy; }
   }
   st4(x + i0, v);
@@ -516,18 +525,21 @@ __device__ __forceinline__ double coarse_dot(const double* row, int m, F rd) {
 template <class V, int LK>
 __device__ __forceinline__ void coarse_warp(const ProblemDev& P, int lane, double* sol) {
   const LevelDev& d = P.lev[P.coarse];
-  const int n = d.n, ni = n - 2, m = P.m;
+  const int n = d.n, m = P.m;
+  const UnknownRect ur = unknown_rect(n, d.bc);
   const V* rhs = static_cast<const V*>(d.rhs);
   for (int u = lane; u < m; u += 32) {
     const double* row = P.cinv + (long long)u * m;
-    sol[u] = coarse_dot(row, m, [&](int v) { return double(ld1<LK>(rhs + (v / ni + 1) * n + (v % ni + 1))); });
+    sol[u] = coarse_dot(row, m, [&](int v) {
+      return double(ld1<LK>(rhs + (v / ur.nx + ur.y0) * n + (v % ur.nx + ur.x0)));
+    });
   }
   __syncwarp();
   V* x = static_cast<V*>(d.x[0]);
   for (int q = lane; q < d.pitch; q += 32) {
-    const int iy = q / n, ix = q - iy * n;
+    const int iy = q / n - ur.y0, ix = q - (q / n) * n - ur.x0;
     V val = V(0);
-    if (q < n * n && ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1) val = V(sol[(iy - 1) * ni + (ix - 1)]);
+    if (q < n * n && ix >= 0 && iy >= 0 && ix < ur.nx && iy < ur.ny) val = V(sol[iy * ur.nx + ix]);
     x[q] = val;
   }
   __syncwarp();
@@ -999,41 +1011,20 @@ __device__ __forceinline__ void band_node(const LevelDev& d, int i, bool zg, int
 // full-weighting restriction onto coarse node i (the tile step's formula)
 template <class V>
 __device__ __forceinline__ void restrict_node(const LevelDev& f, const LevelDev& c, int i) {
-  const int nc = c.n, nf = f.n;
-  const int J = i / nc, I = i - J * nc;
-  V v = V(0);
-  if (i < nc * nc && I > 0 && J > 0 && I < nc - 1 && J < nc - 1) {
-    const V* r = static_cast<const V*>(f.r) + (2 * J * nf + 2 * I);
-    const V q = V(0.25), h = V(0.5);
-    v = q * r[-nf - 1];
-    v = fma(h, r[-nf], v);
-    v = fma(q, r[-nf + 1], v);
-    v = fma(h, r[-1], v);
-    v = v + r[0];
-    v = fma(h, r[1], v);
-    v = fma(q, r[nf - 1], v);
-    v = fma(h, r[nf], v);
-    v = fma(q, r[nf + 1], v);
-  }
-  static_cast<V*>(c.rhs)[i] = v;
+  const int nc = c.n, J = i / nc, I = i - J * nc;
+  const V* r = static_cast<const V*>(f.r);
+  static_cast<V*>(c.rhs)[i] = i < nc * nc ? restrict_value<V>(I, J, nc, f.n, c.bc, [&](long long k) { return r[k]; })
+                                          : V(0);
 }
 
 // x_f[x_sel] += P e_c at fine node i (the tile step's formula)
 template <class V>
 __device__ __forceinline__ void prolong_node(const LevelDev& f, const LevelDev& c, int x_sel, int i) {
-  const int nf = f.n, nc = c.n;
-  const int iy = i / nf, ix = i - iy * nf;
-  if (!(i < nf * nf && ix > 0 && iy > 0 && ix < nf - 1 && iy < nf - 1)) return;
+  const int nf = f.n, iy = i / nf, ix = i - iy * nf;
+  if (i >= nf * nf) return;
   const V* e = static_cast<const V*>(c.x[0]);
-  const V* e0 = e + (iy >> 1) * nc;
-  const V* e1 = e + ((iy + 1) >> 1) * nc;
-  const int cx0 = ix >> 1, cx1 = (ix + 1) >> 1;
   V add;
-  const bool ox = ix & 1, oy = iy & 1;
-  if (!ox && !oy) add = e0[cx0];
-  else if (ox && !oy) add = V(0.5) * (e0[cx0] + e0[cx1]);
-  else if (!ox && oy) add = V(0.5) * (e0[cx0] + e1[cx0]);
-  else add = V(0.25) * (((e0[cx0] + e0[cx1]) + e1[cx0]) + e1[cx1]);
+  if (!prolong_value<V>(ix, iy, nf, c.n, f.bc, [&](int k) { return e[k]; }, &add)) return;
   V* x = static_cast<V*>(f.x[x_sel]);
   x[i] = x[i] + add;
 }
@@ -1514,19 +1505,21 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
     if (go) {
       // the coarsest level: the exact solve with the FP64 inverse, one thread per unknown
       const LevelDev& d = sd[c];
-      const int n = d.n, ni = n - 2;
+      const int n = d.n;
+      const UnknownRect ur = unknown_rect(n, d.bc);
       const V* rhs = static_cast<const V*>(d.rhs);
       const double* cinv = s_cinv;
-      for (int v = threadIdx.x; v < m; v += blockDim.x) rd[v] = double(rhs[(v / ni + 1) * n + (v % ni + 1)]);
+      for (int v = threadIdx.x; v < m; v += blockDim.x)
+        rd[v] = double(rhs[(v / ur.nx + ur.y0) * n + (v % ur.nx + ur.x0)]);
       __syncthreads();
       for (int u = threadIdx.x; u < m; u += blockDim.x)
         sol[u] = coarse_dot(cinv + u * m, m, [&](int v) { return rd[v]; });
       __syncthreads();
       V* x = static_cast<V*>(d.x[0]);
       for (int q = threadIdx.x; q < d.pitch; q += blockDim.x) {
-        const int iy = q / n, ix = q - iy * n;
+        const int iy = q / n - ur.y0, ix = q - (q / n) * n - ur.x0;
         V val = V(0);
-        if (q < n * n && ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1) val = V(sol[(iy - 1) * ni + (ix - 1)]);
+        if (q < n * n && ix >= 0 && iy >= 0 && ix < ur.nx && iy < ur.ny) val = V(sol[iy * ur.nx + ix]);
         x[q] = val;
       }
       __syncthreads();
@@ -1645,7 +1638,7 @@ __global__ void __launch_bounds__(256) k_norm_b(EngineDev E, TileList tl) {
   }
 }
 
-// Reject right-hand sides with non-zero boundary entries (one block per problem).
+// Reject right-hand sides with non-zero entries on Dirichlet nodes (one block per problem).
 __global__ void __launch_bounds__(256) k_boundary_check(EngineDev E) {
   pdl_start();
   const int p = blockIdx.x;
@@ -1654,15 +1647,16 @@ __global__ void __launch_bounds__(256) k_boundary_check(EngineDev E) {
   if (st.phase != PH_INIT) return;
   const ProblemDev& P = E.P[p];
   const long long n = n_of_dev(P.L);
+  const int bc = P.lev[P.L].bc;
   int bad = 0;
   for (long long t = threadIdx.x; t < 4 * (n - 1); t += blockDim.x) {
     const long long side = t / (n - 1), k = t - side * (n - 1);
-    long long i;
-    if (side == 0) i = k;                          // bottom row, ix = 0..n-2
-    else if (side == 1) i = k * n + (n - 1);       // right column
-    else if (side == 2) i = (n - 1) * n + (n - 1 - k);   // top row
-    else i = (n - 1 - k) * n;                      // left column
-    if (P.b64[i] != 0.0) bad = 1;
+    long long ix, iy;
+    if (side == 0) { ix = k; iy = 0; }                     // bottom row, ix = 0..n-2
+    else if (side == 1) { ix = n - 1; iy = k; }            // right column
+    else if (side == 2) { ix = n - 1 - k; iy = n - 1; }    // top row
+    else { ix = 0; iy = n - 1 - k; }                       // left column
+    if (is_dirichlet(ix, iy, n, bc) && P.b64[iy * n + ix] != 0.0) bad = 1;
   }
   bad = __syncthreads_or(bad);
   if (bad && threadIdx.x == 0) { st.status = HN_ERR_ARG; st.phase = PH_DONE; }
@@ -1927,9 +1921,15 @@ bool pre_fuses(int) { return true; }
 constexpr long long kTailSmemBudget = 160 * 1024;   // block 0's shared-memory levels
 constexpr long long kTailSmemMax = 212 * 1024;      // with the cluster levels (dynamic part)
 
+// shared memory reserved for a staged coarse inverse: the unknowns of the coarsest level number at
+// most n^2 (free Neumann sides), and an inverse is staged only if it takes <= kCinvSmemMax bytes
+long long tail_cinv_bytes(int coarse) {
+  const long long m = ((1LL << coarse) + 1) * ((1LL << coarse) + 1);
+  return (std::min(m * m * 8, kCinvSmemMax) + 15) / 16 * 16;
+}
+
 int tail_smem_level(int prec, int coarse, int T) {
-  const long long ni = (1LL << coarse) - 1;
-  long long bytes = ni * ni * ni * ni * 8 <= kCinvSmemMax ? ni * ni * ni * ni * 8 : 0;
+  long long bytes = tail_cinv_bytes(coarse);
   int S = coarse;
   for (int l = coarse; l <= T; ++l) {
     bytes += smem_level_bytes(l, prec);
@@ -1942,9 +1942,7 @@ int tail_smem_level(int prec, int coarse, int T) {
 long long tail_smem_bytes(int prec, int coarse, int S) {
   long long bytes = 0;
   for (int l = coarse; l <= S; ++l) bytes += smem_level_bytes(l, prec);
-  const long long ni = (1LL << coarse) - 1;
-  const long long cinv = ni * ni * ni * ni * 8;
-  return bytes + (cinv <= kCinvSmemMax ? (cinv + 15) / 16 * 16 : 0);   // the coarse inverse, when staged
+  return bytes + tail_cinv_bytes(coarse);
 }
 
 // shared memory of the cluster levels (S, T] in distributed shared memory, or -1 if they do not

@@ -15,12 +15,13 @@ __device__ __forceinline__ double kedge() { return -1.0 / 6.0; }
 __device__ __forceinline__ double kcorner() { return -2.0 / 6.0; }
 
 // One thread per node of the padded range.  For node (ix, iy) the 4 surrounding cells are taken
-// in the order sw (ix-1, iy-1), se (ix, iy-1), nw (ix-1, iy), ne (ix, iy); every band entry is
-// the sum of its cells' element-matrix contributions a_c * K in that order, with explicit
-// round-to-nearest operations (no contraction).  Dirichlet nodes are eliminated symmetrically;
-// boundary and padding rows become identity rows.
+// in the order sw (ix-1, iy-1), se (ix, iy-1), nw (ix-1, iy), ne (ix, iy); a cell off the grid
+// (at a free Neumann side) contributes nothing.  Every band entry is the sum of its cells'
+// element-matrix contributions a_c * K in that order, with explicit round-to-nearest operations
+// (no contraction).  Entries towards off-grid or Dirichlet neighbours are exactly 0; Dirichlet
+// nodes are eliminated symmetrically and become identity rows, as do padding rows.
 __global__ void k_assemble(int L, const double* __restrict__ coef, BandPtrs64 band,
-                           double* __restrict__ wdinv, double omega) {
+                           double* __restrict__ wdinv, double omega, int bc) {
   const long long n = n_of_dev(L), N = n * n, nc = n - 1;
   const long long pitch = ((N + kTile - 1) / kTile) * kTile;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -33,12 +34,15 @@ __global__ void k_assemble(int L, const double* __restrict__ coef, BandPtrs64 ba
   if (i < N) {
     iy = i / n;
     ix = i - iy * n;
-    inner = ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1;
+    inner = !is_dirichlet(ix, iy, n, bc);
   }
   if (!inner) {
     v[4] = 1.0;
   } else {
-    auto A = [&](long long ex, long long ey) { return coef ? coef[ey * nc + ex] : 1.0; };
+    auto A = [&](long long ex, long long ey) {
+      if (ex < 0 || ey < 0 || ex >= nc || ey >= nc) return 0.0;   // no cell there
+      return coef ? coef[ey * nc + ex] : 1.0;
+    };
     const double sw = A(ix - 1, iy - 1), se = A(ix, iy - 1), nw = A(ix - 1, iy), ne = A(ix, iy);
     // k = 0: (-1,-1) via sw; 1: (-1,0) via sw, se; 2: (-1,+1) via se; 3: (0,-1) via sw, nw;
     // 4: diagonal via sw, se, nw, ne; 5: (0,+1) via se, ne; 6: (+1,-1) via nw; 7: (+1,0) via
@@ -56,7 +60,7 @@ __global__ void k_assemble(int L, const double* __restrict__ coef, BandPtrs64 ba
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const long long jx = ix + (k % 3 - 1), jy = iy + (k / 3 - 1);
-      if (jx == 0 || jy == 0 || jx == n - 1 || jy == n - 1) v[k] = 0.0;   // Dirichlet column
+      if (jx < 0 || jy < 0 || jx >= n || jy >= n || is_dirichlet(jx, jy, n, bc)) v[k] = 0.0;
     }
   }
 #pragma unroll
@@ -154,9 +158,9 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 }  // namespace
 
 cudaError_t launch_assemble(int L, const double* coef, const BandPtrs64& band, double* wdinv,
-                            double omega, cudaStream_t s) {
+                            double omega, int bc, cudaStream_t s) {
   const long long pitch = pitch_of(L);
-  k_assemble<<<blocks_for(pitch, 256), 256, 0, s>>>(L, coef, band, wdinv, omega);
+  k_assemble<<<blocks_for(pitch, 256), 256, 0, s>>>(L, coef, band, wdinv, omega, bc);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ namespace {
 struct Request {
   unsigned long long ticket = 0;
   int L = 0;
+  unsigned bc = 15u;                 // Dirichlet sides of its operator
   std::vector<double> coef, b, x;
   hn_mg* mg = nullptr;
   int slot = -1;
@@ -114,7 +115,7 @@ void hn_server::run() {
     // build the hierarchies of the admitted requests (explicit copies of their inputs)
     for (Request* r : admitted) {
       hn_band* A = nullptr;
-      hn_status st = hn_band_create(r->L, r->coef.empty() ? nullptr : r->coef.data(), &A);
+      hn_status st = hn_band_create_bc(r->L, r->coef.empty() ? nullptr : r->coef.data(), r->bc, &A);
       hn_mg* mg = nullptr;
       if (st == HN_OK) {
         hn_mg_opts o = opts;
@@ -270,6 +271,7 @@ hn_status hn_mg_submit(hn_server* srv, int L, const double* cell_coef, const dou
   HN_TRY(validate_opts(o, L));
   std::unique_ptr<Request> r(new Request());
   r->L = L;
+  r->bc = o.dirichlet_sides;
   const long long N = N_of(L), cells = (1LL << L) * (1LL << L);
   if (cell_coef) r->coef.assign(cell_coef, cell_coef + cells);
   r->b.assign(b, b + N);

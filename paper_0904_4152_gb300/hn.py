@@ -19,6 +19,9 @@ HN_PREC_FP64, HN_PREC_FP32_DC, HN_PREC_FP16BAND_DC = 0, 1, 2
 HN_OP_SPMV, HN_OP_DEFECT, HN_OP_JACOBI, HN_OP_JACOBI_ZERO = 0, 1, 2, 3
 HN_OP_RESTRICT, HN_OP_PROLONG_ADD, HN_OP_COARSE = 4, 5, 6
 HN_MIN_LEVEL, HN_MAX_LEVEL = 2, 14
+# Dirichlet sides (the others are free Neumann): bottom y = 0, right x = 1, top y = 1, left x = 0
+HN_DIRICHLET_BOTTOM, HN_DIRICHLET_RIGHT, HN_DIRICHLET_TOP, HN_DIRICHLET_LEFT = 1, 2, 4, 8
+HN_DIRICHLET_ALL = 15
 
 STATUS_NAMES = {0: "HN_OK", 1: "HN_ERR_ARG", 2: "HN_ERR_OOM", 3: "HN_ERR_BUDGET", 4: "HN_ERR_CUDA",
                 5: "HN_ERR_NOT_CONVERGED", 6: "HN_ERR_NONFINITE", 7: "HN_PENDING",
@@ -26,7 +29,7 @@ STATUS_NAMES = {0: "HN_OK", 1: "HN_ERR_ARG", 2: "HN_ERR_OOM", 3: "HN_ERR_BUDGET"
 
 # symbols declared in include/*.h (checked by the tests against the shared library)
 EXPORTS = [
-    "hn_band_create", "hn_band_get", "hn_band_level", "hn_band_nodes", "hn_band_destroy",
+    "hn_band_create", "hn_band_create_bc", "hn_band_get", "hn_band_level", "hn_band_nodes", "hn_band_destroy",
     "hn_mg_opts_default", "hn_mg_setup", "hn_mg_solve", "hn_mg_solve_batch", "hn_mg_device_bytes",
     "hn_mg_destroy", "hn_mg_apply", "hn_mg_get_inner_bands", "hn_server_create", "hn_mg_submit",
     "hn_mg_poll", "hn_server_query", "hn_server_destroy", "hn_last_error", "hn_version",
@@ -46,7 +49,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("coarse_L", ctypes.c_int), ("pre", ctypes.c_int), ("post", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("max_outer", ctypes.c_int),
                 ("inner_max", ctypes.c_int), ("omega", ctypes.c_double), ("tol", ctypes.c_double),
-                ("inner_tol", ctypes.c_double), ("prec", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("inner_tol", ctypes.c_double), ("prec", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("dirichlet_sides", ctypes.c_uint)]
 
 
 class Stats(ctypes.Structure):
@@ -90,6 +94,7 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
         L.hn_band_create.argtypes = [ip, vp, ctypes.POINTER(vp)]
+        L.hn_band_create_bc.argtypes = [ip, vp, ctypes.c_uint, ctypes.POINTER(vp)]
         L.hn_band_get.argtypes = [vp, vp]
         L.hn_band_level.argtypes = [vp]
         L.hn_band_nodes.argtypes = [vp]
@@ -182,6 +187,18 @@ def hn_band_create(L, cell_coef=None):
             raise ValueError("cell_coef needs (2^L)^2 entries")
         c = _host_ptr(cell_coef, np.float64)
     _check(lib().hn_band_create(L, c, ctypes.byref(h)))
+    return h
+
+
+def hn_band_create_bc(L, cell_coef=None, dirichlet_sides=HN_DIRICHLET_ALL):
+    h = ctypes.c_void_p()
+    c = None
+    if cell_coef is not None:
+        cell_coef = np.ascontiguousarray(cell_coef, dtype=np.float64)
+        if cell_coef.size != (1 << L) ** 2:
+            raise ValueError("cell_coef needs (2^L)^2 entries")
+        c = _host_ptr(cell_coef, np.float64)
+    _check(lib().hn_band_create_bc(L, c, dirichlet_sides, ctypes.byref(h)))
     return h
 
 

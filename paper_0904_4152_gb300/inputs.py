@@ -5,7 +5,9 @@ SplitMix64 generator (Steele, Lea and Flood, "Fast splittable pseudorandom numbe
 OOPSLA 2014), whose output k (k = 0, 1, ...) for a seed s is mix(s + (k+1) * 0x9E3779B97F4A7C15);
 U[0,1) uses the top 53 bits.  Workload recipes:
 
-* right-hand sides: U[-1, 1] on interior nodes, 0 on the Dirichlet boundary;
+* right-hand sides: U[-1, 1] on interior nodes, 0 on the Dirichlet boundary; with a side mask
+  (bit 1 y = 0, 2 x = 1, 4 y = 1, 8 x = 0 Dirichlet), U[-1, 1] on every node off the Dirichlet
+  sides, including the free Neumann sides;
 * coefficient fields: a = exp(sigma * g) per cell, g a smooth Gaussian field with
   squared-exponential covariance (correlation length ell) sampled by M random Fourier features,
   g(x) = sqrt(2/M) sum_m cos(w_m . x + p_m), w_m ~ N(0, ell^-2 I), p_m ~ U[0, 2 pi), evaluated at
@@ -50,6 +52,26 @@ def rhs_uniform(L: int, seed: int) -> np.ndarray:
     n = n_of(L)
     b = np.zeros(n * n)
     m = interior_mask(L)
+    b[m] = uniform01(seed, int(m.sum())) * 2.0 - 1.0
+    return b
+
+
+def unknown_mask(L: int, dirichlet_sides: int) -> np.ndarray:
+    """Nodes that are not on a Dirichlet side of the side mask."""
+    n = n_of(L)
+    m = np.ones((n, n), dtype=bool)
+    if dirichlet_sides & 1: m[0, :] = False
+    if dirichlet_sides & 2: m[:, -1] = False
+    if dirichlet_sides & 4: m[-1, :] = False
+    if dirichlet_sides & 8: m[:, 0] = False
+    return m.ravel()
+
+
+def rhs_uniform_bc(L: int, seed: int, dirichlet_sides: int) -> np.ndarray:
+    """Right-hand side U[-1,1] on the unknowns of a side mask, 0 on its Dirichlet sides."""
+    n = n_of(L)
+    b = np.zeros(n * n)
+    m = unknown_mask(L, dirichlet_sides)
     b[m] = uniform01(seed, int(m.sum())) * 2.0 - 1.0
     return b
 

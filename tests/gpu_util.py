@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from paper_0904_4152_gb300 import inputs as I
 
 
 def require_gpu():
@@ -24,8 +25,8 @@ def coef_levels(L, coef, coarse=2):
     return out
 
 
-def solve(hn, L, b, coef=None, **opts):
-    A = hn.hn_band_create(L, coef)
+def solve(hn, L, b, coef=None, bc=O.ALL_DIRICHLET, **opts):
+    A = hn.hn_band_create_bc(L, coef, bc)
     try:
         mg = hn.hn_mg_setup(A, **opts)
     finally:
@@ -37,8 +38,8 @@ def solve(hn, L, b, coef=None, **opts):
     return x, st, status
 
 
-def oracle_relres(L, coef, b, x):
-    A = O.assemble(L, coef)
+def oracle_relres(L, coef, b, x, bc=O.ALL_DIRICHLET):
+    A = O.assemble(L, coef, bc=bc)
     return np.linalg.norm(O.defect(L, A, b, x)) / np.linalg.norm(b)
 
 
@@ -47,6 +48,14 @@ def rand_interior(L, seed, dtype=np.float64):
     n = (1 << L) + 1
     v = rng.uniform(-1, 1, n * n)
     v[~interior(L)] = 0.0
+    return v.astype(dtype)
+
+
+def rand_unknowns(L, bc, seed, dtype=np.float64):
+    """U[-1,1] on the nodes off the Dirichlet sides of the side mask bc, 0 on them."""
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(-1, 1, ((1 << L) + 1) ** 2)
+    v[~I.unknown_mask(L, bc)] = 0.0
     return v.astype(dtype)
 
 

@@ -470,3 +470,109 @@ def test_oracle_axpy_single_rounding():
     xd, yd = x.astype(np.float64), y.astype(np.float64)
     assert np.array_equal(O.axpy(2.0, np.ones(3), np.ones(3)), np.full(3, 3.0))
     assert np.all(np.abs(O.axpy(0.5, xd, yd) - (0.5 * xd + yd)) <= 2.0 ** -53 * (np.abs(0.5 * xd) + np.abs(yd)))
+
+
+# ---------------------------------------- mixed free-Neumann / Dirichlet boundaries (Sec. 6.2.2)
+LR = O.DIRICHLET_LEFT_RIGHT          # Dirichlet at x = 0, 1; free Neumann at y = 0, 1
+
+
+def _unknown_mask(L, bc):
+    n = (1 << L) + 1
+    m = np.ones((n, n), dtype=bool)
+    if bc & 1: m[0, :] = False
+    if bc & 2: m[:, -1] = False
+    if bc & 4: m[-1, :] = False
+    if bc & 8: m[:, 0] = False
+    return m.ravel()
+
+
+@pytest.mark.parametrize("bc", [LR, 1, 7, 8])
+def test_mixed_bc_operator_symmetric_and_natural(bc):
+    L = 5
+    n, N = (1 << L) + 1, ((1 << L) + 1) ** 2
+    A = O.assemble(L, None, bc=bc)
+    unk = _unknown_mask(L, bc)
+    # symmetric: a_k[i] = a_{8-k}[i + off_k]
+    for k in range(9):
+        dy, dx = k // 3 - 1, k % 3 - 1
+        for i in np.flatnonzero(unk)[::7]:
+            iy, ix = divmod(i, n)
+            jy, jx = iy + dy, ix + dx
+            if 0 <= jx < n and 0 <= jy < n:
+                assert A[k, i] == A[8 - k, jy * n + jx]
+    # constants are in the kernel away from Dirichlet nodes: zero row sums on unknown rows
+    # whose neighbours are all unknowns (natural boundary condition on the free sides)
+    grid = unk.reshape(n, n)
+    pad = np.pad(grid, 1, constant_values=True)
+    ok = np.ones_like(grid)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            ok &= pad[1 + dy:1 + dy + n, 1 + dx:1 + dx + n]
+    rows = np.flatnonzero(ok.ravel() & unk)
+    assert len(rows) > 0
+    assert np.max(np.abs(A[:, rows].sum(axis=0))) <= 1e-14
+    # Dirichlet rows are identity rows
+    d = np.flatnonzero(~unk)
+    assert np.all(A[4, d] == 1.0) and np.all(A[[0, 1, 2, 3, 5, 6, 7, 8]][:, d] == 0.0)
+
+
+def test_mixed_bc_free_side_stencil_closed_form():
+    # a = 1: an interior node of a free side keeps half the interior stencil 8/3, -1/3:
+    # diagonal 4/3, along the side -1/6, into the domain -1/3 (edge and both corners)
+    L = 4
+    n, N = (1 << L) + 1, ((1 << L) + 1) ** 2
+    A = O.assemble(L, None, bc=LR)
+    i = 0 * n + 5                        # bottom side (y = 0), ix = 5
+    expect = {4: 4 / 3, 3: -1 / 6, 5: -1 / 6, 7: -1 / 3, 6: -1 / 3, 8: -1 / 3, 0: 0.0, 1: 0.0, 2: 0.0}
+    for k, v in expect.items():
+        assert abs(A[k, i] - v) <= 4e-16, (k, A[k, i], v)
+
+
+def test_mixed_bc_transfers_adjoint_and_exact():
+    Lf = 5
+    nf, nc = (1 << Lf) + 1, (1 << (Lf - 1)) + 1
+    rng = np.random.default_rng(11)
+    r = rng.uniform(-1, 1, nf * nf) * _unknown_mask(Lf, LR)
+    e = rng.uniform(-1, 1, nc * nc) * _unknown_mask(Lf - 1, LR)
+    Rr = O.restrict(Lf, r, bc=LR)
+    Pe = O.prolong_add(Lf, e, np.zeros(nf * nf), bc=LR)
+    assert abs(np.dot(Rr, e) - np.dot(r, Pe)) <= 1e-12 * np.sum(np.abs(Rr * e))
+    # P reproduces g(x) (alpha + beta y) for g piecewise linear on the coarse grid, zero at
+    # x = 0, 1: exact on every unknown node, including the free sides y = 0, 1
+    g = rng.uniform(-1, 1, nc)
+    g[0] = g[-1] = 0.0
+    Yc = np.arange(nc) / (nc - 1)
+    ec = (g[None, :] * (0.3 + 0.7 * Yc[:, None])).ravel()
+    gf = np.interp(np.arange(nf) / 2.0, np.arange(nc), g)
+    Yf = np.arange(nf) / (nf - 1)
+    expect = (gf[None, :] * (0.3 + 0.7 * Yf[:, None])).ravel()
+    got = O.prolong_add(Lf, ec, np.zeros(nf * nf), bc=LR)
+    assert np.max(np.abs(got - expect)) <= 1e-15
+
+
+def test_mixed_bc_coarse_solve_exact():
+    L = 3
+    A = O.assemble(L, None, bc=LR)
+    unk = _unknown_mask(L, LR)
+    b = np.random.default_rng(5).uniform(-1, 1, unk.size) * unk
+    x = O.coarse_solve(L, A, b, bc=LR)
+    r = O.defect(L, A, b, x)
+    assert np.max(np.abs(r)) <= 1e-13 and np.all(x[~unk] == 0.0)
+
+
+def test_mixed_bc_manufactured_solution_second_order():
+    # u = sin(pi x) cos(pi y): zero at x = 0, 1, zero normal derivative at y = 0, 1
+    errs = []
+    for L in range(3, 8):
+        b = O.load_sincos(L)
+        x, st = O.mg_solve(L, b, tol=1e-11, bc=LR)
+        assert st["converged"]
+        errs.append(O.l2_error_sincos(L, x))
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.7 < q < 4.3 for q in ratios[1:]), ratios
+    assert errs[-1] < 2e-4
+
+
+def test_boundary_mask_needs_a_dirichlet_side():
+    with pytest.raises(ValueError):
+        O.assemble(3, None, bc=0)
