@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may use this package; the product library never does.  Each function is a thin
 ctypes call into the C++ oracle, which restates the mathematics of the HONEI paper's Poisson
-client (Sec. 2.1 discretisation, Sec. 6.2 multigrid and mixed-precision defect correction).
+client (Sec. 2.1 discretisation, Sec. 6.2 multigrid and mixed-precision defect correction, CG
+with a multigrid preconditioner and CG as the coarse solver).
 
 Vectors are numpy float64 arrays of length N = (2^L+1)^2, node i = iy*n + ix.  Bands are a
 (9, N) float64 array, band k holding A[i, i + dy*n + dx] with (dy, dx) = (k//3 - 1, k%3 - 1).
@@ -65,7 +66,7 @@ def lib():
         L.or_jacobi.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, dp]
         L.or_restrict.argtypes = [ctypes.c_int, dp, dp]
         L.or_prolong_add.argtypes = [ctypes.c_int, dp, dp]
-        L.or_coarse_solve.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.or_coarse_solve.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int]
         L.or_coarse_solve.restype = ctypes.c_int
         L.or_quantize_fp16.argtypes = [ctypes.c_int, dp, fp, up]
         L.or_spmv_rowsum.argtypes = [ctypes.c_int, fp, fp, fp]
@@ -73,9 +74,16 @@ def lib():
         L.or_jacobi_f32.argtypes = [ctypes.c_int, fp, ctypes.c_float, fp, fp, fp, ctypes.c_int]
         L.or_mg_solve.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                  ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp,
-                                  ctypes.POINTER(Stats)]
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, dp, ctypes.POINTER(Stats)]
         L.or_mg_solve.restype = ctypes.c_int
+        L.or_pcg_solve.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(Stats)]
+        L.or_pcg_solve.restype = ctypes.c_int
+        L.or_precondition.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp]
+        L.or_precondition.restype = ctypes.c_int
         L.or_load_sinsin.argtypes = [ctypes.c_int, dp]
         L.or_l2_error_sinsin.argtypes = [ctypes.c_int, dp]
         L.or_l2_error_sinsin.restype = ctypes.c_double
@@ -163,13 +171,15 @@ def prolong_add(Lf, ec, xf, bc=ALL_DIRICHLET):
     return out
 
 
-def coarse_solve(Lc, bands, b, bc=ALL_DIRICHLET):
+def coarse_solve(Lc, bands, b, bc=ALL_DIRICHLET, cg=False, steps=False):
+    """Coarsest-level solve: exact (Cholesky) or unpreconditioned CG (cg=True); with steps=True
+    also returns the CG steps taken."""
     x = np.zeros(N_of(Lc))
     _sides(bc)
-    rc = lib().or_coarse_solve(Lc, _p(_f64(bands)), _p(_f64(b)), _p(x))
-    if rc != 0:
+    rc = lib().or_coarse_solve(Lc, _p(_f64(bands)), _p(_f64(b)), _p(x), 1 if cg else 0)
+    if rc < 0:
         raise ValueError("coarse matrix not positive definite")
-    return x
+    return (x, rc) if steps else x
 
 
 def fp16_rne(v):
@@ -224,7 +234,7 @@ def jacobi_f32(L, bands, omega, b, x, rowsum):
 
 def mg_solve(L, b, coef=None, x0=None, prec=PREC_FP64, pre=2, post=2, omega=0.7, tol=1e-8,
              max_cycles=100, max_outer=50, inner_tol=1e-2, inner_max=10, coarse_L=2,
-             history=False, bc=ALL_DIRICHLET):
+             history=False, bc=ALL_DIRICHLET, coarse_cg=False):
     """Multigrid solve; returns (x, stats dict[, relres history])."""
     _sides(bc)
     N = N_of(L)
@@ -234,8 +244,8 @@ def mg_solve(L, b, coef=None, x0=None, prec=PREC_FP64, pre=2, post=2, omega=0.7,
     hist = np.full(hlen, np.nan) if history else None
     st = Stats()
     rc = lib().or_mg_solve(L, _p(c), _p(_f64(b)), _p(x), prec, pre, post, omega, tol,
-                           max_cycles, max_outer, inner_tol, inner_max, coarse_L, _p(hist),
-                           ctypes.byref(st))
+                           max_cycles, max_outer, inner_tol, inner_max, coarse_L,
+                           1 if coarse_cg else 0, _p(hist), ctypes.byref(st))
     if rc < 0:
         raise ValueError("bad arguments to the oracle solve")
     stats = dict(cycles=st.cycles, outer_iters=st.outer_iters, inner_cycles=st.inner_cycles,
@@ -243,6 +253,41 @@ def mg_solve(L, b, coef=None, x0=None, prec=PREC_FP64, pre=2, post=2, omega=0.7,
     if history:
         return x, stats, hist[~np.isnan(hist)]
     return x, stats
+
+
+def pcg_solve(L, b, coef=None, x0=None, prec=PREC_FP64, pre=2, post=2, omega=0.7, tol=1e-8,
+              max_iters=100, coarse_L=2, coarse_cg=False, history=False, bc=ALL_DIRICHLET):
+    """Conjugate gradients preconditioned by one V cycle (prec 0: FP64 cycle; 1 / 2: FP32 /
+    FP16-band cycle on the scaled residual).  Returns (x, stats dict[, recursive relres history]);
+    stats: outer_iters = CG steps, cycles = preconditioner applications, relres = true residual."""
+    _sides(bc)
+    N = N_of(L)
+    x = np.zeros(N) if x0 is None else _f64(x0).copy()
+    c = None if coef is None else _f64(coef)
+    hist = np.full(max_iters + 2, np.nan) if history else None
+    st = Stats()
+    rc = lib().or_pcg_solve(L, _p(c), _p(_f64(b)), _p(x), prec, pre, post, omega, tol, max_iters,
+                            coarse_L, 1 if coarse_cg else 0, _p(hist), ctypes.byref(st))
+    if rc < 0:
+        raise ValueError("bad arguments to the oracle PCG solve")
+    stats = dict(cycles=st.cycles, outer_iters=st.outer_iters, inner_cycles=st.inner_cycles,
+                 converged=bool(st.converged), relres=st.relres)
+    if history:
+        return x, stats, hist[~np.isnan(hist)]
+    return x, stats
+
+
+def precondition(L, r, coef=None, prec=PREC_FP64, pre=2, post=2, omega=0.7, coarse_L=2,
+                 coarse_cg=False, bc=ALL_DIRICHLET):
+    """z = M r: one V cycle from zero on the right-hand side r (the PCG preconditioner)."""
+    _sides(bc)
+    z = np.zeros(N_of(L))
+    c = None if coef is None else _f64(coef)
+    rc = lib().or_precondition(L, _p(c), prec, pre, post, omega, coarse_L, 1 if coarse_cg else 0,
+                               _p(_f64(r)), _p(z))
+    if rc < 0:
+        raise ValueError("bad arguments to the oracle preconditioner")
+    return z
 
 
 def load_sincos(L):

@@ -14,11 +14,15 @@
 // every operation rounds as written.
 //
 // Readings where the paper is silent (each also listed in the design notes):
-//  * boundary: zero Dirichlet on all four sides, eliminated symmetrically (row and column zeroed,
-//    diagonal 1, right-hand side 0);
+//  * Dirichlet nodes eliminated symmetrically (row and column zeroed, diagonal 1, right-hand
+//    side 0);
 //  * coarse operators by re-discretisation, coarse cell coefficient = mean of its 4 children;
 //  * transfers: bilinear interpolation P (boundary rows/columns zeroed) and restriction R = P^T;
-//  * coarsest level solved exactly (dense Cholesky) instead of the paper's unpreconditioned CG;
+//  * boundary: a mask of Dirichlet sides (all four by default); the other sides are free
+//    Neumann (natural) boundaries whose nodes are unknowns;
+//  * coarsest level solved exactly (dense Cholesky), or by the paper's unpreconditioned CG to a
+//    relative residual of 1e-13 (at most 2m + 10 steps for m unknowns);
+//  * multigrid as a preconditioner of CG: one V cycle from zero per application;
 //  * stopping test ||b - A x||_2 / ||b||_2 <= tol after a complete cycle, x0 given (0 default);
 //  * defect correction: the FP64 defect is scaled by 1/||d|| before the cast to the inner
 //    precision, the inner cycles stop at a relative inner residual <= inner_tol (cap inner_max);
@@ -243,15 +247,25 @@ void restrict_(int Lf, const T* rf, T* rc) {
     }
 }
 
-// ------------------------------------------------------------------- exact coarse solve
-// Dense Cholesky of the coarsest matrix restricted to its unknowns (the paper uses
-// unpreconditioned CG there; on this tiny SPD system both give the exact solution up to rounding).
+// ------------------------------------------------------------------- coarse solvers
+// The coarsest matrix restricted to its unknowns, solved either exactly (dense Cholesky) or, as
+// in the paper's configuration of the solver (Sec. 6.2), by unpreconditioned conjugate gradients.
+// CG (Hestenes and Stiefel 1952), all in FP64: x_0 = 0, r_0 = p_0 = b; per step q = A p,
+// alpha = (r, r) / (p, q), x += alpha p, r -= alpha q, then stop once ||r|| <= kCgTol ||b|| (or
+// after cg_max_steps(m) steps), else beta = (r_new, r_new) / (r, r), p = r + beta p.  Inner
+// products are plain sequential FP64 sums over the unknowns in row-major order.
+constexpr double kCgTol = 1e-13;
+inline long cg_max_steps(long m) { return 2 * m + 10; }
+
 struct CoarseSolver {
   int L = 0;
   long n = 0, m = 0;              // nodes per side, unknowns (nodes that are not Dirichlet)
   std::vector<long> node;         // node of unknown u, row-major order
+  std::vector<double> A;          // the matrix on the unknowns, m*m row-major
   std::vector<double> chol;       // lower factor, m*m row-major
   bool ok = false;
+  bool cg = false;                // solve by CG instead of the Cholesky factor
+  mutable long last_steps = 0;    // CG steps taken by the last solve
   void factor(int Lc, const double* bands) {
     L = Lc; n = n_of(Lc); const long N = N_of(Lc);
     node.clear();
@@ -260,7 +274,7 @@ struct CoarseSolver {
       for (long ix = 0; ix < n; ++ix)
         if (!is_boundary(ix, iy, n)) { unk[iy * n + ix] = (long)node.size(); node.push_back(iy * n + ix); }
     m = (long)node.size();
-    std::vector<double> A(m * m, 0.0);
+    A.assign(m * m, 0.0);
     for (long I = 0; I < m; ++I) {
       const long i = node[I], iy = i / n, ix = i % n;
       for (int k = 0; k < 9; ++k) {
@@ -283,10 +297,47 @@ struct CoarseSolver {
       }
     }
   }
+  // CG on the unknowns: y = A^{-1} rhs up to the stopping rule above
+  void solve_cg(const std::vector<double>& rhs, std::vector<double>& y) const {
+    std::vector<double> r(rhs), p(rhs), q(m);
+    y.assign(m, 0.0);
+    auto dot = [&](const std::vector<double>& u, const std::vector<double>& v) {
+      double t = 0.0;
+      for (long i = 0; i < m; ++i) t += u[i] * v[i];
+      return t;
+    };
+    double rr = dot(r, r);
+    const double stop = kCgTol * kCgTol * rr;
+    last_steps = 0;
+    if (rr == 0.0) return;
+    for (long k = 0; k < cg_max_steps(m); ++k) {
+      for (long i = 0; i < m; ++i) {
+        double t = 0.0;
+        for (long j = 0; j < m; ++j) t += A[i * m + j] * p[j];
+        q[i] = t;
+      }
+      const double alpha = rr / dot(p, q);
+      for (long i = 0; i < m; ++i) { y[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+      ++last_steps;
+      const double rr_new = dot(r, r);
+      if (rr_new <= stop) break;
+      const double beta = rr_new / rr;
+      rr = rr_new;
+      for (long i = 0; i < m; ++i) p[i] = r[i] + beta * p[i];
+    }
+  }
   // x = A^{-1} b on the unknowns, 0 on Dirichlet nodes.  Solved in FP64, then stored as T.
   template <typename T>
   void solve(const T* b, T* x) const {
     std::vector<double> y(m);
+    if (cg) {
+      std::vector<double> rhs(m);
+      for (long i = 0; i < m; ++i) rhs[i] = (double)b[node[i]];
+      solve_cg(rhs, y);
+      for (long i = 0; i < n * n; ++i) x[i] = 0;
+      for (long i = 0; i < m; ++i) x[node[i]] = (T)y[i];
+      return;
+    }
     for (long i = 0; i < m; ++i) {
       double s = (double)b[node[i]];
       for (long k = 0; k < i; ++k) s -= chol[i * m + k] * y[k];
@@ -396,8 +447,9 @@ struct Hierarchy {
   std::vector<Level> lev;    // lev[0] = finest
   CoarseSolver cs;
   int coarse_L;
-  void build(int L, const double* coef, int coarse, int inner_prec) {
+  void build(int L, const double* coef, int coarse, int inner_prec, bool coarse_cg = false) {
     coarse_L = coarse;
+    cs.cg = coarse_cg;
     std::vector<double> a;
     if (coef) a.assign(coef, coef + (n_of(L) - 1) * (n_of(L) - 1));
     for (int l = L; l >= coarse; --l) {
@@ -485,12 +537,15 @@ void or_jacobi(int L, const double* bands, double omega, const double* b, const 
 }
 void or_restrict(int Lf, const double* rf, double* rc) { restrict_<double>(Lf, rf, rc); }
 void or_prolong_add(int Lf, const double* ec, double* xf) { prolong_add<double>(Lf, ec, xf); }
-int or_coarse_solve(int Lc, const double* bands, const double* b, double* x) {
+// exact (Cholesky, cg = 0) or CG (cg = 1) coarse solve; returns the CG steps taken (0 for the
+// exact solve) or -1 if the matrix is not positive definite
+int or_coarse_solve(int Lc, const double* bands, const double* b, double* x, int cg) {
   CoarseSolver cs;
   cs.factor(Lc, bands);
   if (!cs.ok) return -1;
+  cs.cg = cg != 0;
   cs.solve<double>(b, x);
-  return 0;
+  return (int)cs.last_steps;
 }
 uint16_t or_fp16_rne(double v) { return fp16_rne(v); }
 float or_fp16_to_float(uint16_t h) { return fp16_to_float(h); }
@@ -521,11 +576,11 @@ void or_jacobi_f32(int L, const float* bands, float omega, const float* b, const
 // Returns 0 on convergence, 1 if the cycle cap was hit, -1 on bad arguments.
 int or_mg_solve(int L, const double* coef, const double* b, double* x, int prec, int pre, int post,
                 double omega, double tol, int max_cycles, int max_outer, double inner_tol,
-                int inner_max, int coarse_L, double* relres_hist, or_stats* st) {
+                int inner_max, int coarse_L, int coarse_cg, double* relres_hist, or_stats* st) {
   if (L < coarse_L || coarse_L < 2 || prec < 0 || prec > 3) return -1;
   g_rowsum_form = false;
   Hierarchy H;
-  H.build(L, coef, coarse_L, prec);
+  H.build(L, coef, coarse_L, prec, coarse_cg != 0);
   if (!H.cs.ok) return -1;
   const long N = N_of(L);
   const double* A = H.lev[0].a64.data();
@@ -599,6 +654,108 @@ int or_mg_solve(int L, const double* coef, const double* b, double* x, int prec,
     }
   }
   if (st) *st = s;
+  return s.converged ? 0 : 1;
+}
+
+// The multigrid preconditioner: z = M r, one V(pre, post) cycle from z = 0 on the right-hand side
+// r.  prec 0: in FP64.  prec 1 / 2: in the inner precision (FP32 bands / FP16-band storage) on
+// r / ||r|| cast to float, the result scaled back by ||r|| in FP64 (as in the defect correction).
+static void precondition(const Hierarchy& H, int L, int prec, int pre, int post, double omega,
+                         const double* r, double* z) {
+  const long N = N_of(L);
+  if (prec == 0) {
+    for (long i = 0; i < N; ++i) z[i] = 0.0;
+    vcycle<double>(H, 0, z, r, pre, post, omega);
+    return;
+  }
+  const double rn = norm2<double>(N, r);
+  if (rn == 0.0) { for (long i = 0; i < N; ++i) z[i] = 0.0; return; }
+  std::vector<float> rh(N), c(N, 0.0f);
+  for (long i = 0; i < N; ++i) rh[i] = (float)(r[i] / rn);
+  vcycle<float>(H, 0, c.data(), rh.data(), pre, post, (float)omega);
+  for (long i = 0; i < N; ++i) z[i] = rn * (double)c[i];
+}
+
+static double dot64(long N, const double* u, const double* v) {
+  double t = 0.0;
+  for (long i = 0; i < N; ++i) t += u[i] * v[i];
+  return t;
+}
+
+// One application of the preconditioner (for the tests of its symmetry and of the PCG loop).
+int or_precondition(int L, const double* coef, int prec, int pre, int post, double omega,
+                    int coarse_L, int coarse_cg, const double* r, double* z) {
+  if (L < coarse_L || coarse_L < 2 || prec < 0 || prec > 2) return -1;
+  g_rowsum_form = false;
+  Hierarchy H;
+  H.build(L, coef, coarse_L, prec, coarse_cg != 0);
+  if (!H.cs.ok) return -1;
+  precondition(H, L, prec, pre, post, omega, r, z);
+  g_rowsum_form = false;
+  return 0;
+}
+
+// Conjugate gradients preconditioned by one multigrid cycle (a solver plugged into another as its
+// preconditioner, Sec. 4.1 / Sec. 6.2).  FP64 throughout except inside the preconditioner:
+//   r = b - A x, z = M r, p = z, rho = (r, z); then per step
+//   q = A p, alpha = rho / (p, q), x += alpha p, r -= alpha q,
+//   stop if ||r|| <= tol ||b|| (or max_iters steps), z = M r, rho' = (r, z), p = z + (rho'/rho) p.
+// ||r|| is the recursively updated residual; relres_hist (length >= max_iters + 1) receives it
+// before the first and after every step.  st.outer_iters = steps, st.cycles = preconditioner
+// applications, st.relres = the final true ||b - A x|| / ||b||.
+int or_pcg_solve(int L, const double* coef, const double* b, double* x, int prec, int pre, int post,
+                 double omega, double tol, int max_iters, int coarse_L, int coarse_cg,
+                 double* relres_hist, or_stats* st) {
+  if (L < coarse_L || coarse_L < 2 || prec < 0 || prec > 2 || max_iters < 0) return -1;
+  g_rowsum_form = false;
+  Hierarchy H;
+  H.build(L, coef, coarse_L, prec, coarse_cg != 0);
+  if (!H.cs.ok) return -1;
+  const long N = N_of(L);
+  const double* A = H.lev[0].a64.data();
+  const double bnorm = norm2<double>(N, b);
+  or_stats s = {0, 0, 0, 0, 0.0};
+  int hist = 0;
+  if (bnorm == 0.0) {
+    for (long i = 0; i < N; ++i) x[i] = 0.0;
+    s.converged = 1;
+    if (relres_hist) relres_hist[0] = 0.0;
+    if (st) *st = s;
+    g_rowsum_form = false;
+    return 0;
+  }
+  std::vector<double> r(N), z(N), p(N), q(N);
+  defect<double>(L, A, b, x, r.data());
+  double rr = norm2<double>(N, r.data()) / bnorm;
+  if (relres_hist) relres_hist[hist++] = rr;
+  if (rr > tol && max_iters > 0) {
+    precondition(H, L, prec, pre, post, omega, r.data(), z.data());
+    ++s.cycles;
+    p = z;
+    double rho = dot64(N, r.data(), z.data());
+    for (;;) {
+      spmv<double>(L, A, p.data(), q.data());
+      const double alpha = rho / dot64(N, p.data(), q.data());
+      for (long i = 0; i < N; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+      ++s.outer_iters;
+      rr = norm2<double>(N, r.data()) / bnorm;
+      if (relres_hist) relres_hist[hist++] = rr;
+      if (!(rr > tol) || s.outer_iters >= max_iters) break;
+      precondition(H, L, prec, pre, post, omega, r.data(), z.data());
+      ++s.cycles;
+      const double rho_new = dot64(N, r.data(), z.data());
+      const double beta = rho_new / rho;
+      rho = rho_new;
+      for (long i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+  }
+  s.converged = rr <= tol;
+  s.inner_cycles = prec == 0 ? 0 : s.cycles;
+  std::vector<double> t(N);
+  defect<double>(L, A, b, x, t.data());
+  s.relres = norm2<double>(N, t.data()) / bnorm;
+  if (st) *st = s;
+  g_rowsum_form = false;
   return s.converged ? 0 : 1;
 }
 

@@ -576,3 +576,120 @@ def test_mixed_bc_manufactured_solution_second_order():
 def test_boundary_mask_needs_a_dirichlet_side():
     with pytest.raises(ValueError):
         O.assemble(3, None, bc=0)
+
+
+# ------------------------------------------ CG coarse solver and CG with a multigrid preconditioner
+@pytest.mark.parametrize("Lc,bc", [(2, 15), (3, 15), (4, 15), (3, LR), (4, 1)])
+def test_coarse_cg_matches_cholesky(Lc, bc):
+    coef = I.lognormal_coef(Lc, 70 + Lc)
+    A = O.assemble(Lc, coef, bc=bc)
+    b = np.random.default_rng(Lc).uniform(-1, 1, A.shape[1]) * _unknown_mask(Lc, bc)
+    x_cg, steps = O.coarse_solve(Lc, A, b, bc=bc, cg=True, steps=True)
+    x_ex = O.coarse_solve(Lc, A, b, bc=bc)
+    assert 0 < steps <= 2 * int(_unknown_mask(Lc, bc).sum()) + 10
+    assert np.max(np.abs(x_cg - x_ex)) <= 1e-11 * np.max(np.abs(x_ex))
+    assert np.max(np.abs(O.defect(Lc, A, b, x_cg))) <= 1e-12 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("Lc,bc", [(2, 15), (3, 15), (3, LR)])
+def test_coarse_cg_finite_termination(Lc, bc):
+    # exact-arithmetic CG ends after as many steps as the matrix has distinct eigenvalues whose
+    # eigenvectors the right-hand side excites; a = 1 has many repeated eigenvalues
+    A = O.assemble(Lc, None, bc=bc)
+    n = (1 << Lc) + 1
+    unk = np.flatnonzero(_unknown_mask(Lc, bc))
+    M = np.zeros((len(unk), len(unk)))
+    pos = {g: i for i, g in enumerate(unk)}
+    for i, g in enumerate(unk):
+        iy, ix = divmod(g, n)
+        for k in range(9):
+            jy, jx = iy + k // 3 - 1, ix + k % 3 - 1
+            if 0 <= jx < n and 0 <= jy < n and jy * n + jx in pos:
+                M[i, pos[jy * n + jx]] = A[k, g]
+    ev = np.linalg.eigvalsh(M)
+    distinct = 1 + int(np.sum(np.diff(np.sort(ev)) > 1e-9 * ev.max()))
+    b = np.zeros(A.shape[1])
+    b[unk] = np.random.default_rng(3).uniform(-1, 1, len(unk))
+    _, steps = O.coarse_solve(Lc, A, b, bc=bc, cg=True, steps=True)
+    assert steps <= distinct + 1, (steps, distinct)
+
+
+def test_mg_with_coarse_cg_follows_the_exact_coarse_solve():
+    L = 7
+    coef = I.lognormal_coef(L, 5)
+    b = I.rhs_uniform(L, 6)
+    for coarse_L in (2, 3):
+        x1, s1 = O.mg_solve(L, b, coef=coef, coarse_L=coarse_L)
+        x2, s2 = O.mg_solve(L, b, coef=coef, coarse_L=coarse_L, coarse_cg=True)
+        assert s1["cycles"] == s2["cycles"] and s2["converged"]
+        assert np.max(np.abs(x1 - x2)) <= 1e-9 * np.max(np.abs(x1))
+
+
+@pytest.mark.parametrize("bc,coarse_cg", [(15, False), (15, True), (LR, False)])
+def test_preconditioner_is_symmetric(bc, coarse_cg):
+    # V(nu, nu) with damped Jacobi and R = P^T is an A-self-adjoint error propagation, so
+    # M = (I - E) A^-1 is symmetric: <M u, v> = <u, M v>
+    L = 5
+    coef = I.lognormal_coef(L, 8)
+    rng = np.random.default_rng(9)
+    unk = _unknown_mask(L, bc)
+    u = rng.uniform(-1, 1, unk.size) * unk
+    v = rng.uniform(-1, 1, unk.size) * unk
+    Mu = O.precondition(L, u, coef=coef, bc=bc, coarse_cg=coarse_cg)
+    Mv = O.precondition(L, v, coef=coef, bc=bc, coarse_cg=coarse_cg)
+    a, b = np.dot(Mu, v), np.dot(u, Mv)
+    assert abs(a - b) <= 1e-11 * np.sum(np.abs(Mu * v))
+    assert np.dot(Mu, u) > 0 and np.dot(Mv, v) > 0                 # and positive definite
+
+
+@pytest.mark.parametrize("L,prec", [(5, 0), (6, 0), (5, 1)])
+def test_pcg_follows_scipy_cg(L, prec):
+    # the same iteration run by scipy's conjugate gradient with the oracle's operator and
+    # preconditioner as linear operators
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    coef = I.lognormal_coef(L, 30 + L)
+    b = I.rhs_uniform(L, 31)
+    A = O.assemble(L, coef)
+    N = b.size
+    Aop = spla.LinearOperator((N, N), matvec=lambda v: O.spmv(L, A, v), dtype=np.float64)
+    Mop = spla.LinearOperator((N, N), matvec=lambda v: O.precondition(L, v, coef=coef, prec=prec),
+                              dtype=np.float64)
+    k = 5
+    xs, info = spla.cg(Aop, b, rtol=0.0, atol=0.0, maxiter=k, M=Mop)
+    xo, st = O.pcg_solve(L, b, coef=coef, prec=prec, tol=0.0, max_iters=k)
+    assert info == k and st["outer_iters"] == k and st["cycles"] == k
+    assert np.linalg.norm(xo - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_pcg_with_exact_preconditioner_takes_one_step():
+    # coarse_L = L: the "cycle" is the exact solve, M = A^-1, so p_0 = A^-1 b and alpha = 1
+    L = 3
+    coef = I.lognormal_coef(L, 4)
+    b = I.rhs_uniform(L, 5)
+    x, st = O.pcg_solve(L, b, coef=coef, coarse_L=L, tol=1e-12)
+    assert st["outer_iters"] == 1 and st["relres"] <= 1e-14
+
+
+def test_pcg_accelerates_multigrid():
+    L = 7
+    coef = I.lognormal_coef(L, 12)
+    b = I.rhs_uniform(L, 13)
+    _, sm = O.mg_solve(L, b, coef=coef)
+    x64, s64, h = O.pcg_solve(L, b, coef=coef, history=True)
+    assert s64["converged"] and s64["relres"] <= 1.0001e-8
+    assert s64["outer_iters"] < sm["cycles"]
+    assert np.all(np.diff(h) < 0)                                  # residual falls every step
+    for prec in (1, 2):
+        x, s = O.pcg_solve(L, b, coef=coef, prec=prec)
+        assert s["converged"] and s["relres"] <= 1.0001e-8
+        assert abs(s["outer_iters"] - s64["outer_iters"]) <= 1
+        assert np.linalg.norm(x - x64) <= 1e-7 * np.linalg.norm(x64)
+
+
+def test_pcg_mixed_boundaries_manufactured_solution():
+    L = 6
+    b = O.load_sincos(L)
+    xm, _ = O.mg_solve(L, b, bc=LR, tol=1e-11)
+    xp, sp = O.pcg_solve(L, b, bc=LR, tol=1e-11)
+    assert sp["converged"]
+    assert abs(O.l2_error_sincos(L, xp) / O.l2_error_sincos(L, xm) - 1) < 1e-6
