@@ -6,8 +6,10 @@
  * on a regular grid of refinement level L, i.e. n = 2^L + 1 nodes per side and N = n^2 unknowns
  * numbered in tensor-product order, node i = iy*n + ix with ix fastest (Sec. 2.1).  The matrix is
  * assembled fully into 9 bands at fixed positions (Sec. 2.1, Sec. 4.1) and solved by a geometric
- * multigrid V cycle with damped Jacobi pre/post smoothing and an exact coarse solve, optionally as
- * the single-precision preconditioner of an FP64 defect-correction loop (Sec. 6.2).  Everything
+ * multigrid V cycle with damped Jacobi pre/post smoothing and an exact or CG coarse solve,
+ * optionally as the single-precision preconditioner of an FP64 defect-correction loop (Sec. 6.2),
+ * or as the preconditioner of FP64 conjugate gradients (a solver plugged into another, Sec. 4.1).
+ * Everything
  * runs on one GB300 GPU (sm_103a); data crosses the host-device boundary only at these calls.
  *
  * Conventions shared by every call:
@@ -56,6 +58,21 @@ typedef enum {
  * FP16 with one FP32 scale per band and level (FP32 arithmetic and vectors). */
 typedef enum { HN_PREC_FP64 = 0, HN_PREC_FP32_DC = 1, HN_PREC_FP16BAND_DC = 2 } hn_precision;
 
+/* Outer solver.  MG: V cycles to the tolerance (FP64), or the defect correction of the DC
+ * precisions.  PCG: conjugate gradients in FP64 (x, residual, search direction, inner products
+ * and convergence test in FP64 on the GPU), each step preconditioned by one V cycle from zero on
+ * the current residual (Sec. 4.1: a solver plugged into another as its preconditioner), the cycle
+ * in the hierarchy's precision (FP64, FP32, or FP32 with FP16 band storage; the residual is scaled
+ * by 1 / ||previous residual|| before the cast).  PCG needs pre == post (a symmetric
+ * preconditioner).  Convergence: recursively updated ||r|| / ||b|| <= tol. */
+typedef enum { HN_SOLVER_MG = 0, HN_SOLVER_PCG = 1 } hn_solver;
+
+/* Coarsest-level solver (Sec. 6.2 uses unpreconditioned CG).  EXACT: precomputed FP64 inverse of
+ * the coarse operator on its unknowns.  CG: unpreconditioned conjugate gradients in FP64 from
+ * x = 0 on the coarse unknowns, stopped at ||r|| <= 1e-13 ||b|| or after 2m + 10 steps for m
+ * unknowns. */
+typedef enum { HN_COARSE_EXACT = 0, HN_COARSE_CG = 1 } hn_coarse_solver;
+
 typedef struct hn_band hn_band;      /* an assembled fine-level operator (device resident) */
 typedef struct hn_mg hn_mg;          /* a multigrid hierarchy built from an hn_band (device) */
 typedef struct hn_server hn_server;  /* continuous-batching solve server */
@@ -98,11 +115,11 @@ long long hn_band_nodes(const hn_band* A);
 void hn_band_destroy(hn_band* A);
 
 typedef struct {
-  int coarse_L;      /* coarsest level, solved exactly (2; the paper uses CG there, Sec. 6.2) */
+  int coarse_L;      /* coarsest level (2), solved by coarse_solver */
   int pre, post;     /* damped Jacobi steps before / after the coarse correction (2, 2).  pre >= 1,
                         pre + post even */
   int max_cycles;    /* cap on V cycles (FP64) or inner cycles in total (DC) (100) */
-  int max_outer;     /* cap on defect-correction updates (50) */
+  int max_outer;     /* cap on defect-correction updates, or on PCG steps (50) */
   int inner_max;     /* cap on inner V cycles per defect-correction step (10) */
   double omega;      /* Jacobi damping (0.7) */
   double tol;        /* stop when ||b - A x||_2 / ||b||_2 <= tol, FP64 operator (1e-8) */
@@ -111,11 +128,13 @@ typedef struct {
   void* stream;      /* cudaStream_t the solves run on; NULL = the library's own stream */
   unsigned dirichlet_sides;  /* boundary of the operators hn_mg_submit assembles
                                 (HN_DIRICHLET_ALL); hn_mg_setup takes it from its operator */
+  hn_solver solver;  /* HN_SOLVER_MG */
+  hn_coarse_solver coarse_solver;  /* HN_COARSE_EXACT */
 } hn_mg_opts;
 
 typedef struct {
-  int cycles;        /* V cycles run (inner cycles in DC modes) */
-  int outer_iters;   /* defect-correction updates applied (0 in FP64 mode) */
+  int cycles;        /* V cycles run (inner cycles in DC modes; preconditioner cycles in PCG) */
+  int outer_iters;   /* defect-correction updates applied (0 in FP64 MG mode); PCG steps */
   int inner_cycles;  /* inner V cycles (0 in FP64 mode) */
   int status;        /* hn_status of this solve */
   double relres;     /* final ||b - A x|| / ||b|| with the FP64 operator, FP64 arithmetic */
@@ -127,8 +146,9 @@ void hn_mg_opts_default(hn_mg_opts* opts);
 
 /* Build the multigrid hierarchy of A on the device: coarse operators by re-discretisation with the
  * coarse cell coefficient equal to the mean of its 4 child cells, inner-precision copies of the
- * bands (FP32 cast, or FP16 codes with per-band scales), the exact coarse-level solver, and all
- * work vectors.  A may be destroyed afterwards (its data are copied).  Errors: HN_ERR_ARG (bad
+ * bands (FP32 cast, or FP16 codes with per-band scales), the coarse-level solver (the inverse, or
+ * the dense coarse matrix for CG), and all work vectors (PCG: also FP64 residual, search
+ * direction and its image).  A may be destroyed afterwards (its data are copied).  Errors: HN_ERR_ARG (bad
  * options, A NULL, coarse_L > level of A), HN_ERR_OOM, HN_ERR_CUDA. */
 hn_status hn_mg_setup(const hn_band* A, const hn_mg_opts* opts, hn_mg** out);
 
@@ -142,7 +162,7 @@ hn_status hn_mg_solve(hn_mg* mg, const double* b, double* x, int x_is_guess, int
 /* Solve count independent systems together: one launch per V-cycle phase covers every problem
  * (persistent kernels over a device work list), the per-iteration launch sequence is a CUDA
  * graph, and each problem stops on its own.  All handles must share precision, pre, post, omega,
- * coarse_L and may differ in level and coefficients.  b[j], x[j] as in hn_mg_solve (x zero guess).
+ * coarse_L, solver and coarse solver, and may differ in level, coefficients and boundary.  b[j], x[j] as in hn_mg_solve (x zero guess).
  * stats: count entries or NULL.  Each problem's result is bit-identical to solving it alone.
  * Returns the first non-OK per-problem status, HN_OK if all converged. */
 hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b,
@@ -164,7 +184,7 @@ void hn_mg_destroy(hn_mg* mg);
  *   HN_OP_JACOBI_ZERO out = omega D^-1 in2                         (the step from x = 0)
  *   HN_OP_RESTRICT    out (level l-1) = R in1 (level l), R = P^T full weighting
  *   HN_OP_PROLONG_ADD out (level l) = in2 (level l) + P in1 (level l-1), bilinear
- *   HN_OP_COARSE      out = A_c^-1 in2 (level = coarse_L)
+ *   HN_OP_COARSE      out = A_c^-1 in2 (level = coarse_L; by the hierarchy's coarse solver)
  * Errors: HN_ERR_ARG, HN_ERR_STATE (op not available for that precision/level), HN_ERR_CUDA. */
 typedef enum {
   HN_OP_SPMV = 0, HN_OP_DEFECT = 1, HN_OP_JACOBI = 2, HN_OP_JACOBI_ZERO = 3,
@@ -198,8 +218,9 @@ hn_status hn_mg_get_inner_bands(const hn_mg* mg, int level, void* bands_out, flo
  * queue; a request is admitted once a slot (max_active) and budget room for its hierarchy are
  * free.  Admitted requests are solved together: every scheduler iteration runs one V-cycle phase
  * sequence over all active requests (continuous batching); finished requests leave, free their
- * memory and let queued requests in.  All requests of a server share precision, pre, post, omega
- * and coarse_L (taken from the first submit). */
+ * memory and let queued requests in.  All requests of a server share precision, pre, post, omega,
+ * coarse_L, solver and coarse solver (taken from the first submit; HN_ERR_ARG for a request that
+ * differs). */
 hn_status hn_server_create(size_t budget_bytes, int max_active, hn_server** out);
 
 /* Queue a solve of level L with cell coefficients (NULL = 1) and right-hand side b (host, N

@@ -188,6 +188,8 @@ void hn_mg_opts_default(hn_mg_opts* o) {
   o->prec = HN_PREC_FP64;
   o->stream = nullptr;
   o->dirichlet_sides = HN_DIRICHLET_ALL;
+  o->solver = HN_SOLVER_MG;
+  o->coarse_solver = HN_COARSE_EXACT;
 }
 
 hn_status hn_mg_setup(const hn_band* A, const hn_mg_opts* opts, hn_mg** out) {
@@ -268,8 +270,9 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
     const Params& a = list[0]->prm;
     const Params& c = list[j]->prm;
     if (a.prec != c.prec || a.pre != c.pre || a.post != c.post || a.omega != c.omega ||
-        a.coarse != c.coarse)
-      return set_error(HN_ERR_ARG, "batch members must share precision, pre, post, omega, coarse_L");
+        a.coarse != c.coarse || a.solver != c.solver || a.coarse_cg != c.coarse_cg)
+      return set_error(HN_ERR_ARG, "batch members must share precision, pre, post, omega, coarse_L, "
+                                   "solver and coarse solver");
     for (int i = 0; i < j; ++i)
       if (list[i] == list[j]) return set_error(HN_ERR_ARG, "batch members must be distinct");
   }

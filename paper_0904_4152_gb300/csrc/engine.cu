@@ -60,7 +60,7 @@ struct LevelLayout {
 size_t vec_elems(int l) { return (size_t)(pitch_of(l) + 2 * halo_of(l)); }
 
 template <class F>
-void walk_layout(int L, int coarse, int prec, F&& take) {
+void walk_layout(int L, int coarse, int prec, int solver, F&& take) {
   // take(bytes) is called for every piece in construction order
   const size_t vs = prec == P64 ? 8 : 4;
   const size_t bs = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
@@ -73,7 +73,12 @@ void walk_layout(int L, int coarse, int prec, F&& take) {
     for (int k = 0; k < 9; ++k) take(vec_elems(L) * 8);
     take(vec_elems(L) * 8);
     take(vec_elems(L) * 8);
+  } else if (solver == SOLVER_PCG) {               // x, b apart from the cycle's vectors
+    take(vec_elems(L) * 8);
+    take(vec_elems(L) * 8);
   }
+  if (solver == SOLVER_PCG)
+    for (int v = 0; v < 3; ++v) take(vec_elems(L) * 8);   // r, p, q
   const long long m = n_of(coarse) * n_of(coarse);   // unknowns of the coarsest level, at most
   take((size_t)(m * m) * 8);
 }
@@ -115,9 +120,9 @@ struct TempDev {
 
 }  // namespace
 
-size_t hierarchy_bytes(int L, int coarse, int prec) {
+size_t hierarchy_bytes(int L, int coarse, int prec, int solver) {
   size_t off = 0;
-  walk_layout(L, coarse, prec, [&](size_t b) { off = ((off + 255) & ~size_t(255)) + b; });
+  walk_layout(L, coarse, prec, solver, [&](size_t b) { off = ((off + 255) & ~size_t(255)) + b; });
   return off + 256;
 }
 
@@ -133,6 +138,8 @@ Params params_from(const hn_mg_opts& o) {
   p.omega = o.omega;
   p.tol = o.tol;
   p.inner_tol = o.inner_tol;
+  p.solver = o.solver == HN_SOLVER_PCG ? SOLVER_PCG : SOLVER_MG;
+  p.coarse_cg = o.coarse_solver == HN_COARSE_CG ? 1 : 0;
   return p;
 }
 
@@ -147,6 +154,12 @@ hn_status validate_opts(const hn_mg_opts& o, int L) {
   if (!(o.omega > 0.0 && o.omega < 2.0)) return set_error(HN_ERR_ARG, "omega must be in (0, 2)");
   if (o.dirichlet_sides < 1u || o.dirichlet_sides > 15u)
     return set_error(HN_ERR_ARG, "dirichlet_sides must be a nonzero mask of the 4 sides");
+  if (o.solver != HN_SOLVER_MG && o.solver != HN_SOLVER_PCG)
+    return set_error(HN_ERR_ARG, "unknown solver %d", (int)o.solver);
+  if (o.coarse_solver != HN_COARSE_EXACT && o.coarse_solver != HN_COARSE_CG)
+    return set_error(HN_ERR_ARG, "unknown coarse solver %d", (int)o.coarse_solver);
+  if (o.solver == HN_SOLVER_PCG && o.pre != o.post)
+    return set_error(HN_ERR_ARG, "PCG needs a symmetric cycle (pre == post)");
   if (!(o.tol >= 0.0) || !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
     return set_error(HN_ERR_ARG, "need tol >= 0 and 0 < inner_tol < 1");
   if (o.max_cycles < 1 || o.max_outer < 1 || o.inner_max < 1 || o.max_cycles > 100000 ||
@@ -165,7 +178,7 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
   mg->prm = prm;
   const UnknownRect ur = unknown_rect((int)n_of(c), (int)A->bc);
   mg->m = ur.nx * ur.ny;
-  mg->bytes = hierarchy_bytes(L, c, prec);
+  mg->bytes = hierarchy_bytes(L, c, prec, prm.solver);
   HN_CUDA(cudaMalloc(&mg->mem, mg->bytes));
   HN_CUDA(cudaMemsetAsync(mg->mem, 0, mg->bytes, s));
 
@@ -207,8 +220,18 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
     P.b64 = b.take<double>(vec_elems(L)) + halo_of(L);
   } else {
     for (int k = 0; k < 9; ++k) P.band64[k] = static_cast<const double*>(P.lev[L].band[k]);
-    P.x64 = static_cast<double*>(P.lev[L].x[0]);
-    P.b64 = static_cast<double*>(P.lev[L].rhs);
+    if (prm.solver == SOLVER_PCG) {   // the cycle's top vectors are the preconditioner's
+      P.x64 = b.take<double>(vec_elems(L)) + halo_of(L);
+      P.b64 = b.take<double>(vec_elems(L)) + halo_of(L);
+    } else {
+      P.x64 = static_cast<double*>(P.lev[L].x[0]);
+      P.b64 = static_cast<double*>(P.lev[L].rhs);
+    }
+  }
+  if (prm.solver == SOLVER_PCG) {
+    P.r64 = b.take<double>(vec_elems(L)) + halo_of(L);
+    P.p64 = b.take<double>(vec_elems(L)) + halo_of(L);
+    P.q64 = b.take<double>(vec_elems(L)) + halo_of(L);
   }
   double* cinv = b.take<double>((size_t)mg->m * mg->m);
   P.cinv = cinv;
@@ -299,8 +322,11 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
           a[(size_t)(I * m + J)] = coarse64[(size_t)k * pc + iy * n + ix];
         }
       }
-    if (!invert(a, m)) return set_error(HN_ERR_STATE, "coarse matrix is singular");
-    HN_CUDA(cudaMemcpyAsync(cinv, a.data(), a.size() * 8, cudaMemcpyHostToDevice, s));
+    // CG keeps the matrix itself (the inverse still proves it nonsingular)
+    std::vector<double> inv(a);
+    if (!invert(inv, m)) return set_error(HN_ERR_STATE, "coarse matrix is singular");
+    const std::vector<double>& up = prm.coarse_cg ? a : inv;
+    HN_CUDA(cudaMemcpyAsync(cinv, up.data(), up.size() * 8, cudaMemcpyHostToDevice, s));
     HN_CUDA(cudaStreamSynchronize(s));
   }
   return HN_OK;
@@ -542,8 +568,12 @@ long long Engine::launch_bytes(int cls, int level) const {
     case KC_CHECK: per = 9 * bb + 2 * vb; break;
     case KC_RESTRICT: per = 1.25 * vb; break;                   // per fine node
     case KC_PROLONG: per = 2.25 * vb; break;                    // per fine node
-    case KC_OUTER_DEFECT: per = 72 + 8 + 8 + 4; break;
+    case KC_OUTER_DEFECT: per = 72 + 8 + 8 + vb; break;
     case KC_UPDATE: per = 4 + 8 + 8; break;
+    case KC_PCG_Q: per = 72 + 8 + 8; break;                    // bands, p; write q
+    case KC_PCG_X: per = 4 * 8 + 2 * 8 + vb; break;            // x, r, p, q; write x, r, rhs
+    case KC_PCG_DOT: per = 8 + vb; break;                       // r, z
+    case KC_PCG_P: per = vb + 8 + 8; break;                     // z, p; write p
     default: per = 0; break;
   }
   return (long long)(per * (double)nodes);
@@ -639,7 +669,8 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
     return HN_OK;
   };
   for (int l = Lmax_; l > T; --l) {
-    const bool top = topMaskAll_ || ((topMask_ >> l) & 1u);   // a finest level: lagged check
+    // a finest level: lagged check (the PCG preconditioner's cycle has none)
+    const bool top = prm_.solver != SOLVER_PCG && (topMaskAll_ || ((topMask_ >> l) & 1u));
     if (pre >= 2) {
       HN_LAUNCH(KC_JACOBI_FIRST, l, launch_pre12(E_, lists_[l], l, want, grid_[l], s));
       if (top) {
@@ -677,6 +708,11 @@ hn_status Engine::issue_init(cudaStream_t s, cudaGraphConditionalHandle h, int u
   HN_LAUNCH0(launch_boundary_check(E_, s));
   HN_LAUNCH0(launch_norm_b(E_, fine_, fineGrid_, s));
   HN_LAUNCH0(launch_control(E_, CTRL_INIT, s));
+  if (prm_.solver == SOLVER_PCG) {
+    // the initial residual r = b - A x and its check (then the first cycle preconditions it)
+    HN_LAUNCH0(launch_outer_defect(E_, fine_, fineGrid_, s));
+    HN_LAUNCH0(launch_control(E_, CTRL_OUTER, s));
+  }
   HN_LAUNCH0(launch_summary(E_, h, use_h, 0, s));
   return HN_OK;
 }
@@ -684,7 +720,19 @@ hn_status Engine::issue_init(cudaStream_t s, cudaGraphConditionalHandle h, int u
 hn_status Engine::issue_iteration(cudaStream_t s0, cudaGraphConditionalHandle h, int use_h) {
   cudaStream_t s = s0;
   const int start = counting_;
-  if (prm_.prec == P64) {
+  if (prm_.solver == SOLVER_PCG) {
+    // z = M r (one cycle from zero), rho' = (r, z), beta, p = z + beta p, then the CG step
+    // q = A p, alpha, x += alpha p, r -= alpha q, and its check
+    HN_TRY(issue_vcycle(s, PH_PRECOND));
+    HN_LAUNCH(KC_PCG_DOT, -1, launch_pcg_dot(E_, fine_, fineGrid_, s));
+    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_PCG_BETA, s));
+    HN_LAUNCH(KC_PCG_P, -1, launch_pcg_p(E_, fine_, fineGrid_, s));
+    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_POST, s));
+    HN_LAUNCH(KC_PCG_Q, -1, launch_pcg_q(E_, fine_, fineGrid_, s));
+    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_PCG_ALPHA, s));
+    HN_LAUNCH(KC_PCG_X, -1, launch_pcg_x(E_, fine_, fineGrid_, s));
+    HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_OUTER, s));
+  } else if (prm_.prec == P64) {
     HN_TRY(issue_vcycle(s, PH_CYCLE));
   } else {
     if (cond_on(1)) HN_TRY(open_if(s, 1));
@@ -801,7 +849,7 @@ hn_status Engine::capture_solve(bool cond) {
     // defect correction, where every outer step ends with one cycle that its check stops.  (The
     // outer defect and the update would each skip two small launches: not worth an IF node.)
     const int T = std::max(tune_.tail_level, prm_.coarse);
-    if (Lmax_ > T && prm_.prec != P64) cd.mask |= 1u;
+    if (Lmax_ > T && prm_.prec != P64 && prm_.solver != SOLVER_PCG) cd.mask |= 1u;
     const unsigned defaults[3] = {0u, 1u, 0u};
     for (int w = 0; w < 3; ++w)
       if ((cd.mask >> w) & 1u)
@@ -937,7 +985,7 @@ void Engine::set_profiling(bool on) {
 int Engine::kernel_times(hn_kernel_time* out, int max) const {
   static const char* names[KC_COUNT] = {"jacobi", "jacobi_first", "defect", "restrict", "prolong",
                                         "coarse", "check", "outer_defect", "update", "control",
-                                        "tail"};
+                                        "tail", "pcg_q", "pcg_x", "pcg_dot", "pcg_p"};
   int n = 0;
   for (int c = 0; c < KC_COUNT; ++c)
     for (int l = 0; l <= kMaxLevel; ++l) {
@@ -947,7 +995,8 @@ int Engine::kernel_times(hn_kernel_time* out, int max) const {
         hn_kernel_time& t = out[n];
         std::memset(&t, 0, sizeof t);
         std::snprintf(t.name, sizeof t.name, "%s", names[c]);
-        t.level = (c == KC_CHECK || c == KC_OUTER_DEFECT || c == KC_UPDATE || c == KC_CONTROL) ? -1 : l;
+        t.level = (c == KC_CHECK || c == KC_OUTER_DEFECT || c == KC_UPDATE || c == KC_CONTROL ||
+                   c >= KC_PCG_Q) ? -1 : l;
         t.launches = a.launches;
         t.total_ms = a.ms;
         t.bytes_per_launch = (double)a.bytes;

@@ -51,12 +51,13 @@ struct Bump {
 };
 
 // device bytes a hierarchy of fine level L needs (same arithmetic as its construction)
-size_t hierarchy_bytes(int L, int coarse, int prec);
+size_t hierarchy_bytes(int L, int coarse, int prec, int solver);
 
 // kernel classes timed in profiling mode
 enum KClass {
   KC_JACOBI = 0, KC_JACOBI_FIRST, KC_DEFECT, KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_CHECK,
-  KC_OUTER_DEFECT, KC_UPDATE, KC_CONTROL, KC_TAIL, KC_COUNT
+  KC_OUTER_DEFECT, KC_UPDATE, KC_CONTROL, KC_TAIL, KC_PCG_Q, KC_PCG_X, KC_PCG_DOT, KC_PCG_P,
+  KC_COUNT
 };
 
 // launch shape of the schedule: levels <= tail_level run fused in one cluster launch of

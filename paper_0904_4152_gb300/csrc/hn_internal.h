@@ -30,6 +30,12 @@ inline long long pitch_of(int L) { return round_up(N_of(L), kTile); }
 inline long long halo_of(int L) { return round_up(n_of(L) + 8, 32); }
 
 enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+enum Solver { SOLVER_MG = 0, SOLVER_PCG = 1 };
+
+// unpreconditioned CG on the coarsest level: stop at ||r|| <= kCoarseCgTol ||b|| or after
+// coarse_cg_steps(m) steps (m unknowns)
+constexpr double kCoarseCgTol = 1e-13;
+__host__ __device__ inline int coarse_cg_steps(int m) { return 2 * m + 10; }
 
 // ------------------------------------------------------------------- device descriptors
 // One level of one problem.  Vectors and bands point at element 0 of pitch elements; a zero halo
@@ -70,11 +76,15 @@ struct ProblemDev {
   int coarse;            // coarsest level
   int m;                 // interior unknowns of the coarsest level
   int pad0;
-  const double* cinv;    // m*m inverse of the coarsest interior block, row-major
-  // FP64 fine-level data of the outer loop (aliases of the top level in FP64 mode)
+  const double* cinv;    // m*m inverse of the coarsest block on its unknowns, row-major (for the
+                         // CG coarse solver: the block itself)
+  // FP64 fine-level data of the outer loop (x64, b64 alias the top level in FP64 MG mode)
   const double* band64[9];
   double* x64;           // solution
   double* b64;           // right-hand side
+  double* r64;           // PCG: residual, search direction and its image A p (with zero halos)
+  double* p64;
+  double* q64;
   LevelDev lev[kMaxLevel + 1];   // indexed by level l in [coarse, L]
 };
 
@@ -86,8 +96,11 @@ enum Phase {
   PH_UPDATE = 3,  // defect correction: inner solve finished, apply x += c / s
   PH_CYCLE = 4,   // FP64 multigrid: run a V cycle, then check
   PH_CHECK = 5,   // FP64 multigrid: check the initial guess before cycling
-  PH_INIT = 6     // starting: boundary check and ||b||
+  PH_INIT = 6,    // starting: boundary check and ||b||
+  PH_PRECOND = 7  // PCG: the preconditioner's V cycle on the scaled residual
 };
+// PCG uses PH_OUTER for its step (q = A p, alpha, x and r update, check; the initial residual
+// when no cycle ran yet) and PH_UPDATE for the new direction (beta, p = z + beta p).
 
 struct ProbState {
   int phase;             // Phase
@@ -101,6 +114,9 @@ struct ProbState {
   double s;              // scale applied to the defect before the cast to the inner precision
   double inner_ref;      // ||scaled defect|| (reference of the inner relative residual)
   double inner_res;      // last inner residual norm
+  double rho;            // PCG: (r, z) of the current direction
+  double alpha;          // PCG: step length of the current step
+  double beta;           // PCG: (r_new, z_new) / (r, z)
 };
 
 // solver parameters shared by every problem of an engine
@@ -119,7 +135,8 @@ struct CondDev {
 
 struct Params {
   int prec, pre, post, coarse;
-  int max_cycles, max_outer, inner_max, pad;
+  int max_cycles, max_outer, inner_max, solver;
+  int coarse_cg, pad;
   double omega, tol, inner_tol;
   CondDev cond;
 };
@@ -210,6 +227,13 @@ cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want,
                            int grid, cudaStream_t s);
 cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, cudaStream_t s);
 cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+// PCG vector steps on each problem's finest level (FP64): q = A p with partials (p, q); x += alpha
+// p, r -= alpha q with partials ||r||^2 and the scaled residual as the cycle's right-hand side;
+// partials (r, z); p = z / s + beta p
+cudaError_t launch_pcg_q(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+cudaError_t launch_pcg_x(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+cudaError_t launch_pcg_dot(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+cudaError_t launch_pcg_p(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
 cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
 cudaError_t launch_norm_b(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
 // kind: ControlKind; level: for CTRL_PRE, the finest level whose problems are checked
@@ -221,7 +245,9 @@ cudaError_t launch_boundary_check(const EngineDev& E, cudaStream_t s);
 
 enum ControlKind {
   CTRL_INIT = 0, CTRL_CHECK = 1, CTRL_OUTER = 2, CTRL_INNER = 3, CTRL_POST = 4, CTRL_CHECK0 = 5,
-  CTRL_PRE = 6   // lagged convergence test after the first smoothing step of a cycle
+  CTRL_PRE = 6,  // lagged convergence test after the first smoothing step of a cycle
+  CTRL_PCG_ALPHA = 7,  // PCG: alpha = rho / (p, q)
+  CTRL_PCG_BETA = 8    // PCG: rho' = (r, z), beta = rho' / rho
 };
 
 int sm_count();

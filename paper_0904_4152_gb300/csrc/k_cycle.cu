@@ -545,6 +545,56 @@ __device__ __forceinline__ void coarse_warp(const ProblemDev& P, int lane, doubl
   __syncwarp();
 }
 
+// (u, v) over m <= kMaxCoarseM entries by warp 0 (lane l adds entries l, l + 32, ... in order,
+// then the butterfly), broadcast to the block: the order does not depend on the block size.
+// Every thread of the block calls it.
+__device__ __forceinline__ double warp0_dot(const double* u, const double* v, int m, double* sh) {
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < m; i += 32) t = fma(u[i], v[i], t);
+    t = warp_sum(t);
+    if (threadIdx.x == 0) sh[31] = t;
+  }
+  __syncthreads();
+  const double r = sh[31];
+  __syncthreads();
+  return r;
+}
+
+// Unpreconditioned conjugate gradients on the coarsest level (Sec. 6.2 configures the coarse
+// solver so), in FP64 by the whole block: Am is the m x m matrix on the unknowns (row-major, any
+// memory), r holds the right-hand side on entry and the residual on exit, x receives the
+// approximate solution; p, q are scratch (m doubles each).  Textbook CG from x = 0 (Hestenes and
+// Stiefel): q = A p, alpha = (r, r) / (p, q), x += alpha p, r -= alpha q; stop once (r, r) <=
+// kCoarseCgTol^2 (b, b) or after coarse_cg_steps(m) steps; else p = r + ((r, r)_new / (r, r)) p.
+__device__ void coarse_cg(const double* Am, int m, double* x, double* r, double* p, double* q,
+                          double* sh) {
+  const int nt = blockDim.x;
+  for (int u = threadIdx.x; u < m; u += nt) { x[u] = 0.0; p[u] = r[u]; }
+  __syncthreads();
+  double rr = warp0_dot(r, r, m, sh);
+  const double stop = kCoarseCgTol * kCoarseCgTol * rr;
+  const int kmax = coarse_cg_steps(m);
+  for (int k = 0; k < kmax && rr > 0.0; ++k) {
+    for (int u = threadIdx.x; u < m; u += nt)
+      q[u] = coarse_dot(Am + (long long)u * m, m, [&](int v) { return p[v]; });
+    __syncthreads();
+    const double alpha = rr / warp0_dot(p, q, m, sh);
+    for (int u = threadIdx.x; u < m; u += nt) {
+      x[u] = fma(alpha, p[u], x[u]);
+      r[u] = fma(-alpha, q[u], r[u]);
+    }
+    __syncthreads();
+    const double rr1 = warp0_dot(r, r, m, sh);
+    if (!(rr1 > stop)) break;                   // also ends on a NaN
+    const double beta = rr1 / rr;
+    rr = rr1;
+    for (int u = threadIdx.x; u < m; u += nt) p[u] = fma(beta, p[u], r[u]);
+    __syncthreads();
+  }
+  __syncthreads();
+}
+
 // mbarrier and bulk-copy (TMA engine, 1D) helpers
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
@@ -817,6 +867,33 @@ __global__ void __launch_bounds__(256) k_coarse(EngineDev E, TileList tl, int wa
     const int p = it.x;
     if (E.S[p].phase != want) continue;
     coarse_warp<V, LD_NC>(E.P[p], lane, sol[wib]);
+  }
+}
+
+// the coarsest-level solve by CG, one block per problem slot; result into buffer 0
+template <class V>
+__global__ void __launch_bounds__(256) k_coarse_cg(EngineDev E, int want) {
+  pdl_start();
+  __shared__ double x[kMaxCoarseM], r[kMaxCoarseM], pv[kMaxCoarseM], qv[kMaxCoarseM];
+  __shared__ double sh[32];
+  const int p = blockIdx.x;
+  if (p >= E.nprob || E.S[p].phase != want) return;
+  const ProblemDev& P = E.P[p];
+  if (P.L < HN_MIN_LEVEL) return;
+  const LevelDev& d = P.lev[P.coarse];
+  const int n = d.n, m = P.m;
+  const UnknownRect ur = unknown_rect(n, d.bc);
+  const V* rhs = static_cast<const V*>(d.rhs);
+  for (int v = threadIdx.x; v < m; v += blockDim.x)
+    r[v] = double(rhs[(v / ur.nx + ur.y0) * n + (v % ur.nx + ur.x0)]);
+  __syncthreads();
+  coarse_cg(P.cinv, m, x, r, pv, qv, sh);
+  V* xo = static_cast<V*>(d.x[0]);
+  for (int q = threadIdx.x; q < d.pitch; q += blockDim.x) {
+    const int iy = q / n - ur.y0, ix = q - (q / n) * n - ur.x0;
+    V val = V(0);
+    if (q < n * n && ix >= 0 && iy >= 0 && ix < ur.nx && iy < ur.ny) val = V(x[iy * ur.nx + ix]);
+    xo[q] = val;
   }
 }
 
@@ -1394,10 +1471,16 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
   }
   long long off = 0;
   for (int l = c; l <= Ss; ++l) smem_level_setup<Pol>(gd[l], sd[l], smem, &off, l, rank == 0, &s_bar);
-  {   // the coarse inverse (m*m doubles) is staged in shared memory when it is small
+  double* cg_pq = nullptr;                      // CG coarse solver: p and q (m doubles each)
+  {   // the coarse inverse (CG: the coarse matrix; m*m doubles) is staged in shared memory when
+      // it is small
     const bool staged = (long long)m * m * 8 <= kCinvSmemMax;
     double* dst = reinterpret_cast<double*>(smem + off);
     if (staged) off += ((long long)m * m * 8 + 15) / 16 * 16;
+    if (E.prm.coarse_cg) {
+      cg_pq = reinterpret_cast<double*>(smem + off);
+      off += ((long long)2 * m * 8 + 15) / 16 * 16;
+    }
     if (rank == 0 && threadIdx.x == 0) {
       if (staged) {
         bulk_copy(dst, P.cinv, (unsigned)(m * m / 2) * 16u, &s_bar);
@@ -1512,9 +1595,13 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
       for (int v = threadIdx.x; v < m; v += blockDim.x)
         rd[v] = double(rhs[(v / ur.nx + ur.y0) * n + (v % ur.nx + ur.x0)]);
       __syncthreads();
-      for (int u = threadIdx.x; u < m; u += blockDim.x)
-        sol[u] = coarse_dot(cinv + u * m, m, [&](int v) { return rd[v]; });
-      __syncthreads();
+      if (E.prm.coarse_cg) {
+        coarse_cg(cinv, m, sol, rd, cg_pq, cg_pq + m, sh);
+      } else {
+        for (int u = threadIdx.x; u < m; u += blockDim.x)
+          sol[u] = coarse_dot(cinv + u * m, m, [&](int v) { return rd[v]; });
+        __syncthreads();
+      }
       V* x = static_cast<V*>(d.x[0]);
       for (int q = threadIdx.x; q < d.pitch; q += blockDim.x) {
         const int iy = q / n - ur.y0, ix = q - (q / n) * n - ur.x0;
@@ -1551,7 +1638,9 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
 }
 
 // FP64 outer defect of the defect correction: d = b - A x (FP64 bands, FP64 x), written to the
-// inner top-level right-hand side as float(d * s); partial[g] = sum d^2.  x = 0 gives d = b.
+// inner top-level right-hand side as V(d * s); partial[g] = sum d^2.  x = 0 gives d = b.  PCG:
+// the initial residual (before the first cycle), also kept in FP64 (r64).
+template <class V>
 __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) {
   pdl_start();
   const int lane = threadIdx.x & 31;
@@ -1563,6 +1652,8 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
     const int p = it.x;
     const ProbState& st = E.S[p];
     if (st.phase != PH_OUTER) continue;
+    const bool pcg = E.prm.solver == SOLVER_PCG;
+    if (pcg && st.cycles > 0) continue;
     const ProblemDev& P = E.P[p];
     const LevelDev& top = P.lev[P.L];
     const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
@@ -1580,16 +1671,134 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
       for (int j = 0; j < 4; ++j) r[j] = b[j] - acc[j];
     }
     const double s = st.s;
-    float out[4];
+    V out[4];
     double q = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      out[j] = __double2float_rn(r[j] * s);
+      out[j] = V(r[j] * s);
       q += r[j] * r[j];
     }
-    st4(static_cast<float*>(top.rhs) + i0, out);
+    st4(static_cast<V*>(top.rhs) + i0, out);
+    if (pcg) st4(P.r64 + i0, r);
     q = warp_sum(q);
     if (lane == 0) E.partial[g] = q;
+  }
+}
+
+// ----------------------------------------------------------------- PCG vector steps (FP64)
+// Conjugate gradients on each problem's finest level with the V cycle as preconditioner (a
+// solver plugged into another, Sec. 4.1): every step below is one pass over the fine work list.
+
+// q = A p (FP64 bands, p with zero halos), partial[g] = sum p q, for problems in their CG step
+__global__ void __launch_bounds__(256) k_pcg_q(EngineDev E, TileList tl) {
+  pdl_start();
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int count = *tl.count;
+  for (int g = gw; g < count; g += nw) {
+    const int2 it = tl.items[g];
+    const ProbState& st = E.S[it.x];
+    if (st.phase != PH_OUTER || st.cycles == 0) continue;
+    const ProblemDev& P = E.P[it.x];
+    const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
+    double w[3][8], acc[4], dg[4];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) load_row<double, LD_NC>(P.p64, i0 + dy * (1LL << P.L), lane, w[dy + 1]);
+    stencil_windows<F64, LD_NC>(reinterpret_cast<const void* const*>(P.band64), nullptr, w, i0, acc, dg);
+    st4(P.q64 + i0, acc);
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t = fma(w[1][j + 2], acc[j], t);
+    t = warp_sum(t);
+    if (lane == 0) E.partial[g] = t;
+  }
+}
+
+// x += alpha p, r -= alpha q; partial[g] = sum r^2; the cycle's right-hand side V(s r)
+template <class V>
+__global__ void __launch_bounds__(256) k_pcg_x(EngineDev E, TileList tl) {
+  pdl_start();
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int count = *tl.count;
+  for (int g = gw; g < count; g += nw) {
+    const int2 it = tl.items[g];
+    const ProbState& st = E.S[it.x];
+    if (st.phase != PH_OUTER || st.cycles == 0) continue;
+    const ProblemDev& P = E.P[it.x];
+    const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
+    double x[4], r[4], pv[4], qv[4];
+    ld4c(P.x64 + i0, x);
+    ld4c(P.r64 + i0, r);
+    ld4<LD_NC>(P.p64 + i0, pv);
+    ld4<LD_NC>(P.q64 + i0, qv);
+    const double alpha = st.alpha, sc = st.s;
+    V out[4];
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x[j] = fma(alpha, pv[j], x[j]);
+      r[j] = fma(-alpha, qv[j], r[j]);
+      t = fma(r[j], r[j], t);
+      out[j] = V(r[j] * sc);
+    }
+    st4(P.x64 + i0, x);
+    st4(P.r64 + i0, r);
+    st4(static_cast<V*>(P.lev[P.L].rhs) + i0, out);
+    t = warp_sum(t);
+    if (lane == 0) E.partial[g] = t;
+  }
+}
+
+// partial[g] = sum r c, c = the cycle's result (top-level buffer 0, z = c / s)
+template <class V>
+__global__ void __launch_bounds__(256) k_pcg_dot(EngineDev E, TileList tl) {
+  pdl_start();
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int count = *tl.count;
+  for (int g = gw; g < count; g += nw) {
+    const int2 it = tl.items[g];
+    if (E.S[it.x].phase != PH_PRECOND) continue;
+    const ProblemDev& P = E.P[it.x];
+    const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
+    double r[4];
+    V c[4];
+    ld4<LD_NC>(P.r64 + i0, r);
+    ld4<LD_NC>(static_cast<const V*>(P.lev[P.L].x[0]) + i0, c);
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t = fma(r[j], double(c[j]), t);
+    t = warp_sum(t);
+    if (lane == 0) E.partial[g] = t;
+  }
+}
+
+// p = c / s + beta p (the new search direction), for problems in PH_UPDATE
+template <class V>
+__global__ void __launch_bounds__(256) k_pcg_p(EngineDev E, TileList tl) {
+  pdl_start();
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int count = *tl.count;
+  for (int g = gw; g < count; g += nw) {
+    const int2 it = tl.items[g];
+    const ProbState& st = E.S[it.x];
+    if (st.phase != PH_UPDATE) continue;
+    const ProblemDev& P = E.P[it.x];
+    const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
+    V c[4];
+    double pv[4];
+    ld4<LD_NC>(static_cast<const V*>(P.lev[P.L].x[0]) + i0, c);
+    ld4c(P.p64 + i0, pv);
+    const double beta = st.beta, inv_s = 1.0 / st.s;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) pv[j] = fma(beta, pv[j], double(c[j]) * inv_s);
+    st4(P.p64 + i0, pv);
   }
 }
 
@@ -1686,7 +1895,9 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
                     (kind == CTRL_CHECK && ph == PH_CYCLE) ||
                     (kind == CTRL_OUTER && ph == PH_OUTER) ||
                     (kind == CTRL_INNER && ph == PH_INNER) ||
-                    (kind == CTRL_POST && ph == PH_UPDATE);
+                    (kind == CTRL_POST && ph == PH_UPDATE) ||
+                    (kind == CTRL_PCG_ALPHA && ph == PH_OUTER && st.cycles > 0) ||
+                    (kind == CTRL_PCG_BETA && ph == PH_PRECOND);
   if (!mine) return;
   double sum = 0.0;
   if (kind != CTRL_POST) {
@@ -1707,7 +1918,7 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
       st.bnorm = nrm;
       st.s = 1.0 / nrm;
       st.relres = 1.0;
-      if (prm.prec == P64) {
+      if (prm.prec == P64 && prm.solver != SOLVER_PCG) {
         // a zero initial guess starts its first cycle unchecked (relres 1); a given guess is
         // checked by the first smoothing step of its first cycle
         st.phase = PH_CYCLE;
@@ -1727,6 +1938,21 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
       else st.phase = PH_CYCLE;
       break;
     case CTRL_OUTER:
+      if (prm.solver == SOLVER_PCG) {
+        // after the initial residual or a CG step: check, then precondition the new residual
+        if (st.cycles > 0) st.outer_iters += 1;
+        st.dnorm = nrm;
+        st.relres = nrm / st.bnorm;
+        if (!isfinite(nrm)) { st.status = HN_ERR_NONFINITE; st.phase = PH_DONE; }
+        else if (st.relres <= prm.tol) { st.status = HN_OK; st.phase = PH_DONE; }
+        else if (st.outer_iters >= prm.max_outer || st.cycles >= prm.max_cycles) {
+          st.status = HN_ERR_NOT_CONVERGED; st.phase = PH_DONE;
+        } else {
+          st.phase = PH_PRECOND; st.zero_top = 1; st.cycles += 1;
+          if (prm.prec != P64) st.inner_cycles += 1;
+        }
+        break;
+      }
       st.dnorm = nrm;
       st.relres = nrm / st.bnorm;
       if (!isfinite(nrm)) { st.status = HN_ERR_NONFINITE; st.phase = PH_DONE; }
@@ -1747,7 +1973,28 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
                st.inner_cycles >= prm.max_cycles)
         st.phase = PH_UPDATE;
       break;
+    case CTRL_PCG_ALPHA:
+      // sum = (p, q); a breakdown (not positive: the preconditioned operator is not definite in
+      // this arithmetic) stops the solve
+      if (!isfinite(sum) || !(sum > 0.0)) { st.status = HN_ERR_NONFINITE; st.phase = PH_DONE; }
+      else st.alpha = st.rho / sum;
+      break;
+    case CTRL_PCG_BETA: {
+      // sum = (r, c) with z = c / s: rho' = (r, z); the first direction is z itself
+      const double rho = sum / st.s;
+      if (!isfinite(rho) || !(rho > 0.0)) { st.status = HN_ERR_NONFINITE; st.phase = PH_DONE; break; }
+      st.beta = st.cycles > 1 ? rho / st.rho : 0.0;
+      st.rho = rho;
+      st.phase = PH_UPDATE;
+      break;
+    }
     case CTRL_POST: {
+      if (prm.solver == SOLVER_PCG) {
+        // the next cycle's right-hand side is scaled by 1 / ||r|| of this step
+        if (st.dnorm > 0.0 && isfinite(st.dnorm)) st.s = 1.0 / st.dnorm;
+        st.phase = PH_OUTER;
+        break;
+      }
       st.outer_iters += 1;
       st.x_zero = 0;
       // scale for the next defect: the inner solve reduced the defect by about inner_res/inner_ref
@@ -1923,13 +2170,13 @@ constexpr long long kTailSmemMax = 212 * 1024;      // with the cluster levels (
 
 // shared memory reserved for a staged coarse inverse: the unknowns of the coarsest level number at
 // most n^2 (free Neumann sides), and an inverse is staged only if it takes <= kCinvSmemMax bytes
-long long tail_cinv_bytes(int coarse) {
+long long tail_cinv_bytes(int coarse, int cg) {
   const long long m = ((1LL << coarse) + 1) * ((1LL << coarse) + 1);
-  return (std::min(m * m * 8, kCinvSmemMax) + 15) / 16 * 16;
+  return (std::min(m * m * 8, kCinvSmemMax) + 15) / 16 * 16 + (cg ? (2 * m * 8 + 15) / 16 * 16 : 0);
 }
 
-int tail_smem_level(int prec, int coarse, int T) {
-  long long bytes = tail_cinv_bytes(coarse);
+int tail_smem_level(int prec, int coarse, int cg, int T) {
+  long long bytes = tail_cinv_bytes(coarse, cg);
   int S = coarse;
   for (int l = coarse; l <= T; ++l) {
     bytes += smem_level_bytes(l, prec);
@@ -1939,17 +2186,17 @@ int tail_smem_level(int prec, int coarse, int T) {
   return S;
 }
 
-long long tail_smem_bytes(int prec, int coarse, int S) {
+long long tail_smem_bytes(int prec, int coarse, int cg, int S) {
   long long bytes = 0;
   for (int l = coarse; l <= S; ++l) bytes += smem_level_bytes(l, prec);
-  return bytes + tail_cinv_bytes(coarse);
+  return bytes + tail_cinv_bytes(coarse, cg);
 }
 
 // shared memory of the cluster levels (S, T] in distributed shared memory, or -1 if they do not
 // fit (or the partition would leave a block without rows; C must be a power of two)
-long long tail_dsm_bytes(int prec, int coarse, int S, int T, int C) {
+long long tail_dsm_bytes(int prec, int coarse, int cg, int S, int T, int C) {
   if (T <= S || (1 << (S + 1)) < C || (C & (C - 1)) != 0) return -1;
-  long long bytes = tail_smem_bytes(prec, coarse, S);
+  long long bytes = tail_smem_bytes(prec, coarse, cg, S);
   for (int l = S + 1; l <= T; ++l) bytes += dsm_level_bytes(l, C, S, prec);
   return bytes <= kTailSmemMax ? bytes : -1;
 }
@@ -1985,9 +2232,10 @@ cudaError_t prepare_kernels() {
 
 template <class Pol>
 cudaError_t launch_tail_t(const EngineDev& E, int T, int want, int cluster, cudaStream_t s) {
-  const int S = tail_smem_level(Pol::prec, E.prm.coarse, T);
-  const long long dsm = E.dsm ? tail_dsm_bytes(Pol::prec, E.prm.coarse, S, T, cluster) : -1;
-  const size_t smem = (size_t)(dsm > 0 ? dsm : tail_smem_bytes(Pol::prec, E.prm.coarse, S));
+  const int cg = E.prm.coarse_cg;
+  const int S = tail_smem_level(Pol::prec, E.prm.coarse, cg, T);
+  const long long dsm = E.dsm ? tail_dsm_bytes(Pol::prec, E.prm.coarse, cg, S, T, cluster) : -1;
+  const size_t smem = (size_t)(dsm > 0 ? dsm : tail_smem_bytes(Pol::prec, E.prm.coarse, cg, S));
   return launch_kt(k_tail<Pol>, E.nprob * cluster, kTailThreads, smem, s, E.pdl, cluster, E, T, S, want,
                    dsm > 0 ? 1 : 0);
 }
@@ -2024,13 +2272,34 @@ cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want,
 }
 
 cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, cudaStream_t s) {
+  if (E.prm.coarse_cg) {
+    if (E.prm.prec == P64) return launch_k(k_coarse_cg<double>, E.nprob, 0, s, E.pdl, 0, E, want);
+    return launch_k(k_coarse_cg<float>, E.nprob, 0, s, E.pdl, 0, E, want);
+  }
   grid = grid_or_one(grid);
   if (E.prm.prec == P64) return launch_k(k_coarse<double>, grid, 0, s, E.pdl, 0, E, tl, want);
   return launch_k(k_coarse<float>, grid, 0, s, E.pdl, 0, E, tl, want);
 }
 
 cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  return launch_k(k_outer_defect, grid, 0, s, E.pdl, 0, E, fine);
+  if (E.prm.prec == P64) return launch_k(k_outer_defect<double>, grid, 0, s, E.pdl, 0, E, fine);
+  return launch_k(k_outer_defect<float>, grid, 0, s, E.pdl, 0, E, fine);
+}
+
+cudaError_t launch_pcg_q(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
+  return launch_k(k_pcg_q, grid, 0, s, E.pdl, 0, E, fine);
+}
+cudaError_t launch_pcg_x(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
+  if (E.prm.prec == P64) return launch_k(k_pcg_x<double>, grid, 0, s, E.pdl, 0, E, fine);
+  return launch_k(k_pcg_x<float>, grid, 0, s, E.pdl, 0, E, fine);
+}
+cudaError_t launch_pcg_dot(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
+  if (E.prm.prec == P64) return launch_k(k_pcg_dot<double>, grid, 0, s, E.pdl, 0, E, fine);
+  return launch_k(k_pcg_dot<float>, grid, 0, s, E.pdl, 0, E, fine);
+}
+cudaError_t launch_pcg_p(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
+  if (E.prm.prec == P64) return launch_k(k_pcg_p<double>, grid, 0, s, E.pdl, 0, E, fine);
+  return launch_k(k_pcg_p<float>, grid, 0, s, E.pdl, 0, E, fine);
 }
 
 cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {

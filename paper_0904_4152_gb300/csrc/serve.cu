@@ -60,7 +60,7 @@ namespace {
 size_t request_bytes(int L, const hn_mg_opts& o) {
   const Params p = params_from(o);
   // resident hierarchy + the transient fine operator built during admission
-  return hierarchy_bytes(L, o.coarse_L, p.prec) + (size_t)9 * pitch_of(L) * 8 +
+  return hierarchy_bytes(L, o.coarse_L, p.prec, p.solver) + (size_t)9 * pitch_of(L) * 8 +
          (size_t)(1LL << L) * (1LL << L) * 8 + 4096;
 }
 
@@ -285,7 +285,8 @@ hn_status hn_mg_submit(hn_server* srv, int L, const double* cell_coef, const dou
     const hn_mg_opts& a = srv->opts;
     if (a.prec != o.prec || a.pre != o.pre || a.post != o.post || a.omega != o.omega ||
         a.coarse_L != o.coarse_L || a.tol != o.tol || a.inner_tol != o.inner_tol ||
-        a.max_cycles != o.max_cycles || a.max_outer != o.max_outer || a.inner_max != o.inner_max)
+        a.max_cycles != o.max_cycles || a.max_outer != o.max_outer || a.inner_max != o.inner_max ||
+        a.solver != o.solver || a.coarse_solver != o.coarse_solver)
       return set_error(HN_ERR_ARG, "options differ from the server's (first submit)");
   }
   if (r->bytes > srv->budget) return set_error(HN_ERR_BUDGET, "request needs %zu bytes, budget %zu", r->bytes, srv->budget);

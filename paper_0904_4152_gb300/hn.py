@@ -22,6 +22,8 @@ HN_MIN_LEVEL, HN_MAX_LEVEL = 2, 14
 # Dirichlet sides (the others are free Neumann): bottom y = 0, right x = 1, top y = 1, left x = 0
 HN_DIRICHLET_BOTTOM, HN_DIRICHLET_RIGHT, HN_DIRICHLET_TOP, HN_DIRICHLET_LEFT = 1, 2, 4, 8
 HN_DIRICHLET_ALL = 15
+HN_SOLVER_MG, HN_SOLVER_PCG = 0, 1
+HN_COARSE_EXACT, HN_COARSE_CG = 0, 1
 
 STATUS_NAMES = {0: "HN_OK", 1: "HN_ERR_ARG", 2: "HN_ERR_OOM", 3: "HN_ERR_BUDGET", 4: "HN_ERR_CUDA",
                 5: "HN_ERR_NOT_CONVERGED", 6: "HN_ERR_NONFINITE", 7: "HN_PENDING",
@@ -50,7 +52,8 @@ class Opts(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("max_outer", ctypes.c_int),
                 ("inner_max", ctypes.c_int), ("omega", ctypes.c_double), ("tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("prec", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("dirichlet_sides", ctypes.c_uint)]
+                ("dirichlet_sides", ctypes.c_uint), ("solver", ctypes.c_int),
+                ("coarse_solver", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

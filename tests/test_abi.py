@@ -69,6 +69,7 @@ def test_host_side_argument_checks(lib):
     assert lib.hn_band_create(3, ctypes.c_void_p(bad.ctypes.data), ctypes.byref(h)) == hn.HN_ERR_ARG
     o = hn.hn_mg_opts_default()
     assert (o.coarse_L, o.pre, o.post, o.omega, o.tol, o.inner_tol) == (2, 2, 2, 0.7, 1e-8, 1e-2)
+    assert (o.dirichlet_sides, o.solver, o.coarse_solver) == (15, hn.HN_SOLVER_MG, hn.HN_COARSE_EXACT)
     assert lib.hn_mg_setup(None, ctypes.byref(o), ctypes.byref(h)) == hn.HN_ERR_ARG
     assert lib.hn_server_create(0, 4, ctypes.byref(h)) == hn.HN_ERR_ARG
     assert lib.hn_mg_poll(None, 1, 0, None, None) == hn.HN_ERR_ARG
