@@ -46,14 +46,19 @@ def parse():
     ap.add_argument("--host-loop", action="store_true",
                     help="run solves as one graph launch per iteration (ncu cannot profile kernels "
                          "inside the device-side loop)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve", "kernels", "blas1"],
+    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve", "kernels", "blas1", "swe", "solvers"],
                     help="solve: the L=10 benchmark (default); batch: 256 uneven problems in one "
                          "batched solve; serve: Poisson-arrival requests through the solve server; "
-                         "kernels: band-SpMV / defect / Jacobi alone at L=12 in FP64, FP32, FP16-band")
+                         "kernels: band-SpMV / defect / Jacobi alone at L=12 in FP64, FP32, FP16-band; "
+                         "blas1: axpy / dot rate vs length; swe: fused shallow-water prediction step "
+                         "vs the same step composed from library calls; solvers: solve time of "
+                         "multigrid / defect correction vs PCG, exact vs CG coarse solve")
     ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load / capacity")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: device memory budget")
     ap.add_argument("--slots", type=int, default=64, help="serve: concurrently active requests")
+    ap.add_argument("--swe-grid", type=int, default=0, help="swe: one W x W grid only (default: 256, 1024, 4096)")
+    ap.add_argument("--swe-type", default="all", choices=["all", "f32", "f64"], help="swe: element types")
     return ap.parse_args()
 
 
@@ -276,6 +281,117 @@ def run_blas1(args, rank, local):
                           "peak_kind": kind, "rows": rows}), flush=True)
 
 
+def run_swe(args, rank, local):
+    """Shallow-water prediction step u + M1 v + M2 w + M3 u + M4 u + s with four-band matrices
+    (Sec. 2.2): the fused kernel against the same step composed from library calls (four band
+    products into temporaries, then axpy), on W x W grids, FP32 and FP64."""
+    import torch
+    import __graft_entry__ as g
+    from paper_0904_4152_gb300 import hn
+    torch.cuda.set_device(local)
+    g.build()
+    peak, kind = measured_peak_gbs()
+    stream = torch.cuda.current_stream()
+    rows = []
+    for dtype, name in ((torch.float32, "f32"), (torch.float64, "f64")):
+        if args.swe_type not in ("all", name):
+            continue
+        esize = 4 if dtype == torch.float32 else 8
+        for W in ((args.swe_grid,) if args.swe_grid else (256, 1024, 4096)):
+            n = W * W
+            offs = [[-2, -1, 1, 2], [-2 * W, -W, W, 2 * W], [-1, 0, 1, 2], [-W - 1, -W + 1, W - 1, W + 1]]
+            bands = [[torch.rand(n, dtype=dtype, device="cuda") - 0.5 for _ in range(4)] for _ in range(4)]
+            u, v, w, src = (torch.rand(n, dtype=dtype, device="cuda") for _ in range(4))
+            out = torch.empty_like(u)
+            tmp = [torch.empty_like(u) for _ in range(4)]
+            xs = (v, w, u, u)
+
+            def fused():
+                hn.hn_swe_predict(offs, bands, u, v, w, src, out, stream)
+
+            def composed():
+                for m in range(4):
+                    hn.hn_band4_spmv(offs[m], bands[m], xs[m], tmp[m], stream)
+                out.copy_(u)
+                for m in range(4):
+                    hn.hn_axpy(1.0, tmp[m], out, stream)
+                hn.hn_axpy(1.0, src, out, stream)
+
+            res = {}
+            for label, call in (("fused", fused), ("composed", composed)):
+                for _ in range(3):
+                    call()
+                reps = max(5, min(2000, int(4e9 / (21 * n * esize))))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(reps):
+                    call()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res[label] = e0.elapsed_time(e1) * 1e3 / reps
+            nbytes = 21 * n * esize           # 16 bands + u, v, w, s read, u_new written
+            rows.append({"type": name, "grid": "%dx%d" % (W, W), "n": n, "fused_us": res["fused"],
+                         "composed_us": res["composed"], "speedup": res["composed"] / res["fused"],
+                         "fused_gb_per_s": nbytes / res["fused"] / 1e3,
+                         "fused_frac_hbm": nbytes / res["fused"] / 1e3 / peak,
+                         "in_l2": nbytes < 120e6})
+            del bands, u, v, w, src, out, tmp
+    if rank == 0:
+        print(json.dumps({"metric": "SWE prediction step, fused vs composed (HBM GB/s)", "peak": peak,
+                          "peak_kind": kind, "bytes_per_row": "21 x element size (algorithmic)",
+                          "rows": rows}), flush=True)
+
+
+def run_solvers(args, rank, local):
+    """Solve time to 1e-8 of each outer solver (multigrid / defect correction, CG preconditioned by
+    one V cycle), coarse solver (exact, CG) and precision, at L = 10 (a = 1 and a lognormal field)
+    and L = 12 (a = 1); graph solves, L2 flushed between solves, CUDA events."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    from paper_0904_4152_gb300 import hn, inputs as I
+    torch.cuda.set_device(local)
+    g.build()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for L, lognormal in ((10, False), (10, True), (12, False)):
+        coef = I.lognormal_coef(L, 0) if lognormal else None
+        b = torch.from_numpy(I.rhs_uniform(L, 0)).cuda()
+        x = torch.zeros_like(b)
+        A = hn.hn_band_create(L, coef)
+        for prec in (hn.HN_PREC_FP64, hn.HN_PREC_FP32_DC, hn.HN_PREC_FP16BAND_DC):
+            for solver in (hn.HN_SOLVER_MG, hn.HN_SOLVER_PCG):
+                for coarse in (hn.HN_COARSE_EXACT, hn.HN_COARSE_CG):
+                    mg = hn.hn_mg_setup(A, prec=prec, solver=solver, coarse_solver=coarse,
+                                        stream=stream.cuda_stream)
+                    for _ in range(3):
+                        hn.hn_mg_solve(mg, L, b, x)
+                    ms = []
+                    for _ in range(args.steps):
+                        flush.fill_(1)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        _, st, status = hn.hn_mg_solve(mg, L, b, x)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        assert status == hn.HN_OK
+                        ms.append(e0.elapsed_time(e1))
+                    rows.append({"L": L, "coef": "lognormal" if lognormal else "a=1",
+                                 "prec": ["fp64", "fp32", "fp16band"][prec],
+                                 "solver": "pcg" if solver == hn.HN_SOLVER_PCG else "mg",
+                                 "coarse": "cg" if coarse == hn.HN_COARSE_CG else "exact",
+                                 "ms_median": float(np.median(ms)), "ms_min": float(np.min(ms)),
+                                 "cycles": st["cycles"], "outer_iters": st["outer_iters"],
+                                 "relres": st["relres"], "launches": hn.hn_mg_last_launches(mg)})
+                    hn.hn_mg_destroy(mg)
+        hn.hn_band_destroy(A)
+    if rank == 0:
+        print(json.dumps({"metric": "solve time to 1e-8 per solver, coarse solver and precision",
+                          "l2_between_steps": "flushed (512 MiB write)", "rows": rows}), flush=True)
+
+
 def run_ours(args, rank, world, local, pg):
     import numpy as np
     import torch
@@ -300,9 +416,11 @@ def run_ours(args, rank, world, local, pg):
     A = hn.hn_band_create(L)
     setup_band_s = time.perf_counter() - t0
     mgs = {}
-    for name, prec in (("mixed", hn.HN_PREC_FP32_DC), ("fp64", hn.HN_PREC_FP64),
-                       ("fp16band", hn.HN_PREC_FP16BAND_DC)):
-        mgs[name] = hn.hn_mg_setup(A, prec=prec, stream=stream.cuda_stream)
+    for name, prec, solver in (("mixed", hn.HN_PREC_FP32_DC, hn.HN_SOLVER_MG),
+                               ("fp64", hn.HN_PREC_FP64, hn.HN_SOLVER_MG),
+                               ("fp16band", hn.HN_PREC_FP16BAND_DC, hn.HN_SOLVER_MG),
+                               ("pcg_fp32", hn.HN_PREC_FP32_DC, hn.HN_SOLVER_PCG)):
+        mgs[name] = hn.hn_mg_setup(A, prec=prec, solver=solver, stream=stream.cuda_stream)
         if args.host_loop:
             hn.hn_mg_set_profiling(mgs[name], True)
     hn.hn_band_destroy(A)
@@ -334,6 +452,8 @@ def run_ours(args, rank, world, local, pg):
         ms_mixed, st_mixed, launches = timed(mgs["mixed"], args.steps, args.warmup)
     ms_fp64, st_fp64, _ = timed(mgs["fp64"], args.steps, args.warmup)
     ms_fp16, st_fp16, _ = timed(mgs["fp16band"], args.steps, args.warmup)
+    ms_pcg, st_pcg, _ = timed(mgs["pcg_fp32"], args.steps, args.warmup)
+    total_pcg = max_over_ranks(sum(ms_pcg), pg, dev)
     # the paper's performance configuration: Dirichlet at x = 0, 1, free Neumann at y = 0, 1
     A_lr = hn.hn_band_create_bc(L, None, hn.HN_DIRICHLET_LEFT | hn.HN_DIRICHLET_RIGHT)
     mg_lr = hn.hn_mg_setup(A_lr, prec=hn.HN_PREC_FP32_DC, stream=stream.cuda_stream)
@@ -428,6 +548,10 @@ def run_ours(args, rank, world, local, pg):
                          "cycles": st_fp16["cycles"], "outer_iters": st_fp16["outer_iters"],
                          "relres": st_fp16["relres"]},
             "mixed_over_fp64": value / fp64_value,
+            "pcg_fp32": {"solver": "FP64 CG preconditioned by one FP32 V(2,2) cycle",
+                         "dof_per_s": world * N * args.steps / (total_pcg * 1e-3),
+                         "ms_per_solve": total_pcg / args.steps, "cg_steps": st_pcg["outer_iters"],
+                         "cycles": st_pcg["cycles"], "relres": st_pcg["relres"]},
             "mixed_neumann_dirichlet": {"dirichlet": "x=0, x=1", "free_neumann": "y=0, y=1",
                                         "rhs": "U[-1,1] off the Dirichlet sides, seed=rank",
                                         "dof_per_s": world * N * args.steps / (total_lr * 1e-3),
@@ -649,6 +773,10 @@ def main():
         run_blas1(args, rank, local)
     elif args.workload == "kernels":
         run_kernels(args, rank, local)
+    elif args.workload == "swe":
+        run_swe(args, rank, local)
+    elif args.workload == "solvers":
+        run_solvers(args, rank, local)
     else:
         run_ours(args, rank, world, local, pg)
     if pg is not None:

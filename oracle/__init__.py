@@ -90,6 +90,12 @@ def lib():
         L.or_load_sincos.argtypes = [ctypes.c_int, dp]
         L.or_l2_error_sincos.argtypes = [ctypes.c_int, dp]
         L.or_l2_error_sincos.restype = ctypes.c_double
+        for t, ct in (("f32", ctypes.c_float), ("f64", ctypes.c_double)):
+            vp = ctypes.POINTER(ct)
+            getattr(L, "or_band4_spmv_" + t).argtypes = [ctypes.c_long, ctypes.POINTER(ctypes.c_longlong),
+                                                        ctypes.POINTER(vp), vp, vp]
+            getattr(L, "or_swe_predict_" + t).argtypes = [ctypes.c_long, ctypes.POINTER(ctypes.c_longlong),
+                                                         ctypes.POINTER(vp), vp, vp, vp, vp, vp]
         L.or_set_dirichlet.argtypes = [ctypes.c_uint]
         L.or_set_dirichlet.restype = None
         _lib = L
@@ -339,3 +345,41 @@ def dot(x, y):
     xs, ys = np.ascontiguousarray(x, np.float64), np.ascontiguousarray(y, np.float64)
     dp = ctypes.POINTER(ctypes.c_double)
     return lib().or_dot_f64(len(xs), xs.ctypes.data_as(dp), ys.ctypes.data_as(dp))
+
+
+def _band4_args(offsets, bands, dtype):
+    """offsets: (M, 4) ints; bands: (M, 4, n) arrays -> ctypes arrays (keeps the buffers alive)."""
+    ct = ctypes.c_float if dtype == np.float32 else ctypes.c_double
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64).reshape(-1))
+    ba = np.asarray(bands)
+    bs = [np.ascontiguousarray(ba[idx], dtype=dtype) for idx in np.ndindex(ba.shape[:-1])]
+    arr = (ctypes.POINTER(ct) * len(bs))(*[b.ctypes.data_as(ctypes.POINTER(ct)) for b in bs])
+    return offs.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), arr, (offs, bs), ct
+
+
+def band4_spmv(offsets, bands, x):
+    """y_i = sum_k band_k[i] x[i + offsets[k]] over existing columns (fused multiply-adds, k in
+    order): a banded matrix with four bands at arbitrary positions (Sec. 2.2, Sec. 4.1)."""
+    x = np.asarray(x)
+    dt = np.float32 if x.dtype == np.float32 else np.float64
+    po, pb, keep, ct = _band4_args(offsets, bands, dt)
+    xx = np.ascontiguousarray(x, dtype=dt)
+    y = np.zeros(xx.size, dtype=dt)
+    f = lib().or_band4_spmv_f32 if dt == np.float32 else lib().or_band4_spmv_f64
+    f(xx.size, po, pb, _p(xx, ct), _p(y, ct))
+    return y
+
+
+def swe_predict(offsets, bands, u, v, w, s=None):
+    """u_new = u + M1 v + M2 w + M3 u + M4 u + s, offsets (4, 4), bands (4, 4, n), in the order of
+    the definition (running sum from u, one fused multiply-add per existing entry, s last)."""
+    u = np.asarray(u)
+    dt = np.float32 if u.dtype == np.float32 else np.float64
+    po, pb, keep, ct = _band4_args(offsets, bands, dt)
+    uu, vv, ww = (np.ascontiguousarray(a, dtype=dt) for a in (u, v, w))
+    ss = None if s is None else np.ascontiguousarray(s, dtype=dt)
+    out = np.zeros(uu.size, dtype=dt)
+    f = lib().or_swe_predict_f32 if dt == np.float32 else lib().or_swe_predict_f64
+    f(uu.size, po, pb, _p(uu, ct), _p(vv, ct), _p(ww, ct), _p(ss, ct), _p(out, ct))
+    return out
+

@@ -841,3 +841,61 @@ double or_dot_f64(long n, const double* x, const double* y) {
 }
 
 }  // extern "C"
+
+namespace {
+// ---- Banded matrices with four bands at arbitrary positions and the shallow-water prediction
+// step (Sec. 2.2): u_new = u + M1 v + M2 w + M3 u + M4 u + S, with S given.  Band k of M holds
+// M[i, i + off_k]; an entry whose column i + off_k lies outside 0..n-1 does not exist.  The
+// rounding order is part of the definition: a running sum t updated by one fused multiply-add per
+// existing entry, matrices in order M1..M4, bands k = 0..3 in order; the source term added last.
+template <typename T>
+static void band4_apply(long n, const long long* off, const T* const* band, const T* x, long i,
+                        T& t) {
+  for (int k = 0; k < 4; ++k) {
+    const long long j = (long long)i + off[k];
+    if (j < 0 || j >= n) continue;
+    t = std::fma(band[k][i], x[j], t);
+  }
+}
+
+template <typename T>
+static void band4_spmv(long n, const long long* off, const T* const* band, const T* x, T* y) {
+  for (long i = 0; i < n; ++i) {
+    T t = 0;
+    band4_apply<T>(n, off, band, x, i, t);
+    y[i] = t;
+  }
+}
+
+// off: 16 offsets (matrix m, band k at 4 m + k); band: 16 arrays of n elements; s may be NULL
+template <typename T>
+static void swe_predict(long n, const long long* off, const T* const* band, const T* u, const T* v,
+                        const T* w, const T* s, T* u_new) {
+  const T* xs[4] = {v, w, u, u};
+  for (long i = 0; i < n; ++i) {
+    T t = u[i];
+    for (int m = 0; m < 4; ++m) band4_apply<T>(n, off + 4 * m, band + 4 * m, xs[m], i, t);
+    u_new[i] = s ? t + s[i] : t;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void or_band4_spmv_f32(long n, const long long* off, const float* const* band, const float* x, float* y) {
+  band4_spmv<float>(n, off, band, x, y);
+}
+void or_band4_spmv_f64(long n, const long long* off, const double* const* band, const double* x, double* y) {
+  band4_spmv<double>(n, off, band, x, y);
+}
+void or_swe_predict_f32(long n, const long long* off, const float* const* band, const float* u,
+                        const float* v, const float* w, const float* s, float* u_new) {
+  swe_predict<float>(n, off, band, u, v, w, s, u_new);
+}
+void or_swe_predict_f64(long n, const long long* off, const double* const* band, const double* u,
+                        const double* v, const double* w, const double* s, double* u_new) {
+  swe_predict<double>(n, off, band, u, v, w, s, u_new);
+}
+
+}  // extern "C"

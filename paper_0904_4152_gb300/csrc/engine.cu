@@ -233,7 +233,10 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
     P.p64 = b.take<double>(vec_elems(L)) + halo_of(L);
     P.q64 = b.take<double>(vec_elems(L)) + halo_of(L);
   }
-  double* cinv = b.take<double>((size_t)mg->m * mg->m);
+  // the coarse inverse (m x m), or for the CG coarse solver the 9 coarse bands (9 N_c); the
+  // layout reserves (N_c)^2 >= both
+  const size_t cwords = prm.coarse_cg ? (size_t)(9 * N_of(c)) : (size_t)mg->m * mg->m;
+  double* cinv = b.take<double>(cwords);
   P.cinv = cinv;
   if (b.off > mg->bytes) return set_error(HN_ERR_STATE, "hierarchy layout overflow");
 
@@ -322,11 +325,16 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
           a[(size_t)(I * m + J)] = coarse64[(size_t)k * pc + iy * n + ix];
         }
       }
-    // CG keeps the matrix itself (the inverse still proves it nonsingular)
-    std::vector<double> inv(a);
-    if (!invert(inv, m)) return set_error(HN_ERR_STATE, "coarse matrix is singular");
-    const std::vector<double>& up = prm.coarse_cg ? a : inv;
-    HN_CUDA(cudaMemcpyAsync(cinv, up.data(), up.size() * 8, cudaMemcpyHostToDevice, s));
+    if (!invert(a, m)) return set_error(HN_ERR_STATE, "coarse matrix is singular");
+    if (prm.coarse_cg) {
+      // CG works on the 9 FP64 bands of the level, band k at k * N_c
+      const long long Nc = n * n;
+      std::vector<double> cb((size_t)(9 * Nc));
+      for (int k = 0; k < 9; ++k)
+        for (long long i = 0; i < Nc; ++i) cb[(size_t)(k * Nc + i)] = coarse64[(size_t)k * pc + i];
+      a.swap(cb);
+    }
+    HN_CUDA(cudaMemcpyAsync(cinv, a.data(), a.size() * 8, cudaMemcpyHostToDevice, s));
     HN_CUDA(cudaStreamSynchronize(s));
   }
   return HN_OK;

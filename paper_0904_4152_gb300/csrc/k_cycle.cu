@@ -545,51 +545,70 @@ __device__ __forceinline__ void coarse_warp(const ProblemDev& P, int lane, doubl
   __syncwarp();
 }
 
-// (u, v) over m <= kMaxCoarseM entries by warp 0 (lane l adds entries l, l + 32, ... in order,
-// then the butterfly), broadcast to the block: the order does not depend on the block size.
-// Every thread of the block calls it.
-__device__ __forceinline__ double warp0_dot(const double* u, const double* v, int m, double* sh) {
-  if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int i = threadIdx.x; i < m; i += 32) t = fma(u[i], v[i], t);
-    t = warp_sum(t);
-    if (threadIdx.x == 0) sh[31] = t;
-  }
-  __syncthreads();
-  const double r = sh[31];
-  __syncthreads();
-  return r;
+// Unpreconditioned conjugate gradients on the coarsest level (Sec. 6.2 configures the coarse
+// solver so), in FP64 by the whole block over all N_c = n^2 nodes of the level: ab holds its 9
+// FP64 bands (band k at ab + k N_c; Dirichlet rows are identity rows and no row couples to a
+// Dirichlet node, so with a zero right-hand side there these nodes stay 0 and the iteration is CG
+// on the unknowns).  r holds the right-hand side on entry and the residual on exit, x receives the
+// solution, p, q and sc (4 doubles) are scratch.  Textbook CG from x = 0 (Hestenes and Stiefel):
+// q = A p, alpha = (r, r) / (p, q), x += alpha p, r -= alpha q; stop once (r, r) <=
+// kCoarseCgTol^2 (b, b) or after coarse_cg_steps(m) steps (m unknowns); else p = r + ((r, r)_new /
+// (r, r)) p.  Inner products: warp 0, lane l adds nodes l, l + 32, ... in order, then the
+// butterfly, so the result does not depend on the block size; the scalar divisions run in one
+// thread (FP64 is slow on this part: redundant divisions across the block cost microseconds).
+__device__ __forceinline__ double coarse_warp0_dot(const double* u, const double* v, int N) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < N; i += 32) t = fma(u[i], v[i], t);
+  return warp_sum(t);
 }
 
-// Unpreconditioned conjugate gradients on the coarsest level (Sec. 6.2 configures the coarse
-// solver so), in FP64 by the whole block: Am is the m x m matrix on the unknowns (row-major, any
-// memory), r holds the right-hand side on entry and the residual on exit, x receives the
-// approximate solution; p, q are scratch (m doubles each).  Textbook CG from x = 0 (Hestenes and
-// Stiefel): q = A p, alpha = (r, r) / (p, q), x += alpha p, r -= alpha q; stop once (r, r) <=
-// kCoarseCgTol^2 (b, b) or after coarse_cg_steps(m) steps; else p = r + ((r, r)_new / (r, r)) p.
-__device__ void coarse_cg(const double* Am, int m, double* x, double* r, double* p, double* q,
-                          double* sh) {
-  const int nt = blockDim.x;
-  for (int u = threadIdx.x; u < m; u += nt) { x[u] = 0.0; p[u] = r[u]; }
+__device__ void coarse_cg(const double* ab, int n, int m, double* x, double* r, double* p,
+                          double* q, double* sc) {
+  const int N = n * n, nt = blockDim.x;
+  for (int i = threadIdx.x; i < N; i += nt) { x[i] = 0.0; p[i] = r[i]; }
   __syncthreads();
-  double rr = warp0_dot(r, r, m, sh);
-  const double stop = kCoarseCgTol * kCoarseCgTol * rr;
+  if (threadIdx.x < 32) {
+    const double rr = coarse_warp0_dot(r, r, N);
+    if (threadIdx.x == 0) { sc[0] = rr; sc[1] = kCoarseCgTol * kCoarseCgTol * rr; }
+  }
+  __syncthreads();
   const int kmax = coarse_cg_steps(m);
-  for (int k = 0; k < kmax && rr > 0.0; ++k) {
-    for (int u = threadIdx.x; u < m; u += nt)
-      q[u] = coarse_dot(Am + (long long)u * m, m, [&](int v) { return p[v]; });
-    __syncthreads();
-    const double alpha = rr / warp0_dot(p, q, m, sh);
-    for (int u = threadIdx.x; u < m; u += nt) {
-      x[u] = fma(alpha, p[u], x[u]);
-      r[u] = fma(-alpha, q[u], r[u]);
+  for (int k = 0; k < kmax; ++k) {
+    if (!(sc[0] > 0.0)) break;                  // uniform: read by all after a barrier
+    for (int i = threadIdx.x; i < N; i += nt) {
+      // one chain per stencil row (FP64 latency), then (row -1 + row 0) + row +1
+      const int iy = i / n, ix = i - iy * n;
+      double t[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int b = 0; b < 9; ++b) {
+        const int jx = ix + b % 3 - 1, jy = iy + b / 3 - 1;
+        if (jx >= 0 && jy >= 0 && jx < n && jy < n) t[b / 3] = fma(ab[b * N + i], p[jy * n + jx], t[b / 3]);
+      }
+      q[i] = (t[0] + t[1]) + t[2];
     }
     __syncthreads();
-    const double rr1 = warp0_dot(r, r, m, sh);
-    if (!(rr1 > stop)) break;                   // also ends on a NaN
-    const double beta = rr1 / rr;
-    rr = rr1;
-    for (int u = threadIdx.x; u < m; u += nt) p[u] = fma(beta, p[u], r[u]);
+    if (threadIdx.x < 32) {
+      const double pq = coarse_warp0_dot(p, q, N);
+      if (threadIdx.x == 0) sc[2] = sc[0] / pq;             // alpha
+    }
+    __syncthreads();
+    const double alpha = sc[2];
+    for (int i = threadIdx.x; i < N; i += nt) {
+      x[i] = fma(alpha, p[i], x[i]);
+      r[i] = fma(-alpha, q[i], r[i]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const double rr1 = coarse_warp0_dot(r, r, N);
+      if (threadIdx.x == 0) {
+        sc[3] = rr1 > sc[1] ? rr1 / sc[0] : -1.0;            // beta, or stop (also on a NaN)
+        sc[0] = rr1;
+      }
+    }
+    __syncthreads();
+    const double beta = sc[3];
+    if (beta < 0.0) break;
+    for (int i = threadIdx.x; i < N; i += nt) p[i] = fma(beta, p[i], r[i]);
     __syncthreads();
   }
   __syncthreads();
@@ -875,26 +894,20 @@ template <class V>
 __global__ void __launch_bounds__(256) k_coarse_cg(EngineDev E, int want) {
   pdl_start();
   __shared__ double x[kMaxCoarseM], r[kMaxCoarseM], pv[kMaxCoarseM], qv[kMaxCoarseM];
-  __shared__ double sh[32];
+  __shared__ double sc[4];
   const int p = blockIdx.x;
   if (p >= E.nprob || E.S[p].phase != want) return;
   const ProblemDev& P = E.P[p];
   if (P.L < HN_MIN_LEVEL) return;
   const LevelDev& d = P.lev[P.coarse];
-  const int n = d.n, m = P.m;
-  const UnknownRect ur = unknown_rect(n, d.bc);
+  const int n = d.n, N = n * n;
   const V* rhs = static_cast<const V*>(d.rhs);
-  for (int v = threadIdx.x; v < m; v += blockDim.x)
-    r[v] = double(rhs[(v / ur.nx + ur.y0) * n + (v % ur.nx + ur.x0)]);
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    r[i] = is_dirichlet(i % n, i / n, n, d.bc) ? 0.0 : double(rhs[i]);
   __syncthreads();
-  coarse_cg(P.cinv, m, x, r, pv, qv, sh);
+  coarse_cg(P.cinv, n, P.m, x, r, pv, qv, sc);
   V* xo = static_cast<V*>(d.x[0]);
-  for (int q = threadIdx.x; q < d.pitch; q += blockDim.x) {
-    const int iy = q / n - ur.y0, ix = q - (q / n) * n - ur.x0;
-    V val = V(0);
-    if (q < n * n && ix >= 0 && iy >= 0 && ix < ur.nx && iy < ur.ny) val = V(x[iy * ur.nx + ix]);
-    xo[q] = val;
-  }
+  for (int i = threadIdx.x; i < d.pitch; i += blockDim.x) xo[i] = i < N ? V(x[i]) : V(0);
 }
 
 // ----------------------------------------------------------- fused coarse-level V cycle
@@ -1471,20 +1484,22 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
   }
   long long off = 0;
   for (int l = c; l <= Ss; ++l) smem_level_setup<Pol>(gd[l], sd[l], smem, &off, l, rank == 0, &s_bar);
-  double* cg_pq = nullptr;                      // CG coarse solver: p and q (m doubles each)
-  {   // the coarse inverse (CG: the coarse matrix; m*m doubles) is staged in shared memory when
-      // it is small
-    const bool staged = (long long)m * m * 8 <= kCinvSmemMax;
+  double* cg_pq = nullptr;                      // CG coarse solver: p and q (N_c doubles each)
+  {   // the coarse inverse (m*m doubles; CG: the 9 FP64 coarse bands, 9 N_c doubles) is staged in
+      // shared memory when it is small
+    const int Nc = (int)(n_of_dev(c) * n_of_dev(c));
+    const long long words = E.prm.coarse_cg ? 9LL * Nc : (long long)m * m;
+    const bool staged = words * 8 <= kCinvSmemMax;
     double* dst = reinterpret_cast<double*>(smem + off);
-    if (staged) off += ((long long)m * m * 8 + 15) / 16 * 16;
+    if (staged) off += (words * 8 + 15) / 16 * 16;
     if (E.prm.coarse_cg) {
       cg_pq = reinterpret_cast<double*>(smem + off);
-      off += ((long long)2 * m * 8 + 15) / 16 * 16;
+      off += ((long long)2 * Nc * 8 + 15) / 16 * 16;
     }
     if (rank == 0 && threadIdx.x == 0) {
       if (staged) {
-        bulk_copy(dst, P.cinv, (unsigned)(m * m / 2) * 16u, &s_bar);
-        if ((m * m) & 1) dst[m * m - 1] = __ldg(P.cinv + m * m - 1);
+        bulk_copy(dst, P.cinv, (unsigned)(words / 2) * 16u, &s_bar);
+        if (words & 1) dst[words - 1] = __ldg(P.cinv + words - 1);
       }
       s_cinv = staged ? dst : P.cinv;
     }
@@ -1592,22 +1607,28 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
       const UnknownRect ur = unknown_rect(n, d.bc);
       const V* rhs = static_cast<const V*>(d.rhs);
       const double* cinv = s_cinv;
-      for (int v = threadIdx.x; v < m; v += blockDim.x)
-        rd[v] = double(rhs[(v / ur.nx + ur.y0) * n + (v % ur.nx + ur.x0)]);
-      __syncthreads();
+      V* x = static_cast<V*>(d.x[0]);
       if (E.prm.coarse_cg) {
-        coarse_cg(cinv, m, sol, rd, cg_pq, cg_pq + m, sh);
+        // CG over all nodes of the level (sol, rd: N_c <= kMaxCoarseM doubles)
+        const int Nc = n * n;
+        for (int i = threadIdx.x; i < Nc; i += blockDim.x)
+          rd[i] = is_dirichlet(i % n, i / n, n, d.bc) ? 0.0 : double(rhs[i]);
+        __syncthreads();
+        coarse_cg(cinv, n, m, sol, rd, cg_pq, cg_pq + Nc, sh);
+        for (int q = threadIdx.x; q < d.pitch; q += blockDim.x) x[q] = q < Nc ? V(sol[q]) : V(0);
       } else {
+        for (int v = threadIdx.x; v < m; v += blockDim.x)
+          rd[v] = double(rhs[(v / ur.nx + ur.y0) * n + (v % ur.nx + ur.x0)]);
+        __syncthreads();
         for (int u = threadIdx.x; u < m; u += blockDim.x)
           sol[u] = coarse_dot(cinv + u * m, m, [&](int v) { return rd[v]; });
         __syncthreads();
-      }
-      V* x = static_cast<V*>(d.x[0]);
-      for (int q = threadIdx.x; q < d.pitch; q += blockDim.x) {
-        const int iy = q / n - ur.y0, ix = q - (q / n) * n - ur.x0;
-        V val = V(0);
-        if (q < n * n && ix >= 0 && iy >= 0 && ix < ur.nx && iy < ur.ny) val = V(sol[iy * ur.nx + ix]);
-        x[q] = val;
+        for (int q = threadIdx.x; q < d.pitch; q += blockDim.x) {
+          const int iy = q / n - ur.y0, ix = q - (q / n) * n - ur.x0;
+          V val = V(0);
+          if (q < n * n && ix >= 0 && iy >= 0 && ix < ur.nx && iy < ur.ny) val = V(sol[iy * ur.nx + ix]);
+          x[q] = val;
+        }
       }
       __syncthreads();
       for (int l = c + 1; l <= Ss; ++l) vcycle_up_smem<Pol>(sd[l], sd[l - 1], pre, post, omega);
@@ -2171,8 +2192,9 @@ constexpr long long kTailSmemMax = 212 * 1024;      // with the cluster levels (
 // shared memory reserved for a staged coarse inverse: the unknowns of the coarsest level number at
 // most n^2 (free Neumann sides), and an inverse is staged only if it takes <= kCinvSmemMax bytes
 long long tail_cinv_bytes(int coarse, int cg) {
-  const long long m = ((1LL << coarse) + 1) * ((1LL << coarse) + 1);
-  return (std::min(m * m * 8, kCinvSmemMax) + 15) / 16 * 16 + (cg ? (2 * m * 8 + 15) / 16 * 16 : 0);
+  const long long m = ((1LL << coarse) + 1) * ((1LL << coarse) + 1);   // nodes >= unknowns
+  if (cg) return (std::min(9 * m * 8, kCinvSmemMax) + 15) / 16 * 16 + (2 * m * 8 + 15) / 16 * 16;
+  return (std::min(m * m * 8, kCinvSmemMax) + 15) / 16 * 16;
 }
 
 int tail_smem_level(int prec, int coarse, int cg, int T) {

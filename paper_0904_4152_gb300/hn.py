@@ -38,6 +38,7 @@ EXPORTS = [
     "hn_mg_set_profiling", "hn_mg_kernel_times", "hn_mg_last_launches",
     "hn_band_defect_norm_static", "hn_mg_set_tuning", "hn_mg_get_tuning", "hn_mg_autotune",
     "hn_mg_autotune_batch", "hn_mg_time_kernel", "hn_axpy", "hn_dot", "hn_nrm2",
+    "hn_band4_spmv", "hn_swe_predict",
 ]
 
 
@@ -140,6 +141,8 @@ def lib():
         L.hn_axpy.argtypes = [ip, ctypes.c_longlong, ctypes.c_double, vp, vp, vp]
         L.hn_dot.argtypes = [ip, ctypes.c_longlong, vp, vp, vp, vp]
         L.hn_nrm2.argtypes = [ip, ctypes.c_longlong, vp, vp, vp]
+        L.hn_band4_spmv.argtypes = [ip, ctypes.c_longlong, vp, vp, vp, vp]
+        L.hn_swe_predict.argtypes = [ip, ctypes.c_longlong, vp, vp, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -474,3 +477,48 @@ def hn_nrm2(x, result, stream=None):
     """result[0] = ||x||_2 (result: a CUDA float64 tensor of at least one element)."""
     t, n, px = _blas_vec(x)
     _check(lib().hn_nrm2(t, n, px, ctypes.c_void_p(result.data_ptr()), _stream_ptr(stream)))
+
+
+# -------------------------------------- four-band matrices and the prediction step (hn_swe.h)
+class Band4(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_longlong * 4), ("band", ctypes.c_void_p * 4)]
+
+
+def _band4(offsets, bands, t, n):
+    """An hn_band4 of 4 offsets and 4 CUDA tensors of type t and length n."""
+    if len(offsets) != 4 or len(bands) != 4:
+        raise ValueError("a four-band matrix needs 4 offsets and 4 bands")
+    m = Band4()
+    for k in range(4):
+        tk, nk, pk = _blas_vec(bands[k])
+        if (tk, nk) != (t, n):
+            raise ValueError("band %d differs in type or length" % k)
+        m.offset[k] = int(offsets[k])
+        m.band[k] = pk.value
+    return m
+
+
+def hn_band4_spmv(offsets, bands, x, y, stream=None):
+    """y = M x, M[i, i + offsets[k]] = bands[k][i] (CUDA tensors of x's type and length)."""
+    t, n, px = _blas_vec(x)
+    t2, n2, py = _blas_vec(y)
+    if (t, n) != (t2, n2):
+        raise ValueError("x and y differ in type or length")
+    m = _band4(offsets, bands, t, n)
+    _check(lib().hn_band4_spmv(t, n, ctypes.byref(m), px, py, _stream_ptr(stream)))
+
+
+def hn_swe_predict(offsets, bands, u, v, w, s, u_new, stream=None):
+    """u_new = u + M1 v + M2 w + M3 u + M4 u + s; offsets: 4 x 4 ints, bands: 4 x 4 CUDA tensors;
+    s may be None."""
+    t, n, pu = _blas_vec(u)
+    ptrs = []
+    for vec in (v, w, u_new) + (() if s is None else (s,)):
+        tv, nv, pv = _blas_vec(vec)
+        if (tv, nv) != (t, n):
+            raise ValueError("vectors differ in type or length")
+        ptrs.append(pv)
+    ms = (Band4 * 4)(*[_band4(offsets[i], bands[i], t, n) for i in range(4)])
+    _check(lib().hn_swe_predict(t, n, ms, pu, ptrs[0], ptrs[1], None if s is None else ptrs[3],
+                                ptrs[2], _stream_ptr(stream)))
+

@@ -693,3 +693,58 @@ def test_pcg_mixed_boundaries_manufactured_solution():
     xp, sp = O.pcg_solve(L, b, bc=LR, tol=1e-11)
     assert sp["converged"]
     assert abs(O.l2_error_sincos(L, xp) / O.l2_error_sincos(L, xm) - 1) < 1e-6
+
+
+# ------------------------------------------- four-band matrices and the shallow-water prediction step
+def _dense_band4(offsets, bands, n):
+    """The matrix itself, entry by entry: M[i, i + off_k] = band_k[i] where the column exists."""
+    M = np.zeros((n, n))
+    for k, d in enumerate(offsets):
+        for i in range(n):
+            if 0 <= i + d < n:
+                M[i, i + d] += bands[k][i]
+    return M
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_swe_predict_exact_on_integers(dtype):
+    # small integers: every product and sum is exact in both precisions, so the result must equal
+    # the integer linear combination exactly (pins indexing, offsets, edges and the operands)
+    n = 61
+    rng = np.random.default_rng(1)
+    offs = np.array([[-2, -1, 1, 2], [-12, -6, 6, 12], [-1, 0, 1, 3], [-70, 4, 7, 60]])
+    bands = rng.integers(-3, 4, (4, 4, n))
+    u, v, w, s = (rng.integers(-5, 6, n) for _ in range(4))
+    ref = u + s
+    for m, x in enumerate((v, w, u, u)):
+        ref = ref + _dense_band4(offs[m], bands[m], n).astype(np.int64) @ x
+    got = O.swe_predict(offs, bands.astype(dtype), u.astype(dtype), v.astype(dtype), w.astype(dtype),
+                        s.astype(dtype))
+    assert got.dtype == dtype
+    np.testing.assert_array_equal(got.astype(np.int64), ref)
+    got = O.swe_predict(offs, bands.astype(dtype), u.astype(dtype), v.astype(dtype), w.astype(dtype))
+    np.testing.assert_array_equal(got.astype(np.int64), ref - s)
+
+
+def test_band4_against_scipy_diagonals():
+    sp = pytest.importorskip("scipy.sparse")
+    n = 300
+    rng = np.random.default_rng(2)
+    offs = [-17, -1, 2, 17]
+    bands = rng.uniform(-1, 1, (4, n))
+    x = rng.uniform(-1, 1, n)
+    diags = [bands[k][max(0, -d):n - max(0, d)] for k, d in enumerate(offs)]
+    M = sp.diags(diags, offs, shape=(n, n))
+    y = O.band4_spmv(offs, bands, x)
+    ref = M @ x
+    assert np.max(np.abs(y - ref)) <= 1e-15 * 4 * np.max(np.abs(bands)) * np.max(np.abs(x))
+    y32 = O.band4_spmv(offs, bands.astype(np.float32), x.astype(np.float32))
+    assert np.max(np.abs(y32 - ref)) <= 4 * 4 * 2.0 ** -24 * 4
+
+
+def test_band4_degenerate_sizes():
+    offs = [[5, 6, 7, 8]] * 4                  # every column beyond n = 4: no entries
+    bands = np.ones((4, 4, 4))
+    u = np.arange(4.0)
+    np.testing.assert_array_equal(O.swe_predict(offs, bands, u, u, u, u), 2 * u)
+    assert O.swe_predict(offs, np.ones((4, 4, 0)), np.zeros(0), np.zeros(0), np.zeros(0)).size == 0
