@@ -5,6 +5,8 @@
 // x[i + offset .. i + offset + 3] with two aligned 16-byte loads (the misalignment offset mod 4 is
 // the same for every thread of a launch, so the selection does not diverge); neighbouring
 // threads share those lines through L1.  Rows whose window leaves 0..n-1 take a checked path.
+#include <climits>
+
 #include "engine.h"
 #include "../../include/hn_swe.h"
 
@@ -24,6 +26,7 @@ struct SweArg {
   const void* s;         // added last (nullptr: nothing)
   void* out;
   long long n;
+  long long lo, hi;      // rows i0 with i0 + lo >= 0 and i0 + hi <= n read every window in range
   int nmat;
 };
 
@@ -49,20 +52,39 @@ template <> struct Vec4<double> {
   }
 };
 
-// x[j0 .. j0+3] for an in-range window, j0 = i0 + off with i0 a multiple of 4: from the aligned
-// 8-element span starting at j0 - (off mod 4) (one 4-vector when aligned)
+// x[j0 .. j0+3], j0 = i0 + off with i0 a multiple of 4: from the aligned 8-element span starting
+// at j0 - mis, mis = off mod 4 (the same for every thread of a launch); selects, not branches, so
+// the loads of all bands can be issued together
 template <class T>
-__device__ __forceinline__ void window4(const T* x, long long j0, int mis, T (&o)[4]) {
-  if (mis == 0) { Vec4<T>::ld(x + j0, o); return; }
-  T a[4], b[4];
-  Vec4<T>::ld(x + j0 - mis, a);
-  Vec4<T>::ld(x + j0 - mis + 4, b);
-  if (mis == 1) { o[0] = a[1]; o[1] = a[2]; o[2] = a[3]; o[3] = b[0]; }
-  else if (mis == 2) { o[0] = a[2]; o[1] = a[3]; o[2] = b[0]; o[3] = b[1]; }
-  else { o[0] = a[3]; o[1] = b[0]; o[2] = b[1]; o[3] = b[2]; }
+__device__ __forceinline__ void window4(const T* x, long long base, int mis, T (&o)[4]) {
+  T v[8];
+  Vec4<T>::ld(x + base, *reinterpret_cast<T(*)[4]>(&v[0]));
+  Vec4<T>::ld(x + base + 4, *reinterpret_cast<T(*)[4]>(&v[4]));
+#pragma unroll
+  for (int e = 0; e < 4; ++e) o[e] = mis == 0 ? v[e] : mis == 1 ? v[e + 1] : mis == 2 ? v[e + 2] : v[e + 3];
 }
 
-template <class T>
+// rows i0..i0+3, every window inside the vector (the caller checked the extreme offsets)
+template <class T, int NMAT>
+__device__ __forceinline__ void rows4_fast(const SweArg& a, long long i0, T (&t)[4]) {
+#pragma unroll
+  for (int m = 0; m < NMAT; ++m) {
+    const T* x = static_cast<const T*>(a.x[m]);
+    T b[4][4], xv[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long off = a.M[m].off[k];
+      Vec4<T>::ld(static_cast<const T*>(a.M[m].band[k]) + i0, b[k]);
+      window4<T>(x, i0 + (off & ~3LL), (int)(off & 3), xv[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) t[e] = fma(b[k][e], xv[k][e], t[e]);
+  }
+}
+
+template <class T, int NMAT>
 __global__ void __launch_bounds__(kThreads) k_band4(SweArg a) {
   const long long n = a.n;
   const long long stride = 4LL * gridDim.x * blockDim.x;
@@ -71,23 +93,19 @@ __global__ void __launch_bounds__(kThreads) k_band4(SweArg a) {
     if (i0 + 4 <= n) {
       if (a.u) Vec4<T>::ld(static_cast<const T*>(a.u) + i0, t);
       else t[0] = t[1] = t[2] = t[3] = T(0);
-      for (int m = 0; m < a.nmat; ++m) {
-        const T* x = static_cast<const T*>(a.x[m]);
+      if (i0 + a.lo >= 0 && i0 + a.hi <= n) {
+        rows4_fast<T, NMAT>(a, i0, t);
+      } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const long long off = a.M[m].off[k];
-          T b[4], xv[4];
-          Vec4<T>::ld(static_cast<const T*>(a.M[m].band[k]) + i0, b);
-          const long long j0 = i0 + off;
-          const int mis = (int)(off & 3);
-          if (j0 - mis >= 0 && j0 - mis + (mis ? 8 : 4) <= n) {
-            window4<T>(x, j0, mis, xv);
+        for (int m = 0; m < NMAT; ++m) {
+          const T* x = static_cast<const T*>(a.x[m]);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) t[e] = fma(b[e], xv[e], t[e]);
-          } else {
+          for (int k = 0; k < 4; ++k) {
+            T b[4];
+            Vec4<T>::ld(static_cast<const T*>(a.M[m].band[k]) + i0, b);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              const long long j = j0 + e;
+              const long long j = i0 + a.M[m].off[k] + e;
               if (j >= 0 && j < n) t[e] = fma(b[e], __ldg(x + j), t[e]);
             }
           }
@@ -103,7 +121,7 @@ __global__ void __launch_bounds__(kThreads) k_band4(SweArg a) {
     } else {
       for (long long i = i0; i < n; ++i) {          // the last, partial group of rows
         T r = a.u ? __ldg(static_cast<const T*>(a.u) + i) : T(0);
-        for (int m = 0; m < a.nmat; ++m) {
+        for (int m = 0; m < NMAT; ++m) {
           const T* x = static_cast<const T*>(a.x[m]);
           for (int k = 0; k < 4; ++k) {
             const long long j = i + a.M[m].off[k];
@@ -119,13 +137,27 @@ __global__ void __launch_bounds__(kThreads) k_band4(SweArg a) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-hn_status launch(hn_dtype type, const SweArg& a, cudaStream_t s) {
+hn_status launch(hn_dtype type, SweArg a, cudaStream_t s) {
   if (a.n == 0) return HN_OK;
+  // the aligned 8-element span of a window starts at i0 + (off & ~3)
+  a.lo = LLONG_MAX;
+  a.hi = LLONG_MIN;
+  for (int m = 0; m < a.nmat; ++m)
+    for (int k = 0; k < 4; ++k) {
+      const long long base = a.M[m].off[k] & ~3LL;
+      a.lo = std::min(a.lo, base);
+      a.hi = std::max(a.hi, base + 8);
+    }
+  void (*kern)(SweArg) = type == HN_F32 ? (a.nmat == 1 ? k_band4<float, 1> : k_band4<float, 4>)
+                                         : (a.nmat == 1 ? k_band4<double, 1> : k_band4<double, 4>);
+  // one wave of resident blocks (grid-stride loop); the occupancy of each kernel is asked once
+  static int occ[2][2] = {{0, 0}, {0, 0}};
+  int& per_sm = occ[type == HN_F32 ? 0 : 1][a.nmat == 1 ? 0 : 1];
+  if (per_sm == 0) HN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
   const long long groups = (a.n + 3) / 4;
-  const long long cap = (long long)sm_count() * 8;
+  const long long cap = (long long)sm_count() * std::max(per_sm, 1);
   const int grid = (int)std::max<long long>(1, std::min((groups + kThreads - 1) / kThreads, cap));
-  if (type == HN_F32) k_band4<float><<<grid, kThreads, 0, s>>>(a);
-  else k_band4<double><<<grid, kThreads, 0, s>>>(a);
+  kern<<<grid, kThreads, 0, s>>>(a);
   HN_CUDA(cudaGetLastError());
   return HN_OK;
 }
