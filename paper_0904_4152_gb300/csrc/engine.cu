@@ -567,11 +567,11 @@ long long Engine::launch_bytes(int cls, int level) const {
   const int prec = prm_.prec;
   const double vb = prec == P64 ? 8 : 4;
   const double bb = prec == P64 ? 8 : (prec == P32 ? 4 : 2);
-  const double wd = prec == P64 ? 8 : 0;   // stored omega/diag (FP64 hierarchy only)
+  const double wd = prec == P64 ? 8 : 0;   // stored omega/diag read by Jacobi (FP64 hierarchy only)
   double per = 0;
   switch (cls) {
     case KC_JACOBI: per = 9 * bb + 3 * vb + wd; break;
-    case KC_JACOBI_FIRST: per = 9 * bb + 2 * vb + wd; break;   // two fused steps from x = 0
+    case KC_JACOBI_FIRST: per = 9 * bb + 2 * vb + (prec == P64 ? 8 : 4); break;   // fused from x = 0
     case KC_DEFECT: per = 9 * bb + 3 * vb; break;
     case KC_CHECK: per = 9 * bb + 2 * vb; break;
     case KC_RESTRICT: per = 1.25 * vb; break;                   // per fine node

@@ -290,7 +290,9 @@ enum BandMode {
 
 template <class Pol> __device__ __forceinline__ constexpr bool fuses_pre() { return true; }
 
-// omega / diag at the lane's 4 nodes from the stored array (FP64) or the diagonal band (FP32)
+// omega / diag at the lane's 4 nodes.  FP64: the stored wdinv (LKB: load kind of the bands, with
+// which it is staged).  FP32 / FP16: omega / dg from the diagonal the stencil formed anyway;
+// reading the stored wdf instead (4 more bytes per node) measured slower for both.
 template <class Pol, int LKB>
 __device__ __forceinline__ void wd4_of(const LevelDev& d, long long i0, typename Pol::A omega,
                                        const typename Pol::A (&dg)[4], typename Pol::A (&wd)[4]) {
@@ -448,20 +450,25 @@ __device__ __forceinline__ V restrict_value(int I, int J, int nc, int nf, int bc
   return v;
 }
 
+// Restriction of the coarse warp-tile starting at t0 (128 nodes): lane l takes the coarse nodes
+// t0 + l + 32 j, j = 0..3, so that the lanes of one load read consecutive pairs of fine nodes (a
+// coalesced span of the fine row) and the stores are coalesced too; padding nodes get 0.
 template <class V, int LK>
-__device__ __forceinline__ void restrict_tile(const LevelDev& f, const LevelDev& c, long long i0) {
+__device__ __forceinline__ void restrict_tile(const LevelDev& f, const LevelDev& c, long long t0,
+                                              int lane) {
   const int nc = c.n, nf = f.n, Nc = nc * nc;
   const V* r = static_cast<const V*>(f.r);
-  // coarse coordinates of the lane's first node, then step along the row (one wrap at most)
-  int J = (int)((unsigned)i0 / (unsigned)nc), I = (int)i0 - J * nc;
-  V out[4];
+  V* out = static_cast<V*>(c.rhs);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    out[j] = (int)i0 + j < Nc ? restrict_value<V>(I, J, nc, nf, c.bc, [&](long long k) { return ld1<LK>(r + k); })
-                              : V(0);
-    if (++I == nc) { I = 0; ++J; }
+    const int q = (int)t0 + lane + 32 * j;
+    V v = V(0);
+    if (q < Nc) {
+      const int J = (int)((unsigned)q / (unsigned)nc), I = q - J * nc;
+      v = restrict_value<V>(I, J, nc, nf, c.bc, [&](long long k) { return ld1<LK>(r + k); });
+    }
+    out[q] = v;
   }
-  st4(static_cast<V*>(c.rhs) + i0, out);
 }
 
 // x_f[x_sel] += P e_c at fine node (ix, iy): bilinear interpolation of the coarse iterate
@@ -489,14 +496,42 @@ __device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& 
   V v[4];
   if constexpr (LK == LD_NC) ld4c(x + i0, v);   // read and rewritten by this thread only
   else ld4<LK>(x + i0, v);                      // written earlier in this launch
-  // fine coordinates of the lane's first node, then step along the row (one wrap at most)
+  // fine coordinates of the lane's first node
   int iy = (int)((unsigned)i0 / (unsigned)nf), ix = (int)i0 - iy * nf;
+  if (ix + 3 < nf && (int)i0 + 3 < Nf) {
+    // the 4 nodes lie in one fine row: they interpolate from coarse columns cxa .. cxa + 2 (all on
+    // the grid, as ix + 3 <= nf - 1) of coarse row iy / 2 and, for an odd row, of the next one;
+    // each coarse value is loaded once and the arithmetic is prolong_value's, term for term
+    const int cxa = ix >> 1, cy0 = iy >> 1, odd = ix & 1;
+    const bool oy = iy & 1;
+    V e0[3], e1[3];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    V add;
-    if ((int)i0 + j < Nf && prolong_value<V>(ix, iy, nf, nc, f.bc, [&](int k) { return ld1<LK>(e + k); }, &add))
+    for (int k = 0; k < 3; ++k) {
+      e0[k] = ld1<LK>(e + cy0 * nc + cxa + k);
+      e1[k] = oy ? ld1<LK>(e + (cy0 + 1) * nc + cxa + k) : V(0);
+    }
+    auto pick = [](const V (&a)[3], int q) { return q == 0 ? a[0] : (q == 1 ? a[1] : a[2]); };
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (is_dirichlet(ix + j, iy, nf, f.bc)) continue;
+      const int c0 = (j + odd) >> 1, c1 = (j + 1 + odd) >> 1;   // columns of (ix + j) / 2, (ix + j + 1) / 2
+      const bool ox = (j + odd) & 1;
+      V add;
+      if (!ox && !oy) add = pick(e0, c0);
+      else if (ox && !oy) add = V(0.5) * (pick(e0, c0) + pick(e0, c1));
+      else if (!ox && oy) add = V(0.5) * (pick(e0, c0) + pick(e1, c0));
+      else add = V(0.25) * (((pick(e0, c0) + pick(e0, c1)) + pick(e1, c0)) + pick(e1, c1));
       v[j] = v[j] + add;
-    if (++ix == nf) { ix = 0; ++iy; }
+    }
+  } else {
+    // the nodes wrap into the next row (or reach the padding): node by node
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      V add;
+      if ((int)i0 + j < Nf && prolong_value<V>(ix, iy, nf, nc, f.bc, [&](int k) { return ld1<LK>(e + k); }, &add))
+        v[j] = v[j] + add;
+      if (++ix == nf) { ix = 0; ++iy; }
+    }
   }
   st4(x + i0, v);
 }
@@ -834,7 +869,7 @@ __global__ void __launch_bounds__(256) k_restrict(EngineDev E, TileList tl, int 
   if (tl.solo_tiles > 0) {                        // one problem: tl is the coarse level's list
     if (tl.solo_L < fine_level || E.S[0].phase != want) return;   // (no finer level: no descriptor)
     for (int t = gw; t < tl.solo_tiles; t += nw)
-      restrict_tile<V, LD_NC>(tl.solo_f, tl.solo_d, (long long)t * kTile + lane * kLaneNodes);
+      restrict_tile<V, LD_NC>(tl.solo_f, tl.solo_d, (long long)t * kTile, lane);
     return;
   }
   const int count = *tl.count;
@@ -843,8 +878,7 @@ __global__ void __launch_bounds__(256) k_restrict(EngineDev E, TileList tl, int 
     const int p = it.x;
     const ProblemDev& P = E.P[p];
     if (P.L < fine_level || E.S[p].phase != want) continue;
-    restrict_tile<V, LD_NC>(P.lev[fine_level], P.lev[fine_level - 1],
-                            (long long)it.y * kTile + lane * kLaneNodes);
+    restrict_tile<V, LD_NC>(P.lev[fine_level], P.lev[fine_level - 1], (long long)it.y * kTile, lane);
   }
 }
 
@@ -1414,7 +1448,7 @@ __device__ __forceinline__ bool vcycle_down_level(const LevelDev& d, const Level
   sync();
   const int ctiles = dc.pitch / kTile;
   for (int t = w0; t < ctiles; t += nw)
-    restrict_tile<typename Pol::V, LK>(d, dc, (long long)t * kTile + lane * kLaneNodes);
+    restrict_tile<typename Pol::V, LK>(d, dc, (long long)t * kTile, lane);
   sync();
   return true;
 }
