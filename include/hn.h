@@ -14,7 +14,7 @@
  *
  * Conventions shared by every call:
  *  - Every function returning hn_status returns HN_OK (0) on success and never exits or aborts,
- *    also not when device memory runs out (cf. Sec. 4.2, "exits cleanly").  hn_last_error()
+ *    also not when device memory runs out (Sec. 4.2 asks the same of an out-of-memory request).  hn_last_error()
  *    returns a message for the calling thread's last failure.
  *  - Explicit copy (Sec. 4.1): the library copies every input at call time and never keeps or
  *    aliases a caller pointer; outputs are written into caller buffers.  Handles are opaque and

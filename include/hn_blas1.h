@@ -2,8 +2,8 @@
  *
  * The paper measures the axpy kernel y = a x + y on every backend it supports and notes that the
  * other level-1 operations behave alike (Sec. 6.1, Fig. 2): they are purely memory bound, so
- * their rate is set by the off-chip bandwidth once the vectors are large enough to hide the
- * launch overhead.  These entry points are those operations on one GB300.
+ * their rate is set by the off-chip bandwidth once the vectors are long, and by the launch
+ * overhead below that.  These entry points are those operations on one GB300.
  *
  * Conventions:
  *  - x, y, result are DEVICE pointers (cudaMalloc or equivalent).  Vectors of n elements of the
