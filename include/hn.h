@@ -188,7 +188,8 @@ void hn_mg_destroy(hn_mg* mg);
  * Errors: HN_ERR_ARG, HN_ERR_STATE (op not available for that precision/level), HN_ERR_CUDA. */
 typedef enum {
   HN_OP_SPMV = 0, HN_OP_DEFECT = 1, HN_OP_JACOBI = 2, HN_OP_JACOBI_ZERO = 3,
-  HN_OP_RESTRICT = 4, HN_OP_PROLONG_ADD = 5, HN_OP_COARSE = 6
+  HN_OP_RESTRICT = 4, HN_OP_PROLONG_ADD = 5, HN_OP_COARSE = 6,
+  HN_OP_PROLONG_JACOBI = 7   /* prolongation fused into a Jacobi step: hn_mg_time_kernel only */
 } hn_op;
 hn_status hn_mg_apply(hn_mg* mg, hn_op op, int level, int inner, const void* in1,
                       const void* in2, void* out, double* norm_out);

@@ -14,8 +14,9 @@ extern "C" {
 #endif
 
 typedef struct {
-  char name[24];          /* kernel class: jacobi, jacobi_first, defect, restrict, prolong, coarse,
-                             check, outer_defect, update, control */
+  char name[24];          /* kernel class: jacobi, jacobi_first, defect, restrict, prolong,
+                             prolong_jacobi, coarse, check, outer_defect, update, control, tail,
+                             pcg_q, pcg_x, pcg_dot, pcg_p */
   int level;              /* refinement level the launches worked on (-1: per-problem finest) */
   long long launches;     /* launches timed */
   double total_ms;        /* summed event-to-event time */
@@ -30,9 +31,9 @@ hn_status hn_mg_set_profiling(hn_mg* mg, int enable);
 int hn_mg_kernel_times(const hn_mg* mg, hn_kernel_time* out, int max);
 
 /* Time one kernel of the solver on its own: `reps` back-to-back launches of op (HN_OP_SPMV,
- * HN_OP_DEFECT, HN_OP_JACOBI, HN_OP_RESTRICT or HN_OP_PROLONG_ADD) on `level` of mg's hierarchy (the inner hierarchy of a DC
- * hierarchy), on whatever the level's vectors hold, timed with CUDA events on mg's stream after
- * one warm-up launch.  *avg_ms receives the mean launch time, *bytes the algorithmic DRAM bytes of
+ * HN_OP_DEFECT, HN_OP_JACOBI, HN_OP_RESTRICT, HN_OP_PROLONG_ADD or HN_OP_PROLONG_JACOBI) on
+ * `level` of mg's hierarchy (the inner hierarchy of a DC hierarchy), on whatever the level's
+ * vectors hold, timed with CUDA events on mg's stream after one warm-up launch.  *avg_ms receives the mean launch time, *bytes the algorithmic DRAM bytes of
  * one launch (N_l x bytes per node of the kernel and precision). */
 hn_status hn_mg_time_kernel(hn_mg* mg, int op, int level, int reps, double* avg_ms, double* bytes);
 

@@ -27,6 +27,10 @@ typedef struct {
                        shared memory with bulk copies (TMA engine) on mbarriers; 0: register path */
   int dsm;          /* 1: the fused launch keeps its cluster levels in distributed shared memory
                        when they fit (else, and with 0, they run through L2) */
+  int fuse_up;      /* 1: on the levels above tail_level the prolongation runs inside the first
+                       post-smoothing step (one pass instead of two, each lane forming the
+                       prolonged values of its three stencil rows); 0: separate kernels (default:
+                       the fused pass measured slower, its extra work outweighing the pass saved) */
 } hn_tuning;
 
 /* Set / read the launch shape used by mg's later solves.  HN_ERR_ARG on values out of range. */

@@ -71,7 +71,8 @@ Tuning batch_tuning(const std::vector<hn_mg*>& list) {
   for (hn_mg* mg : list)
     same = same && mg->tuned && mg->tuning.tail_level == list[0]->tuning.tail_level &&
            mg->tuning.cluster == list[0]->tuning.cluster && mg->tuning.pdl == list[0]->tuning.pdl &&
-           mg->tuning.staged == list[0]->tuning.staged && mg->tuning.dsm == list[0]->tuning.dsm;
+           mg->tuning.staged == list[0]->tuning.staged && mg->tuning.dsm == list[0]->tuning.dsm &&
+           mg->tuning.fuse_up == list[0]->tuning.fuse_up;
   if (same) return list[0]->tuning;
   Tuning t;
   const int n = (int)list.size();
@@ -303,7 +304,7 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
     const Tuning t = batch_tuning(list);
     const Tuning& c = e.tuning();
     if (t.tail_level != c.tail_level || t.cluster != c.cluster || t.pdl != c.pdl || t.staged != c.staged ||
-        t.dsm != c.dsm)
+        t.dsm != c.dsm || t.fuse_up != c.fuse_up)
       e.set_tuning(t);
   }
   cudaStream_t s = e.stream();
@@ -429,12 +430,14 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
   if (t->pdl < 0 || t->pdl > 3) return set_error(HN_ERR_ARG, "pdl must be 0, 1, 2 or 3");
   if (t->staged != 0 && t->staged != 1) return set_error(HN_ERR_ARG, "staged must be 0 or 1");
   if (t->dsm != 0 && t->dsm != 1) return set_error(HN_ERR_ARG, "dsm must be 0 or 1");
+  if (t->fuse_up != 0 && t->fuse_up != 1) return set_error(HN_ERR_ARG, "fuse_up must be 0 or 1");
   Tuning tu;
   tu.tail_level = t->tail_level;
   tu.cluster = c;
   tu.pdl = t->pdl;
   tu.staged = t->staged;
   tu.dsm = t->dsm;
+  tu.fuse_up = t->fuse_up;
   mg->solo->set_tuning(tu);
   mg->tuning = tu;
   mg->tuned = true;
@@ -450,6 +453,7 @@ hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t) {
   t->pdl = tu.pdl;
   t->staged = tu.staged;
   t->dsm = tu.dsm;
+  t->fuse_up = tu.fuse_up;
   return HN_OK;
 }
 
@@ -464,7 +468,7 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
   struct Free { double* p; ~Free() { cudaFreeHost(p); } } fr{x};
   const int clusters[5] = {1, 2, 4, 8, 16};
   double best_ms = 1e300;
-  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 2, 0, 1};
+  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 2, 0, 1, 0};
   cudaEvent_t e0, e1;
   HN_CUDA(cudaEventCreate(&e0));
   HN_CUDA(cudaEventCreate(&e1));
@@ -472,7 +476,7 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
   const int tmax = std::min(mg->L, 9);
   for (int T = mg->coarse; T <= tmax; ++T)
     for (int ci = 0; ci < 5; ++ci) {
-      hn_tuning t{T, clusters[ci], 2, 0, 1};
+      hn_tuning t{T, clusters[ci], 2, 0, 1, 0};
       HN_TRY(hn_mg_set_tuning(mg, &t));
       HN_TRY(hn_mg_solve(mg, b, x, 0, 0, nullptr));            // capture + warm-up
       HN_CUDA(cudaEventRecord(e0, mg->solo->stream()));
@@ -506,10 +510,10 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
   int Lmax = 0;
   for (int j = 0; j < count; ++j) Lmax = std::max(Lmax, mgs[j]->L);
   double best_ms = 1e300;
-  hn_tuning bt{5, 1, 2, 0, 1};
+  hn_tuning bt{5, 1, 2, 0, 1, 0};
   for (int T = mgs[0]->coarse; T <= std::min(Lmax, 8); ++T)
     for (int ci = 0; ci < 3; ++ci) {
-      hn_tuning t{T, clusters[ci], 2, 0, 1};
+      hn_tuning t{T, clusters[ci], 2, 0, 1, 0};
       for (int j = 0; j < count; ++j) {
         Tuning tu; tu.tail_level = T; tu.cluster = clusters[ci]; tu.pdl = 2;
         mgs[j]->tuning = tu;
@@ -542,9 +546,9 @@ hn_status hn_mg_time_kernel(hn_mg* mg, int op, int level, int reps, double* avg_
   clear_error();
   if (!mg || !avg_ms || reps < 1) return set_error(HN_ERR_ARG, "bad arguments");
   if (op != HN_OP_SPMV && op != HN_OP_DEFECT && op != HN_OP_JACOBI && op != HN_OP_RESTRICT &&
-      op != HN_OP_PROLONG_ADD)
-    return set_error(HN_ERR_ARG, "op must be SPMV, DEFECT, JACOBI, RESTRICT or PROLONG_ADD");
-  if (level <= mg->coarse && (op == HN_OP_RESTRICT || op == HN_OP_PROLONG_ADD))
+      op != HN_OP_PROLONG_ADD && op != HN_OP_PROLONG_JACOBI)
+    return set_error(HN_ERR_ARG, "op must be SPMV, DEFECT, JACOBI, RESTRICT, PROLONG_ADD or PROLONG_JACOBI");
+  if (level <= mg->coarse && (op == HN_OP_RESTRICT || op == HN_OP_PROLONG_ADD || op == HN_OP_PROLONG_JACOBI))
     return set_error(HN_ERR_ARG, "transfers need a coarser level");
   if (level < mg->coarse || level > mg->L) return set_error(HN_ERR_ARG, "level out of range");
   HN_TRY(ensure_solo(mg));
@@ -572,6 +576,7 @@ hn_status hn_mg_time_kernel(hn_mg* mg, int op, int level, int reps, double* avg_
                      : op == HN_OP_DEFECT ? 9 * bb + 3 * vb
                      : op == HN_OP_RESTRICT ? 1.25 * vb
                      : op == HN_OP_PROLONG_ADD ? 2.25 * vb
+                     : op == HN_OP_PROLONG_JACOBI ? 9 * bb + 3.25 * vb + (prec == P64 ? 8 : 0)
                      : 9 * bb + 3 * vb + (prec == P64 ? 8 : 0);
     *bytes = per * (double)N_of(level);
   }

@@ -576,6 +576,7 @@ long long Engine::launch_bytes(int cls, int level) const {
     case KC_CHECK: per = 9 * bb + 2 * vb; break;
     case KC_RESTRICT: per = 1.25 * vb; break;                   // per fine node
     case KC_PROLONG: per = 2.25 * vb; break;                    // per fine node
+    case KC_PROLONG_JACOBI: per = 9 * bb + 3.25 * vb + wd; break; // Jacobi + coarse reads
     case KC_OUTER_DEFECT: per = 72 + 8 + 8 + vb; break;
     case KC_UPDATE: per = 4 + 8 + 8; break;
     case KC_PCG_Q: per = 72 + 8 + 8; break;                    // bands, p; write q
@@ -701,8 +702,15 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
   }
   HN_LAUNCH(KC_TAIL, T, launch_tail(E_, T, want, tune_.cluster, s));
   for (int l = T + 1; l <= Lmax_; ++l) {
-    HN_LAUNCH(KC_PROLONG, l, launch_prolong(E_, lists_[l], l, want, pre & 1, grid_[l], s));
-    for (int sw = 1; sw <= post; ++sw)
+    int sw = 1;
+    if (tune_.fuse_up && post >= 1) {
+      // prolongation and the first post-smoothing step in one pass
+      HN_LAUNCH(KC_PROLONG_JACOBI, l, launch_prolong_jacobi(E_, lists_[l], l, want, pre & 1, grid_[l], s));
+      sw = 2;
+    } else {
+      HN_LAUNCH(KC_PROLONG, l, launch_prolong(E_, lists_[l], l, want, pre & 1, grid_[l], s));
+    }
+    for (; sw <= post; ++sw)
       HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (pre + sw - 1) & 1, 0, grid_[l], s));
   }
   if (opened) {
@@ -993,7 +1001,8 @@ void Engine::set_profiling(bool on) {
 int Engine::kernel_times(hn_kernel_time* out, int max) const {
   static const char* names[KC_COUNT] = {"jacobi", "jacobi_first", "defect", "restrict", "prolong",
                                         "coarse", "check", "outer_defect", "update", "control",
-                                        "tail", "pcg_q", "pcg_x", "pcg_dot", "pcg_p"};
+                                        "tail", "pcg_q", "pcg_x", "pcg_dot", "pcg_p",
+                                        "prolong_jacobi"};
   int n = 0;
   for (int c = 0; c < KC_COUNT; ++c)
     for (int l = 0; l <= kMaxLevel; ++l) {
@@ -1004,7 +1013,7 @@ int Engine::kernel_times(hn_kernel_time* out, int max) const {
         std::memset(&t, 0, sizeof t);
         std::snprintf(t.name, sizeof t.name, "%s", names[c]);
         t.level = (c == KC_CHECK || c == KC_OUTER_DEFECT || c == KC_UPDATE || c == KC_CONTROL ||
-                   c >= KC_PCG_Q) ? -1 : l;
+                   (c >= KC_PCG_Q && c <= KC_PCG_P)) ? -1 : l;
         t.launches = a.launches;
         t.total_ms = a.ms;
         t.bytes_per_launch = (double)a.bytes;
@@ -1043,6 +1052,9 @@ hn_status Engine::apply(int op, int level, int want, cudaStream_t s) {
       HN_CUDA(launch_restrict(E_, lists_[level - 1], level, want, grid_[level - 1], s));
       break;
     case HN_OP_PROLONG_ADD: HN_CUDA(launch_prolong(E_, lists_[level], level, want, 0, grid_[level], s)); break;
+    case HN_OP_PROLONG_JACOBI:
+      HN_CUDA(launch_prolong_jacobi(E_, lists_[level], level, want, 0, grid_[level], s));
+      break;
     case HN_OP_COARSE: HN_CUDA(launch_coarse(E_, lists_[level], want, grid_[level], s)); break;
     default: return set_error(HN_ERR_ARG, "unknown op %d", op);
   }

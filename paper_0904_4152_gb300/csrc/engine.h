@@ -57,7 +57,7 @@ size_t hierarchy_bytes(int L, int coarse, int prec, int solver);
 enum KClass {
   KC_JACOBI = 0, KC_JACOBI_FIRST, KC_DEFECT, KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_CHECK,
   KC_OUTER_DEFECT, KC_UPDATE, KC_CONTROL, KC_TAIL, KC_PCG_Q, KC_PCG_X, KC_PCG_DOT, KC_PCG_P,
-  KC_COUNT
+  KC_PROLONG_JACOBI, KC_COUNT
 };
 
 // launch shape of the schedule: levels <= tail_level run fused in one cluster launch of
@@ -69,6 +69,8 @@ struct Tuning {
   int staged = 0;   // stream the bands of large FP32/FP16 levels through shared memory by bulk
                     // copies (measured slower than the register path at L=12; off)
   int dsm = 1;      // fused tail: cluster levels in distributed shared memory when they fit
+  int fuse_up = 0;  // levels above the tail: prolongation inside the first post-smoothing step
+                    // (measured slower than the two kernels: 192 vs 157 us at L=12 FP32; off)
 };
 
 class Engine;

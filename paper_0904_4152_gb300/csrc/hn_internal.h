@@ -225,6 +225,9 @@ cudaError_t launch_restrict(const EngineDev& E, TileList tl_coarse, int fine_lev
                             int grid, cudaStream_t s);
 cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want, int x_sel,
                            int grid, cudaStream_t s);
+// the prolongation into x[x_sel] fused into the first post-smoothing step (result in x[1 - x_sel])
+cudaError_t launch_prolong_jacobi(const EngineDev& E, TileList tl, int level, int want, int x_sel,
+                                  int grid, cudaStream_t s);
 cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, cudaStream_t s);
 cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
 // PCG vector steps on each problem's finest level (FP64): q = A p with partials (p, q); x += alpha

@@ -285,7 +285,8 @@ __device__ void pre_check(ProbState& st, const Params& prm, double nrm) {
 // skips the tile; otherwise PRE12 does step 1 (buffer 0 -> 1) and PRE2B step 2 (1 -> 0).
 enum BandMode {
   M_SPMV = 0, M_DEFECT = 1, M_JACOBI = 2, M_JACOBI_FIRST = 3, M_CHECK = 4, M_PRE12 = 5,
-  M_PRE2B = 6
+  M_PRE2B = 6,
+  M_PJ = 7        // prolongation x += P e_c fused into the first post-smoothing step
 };
 
 template <class Pol> __device__ __forceinline__ constexpr bool fuses_pre() { return true; }
@@ -536,6 +537,123 @@ __device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& 
   st4(x + i0, v);
 }
 
+// P e_c at fine node q = (qx, qy) if q is a grid node (0 <= q < Nf), else 0 (halo, padding, or a
+// Dirichlet node); the same value prolong_value adds
+template <class V, int LK>
+__device__ __forceinline__ V prolong_at(const V* e, long long q, int qx, int qy, int nf, int nc,
+                                        int bc, long long Nf) {
+  V add = V(0);
+  if (q >= 0 && q < Nf && !prolong_value<V>(qx, qy, nf, nc, bc, [&](int k) { return ld1<LK>(e + k); }, &add))
+    add = V(0);
+  return add;
+}
+
+// (qx, qy) of flat index a + o from (ax, ay) of a, |o| < nf: one wrap at most
+__device__ __forceinline__ void step_xy(int ax, int ay, int o, int nf, int& qx, int& qy) {
+  qx = ax + o;
+  qy = ay;
+  if (qx < 0) { qx += nf; --qy; }
+  else if (qx >= nf) { qx -= nf; ++qy; }
+}
+
+// Row window of y = x + P e_c around the lane's 4 nodes: w[o + 2] = y at a + o, o = -2..5 (a =
+// the flat index of the lane's first node in this row, (ax, ay) its coordinates, possibly off the
+// grid).  Each y is formed exactly as the prolongation kernel forms it (x + add), so the step that
+// follows sees the same values it would read after a separate prolongation.
+template <class V, int LK>
+__device__ __forceinline__ void load_row_prolonged(const V* x, const V* e, long long a, int ax, int ay,
+                                                   int nf, int nc, int bc, long long Nf, int lane,
+                                                   V (&w)[8]) {
+  V c[4];
+  ld4<LK>(x + a, c);
+  if (a >= 0 && a + 3 < Nf && ax + 3 < nf && ay >= 0) {
+    // one fine row: coarse columns cxa .. cxa + 2 of coarse row ay / 2 (and the next one)
+    const int cxa = ax >> 1, cy0 = ay >> 1, odd = ax & 1;
+    const bool oy = ay & 1;
+    V e0[3], e1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      e0[k] = ld1<LK>(e + cy0 * nc + cxa + k);
+      e1[k] = oy ? ld1<LK>(e + (cy0 + 1) * nc + cxa + k) : V(0);
+    }
+    auto pick = [](const V (&q)[3], int i) { return i == 0 ? q[0] : (i == 1 ? q[1] : q[2]); };
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (is_dirichlet(ax + j, ay, nf, bc)) continue;
+      const int c0 = (j + odd) >> 1, c1 = (j + 1 + odd) >> 1;
+      const bool ox = (j + odd) & 1;
+      V add;
+      if (!ox && !oy) add = pick(e0, c0);
+      else if (ox && !oy) add = V(0.5) * (pick(e0, c0) + pick(e0, c1));
+      else if (!ox && oy) add = V(0.5) * (pick(e0, c0) + pick(e1, c0));
+      else add = V(0.25) * (((pick(e0, c0) + pick(e0, c1)) + pick(e1, c0)) + pick(e1, c1));
+      c[j] = c[j] + add;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int qx, qy;
+      step_xy(ax, ay, j, nf, qx, qy);
+      if (a + j >= 0 && a + j < Nf) {
+        V add;
+        if (prolong_value<V>(qx, qy, nf, nc, bc, [&](int k) { return ld1<LK>(e + k); }, &add)) c[j] = c[j] + add;
+      }
+    }
+  }
+  V l2 = __shfl_up_sync(kFull, c[2], 1), l1 = __shfl_up_sync(kFull, c[3], 1);
+  V r0 = __shfl_down_sync(kFull, c[0], 1), r1 = __shfl_down_sync(kFull, c[1], 1);
+  if (lane == 0) {
+    int qx, qy;
+    step_xy(ax, ay, -2, nf, qx, qy);
+    l2 = ld1<LK>(x + a - 2) + prolong_at<V, LK>(e, a - 2, qx, qy, nf, nc, bc, Nf);
+    step_xy(ax, ay, -1, nf, qx, qy);
+    l1 = ld1<LK>(x + a - 1) + prolong_at<V, LK>(e, a - 1, qx, qy, nf, nc, bc, Nf);
+  }
+  if (lane == 31) {
+    int qx, qy;
+    step_xy(ax, ay, 4, nf, qx, qy);
+    r0 = ld1<LK>(x + a + 4) + prolong_at<V, LK>(e, a + 4, qx, qy, nf, nc, bc, Nf);
+    step_xy(ax, ay, 5, nf, qx, qy);
+    r1 = ld1<LK>(x + a + 5) + prolong_at<V, LK>(e, a + 5, qx, qy, nf, nc, bc, Nf);
+  }
+  w[0] = l2; w[1] = l1; w[2] = c[0]; w[3] = c[1]; w[4] = c[2]; w[5] = c[3]; w[6] = r0; w[7] = r1;
+}
+
+// The prolongation x_f[in_sel] += P e_c and the first post-smoothing Jacobi step in one pass:
+// the step's windows are formed from x and e_c on the fly, the corrected iterate is not stored
+// (the second step overwrites it), the step's result goes to buffer 1 - in_sel.  Identical values
+// to the separate prolongation and Jacobi kernels.
+template <class Pol, int LK>
+__device__ __forceinline__ void prolong_jacobi_tile(const LevelDev& d, const LevelDev& c, long long shift,
+                                                    long long i0, int lane, int in_sel,
+                                                    typename Pol::A omega) {
+  using A = typename Pol::A;
+  using V = typename Pol::V;
+  const int nf = d.n, nc = c.n;
+  const long long Nf = (long long)nf * nf;
+  const V* x = static_cast<const V*>(d.x[in_sel]);
+  const V* e = static_cast<const V*>(c.x[0]);
+  const int iy0 = (int)((unsigned long long)i0 / (unsigned)nf), ix0 = (int)(i0 - (long long)iy0 * nf);
+  V w[3][8];
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+    int ax = ix0 - dy, ay = iy0 + dy;                 // i0 + dy * shift, shift = nf - 1
+    if (ax < 0) { ax += nf; --ay; } else if (ax >= nf) { ax -= nf; ++ay; }
+    load_row_prolonged<V, LK>(x, e, i0 + dy * shift, ax, ay, nf, nc, d.bc, Nf, lane, w[dy + 1]);
+  }
+  A acc[4], dg[4];
+  if constexpr (Pol::prec == P16) stencil_windows_rowsum<band_kind<LK>()>(d.band, d.scale, w, i0, acc, dg);
+  else stencil_windows<Pol, band_kind<LK>()>(d.band, nullptr, w, i0, acc, dg);
+  V b[4];
+  ld4<LK>(static_cast<const V*>(d.rhs) + i0, b);
+  A wd[4];
+  wd4_of<Pol, band_kind<LK>()>(d, i0, omega, dg, wd);
+  V out[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) out[j] = fma(wd[j], A(b[j]) - acc[j], A(w[1][j + 2]));
+  st4(static_cast<V*>(d.x[1 - in_sel]) + i0, out);
+}
+
 // One row of the coarse inverse times the coarse right-hand side: four interleaved FP64 chains
 // (v mod 4), then (a0 + a1) + (a2 + a3); a dependent FP64 operation costs ~64 cycles on this part,
 // so one chain of m would dominate the coarse solve.  rd(v) gives the v-th interior rhs in FP64.
@@ -711,6 +829,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 template <class Pol, int MODE> constexpr int band_min_blocks() {
   if (MODE == M_CHECK) return Pol::prec == P64 ? 2 : 3;
   if (MODE == M_PRE12) return Pol::prec == P64 ? 2 : 4;
+  if (MODE == M_PJ) return Pol::prec == P64 ? 2 : (Pol::prec == P32 ? 4 : 3);
   if (Pol::prec == P32) return 5;
   if (Pol::prec == P16) return (MODE == M_SPMV || MODE == M_DEFECT) ? 5 : 4;
   return 4;
@@ -729,6 +848,13 @@ __global__ void __launch_bounds__(256, band_min_blocks<Pol, MODE>()) k_band(Engi
   if (tl.solo_tiles > 0 && level >= 0) {          // one problem: descriptors by value
     const ProbState& st = E.S[0];
     if (st.phase != want) return;
+    if constexpr (MODE == M_PJ) {
+      if (tl.solo_c.n == 0) return;               // (no coarser level: nothing to prolong)
+      for (int t = gw; t < tl.solo_tiles; t += nw)
+        prolong_jacobi_tile<Pol, LD_NC>(tl.solo_d, tl.solo_c, 1LL << level, (long long)t * kTile + lane * kLaneNodes,
+                                        lane, in_sel, omega);
+      return;
+    }
     const bool zg = (tl.solo_L > level) || st.zero_top;
     for (int t = gw; t < tl.solo_tiles; t += nw) {
       double* slot = nullptr;
@@ -748,6 +874,11 @@ __global__ void __launch_bounds__(256, band_min_blocks<Pol, MODE>()) k_band(Engi
     if (st.phase != want) continue;
     const ProblemDev& P = E.P[p];
     const int lv = level < 0 ? P.L : level;
+    if constexpr (MODE == M_PJ) {
+      prolong_jacobi_tile<Pol, LD_NC>(P.lev[lv], P.lev[lv - 1], 1LL << lv, (long long)it.y * kTile + lane * kLaneNodes,
+                                      lane, in_sel, omega);
+      continue;
+    }
     const bool zg = (P.L > lv) || st.zero_top;
     double* slot = nullptr;
     if constexpr (MODE == M_CHECK) slot = E.partial + E.fine_off[p] + it.y;
@@ -2188,6 +2319,7 @@ cudaError_t launch_band_t(int mode, const EngineDev& E, TileList tl, int level, 
     case M_CHECK: return launch_k(k_band<Pol, M_CHECK>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
     case M_PRE12: return launch_k(k_band<Pol, M_PRE12>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
     case M_PRE2B: return launch_k(k_band<Pol, M_PRE2B>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
+    case M_PJ: return launch_k(k_band<Pol, M_PJ>, grid, 0, s, E.pdl, 0, E, tl, level, want, in_sel);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -2216,6 +2348,10 @@ cudaError_t launch_pre12(const EngineDev& E, TileList tl, int level, int want, i
 cudaError_t launch_pre2b(const EngineDev& E, TileList tl, int level, int want, int grid,
                          cudaStream_t s) {
   return launch_band(M_PRE2B, E, tl, level, want, 0, grid, s);
+}
+cudaError_t launch_prolong_jacobi(const EngineDev& E, TileList tl, int level, int want, int x_sel,
+                                  int grid, cudaStream_t s) {
+  return launch_band(M_PJ, E, tl, level, want, x_sel, grid, s);
 }
 bool pre_fuses(int) { return true; }
 

@@ -17,7 +17,7 @@ HN_OK, HN_ERR_ARG, HN_ERR_OOM, HN_ERR_BUDGET, HN_ERR_CUDA = 0, 1, 2, 3, 4
 HN_ERR_NOT_CONVERGED, HN_ERR_NONFINITE, HN_PENDING, HN_ERR_TIMEOUT, HN_ERR_STATE = 5, 6, 7, 8, 9
 HN_PREC_FP64, HN_PREC_FP32_DC, HN_PREC_FP16BAND_DC = 0, 1, 2
 HN_OP_SPMV, HN_OP_DEFECT, HN_OP_JACOBI, HN_OP_JACOBI_ZERO = 0, 1, 2, 3
-HN_OP_RESTRICT, HN_OP_PROLONG_ADD, HN_OP_COARSE = 4, 5, 6
+HN_OP_RESTRICT, HN_OP_PROLONG_ADD, HN_OP_COARSE, HN_OP_PROLONG_JACOBI = 4, 5, 6, 7
 HN_MIN_LEVEL, HN_MAX_LEVEL = 2, 14
 # Dirichlet sides (the others are free Neumann): bottom y = 0, right x = 1, top y = 1, left x = 0
 HN_DIRICHLET_BOTTOM, HN_DIRICHLET_RIGHT, HN_DIRICHLET_TOP, HN_DIRICHLET_LEFT = 1, 2, 4, 8
@@ -76,7 +76,7 @@ class ServerInfo(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tail_level", ctypes.c_int), ("cluster", ctypes.c_int), ("pdl", ctypes.c_int),
-                ("staged", ctypes.c_int), ("dsm", ctypes.c_int)]
+                ("staged", ctypes.c_int), ("dsm", ctypes.c_int), ("fuse_up", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -350,14 +350,14 @@ def hn_mg_kernel_times(mg, max_entries=256):
             for i in range(n)]
 
 
-def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0, dsm=1):
-    _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl, staged, dsm))))
+def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0, dsm=1, fuse_up=0):
+    _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl, staged, dsm, fuse_up))))
 
 
 def hn_mg_get_tuning(mg):
     t = Tuning()
     _check(lib().hn_mg_get_tuning(mg, ctypes.byref(t)))
-    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm
+    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm, t.fuse_up
 
 
 def hn_mg_autotune(mg, b, reps=3, coarse_L=2):

@@ -277,8 +277,9 @@ def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L):
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_launch_shapes_do_not_change_results(hn, prec):
-    # the tail level, cluster size, programmatic dependent launch, bulk-copy staging and the
-    # distributed shared-memory cluster levels only change where work runs
+    # the tail level, cluster size, programmatic dependent launch, bulk-copy staging, the
+    # distributed shared-memory cluster levels and the prolongation fused into the first
+    # post-smoothing step only change where work runs
     L = 10                 # levels 9 and 10 are large enough for the bulk-copy kernels
     coef, b = I.batch_problem(3, L)
     A = hn.hn_band_create(L, coef)
@@ -286,8 +287,9 @@ def test_launch_shapes_do_not_change_results(hn, prec):
     hn.hn_band_destroy(A)
     try:
         ref, st0, _ = hn.hn_mg_solve(mg, L, b)
-        for shape in [(2, 1, 0, 0, 1), (4, 2, 0, 1, 1), (5, 16, 1, 0, 0), (7, 8, 2, 1, 1),
-                      (7, 16, 2, 0, 0), (7, 16, 2, 0, 1), (6, 4, 2, 0, 1), (8, 16, 1, 1, 1)]:
+        for shape in [(2, 1, 0, 0, 1, 1), (4, 2, 0, 1, 1, 0), (5, 16, 1, 0, 0, 1), (7, 8, 2, 1, 1, 1),
+                      (7, 16, 2, 0, 0, 0), (7, 16, 2, 0, 1, 0), (6, 4, 2, 0, 1, 1), (8, 16, 1, 1, 1, 0),
+                      (7, 16, 2, 0, 1, 1)]:
             hn.hn_mg_set_tuning(mg, *shape)
             assert hn.hn_mg_get_tuning(mg) == shape
             x, st, _ = hn.hn_mg_solve(mg, L, b)
