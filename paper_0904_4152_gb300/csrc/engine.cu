@@ -530,6 +530,7 @@ hn_status Engine::start(const std::vector<int>& slots, const std::vector<int>& h
     st.zero_top = g ? 0 : 1;
     st.x_zero = g ? 0 : 1;
     st.s = 1.0;
+    st.inv_s = 1.0;
     HN_CUDA(cudaMemcpyAsync(dS_ + slots[q], &st, sizeof st, cudaMemcpyHostToDevice, s_));
   }
   // the iteration counter restarts with every closed-world solve (serving keeps counting and
@@ -551,6 +552,7 @@ hn_status Engine::set_phase(int slot, int phase, int zero_top) {
   st.zero_top = zero_top;
   st.x_zero = zero_top;
   st.s = 1.0;
+  st.inv_s = 1.0;
   HN_CUDA(cudaMemcpyAsync(dS_ + slot, &st, sizeof st, cudaMemcpyHostToDevice, s_));
   return HN_OK;
 }

@@ -112,6 +112,8 @@ struct ProbState {
   double dnorm;          // ||b - A x|| at the last outer defect / FP64 check
   double relres;         // dnorm / bnorm
   double s;              // scale applied to the defect before the cast to the inner precision
+  double inv_s;          // 1 / s, formed once when s changes (an FP64 division per thread of a
+                         // streaming kernel would cost more than the kernel's memory traffic)
   double inner_ref;      // ||scaled defect|| (reference of the inner relative residual)
   double inner_res;      // last inner residual norm
   double rho;            // PCG: (r, z) of the current direction

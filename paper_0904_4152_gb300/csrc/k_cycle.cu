@@ -232,6 +232,20 @@ __device__ double problem_partial_sum(const double* part, int ntiles, double* sh
   double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
   if (threadIdx.x < 256) {                    // larger blocks: the other threads add +0.0
     int q = threadIdx.x;
+    // batches of 8 rounds: the 32 loads of a batch are issued before its adds (the adds keep
+    // the order above), so L2 latency is paid once per batch rather than once per round
+    for (; q + 31 * 256 < ntiles; q += 32 * 256) {
+      double v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = __ldcg(part + q + k * 256);
+#pragma unroll
+      for (int k = 0; k < 32; k += 4) {
+        c0 += v[k];
+        c1 += v[k + 1];
+        c2 += v[k + 2];
+        c3 += v[k + 3];
+      }
+    }
     for (; q + 3 * 256 < ntiles; q += 4 * 256) {
       c0 += __ldcg(part + q);
       c1 += __ldcg(part + q + 256);
@@ -1981,7 +1995,7 @@ __global__ void __launch_bounds__(256) k_pcg_p(EngineDev E, TileList tl) {
     double pv[4];
     ld4<LD_NC>(static_cast<const V*>(P.lev[P.L].x[0]) + i0, c);
     ld4c(P.p64 + i0, pv);
-    const double beta = st.beta, inv_s = 1.0 / st.s;
+    const double beta = st.beta, inv_s = st.inv_s;
 #pragma unroll
     for (int j = 0; j < 4; ++j) pv[j] = fma(beta, pv[j], double(c[j]) * inv_s);
     st4(P.p64 + i0, pv);
@@ -2006,7 +2020,7 @@ __global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl) {
     ld4<LD_NC>(static_cast<const float*>(P.lev[P.L].x[0]) + i0, c);
     double x[4];
     ld4c(P.x64 + i0, x);
-    const double inv_s = 1.0 / st.s;
+    const double inv_s = st.inv_s;
 #pragma unroll
     for (int j = 0; j < 4; ++j) x[j] = fma(double(c[j]), inv_s, x[j]);
     st4(P.x64 + i0, x);
@@ -2103,6 +2117,7 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
       if (nrm == 0.0) { st.bnorm = 0.0; st.relres = 0.0; st.status = HN_OK; st.phase = PH_DONE; break; }
       st.bnorm = nrm;
       st.s = 1.0 / nrm;
+      st.inv_s = 1.0 / st.s;
       st.relres = 1.0;
       if (prm.prec == P64 && prm.solver != SOLVER_PCG) {
         // a zero initial guess starts its first cycle unchecked (relres 1); a given guess is
@@ -2177,7 +2192,7 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
     case CTRL_POST: {
       if (prm.solver == SOLVER_PCG) {
         // the next cycle's right-hand side is scaled by 1 / ||r|| of this step
-        if (st.dnorm > 0.0 && isfinite(st.dnorm)) st.s = 1.0 / st.dnorm;
+        if (st.dnorm > 0.0 && isfinite(st.dnorm)) { st.s = 1.0 / st.dnorm; st.inv_s = 1.0 / st.s; }
         st.phase = PH_OUTER;
         break;
       }
@@ -2186,7 +2201,7 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
       // scale for the next defect: the inner solve reduced the defect by about inner_res/inner_ref
       const double red = st.inner_ref > 0.0 ? st.inner_res / st.inner_ref : 1.0;
       const double pred = st.dnorm * fmax(red, 1e-7);
-      if (pred > 0.0 && isfinite(pred)) st.s = 1.0 / pred;
+      if (pred > 0.0 && isfinite(pred)) { st.s = 1.0 / pred; st.inv_s = 1.0 / st.s; }
       st.phase = PH_OUTER;
       break;
     }
