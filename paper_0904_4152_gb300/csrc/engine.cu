@@ -398,6 +398,10 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   take(sizeof(unsigned));
   take(sizeof(unsigned) * 4);
   take(sizeof(unsigned long long));
+  // the control kernel's groups: as many as the largest problem's norm sum has
+  const int ctl_groups = (int)((pitch_of(Lmax) / kTile + kSumGroup - 1) / kSumGroup);
+  take(sizeof(double) * (size_t)cap * ctl_groups);
+  take(sizeof(unsigned) * (size_t)cap);
   bytes += 256;
   HN_CUDA(cudaMalloc(&mem_, bytes));
   HN_CUDA(cudaMemsetAsync(mem_, 0, bytes, s_));
@@ -418,6 +422,8 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   unsigned* iter = b.take<unsigned>(1);
   dTaken_ = b.take<unsigned>(4);
   dLaunches_ = b.take<unsigned long long>(1);
+  double* gsum = b.take<double>((size_t)cap * ctl_groups);
+  unsigned* gticket = b.take<unsigned>((size_t)cap);
   HN_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&hActive_), sizeof(unsigned), cudaHostAllocMapped));
   *hActive_ = 0;
   unsigned* dActive = nullptr;
@@ -435,6 +441,9 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   E_.err = dErr_;
   E_.staged = tune_.staged;
   E_.dsm = tune_.dsm;
+  E_.ctl_groups = ctl_groups;
+  E_.gsum = gsum;
+  E_.gticket = gticket;
   E_.iter_limit = (unsigned)(prm.max_cycles + prm.max_outer + 8);
   for (int l = 0; l <= kMaxLevel; ++l) {
     lists_[l] = TileList{dItems_[l], dCounts_ + l, dChunks_[l], dChunkCounts_ + l, (int)chunkCap_[l]};

@@ -18,6 +18,7 @@ constexpr int kLaneNodes = 4;
 constexpr int kMaxLevel = HN_MAX_LEVEL;
 constexpr int kMaxCoarse = 4;                       // coarse_L <= 4: at most 225 interior unknowns
 constexpr int kMaxCoarseM = 289;   // unknowns of the coarsest level (17 x 17 at level 4)
+constexpr int kSumGroup = 16384;   // tiles per group of a problem's norm partial sum
 
 __host__ __device__ inline long long n_of_dev(int L) { return (1LL << L) + 1; }
 inline long long n_of(int L) { return (1LL << L) + 1; }
@@ -198,6 +199,10 @@ struct EngineDev {
   int staged;                  // host-side flag: large FP32/FP16 levels use the bulk-copy kernels
   int dsm;                     // host-side flag: the fused tail keeps its cluster levels in
                                // distributed shared memory when they fit
+  int ctl_groups;              // blocks per problem of the control kernel (groups of the largest
+                               // problem's norm partial sum)
+  double* gsum;                // [nprob * ctl_groups] group sums of the control kernel
+  unsigned* gticket;           // [nprob] blocks of a problem's control launch that finished
 };
 
 // Launch wrappers for one step of the schedule; grid = CTAs of 256 threads.  level < 0 means

@@ -40,6 +40,11 @@ __device__ __forceinline__ void pdl_start() {
   pdl_wait();
 }
 
+// An engine of one problem skips a whole fine-level launch when its problem is not in the phase
+// the kernel serves (otherwise every warp would walk its share of the work list to find that out:
+// ~20 us per empty launch at L = 12)
+__device__ __forceinline__ bool solo_idle(const EngineDev& E, int phase);
+
 // -------------------------------------------------------------------- precision policies
 struct F64 { using B = double; using V = double; using A = double; static constexpr int prec = P64; };
 struct F32 { using B = float; using V = float; using A = float; static constexpr int prec = P32; };
@@ -259,6 +264,29 @@ __device__ double problem_partial_sum(const double* part, int ntiles, double* sh
   return block_sum256((c0 + c1) + (c2 + c3), sh);
 }
 
+// A problem's tiles are summed in groups of kSumGroup consecutive tiles when it has more than one
+// group: each group by problem_partial_sum, then the group sums in group order.  (One block adding
+// 131,072 FP64 partials at L = 12 is bound by one SM's FP64 rate, ~30 us; the control kernel
+// gives each group its own block.)  Every path that forms a problem's norm uses this order.
+__device__ __forceinline__ int sum_groups(int ntiles) { return (ntiles + kSumGroup - 1) / kSumGroup; }
+
+__device__ double group_partial_sum(const double* part, int ntiles, int j, double* sh) {
+  const int lo = j * kSumGroup;
+  return problem_partial_sum(part + lo, min(kSumGroup, ntiles - lo), sh);
+}
+
+// the same order in one block (valid in thread 0)
+__device__ double problem_norm_sum(const double* part, int ntiles, double* sh) {
+  const int ng = sum_groups(ntiles);
+  if (ng == 1) return problem_partial_sum(part, ntiles, sh);
+  double t = 0.0;
+  for (int j = 0; j < ng; ++j) {
+    const double g = group_partial_sum(part, ntiles, j, sh);
+    if (threadIdx.x == 0) t += g;
+  }
+  return t;
+}
+
 __host__ __device__ inline int fine_tiles(int L) {
   const long long n = (1LL << L) + 1;
   return (int)((n * n + kTile - 1) / kTile);
@@ -291,6 +319,10 @@ __device__ void pre_check(ProbState& st, const Params& prm, double nrm) {
       cond_set(prm.cond, 2, 1u);
     } else { st.inner_k += 1; st.inner_cycles += 1; st.cycles += 1; }
   }
+}
+
+__device__ __forceinline__ bool solo_idle(const EngineDev& E, int phase) {
+  return E.nprob == 1 && E.S[0].phase != phase;
 }
 
 // Modes of the band kernel.  PRE12 / PRE2B split the first two smoothing steps: from a zero
@@ -880,6 +912,7 @@ __global__ void __launch_bounds__(256, band_min_blocks<Pol, MODE>()) k_band(Engi
     }
     return;
   }
+  if (solo_idle(E, want)) return;
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
@@ -1317,7 +1350,7 @@ __device__ bool vcycle_down_smem(const LevelDev& d, const LevelDev& dc, int l, b
                                                lane, 0, omega, check_part + t);
     }
     __syncthreads();
-    const double sum = problem_partial_sum(check_part, fine_tiles(l), sh);
+    const double sum = problem_norm_sum(check_part, fine_tiles(l), sh);
     if (tid == 0) pre_check(*st, prm, sqrt(sum));
     __syncthreads();
     if (__ldcg(&st->phase) != want) return false;
@@ -1570,7 +1603,7 @@ __device__ __forceinline__ bool vcycle_down_level(const LevelDev& d, const Level
   sync();
   if (check_part) {
     if (rank == 0) {
-      const double sum = problem_partial_sum(check_part, fine_tiles(l), sh);
+      const double sum = problem_norm_sum(check_part, fine_tiles(l), sh);
       if (threadIdx.x == 0) pre_check(*st, prm, sqrt(sum));
     }
     sync();
@@ -1774,7 +1807,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
         band_tile<Pol, M_CHECK, LD_GEN>(d, 1LL << c, false, (long long)t * kTile + lane * kLaneNodes, lane, 0,
                                         omega, check_part + t);
       __syncthreads();
-      const double sum = problem_partial_sum(check_part, fine_tiles(c), sh);
+      const double sum = problem_norm_sum(check_part, fine_tiles(c), sh);
       if (threadIdx.x == 0) pre_check(*stw, E.prm, sqrt(sum));
       __syncthreads();
       go = __ldcg(&stw->phase) == want;
@@ -1843,6 +1876,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
 template <class V>
 __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) {
   pdl_start();
+  if (solo_idle(E, PH_OUTER)) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -1892,6 +1926,7 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
 // q = A p (FP64 bands, p with zero halos), partial[g] = sum p q, for problems in their CG step
 __global__ void __launch_bounds__(256) k_pcg_q(EngineDev E, TileList tl) {
   pdl_start();
+  if (solo_idle(E, PH_OUTER)) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -1919,6 +1954,7 @@ __global__ void __launch_bounds__(256) k_pcg_q(EngineDev E, TileList tl) {
 template <class V>
 __global__ void __launch_bounds__(256) k_pcg_x(EngineDev E, TileList tl) {
   pdl_start();
+  if (solo_idle(E, PH_OUTER)) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -1956,6 +1992,7 @@ __global__ void __launch_bounds__(256) k_pcg_x(EngineDev E, TileList tl) {
 template <class V>
 __global__ void __launch_bounds__(256) k_pcg_dot(EngineDev E, TileList tl) {
   pdl_start();
+  if (solo_idle(E, PH_PRECOND)) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -1981,6 +2018,7 @@ __global__ void __launch_bounds__(256) k_pcg_dot(EngineDev E, TileList tl) {
 template <class V>
 __global__ void __launch_bounds__(256) k_pcg_p(EngineDev E, TileList tl) {
   pdl_start();
+  if (solo_idle(E, PH_UPDATE)) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -2005,6 +2043,7 @@ __global__ void __launch_bounds__(256) k_pcg_p(EngineDev E, TileList tl) {
 // x64 += c / s (c = inner top-level iterate, buffer 0), for problems in PH_UPDATE
 __global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl) {
   pdl_start();
+  if (solo_idle(E, PH_UPDATE)) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -2030,6 +2069,7 @@ __global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl) {
 // ||b||^2 partials for problems starting a solve
 __global__ void __launch_bounds__(256) k_norm_b(EngineDev E, TileList tl) {
   pdl_start();
+  if (solo_idle(E, PH_INIT)) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -2073,20 +2113,53 @@ __global__ void __launch_bounds__(256) k_boundary_check(EngineDev E) {
 
 // Per-problem control of the solver state machine: reduce the problem's norm partials in a fixed
 // order (bit-reproducible, independent of the batch), then update its state.
+// The norm of problem p from its tile partials, by the ctl_groups blocks of p in this launch
+// (block j adds group j; the block that finishes last adds the group sums in order).  Returns
+// true in the one block that holds the result (in thread 0); the others return false.
+__device__ bool control_sum(const EngineDev& E, int p, int j, const double* part, int ntiles,
+                            double* sh, double* sum) {
+  const int ng = sum_groups(ntiles);
+  if (ng == 1) {
+    if (j != 0) return false;
+    *sum = problem_partial_sum(part, ntiles, sh);
+    return true;
+  }
+  if (j >= ng) return false;
+  __shared__ int last;
+  const double g = group_partial_sum(part, ntiles, j, sh);
+  if (threadIdx.x == 0) {
+    E.gsum[(long long)p * E.ctl_groups + j] = g;
+    __threadfence();
+    last = atomicAdd(E.gticket + p, 1u) == (unsigned)(ng - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    double t = 0.0;
+    for (int q = 0; q < ng; ++q) t += __ldcg(E.gsum + (long long)p * E.ctl_groups + q);
+    *sum = t;
+    E.gticket[p] = 0u;                          // ready for the next launch
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int level) {
   pdl_start();
   __shared__ double sh[32];
-  const int p = blockIdx.x;
+  const int p = blockIdx.x / E.ctl_groups, j = blockIdx.x - p * E.ctl_groups;
   if (p >= E.nprob) return;
   ProbState& st = E.S[p];
   const int ph = st.phase;
   if (kind == CTRL_PRE) {
+    bool owner = j == 0;                        // the block that sets the cycle's IF value
     if ((ph == PH_INNER || ph == PH_CYCLE) && E.P[p].L == level && !st.zero_top) {
-      const double sum = problem_partial_sum(E.partial + E.fine_off[p], fine_tiles(level), sh);
-      if (threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
+      double sum = 0.0;
+      owner = control_sum(E, p, j, E.partial + E.fine_off[p], fine_tiles(level), sh, &sum);
+      if (owner && threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
     }
     // the rest of the V cycle runs if any problem is still in it
-    if (threadIdx.x == 0 && (st.phase == PH_INNER || st.phase == PH_CYCLE))
+    if (owner && threadIdx.x == 0 && (st.phase == PH_INNER || st.phase == PH_CYCLE))
       cond_set(E.prm.cond, 0, 1u);
     return;
   }
@@ -2102,10 +2175,9 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
   double sum = 0.0;
   if (kind != CTRL_POST) {
     const double* part = kind == CTRL_INIT ? E.partial2 : E.partial;
-    const int L = E.P[p].L;
-    const int ntiles = (int)(((n_of_dev(L) * n_of_dev(L)) + kTile - 1) / kTile);
-    const int off = E.fine_off[p];
-    sum = problem_partial_sum(part + off, ntiles, sh);
+    if (!control_sum(E, p, j, part + E.fine_off[p], fine_tiles(E.P[p].L), sh, &sum)) return;
+  } else if (j != 0) {
+    return;
   }
   if (threadIdx.x != 0) return;
   const Params& prm = E.prm;
@@ -2518,7 +2590,7 @@ cudaError_t launch_norm_b(const EngineDev& E, TileList fine, int grid, cudaStrea
 }
 
 cudaError_t launch_control(const EngineDev& E, int kind, cudaStream_t s, int level) {
-  return launch_k(k_control, E.nprob, 0, s, E.pdl, 0, E, kind, level);
+  return launch_k(k_control, E.nprob * E.ctl_groups, 0, s, E.pdl, 0, E, kind, level);
 }
 
 cudaError_t launch_summary(const EngineDev& E, cudaGraphConditionalHandle h, int use_handle,

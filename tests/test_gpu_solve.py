@@ -313,3 +313,32 @@ def test_other_coarse_levels_lockstep(hn, coarse_L):
     assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-9
     x, st, status = solve(hn, L, b, coef, coarse_L=coarse_L, prec=1)
     assert status == hn.HN_OK and oracle_relres(L, coef, b, x) <= RELRES
+
+
+def test_grouped_norm_sums_do_not_depend_on_the_schedule(hn):
+    # L = 11 has 32,776 tiles: its norms are summed in two groups (two control blocks, or one
+    # block group after group inside the fused tail); alone, in a batch with a small problem, and
+    # with the whole cycle inside the fused tail, the results are the same bits
+    L = 11
+    coef, b = I.batch_problem(7, L)
+    A = hn.hn_band_create(L, coef)
+    mg = hn.hn_mg_setup(A, prec=1)
+    hn.hn_band_destroy(A)
+    c2, b2 = I.batch_problem(8, 5)
+    A2 = hn.hn_band_create(5, c2)
+    mg2 = hn.hn_mg_setup(A2, prec=1)
+    hn.hn_band_destroy(A2)
+    try:
+        ref, st, status = hn.hn_mg_solve(mg, L, b)
+        assert status == hn.HN_OK and oracle_relres(L, coef, b, ref) <= RELRES
+        xs, stats, status = hn.hn_mg_solve_batch([mg, mg2], [L, 5], [b, b2])
+        assert status == hn.HN_OK
+        np.testing.assert_array_equal(xs[0], ref)
+        assert stats[0]["cycles"] == st["cycles"]
+        hn.hn_mg_set_tuning(mg, 11, 16, 2, 0, 1)
+        x, st2, _ = hn.hn_mg_solve(mg, L, b)
+        np.testing.assert_array_equal(x, ref)
+        assert st2["cycles"] == st["cycles"]
+    finally:
+        hn.hn_mg_destroy(mg)
+        hn.hn_mg_destroy(mg2)
