@@ -870,14 +870,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // ------------------------------------------------------------------ per-level kernels
 // One warp-tile per loop trip over the work list.  level < 0: each problem's own finest level.
 // Resident blocks per SM asked of the register allocator.  The streaming modes keep 5 blocks
-// (40 warps) of FP32 (FP16 for SpMV/defect) loads in flight, enough to saturate HBM; the fused
+// (40 warps) of FP32 / FP16 loads in flight, enough to saturate HBM (the FP16 Jacobi step spills
+// a few bytes at 5 blocks and is still faster than at 4: 89.8 vs 96.3 us at L = 12); the fused
 // pre-smoothing (4 blocks) and check modes run once per cycle and get more registers per thread.
 template <class Pol, int MODE> constexpr int band_min_blocks() {
   if (MODE == M_CHECK) return Pol::prec == P64 ? 2 : 3;
   if (MODE == M_PRE12) return Pol::prec == P64 ? 2 : 4;
   if (MODE == M_PJ) return Pol::prec == P64 ? 2 : (Pol::prec == P32 ? 4 : 3);
   if (Pol::prec == P32) return 5;
-  if (Pol::prec == P16) return (MODE == M_SPMV || MODE == M_DEFECT) ? 5 : 4;
+  if (Pol::prec == P16) return (MODE == M_SPMV || MODE == M_DEFECT || MODE == M_JACOBI) ? 5 : 4;
   return 4;
 }
 
