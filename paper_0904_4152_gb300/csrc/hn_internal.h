@@ -254,7 +254,7 @@ cudaError_t launch_summary(const EngineDev& E, cudaGraphConditionalHandle h, int
 cudaError_t launch_boundary_check(const EngineDev& E, cudaStream_t s);
 
 enum ControlKind {
-  CTRL_INIT = 0, CTRL_CHECK = 1, CTRL_OUTER = 2, CTRL_INNER = 3, CTRL_POST = 4, CTRL_CHECK0 = 5,
+  CTRL_INIT = 0, CTRL_CHECK = 1, CTRL_OUTER = 2, CTRL_POST = 4, CTRL_CHECK0 = 5,
   CTRL_PRE = 6,  // lagged convergence test after the first smoothing step of a cycle
   CTRL_PCG_ALPHA = 7,  // PCG: alpha = rho / (p, q)
   CTRL_PCG_BETA = 8    // PCG: rho' = (r, z), beta = rho' / rho

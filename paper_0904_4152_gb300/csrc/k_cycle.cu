@@ -2168,7 +2168,6 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
                     (kind == CTRL_CHECK0 && ph == PH_CHECK) ||
                     (kind == CTRL_CHECK && ph == PH_CYCLE) ||
                     (kind == CTRL_OUTER && ph == PH_OUTER) ||
-                    (kind == CTRL_INNER && ph == PH_INNER) ||
                     (kind == CTRL_POST && ph == PH_UPDATE) ||
                     (kind == CTRL_PCG_ALPHA && ph == PH_OUTER && st.cycles > 0) ||
                     (kind == CTRL_PCG_BETA && ph == PH_PRECOND);
@@ -2238,14 +2237,6 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
         st.phase = PH_INNER; st.zero_top = 1; st.inner_ref = st.s * nrm;
         st.inner_k = 1; st.inner_cycles += 1; st.cycles += 1;
       }
-      break;
-    case CTRL_INNER:
-      st.inner_res = nrm;
-      st.inner_k += 1; st.inner_cycles += 1; st.cycles += 1; st.zero_top = 0;
-      if (!isfinite(nrm)) { st.status = HN_ERR_NONFINITE; st.phase = PH_DONE; }
-      else if (nrm <= prm.inner_tol * st.inner_ref || st.inner_k >= prm.inner_max ||
-               st.inner_cycles >= prm.max_cycles)
-        st.phase = PH_UPDATE;
       break;
     case CTRL_PCG_ALPHA:
       // sum = (p, q); a breakdown (not positive: the preconditioned operator is not definite in
