@@ -128,23 +128,33 @@ __device__ __forceinline__ void load_row(const V* __restrict__ v, long long a, i
   w[0] = l2; w[1] = l1; w[2] = c[0]; w[3] = c[1]; w[4] = c[2]; w[5] = c[3]; w[6] = r0; w[7] = r1;
 }
 
+// The FP64 kernels form a defect b - A x as one FMA chain from b (b - a_0 x_0 - a_1 x_1 ...), one
+// FP64 operation per node fewer than b - (A x): they are bound by the FP64 pipe on this part.  The
+// FP32 and FP16-band kernels, bound by HBM, subtract the finished product.
+template <class Pol> __device__ __forceinline__ constexpr bool def_chain() { return Pol::prec == P64; }
+
 // acc[j] = sum_k band_k[i0+j] * x[i0+j+off_k] over the windows w (rows dy = -1, 0, 1), in band
 // order k = 0..8; also the diagonal.  off_k = dy*n + dx = dy*shift + (dy + dx), shift = n - 1.
-template <class Pol, int LKB>
+// DEF: acc enters holding b and leaves holding b - sum_k (same order).
+template <class Pol, int LKB, bool DEF = false>
 __device__ __forceinline__ void stencil_windows(const void* const* band, const float* scale,
                                                 const typename Pol::V (&w)[3][8], long long i0,
                                                 typename Pol::A (&acc)[4],
                                                 typename Pol::A (&dg)[4]) {
   using A = typename Pol::A;
+  if constexpr (!DEF) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) acc[j] = A(0);
+    for (int j = 0; j < 4; ++j) acc[j] = A(0);
+  }
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int dy = k / 3 - 1, dx = k % 3 - 1;
     A b[4];
     load_band<Pol, LKB>(band[k], scale ? scale[k] : 1.0f, i0, b);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[j] = fma(b[j], A(w[dy + 1][j + dy + dx + 2]), acc[j]);
+    for (int j = 0; j < 4; ++j)
+      acc[j] = DEF ? fma(-b[j], A(w[dy + 1][j + dy + dx + 2]), acc[j])
+                   : fma(b[j], A(w[dy + 1][j + dy + dx + 2]), acc[j]);
     if (k == 4) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) dg[j] = b[j];
@@ -191,8 +201,9 @@ __device__ __forceinline__ void diag_rowsum(const void* const* band, const float
   }
 }
 
-// y = A x at the lane's 4 nodes (x read with load kind LK); xc = x at the nodes, dg = diagonal
-template <class Pol, int LK>
+// y = A x at the lane's 4 nodes (x read with load kind LK); xc = x at the nodes, dg = diagonal.
+// DEF (plain band form, not the FP16 row sums): acc enters holding b and leaves holding b - A x.
+template <class Pol, int LK, bool DEF = false>
 __device__ __forceinline__ void apply_op4(const LevelDev& d, const typename Pol::V* __restrict__ x,
                                           long long i0, long long ib, long long shift, int lane,
                                           typename Pol::A (&acc)[4], typename Pol::V (&xc)[4],
@@ -203,7 +214,7 @@ __device__ __forceinline__ void apply_op4(const LevelDev& d, const typename Pol:
 #pragma unroll
   for (int j = 0; j < 4; ++j) xc[j] = w[1][j + 2];
   if constexpr (Pol::prec == P16) stencil_windows_rowsum<band_kind<LK>()>(d.band, d.scale, w, ib, acc, dg);
-  else stencil_windows<Pol, band_kind<LK>()>(d.band, nullptr, w, ib, acc, dg);
+  else stencil_windows<Pol, band_kind<LK>(), DEF>(d.band, nullptr, w, ib, acc, dg);
 }
 
 // deterministic warp sum (butterfly; every lane ends with the same value)
@@ -400,12 +411,20 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
         for (int r = 0; r < 3; ++r)
 #pragma unroll
           for (int o = 0; o < 8; ++o) x1[r][o] = mul_rn(dw[r][o], bw[r][o]);
+        constexpr bool DEF = def_chain<Pol>();
         A acc[4], dg[4];
+        if constexpr (DEF) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[j] = A(bw[1][j + 2]);
+        }
         if constexpr (Pol::prec == P16) stencil_windows_rowsum<LKB>(d.band, d.scale, x1, ib, acc, dg);
-        else stencil_windows<Pol, LKB>(d.band, nullptr, x1, ib, acc, dg);
+        else stencil_windows<Pol, LKB, DEF>(d.band, nullptr, x1, ib, acc, dg);
         V out[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) out[j] = fma(A(dw[1][j + 2]), A(bw[1][j + 2]) - acc[j], A(x1[1][j + 2]));
+        for (int j = 0; j < 4; ++j) {
+          const A r = DEF ? acc[j] : A(bw[1][j + 2]) - acc[j];
+          out[j] = fma(A(dw[1][j + 2]), r, A(x1[1][j + 2]));
+        }
         st4(static_cast<V*>(d.x[0]) + i0, out);
         return;
       }
@@ -415,9 +434,15 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
   if constexpr (MODE == M_JACOBI_FIRST || MODE == M_PRE12) { src = 0; dst = 1; }
   if constexpr (MODE == M_PRE2B) { src = 1; dst = 0; }
   const V* xin = static_cast<const V*>(d.x[src]);
+  constexpr bool DEF = MODE != M_SPMV && def_chain<Pol>();
   A acc[4], dg[4];
-  V xc[4];
-  if constexpr (LKB == band_kind<LK>()) apply_op4<Pol, LK>(d, xin, i0, ib, shift, lane, acc, xc, dg);
+  V xc[4], b[4];
+  if constexpr (DEF) {                            // the chain starts from b
+    ld4<LK>(rhs + i0, b);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = A(b[j]);
+  }
+  if constexpr (LKB == band_kind<LK>()) apply_op4<Pol, LK, DEF>(d, xin, i0, ib, shift, lane, acc, xc, dg);
   else {                                          // bands from a shared-memory stage
     V w[3][8];
 #pragma unroll
@@ -425,7 +450,7 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
 #pragma unroll
     for (int j = 0; j < 4; ++j) xc[j] = w[1][j + 2];
     if constexpr (Pol::prec == P16) stencil_windows_rowsum<LKB>(d.band, d.scale, w, ib, acc, dg);
-    else stencil_windows<Pol, LKB>(d.band, nullptr, w, ib, acc, dg);
+    else stencil_windows<Pol, LKB, DEF>(d.band, nullptr, w, ib, acc, dg);
   }
   if constexpr (MODE == M_SPMV) {
     V out[4];
@@ -433,20 +458,19 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
     for (int j = 0; j < 4; ++j) out[j] = V(acc[j]);
     st4(static_cast<V*>(d.r) + i0, out);
   } else {
-    V b[4];
-    ld4<LK>(rhs + i0, b);
+    if constexpr (!DEF) ld4<LK>(rhs + i0, b);
+    A r[4];                                       // the defect b - A x
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r[j] = DEF ? acc[j] : A(b[j]) - acc[j];
     if constexpr (MODE == M_DEFECT) {
       V out[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) out[j] = V(A(b[j]) - acc[j]);
+      for (int j = 0; j < 4; ++j) out[j] = V(r[j]);
       st4(static_cast<V*>(d.r) + i0, out);
     } else if constexpr (MODE == M_CHECK) {
       double q = 0.0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const double r = double(A(b[j]) - acc[j]);
-        q += r * r;
-      }
+      for (int j = 0; j < 4; ++j) q += double(r[j]) * double(r[j]);
       q = warp_sum(q);
       if (lane == 0) *partial_slot = q;
     } else {                                      // a Jacobi step src -> dst
@@ -454,16 +478,13 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
       wd4_of<Pol, LKB>(d, i0, omega, dg, wd);
       V out[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) out[j] = fma(wd[j], A(b[j]) - acc[j], A(xc[j]));
+      for (int j = 0; j < 4; ++j) out[j] = fma(wd[j], r[j], A(xc[j]));
       st4(static_cast<V*>(d.x[dst]) + i0, out);
       if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST) {
         if (partial_slot) {                       // residual norm of the iterate (lagged check)
           double q = 0.0;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const double r = double(A(b[j]) - acc[j]);
-            q += r * r;
-          }
+          for (int j = 0; j < 4; ++j) q += double(r[j]) * double(r[j]);
           q = warp_sum(q);
           if (lane == 0) *partial_slot = q;
         }
@@ -687,16 +708,22 @@ __device__ __forceinline__ void prolong_jacobi_tile(const LevelDev& d, const Lev
     if (ax < 0) { ax += nf; --ay; } else if (ax >= nf) { ax -= nf; ++ay; }
     load_row_prolonged<V, LK>(x, e, i0 + dy * shift, ax, ay, nf, nc, d.bc, Nf, lane, w[dy + 1]);
   }
+  constexpr bool DEF = def_chain<Pol>();
   A acc[4], dg[4];
-  if constexpr (Pol::prec == P16) stencil_windows_rowsum<band_kind<LK>()>(d.band, d.scale, w, i0, acc, dg);
-  else stencil_windows<Pol, band_kind<LK>()>(d.band, nullptr, w, i0, acc, dg);
   V b[4];
-  ld4<LK>(static_cast<const V*>(d.rhs) + i0, b);
+  if constexpr (DEF) {
+    ld4<LK>(static_cast<const V*>(d.rhs) + i0, b);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = A(b[j]);
+  }
+  if constexpr (Pol::prec == P16) stencil_windows_rowsum<band_kind<LK>()>(d.band, d.scale, w, i0, acc, dg);
+  else stencil_windows<Pol, band_kind<LK>(), DEF>(d.band, nullptr, w, i0, acc, dg);
+  if constexpr (!DEF) ld4<LK>(static_cast<const V*>(d.rhs) + i0, b);
   A wd[4];
   wd4_of<Pol, band_kind<LK>()>(d, i0, omega, dg, wd);
   V out[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) out[j] = fma(wd[j], A(b[j]) - acc[j], A(w[1][j + 2]));
+  for (int j = 0; j < 4; ++j) out[j] = fma(wd[j], DEF ? acc[j] : A(b[j]) - acc[j], A(w[1][j + 2]));
   st4(static_cast<V*>(d.x[1 - in_sel]) + i0, out);
 }
 
@@ -1207,7 +1234,8 @@ __device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* 
 // operands, same order of operations), so the results do not depend on which path ran.
 
 // acc = sum_k a_k[i] x[i + off_k] in band order (FP16: the row-sum form), dg = the diagonal
-template <class Pol>
+// DEF (plain band form): acc enters holding b and leaves holding b - A x (the tile step's chain)
+template <class Pol, bool DEF = false>
 __device__ __forceinline__ void stencil_node(const LevelDev& d, const typename Pol::V* x, int i,
                                              typename Pol::A& acc, typename Pol::A& dg) {
   using A = typename Pol::A;
@@ -1227,12 +1255,12 @@ __device__ __forceinline__ void stencil_node(const LevelDev& d, const typename P
       dg -= b;
     }
   } else {
-    acc = A(0);
+    if constexpr (!DEF) acc = A(0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const int off = (k / 3 - 1) * n + (k % 3 - 1);
       const A b = static_cast<const B*>(d.band[k])[i];
-      acc = fma(b, A(x[i + off]), acc);
+      acc = DEF ? fma(-b, A(x[i + off]), acc) : fma(b, A(x[i + off]), acc);
       if (k == 4) dg = b;
     }
   }
@@ -1283,6 +1311,11 @@ __device__ __forceinline__ void band_node(const LevelDev& d, int i, bool zg, int
             const float b = __fmul_rn(d.scale[k], __half2float(static_cast<const __half*>(d.band[k])[i]));
             acc = fmaf(b, x1[k] - x1[4], acc);
           }
+        } else if constexpr (def_chain<Pol>()) {
+          acc = A(rhs[i]);
+#pragma unroll
+          for (int k = 0; k < 9; ++k)
+            acc = fma(-A(static_cast<const typename Pol::B*>(d.band[k])[i]), A(x1[k]), acc);
         } else {
           acc = A(0);
 #pragma unroll
@@ -1292,7 +1325,8 @@ __device__ __forceinline__ void band_node(const LevelDev& d, int i, bool zg, int
         A wd;
         if constexpr (Pol::prec == P64) wd = d.wdinv[i];
         else wd = d.wdf[i];
-        static_cast<V*>(d.x[0])[i] = fma(wd, A(rhs[i]) - acc, A(x1[4]));
+        const A r = def_chain<Pol>() ? acc : A(rhs[i]) - acc;
+        static_cast<V*>(d.x[0])[i] = fma(wd, r, A(x1[4]));
         return;
       }
     }
@@ -1301,13 +1335,16 @@ __device__ __forceinline__ void band_node(const LevelDev& d, int i, bool zg, int
   if constexpr (MODE == M_JACOBI_FIRST || MODE == M_PRE12) { src = 0; dst = 1; }
   if constexpr (MODE == M_PRE2B) { src = 1; dst = 0; }
   const V* xin = static_cast<const V*>(d.x[src]);
+  constexpr bool DEF = def_chain<Pol>();
   A acc, dg;
-  stencil_node<Pol>(d, xin, i, acc, dg);
+  if constexpr (DEF) acc = A(rhs[i]);
+  stencil_node<Pol, DEF>(d, xin, i, acc, dg);
+  const A r = DEF ? acc : A(rhs[i]) - acc;
   if constexpr (MODE == M_DEFECT) {
-    static_cast<V*>(d.r)[i] = V(A(rhs[i]) - acc);
+    static_cast<V*>(d.r)[i] = V(r);
   } else {                                        // a Jacobi step src -> dst
     const A wd = wd_node<Pol>(d, i, omega, dg);
-    static_cast<V*>(d.x[dst])[i] = fma(wd, A(rhs[i]) - acc, A(xin[i]));
+    static_cast<V*>(d.x[dst])[i] = fma(wd, r, A(xin[i]));
   }
 }
 
@@ -1898,12 +1935,12 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
 #pragma unroll
       for (int j = 0; j < 4; ++j) r[j] = b[j];
     } else {
-      double w[3][8], acc[4], dg[4];
+      double w[3][8], dg[4];
 #pragma unroll
       for (int dy = -1; dy <= 1; ++dy) load_row<double, LD_NC>(P.x64, i0 + dy * (1LL << P.L), lane, w[dy + 1]);
-      stencil_windows<F64, LD_NC>(reinterpret_cast<const void* const*>(P.band64), nullptr, w, i0, acc, dg);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) r[j] = b[j] - acc[j];
+      for (int j = 0; j < 4; ++j) r[j] = b[j];       // r = b - A x as one chain from b
+      stencil_windows<F64, LD_NC, true>(reinterpret_cast<const void* const*>(P.band64), nullptr, w, i0, r, dg);
     }
     const double s = st.s;
     V out[4];
