@@ -578,19 +578,32 @@ __device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& 
       e0[k] = ld1<LK>(e + cy0 * nc + cxa + k);
       e1[k] = oy ? ld1<LK>(e + (cy0 + 1) * nc + cxa + k) : V(0);
     }
-    auto pick = [](const V (&a)[3], int q) { return q == 0 ? a[0] : (q == 1 ? a[1] : a[2]); };
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (is_dirichlet(ix + j, iy, nf, f.bc)) continue;
-      const int c0 = (j + odd) >> 1, c1 = (j + 1 + odd) >> 1;   // columns of (ix + j) / 2, (ix + j + 1) / 2
-      const bool ox = (j + odd) & 1;
-      V add;
-      if (!ox && !oy) add = pick(e0, c0);
-      else if (ox && !oy) add = V(0.5) * (pick(e0, c0) + pick(e0, c1));
-      else if (!ox && oy) add = V(0.5) * (pick(e0, c0) + pick(e1, c0));
-      else add = V(0.25) * (((pick(e0, c0) + pick(e0, c1)) + pick(e1, c0)) + pick(e1, c1));
-      v[j] = v[j] + add;
+    // Node j sits at fine column 2 cxa + odd + j.  The row parity (oy) and the column parity
+    // (odd) are the same for all lanes of a warp that lie in one fine row, so the four cases
+    // below are separate code paths: each node does its own formula's operations only (a
+    // per-node choice between the formulas had the FP64 pipe evaluate several of them).
+    auto mid = [](V a, V b) { return V(0.5) * (a + b); };                    // edge midpoint
+    auto ctr = [](V a, V b, V c, V d) { return V(0.25) * (((a + b) + c) + d); };   // cell centre
+    V add[4];
+    if (!oy) {
+      if (!odd) { add[0] = e0[0]; add[1] = mid(e0[0], e0[1]); add[2] = e0[1]; add[3] = mid(e0[1], e0[2]); }
+      else      { add[0] = mid(e0[0], e0[1]); add[1] = e0[1]; add[2] = mid(e0[1], e0[2]); add[3] = e0[2]; }
+    } else {
+      if (!odd) {
+        add[0] = mid(e0[0], e1[0]);
+        add[1] = ctr(e0[0], e0[1], e1[0], e1[1]);
+        add[2] = mid(e0[1], e1[1]);
+        add[3] = ctr(e0[1], e0[2], e1[1], e1[2]);
+      } else {
+        add[0] = ctr(e0[0], e0[1], e1[0], e1[1]);
+        add[1] = mid(e0[1], e1[1]);
+        add[2] = ctr(e0[1], e0[2], e1[1], e1[2]);
+        add[3] = mid(e0[2], e1[2]);
+      }
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (!is_dirichlet(ix + j, iy, nf, f.bc)) v[j] = v[j] + add[j];
   } else {
     // the nodes wrap into the next row (or reach the padding): node by node
 #pragma unroll
