@@ -919,7 +919,7 @@ template <class Pol, int MODE> constexpr int band_min_blocks() {
   if (MODE == M_PJ) return Pol::prec == P64 ? 2 : (Pol::prec == P32 ? 4 : 3);
   if (Pol::prec == P32) return 5;
   if (Pol::prec == P16) return (MODE == M_SPMV || MODE == M_DEFECT || MODE == M_JACOBI) ? 5 : 4;
-  return 4;
+  return MODE == M_SPMV ? 4 : 3;
 }
 
 template <class Pol, int MODE>
