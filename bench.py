@@ -794,6 +794,7 @@ def run_serve(args, rank, world, local, pg):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                            "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
             "dof_per_s": dofs / wall, "scheduler_iterations": info["iterations"],
+            "worker_s": {k: info[k + "_ns"] * 1e-9 for k in ("admit", "schedule", "iterate", "retire")},
             "relres_max": max(r[2] for r in done if r[0] == hn.HN_OK)}), flush=True)
 
 

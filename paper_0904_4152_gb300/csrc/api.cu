@@ -126,39 +126,10 @@ hn_status hn_band_create_bc(int L, const double* cell_coef, unsigned dirichlet_s
   clear_error();
   if (!out) return set_error(HN_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (dirichlet_sides < 1u || dirichlet_sides > 15u)
-    return set_error(HN_ERR_ARG, "dirichlet_sides %u: need a nonzero mask of the 4 sides", dirichlet_sides);
-  if (L < HN_MIN_LEVEL || L > HN_MAX_LEVEL)
-    return set_error(HN_ERR_ARG, "level %d outside [%d, %d]", L, HN_MIN_LEVEL, HN_MAX_LEVEL);
-  const long long cells = (1LL << L) * (1LL << L);
-  if (cell_coef)
-    for (long long i = 0; i < cells; ++i)
-      if (!(std::isfinite(cell_coef[i]) && cell_coef[i] > 0.0))
-        return set_error(HN_ERR_ARG, "cell coefficient %lld is not a positive finite number", i);
-  std::unique_ptr<hn_band> A(new hn_band());
-  A->L = L;
-  A->bc = dirichlet_sides;
-  A->n = n_of(L);
-  A->N = N_of(L);
-  A->pitch = pitch_of(L);
-  size_t bytes = 0;
-  auto take = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
-  for (int k = 0; k < 9; ++k) take((size_t)A->pitch * 8);
-  if (cell_coef) take((size_t)cells * 8);
-  bytes += 256;
+  HN_TRY(check_band_inputs(L, cell_coef, dirichlet_sides));
   OwnedStream os;
   HN_CUDA(cudaStreamCreateWithFlags(&os.s, cudaStreamNonBlocking));
-  HN_CUDA(cudaMalloc(&A->mem, bytes));
-  Bump b{static_cast<char*>(A->mem), 0};
-  BandPtrs64 bp{};
-  for (int k = 0; k < 9; ++k) bp.p[k] = A->band[k] = b.take<double>(A->pitch);
-  if (cell_coef) {
-    A->coef = b.take<double>((size_t)cells);
-    HN_CUDA(cudaMemcpyAsync(A->coef, cell_coef, (size_t)cells * 8, cudaMemcpyHostToDevice, os.s));
-  }
-  HN_CUDA(launch_assemble(L, A->coef, bp, nullptr, 1.0, (int)A->bc, os.s));
-  HN_CUDA(cudaStreamSynchronize(os.s));
-  *out = A.release();
+  HN_TRY(build_band(L, cell_coef, dirichlet_sides, os.s, nullptr, out));
   return HN_OK;
 }
 

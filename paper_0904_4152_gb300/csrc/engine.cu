@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 
 #include "engine.h"
@@ -168,7 +169,60 @@ hn_status validate_opts(const hn_mg_opts& o, int L) {
   return HN_OK;
 }
 
-hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s, hn_mg* mg) {
+hn_status check_band_inputs(int L, const double* cell_coef, unsigned dirichlet_sides) {
+  if (dirichlet_sides < 1u || dirichlet_sides > 15u)
+    return set_error(HN_ERR_ARG, "dirichlet_sides %u: need a nonzero mask of the 4 sides", dirichlet_sides);
+  if (L < HN_MIN_LEVEL || L > HN_MAX_LEVEL)
+    return set_error(HN_ERR_ARG, "level %d outside [%d, %d]", L, HN_MIN_LEVEL, HN_MAX_LEVEL);
+  const long long cells = (1LL << L) * (1LL << L);
+  if (cell_coef)
+    for (long long i = 0; i < cells; ++i)
+      if (!(std::isfinite(cell_coef[i]) && cell_coef[i] > 0.0))
+        return set_error(HN_ERR_ARG, "cell coefficient %lld is not a positive finite number", i);
+  return HN_OK;
+}
+
+size_t band_bytes(int L, bool has_coef) {
+  size_t bytes = 0;
+  auto take = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
+  for (int k = 0; k < 9; ++k) take((size_t)pitch_of(L) * 8);
+  if (has_coef) take((size_t)(1LL << L) * (1LL << L) * 8);
+  return bytes + 256;
+}
+
+hn_status build_band(int L, const double* cell_coef, unsigned bc, cudaStream_t s, void* mem,
+                     hn_band** out) {
+  std::unique_ptr<hn_band> A(new hn_band());
+  A->L = L;
+  A->bc = bc;
+  A->n = n_of(L);
+  A->N = N_of(L);
+  A->pitch = pitch_of(L);
+  const long long cells = (1LL << L) * (1LL << L);
+  if (mem) A->mem = mem;
+  else HN_CUDA(cudaMalloc(&A->mem, band_bytes(L, cell_coef != nullptr)));
+  Bump b{static_cast<char*>(A->mem), 0};
+  BandPtrs64 bp{};
+  for (int k = 0; k < 9; ++k) bp.p[k] = A->band[k] = b.take<double>(A->pitch);
+  if (cell_coef) {
+    A->coef = b.take<double>((size_t)cells);
+    HN_CUDA(cudaMemcpyAsync(A->coef, cell_coef, (size_t)cells * 8, cudaMemcpyHostToDevice, s));
+  }
+  HN_CUDA(launch_assemble(L, A->coef, bp, nullptr, 1.0, (int)A->bc, s));
+  HN_CUDA(cudaStreamSynchronize(s));
+  *out = A.release();
+  return HN_OK;
+}
+
+size_t hierarchy_tmp_bytes(int L, int c, int prec, bool has_coef) {
+  const long long cells_L = (1LL << L) * (1LL << L);
+  const size_t coef_bytes = has_coef ? (size_t)(cells_L + cells_L / 4 + 64) * 8 : 0;
+  const size_t tmpband_bytes = (prec != P64 && L > c) ? (size_t)9 * pitch_of(L - 1) * 8 + 9 * 256 : 0;
+  return coef_bytes + tmpband_bytes + 1024;
+}
+
+hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s, hn_mg* mg,
+                          void* mem, void* scratch, size_t scratch_bytes) {
   const int L = A->L, c = o.coarse_L;
   const Params prm = params_from(o);
   const int prec = prm.prec;
@@ -179,7 +233,8 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
   const UnknownRect ur = unknown_rect((int)n_of(c), (int)A->bc);
   mg->m = ur.nx * ur.ny;
   mg->bytes = hierarchy_bytes(L, c, prec, prm.solver);
-  HN_CUDA(cudaMalloc(&mg->mem, mg->bytes));
+  if (mem) mg->mem = mem;                       // a block of exactly mg->bytes from the caller
+  else HN_CUDA(cudaMalloc(&mg->mem, mg->bytes));
   HN_CUDA(cudaMemsetAsync(mg->mem, 0, mg->bytes, s));
 
   ProblemDev& P = mg->host;
@@ -241,14 +296,17 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
   if (b.off > mg->bytes) return set_error(HN_ERR_STATE, "hierarchy layout overflow");
 
   // temporaries: coefficients of two consecutive levels, FP64 bands of one coarse level,
-  // FP16 scale reduction words
+  // FP16 scale reduction words (in the caller's scratch when it is large enough)
   const long long cells_L = (1LL << L) * (1LL << L);
-  const size_t coef_bytes = A->coef ? (size_t)(cells_L + cells_L / 4 + 64) * 8 : 0;
   const size_t tmpband_bytes = (prec != P64 && L > c) ? (size_t)9 * pitch_of(L - 1) * 8 + 9 * 256 : 0;
   TempDev tmp;
-  const size_t tmp_bytes = coef_bytes + tmpband_bytes + 1024;
-  HN_CUDA(cudaMalloc(&tmp.p, tmp_bytes));
-  Bump tb{static_cast<char*>(tmp.p), 0};
+  const size_t tmp_bytes = hierarchy_tmp_bytes(L, c, prec, A->coef != nullptr);
+  char* tmp_base = static_cast<char*>(scratch);
+  if (!scratch || scratch_bytes < tmp_bytes) {
+    HN_CUDA(cudaMalloc(&tmp.p, tmp_bytes));
+    tmp_base = static_cast<char*>(tmp.p);
+  }
+  Bump tb{tmp_base, 0};
   double* coef_a = A->coef ? tb.take<double>((size_t)cells_L) : nullptr;
   double* coef_b = A->coef ? tb.take<double>((size_t)(cells_L / 4 + 1)) : nullptr;
   double* tband[9] = {};

@@ -105,7 +105,18 @@ struct hn_mg {
 
 namespace hn {
 
-hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t stream, hn_mg* mg);
+// Device memory of the hierarchy: a block of exactly hierarchy_bytes() from the caller (mem) or
+// a new allocation (mem == nullptr); the setup temporaries go to scratch when it holds
+// hierarchy_tmp_bytes(), else to a transient allocation.
+hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t stream, hn_mg* mg,
+                          void* mem = nullptr, void* scratch = nullptr, size_t scratch_bytes = 0);
+size_t hierarchy_tmp_bytes(int L, int c, int prec, bool has_coef);
+// Q1 operator of level L (hn_band_create_bc without the input checks, on stream s, in mem of
+// band_bytes() when given); check_band_inputs holds the checks.
+hn_status check_band_inputs(int L, const double* cell_coef, unsigned dirichlet_sides);
+size_t band_bytes(int L, bool has_coef);
+hn_status build_band(int L, const double* cell_coef, unsigned bc, cudaStream_t s, void* mem,
+                     hn_band** out);
 hn_status validate_opts(const hn_mg_opts& o, int L);
 Params params_from(const hn_mg_opts& o);
 

@@ -19,11 +19,76 @@ using namespace hn;
 
 namespace {
 
+// Page-locked host buffers, recycled by size: a request's inputs and result live in them, so
+// the copies to and from the device are plain DMA and no fresh host pages are touched per request.
+struct HostPool {
+  std::mutex mu;
+  std::multimap<size_t, void*> blocks;
+  size_t cached = 0;
+  static constexpr size_t kCap = size_t(4) << 30;   // cached bytes kept at most
+  void* take(size_t bytes) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = blocks.find(bytes);
+      if (it != blocks.end()) {
+        void* p = it->second;
+        blocks.erase(it);
+        cached -= bytes;
+        return p;
+      }
+    }
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void give(void* p, size_t bytes) {
+    if (!p) return;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (cached + bytes <= kCap) {
+        blocks.emplace(bytes, p);
+        cached += bytes;
+        return;
+      }
+    }
+    cudaFreeHost(p);
+  }
+  ~HostPool() {
+    for (auto& kv : blocks) cudaFreeHost(kv.second);
+  }
+};
+
+// n doubles in a HostPool block, returned to the pool on release / destruction
+struct HostBuf {
+  HostPool* pool = nullptr;
+  double* p = nullptr;
+  size_t n = 0;
+  HostBuf() = default;
+  HostBuf(const HostBuf&) = delete;
+  HostBuf& operator=(const HostBuf&) = delete;
+  ~HostBuf() { release(); }
+  bool alloc(HostPool* pl, size_t count) {
+    release();
+    pool = pl;
+    p = static_cast<double*>(pl->take(count * 8));
+    n = p ? count : 0;
+    return p != nullptr;
+  }
+  void release() {
+    if (p) pool->give(p, n * 8);
+    p = nullptr;
+    n = 0;
+  }
+};
+
 struct Request {
   unsigned long long ticket = 0;
   int L = 0;
   unsigned bc = 15u;                 // Dirichlet sides of its operator
-  std::vector<double> coef, b, x;
+  HostBuf coef, b, x;                // coef empty for a = 1
   hn_mg* mg = nullptr;
   int slot = -1;
   size_t bytes = 0;
@@ -33,9 +98,36 @@ struct Request {
   long long t_submit = 0, t_admit = 0, t_done = 0;
 };
 
+// Device blocks of retired requests (hierarchies, transient operators), kept for the next
+// request that needs a block of the same size: cudaMalloc / cudaFree of these sizes take
+// milliseconds and synchronize the device, on the worker's critical path.
+struct BlockCache {
+  std::multimap<size_t, void*> blocks;
+  size_t bytes = 0;
+  void* take(size_t b) {
+    auto it = blocks.find(b);
+    if (it == blocks.end()) return nullptr;
+    void* p = it->second;
+    blocks.erase(it);
+    bytes -= b;
+    return p;
+  }
+  void give(void* p, size_t b) {
+    if (!p) return;
+    blocks.emplace(b, p);
+    bytes += b;
+  }
+  void clear() {
+    for (auto& kv : blocks) cudaFree(kv.second);
+    blocks.clear();
+    bytes = 0;
+  }
+};
+
 }  // namespace
 
 struct hn_server {
+  HostPool host;                     // first member: outlives the requests' buffers
   size_t budget = 0;
   int max_active = 0;
   int device = 0;
@@ -49,7 +141,11 @@ struct hn_server {
   hn_mg_opts opts{};
   size_t in_use = 0;
   long long submitted = 0, completed = 0, iterations = 0;
+  long long admit_ns = 0, schedule_ns = 0, iterate_ns = 0, retire_ns = 0;   // worker time
   std::vector<Request*> slots;
+  BlockCache cache;                  // worker only
+  void* scratch = nullptr;           // worker only: setup temporaries, grown on demand
+  size_t scratch_bytes = 0;
   std::thread worker;
   std::string worker_error;
   void run();
@@ -102,6 +198,13 @@ void hn_server::run() {
           auto free_slot = std::find(slots.begin(), slots.end(), nullptr);
           if (free_slot == slots.end()) break;
           Request* r = queue.front();
+          if (in_use + r->bytes + cache.bytes + scratch_bytes > budget) {
+            // cached blocks count against the budget: give them back before waiting
+            cache.clear();
+            if (scratch) cudaFree(scratch);
+            scratch = nullptr;
+            scratch_bytes = 0;
+          }
           if (in_use + r->bytes > budget) break;    // FIFO: the head waits for memory
           queue.pop_front();
           in_use += r->bytes;
@@ -113,19 +216,42 @@ void hn_server::run() {
       }
     }
     // build the hierarchies of the admitted requests (explicit copies of their inputs)
+    const long long t_admit0 = now_ns();
     for (Request* r : admitted) {
+      // inputs were checked at submit; device blocks come from the cache when it has one
+      const long long t0 = now_ns();
+      const bool has_coef = r->coef.p != nullptr;
+      const size_t bb = band_bytes(r->L, has_coef);
       hn_band* A = nullptr;
-      hn_status st = hn_band_create_bc(r->L, r->coef.empty() ? nullptr : r->coef.data(), r->bc, &A);
+      hn_status st = build_band(r->L, has_coef ? r->coef.p : nullptr, r->bc, s, cache.take(bb), &A);
       hn_mg* mg = nullptr;
       if (st == HN_OK) {
         hn_mg_opts o = opts;
         o.stream = s;
-        st = hn_mg_setup(A, &o, &mg);
+        const Params prm = params_from(o);
+        const size_t tmp = hierarchy_tmp_bytes(r->L, o.coarse_L, prm.prec, has_coef);
+        if (tmp > scratch_bytes) {
+          if (scratch) cudaFree(scratch);
+          scratch = nullptr;
+          scratch_bytes = 0;
+          if (cudaMalloc(&scratch, tmp) == cudaSuccess) scratch_bytes = tmp;
+          else cudaGetLastError();                  // build_hierarchy allocates its own then
+        }
+        std::unique_ptr<hn_mg> h(new hn_mg());
+        h->stream = s;
+        st = build_hierarchy(A, o, s, h.get(), cache.take(hierarchy_bytes(r->L, o.coarse_L, prm.prec, prm.solver)),
+                             scratch, scratch_bytes);
+        h->setup_ns = now_ns() - t0;
+        mg = h.release();
       }
-      hn_band_destroy(A);
+      if (A) {                                      // (later users of the block run on stream s)
+        cache.give(A->mem, bb);
+        A->mem = nullptr;
+        hn_band_destroy(A);
+      }
       if (st == HN_OK) {
         const long long N = N_of(r->L);
-        if (cudaMemcpyAsync(mg->host.b64, r->b.data(), (size_t)N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        if (cudaMemcpyAsync(mg->host.b64, r->b.p, (size_t)N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(mg->host.x64, 0, (size_t)N * 8, s) != cudaSuccess)
           st = HN_ERR_CUDA;
       }
@@ -144,6 +270,11 @@ void hn_server::run() {
       r->stats.setup_ns = mg->setup_ns;
       fresh.push_back(r->slot);
       members_dirty = true;
+    }
+    const long long t_sched0 = now_ns();
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      admit_ns += t_sched0 - t_admit0;
     }
     // (re)build the engine for the current highest level, then refresh its work lists
     int lmax = 0;
@@ -200,12 +331,16 @@ void hn_server::run() {
       fresh.erase(std::remove_if(fresh.begin(), fresh.end(), [&](int q) { return members[q] != nullptr; }), fresh.end());
     }
     unsigned active = 0;
+    const long long t_iter0 = now_ns();
     if (engine->run_iteration(&active) != HN_OK) { fail_all(hn_last_error()); break; }
     std::vector<ProbState> st;
     if (engine->read_states(st) != HN_OK) { fail_all(hn_last_error()); break; }
+    const long long t_ret0 = now_ns();
     {
       std::lock_guard<std::mutex> lk(mu);
       ++iterations;
+      schedule_ns += t_iter0 - t_sched0;
+      iterate_ns += t_ret0 - t_iter0;
     }
     // retire finished requests
     for (int q = 0; q < max_active; ++q) {
@@ -216,11 +351,17 @@ void hn_server::run() {
         r = slots[q];
       }
       const long long N = N_of(r->L);
-      r->x.resize((size_t)N);
-      if (st[q].status == HN_OK && st[q].bnorm == 0.0) std::fill(r->x.begin(), r->x.end(), 0.0);
-      else if (cudaMemcpyAsync(r->x.data(), r->mg->host.x64, (size_t)N * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      if (!r->x.alloc(&host, (size_t)N)) { fail_all("pinned host memory for a result"); break; }
+      if (st[q].status == HN_OK && st[q].bnorm == 0.0) std::fill(r->x.p, r->x.p + N, 0.0);
+      else if (cudaMemcpyAsync(r->x.p, r->mg->host.x64, (size_t)N * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                cudaStreamSynchronize(s) != cudaSuccess) { fail_all("result copy failed"); break; }
+      r->b.release();                               // the inputs were consumed at admission
+      r->coef.release();
+      void* hmem = r->mg->mem;                      // kept for the next request of its size
+      const size_t hbytes = r->mg->bytes;
+      r->mg->mem = nullptr;
       hn_mg_destroy(r->mg);
+      cache.give(hmem, hbytes);
       std::lock_guard<std::mutex> lk(mu);
       r->mg = nullptr;
       r->status = st[q].status;
@@ -238,9 +379,18 @@ void hn_server::run() {
       members_dirty = true;
       cv_done.notify_all();
     }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      retire_ns += now_ns() - t_ret0;
+    }
     if (stop && worker_error.size()) break;
   }
   engine.reset();
+  cudaStreamSynchronize(s);
+  cache.clear();
+  if (scratch) cudaFree(scratch);
+  scratch = nullptr;
+  scratch_bytes = 0;
   cudaStreamDestroy(s);
 }
 
@@ -269,12 +419,17 @@ hn_status hn_mg_submit(hn_server* srv, int L, const double* cell_coef, const dou
   hn_mg_opts o;
   if (opts) o = *opts; else hn_mg_opts_default(&o);
   HN_TRY(validate_opts(o, L));
+  HN_TRY(check_band_inputs(L, cell_coef, o.dirichlet_sides));   // here, not on the worker
   std::unique_ptr<Request> r(new Request());
   r->L = L;
   r->bc = o.dirichlet_sides;
   const long long N = N_of(L), cells = (1LL << L) * (1LL << L);
-  if (cell_coef) r->coef.assign(cell_coef, cell_coef + cells);
-  r->b.assign(b, b + N);
+  if (cell_coef) {
+    if (!r->coef.alloc(&srv->host, (size_t)cells)) return set_error(HN_ERR_OOM, "pinned host memory for the coefficients");
+    std::memcpy(r->coef.p, cell_coef, (size_t)cells * 8);
+  }
+  if (!r->b.alloc(&srv->host, (size_t)N)) return set_error(HN_ERR_OOM, "pinned host memory for b");
+  std::memcpy(r->b.p, b, (size_t)N * 8);
   r->bytes = request_bytes(L, o);
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->stop) return set_error(HN_ERR_STATE, "server stopped: %s", srv->worker_error.c_str());
@@ -318,7 +473,7 @@ hn_status hn_mg_poll(hn_server* srv, unsigned long long ticket, long long timeou
         return set_error(HN_ERR_TIMEOUT, "request %llu not finished before the deadline", ticket);
     }
   }
-  if (x_out && !r->x.empty()) std::memcpy(x_out, r->x.data(), r->x.size() * 8);
+  if (x_out && r->x.p) std::memcpy(x_out, r->x.p, r->x.n * 8);
   if (stats) *stats = r->stats;
   const hn_status st = (hn_status)r->status;
   srv->all.erase(it);
@@ -337,6 +492,10 @@ hn_status hn_server_query(hn_server* srv, hn_server_info* info) {
   info->iterations = srv->iterations;
   info->bytes_in_use = srv->in_use;
   info->budget = srv->budget;
+  info->admit_ns = srv->admit_ns;
+  info->schedule_ns = srv->schedule_ns;
+  info->iterate_ns = srv->iterate_ns;
+  info->retire_ns = srv->retire_ns;
   return HN_OK;
 }
 

@@ -71,7 +71,9 @@ class ServerInfo(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
                 ("active", ctypes.c_longlong), ("queued", ctypes.c_longlong),
                 ("iterations", ctypes.c_longlong), ("bytes_in_use", ctypes.c_size_t),
-                ("budget", ctypes.c_size_t)]
+                ("budget", ctypes.c_size_t), ("admit_ns", ctypes.c_longlong),
+                ("schedule_ns", ctypes.c_longlong), ("iterate_ns", ctypes.c_longlong),
+                ("retire_ns", ctypes.c_longlong)]
 
 
 class Tuning(ctypes.Structure):

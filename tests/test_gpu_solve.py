@@ -224,6 +224,37 @@ def test_server_results_match_alone(hn, slots):
         hn.hn_server_destroy(srv)
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_server_reuses_device_blocks_without_leaking_state(hn, prec):
+    # one slot: every request is admitted after the previous one retired, so its operator and
+    # hierarchy are built in the blocks the previous request of the same level left behind
+    srv = hn.hn_server_create(2 << 30, 1)
+    try:
+        reqs = []
+        for j, L in enumerate([7, 7, 6, 7, 6, 7]):
+            coef, b = I.batch_problem(40 + j, L)
+            reqs.append((hn.hn_mg_submit(srv, L, b, coef if j % 3 else None, prec=prec), L,
+                         coef if j % 3 else None, b))
+        for t, L, coef, b in reqs:
+            status, x, st = hn.hn_mg_poll(srv, t, L, timeout_ns=60_000_000_000)
+            assert status == hn.HN_OK
+            xa, sa, _ = solve(hn, L, b, coef, prec=prec)
+            np.testing.assert_array_equal(x, xa)
+            assert st["cycles"] == sa["cycles"]
+        # inputs are checked when submitted
+        coef, b = I.batch_problem(50, 6)
+        coef = coef.copy()
+        coef[3] = -1.0
+        with pytest.raises(hn.HnError) as e:
+            hn.hn_mg_submit(srv, 6, b, coef, prec=prec)
+        assert e.value.status == hn.HN_ERR_ARG
+        info = hn.hn_server_query(srv)
+        assert info["completed"] == len(reqs) and info["iterations"] > 0
+        assert info["iterate_ns"] > 0 and info["admit_ns"] > 0
+    finally:
+        hn.hn_server_destroy(srv)
+
+
 def test_profiling_times_kernels_without_changing_results(hn):
     L = 9                  # levels 9 and 8 above the tail: separate restriction and prolongation
     b = I.rhs_uniform(L, 21)
