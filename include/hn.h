@@ -240,8 +240,9 @@ typedef struct {
   long long submitted, completed, active, queued;
   long long iterations;        /* scheduler iterations run */
   size_t bytes_in_use, budget;
-  /* worker time (ns) spent building the hierarchies of admitted requests, (re)building the
-   * schedule and starting requests, running scheduler iterations, and retiring requests */
+  /* worker time (ns) spent building the hierarchies of admitted requests (while the running
+   * requests' iteration is on the device), waiting for iterations to finish, retiring requests,
+   * and (re)building the schedule and starting requests */
   long long admit_ns, schedule_ns, iterate_ns, retire_ns;
 } hn_server_info;
 hn_status hn_server_query(hn_server* srv, hn_server_info* info);

@@ -169,6 +169,43 @@ hn_status validate_opts(const hn_mg_opts& o, int L) {
   return HN_OK;
 }
 
+namespace {
+
+// the work lists of Engine::set_members: block row y = level (items and chunks), y = kMaxLevel + 1
+// the fine list
+__global__ void __launch_bounds__(256) k_work_lists(WorkListOut o, const int* slots, const int* fslots,
+                                                    const int* foff, int cap) {
+  const int l = blockIdx.y;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l <= kMaxLevel) {
+    const int n = o.n[l], nt = o.nt[l];
+    if (n == 0) return;
+    const int cpl = (nt + kChunkTiles - 1) / kChunkTiles;
+    for (long long i = i0; i < (long long)n * nt; i += stride) {
+      const int k = (int)(i / nt);
+      o.items[l][i] = make_int2(slots[(size_t)l * cap + k], (int)(i - (long long)k * nt));
+    }
+    for (long long j = i0; j < (long long)n * cpl; j += stride) {
+      const int k = (int)(j / cpl);
+      const int t = (int)(j - (long long)k * cpl) * kChunkTiles;
+      o.chunks[l][j] = make_int4(slots[(size_t)l * cap + k], t, min(kChunkTiles, nt - t), 0);
+    }
+  } else {
+    const int nf = o.nfine;
+    for (long long i = i0; i < foff[nf]; i += stride) {
+      int lo = 0, hi = nf - 1;                      // the member k with foff[k] <= i < foff[k + 1]
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (foff[mid] <= i) lo = mid; else hi = mid - 1;
+      }
+      o.fine[i] = make_int2(fslots[lo], (int)(i - foff[lo]));
+    }
+  }
+}
+
+}  // namespace
+
 hn_status check_band_inputs(int L, const double* cell_coef, unsigned dirichlet_sides) {
   if (dirichlet_sides < 1u || dirichlet_sides > 15u)
     return set_error(HN_ERR_ARG, "dirichlet_sides %u: need a nonzero mask of the 4 sides", dirichlet_sides);
@@ -402,8 +439,11 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
 Engine::~Engine() {
   destroy_graphs();
   for (auto& m : marks_) { cudaEventDestroy(m.b); cudaEventDestroy(m.e); }
+  if (upEv_) cudaEventSynchronize(upEv_);
   if (mem_) cudaFree(mem_);
   if (hActive_) cudaFreeHost(hActive_);
+  if (hStage_) cudaFreeHost(hStage_);
+  if (upEv_) cudaEventDestroy(upEv_);
 }
 
 void Engine::destroy_graphs() {
@@ -460,6 +500,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   const int ctl_groups = (int)((pitch_of(Lmax) / kTile + kSumGroup - 1) / kSumGroup);
   take(sizeof(double) * (size_t)cap * ctl_groups);
   take(sizeof(unsigned) * (size_t)cap);
+  take(sizeof(int) * plan_ints());
   bytes += 256;
   HN_CUDA(cudaMalloc(&mem_, bytes));
   HN_CUDA(cudaMemsetAsync(mem_, 0, bytes, s_));
@@ -482,6 +523,9 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   dLaunches_ = b.take<unsigned long long>(1);
   double* gsum = b.take<double>((size_t)cap * ctl_groups);
   unsigned* gticket = b.take<unsigned>((size_t)cap);
+  dPlan_ = b.take<int>(plan_ints());
+  HN_CUDA(cudaHostAlloc(&hStage_, stage_bytes(), cudaHostAllocDefault));
+  HN_CUDA(cudaEventCreateWithFlags(&upEv_, cudaEventDisableTiming));
   HN_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&hActive_), sizeof(unsigned), cudaHostAllocMapped));
   *hActive_ = 0;
   unsigned* dActive = nullptr;
@@ -516,50 +560,66 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
 
 hn_status Engine::set_members(const std::vector<hn_mg*>& slots) {
   if ((int)slots.size() > cap_) return set_error(HN_ERR_ARG, "too many problems for the engine");
-  std::vector<std::vector<int2>> items(kMaxLevel + 1);
-  std::vector<std::vector<int4>> chunks(kMaxLevel + 1);
-  std::vector<int2> fine;
-  std::vector<int> fine_off(cap_, 0);
-  std::vector<ProblemDev> probs(cap_);
-  std::memset(probs.data(), 0, sizeof(ProblemDev) * cap_);
+  // The work lists hold, per level, the (problem, tile) pairs of every member having that level,
+  // members in slot order; the chunk lists the same in chunks of kChunkTiles tiles; the fine list
+  // each member's tiles of its finest level.  Every member contributes the same tiles to a level,
+  // so the host only ranks the members (O(slots)) and k_work_lists writes the pairs.
+  HN_CUDA(cudaEventSynchronize(upEv_));        // the previous upload has left the staging area
+  char* stage = static_cast<char*>(hStage_);
+  int* h_counts = reinterpret_cast<int*>(stage);                 // kMaxLevel + 2
+  int* h_ccounts = h_counts + (kMaxLevel + 2);                   // kMaxLevel + 1
+  int* h_fine_off = h_ccounts + (kMaxLevel + 1);                 // cap
+  int* h_plan = h_fine_off + cap_;                               // plan_ints()
+  int* h_slots = h_plan;                                         // (kMaxLevel + 1) x cap
+  int* h_fslots = h_slots + (size_t)(kMaxLevel + 1) * cap_;      // cap
+  int* h_foff = h_fslots + cap_;                                 // cap + 1
+  ProblemDev* h_probs = reinterpret_cast<ProblemDev*>(stage + stage_probs_off());
+  std::memset(h_probs, 0, sizeof(ProblemDev) * cap_);
+  std::memset(h_fine_off, 0, sizeof(int) * cap_);
+  WorkListOut o{};
+  int nfine = 0;
+  long long fine_total = 0;
   for (int p = 0; p < (int)slots.size(); ++p) {
     hn_mg* mg = slots[p];
     if (!mg) continue;
     if (mg->L > Lmax_) return set_error(HN_ERR_ARG, "level %d above the engine's %d", mg->L, Lmax_);
-    probs[p] = mg->host;
-    for (int l = mg->coarse; l <= mg->L; ++l) {
-      const int nt = (int)(pitch_of(l) / kTile);
-      for (int t = 0; t < nt; ++t) items[l].push_back(make_int2(p, t));
-      for (int t = 0; t < nt; t += kChunkTiles)
-        chunks[l].push_back(make_int4(p, t, std::min(kChunkTiles, nt - t), 0));
-    }
-    fine_off[p] = (int)fine.size();
-    const int nt = (int)(pitch_of(mg->L) / kTile);
-    for (int t = 0; t < nt; ++t) fine.push_back(make_int2(p, t));
+    h_probs[p] = mg->host;
+    for (int l = mg->coarse; l <= mg->L; ++l) h_slots[(size_t)l * cap_ + o.n[l]++] = p;
+    h_fine_off[p] = (int)fine_total;
+    h_fslots[nfine] = p;
+    h_foff[nfine++] = (int)fine_total;
+    fine_total += pitch_of(mg->L) / kTile;
   }
-  for (int l = 0; l <= kMaxLevel; ++l)
-    if ((long long)items[l].size() > itemCap_[l] || (long long)chunks[l].size() > chunkCap_[l])
-      return set_error(HN_ERR_ARG, "work list of level %d exceeds the engine capacity", l);
-  if ((long long)fine.size() > fineCap_) return set_error(HN_ERR_ARG, "fine work list exceeds capacity");
-  std::vector<int> chunkCounts(kMaxLevel + 1, 0);
+  h_foff[nfine] = (int)fine_total;
+  o.nfine = nfine;
+  long long most = fine_total;
   for (int l = 0; l <= kMaxLevel; ++l) {
-    hCounts_[l] = (int)items[l].size();
-    chunkCounts[l] = (int)chunks[l].size();
-    if (!items[l].empty())
-      HN_CUDA(cudaMemcpyAsync(dItems_[l], items[l].data(), items[l].size() * sizeof(int2),
-                              cudaMemcpyHostToDevice, s_));
-    if (!chunks[l].empty())
-      HN_CUDA(cudaMemcpyAsync(dChunks_[l], chunks[l].data(), chunks[l].size() * sizeof(int4),
-                              cudaMemcpyHostToDevice, s_));
+    o.nt[l] = (int)(pitch_of(l) / kTile);
+    const long long items = (long long)o.n[l] * o.nt[l];
+    const long long chunks = (long long)o.n[l] * ((o.nt[l] + kChunkTiles - 1) / kChunkTiles);
+    if (items > itemCap_[l] || chunks > chunkCap_[l])
+      return set_error(HN_ERR_ARG, "work list of level %d exceeds the engine capacity", l);
+    hCounts_[l] = h_counts[l] = (int)items;
+    h_ccounts[l] = (int)chunks;
+    o.items[l] = dItems_[l];
+    o.chunks[l] = dChunks_[l];
+    most = std::max(most, items);
   }
-  HN_CUDA(cudaMemcpyAsync(dChunkCounts_, chunkCounts.data(), chunkCounts.size() * sizeof(int),
-                          cudaMemcpyHostToDevice, s_));
-  hCounts_[kMaxLevel + 1] = (int)fine.size();
-  if (!fine.empty())
-    HN_CUDA(cudaMemcpyAsync(dFine_, fine.data(), fine.size() * sizeof(int2), cudaMemcpyHostToDevice, s_));
-  HN_CUDA(cudaMemcpyAsync(dCounts_, hCounts_.data(), hCounts_.size() * sizeof(int), cudaMemcpyHostToDevice, s_));
-  HN_CUDA(cudaMemcpyAsync(dFineOff_, fine_off.data(), fine_off.size() * sizeof(int), cudaMemcpyHostToDevice, s_));
-  HN_CUDA(cudaMemcpyAsync(dP_, probs.data(), sizeof(ProblemDev) * cap_, cudaMemcpyHostToDevice, s_));
+  if (fine_total > fineCap_) return set_error(HN_ERR_ARG, "fine work list exceeds capacity");
+  hCounts_[kMaxLevel + 1] = h_counts[kMaxLevel + 1] = (int)fine_total;
+  o.fine = dFine_;
+  HN_CUDA(cudaMemcpyAsync(dCounts_, h_counts, sizeof(int) * (kMaxLevel + 2), cudaMemcpyHostToDevice, s_));
+  HN_CUDA(cudaMemcpyAsync(dChunkCounts_, h_ccounts, sizeof(int) * (kMaxLevel + 1), cudaMemcpyHostToDevice, s_));
+  HN_CUDA(cudaMemcpyAsync(dFineOff_, h_fine_off, sizeof(int) * cap_, cudaMemcpyHostToDevice, s_));
+  HN_CUDA(cudaMemcpyAsync(dPlan_, h_plan, sizeof(int) * plan_ints(), cudaMemcpyHostToDevice, s_));
+  HN_CUDA(cudaMemcpyAsync(dP_, h_probs, sizeof(ProblemDev) * cap_, cudaMemcpyHostToDevice, s_));
+  if (most > 0) {
+    const int gx = (int)std::min<long long>((most + 255) / 256, 1024);
+    k_work_lists<<<dim3((unsigned)gx, kMaxLevel + 2), 256, 0, s_>>>(
+        o, dPlan_, dPlan_ + (size_t)(kMaxLevel + 1) * cap_, dPlan_ + (size_t)(kMaxLevel + 2) * cap_, cap_);
+    HN_CUDA(cudaGetLastError());
+  }
+  HN_CUDA(cudaEventRecord(upEv_, s_));
   // an engine of one problem passes its descriptors to the kernels by value (captured into its
   // graphs, which therefore must be captured again when its member changes)
   if (cap_ == 1) graphsValid_ = false;
@@ -1023,6 +1083,11 @@ hn_status Engine::run_init() {
 }
 
 hn_status Engine::run_iteration(unsigned* active_out) {
+  HN_TRY(launch_iteration());
+  return finish_iteration(active_out);
+}
+
+hn_status Engine::launch_iteration() {
   if (profiling_) {
     clear_marks();
     counting_ = 0;
@@ -1034,8 +1099,12 @@ hn_status Engine::run_iteration(unsigned* active_out) {
   } else {
     if (!graphsValid_) HN_TRY(capture_graphs());
     HN_CUDA(cudaGraphLaunch(gIter_, s_));
-    HN_CUDA(cudaStreamSynchronize(s_));
   }
+  return HN_OK;
+}
+
+hn_status Engine::finish_iteration(unsigned* active_out) {
+  HN_CUDA(cudaStreamSynchronize(s_));
   if (active_out) *active_out = *reinterpret_cast<volatile unsigned*>(hActive_);
   return HN_OK;
 }

@@ -77,6 +77,18 @@ class Engine;
 
 }  // namespace hn
 
+namespace hn {
+// output of the work-list kernel (engine.cu)
+struct WorkListOut {
+  int2* items[kMaxLevel + 1];
+  int4* chunks[kMaxLevel + 1];
+  int2* fine;
+  int n[kMaxLevel + 1];              // members having level l
+  int nt[kMaxLevel + 1];             // tiles of level l
+  int nfine;                         // members
+};
+}  // namespace hn
+
 struct hn_band {
   int L = 0;
   long long n = 0, N = 0, pitch = 0;
@@ -138,6 +150,10 @@ class Engine {
   // host-driven steps (serving / profiling)
   hn_status run_init();
   hn_status run_iteration(unsigned* active_out);
+  // the same in two halves: launch (returns at once unless profiling) and wait for the result,
+  // so that the caller can do host work while the iteration runs
+  hn_status launch_iteration();
+  hn_status finish_iteration(unsigned* active_out);
   hn_status read_states(std::vector<ProbState>& out);
   // the device error word (a bounded wait gave up); reset by start()
   hn_status read_error(int* err);
@@ -203,6 +219,15 @@ class Engine {
   int maxGrid_ = 1;
   std::vector<hn_mg*> members_;
   std::vector<int> hCounts_;
+  // set_members' plan (device) and its pinned staging area: counts, fine offsets, plan, problems
+  int* dPlan_ = nullptr;
+  void* hStage_ = nullptr;
+  cudaEvent_t upEv_ = nullptr;       // the last upload from the staging area
+  size_t plan_ints() const { return (size_t)(kMaxLevel + 2) * cap_ + cap_ + 1; }
+  size_t stage_probs_off() const {
+    return (((size_t)(kMaxLevel + 2) + (kMaxLevel + 1) + cap_ + plan_ints()) * sizeof(int) + 255) & ~size_t(255);
+  }
+  size_t stage_bytes() const { return stage_probs_off() + sizeof(ProblemDev) * cap_; }
   cudaGraphExec_t gSolve_ = nullptr, gInit_ = nullptr, gIter_ = nullptr;
   bool graphsValid_ = false;
   int initLaunches_ = 0, iterLaunches_ = 0, counting_ = 0;

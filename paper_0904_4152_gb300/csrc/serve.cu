@@ -164,18 +164,23 @@ size_t request_bytes(int L, const hn_mg_opts& o) {
 
 void hn_server::run() {
   cudaSetDevice(device);
-  cudaStream_t s = nullptr;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+  // s: the schedule's iterations and the results; s2: building admitted requests' hierarchies
+  // while an iteration of the running requests is on the device
+  cudaStream_t s = nullptr, s2 = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) {
     std::lock_guard<std::mutex> lk(mu);
     worker_error = "stream creation failed";
     stop = true;
     cv_done.notify_all();
+    if (s) cudaStreamDestroy(s);
     return;
   }
   std::unique_ptr<Engine> engine;
   int engine_lmax = 0;
   bool members_dirty = false;
   std::vector<int> fresh;
+  std::vector<hn_mg*> running(max_active, nullptr);   // members of the schedule the engine runs
   auto fail_all = [&](const char* why) {
     std::lock_guard<std::mutex> lk(mu);
     worker_error = why;
@@ -215,19 +220,23 @@ void hn_server::run() {
         }
       }
     }
-    // build the hierarchies of the admitted requests (explicit copies of their inputs)
+    // the next iteration of the running requests ...
+    const bool launched = engine && std::any_of(running.begin(), running.end(), [](hn_mg* m) { return m != nullptr; });
+    if (launched && engine->launch_iteration() != HN_OK) { fail_all(hn_last_error()); break; }
+    // ... while the hierarchies of the admitted requests are built (explicit copies of their
+    // inputs, checked at submit; device blocks from the cache when it has one)
     const long long t_admit0 = now_ns();
+    bool setup_failed = false;
     for (Request* r : admitted) {
-      // inputs were checked at submit; device blocks come from the cache when it has one
       const long long t0 = now_ns();
       const bool has_coef = r->coef.p != nullptr;
       const size_t bb = band_bytes(r->L, has_coef);
       hn_band* A = nullptr;
-      hn_status st = build_band(r->L, has_coef ? r->coef.p : nullptr, r->bc, s, cache.take(bb), &A);
+      hn_status st = build_band(r->L, has_coef ? r->coef.p : nullptr, r->bc, s2, cache.take(bb), &A);
       hn_mg* mg = nullptr;
       if (st == HN_OK) {
         hn_mg_opts o = opts;
-        o.stream = s;
+        o.stream = s2;
         const Params prm = params_from(o);
         const size_t tmp = hierarchy_tmp_bytes(r->L, o.coarse_L, prm.prec, has_coef);
         if (tmp > scratch_bytes) {
@@ -238,21 +247,21 @@ void hn_server::run() {
           else cudaGetLastError();                  // build_hierarchy allocates its own then
         }
         std::unique_ptr<hn_mg> h(new hn_mg());
-        h->stream = s;
-        st = build_hierarchy(A, o, s, h.get(), cache.take(hierarchy_bytes(r->L, o.coarse_L, prm.prec, prm.solver)),
+        h->stream = s2;
+        st = build_hierarchy(A, o, s2, h.get(), cache.take(hierarchy_bytes(r->L, o.coarse_L, prm.prec, prm.solver)),
                              scratch, scratch_bytes);
         h->setup_ns = now_ns() - t0;
         mg = h.release();
       }
-      if (A) {                                      // (later users of the block run on stream s)
+      if (A) {                                      // (later users of the block run on stream s2)
         cache.give(A->mem, bb);
         A->mem = nullptr;
         hn_band_destroy(A);
       }
       if (st == HN_OK) {
         const long long N = N_of(r->L);
-        if (cudaMemcpyAsync(mg->host.b64, r->b.p, (size_t)N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(mg->host.x64, 0, (size_t)N * 8, s) != cudaSuccess)
+        if (cudaMemcpyAsync(mg->host.b64, r->b.p, (size_t)N * 8, cudaMemcpyHostToDevice, s2) != cudaSuccess ||
+            cudaMemsetAsync(mg->host.x64, 0, (size_t)N * 8, s2) != cudaSuccess)
           st = HN_ERR_CUDA;
       }
       std::lock_guard<std::mutex> lk(mu);
@@ -271,12 +280,71 @@ void hn_server::run() {
       fresh.push_back(r->slot);
       members_dirty = true;
     }
+    if (!admitted.empty() && cudaStreamSynchronize(s2) != cudaSuccess) setup_failed = true;
+    if (setup_failed) { fail_all("hierarchy setup failed"); break; }
+    // the iteration's result; retire the requests it finished (their results in one batch of copies)
+    const long long t_wait0 = now_ns();
+    std::vector<ProbState> st;
+    if (launched && (engine->finish_iteration(nullptr) != HN_OK || engine->read_states(st) != HN_OK)) {
+      fail_all(hn_last_error());
+      break;
+    }
+    const long long t_ret0 = now_ns();
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (launched) ++iterations;
+      admit_ns += t_wait0 - t_admit0;
+      iterate_ns += t_ret0 - t_wait0;
+    }
+    std::vector<std::pair<int, Request*>> done_now;
+    if (launched) {
+      std::lock_guard<std::mutex> lk(mu);
+      for (int q = 0; q < max_active; ++q)
+        if (running[q] && st[q].phase == PH_DONE) done_now.emplace_back(q, slots[q]);
+    }
+    bool copy_failed = false;
+    for (auto& [q, r] : done_now) {
+      const long long N = N_of(r->L);
+      if (!r->x.alloc(&host, (size_t)N)) { copy_failed = true; break; }
+      if (st[q].status == HN_OK && st[q].bnorm == 0.0) std::fill(r->x.p, r->x.p + N, 0.0);
+      else if (cudaMemcpyAsync(r->x.p, r->mg->host.x64, (size_t)N * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        copy_failed = true;
+    }
+    if (!done_now.empty() && cudaStreamSynchronize(s) != cudaSuccess) copy_failed = true;
+    if (copy_failed) { fail_all("result copy failed"); break; }
+    for (auto& [q, r] : done_now) {
+      r->b.release();                               // the inputs were consumed at admission
+      r->coef.release();
+      void* hmem = r->mg->mem;                      // kept for the next request of its size
+      const size_t hbytes = r->mg->bytes;
+      r->mg->mem = nullptr;
+      hn_mg_destroy(r->mg);
+      cache.give(hmem, hbytes);
+      running[q] = nullptr;
+      std::lock_guard<std::mutex> lk(mu);
+      r->mg = nullptr;
+      r->status = st[q].status;
+      r->stats.cycles = st[q].cycles;
+      r->stats.outer_iters = st[q].outer_iters;
+      r->stats.inner_cycles = st[q].inner_cycles;
+      r->stats.status = st[q].status;
+      r->stats.relres = st[q].relres;
+      r->t_done = now_ns();
+      r->stats.solve_ns = r->t_done - r->t_submit;
+      r->done = true;
+      in_use -= r->bytes;
+      slots[q] = nullptr;
+      ++completed;
+      members_dirty = true;
+      cv_done.notify_all();
+    }
     const long long t_sched0 = now_ns();
     {
       std::lock_guard<std::mutex> lk(mu);
-      admit_ns += t_sched0 - t_admit0;
+      retire_ns += t_sched0 - t_ret0;
     }
-    // (re)build the engine for the current highest level, then refresh its work lists
+    // the schedule of the next iteration: (re)build the engine for the current highest level,
+    // refresh its work lists, start the new requests
     int lmax = 0;
     std::vector<hn_mg*> members(max_active, nullptr);
     {
@@ -284,7 +352,10 @@ void hn_server::run() {
       for (int q = 0; q < max_active; ++q)
         if (slots[q] && slots[q]->mg) { members[q] = slots[q]->mg; lmax = std::max(lmax, slots[q]->L); }
     }
-    if (lmax == 0) continue;
+    if (lmax == 0) {
+      running = members;
+      continue;
+    }
     if (!engine || lmax > engine_lmax) {
       // a larger level than the schedule covers: wait until the running requests drain
       bool running_old = false;
@@ -330,67 +401,21 @@ void hn_server::run() {
           engine->run_init() != HN_OK) { fail_all(hn_last_error()); break; }
       fresh.erase(std::remove_if(fresh.begin(), fresh.end(), [&](int q) { return members[q] != nullptr; }), fresh.end());
     }
-    unsigned active = 0;
-    const long long t_iter0 = now_ns();
-    if (engine->run_iteration(&active) != HN_OK) { fail_all(hn_last_error()); break; }
-    std::vector<ProbState> st;
-    if (engine->read_states(st) != HN_OK) { fail_all(hn_last_error()); break; }
-    const long long t_ret0 = now_ns();
+    running = members;
     {
       std::lock_guard<std::mutex> lk(mu);
-      ++iterations;
-      schedule_ns += t_iter0 - t_sched0;
-      iterate_ns += t_ret0 - t_iter0;
-    }
-    // retire finished requests
-    for (int q = 0; q < max_active; ++q) {
-      if (!members[q] || st[q].phase != PH_DONE) continue;
-      Request* r;
-      {
-        std::lock_guard<std::mutex> lk(mu);
-        r = slots[q];
-      }
-      const long long N = N_of(r->L);
-      if (!r->x.alloc(&host, (size_t)N)) { fail_all("pinned host memory for a result"); break; }
-      if (st[q].status == HN_OK && st[q].bnorm == 0.0) std::fill(r->x.p, r->x.p + N, 0.0);
-      else if (cudaMemcpyAsync(r->x.p, r->mg->host.x64, (size_t)N * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-               cudaStreamSynchronize(s) != cudaSuccess) { fail_all("result copy failed"); break; }
-      r->b.release();                               // the inputs were consumed at admission
-      r->coef.release();
-      void* hmem = r->mg->mem;                      // kept for the next request of its size
-      const size_t hbytes = r->mg->bytes;
-      r->mg->mem = nullptr;
-      hn_mg_destroy(r->mg);
-      cache.give(hmem, hbytes);
-      std::lock_guard<std::mutex> lk(mu);
-      r->mg = nullptr;
-      r->status = st[q].status;
-      r->stats.cycles = st[q].cycles;
-      r->stats.outer_iters = st[q].outer_iters;
-      r->stats.inner_cycles = st[q].inner_cycles;
-      r->stats.status = st[q].status;
-      r->stats.relres = st[q].relres;
-      r->t_done = now_ns();
-      r->stats.solve_ns = r->t_done - r->t_submit;
-      r->done = true;
-      in_use -= r->bytes;
-      slots[q] = nullptr;
-      ++completed;
-      members_dirty = true;
-      cv_done.notify_all();
-    }
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      retire_ns += now_ns() - t_ret0;
+      schedule_ns += now_ns() - t_sched0;
     }
     if (stop && worker_error.size()) break;
   }
   engine.reset();
   cudaStreamSynchronize(s);
+  cudaStreamSynchronize(s2);
   cache.clear();
   if (scratch) cudaFree(scratch);
   scratch = nullptr;
   scratch_bytes = 0;
+  cudaStreamDestroy(s2);
   cudaStreamDestroy(s);
 }
 
