@@ -55,6 +55,8 @@ def parse():
                          "multigrid / defect correction vs PCG, exact vs CG coarse solve")
     ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load / capacity")
+    ap.add_argument("--serve-requests", type=int, default=1500,
+                    help="requests of the serving sample in the default line (0: none)")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: device memory budget")
     ap.add_argument("--slots", type=int, default=64, help="serve: concurrently active requests")
     ap.add_argument("--swe-grid", type=int, default=0, help="swe: one W x W grid only (default: 256, 1024, 4096)")
@@ -560,6 +562,12 @@ def run_ours(args, rank, world, local, pg):
     if rank == 0 and world == 1 and L <= 11:
         cpu = cpu_baseline(L, 0, 1)
         cpu.pop("seconds")
+    # serving latency on a short sample of the serve workload (after the timed region; the full
+    # run is --workload serve)
+    serve = None
+    if rank == 0 and not args.quick and args.serve_requests > 0:
+        serve = serve_sample(hn, I, args.serve_requests, 0.7, 40.0, 64, 0)
+        serve["note"] = "sample of --workload serve: Poisson arrivals at 0.7 x burst capacity, L 6..11, lognormal a, FP32-inner DC"
 
     if rank == 0:
         line = {
@@ -611,6 +619,8 @@ def run_ours(args, rank, world, local, pg):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
+        if serve is not None:
+            line["serve"] = serve
         print(json.dumps(line), flush=True)
 
 
@@ -704,55 +714,48 @@ def run_batch(args, rank, world, local, pg):
         hn.hn_mg_destroy(mg)
 
 
-def run_serve(args, rank, world, local, pg):
+def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
     """Continuous-batching server: Poisson arrivals, L uniform over {6..11}, seeded lognormal
     coefficients and U[-1,1] right-hand sides (drawn from pools of 4 per level, scaled per
     request: host-side generation would otherwise dominate), FP32-inner DC to 1e-8 under a
-    device-memory budget; reports throughput and p50/p99 latency (submit to completion)."""
+    device-memory budget.  The arrival rate is `load` x the capacity measured on a burst of 120
+    requests of the same mix.  Returns throughput, latency percentiles (submit to completion) and
+    the worker's time split."""
     import threading
     import numpy as np
-    import torch
-    import __graft_entry__ as g
-    from paper_0904_4152_gb300 import hn, inputs as I
-    torch.cuda.set_device(local)
-    if rank == 0:
-        g.build()
-    barrier(pg)
-    hn.lib()
     pools = {}
     for L in range(6, 12):
         pools[L] = [(I.lognormal_coef(L, 500 + 10 * L + k), I.rhs_uniform(L, 600 + 10 * L + k))
                     for k in range(4)]
     opts = hn.hn_mg_opts_default(prec=hn.HN_PREC_FP32_DC)
 
-    def request(seed, L):
-        coef, b = pools[L][seed % 4]
-        scale = 0.5 + (seed % 97) / 97.0
+    def request(sd, L):
+        coef, b = pools[L][sd % 4]
+        scale = 0.5 + (sd % 97) / 97.0
         return coef, b * scale
 
-    srv = hn.hn_server_create(int(args.budget_gb * (1 << 30)), args.slots)
+    srv = hn.hn_server_create(int(budget_gb * (1 << 30)), slots)
     try:
-        # capacity: a burst of requests with the same level mix, all submitted at once
         calib = 120
-        _, lv, sd = I.serve_requests(calib, 1.0, seed=11 + rank)
+        _, lv, sd = I.serve_requests(calib, 1.0, seed=11 + seed)
         t0 = time.perf_counter()
         tickets = []
-        for L, seed in zip(lv, sd):
-            coef, b = request(int(seed), int(L))
+        for L, q in zip(lv, sd):
+            coef, b = request(int(q), int(L))
             tickets.append((hn.hn_mg_submit(srv, int(L), b, coef, opts=opts), int(L)))
         for t, L in tickets:
             status, _, _ = hn.hn_mg_poll(srv, t, L)
             assert status == hn.HN_OK
         capacity = calib / (time.perf_counter() - t0)
-        rate = args.load * capacity
-        arrivals, levels, seeds = I.serve_requests(args.requests, rate, seed=7 + rank)
-        sub = [None] * args.requests
-        res = [None] * args.requests
+        rate = load * capacity
+        arrivals, levels, seeds = I.serve_requests(requests, rate, seed=7 + seed)
+        sub = [None] * requests
+        res = [None] * requests
         err = []
 
         def submitter():
             start = time.perf_counter()
-            for i in range(args.requests):
+            for i in range(requests):
                 dt = start + arrivals[i] - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
@@ -766,7 +769,7 @@ def run_serve(args, rank, world, local, pg):
         th = threading.Thread(target=submitter)
         t_start = time.perf_counter()
         th.start()
-        for i in range(args.requests):
+        for i in range(requests):
             while sub[i] is None and th.is_alive():
                 time.sleep(0.0005)
             if sub[i] is None:
@@ -780,22 +783,41 @@ def run_serve(args, rank, world, local, pg):
         hn.hn_server_destroy(srv)
     done = [r for r in res if r is not None]
     lat = np.array([r[1] for r in done if r[0] == hn.HN_OK])
-    ok = len(lat)
-    dofs = sum(((1 << int(L)) + 1) ** 2 for L, r in zip(levels, res) if r is not None and r[0] == hn.HN_OK)
     wall = t_end - t_start
+    dofs = sum(((1 << int(L)) + 1) ** 2 for L, r in zip(levels, res) if r is not None and r[0] == hn.HN_OK)
+    return {"requests": requests, "completed_ok": len(lat), "errors": err[:3], "offered_load": load,
+            "arrival_rate_per_s": rate, "capacity_per_s": capacity,
+            "requests_per_s": len(lat) / wall, "dof_per_s": dofs / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "scheduler_iterations": info["iterations"],
+            "worker_s": {k: info[k + "_ns"] * 1e-9 for k in ("admit", "schedule", "iterate", "retire")},
+            "relres_max": max(r[2] for r in done if r[0] == hn.HN_OK)}
+
+
+def run_serve(args, rank, world, local, pg):
+    """The serving workload (serve_sample) on its own: one JSON line with p50/p99 and throughput."""
+    import torch
+    import __graft_entry__ as g
+    from paper_0904_4152_gb300 import hn, inputs as I
+    torch.cuda.set_device(local)
+    if rank == 0:
+        g.build()
+    barrier(pg)
+    hn.lib()
+    r = serve_sample(hn, I, args.requests, args.load, args.budget_gb, args.slots, rank)
     if rank == 0:
         print(json.dumps({
             "metric": "serve p50/p99 latency and throughput (Poisson arrivals, L 6..11, FP32-inner DC)",
-            "value": ok / wall, "unit": "requests/s", "n_gpus": world, "requests": args.requests,
-            "completed_ok": ok, "errors": err[:3], "higher_is_better": True, "data": "synthetic",
+            "value": r["requests_per_s"], "unit": "requests/s", "n_gpus": world, "requests": args.requests,
+            "completed_ok": r["completed_ok"], "errors": r["errors"], "higher_is_better": True,
+            "data": "synthetic",
             "config": {"workload": "serve-poisson-L6to11-lognormal", "offered_load": args.load,
-                       "arrival_rate_per_s": rate, "capacity_per_s": capacity,
+                       "arrival_rate_per_s": r["arrival_rate_per_s"], "capacity_per_s": r["capacity_per_s"],
                        "budget_gb": args.budget_gb, "slots": args.slots},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
-                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-            "dof_per_s": dofs / wall, "scheduler_iterations": info["iterations"],
-            "worker_s": {k: info[k + "_ns"] * 1e-9 for k in ("admit", "schedule", "iterate", "retire")},
-            "relres_max": max(r[2] for r in done if r[0] == hn.HN_OK)}), flush=True)
+            "latency_ms": r["latency_ms"], "dof_per_s": r["dof_per_s"],
+            "scheduler_iterations": r["scheduler_iterations"], "worker_s": r["worker_s"],
+            "relres_max": r["relres_max"]}), flush=True)
 
 
 def main():
