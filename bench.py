@@ -14,7 +14,7 @@ measurement through the same C call with host buffers (host->device copy of b an
 copy of x inside the timed region).  `roofline` times the dominant kernel of the headline solve
 with events around each of its launches (a separate profiled pass over K solves), against the
 measured HBM copy bandwidth.  `cpu_baseline` times the FP64 CPU oracle on one full solve of the
-same problem on one host core.  With N > 1 (torchrun) every rank solves its own independent
+same problem on one host core (and, under `all_cores`, one independent solve per host core).  With N > 1 (torchrun) every rank solves its own independent
 problem (weak scaling, no collective on the data path); value = all ranks' DOF / slowest rank.
 """
 import argparse
@@ -180,6 +180,39 @@ def cpu_baseline(L, seed, prec):
             "sample": "one full %s solve to 1e-8 at L=%d (%d DOF), %.2f s, %d cycles"
                       % ("FP32-inner DC" if prec == 1 else "FP64 MG", L, N, dt, st["cycles"]),
             "seconds": dt}
+
+
+def _oracle_warm(_):
+    import oracle as O
+    from paper_0904_4152_gb300 import inputs as I   # noqa: F401
+    O.lib()
+    return os.getpid()
+
+
+def _oracle_solve(task):
+    L, seed, prec = task
+    import oracle as O
+    from paper_0904_4152_gb300 import inputs as I
+    b = I.rhs_uniform(L, seed)
+    t0 = time.perf_counter()
+    O.mg_solve(L, b, prec=prec, tol=TOL)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(L, seed, prec):
+    """The same oracle, unchanged, on every host core: one independent solve per core in spawned
+    processes (spawned, not forked: this process has a CUDA context)."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(n) as pool:
+        pool.map(_oracle_warm, range(n))           # imports and library loads outside the timing
+        t0 = time.perf_counter()
+        pool.map(_oracle_solve, [(L, seed + k, prec) for k in range(n)], chunksize=1)
+        wall = time.perf_counter() - t0
+    N = ((1 << L) + 1) ** 2
+    return {"value": n * N / wall, "unit": "DOF/s", "cores": n, "kind": "oracle",
+            "sample": "%d independent %s solves to 1e-8 at L=%d, one per core, %.2f s wall"
+                      % (n, "FP32-inner DC" if prec == 1 else "FP64 MG", L, wall)}
 
 
 def run_reference(args, rank, world, pg):
@@ -562,6 +595,8 @@ def run_ours(args, rank, world, local, pg):
     if rank == 0 and world == 1 and L <= 11:
         cpu = cpu_baseline(L, 0, 1)
         cpu.pop("seconds")
+        if not args.quick:
+            cpu["all_cores"] = cpu_baseline_all_cores(L, 0, 1)
     # serving latency on a short sample of the serve workload (after the timed region; the full
     # run is --workload serve)
     serve = None
