@@ -39,8 +39,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--level", type=int, default=L_BENCH,
-                    help="refinement level (default 10, the benchmark workload; others for profiling)")
+    ap.add_argument("--level", type=int, default=None,
+                    help="refinement level (default 10, the benchmark workload, and 12 for the "
+                         "kernels workload; others for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="timed solves only (no e2e, profiled pass or CPU baseline): for ncu captures")
     ap.add_argument("--host-loop", action="store_true",
@@ -270,7 +271,7 @@ def run_kernels(args, rank, local):
     torch.cuda.set_device(local)
     g.build()
     peak, kind = measured_peak_gbs()
-    band = band_kernels(hn, torch.cuda.current_stream(), peak, L=args.level if args.level != L_BENCH else 12)
+    band = band_kernels(hn, torch.cuda.current_stream(), peak, L=args.level if args.level is not None else 12)
     if rank == 0:
         print(json.dumps({"metric": "band kernels alone, HBM GB/s", "peak": peak, "peak_kind": kind,
                           "kernels": band}), flush=True)
@@ -474,7 +475,7 @@ def run_ours(args, rank, world, local, pg):
         g.build()
     barrier(pg, dev)
     hn.lib()
-    L = args.level
+    L = args.level if args.level is not None else L_BENCH
     N = ((1 << L) + 1) ** 2
     stream = torch.cuda.current_stream(dev)
     b_host = I.rhs_uniform(L, rank)                       # rank r solves its own problem
