@@ -417,7 +417,8 @@ def run_swe(args, rank, local):
 def run_solvers(args, rank, local):
     """Solve time to 1e-8 of each outer solver (multigrid / defect correction, CG preconditioned by
     one V cycle), coarse solver (exact, CG) and precision, at L = 10 (a = 1 and a lognormal field)
-    and L = 12 (a = 1); graph solves, L2 flushed between solves, CUDA events."""
+    and L = 12 (a = 1, and the lognormal field seed 0 with right-hand side seed 1); graph solves,
+    L2 flushed between solves, CUDA events."""
     import numpy as np
     import torch
     import __graft_entry__ as g
@@ -427,9 +428,9 @@ def run_solvers(args, rank, local):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     rows = []
-    for L, lognormal in ((10, False), (10, True), (12, False)):
+    for L, lognormal, rhs_seed in ((10, False, 0), (10, True, 0), (12, False, 0), (12, True, 1)):
         coef = I.lognormal_coef(L, 0) if lognormal else None
-        b = torch.from_numpy(I.rhs_uniform(L, 0)).cuda()
+        b = torch.from_numpy(I.rhs_uniform(L, rhs_seed)).cuda()
         x = torch.zeros_like(b)
         A = hn.hn_band_create(L, coef)
         for prec in (hn.HN_PREC_FP64, hn.HN_PREC_FP32_DC, hn.HN_PREC_FP16BAND_DC):
@@ -449,7 +450,7 @@ def run_solvers(args, rank, local):
                         torch.cuda.synchronize()
                         assert status == hn.HN_OK
                         ms.append(e0.elapsed_time(e1))
-                    rows.append({"L": L, "coef": "lognormal" if lognormal else "a=1",
+                    rows.append({"L": L, "coef": "lognormal" if lognormal else "a=1", "rhs_seed": rhs_seed,
                                  "prec": ["fp64", "fp32", "fp16band"][prec],
                                  "solver": "pcg" if solver == hn.HN_SOLVER_PCG else "mg",
                                  "coarse": "cg" if coarse == hn.HN_COARSE_CG else "exact",
