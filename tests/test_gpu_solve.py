@@ -255,6 +255,37 @@ def test_server_reuses_device_blocks_without_leaking_state(hn, prec):
         hn.hn_server_destroy(srv)
 
 
+def test_server_under_a_tight_budget_waits_and_releases_cached_blocks(hn):
+    # a budget of 1.5 requests: the head of the queue waits for memory, and the blocks that the
+    # finished request left in the cache are released to admit it; results stay those of the
+    # solves alone
+    L = 8
+    A = hn.hn_band_create(L)
+    mg = hn.hn_mg_setup(A, prec=1)
+    hier = hn.hn_mg_device_bytes(mg)
+    hn.hn_mg_destroy(mg)
+    hn.hn_band_destroy(A)
+    N = ((1 << L) + 1) ** 2
+    pitch = -(-N // 128) * 128
+    request = hier + 9 * pitch * 8 + (1 << L) * (1 << L) * 8 + 4096   # as the server counts it
+    srv = hn.hn_server_create(int(1.5 * request), 4)
+    try:
+        reqs = []
+        for j in range(4):
+            coef, b = I.batch_problem(60 + j, L)
+            reqs.append((hn.hn_mg_submit(srv, L, b, coef, prec=1), coef, b))
+        for t, coef, b in reqs:
+            status, x, st = hn.hn_mg_poll(srv, t, L, timeout_ns=60_000_000_000)
+            assert status == hn.HN_OK
+            xa, sa, _ = solve(hn, L, b, coef, prec=1)
+            np.testing.assert_array_equal(x, xa)
+            assert st["cycles"] == sa["cycles"]
+        info = hn.hn_server_query(srv)
+        assert info["completed"] == 4 and info["bytes_in_use"] == 0
+    finally:
+        hn.hn_server_destroy(srv)
+
+
 def test_profiling_times_kernels_without_changing_results(hn):
     L = 9                  # levels 9 and 8 above the tail: separate restriction and prolongation
     b = I.rhs_uniform(L, 21)
