@@ -198,6 +198,28 @@ def test_batch_alone_equals_in_mix(hn, prec):
             hn.hn_mg_destroy(m)
 
 
+def test_fp16_large_level_alone_equals_in_batch(hn):
+    # alone, an engine of one problem passes its descriptors by value (and at L = 10 its levels
+    # take the bulk-sized grids); in a batch the same kernels walk the work lists: same bits
+    levels = [10, 6]
+    mgs, bs = [], []
+    for j, L in enumerate(levels):
+        coef, b = I.batch_problem(70 + j, L)
+        A = hn.hn_band_create(L, coef)
+        mgs.append(hn.hn_mg_setup(A, prec=2))
+        hn.hn_band_destroy(A)
+        bs.append(b)
+    try:
+        xs, stats, status = hn.hn_mg_solve_batch(mgs, levels, bs)
+        assert status == hn.HN_OK
+        xa, sa, _ = hn.hn_mg_solve(mgs[0], levels[0], bs[0])
+        np.testing.assert_array_equal(xs[0], xa)
+        assert stats[0]["cycles"] == sa["cycles"]
+    finally:
+        for m in mgs:
+            hn.hn_mg_destroy(m)
+
+
 @pytest.mark.parametrize("slots", [4, 1])
 def test_server_results_match_alone(hn, slots):
     # one slot: the engine of one problem passes descriptors by value and recaptures its graphs
