@@ -1,0 +1,40 @@
+"""The JSON line of bench.py's reference arm (the oracle on the host, no GPU) and the argument
+defaults that the benchmark contract fixes."""
+import contextlib
+import io
+import json
+import sys
+
+import bench
+
+
+def test_defaults_keep_the_contract():
+    sys_argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        a = bench.parse()
+    finally:
+        sys.argv = sys_argv
+    assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1 and a.impl == "ours"
+    assert a.level is None and a.workload == "solve"
+
+
+def test_reference_arm_prints_one_line_with_the_contract_keys():
+    class Args:
+        steps, warmup = 1, 0
+    out = io.StringIO()
+    with contextlib.redirect_stdout(out):
+        bench.run_reference(Args, 0, 1, None)
+    lines = [l for l in out.getvalue().splitlines() if l.strip()]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference"
+    assert j["metric"] == "MG Poisson DOF/s to 1e-8 (mixed vs FP64)" and j["unit"] == "DOF/s"
+    assert j["higher_is_better"] is True and j["n_gpus"] == 1 and j["steps"] == 1
+    assert j["config"]["workload"] == bench.WORKLOAD and j["config"]["dof"] == (2 ** 10 + 1) ** 2
+    assert j["value"] > 0 and j["ms_per_step"] > 0
+    e2e = j["e2e"]
+    assert e2e["value"] == j["value"] and e2e["unit"] == j["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    cb = j["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == j["value"] and cb["sample"]
