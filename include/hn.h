@@ -225,8 +225,10 @@ hn_status hn_mg_get_inner_bands(const hn_mg* mg, int level, void* bands_out, flo
 hn_status hn_server_create(size_t budget_bytes, int max_active, hn_server** out);
 
 /* Queue a solve of level L with cell coefficients (NULL = 1) and right-hand side b (host, N
- * doubles); both are copied.  *ticket identifies the request.  HN_ERR_BUDGET if the request
- * alone exceeds the budget; HN_ERR_ARG on bad input. */
+ * doubles); both are copied (into page-locked buffers the server recycles).  *ticket identifies
+ * the request.  HN_ERR_BUDGET if the request alone exceeds the budget; HN_ERR_ARG on bad input,
+ * coefficients included (checked here, in the caller's thread, as hn_band_create_bc checks them);
+ * HN_ERR_OOM if no page-locked host memory is left. */
 hn_status hn_mg_submit(hn_server* srv, int L, const double* cell_coef, const double* b,
                        const hn_mg_opts* opts, unsigned long long* ticket);
 
