@@ -13,9 +13,15 @@ written between timed steps (outside the events) to flush the 129 MB L2.  `e2e` 
 measurement through the same C call with host buffers (host->device copy of b and device->host
 copy of x inside the timed region).  `roofline` times the dominant kernel of the headline solve
 with events around each of its launches (a separate profiled pass over K solves), against the
-measured HBM copy bandwidth.  `cpu_baseline` times the FP64 CPU oracle on one full solve of the
-same problem on one host core (and, under `all_cores`, one independent solve per host core).  With N > 1 (torchrun) every rank solves its own independent
-problem (weak scaling, no collective on the data path); value = all ranks' DOF / slowest rank.
+measured HBM copy bandwidth.  Beside the headline the line carries the band kernels alone at
+L = 12, the L = 12 lognormal configuration (`l12_lognormal`: FP64 MG, FP32-inner and FP16-band
+DC), the 256-problem batch (`batch256`), a sample of the serving workload (`serve`), and at the
+end the L = 10 solves per precision (`mixed`, `fp64`, `fp16band`, `pcg_fp32`), each with its
+relative L2 difference from the oracle solved to 1e-13.  `cpu_baseline` times the FP64 CPU oracle
+on one full solve of the same problem on one host core (and, under `all_cores`, one independent
+solve per host core); that leg also evaluates this run's results with the oracle.  With N > 1
+(torchrun) every rank solves its own independent problem (weak scaling, no collective on the data
+path); value = all ranks' DOF / slowest rank.
 """
 import argparse
 import json
@@ -31,6 +37,27 @@ sys.path.insert(0, ROOT)
 L_BENCH = 10
 TOL = 1e-8
 WORKLOAD = "poisson-q1-L10-const-coef-uniform-rhs"
+
+
+def bench_config(L=L_BENCH):
+    """The workload of the default line (both arms print the same dict)."""
+    N = ((1 << L) + 1) ** 2
+    return {"workload": WORKLOAD if L == L_BENCH else "poisson-q1-L%d-const-coef-uniform-rhs" % L,
+            "L": L, "dof": N, "coef": "a=1", "rhs": "U[-1,1] interior, seed=rank",
+            "cycle": "V(2,2) jacobi omega=0.7", "coarse_L": 2, "tol": TOL,
+            "prec": "fp32-inner defect correction, inner 1e-2",
+            "l2_between_steps": "flushed (512 MiB write)"}
+
+
+def sig(v, d=4):
+    """Round floats (recursively) to d significant digits: keeps the line short."""
+    if isinstance(v, float):
+        return float("%.*g" % (d, v)) if v == v and abs(v) != float("inf") else v
+    if isinstance(v, dict):
+        return {k: sig(x, d) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [sig(x, d) for x in v]
+    return v
 
 
 def parse():
@@ -233,11 +260,10 @@ def run_reference(args, rank, world, pg):
             "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "L": L_BENCH, "dof": N,
-                                            "prec": "fp32-inner defect correction",
-                                            "solver": "CPU oracle (plain C++), 1 core"},
+            "data": "synthetic", "config": bench_config(),
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d full FP32-inner DC solves at L=%d" % (len(times), L_BENCH)},
+                             "sample": "%d full FP32-inner DC solves to 1e-8 at L=%d on one core "
+                                       "(CPU oracle, plain C++)" % (len(times), L_BENCH)},
             "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -464,6 +490,143 @@ def run_solvers(args, rank, local):
                           "l2_between_steps": "flushed (512 MiB write)", "rows": rows}), flush=True)
 
 
+def l12_solves(hn, I, stream, flush, dev, steps, warmup):
+    """The L = 12 configuration: lognormal a (sigma 1, correlation length 0.1, field seed 0),
+    b ~ U[-1,1] seed 1; FP64 multigrid, FP32-inner and FP16-band-inner defect correction; CUDA
+    events per solve, L2 flushed between solves.  Returns the rows and the solutions (host)."""
+    import torch
+    L = 12
+    N = ((1 << L) + 1) ** 2
+    coef = I.lognormal_coef(L, 0)
+    b = torch.from_numpy(I.rhs_uniform(L, 1)).to(dev)
+    x = torch.zeros_like(b)
+    A = hn.hn_band_create(L, coef)
+    rows, sols = {}, {}
+    try:
+        for name, prec in (("fp64", hn.HN_PREC_FP64), ("fp32dc", hn.HN_PREC_FP32_DC),
+                           ("fp16dc", hn.HN_PREC_FP16BAND_DC)):
+            mg = hn.hn_mg_setup(A, prec=prec, stream=stream.cuda_stream)
+            try:
+                for _ in range(warmup):
+                    hn.hn_mg_solve(mg, L, b, x)
+                ms = []
+                for _ in range(steps):
+                    flush.fill_(1)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    _, st, status = hn.hn_mg_solve(mg, L, b, x)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    assert status == hn.HN_OK, st
+                    ms.append(e0.elapsed_time(e1))
+            finally:
+                hn.hn_mg_destroy(mg)
+            t = statistics.median(ms)
+            rows[name] = {"dof_per_s": N / (t * 1e-3), "ms": t, "cycles": st["cycles"],
+                          "outer": st["outer_iters"], "relres": st["relres"]}
+            sols[name] = x.cpu().numpy().copy()
+    finally:
+        hn.hn_band_destroy(A)
+    return rows, sols, (L, coef, b.cpu().numpy())
+
+
+def batch256_solves(hn, I, stream, flush, dev, steps, warmup):
+    """The batched configuration: 256 problems, L ~ U{5..9} (seed 0), lognormal a (seeds 1000 + j),
+    b ~ U[-1,1] (seeds 2000 + j), FP32-inner defect correction, one batched solve per step against
+    the same problems solved one after the other.  Returns the row and a sample of solutions."""
+    import torch
+    count = 256
+    levels = [int(v) for v in I.batch_levels(count, seed=0)]
+    mgs, bs, xs, probs = [], [], [], []
+    try:
+        for j, L in enumerate(levels):
+            coef, b = I.batch_problem(j, L)
+            A = hn.hn_band_create(L, coef)
+            try:
+                mgs.append(hn.hn_mg_setup(A, prec=hn.HN_PREC_FP32_DC, stream=stream.cuda_stream))
+            finally:
+                hn.hn_band_destroy(A)
+            probs.append((L, coef, b))
+            bs.append(torch.from_numpy(b).to(dev))
+            xs.append(torch.zeros_like(bs[-1]))
+        dofs = sum(((1 << L) + 1) ** 2 for L in levels)
+        stats = {}
+
+        def batched():
+            _, st, status = hn.hn_mg_solve_batch(mgs, levels, bs, xs)
+            assert status == hn.HN_OK
+            stats["b"] = st
+
+        def looped():
+            for mg, L, b, x in zip(mgs, levels, bs, xs):
+                _, st, status = hn.hn_mg_solve(mg, L, b, x)
+                assert status == hn.HN_OK
+
+        def timed(fn, n, w):
+            for _ in range(w):
+                fn()
+            ms = []
+            for _ in range(n):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(e0.elapsed_time(e1))
+            return statistics.median(ms)
+
+        t_loop = timed(looped, 1, 1)
+        t_b = timed(batched, steps, warmup)            # last: xs hold the batched results
+        cyc = [s["cycles"] for s in stats["b"]]
+        sample = list(range(0, count, 16))
+        sols = {j: (probs[j], xs[j].cpu().numpy().copy()) for j in sample}
+        row = {"dof_per_s": dofs / (t_b * 1e-3), "ms": t_b, "dof": dofs,
+               "over_one_by_one": t_loop / t_b, "cycles_min": min(cyc), "cycles_max": max(cyc)}
+        return row, sols
+    finally:
+        for m in mgs:
+            hn.hn_mg_destroy(m)
+
+
+def oracle_leg(L, sols10, l12, batch):
+    """CPU-baseline leg: the oracle, as it stands, timed on the host (one core, then every core),
+    and the oracle's view of the GPU results of this run: the relative L2 difference of each L = 10
+    solution from the oracle solved to 1e-13, and the relative residual of the L = 12 and sampled
+    batch results under the oracle's FP64 operator."""
+    import numpy as np
+    import oracle as O
+    from paper_0904_4152_gb300 import inputs as I
+    cpu = cpu_baseline(L, 0, 1)
+    cpu.pop("seconds")
+    try:
+        cpu["all_cores"] = cpu_baseline_all_cores(L, 0, 1)
+    except Exception as e:                            # a side measurement: never costs the line
+        cpu["all_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    err = {}
+    b = I.rhs_uniform(L, 0)
+    xs, _ = O.mg_solve(L, b, tol=1e-13)
+    A = O.assemble(L)
+    nb = np.linalg.norm(b)
+    err["l10"] = {k: {"l2_diff": float(np.linalg.norm(x - xs) / np.linalg.norm(xs)),
+                      "relres": float(np.linalg.norm(O.defect(L, A, b, x)) / nb)}
+                  for k, x in sols10.items()}
+    if l12 is not None:
+        rows, sols, (L12, coef, b12) = l12
+        A12 = O.assemble(L12, coef)
+        nb = np.linalg.norm(b12)
+        err["l12_relres"] = {k: float(np.linalg.norm(O.defect(L12, A12, b12, x)) / nb)
+                             for k, x in sols.items()}
+    if batch is not None:
+        worst = 0.0
+        for (Lj, coef, bj), x in batch.values():
+            Aj = O.assemble(Lj, coef)
+            worst = max(worst, float(np.linalg.norm(O.defect(Lj, Aj, bj, x)) / np.linalg.norm(bj)))
+        err["batch_relres_max"] = worst
+        err["batch_sample"] = len(batch)
+    return cpu, err
+
+
 def run_ours(args, rank, world, local, pg):
     import numpy as np
     import torch
@@ -520,11 +683,16 @@ def run_ours(args, rank, world, local, pg):
         ms = [s.elapsed_time(e) for s, e in ev]
         return ms, stats, launches
 
+    sols10 = {}
     with ClockSampler(local) as clk:
         ms_mixed, st_mixed, launches = timed(mgs["mixed"], args.steps, args.warmup)
+    sols10["mixed"] = x.cpu().numpy().copy()
     ms_fp64, st_fp64, _ = timed(mgs["fp64"], args.steps, args.warmup)
+    sols10["fp64"] = x.cpu().numpy().copy()
     ms_fp16, st_fp16, _ = timed(mgs["fp16band"], args.steps, args.warmup)
+    sols10["fp16band"] = x.cpu().numpy().copy()
     ms_pcg, st_pcg, _ = timed(mgs["pcg_fp32"], args.steps, args.warmup)
+    sols10["pcg_fp32"] = x.cpu().numpy().copy()
     total_pcg = max_over_ranks(sum(ms_pcg), pg, dev)
     # the paper's performance configuration: Dirichlet at x = 0, 1, free Neumann at y = 0, 1
     A_lr = hn.hn_band_create_bc(L, None, hn.HN_DIRICHLET_LEFT | hn.HN_DIRICHLET_RIGHT)
@@ -590,82 +758,83 @@ def run_ours(args, rank, world, local, pg):
         by_class[t["name"]] += t["total_ms"]
     prof_total = sum(by_class.values())
 
-    # band kernels alone at L=12 (data >> L2): band-SpMV, defect and Jacobi HBM GB/s per precision
-    band = band_kernels(hn, stream, peak) if rank == 0 else {}
+    # the larger configurations on rank 0: band kernels alone at L = 12 (data >> L2), the L = 12
+    # lognormal solves, the 256-problem batch
+    band = l12 = batch = None
+    if rank == 0:
+        band = band_kernels(hn, stream, peak)
+        k_steps, k_warm = max(1, min(args.steps, 5)), max(1, min(args.warmup, 2))
+        l12 = l12_solves(hn, I, stream, flush, dev, k_steps, k_warm)
+        batch = batch256_solves(hn, I, stream, flush, dev, max(1, min(args.steps, 10)), k_warm)
+    for m in mgs.values():
+        hn.hn_mg_destroy(m)
 
-    cpu = None
+    # CPU-baseline leg (rank 0 at N = 1): the oracle timed, and its view of this run's results
+    cpu = oracle_err = None
     if rank == 0 and world == 1 and L <= 11:
-        cpu = cpu_baseline(L, 0, 1)
-        cpu.pop("seconds")
-        if not args.quick:
-            try:
-                cpu["all_cores"] = cpu_baseline_all_cores(L, 0, 1)
-            except Exception as e:                    # a side measurement: never costs the line
-                cpu["all_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
+        try:
+            cpu, oracle_err = oracle_leg(L, sols10, l12, {} if batch is None else batch[1])
+        except Exception as e:                        # a side measurement: never costs the line
+            cpu = {"error": "%s: %s" % (type(e).__name__, e)}
     # serving latency on a short sample of the serve workload (after the timed region; the full
     # run is --workload serve)
     serve = None
-    if rank == 0 and not args.quick and args.serve_requests > 0:
+    if rank == 0 and args.serve_requests > 0:
         try:
             serve = serve_sample(hn, I, args.serve_requests, 0.7, 40.0, 64, 0)
-            serve["note"] = ("sample of --workload serve: Poisson arrivals at 0.7 x burst capacity, "
-                             "L 6..11, lognormal a, FP32-inner DC")
         except Exception as e:                        # a side measurement: never costs the line
             serve = {"error": "%s: %s" % (type(e).__name__, e)}
 
     if rank == 0:
+        cfg = bench_config(L)
+        cfg["setup_ms"] = {"band": 1e3 * setup_band_s, "hierarchy_mixed": st_mixed["setup_ns"] / 1e6,
+                           "hierarchy_fp64": st_fp64["setup_ns"] / 1e6}
+        err10 = (oracle_err or {}).get("l10", {})
+
+        def solve_row(ms_total, st, name, extra=None):
+            r = {"dof_per_s": world * N * args.steps / (ms_total * 1e-3), "ms": ms_total / args.steps,
+                 "cycles": st["cycles"], "outer": st["outer_iters"], "relres": st["relres"]}
+            if name in err10:
+                r["oracle_l2_diff"] = err10[name]["l2_diff"]
+                r["oracle_relres"] = err10[name]["relres"]
+            if extra:
+                r.update(extra)
+            return r
+
         line = {
             "metric": "MG Poisson DOF/s to 1e-8 (mixed vs FP64)",
             "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_mixed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if L == L_BENCH else "poisson-q1-L%d-const-coef-uniform-rhs" % L,
-                       "L": L, "dof": N, "coef": "a=1",
-                       "rhs": "U[-1,1] interior, seed=rank", "cycle": "V(2,2) jacobi omega=0.7",
-                       "coarse_L": 2, "tol": TOL, "prec": "fp32-inner defect correction, inner 1e-2",
-                       "l2_between_steps": "flushed (512 MiB write)",
-                       "setup_ms": {"band": 1e3 * setup_band_s,
-                                    "hierarchy_mixed": st_mixed["setup_ns"] / 1e6,
-                                    "hierarchy_fp64": st_fp64["setup_ns"] / 1e6}},
-            "mixed": {"dof_per_s": value, "ms_per_solve": total_mixed / args.steps,
-                      "cycles": st_mixed["cycles"], "outer_iters": st_mixed["outer_iters"],
-                      "relres": st_mixed["relres"]},
-            "fp64": {"dof_per_s": fp64_value, "ms_per_solve": total_fp64 / args.steps,
-                     "cycles": st_fp64["cycles"], "relres": st_fp64["relres"]},
-            "fp16band": {"dof_per_s": fp16_value, "ms_per_solve": total_fp16 / args.steps,
-                         "cycles": st_fp16["cycles"], "outer_iters": st_fp16["outer_iters"],
-                         "relres": st_fp16["relres"]},
-            "mixed_over_fp64": value / fp64_value,
-            "pcg_fp32": {"solver": "FP64 CG preconditioned by one FP32 V(2,2) cycle",
-                         "dof_per_s": world * N * args.steps / (total_pcg * 1e-3),
-                         "ms_per_solve": total_pcg / args.steps, "cg_steps": st_pcg["outer_iters"],
-                         "cycles": st_pcg["cycles"], "relres": st_pcg["relres"]},
-            "mixed_neumann_dirichlet": {"dirichlet": "x=0, x=1", "free_neumann": "y=0, y=1",
-                                        "rhs": "U[-1,1] off the Dirichlet sides, seed=rank",
-                                        "dof_per_s": world * N * args.steps / (total_lr * 1e-3),
-                                        "ms_per_solve": total_lr / args.steps,
-                                        "cycles": st_lr["cycles"], "outer_iters": st_lr["outer_iters"],
-                                        "relres": st_lr["relres"]},
+            "dtype": "f64+f32", "data": "synthetic", "gpu_launches": launches,
+            "config": cfg, "clocks": clk.summary(),
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": N * 8,
                     "d2h_bytes_per_step": N * 8},
             "roofline": {"bound": "hbm", "kernel": "%s L%d" % (dom["name"], dom["level"]),
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                         "traffic_note": "ncu DRAM read+write per node of this kernel at L=12 "
-                                         "(data >> L2) x nodes of one launch",
                          "bytes_per_launch": dom["bytes_per_launch"],
                          "avg_launch_us": avg_s * 1e6, "launches": dom["launches"],
                          "share_of_profiled": dom["total_ms"] / prof_total if prof_total else None},
-            "kernel_share": {k: v / prof_total for k, v in sorted(by_class.items())} if prof_total else {},
-            "band_kernels_L12": band,
-            "gpu_launches": launches,
-            "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "kernel_share": dict(sorted(((k, v / prof_total) for k, v in by_class.items()),
+                                        key=lambda kv: -kv[1])[:6]) if prof_total else {},
+            "band_kernels_L12_frac": {p: {o: r["frac"] for o, r in row.items()} for p, row in band.items()},
         }
         if serve is not None:
             line["serve"] = serve
-        print(json.dumps(line), flush=True)
+        if batch is not None:
+            line["batch256"] = dict(batch[0], oracle_relres_max_sampled=(oracle_err or {}).get("batch_relres_max"))
+        if l12 is not None:
+            rel12 = (oracle_err or {}).get("l12_relres", {})
+            line["l12_lognormal"] = {k: dict(r, oracle_relres=rel12.get(k)) for k, r in l12[0].items()}
+        line["mixed_neumann_dirichlet"] = solve_row(total_lr, st_lr, "")
+        line["pcg_fp32"] = solve_row(total_pcg, st_pcg, "pcg_fp32")
+        line["fp16band"] = solve_row(total_fp16, st_fp16, "fp16band")
+        line["fp64"] = solve_row(total_fp64, st_fp64, "fp64")
+        line["mixed"] = solve_row(total_mixed, st_mixed, "mixed")
+        line["mixed_over_fp64"] = value / fp64_value
+        print(json.dumps(sig(line)), flush=True)
 
 
 def run_batch(args, rank, world, local, pg):
@@ -733,13 +902,7 @@ def run_batch(args, rank, world, local, pg):
     tb = max_over_ranks(sum(ms_b), pg, dev)
     value = world * dofs * len(ms_b) / (tb * 1e-3)
     loop_value = world * dofs * len(ms_l) / (max_over_ranks(sum(ms_l), pg, dev) * 1e-3)
-    # parity sample: the oracle's FP64 operator evaluates a few batched results
-    import oracle as O
-    worst = 0.0
-    for j in range(0, count, 32):
-        x = xs[j].cpu().numpy()
-        A64 = O.assemble(levels[j], coefs[j])
-        worst = max(worst, np.linalg.norm(O.defect(levels[j], A64, bh[j], x)) / np.linalg.norm(bh[j]))
+    cpu = batch_oracle_leg(levels, coefs, bh, xs) if rank == 0 and world == 1 else None
     if rank == 0:
         cyc = [s["cycles"] for s in stats["b"]]
         print(json.dumps({
@@ -753,57 +916,92 @@ def run_batch(args, rank, world, local, pg):
                        "l2_between_steps": "flushed (512 MiB write)"},
             "per_problem_loop_dof_per_s": loop_value, "batched_over_loop": value / loop_value,
             "inner_cycles": {"min": min(cyc), "max": max(cyc)},
-            "oracle_relres_max_sampled": worst, "clocks": clk.summary()}), flush=True)
+            "cpu_baseline": cpu, "clocks": clk.summary()}), flush=True)
     for mg in mgs:
         hn.hn_mg_destroy(mg)
 
 
+def batch_oracle_leg(levels, coefs, bh, xs, every=32):
+    """CPU-baseline leg of the batch workload: the oracle, as it stands, on one host core solving a
+    sample of the batch's problems one after the other (DOF/s), and the relative residual of the
+    same problems' batched GPU results under the oracle's FP64 operator."""
+    import numpy as np
+    import oracle as O
+    O.lib()
+    sample = list(range(0, len(levels), every))
+    worst, dofs, secs = 0.0, 0, 0.0
+    for j in sample:
+        L = levels[j]
+        A64 = O.assemble(L, coefs[j])
+        x = xs[j].cpu().numpy()
+        worst = max(worst, float(np.linalg.norm(O.defect(L, A64, bh[j], x)) / np.linalg.norm(bh[j])))
+        t0 = time.perf_counter()
+        O.mg_solve(L, bh[j], coef=coefs[j], prec=1, tol=TOL)
+        secs += time.perf_counter() - t0
+        dofs += ((1 << L) + 1) ** 2
+    return {"value": dofs / secs, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": "problems %s of the batch (every %dth), FP32-inner DC to 1e-8 one after the "
+                      "other, %.2f s" % (",".join(map(str, sample)), every, secs),
+            "oracle_relres_max_sampled": worst}
+
+
 def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
-    """Continuous-batching server: Poisson arrivals, L uniform over {6..11}, seeded lognormal
-    coefficients and U[-1,1] right-hand sides (drawn from pools of 4 per level, scaled per
-    request: host-side generation would otherwise dominate), FP32-inner DC to 1e-8 under a
+    """Continuous-batching server: Poisson arrivals, L uniform over {6..11}, every request with its
+    own seeded lognormal coefficient field and U[-1,1] right-hand side (generated ahead of its
+    arrival by a pool of host threads, outside the latency), FP32-inner DC to 1e-8 under a
     device-memory budget.  The arrival rate is `load` x the capacity measured on a burst of 120
-    requests of the same mix.  Returns throughput, latency percentiles (submit to completion) and
-    the worker's time split."""
+    requests of the same mix.  Returns throughput, latency percentiles (submit to completion, also
+    per tenth of the run in arrival order) and the worker's time split."""
+    import concurrent.futures as cf
     import threading
     import numpy as np
-    pools = {}
-    for L in range(6, 12):
-        pools[L] = [(I.lognormal_coef(L, 500 + 10 * L + k), I.rhs_uniform(L, 600 + 10 * L + k))
-                    for k in range(4)]
     opts = hn.hn_mg_opts_default(prec=hn.HN_PREC_FP32_DC)
 
-    def request(sd, L):
-        coef, b = pools[L][sd % 4]
-        scale = 0.5 + (sd % 97) / 97.0
-        return coef, b * scale
+    def make(sd, L):
+        return I.lognormal_coef(L, int(sd)), I.rhs_uniform(L, int(sd) + 1_000_000)
 
+    pool = cf.ThreadPoolExecutor(max_workers=max(2, min(8, (os.cpu_count() or 4) // 2)))
     srv = hn.hn_server_create(int(budget_gb * (1 << 30)), slots)
     try:
         calib = 120
         _, lv, sd = I.serve_requests(calib, 1.0, seed=11 + seed)
+        inputs = [make(int(q) + 500_000, int(L)) for L, q in zip(lv, sd)]
         t0 = time.perf_counter()
         tickets = []
-        for L, q in zip(lv, sd):
-            coef, b = request(int(q), int(L))
+        for L, (coef, b) in zip(lv, inputs):
             tickets.append((hn.hn_mg_submit(srv, int(L), b, coef, opts=opts), int(L)))
         for t, L in tickets:
             status, _, _ = hn.hn_mg_poll(srv, t, L)
             assert status == hn.HN_OK
         capacity = calib / (time.perf_counter() - t0)
+        del inputs
         rate = load * capacity
         arrivals, levels, seeds = I.serve_requests(requests, rate, seed=7 + seed)
+        ahead = 48                                     # requests generated ahead of their arrival
+        futs = {}
+        issued = [0]
+
+        def prefetch(upto):
+            while issued[0] < min(upto, requests):
+                k = issued[0]
+                futs[k] = pool.submit(make, seeds[k], int(levels[k]))
+                issued[0] += 1
+
+        prefetch(ahead)
         sub = [None] * requests
+        late = np.zeros(requests)
         res = [None] * requests
         err = []
 
         def submitter():
             start = time.perf_counter()
             for i in range(requests):
+                prefetch(i + ahead)
+                coef, b = futs.pop(i).result()
                 dt = start + arrivals[i] - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
-                coef, b = request(int(seeds[i]), int(levels[i]))
+                late[i] = max(0.0, -dt)
                 try:
                     sub[i] = hn.hn_mg_submit(srv, int(levels[i]), b, coef, opts=opts)
                 except hn.HnError as e:
@@ -825,18 +1023,22 @@ def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
         info = hn.hn_server_query(srv)
     finally:
         hn.hn_server_destroy(srv)
-    done = [r for r in res if r is not None]
-    lat = np.array([r[1] for r in done if r[0] == hn.HN_OK])
+        pool.shutdown(wait=False, cancel_futures=True)
+    ok = [i for i, r in enumerate(res) if r is not None and r[0] == hn.HN_OK]
+    lat = np.array([res[i][1] for i in ok])
     wall = t_end - t_start
-    dofs = sum(((1 << int(L)) + 1) ** 2 for L, r in zip(levels, res) if r is not None and r[0] == hn.HN_OK)
+    dofs = sum(((1 << int(levels[i])) + 1) ** 2 for i in ok)
+    tenth = [float(np.percentile(lat[k * len(lat) // 10:(k + 1) * len(lat) // 10], 99))
+             for k in range(10)] if len(lat) >= 10 else []
     return {"requests": requests, "completed_ok": len(lat), "errors": err[:3], "offered_load": load,
             "arrival_rate_per_s": rate, "capacity_per_s": capacity,
             "requests_per_s": len(lat) / wall, "dof_per_s": dofs / wall,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
-                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-            "scheduler_iterations": info["iterations"],
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
+                           "argmax": int(ok[int(lat.argmax())]), "p99_by_tenth": tenth},
+            "submit_late_ms_p99": float(np.percentile(late, 99) * 1e3),
             "worker_s": {k: info[k + "_ns"] * 1e-9 for k in ("admit", "schedule", "iterate", "retire")},
-            "relres_max": max(r[2] for r in done if r[0] == hn.HN_OK)}
+            "relres_max": max(res[i][2] for i in ok)}
 
 
 def run_serve(args, rank, world, local, pg):
@@ -860,7 +1062,7 @@ def run_serve(args, rank, world, local, pg):
                        "arrival_rate_per_s": r["arrival_rate_per_s"], "capacity_per_s": r["capacity_per_s"],
                        "budget_gb": args.budget_gb, "slots": args.slots},
             "latency_ms": r["latency_ms"], "dof_per_s": r["dof_per_s"],
-            "scheduler_iterations": r["scheduler_iterations"], "worker_s": r["worker_s"],
+            "submit_late_ms_p99": r["submit_late_ms_p99"], "worker_s": r["worker_s"],
             "relres_max": r["relres_max"]}), flush=True)
 
 

@@ -199,14 +199,19 @@ hn_status hn_mg_apply(hn_mg* mg, hn_op op, int level, int inner, const void* in1
  * CUDA graph in global mode, where cudaMalloc is not permitted; processes that hand out their
  * whole device-memory plan up front; latency-critical paths where cudaMalloc / cudaFree would
  * synchronize the device).  Computes r = b - A x and ||r||_2 for an operator from hn_band_create.
- * x, b, r: device pointers to N doubles, 16-byte aligned, caller-owned; norm: device pointer to one
- * double.  Runs on stream (cudaStream_t, NULL = default stream) and returns without waiting.
+ * x, b, r: device pointers to N doubles, 16-byte aligned, caller-owned; r must not overlap x or b
+ * (it is written while other threads still read their stencil neighbourhoods); norm: device
+ * pointer to one double.  The operator's device must be the current device.  Runs on stream
+ * (cudaStream_t, NULL = the legacy default stream) and returns without waiting; a caller that
+ * launches while another thread captures a graph in global mode must pass a stream created with
+ * cudaStreamNonBlocking, since the legacy default stream synchronizes with every blocking stream.
  * The only temporary (one partial sum per 128-node tile) is a fixed device array inside the library
  * (512 KiB, held by every GPU that loads the library until exit), so at most 8,388,608 nodes
  * (level 11) are accepted; larger operators get HN_ERR_ARG.  The call allocates nothing.  The first
  * call on a device looks up that array's address and should come before any stream capture.  All
  * calls share the array: calls that overlap on the GPU (e.g. on two streams) race and must be
- * ordered by the caller.  Errors: HN_ERR_ARG, HN_ERR_CUDA. */
+ * ordered by the caller.  Errors: HN_ERR_ARG (null or misaligned pointer, r overlapping x or b,
+ * the operator on another device, too many nodes), HN_ERR_CUDA. */
 hn_status hn_band_defect_norm_static(const hn_band* A, const double* x, const double* b, double* r,
                                      double* norm, void* stream);
 

@@ -231,6 +231,7 @@ hn_status build_band(int L, const double* cell_coef, unsigned bc, cudaStream_t s
                      hn_band** out) {
   std::unique_ptr<hn_band> A(new hn_band());
   A->L = L;
+  HN_CUDA(cudaGetDevice(&A->device));
   A->bc = bc;
   A->n = n_of(L);
   A->N = N_of(L);

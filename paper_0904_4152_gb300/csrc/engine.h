@@ -96,6 +96,7 @@ struct hn_band {
   double* band[9] = {};
   double* coef = nullptr;   // device cell coefficients, nullptr for a = 1
   unsigned bc = 15u;        // Dirichlet sides (HN_DIRICHLET_*); the others are free Neumann
+  int device = 0;           // CUDA device the bands live on (current at creation)
   ~hn_band();
 };
 

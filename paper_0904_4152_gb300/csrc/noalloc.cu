@@ -147,6 +147,20 @@ extern "C" hn_status hn_band_defect_norm_static(const hn_band* A, const double* 
     return set_error(HN_ERR_ARG, "x, b and r must be 16-byte aligned device pointers");
   if ((reinterpret_cast<uintptr_t>(norm) & 7))
     return set_error(HN_ERR_ARG, "norm must be an 8-byte aligned device pointer");
+  {   // r is written while neighbouring warps still read x and b over the stencil's reach
+    const uintptr_t r0 = reinterpret_cast<uintptr_t>(r), r1 = r0 + (uintptr_t)A->N * 8;
+    for (const double* v : {x, b}) {
+      const uintptr_t v0 = reinterpret_cast<uintptr_t>(v), v1 = v0 + (uintptr_t)A->N * 8;
+      if (r0 < v1 && v0 < r1) return set_error(HN_ERR_ARG, "r must not overlap x or b");
+    }
+  }
+  {
+    int dev = 0;
+    HN_CUDA(cudaGetDevice(&dev));
+    if (dev != A->device)
+      return set_error(HN_ERR_ARG, "the operator lives on device %d, the current device is %d",
+                       A->device, dev);
+  }
   if (A->N > kStaticMaxNodes)
     return set_error(HN_ERR_ARG,
                      "%lld nodes exceed the static scratch of this entry point (at most %lld nodes, "
@@ -157,7 +171,9 @@ extern "C" hn_status hn_band_defect_norm_static(const hn_band* A, const double* 
   const int tiles = (int)((A->N + kTile - 1) / kTile);
   BandPtrs64c bp{};
   for (int k = 0; k < 9; ++k) bp.p[k] = A->band[k];
-  const int grid = std::max(1, std::min((tiles + 7) / 8, sm_count() * 4));
+  int sms = 0;
+  HN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, A->device));
+  const int grid = std::max(1, std::min((tiles + 7) / 8, std::max(sms, 1) * 4));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_defect_static<<<grid, 256, 0, s>>>(bp, A->L, A->N, x, b, r, scratch, tiles);
   HN_CUDA(cudaGetLastError());

@@ -122,6 +122,32 @@ struct BlockCache {
     blocks.clear();
     bytes = 0;
   }
+  // free cached blocks, largest first, until at most `target` bytes stay cached; one block of
+  // each size in `keep` (the blocks the next request will take) is freed last
+  void release_to(size_t target, size_t keep0, size_t keep1) {
+    bool kept0 = false, kept1 = false;
+    std::vector<std::pair<size_t, void*>> spared;
+    while (bytes > target && !blocks.empty()) {
+      auto it = std::prev(blocks.end());
+      if ((!kept0 && it->first == keep0) || (!kept1 && it->first == keep1)) {
+        if (it->first == keep0 && !kept0) kept0 = true; else kept1 = true;
+        spared.emplace_back(*it);
+        bytes -= it->first;                         // set aside, counted again below
+        blocks.erase(it);
+        continue;
+      }
+      cudaFree(it->second);
+      bytes -= it->first;
+      blocks.erase(it);
+    }
+    for (auto& kv : spared) { blocks.emplace(kv.first, kv.second); bytes += kv.first; }
+    while (bytes > target && !blocks.empty()) {    // still above: the spared blocks too
+      auto it = std::prev(blocks.end());
+      cudaFree(it->second);
+      bytes -= it->first;
+      blocks.erase(it);
+    }
+  }
 };
 
 }  // namespace
@@ -204,11 +230,19 @@ void hn_server::run() {
           if (free_slot == slots.end()) break;
           Request* r = queue.front();
           if (in_use + r->bytes + cache.bytes + scratch_bytes > budget) {
-            // cached blocks count against the budget: give them back before waiting
-            cache.clear();
-            if (scratch) cudaFree(scratch);
-            scratch = nullptr;
-            scratch_bytes = 0;
+            // cached blocks count against the budget: give back only as many as the head of the
+            // queue needs (largest first, the blocks it will reuse last), then the scratch block;
+            // freeing every cached block would make the next requests of each size allocate anew
+            const Params hp = params_from(opts);
+            const size_t hb = hierarchy_bytes(r->L, opts.coarse_L, hp.prec, hp.solver);
+            const size_t bb = band_bytes(r->L, r->coef.p != nullptr);
+            const size_t need = in_use + r->bytes + scratch_bytes;
+            cache.release_to(need < budget ? budget - need : 0, hb, bb);
+            if (in_use + r->bytes + cache.bytes + scratch_bytes > budget) {
+              if (scratch) cudaFree(scratch);
+              scratch = nullptr;
+              scratch_bytes = 0;
+            }
           }
           if (in_use + r->bytes > budget) break;    // FIFO: the head waits for memory
           queue.pop_front();

@@ -75,16 +75,6 @@ def test_g2_config_L10(hn, prec):
     assert oracle_relres(L, None, b, x) <= RELRES
 
 
-def test_g2_config_L12_fp16(hn):
-    # the largest configuration: L=12 lognormal field, FP16-band inner multigrid
-    L = 12
-    coef = I.lognormal_coef(L, 0)
-    b = I.rhs_uniform(L, 1)
-    x, st, status = solve(hn, L, b, coef, prec=2)
-    assert status == hn.HN_OK
-    assert oracle_relres(L, coef, b, x) <= RELRES
-
-
 def test_device_and_host_pointers_agree(hn):
     torch = pytest.importorskip("torch")
     L = 7

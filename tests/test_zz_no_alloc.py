@@ -1,11 +1,12 @@
-"""The allocation-free defect/norm entry point (hn_band_defect_norm_static) against the solver's own
-defect kernel (hn_mg_apply with HN_OP_DEFECT on an FP64 hierarchy of the same operator).
+"""The allocation-free defect/norm entry point (hn_band_defect_norm_static) against the oracle's
+defect of the same operator, and against the solver's own defect kernel.
 
 The entry point serves callers that cannot allocate device memory when they call it (code that
 runs while another thread captures a CUDA graph in global mode, processes whose device memory is
 fully planned up front, latency-critical paths where cudaMalloc would synchronize the device).
 Its scratch is a fixed array inside the library that every call reuses, so the test checks two
-calls in a row with different data, and that operators larger than the array's limit are refused.
+calls in a row with different data, that the device's free memory does not change across a call,
+and that operators larger than the array's limit and outputs overlapping the inputs are refused.
 This file is collected last so that a run stopping at the first failure has run every other test.
 """
 import numpy as np
@@ -19,7 +20,7 @@ pytestmark = pytest.mark.gpu
 U64 = 2.0 ** -53
 
 
-def test_static_defect_norm_matches_solver_kernel_twice():
+def test_static_defect_norm_matches_the_oracle_twice():
     hn = require_gpu()
     import torch
     L = 9
@@ -31,17 +32,31 @@ def test_static_defect_norm_matches_solver_kernel_twice():
         N = hn.hn_band_nodes(A)
         r = torch.empty(N, dtype=torch.float64, device="cuda")
         nrm = torch.empty(1, dtype=torch.float64, device="cuda")
+        # a first call loads the kernels and looks up the scratch address (lazy module loading
+        # maps the module's fixed array then); the calls measured below find both in place
+        z = torch.zeros(N, dtype=torch.float64, device="cuda")
+        hn.hn_band_defect_norm_static(A, z, z, r, nrm)
         for call, seed in enumerate((1, 2)):
             x = rand_interior(L, 10 + seed)
             b = rand_interior(L, 20 + seed)
-            hn.hn_band_defect_norm_static(A, torch.from_numpy(x).cuda(), torch.from_numpy(b).cuda(),
-                                          r, nrm)
+            xd, bd = torch.from_numpy(x).cuda(), torch.from_numpy(b).cuda()
             torch.cuda.synchronize()
-            ref, ref_norm = hn.hn_mg_apply(mg, hn.HN_OP_DEFECT, L, 0, x, b, want_norm=True)
+            free0 = torch.cuda.mem_get_info()[0]
+            alloc0 = torch.cuda.memory_allocated()
+            hn.hn_band_defect_norm_static(A, xd, bd, r, nrm)
+            torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info()[0] == free0, call
+            assert torch.cuda.memory_allocated() == alloc0, call
             got = r.cpu().numpy()
+            ref = O.defect(L, B, b, x)
             tol = 16 * U64 * (abs_spmv(L, B, x) + np.abs(b))
             assert np.all(np.abs(got - ref) <= tol), call
+            ref_norm = np.linalg.norm(ref)
             assert abs(nrm.item() - ref_norm) <= 1e-12 * ref_norm, call
+            # the solver's own defect kernel on the same operator gives the same values
+            k, k_norm = hn.hn_mg_apply(mg, hn.HN_OP_DEFECT, L, 0, x, b, want_norm=True)
+            assert np.all(np.abs(got - k) <= tol), call
+            assert abs(nrm.item() - k_norm) <= 1e-12 * ref_norm, call
     finally:
         hn.hn_mg_destroy(mg)
         hn.hn_band_destroy(A)
@@ -55,9 +70,28 @@ def test_static_defect_norm_refuses_operators_beyond_its_scratch():
     try:
         N = hn.hn_band_nodes(A)
         v = torch.zeros(N, dtype=torch.float64, device="cuda")
+        w = torch.zeros(N, dtype=torch.float64, device="cuda")
         nrm = torch.empty(1, dtype=torch.float64, device="cuda")
         with pytest.raises(hn.HnError) as e:
-            hn.hn_band_defect_norm_static(A, v, v, v, nrm)
+            hn.hn_band_defect_norm_static(A, v, v, w, nrm)
         assert e.value.status == hn.HN_ERR_ARG and "static scratch" in str(e.value)
+    finally:
+        hn.hn_band_destroy(A)
+
+
+def test_static_defect_norm_refuses_an_output_overlapping_its_inputs():
+    hn = require_gpu()
+    import torch
+    L = 5
+    A = hn.hn_band_create(L)
+    try:
+        N = hn.hn_band_nodes(A)
+        x = torch.zeros(N, dtype=torch.float64, device="cuda")
+        b = torch.zeros(N, dtype=torch.float64, device="cuda")
+        nrm = torch.empty(1, dtype=torch.float64, device="cuda")
+        for r in (x, b):
+            with pytest.raises(hn.HnError) as e:
+                hn.hn_band_defect_norm_static(A, x, b, r, nrm)
+            assert e.value.status == hn.HN_ERR_ARG and "overlap" in str(e.value)
     finally:
         hn.hn_band_destroy(A)
