@@ -945,46 +945,137 @@ def batch_oracle_leg(levels, coefs, bh, xs, every=32):
             "oracle_relres_max_sampled": worst}
 
 
+def _gen_init(cores):
+    """Worker of the serving input generators: keep off the cores of the benchmark process."""
+    try:
+        os.sched_setaffinity(0, cores)
+    except (AttributeError, OSError):
+        pass
+
+
+def _gen_request(task):
+    """One request's seeded coefficient field and right-hand side, left in a shared-memory block
+    (coefficients first) so that the benchmark process maps them without a copy."""
+    from multiprocessing import shared_memory
+    import numpy as np
+    from paper_0904_4152_gb300 import inputs as I
+    L, sd = task
+    coef = I.lognormal_coef(L, sd)
+    b = I.rhs_uniform(L, sd + 1_000_000)
+    shm = shared_memory.SharedMemory(create=True, size=(coef.size + b.size) * 8)
+    a = np.ndarray(coef.size + b.size, dtype=np.float64, buffer=shm.buf)
+    a[:coef.size] = coef
+    a[coef.size:] = b
+    name = shm.name
+    del a
+    shm.close()
+    return name, coef.size, b.size
+
+
+class RequestInputs:
+    """Seeded per-request inputs of the serving workload, generated ahead of their arrival by a
+    pool of spawned processes on the host cores the benchmark process does not use (this process
+    keeps `keep` cores for itself and the server's worker thread)."""
+
+    def __init__(self, keep=4):
+        import multiprocessing as mp
+        n = os.cpu_count() or 1
+        self.saved = None
+        try:
+            self.saved = os.sched_getaffinity(0)
+        except (AttributeError, OSError):
+            pass
+        own = set(range(min(keep, n)))
+        gen = set(range(min(keep, n), n)) or own
+        # one BLAS thread per generator process (the processes already fill the cores)
+        env = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
+        os.environ.update({k: "1" for k in env})
+        try:
+            self.pool = mp.get_context("spawn").Pool(max(1, len(gen)), initializer=_gen_init,
+                                                     initargs=(gen,))
+        finally:
+            for k, v in env.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        try:
+            os.sched_setaffinity(0, own)
+        except (AttributeError, OSError):
+            pass
+        self.pending = {}
+
+    def request(self, key, L, seed):
+        self.pending[key] = self.pool.apply_async(_gen_request, ((int(L), int(seed)),))
+
+    def take(self, key):
+        """(coefficients, right-hand side, release) of a requested input."""
+        from multiprocessing import shared_memory
+        import numpy as np
+        name, nc, nb = self.pending.pop(key).get()
+        shm = shared_memory.SharedMemory(name=name)
+        a = np.ndarray(nc + nb, dtype=np.float64, buffer=shm.buf)
+
+        def release():
+            shm.close()
+            shm.unlink()
+        return a[:nc], a[nc:], release
+
+    def close(self):
+        for k in list(self.pending):
+            try:
+                _, _, rel = self.take(k)
+                rel()
+            except Exception:
+                pass
+        self.pool.terminate()
+        if self.saved is not None:
+            try:
+                os.sched_setaffinity(0, self.saved)
+            except OSError:
+                pass
+
+
 def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
     """Continuous-batching server: Poisson arrivals, L uniform over {6..11}, every request with its
     own seeded lognormal coefficient field and U[-1,1] right-hand side (generated ahead of its
-    arrival by a pool of host threads, outside the latency), FP32-inner DC to 1e-8 under a
-    device-memory budget.  The arrival rate is `load` x the capacity measured on a burst of 120
-    requests of the same mix.  Returns throughput, latency percentiles (submit to completion, also
-    per tenth of the run in arrival order) and the worker's time split."""
-    import concurrent.futures as cf
+    arrival by host processes on cores apart from this process, outside the latency),
+    FP32-inner DC to 1e-8 under a device-memory budget.  The arrival rate is `load` x the capacity
+    measured on a burst of 120 requests of the same mix.  Returns throughput, latency percentiles
+    (submit to completion, also per tenth of the run in arrival order) and the worker's time
+    split."""
     import threading
     import numpy as np
     opts = hn.hn_mg_opts_default(prec=hn.HN_PREC_FP32_DC)
-
-    def make(sd, L):
-        return I.lognormal_coef(L, int(sd)), I.rhs_uniform(L, int(sd) + 1_000_000)
-
-    pool = cf.ThreadPoolExecutor(max_workers=max(2, min(8, (os.cpu_count() or 4) // 2)))
-    srv = hn.hn_server_create(int(budget_gb * (1 << 30)), slots)
+    gen = RequestInputs()
+    srv = None
     try:
+        srv = hn.hn_server_create(int(budget_gb * (1 << 30)), slots)
         calib = 120
         _, lv, sd = I.serve_requests(calib, 1.0, seed=11 + seed)
-        inputs = [make(int(q) + 500_000, int(L)) for L, q in zip(lv, sd)]
+        for k, (L, q) in enumerate(zip(lv, sd)):
+            gen.request(("c", k), L, int(q) + 500_000)
+        inputs = [gen.take(("c", k)) for k in range(calib)]
         t0 = time.perf_counter()
         tickets = []
-        for L, (coef, b) in zip(lv, inputs):
+        for L, (coef, b, _) in zip(lv, inputs):
             tickets.append((hn.hn_mg_submit(srv, int(L), b, coef, opts=opts), int(L)))
         for t, L in tickets:
             status, _, _ = hn.hn_mg_poll(srv, t, L)
             assert status == hn.HN_OK
         capacity = calib / (time.perf_counter() - t0)
+        for _, _, rel in inputs:
+            rel()
         del inputs
         rate = load * capacity
         arrivals, levels, seeds = I.serve_requests(requests, rate, seed=7 + seed)
-        ahead = 48                                     # requests generated ahead of their arrival
-        futs = {}
+        ahead = 96                                     # requests generated ahead of their arrival
         issued = [0]
 
         def prefetch(upto):
             while issued[0] < min(upto, requests):
                 k = issued[0]
-                futs[k] = pool.submit(make, seeds[k], int(levels[k]))
+                gen.request(k, levels[k], seeds[k])
                 issued[0] += 1
 
         prefetch(ahead)
@@ -997,7 +1088,7 @@ def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
             start = time.perf_counter()
             for i in range(requests):
                 prefetch(i + ahead)
-                coef, b = futs.pop(i).result()
+                coef, b, release = gen.take(i)
                 dt = start + arrivals[i] - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
@@ -1007,6 +1098,8 @@ def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
                 except hn.HnError as e:
                     err.append(str(e))
                     return
+                finally:
+                    release()                          # the server copied the inputs
 
         th = threading.Thread(target=submitter)
         t_start = time.perf_counter()
@@ -1022,8 +1115,9 @@ def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
         t_end = time.perf_counter()
         info = hn.hn_server_query(srv)
     finally:
-        hn.hn_server_destroy(srv)
-        pool.shutdown(wait=False, cancel_futures=True)
+        if srv is not None:
+            hn.hn_server_destroy(srv)
+        gen.close()
     ok = [i for i, r in enumerate(res) if r is not None and r[0] == hn.HN_OK]
     lat = np.array([res[i][1] for i in ok])
     wall = t_end - t_start
