@@ -1,8 +1,10 @@
 /* hn_tune.h -- launch-shape tuning of the hn solver (performance only; results do not change).
  *
- * The V-cycle schedule runs levels above `tail_level` as one launch per step over the device work
- * list, and levels coarse_L..tail_level of every problem inside one fused launch of one
- * thread-block cluster (`cluster` blocks of 512 threads) per problem.  Inside that launch the
+ * The V-cycle schedule runs levels coarse_L..tail_level of every problem inside one fused launch
+ * of one thread-block cluster (`cluster` blocks of 512 threads) per problem, levels
+ * tail_level+1..mid in two persistent cooperative launches per cycle (one down, one up; their
+ * steps separated by grid-wide barriers), and levels above mid as one launch per step over the
+ * device work list.  Inside that launch the
  * smallest levels live in the shared memory of the cluster's first block; the levels between
  * them and tail_level either live in the distributed shared memory of the whole cluster (`dsm`,
  * when they fit) or are read through L2.  The best split depends on the levels and the batch;
@@ -31,22 +33,27 @@ typedef struct {
                        post-smoothing step (one pass instead of two, each lane forming the
                        prolonged values of its three stencil rows); 0: separate kernels (default:
                        the fused pass measured slower, its extra work outweighing the pass saved) */
+  int mid;          /* levels tail_level+1 .. mid run in the persistent kernels (0, or any value
+                       <= tail_level: none); not combined with staged or fuse_up, which are forms
+                       of the per-step launches (default 10) */
 } hn_tuning;
 
 /* Set / read the launch shape used by mg's later solves.  HN_ERR_ARG on values out of range. */
 hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t);
 hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t);
 
-/* Time `reps` solves of b (host vector, N doubles) for every candidate shape (tail_level from
- * coarse_L to min(L, 9), cluster 1..16) and keep the fastest; the candidate timings are returned
- * in `times_ms` (may be NULL, capacity `cap` entries, row-major tail_level x 5 cluster sizes) and
- * the chosen shape in *best.  The solution is unchanged by the shape. */
+/* Time `reps` solves of b (host vector, N doubles) for every candidate shape (persistent kernels
+ * off and on (mid 0 and 10), tail_level from coarse_L to min(L, 9), cluster 1..16) and keep the
+ * fastest; the candidate timings are returned in `times_ms` (may be NULL, capacity `cap` entries,
+ * row-major 2 mid settings x tail_level x 5 cluster sizes) and the chosen shape in *best.  The
+ * solution is unchanged by the shape. */
 hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, double* times_ms,
                          int cap);
 
-/* The same for a batch (hn_mg_solve_batch over mgs[0..count)): candidates tail_level coarse_L..8,
- * cluster 1, 2, 4; the fastest shape is stored in every member and used by later batch solves of
- * the same members (a batch whose members carry no common tuned shape picks one by its size). */
+/* The same for a batch (hn_mg_solve_batch over mgs[0..count)): candidates mid 0 and 10,
+ * tail_level coarse_L..8, cluster 1, 2, 4; the fastest shape is stored in every member and used by
+ * later batch solves of the same members (a batch whose members carry no common tuned shape picks
+ * one by its size). */
 hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const* b, int reps,
                                hn_tuning* best);
 

@@ -72,7 +72,7 @@ Tuning batch_tuning(const std::vector<hn_mg*>& list) {
     same = same && mg->tuned && mg->tuning.tail_level == list[0]->tuning.tail_level &&
            mg->tuning.cluster == list[0]->tuning.cluster && mg->tuning.pdl == list[0]->tuning.pdl &&
            mg->tuning.staged == list[0]->tuning.staged && mg->tuning.dsm == list[0]->tuning.dsm &&
-           mg->tuning.fuse_up == list[0]->tuning.fuse_up;
+           mg->tuning.fuse_up == list[0]->tuning.fuse_up && mg->tuning.mid == list[0]->tuning.mid;
   if (same) return list[0]->tuning;
   Tuning t;
   const int n = (int)list.size();
@@ -215,7 +215,8 @@ hn_status hn_mg_solve(hn_mg* mg, const double* b, double* x, int x_is_guess, int
   HN_TRY(e.read_states(st));
   int derr = 0;
   HN_TRY(e.read_error(&derr));
-  if (derr) return set_error(HN_ERR_CUDA, "a bounded device wait for a bulk copy gave up");
+  if (derr) return set_error(HN_ERR_CUDA, derr == 3 ? "a grid barrier of the persistent kernels timed out"
+                                                  : "a bounded device wait for a bulk copy gave up");
   if (st[0].status != HN_ERR_ARG) {
     if (st[0].status == HN_OK && st[0].bnorm == 0.0) HN_CUDA(cudaMemsetAsync(P.x64, 0, (size_t)N * 8, s));
     HN_TRY(copy_out(x, P.x64, N, device_ptrs, s));
@@ -293,7 +294,8 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
   HN_TRY(e.read_states(st));
   int derr = 0;
   HN_TRY(e.read_error(&derr));
-  if (derr) return set_error(HN_ERR_CUDA, "a bounded device wait for a bulk copy gave up");
+  if (derr) return set_error(HN_ERR_CUDA, derr == 3 ? "a grid barrier of the persistent kernels timed out"
+                                                  : "a bounded device wait for a bulk copy gave up");
   hn_status first_bad = HN_OK;
   for (int j = 0; j < count; ++j) {
     ProblemDev& P = list[j]->host;
@@ -402,6 +404,7 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
   if (t->staged != 0 && t->staged != 1) return set_error(HN_ERR_ARG, "staged must be 0 or 1");
   if (t->dsm != 0 && t->dsm != 1) return set_error(HN_ERR_ARG, "dsm must be 0 or 1");
   if (t->fuse_up != 0 && t->fuse_up != 1) return set_error(HN_ERR_ARG, "fuse_up must be 0 or 1");
+  if (t->mid < 0 || t->mid > HN_MAX_LEVEL) return set_error(HN_ERR_ARG, "mid must be in [0, %d]", HN_MAX_LEVEL);
   Tuning tu;
   tu.tail_level = t->tail_level;
   tu.cluster = c;
@@ -409,6 +412,7 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
   tu.staged = t->staged;
   tu.dsm = t->dsm;
   tu.fuse_up = t->fuse_up;
+  tu.mid = t->mid;
   mg->solo->set_tuning(tu);
   mg->tuning = tu;
   mg->tuned = true;
@@ -425,6 +429,7 @@ hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t) {
   t->staged = tu.staged;
   t->dsm = tu.dsm;
   t->fuse_up = tu.fuse_up;
+  t->mid = tu.mid;
   return HN_OK;
 }
 
@@ -438,16 +443,18 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
   HN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&x), (size_t)N * 8));
   struct Free { double* p; ~Free() { cudaFreeHost(p); } } fr{x};
   const int clusters[5] = {1, 2, 4, 8, 16};
+  const int mids[2] = {0, Tuning{}.mid};
   double best_ms = 1e300;
-  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 2, 0, 1, 0};
+  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 2, 0, 1, 0, mg->solo->tuning().mid};
   cudaEvent_t e0, e1;
   HN_CUDA(cudaEventCreate(&e0));
   HN_CUDA(cudaEventCreate(&e1));
   struct Ev { cudaEvent_t a, b; ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); } } ev{e0, e1};
   const int tmax = std::min(mg->L, 9);
+  for (int mi = 0; mi < 2; ++mi)
   for (int T = mg->coarse; T <= tmax; ++T)
     for (int ci = 0; ci < 5; ++ci) {
-      hn_tuning t{T, clusters[ci], 2, 0, 1, 0};
+      hn_tuning t{T, clusters[ci], 2, 0, 1, 0, mids[mi]};
       HN_TRY(hn_mg_set_tuning(mg, &t));
       HN_TRY(hn_mg_solve(mg, b, x, 0, 0, nullptr));            // capture + warm-up
       HN_CUDA(cudaEventRecord(e0, mg->solo->stream()));
@@ -460,7 +467,7 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
       float ms = 0.0f;
       HN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       const double per = ms / reps;
-      const int idx = (T - mg->coarse) * 5 + ci;
+      const int idx = (mi * (tmax - mg->coarse + 1) + (T - mg->coarse)) * 5 + ci;
       if (times_ms && idx < cap) times_ms[idx] = per;
       if (per < best_ms) { best_ms = per; bt = t; }
     }
@@ -481,12 +488,14 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
   int Lmax = 0;
   for (int j = 0; j < count; ++j) Lmax = std::max(Lmax, mgs[j]->L);
   double best_ms = 1e300;
-  hn_tuning bt{5, 1, 2, 0, 1, 0};
+  const int mids[2] = {0, Tuning{}.mid};
+  hn_tuning bt{5, 1, 2, 0, 1, 0, mids[1]};
+  for (int mi = 0; mi < 2; ++mi)
   for (int T = mgs[0]->coarse; T <= std::min(Lmax, 8); ++T)
     for (int ci = 0; ci < 3; ++ci) {
-      hn_tuning t{T, clusters[ci], 2, 0, 1, 0};
+      hn_tuning t{T, clusters[ci], 2, 0, 1, 0, mids[mi]};
       for (int j = 0; j < count; ++j) {
-        Tuning tu; tu.tail_level = T; tu.cluster = clusters[ci]; tu.pdl = 2;
+        Tuning tu; tu.tail_level = T; tu.cluster = clusters[ci]; tu.pdl = 2; tu.mid = mids[mi];
         mgs[j]->tuning = tu;
         mgs[j]->tuned = true;
       }
@@ -500,7 +509,7 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
       if (ms < best_ms) { best_ms = ms; bt = t; }
     }
   for (int j = 0; j < count; ++j) {
-    Tuning tu; tu.tail_level = bt.tail_level; tu.cluster = bt.cluster; tu.pdl = bt.pdl;
+    Tuning tu; tu.tail_level = bt.tail_level; tu.cluster = bt.cluster; tu.pdl = bt.pdl; tu.mid = bt.mid;
     mgs[j]->tuning = tu;
     mgs[j]->tuned = true;
   }

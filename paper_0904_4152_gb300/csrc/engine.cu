@@ -444,6 +444,7 @@ Engine::~Engine() {
   if (mem_) cudaFree(mem_);
   if (hActive_) cudaFreeHost(hActive_);
   if (hStage_) cudaFreeHost(hStage_);
+  if (hLists_) cudaFreeHost(hLists_);
   if (upEv_) cudaEventDestroy(upEv_);
 }
 
@@ -502,6 +503,8 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   take(sizeof(double) * (size_t)cap * ctl_groups);
   take(sizeof(unsigned) * (size_t)cap);
   take(sizeof(int) * plan_ints());
+  take(sizeof(TileList) * (kMaxLevel + 1));
+  take(sizeof(unsigned) * 2);
   bytes += 256;
   HN_CUDA(cudaMalloc(&mem_, bytes));
   HN_CUDA(cudaMemsetAsync(mem_, 0, bytes, s_));
@@ -525,7 +528,11 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   double* gsum = b.take<double>((size_t)cap * ctl_groups);
   unsigned* gticket = b.take<unsigned>((size_t)cap);
   dPlan_ = b.take<int>(plan_ints());
+  dLists_ = b.take<TileList>(kMaxLevel + 1);
+  dBar_ = b.take<unsigned>(2);
   HN_CUDA(cudaHostAlloc(&hStage_, stage_bytes(), cudaHostAllocDefault));
+  HN_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&hLists_), sizeof(TileList) * (kMaxLevel + 1),
+                        cudaHostAllocDefault));
   HN_CUDA(cudaEventCreateWithFlags(&upEv_, cudaEventDisableTiming));
   HN_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&hActive_), sizeof(unsigned), cudaHostAllocMapped));
   *hActive_ = 0;
@@ -547,6 +554,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   E_.ctl_groups = ctl_groups;
   E_.gsum = gsum;
   E_.gticket = gticket;
+  E_.gbar = dBar_;
   E_.iter_limit = (unsigned)(prm.max_cycles + prm.max_outer + 8);
   for (int l = 0; l <= kMaxLevel; ++l) {
     lists_[l] = TileList{dItems_[l], dCounts_ + l, dChunks_[l], dChunkCounts_ + l, (int)chunkCap_[l]};
@@ -638,6 +646,11 @@ hn_status Engine::set_members(const std::vector<hn_mg*>& slots) {
     if (l > P.coarse) t.solo_c = P.lev[l - 1];
     if (l < P.L) t.solo_f = P.lev[l + 1];
   }
+  // the persistent kernels read the tile lists (with the one-problem descriptors) from device
+  // memory; the staging copy is free again once the previous upload finished (event above)
+  std::memcpy(hLists_, lists_, sizeof(TileList) * (kMaxLevel + 1));
+  HN_CUDA(cudaMemcpyAsync(dLists_, hLists_, sizeof(TileList) * (kMaxLevel + 1), cudaMemcpyHostToDevice, s_));
+  HN_CUDA(cudaEventRecord(upEv_, s_));
   members_ = slots;
   members_.resize(cap_, nullptr);
   unsigned mask = 0;
@@ -665,6 +678,7 @@ hn_status Engine::start(const std::vector<int>& slots, const std::vector<int>& h
   // relies on per-problem caps; its limit is set out of reach)
   HN_CUDA(cudaMemsetAsync(E_.iter, 0, sizeof(unsigned), s_));
   HN_CUDA(cudaMemsetAsync(dErr_, 0, sizeof(int), s_));
+  HN_CUDA(cudaMemsetAsync(dBar_, 0, sizeof(unsigned) * 2, s_));
   // mirrors of the IF values as the closed-world graph sets them at its launch
   static const unsigned taken0[4] = {0u, 1u, 0u, 0u};
   HN_CUDA(cudaMemcpyAsync(dTaken_, taken0, sizeof taken0, cudaMemcpyHostToDevice, s_));
@@ -713,6 +727,24 @@ long long Engine::launch_bytes(int cls, int level) const {
     case KC_PCG_X: per = 4 * 8 + 2 * 8 + vb; break;            // x, r, p, q; write x, r, rhs
     case KC_PCG_DOT: per = 8 + vb; break;                       // r, z
     case KC_PCG_P: per = vb + 8 + 8; break;                     // z, p; write p
+    case KC_MID_DOWN:
+    case KC_MID_UP: {
+      // the persistent kernels: the sum of their steps' bytes over levels T+1..level (the top
+      // level of a problem counted with two full smoothing steps, the levels below it with the
+      // two steps fused from a zero iterate)
+      const int T = std::max(tune_.tail_level, prm_.coarse);
+      long long sum = 0;
+      for (int l = T + 1; l <= level; ++l)
+        sum += cls == KC_MID_DOWN
+                   ? launch_bytes(KC_JACOBI_FIRST, l) + launch_bytes(KC_DEFECT, l) + launch_bytes(KC_RESTRICT, l)
+                   : launch_bytes(KC_PROLONG, l) + prm_.post * launch_bytes(KC_JACOBI, l);
+      if (cls == KC_MID_DOWN)
+        for (hn_mg* mg : members_)
+          if (mg && mg->L > T && mg->L <= level)
+            sum += (long long)((2 * (9 * bb + 3 * vb + wd) - (9 * bb + 2 * vb + (prec == P64 ? 8 : 4))) *
+                               (double)N_of(mg->L));
+      return sum;
+    }
     default: per = 0; break;
   }
   return (long long)(per * (double)nodes);
@@ -793,6 +825,12 @@ hn_status Engine::close_if(cudaStream_t& s, cudaStream_t outer) {
   return HN_OK;
 }
 
+int Engine::mid_top() const {
+  const int T = std::max(tune_.tail_level, prm_.coarse);
+  if (tune_.mid <= T || tune_.staged || tune_.fuse_up) return T;
+  return std::min(Lmax_, tune_.mid);
+}
+
 hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
   const int c = prm_.coarse, pre = prm_.pre, post = prm_.post;
   const int T = std::max(tune_.tail_level, c);
@@ -807,7 +845,8 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
     c0 = counting_;
     return HN_OK;
   };
-  for (int l = Lmax_; l > T; --l) {
+  const int M = mid_top();                 // levels T+1..M: the persistent kernels
+  for (int l = Lmax_; l > std::max(T, M); --l) {
     // a finest level: lagged check (the PCG preconditioner's cycle has none)
     const bool top = prm_.solver != SOLVER_PCG && (topMaskAll_ || ((topMask_ >> l) & 1u));
     if (pre >= 2) {
@@ -830,8 +869,10 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
     HN_LAUNCH(KC_DEFECT, l, launch_defect(E_, lists_[l], l, want, pre & 1, grid_[l], s));
     HN_LAUNCH(KC_RESTRICT, l, launch_restrict(E_, lists_[l - 1], l, want, grid_[l - 1], s));
   }
+  if (M > T) HN_LAUNCH(KC_MID_DOWN, M, launch_mid(E_, dLists_, M, T, want, 0, s));
   HN_LAUNCH(KC_TAIL, T, launch_tail(E_, T, want, tune_.cluster, s));
-  for (int l = T + 1; l <= Lmax_; ++l) {
+  if (M > T) HN_LAUNCH(KC_MID_UP, M, launch_mid(E_, dLists_, M, T, want, 1, s));
+  for (int l = std::max(T, M) + 1; l <= Lmax_; ++l) {
     int sw = 1;
     if (tune_.fuse_up && post >= 1) {
       // prolongation and the first post-smoothing step in one pass
@@ -994,7 +1035,7 @@ hn_status Engine::capture_solve(bool cond) {
     // taken), so only the rest of a V cycle after the lagged check gets one, and only in the
     // defect correction, where every outer step ends with one cycle that its check stops.  (The
     // outer defect and the update would each skip two small launches: not worth an IF node.)
-    const int T = std::max(tune_.tail_level, prm_.coarse);
+    const int T = std::max(std::max(tune_.tail_level, prm_.coarse), mid_top());
     if (Lmax_ > T && prm_.prec != P64 && prm_.solver != SOLVER_PCG) cd.mask |= 1u;
     const unsigned defaults[3] = {0u, 1u, 0u};
     for (int w = 0; w < 3; ++w)
@@ -1141,7 +1182,7 @@ int Engine::kernel_times(hn_kernel_time* out, int max) const {
   static const char* names[KC_COUNT] = {"jacobi", "jacobi_first", "defect", "restrict", "prolong",
                                         "coarse", "check", "outer_defect", "update", "control",
                                         "tail", "pcg_q", "pcg_x", "pcg_dot", "pcg_p",
-                                        "prolong_jacobi"};
+                                        "prolong_jacobi", "mid_down", "mid_up"};
   int n = 0;
   for (int c = 0; c < KC_COUNT; ++c)
     for (int l = 0; l <= kMaxLevel; ++l) {

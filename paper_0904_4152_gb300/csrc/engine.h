@@ -57,7 +57,7 @@ size_t hierarchy_bytes(int L, int coarse, int prec, int solver);
 enum KClass {
   KC_JACOBI = 0, KC_JACOBI_FIRST, KC_DEFECT, KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_CHECK,
   KC_OUTER_DEFECT, KC_UPDATE, KC_CONTROL, KC_TAIL, KC_PCG_Q, KC_PCG_X, KC_PCG_DOT, KC_PCG_P,
-  KC_PROLONG_JACOBI, KC_COUNT
+  KC_PROLONG_JACOBI, KC_MID_DOWN, KC_MID_UP, KC_COUNT
 };
 
 // launch shape of the schedule: levels <= tail_level run fused in one cluster launch of
@@ -71,6 +71,9 @@ struct Tuning {
   int dsm = 1;      // fused tail: cluster levels in distributed shared memory when they fit
   int fuse_up = 0;  // levels above the tail: prolongation inside the first post-smoothing step
                     // (measured slower than the two kernels: 192 vs 157 us at L=12 FP32; off)
+  int mid = 10;     // levels tail_level+1..mid run in the two persistent (cooperative) kernels
+                    // of each cycle; levels above mid as one launch per step; 0: no persistent
+                    // kernels.  (Not combined with staged or fuse_up, which are per-step forms.)
 };
 
 class Engine;
@@ -216,6 +219,10 @@ class Engine {
   TileList lists_[kMaxLevel + 1] = {};
   TileList fine_{};
   int grid_[kMaxLevel + 1] = {};
+  TileList* dLists_ = nullptr;      // device copy of lists_ (read by the persistent kernels)
+  TileList* hLists_ = nullptr;      // its pinned staging copy
+  unsigned* dBar_ = nullptr;        // grid barrier of the persistent kernels
+  int mid_top() const;              // top level of the persistent kernels (<= tail level: none)
   int fineGrid_ = 1;
   int maxGrid_ = 1;
   std::vector<hn_mg*> members_;

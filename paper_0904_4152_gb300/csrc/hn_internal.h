@@ -203,6 +203,7 @@ struct EngineDev {
                                // problem's norm partial sum)
   double* gsum;                // [nprob * ctl_groups] group sums of the control kernel
   unsigned* gticket;           // [nprob] blocks of a problem's control launch that finished
+  unsigned* gbar;              // [2] grid barrier of the persistent kernels: arrivals, generation
 };
 
 // Launch wrappers for one step of the schedule; grid = CTAs of 256 threads.  level < 0 means
@@ -227,6 +228,12 @@ bool pre_fuses(int prec);
 cudaError_t launch_tail(const EngineDev& E, int T, int want, int cluster, cudaStream_t s);
 // one-time kernel attributes (cluster-size opt-in); call outside stream capture
 cudaError_t prepare_kernels();
+
+// the levels T+1..M of the V cycle in one cooperative launch each way (down: smoothing, defect,
+// restriction and the lagged checks of problems whose finest level is there; up: prolongation
+// and smoothing); lists: device copy of the engine's per-level tile lists
+cudaError_t launch_mid(const EngineDev& E, const TileList* lists, int M, int T, int want, int up,
+                       cudaStream_t s);
 
 cudaError_t launch_restrict(const EngineDev& E, TileList tl_coarse, int fine_level, int want,
                             int grid, cudaStream_t s);

@@ -1921,6 +1921,263 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
   }
 }
 
+// ------------------------------------------------- persistent kernels of the middle levels
+// The levels between the fused coarse-level kernel (k_tail, levels coarse..T) and a top level M
+// run in two cooperative launches per V cycle: k_mid_down does pre-smoothing, defect and
+// restriction on levels M..T+1, k_mid_up prolongation and post-smoothing on levels T+1..M.  All
+// blocks of a cooperative launch are resident at once, so the steps are separated by grid-wide
+// barriers instead of kernel boundaries (a barrier costs about a microsecond; a kernel boundary
+// on these latency-bound levels several).  The lagged convergence test of a problem whose finest
+// level lies in this range is taken by the last block to reach the barrier after that level's
+// first smoothing step, in the fixed summation order every other path uses.  Each step calls the
+// same tile functions as the per-level kernels (vectors written inside the launch are read from
+// L2), so the results do not depend on which path ran.
+
+// wait limit of a grid barrier (globaltimer ns): a barrier that does not complete by then sets
+// the error word, and every block leaves the kernel at its next barrier
+constexpr unsigned long long kGridWaitNs = 500ull * 1000ull * 1000ull;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is the generation.
+// The last block to arrive runs last() (block-wide), resets the count and opens the next
+// generation; the others poll the generation (bounded).  Returns false in every thread of a block
+// whose wait gave up, or that found the error word set (another block gave up).
+template <class F>
+__device__ bool grid_barrier(const EngineDev& E, F&& last) {
+  __shared__ unsigned s_gen;
+  __shared__ int s_state;                       // 1: last to arrive; 0: waiting; -1: failed
+  unsigned* bar = E.gbar;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_gen = ld_acquire_gpu(bar + 1);
+    __threadfence();                            // this block's writes before its arrival
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    s_state = arrived == gridDim.x ? 1 : 0;
+    if (arrived == gridDim.x) __threadfence();  // every other block's writes before last()
+  }
+  __syncthreads();
+  if (s_state == 1) {
+    last();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bar[0] = 0u;
+      st_release_gpu(bar + 1, s_gen + 1u);
+    }
+    __syncthreads();
+    return true;
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = global_ns();
+    unsigned nap = 32;
+    for (;;) {
+      if (ld_acquire_gpu(bar + 1) != s_gen) break;
+      if (*reinterpret_cast<volatile int*>(E.err) != 0) { s_state = -1; break; }
+      if (global_ns() - t0 > kGridWaitNs) {
+        atomicExch(E.err, 3);
+        s_state = -1;
+        break;
+      }
+      __nanosleep(nap);
+      if (nap < 512) nap <<= 1;
+    }
+  }
+  __syncthreads();
+  return s_state == 0;
+}
+
+template <class Pol> constexpr int mid_threads() { return Pol::prec == P64 ? 512 : 1024; }
+
+// One pass of band-kernel mode MODE over level l of every problem in phase `want`, spread over all
+// warps of the grid (an engine of one problem uses the descriptors of its tile list).
+template <class Pol, int MODE>
+__device__ __forceinline__ void mid_band_pass(const EngineDev& E, const TileList& tl, int l, int want,
+                                              int in_sel, int gw, int nw, int lane) {
+  using A = typename Pol::A;
+  const A omega = A(E.prm.omega);
+  const long long shift = 1LL << l;
+  if (tl.solo_tiles > 0) {
+    const ProbState& st = E.S[0];
+    if (__ldcg(&st.phase) != want) return;
+    const bool zg = (tl.solo_L > l) || __ldcg(&st.zero_top);
+    const bool slot = (MODE == M_PRE12 || MODE == M_JACOBI_FIRST) && l == tl.solo_L && !zg;
+    for (int t = gw; t < tl.solo_tiles; t += nw)
+      band_tile<Pol, MODE, LD_CG>(tl.solo_d, shift, zg, (long long)t * kTile + lane * kLaneNodes, lane,
+                                  in_sel, omega, slot ? E.partial + t : nullptr);
+    return;
+  }
+  const int count = *tl.count;
+  for (int g = gw; g < count; g += nw) {
+    const int2 it = tl.items[g];
+    const int p = it.x;
+    const ProbState& st = E.S[p];
+    if (__ldcg(&st.phase) != want) continue;
+    const ProblemDev& P = E.P[p];
+    const bool zg = (P.L > l) || __ldcg(&st.zero_top);
+    double* slot = nullptr;
+    if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST)
+      if (l == P.L && !zg) slot = E.partial + E.fine_off[p] + it.y;
+    band_tile<Pol, MODE, LD_CG>(P.lev[l], shift, zg, (long long)it.y * kTile + lane * kLaneNodes, lane,
+                                in_sel, omega, slot);
+  }
+}
+
+// restriction of level l's defect onto level l - 1 (tl: the coarse level's tile list)
+template <class V>
+__device__ __forceinline__ void mid_restrict_pass(const EngineDev& E, const TileList& tl, int l, int want,
+                                                  int gw, int nw, int lane) {
+  if (tl.solo_tiles > 0) {
+    if (tl.solo_L < l || __ldcg(&E.S[0].phase) != want) return;
+    for (int t = gw; t < tl.solo_tiles; t += nw)
+      restrict_tile<V, LD_CG>(tl.solo_f, tl.solo_d, (long long)t * kTile, lane);
+    return;
+  }
+  const int count = *tl.count;
+  for (int g = gw; g < count; g += nw) {
+    const int2 it = tl.items[g];
+    const int p = it.x;
+    const ProblemDev& P = E.P[p];
+    if (P.L < l || __ldcg(&E.S[p].phase) != want) continue;
+    restrict_tile<V, LD_CG>(P.lev[l], P.lev[l - 1], (long long)it.y * kTile, lane);
+  }
+}
+
+// x_l[x_sel] += P e_{l-1} on level l
+template <class V>
+__device__ __forceinline__ void mid_prolong_pass(const EngineDev& E, const TileList& tl, int l, int want,
+                                                 int x_sel, int gw, int nw, int lane) {
+  (void)lane;
+  if (tl.solo_tiles > 0) {
+    if (__ldcg(&E.S[0].phase) != want) return;
+    for (int t = gw; t < tl.solo_tiles; t += nw)
+      prolong_tile<V, LD_CG>(tl.solo_d, tl.solo_c, x_sel, (long long)t * kTile + lane * kLaneNodes);
+    return;
+  }
+  const int count = *tl.count;
+  for (int g = gw; g < count; g += nw) {
+    const int2 it = tl.items[g];
+    const int p = it.x;
+    if (__ldcg(&E.S[p].phase) != want) continue;
+    const ProblemDev& P = E.P[p];
+    prolong_tile<V, LD_CG>(P.lev[l], P.lev[l - 1], x_sel, (long long)it.y * kTile + lane * kLaneNodes);
+  }
+}
+
+// The lagged convergence test of the problems whose finest level is l and whose iterate is not
+// zero: problems p = first, first + stride, ... (one block: all of them, run by the last block to
+// reach the barrier after the level's first smoothing step; many problems: spread over the blocks,
+// followed by one more barrier).
+__device__ void mid_check(const EngineDev& E, int l, int want, int first, int stride, double* sh) {
+  for (int p = first; p < E.nprob; p += stride) {
+    ProbState& st = E.S[p];
+    if (E.P[p].L != l || __ldcg(&st.phase) != want || __ldcg(&st.zero_top)) continue;
+    const double sum = problem_norm_sum(E.partial + E.fine_off[p], fine_tiles(l), sh);
+    if (threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
+    __syncthreads();
+  }
+}
+
+// problems in phase `want` whose first smoothing step at their finest level l carries the lagged
+// check, counted per level into cnt[0..kMaxLevel]; the same in every block (read before any block
+// can change a state)
+__device__ void mid_check_levels(const EngineDev& E, int want, int T, int M, int* cnt) {
+  for (int l = threadIdx.x; l <= kMaxLevel; l += blockDim.x) cnt[l] = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < E.nprob; p += blockDim.x) {
+    const int L = E.P[p].L;
+    if (L > T && L <= M && __ldcg(&E.S[p].phase) == want && !__ldcg(&E.S[p].zero_top))
+      atomicAdd(&cnt[L], 1);
+  }
+  __syncthreads();
+}
+
+// up to this many checks at one level run in the last block to arrive; more are spread
+constexpr int kMidCheckSerial = 2;
+
+// Down part of the V cycle on levels M..T+1 (mirrors vcycle_down_level step for step).
+template <class Pol>
+__global__ void __launch_bounds__(mid_threads<Pol>(), 1) k_mid_down(EngineDev E, const TileList* lists,
+                                                                    int M, int T, int want) {
+  __shared__ double sh[32];
+  pdl_wait();
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int pre = E.prm.pre;
+  __shared__ int cnt[kMaxLevel + 1];
+  if (E.nprob == 1 && __ldcg(&E.S[0].phase) != want) return;    // (every block alike)
+  mid_check_levels(E, want, T, M, cnt);
+  auto nothing = [] {};
+  // an engine of one problem leaves as soon as its problem has left the cycle
+  auto gone = [&] { return E.nprob == 1 && __ldcg(&E.S[0].phase) != want; };
+  for (int l = M; l > T; --l) {
+    const TileList& tl = lists[l];
+    const int nc = cnt[l];
+    const bool c = nc > 0;
+    auto check = [&] { if (c && nc <= kMidCheckSerial) mid_check(E, l, want, 0, 1, sh); };
+    // the checks of many problems: each block takes its share, then all wait for the decisions
+    auto spread = [&] {
+      if (nc <= kMidCheckSerial) return true;
+      mid_check(E, l, want, blockIdx.x, gridDim.x, sh);
+      return grid_barrier(E, nothing);
+    };
+    if (pre >= 2) {
+      mid_band_pass<Pol, M_PRE12>(E, tl, l, want, 0, gw, nw, lane);
+      if (!grid_barrier(E, check) || !spread() || gone()) return;
+      if (c) {
+        mid_band_pass<Pol, M_PRE2B>(E, tl, l, want, 0, gw, nw, lane);
+        if (!grid_barrier(E, nothing)) return;
+      }
+      for (int s = 3; s <= pre; ++s) {
+        mid_band_pass<Pol, M_JACOBI>(E, tl, l, want, (s - 1) & 1, gw, nw, lane);
+        if (!grid_barrier(E, nothing)) return;
+      }
+    } else {
+      mid_band_pass<Pol, M_JACOBI_FIRST>(E, tl, l, want, 0, gw, nw, lane);
+      if (!grid_barrier(E, check) || !spread() || gone()) return;
+    }
+    mid_band_pass<Pol, M_DEFECT>(E, tl, l, want, pre & 1, gw, nw, lane);
+    if (!grid_barrier(E, nothing)) return;
+    if (l - 1 == T) pdl_trigger();            // the fused tail may start its constant-data staging
+    mid_restrict_pass<typename Pol::V>(E, lists[l - 1], l, want, gw, nw, lane);
+    if (l - 1 > T && !grid_barrier(E, nothing)) return;
+  }
+}
+
+// Up part of the V cycle on levels T+1..M (mirrors vcycle_up_level).
+template <class Pol>
+__global__ void __launch_bounds__(mid_threads<Pol>(), 1) k_mid_up(EngineDev E, const TileList* lists,
+                                                                  int M, int T, int want) {
+  pdl_wait();
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int pre = E.prm.pre, post = E.prm.post;
+  if (E.nprob == 1 && __ldcg(&E.S[0].phase) != want) return;
+  auto nothing = [] {};
+  for (int l = T + 1; l <= M; ++l) {
+    const TileList& tl = lists[l];
+    mid_prolong_pass<typename Pol::V>(E, tl, l, want, pre & 1, gw, nw, lane);
+    if ((post > 0 || l < M) && !grid_barrier(E, nothing)) return;
+    for (int s = 1; s <= post; ++s) {
+      mid_band_pass<Pol, M_JACOBI>(E, tl, l, want, (pre + s - 1) & 1, gw, nw, lane);
+      if ((s < post || l < M) && !grid_barrier(E, nothing)) return;
+    }
+  }
+}
+
 // FP64 outer defect of the defect correction: d = b - A x (FP64 bands, FP64 x), written to the
 // inner top-level right-hand side as V(d * s); partial[g] = sum d^2.  x = 0 gives d = b.  PCG:
 // the initial residual (before the first cycle), also kept in FP64 (r64).
@@ -2410,6 +2667,23 @@ cudaError_t launch_kt(void (*kern)(KArgs...), int grid, int threads, size_t smem
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// cooperative launch of one wave of resident blocks (all blocks run at once: grid barriers)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_coop(void (*kern)(KArgs...), int threads, cudaStream_t s, Args... args) {
+  const int grid = resident_blocks(reinterpret_cast<const void*>(kern), threads, 0) * sm_count();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t s, int pdl,
                      int cluster, Args... args) {
@@ -2569,6 +2843,23 @@ cudaError_t launch_tail(const EngineDev& E, int T, int want, int cluster, cudaSt
   }
   return cudaErrorInvalidValue;
 }
+template <class Pol>
+cudaError_t launch_mid_t(const EngineDev& E, const TileList* lists, int M, int T, int want, int up,
+                         cudaStream_t s) {
+  if (up) return launch_coop(k_mid_up<Pol>, mid_threads<Pol>(), s, E, lists, M, T, want);
+  return launch_coop(k_mid_down<Pol>, mid_threads<Pol>(), s, E, lists, M, T, want);
+}
+
+cudaError_t launch_mid(const EngineDev& E, const TileList* lists, int M, int T, int want, int up,
+                       cudaStream_t s) {
+  switch (E.prm.prec) {
+    case P64: return launch_mid_t<F64>(E, lists, M, T, want, up, s);
+    case P32: return launch_mid_t<F32>(E, lists, M, T, want, up, s);
+    case P16: return launch_mid_t<F16>(E, lists, M, T, want, up, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_defect(const EngineDev& E, TileList tl, int level, int want, int in_sel,
                           int grid, cudaStream_t s) {
   return launch_band(M_DEFECT, E, tl, level, want, in_sel, grid, s);

@@ -78,7 +78,8 @@ class ServerInfo(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tail_level", ctypes.c_int), ("cluster", ctypes.c_int), ("pdl", ctypes.c_int),
-                ("staged", ctypes.c_int), ("dsm", ctypes.c_int), ("fuse_up", ctypes.c_int)]
+                ("staged", ctypes.c_int), ("dsm", ctypes.c_int), ("fuse_up", ctypes.c_int),
+                ("mid", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -352,30 +353,32 @@ def hn_mg_kernel_times(mg, max_entries=256):
             for i in range(n)]
 
 
-def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0, dsm=1, fuse_up=0):
-    _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl, staged, dsm, fuse_up))))
+def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0, dsm=1, fuse_up=0, mid=10):
+    _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl, staged, dsm, fuse_up, mid))))
 
 
 def hn_mg_get_tuning(mg):
     t = Tuning()
     _check(lib().hn_mg_get_tuning(mg, ctypes.byref(t)))
-    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm, t.fuse_up
+    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm, t.fuse_up, t.mid
 
 
 def hn_mg_autotune(mg, b, reps=3, coarse_L=2):
     """Time every launch shape on this hierarchy, keep the fastest; returns (best, {shape: ms})."""
     b = np.ascontiguousarray(b, dtype=np.float64)
-    cap = 5 * 16
+    cap = 2 * 5 * 16
     times = np.full(cap, np.nan)
     best = Tuning()
     _check(lib().hn_mg_autotune(mg, _host_ptr(b, np.float64), reps, ctypes.byref(best),
                                 times.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cap))
     clusters = (1, 2, 4, 8, 16)
+    rows = int(np.count_nonzero(~np.isnan(times))) // 10     # tail levels per mid setting
     table = {}
     for i, v in enumerate(times):
         if not np.isnan(v):
-            table[(coarse_L + i // 5, clusters[i % 5])] = float(v)
-    return (best.tail_level, best.cluster), table
+            mi, k = divmod(i, 5 * rows)
+            table[(coarse_L + k // 5, clusters[k % 5], (0, 10)[mi])] = float(v)
+    return (best.tail_level, best.cluster, best.mid), table
 
 
 def hn_mg_autotune_batch(mgs, bs, reps=2):
@@ -386,7 +389,7 @@ def hn_mg_autotune_batch(mgs, bs, reps=2):
     best = Tuning()
     _check(lib().hn_mg_autotune_batch(arr([m.value for m in mgs]), n, arr([b.ctypes.data for b in bs]),
                                       reps, ctypes.byref(best)))
-    return best.tail_level, best.cluster, best.pdl
+    return best.tail_level, best.cluster, best.pdl, best.mid
 
 
 def hn_mg_time_kernel(mg, op, level, reps=20):

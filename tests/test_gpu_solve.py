@@ -306,29 +306,38 @@ def test_profiling_times_kernels_without_changing_results(hn):
     hn.hn_band_destroy(A)
     try:
         x0, _, _ = hn.hn_mg_solve(mg, L, b)
-        hn.hn_mg_set_profiling(mg, True)
-        x1, _, _ = hn.hn_mg_solve(mg, L, b)
-        times = hn.hn_mg_kernel_times(mg)
-        names = {t["name"] for t in times}
-        assert {"jacobi", "defect", "restrict", "prolong", "tail", "outer_defect"} <= names
-        assert all(t["total_ms"] > 0 for t in times)
-        np.testing.assert_array_equal(x0, x1)
-        hn.hn_mg_set_profiling(mg, False)
+        tail = hn.hn_mg_get_tuning(mg)[0]
+        # levels above the tail in the persistent kernels, then as one launch per step
+        for mid, want in ((10, {"mid_down", "mid_up", "tail", "outer_defect"}),
+                          (0, {"jacobi", "defect", "restrict", "prolong", "tail", "outer_defect"})):
+            hn.hn_mg_set_tuning(mg, tail, 16, 2, 0, 1, 0, mid)
+            hn.hn_mg_set_profiling(mg, True)
+            x1, _, _ = hn.hn_mg_solve(mg, L, b)
+            times = hn.hn_mg_kernel_times(mg)
+            names = {t["name"] for t in times}
+            assert want <= names, (mid, names)
+            assert all(t["total_ms"] > 0 for t in times)
+            np.testing.assert_array_equal(x0, x1)
+            hn.hn_mg_set_profiling(mg, False)
     finally:
         hn.hn_mg_destroy(mg)
 
 
+@pytest.mark.parametrize("mid", [0, 10])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("L", [6, 9])
-def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L):
+def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L, mid):
     # the one-launch solve of the defect correction skips, through an IF node, the rest of a V
-    # cycle after a lagged check that ends the inner solve (levels above the fused tail only);
+    # cycle after a lagged check that ends the inner solve (a check on a level run by one launch
+    # per step; the persistent kernels take their checks inside and skip the rest themselves);
     # the host-driven iterations (profiling) run every kernel of every iteration
     coef, b = I.batch_problem(5, L)
     A = hn.hn_band_create(L, coef)
     mg = hn.hn_mg_setup(A, prec=prec)
     hn.hn_band_destroy(A)
     try:
+        tail = hn.hn_mg_get_tuning(mg)[0]
+        hn.hn_mg_set_tuning(mg, tail, 16, 2, 0, 1, 0, mid)
         x0, st0, s0 = hn.hn_mg_solve(mg, L, b)
         n_loop = hn.hn_mg_last_launches(mg)
         hn.hn_mg_set_profiling(mg, True)
@@ -340,7 +349,7 @@ def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L):
         for k in ("cycles", "outer_iters", "inner_cycles", "relres"):
             assert st0[k] == st1[k], k
         assert 0 < n_loop <= n_host
-        if prec != 0 and L > hn.hn_mg_get_tuning(mg)[0]:
+        if prec != 0 and L > max(tail, mid):
             assert n_loop < n_host
         # a second solve counts its own launches again
         hn.hn_mg_solve(mg, L, b)
@@ -352,8 +361,8 @@ def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L):
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_launch_shapes_do_not_change_results(hn, prec):
     # the tail level, cluster size, programmatic dependent launch, bulk-copy staging, the
-    # distributed shared-memory cluster levels and the prolongation fused into the first
-    # post-smoothing step only change where work runs
+    # distributed shared-memory cluster levels, the prolongation fused into the first
+    # post-smoothing step and the top level of the persistent kernels only change where work runs
     L = 10                 # levels 9 and 10 are large enough for the bulk-copy kernels
     coef, b = I.batch_problem(3, L)
     A = hn.hn_band_create(L, coef)
@@ -361,16 +370,17 @@ def test_launch_shapes_do_not_change_results(hn, prec):
     hn.hn_band_destroy(A)
     try:
         ref, st0, _ = hn.hn_mg_solve(mg, L, b)
-        for shape in [(2, 1, 0, 0, 1, 1), (4, 2, 0, 1, 1, 0), (5, 16, 1, 0, 0, 1), (7, 8, 2, 1, 1, 1),
-                      (7, 16, 2, 0, 0, 0), (7, 16, 2, 0, 1, 0), (6, 4, 2, 0, 1, 1), (8, 16, 1, 1, 1, 0),
-                      (7, 16, 2, 0, 1, 1)]:
+        for shape in [(2, 1, 0, 0, 1, 1, 0), (4, 2, 0, 1, 1, 0, 0), (5, 16, 1, 0, 0, 1, 0), (7, 8, 2, 1, 1, 1, 0),
+                      (7, 16, 2, 0, 0, 0, 0), (7, 16, 2, 0, 1, 0, 0), (6, 4, 2, 0, 1, 1, 0), (8, 16, 1, 1, 1, 0, 0),
+                      (7, 16, 2, 0, 1, 1, 0), (7, 16, 2, 0, 1, 0, 10), (7, 16, 2, 0, 1, 0, 9), (7, 16, 2, 0, 1, 0, 8),
+                      (5, 16, 2, 0, 1, 0, 10), (2, 1, 2, 0, 1, 0, 10), (6, 4, 0, 0, 0, 0, 10), (9, 16, 2, 0, 1, 0, 10)]:
             hn.hn_mg_set_tuning(mg, *shape)
             assert hn.hn_mg_get_tuning(mg) == shape
             x, st, _ = hn.hn_mg_solve(mg, L, b)
             np.testing.assert_array_equal(x, ref)
             assert st["cycles"] == st0["cycles"]
         best, table = hn.hn_mg_autotune(mg, b, reps=1)
-        assert best in table and len(table) == 5 * 8
+        assert best in table and len(table) == 2 * 5 * 8
         x, _, _ = hn.hn_mg_solve(mg, L, b)
         np.testing.assert_array_equal(x, ref)
     finally:
