@@ -35,7 +35,8 @@ typedef struct {
                        the fused pass measured slower, its extra work outweighing the pass saved) */
   int mid;          /* levels tail_level+1 .. mid run in the persistent kernels (0, or any value
                        <= tail_level: none); not combined with staged or fuse_up, which are forms
-                       of the per-step launches (default 10) */
+                       of the per-step launches (default 0: on this part a grid barrier plus the
+                       memory latency of a step costs as much as a kernel boundary) */
 } hn_tuning;
 
 /* Set / read the launch shape used by mg's later solves.  HN_ERR_ARG on values out of range. */

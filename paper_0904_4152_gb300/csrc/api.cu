@@ -29,6 +29,9 @@ void exact_caps(const std::vector<hn_mg*>& mgs, std::vector<long long>& caps, lo
   }
 }
 
+// top level of the persistent kernels among the autotuner's candidates
+constexpr int kMidCandidate = 10;
+
 // default launch shape of one problem: FP64 arithmetic is slow enough on this part that the
 // fused tail pays from level 6 down (its levels then fit in distributed shared memory); the
 // FP32/FP16 inner cycles fuse from level 7 down (measured at L=10)
@@ -443,7 +446,7 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
   HN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&x), (size_t)N * 8));
   struct Free { double* p; ~Free() { cudaFreeHost(p); } } fr{x};
   const int clusters[5] = {1, 2, 4, 8, 16};
-  const int mids[2] = {0, Tuning{}.mid};
+  const int mids[2] = {0, kMidCandidate};
   double best_ms = 1e300;
   hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 2, 0, 1, 0, mg->solo->tuning().mid};
   cudaEvent_t e0, e1;
@@ -488,7 +491,7 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
   int Lmax = 0;
   for (int j = 0; j < count; ++j) Lmax = std::max(Lmax, mgs[j]->L);
   double best_ms = 1e300;
-  const int mids[2] = {0, Tuning{}.mid};
+  const int mids[2] = {0, kMidCandidate};
   hn_tuning bt{5, 1, 2, 0, 1, 0, mids[1]};
   for (int mi = 0; mi < 2; ++mi)
   for (int T = mgs[0]->coarse; T <= std::min(Lmax, 8); ++T)

@@ -504,7 +504,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   take(sizeof(unsigned) * (size_t)cap);
   take(sizeof(int) * plan_ints());
   take(sizeof(TileList) * (kMaxLevel + 1));
-  take(sizeof(unsigned) * 2);
+  take(sizeof(unsigned long long) * 3);
   bytes += 256;
   HN_CUDA(cudaMalloc(&mem_, bytes));
   HN_CUDA(cudaMemsetAsync(mem_, 0, bytes, s_));
@@ -529,7 +529,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   unsigned* gticket = b.take<unsigned>((size_t)cap);
   dPlan_ = b.take<int>(plan_ints());
   dLists_ = b.take<TileList>(kMaxLevel + 1);
-  dBar_ = b.take<unsigned>(2);
+  dBar_ = b.take<unsigned long long>(3);
   HN_CUDA(cudaHostAlloc(&hStage_, stage_bytes(), cudaHostAllocDefault));
   HN_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&hLists_), sizeof(TileList) * (kMaxLevel + 1),
                         cudaHostAllocDefault));
@@ -678,7 +678,7 @@ hn_status Engine::start(const std::vector<int>& slots, const std::vector<int>& h
   // relies on per-problem caps; its limit is set out of reach)
   HN_CUDA(cudaMemsetAsync(E_.iter, 0, sizeof(unsigned), s_));
   HN_CUDA(cudaMemsetAsync(dErr_, 0, sizeof(int), s_));
-  HN_CUDA(cudaMemsetAsync(dBar_, 0, sizeof(unsigned) * 2, s_));
+  HN_CUDA(cudaMemsetAsync(dBar_, 0, sizeof(unsigned long long) * 3, s_));
   // mirrors of the IF values as the closed-world graph sets them at its launch
   static const unsigned taken0[4] = {0u, 1u, 0u, 0u};
   HN_CUDA(cudaMemcpyAsync(dTaken_, taken0, sizeof taken0, cudaMemcpyHostToDevice, s_));

@@ -71,9 +71,11 @@ struct Tuning {
   int dsm = 1;      // fused tail: cluster levels in distributed shared memory when they fit
   int fuse_up = 0;  // levels above the tail: prolongation inside the first post-smoothing step
                     // (measured slower than the two kernels: 192 vs 157 us at L=12 FP32; off)
-  int mid = 10;     // levels tail_level+1..mid run in the two persistent (cooperative) kernels
-                    // of each cycle; levels above mid as one launch per step; 0: no persistent
-                    // kernels.  (Not combined with staged or fuse_up, which are per-step forms.)
+  int mid = 0;      // levels tail_level+1..mid run in the two persistent (cooperative) kernels
+                    // of each cycle, levels above mid as one launch per step; 0: no persistent
+                    // kernels (default: a grid barrier plus the memory latency of a step measured
+                    // as long as a kernel boundary, ~3.5 us at L = 10, so they did not pay).
+                    // Not combined with staged or fuse_up, which are per-step forms.
 };
 
 class Engine;
@@ -221,7 +223,7 @@ class Engine {
   int grid_[kMaxLevel + 1] = {};
   TileList* dLists_ = nullptr;      // device copy of lists_ (read by the persistent kernels)
   TileList* hLists_ = nullptr;      // its pinned staging copy
-  unsigned* dBar_ = nullptr;        // grid barrier of the persistent kernels
+  unsigned long long* dBar_ = nullptr;   // grid barriers of the persistent kernels
   int mid_top() const;              // top level of the persistent kernels (<= tail level: none)
   int fineGrid_ = 1;
   int maxGrid_ = 1;

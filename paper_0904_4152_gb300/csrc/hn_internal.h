@@ -203,7 +203,8 @@ struct EngineDev {
                                // problem's norm partial sum)
   double* gsum;                // [nprob * ctl_groups] group sums of the control kernel
   unsigned* gticket;           // [nprob] blocks of a problem's control launch that finished
-  unsigned* gbar;              // [2] grid barrier of the persistent kernels: arrivals, generation
+  unsigned long long* gbar;    // [3] grid barriers of the persistent kernels: arrivals of the
+                               // down kernel, of the up kernel, barrier actions completed
 };
 
 // Launch wrappers for one step of the schedule; grid = CTAs of 256 threads.  level < 0 means

@@ -1926,24 +1926,29 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
 // run in two cooperative launches per V cycle: k_mid_down does pre-smoothing, defect and
 // restriction on levels M..T+1, k_mid_up prolongation and post-smoothing on levels T+1..M.  All
 // blocks of a cooperative launch are resident at once, so the steps are separated by grid-wide
-// barriers instead of kernel boundaries (a barrier costs about a microsecond; a kernel boundary
-// on these latency-bound levels several).  The lagged convergence test of a problem whose finest
+// barriers instead of kernel boundaries.  The lagged convergence test of a problem whose finest
 // level lies in this range is taken by the last block to reach the barrier after that level's
 // first smoothing step, in the fixed summation order every other path uses.  Each step calls the
 // same tile functions as the per-level kernels (vectors written inside the launch are read from
-// L2), so the results do not depend on which path ran.
+// L2), so the results do not depend on which path ran.  An engine of one problem copies its level
+// descriptors to shared memory once per launch, so that no step waits on descriptor loads.
 
 // wait limit of a grid barrier (globaltimer ns): a barrier that does not complete by then sets
 // the error word, and every block leaves the kernel at its next barrier
 constexpr unsigned long long kGridWaitNs = 500ull * 1000ull * 1000ull;
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long atom_add_acq_rel64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;\n" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
 }
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -1951,70 +1956,108 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is the generation.
-// The last block to arrive runs last() (block-wide), resets the count and opens the next
-// generation; the others poll the generation (bounded).  Returns false in every thread of a block
-// whose wait gave up, or that found the error word set (another block gave up).
-template <class F>
-__device__ bool grid_barrier(const EngineDev& E, F&& last) {
-  __shared__ unsigned s_gen;
-  __shared__ int s_state;                       // 1: last to arrive; 0: waiting; -1: failed
-  unsigned* bar = E.gbar;
+// bounded wait (one thread) until *p >= target; false if it gave up or found the error word set
+__device__ bool wait_at_least(const unsigned long long* p, unsigned long long target, int* err) {
+  if (ld_acquire64(p) >= target) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (ld_acquire64(p) >= target) return true;
+    if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+    if (global_ns() - t0 > kGridWaitNs) {
+      atomicExch(err, 3);
+      return false;
+    }
+  }
+}
+
+// Grid barrier state (used by thread 0 of each block).  cnt counts the arrivals of every launch
+// of one kernel (monotonic; each launch has the same grid, so a launch starts at a multiple of
+// it), done the barrier actions completed.  Both are read at the start of a launch, before any
+// block of the launch can have completed a barrier.
+struct GridBar {
+  unsigned long long* cnt;
+  unsigned long long* done;
+  unsigned long long target, dtarget;
+};
+
+__device__ __forceinline__ void grid_bar_init(GridBar& g, unsigned long long* cnt, unsigned long long* done) {
+  g.cnt = cnt;
+  g.done = done;
+  g.target = 0;
+  g.dtarget = 0;
+  if (threadIdx.x == 0) {
+    g.target = ld_acquire64(cnt) / gridDim.x * gridDim.x;
+    g.dtarget = ld_acquire64(done);
+  }
+}
+
+// Grid-wide barrier of a cooperative launch.  With ACTION, the last block to arrive runs last()
+// (block-wide) before any block goes on.  Returns false in every thread of a block whose wait gave
+// up or that found the error word set (another block gave up): the block then leaves the kernel.
+template <bool ACTION, class F>
+__device__ bool grid_sync(const EngineDev& E, GridBar& g, F&& last) {
+  __shared__ int s_state;                       // 1: runs the action; 0: go on; -1: failed
   __syncthreads();
   if (threadIdx.x == 0) {
-    s_gen = ld_acquire_gpu(bar + 1);
-    __threadfence();                            // this block's writes before its arrival
-    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-    s_state = arrived == gridDim.x ? 1 : 0;
-    if (arrived == gridDim.x) __threadfence();  // every other block's writes before last()
+    g.target += gridDim.x;
+    const unsigned long long old = atom_add_acq_rel64(g.cnt, 1ull);   // releases this block's writes
+    if (ACTION) {
+      g.dtarget += 1;
+      s_state = old + 1 == g.target ? 1 : (wait_at_least(g.done, g.dtarget, E.err) ? 0 : -1);
+    } else {
+      s_state = wait_at_least(g.cnt, g.target, E.err) ? 0 : -1;
+    }
   }
   __syncthreads();
-  if (s_state == 1) {
+  if (ACTION && s_state == 1) {
     last();
     __syncthreads();
-    if (threadIdx.x == 0) {
-      bar[0] = 0u;
-      st_release_gpu(bar + 1, s_gen + 1u);
-    }
-    __syncthreads();
+    if (threadIdx.x == 0) st_release64(g.done, g.dtarget);
     return true;
   }
-  if (threadIdx.x == 0) {
-    const unsigned long long t0 = global_ns();
-    unsigned nap = 32;
-    for (;;) {
-      if (ld_acquire_gpu(bar + 1) != s_gen) break;
-      if (*reinterpret_cast<volatile int*>(E.err) != 0) { s_state = -1; break; }
-      if (global_ns() - t0 > kGridWaitNs) {
-        atomicExch(E.err, 3);
-        s_state = -1;
-        break;
-      }
-      __nanosleep(nap);
-      if (nap < 512) nap <<= 1;
-    }
-  }
-  __syncthreads();
   return s_state == 0;
 }
 
 template <class Pol> constexpr int mid_threads() { return Pol::prec == P64 ? 512 : 1024; }
 
+// Per-block view of an engine of one problem: its descriptors of levels T..M (shared memory),
+// its finest level, and whether it is in the phase the launch serves.
+struct MidSolo {
+  LevelDev lev[kMaxLevel + 1];
+  int on, L, in_phase, zero_top;
+};
+
+__device__ void mid_solo_load(const EngineDev& E, const TileList* lists, int M, int T, int want,
+                              MidSolo& ms) {
+  if (threadIdx.x == 0) {
+    ms.on = lists[M].solo_tiles > 0;
+    ms.L = lists[M].solo_L;
+    ms.in_phase = __ldcg(&E.S[0].phase) == want;
+    ms.zero_top = __ldcg(&E.S[0].zero_top);
+  }
+  constexpr int words = (int)(sizeof(LevelDev) / 4);
+  for (int q = threadIdx.x; q < words * (M - T + 1); q += blockDim.x) {
+    const int l = T + q / words, w = q - (q / words) * words;
+    reinterpret_cast<unsigned*>(&ms.lev[l])[w] = reinterpret_cast<const unsigned*>(&lists[l].solo_d)[w];
+  }
+  __syncthreads();
+}
+
 // One pass of band-kernel mode MODE over level l of every problem in phase `want`, spread over all
-// warps of the grid (an engine of one problem uses the descriptors of its tile list).
+// warps of the grid.
 template <class Pol, int MODE>
-__device__ __forceinline__ void mid_band_pass(const EngineDev& E, const TileList& tl, int l, int want,
-                                              int in_sel, int gw, int nw, int lane) {
+__device__ __forceinline__ void mid_band_pass(const EngineDev& E, const MidSolo& ms, const TileList& tl,
+                                              int l, int want, int in_sel, int gw, int nw, int lane) {
   using A = typename Pol::A;
   const A omega = A(E.prm.omega);
   const long long shift = 1LL << l;
-  if (tl.solo_tiles > 0) {
-    const ProbState& st = E.S[0];
-    if (__ldcg(&st.phase) != want) return;
-    const bool zg = (tl.solo_L > l) || __ldcg(&st.zero_top);
-    const bool slot = (MODE == M_PRE12 || MODE == M_JACOBI_FIRST) && l == tl.solo_L && !zg;
-    for (int t = gw; t < tl.solo_tiles; t += nw)
-      band_tile<Pol, MODE, LD_CG>(tl.solo_d, shift, zg, (long long)t * kTile + lane * kLaneNodes, lane,
+  if (ms.on) {
+    if (!ms.in_phase) return;
+    const bool zg = (ms.L > l) || ms.zero_top;
+    const bool slot = (MODE == M_PRE12 || MODE == M_JACOBI_FIRST) && l == ms.L && !zg;
+    const int tiles = ms.lev[l].pitch / kTile;
+    for (int t = gw; t < tiles; t += nw)
+      band_tile<Pol, MODE, LD_CG>(ms.lev[l], shift, zg, (long long)t * kTile + lane * kLaneNodes, lane,
                                   in_sel, omega, slot ? E.partial + t : nullptr);
     return;
   }
@@ -2036,12 +2079,13 @@ __device__ __forceinline__ void mid_band_pass(const EngineDev& E, const TileList
 
 // restriction of level l's defect onto level l - 1 (tl: the coarse level's tile list)
 template <class V>
-__device__ __forceinline__ void mid_restrict_pass(const EngineDev& E, const TileList& tl, int l, int want,
-                                                  int gw, int nw, int lane) {
-  if (tl.solo_tiles > 0) {
-    if (tl.solo_L < l || __ldcg(&E.S[0].phase) != want) return;
-    for (int t = gw; t < tl.solo_tiles; t += nw)
-      restrict_tile<V, LD_CG>(tl.solo_f, tl.solo_d, (long long)t * kTile, lane);
+__device__ __forceinline__ void mid_restrict_pass(const EngineDev& E, const MidSolo& ms, const TileList& tl,
+                                                  int l, int want, int gw, int nw, int lane) {
+  if (ms.on) {
+    if (!ms.in_phase) return;
+    const int tiles = ms.lev[l - 1].pitch / kTile;
+    for (int t = gw; t < tiles; t += nw)
+      restrict_tile<V, LD_CG>(ms.lev[l], ms.lev[l - 1], (long long)t * kTile, lane);
     return;
   }
   const int count = *tl.count;
@@ -2056,13 +2100,13 @@ __device__ __forceinline__ void mid_restrict_pass(const EngineDev& E, const Tile
 
 // x_l[x_sel] += P e_{l-1} on level l
 template <class V>
-__device__ __forceinline__ void mid_prolong_pass(const EngineDev& E, const TileList& tl, int l, int want,
-                                                 int x_sel, int gw, int nw, int lane) {
-  (void)lane;
-  if (tl.solo_tiles > 0) {
-    if (__ldcg(&E.S[0].phase) != want) return;
-    for (int t = gw; t < tl.solo_tiles; t += nw)
-      prolong_tile<V, LD_CG>(tl.solo_d, tl.solo_c, x_sel, (long long)t * kTile + lane * kLaneNodes);
+__device__ __forceinline__ void mid_prolong_pass(const EngineDev& E, const MidSolo& ms, const TileList& tl,
+                                                 int l, int want, int x_sel, int gw, int nw, int lane) {
+  if (ms.on) {
+    if (!ms.in_phase) return;
+    const int tiles = ms.lev[l].pitch / kTile;
+    for (int t = gw; t < tiles; t += nw)
+      prolong_tile<V, LD_CG>(ms.lev[l], ms.lev[l - 1], x_sel, (long long)t * kTile + lane * kLaneNodes);
     return;
   }
   const int count = *tl.count;
@@ -2092,13 +2136,17 @@ __device__ void mid_check(const EngineDev& E, int l, int want, int first, int st
 // problems in phase `want` whose first smoothing step at their finest level l carries the lagged
 // check, counted per level into cnt[0..kMaxLevel]; the same in every block (read before any block
 // can change a state)
-__device__ void mid_check_levels(const EngineDev& E, int want, int T, int M, int* cnt) {
+__device__ void mid_check_levels(const EngineDev& E, const MidSolo& ms, int want, int T, int M, int* cnt) {
   for (int l = threadIdx.x; l <= kMaxLevel; l += blockDim.x) cnt[l] = 0;
   __syncthreads();
-  for (int p = threadIdx.x; p < E.nprob; p += blockDim.x) {
-    const int L = E.P[p].L;
-    if (L > T && L <= M && __ldcg(&E.S[p].phase) == want && !__ldcg(&E.S[p].zero_top))
-      atomicAdd(&cnt[L], 1);
+  if (ms.on) {
+    if (threadIdx.x == 0 && ms.in_phase && !ms.zero_top && ms.L > T && ms.L <= M) cnt[ms.L] = 1;
+  } else {
+    for (int p = threadIdx.x; p < E.nprob; p += blockDim.x) {
+      const int L = E.P[p].L;
+      if (L > T && L <= M && __ldcg(&E.S[p].phase) == want && !__ldcg(&E.S[p].zero_top))
+        atomicAdd(&cnt[L], 1);
+    }
   }
   __syncthreads();
 }
@@ -2111,48 +2159,66 @@ template <class Pol>
 __global__ void __launch_bounds__(mid_threads<Pol>(), 1) k_mid_down(EngineDev E, const TileList* lists,
                                                                     int M, int T, int want) {
   __shared__ double sh[32];
+  __shared__ int cnt[kMaxLevel + 1];
+  __shared__ MidSolo ms;
   pdl_wait();
+  GridBar gb;
+  grid_bar_init(gb, E.gbar, E.gbar + 2);
+  mid_solo_load(E, lists, M, T, want, ms);
+  if (ms.on && !ms.in_phase) return;                             // (every block alike)
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   const int pre = E.prm.pre;
-  __shared__ int cnt[kMaxLevel + 1];
-  if (E.nprob == 1 && __ldcg(&E.S[0].phase) != want) return;    // (every block alike)
-  mid_check_levels(E, want, T, M, cnt);
+  mid_check_levels(E, ms, want, T, M, cnt);
   auto nothing = [] {};
-  // an engine of one problem leaves as soon as its problem has left the cycle
-  auto gone = [&] { return E.nprob == 1 && __ldcg(&E.S[0].phase) != want; };
   for (int l = M; l > T; --l) {
     const TileList& tl = lists[l];
     const int nc = cnt[l];
-    const bool c = nc > 0;
-    auto check = [&] { if (c && nc <= kMidCheckSerial) mid_check(E, l, want, 0, 1, sh); };
-    // the checks of many problems: each block takes its share, then all wait for the decisions
-    auto spread = [&] {
-      if (nc <= kMidCheckSerial) return true;
-      mid_check(E, l, want, blockIdx.x, gridDim.x, sh);
-      return grid_barrier(E, nothing);
+    // after the first smoothing step: the checks (in the last block to arrive, or spread over
+    // the blocks followed by one more barrier); an engine of one problem leaves once its problem
+    // has left the cycle
+    auto first_done = [&]() -> bool {
+      bool ok;
+      if (nc == 0) {
+        ok = grid_sync<false>(E, gb, nothing);
+      } else if (nc <= kMidCheckSerial) {
+        ok = grid_sync<true>(E, gb, [&] { mid_check(E, l, want, 0, 1, sh); });
+      } else {
+        ok = grid_sync<false>(E, gb, nothing);
+        if (ok) {
+          mid_check(E, l, want, blockIdx.x, gridDim.x, sh);
+          ok = grid_sync<false>(E, gb, nothing);
+        }
+      }
+      if (!ok) return false;
+      if (nc > 0 && ms.on) {
+        if (threadIdx.x == 0) ms.in_phase = __ldcg(&E.S[0].phase) == want;
+        __syncthreads();
+        if (!ms.in_phase) return false;
+      }
+      return true;
     };
     if (pre >= 2) {
-      mid_band_pass<Pol, M_PRE12>(E, tl, l, want, 0, gw, nw, lane);
-      if (!grid_barrier(E, check) || !spread() || gone()) return;
-      if (c) {
-        mid_band_pass<Pol, M_PRE2B>(E, tl, l, want, 0, gw, nw, lane);
-        if (!grid_barrier(E, nothing)) return;
+      mid_band_pass<Pol, M_PRE12>(E, ms, tl, l, want, 0, gw, nw, lane);
+      if (!first_done()) return;
+      if (nc > 0) {
+        mid_band_pass<Pol, M_PRE2B>(E, ms, tl, l, want, 0, gw, nw, lane);
+        if (!grid_sync<false>(E, gb, nothing)) return;
       }
       for (int s = 3; s <= pre; ++s) {
-        mid_band_pass<Pol, M_JACOBI>(E, tl, l, want, (s - 1) & 1, gw, nw, lane);
-        if (!grid_barrier(E, nothing)) return;
+        mid_band_pass<Pol, M_JACOBI>(E, ms, tl, l, want, (s - 1) & 1, gw, nw, lane);
+        if (!grid_sync<false>(E, gb, nothing)) return;
       }
     } else {
-      mid_band_pass<Pol, M_JACOBI_FIRST>(E, tl, l, want, 0, gw, nw, lane);
-      if (!grid_barrier(E, check) || !spread() || gone()) return;
+      mid_band_pass<Pol, M_JACOBI_FIRST>(E, ms, tl, l, want, 0, gw, nw, lane);
+      if (!first_done()) return;
     }
-    mid_band_pass<Pol, M_DEFECT>(E, tl, l, want, pre & 1, gw, nw, lane);
-    if (!grid_barrier(E, nothing)) return;
+    mid_band_pass<Pol, M_DEFECT>(E, ms, tl, l, want, pre & 1, gw, nw, lane);
+    if (!grid_sync<false>(E, gb, nothing)) return;
     if (l - 1 == T) pdl_trigger();            // the fused tail may start its constant-data staging
-    mid_restrict_pass<typename Pol::V>(E, lists[l - 1], l, want, gw, nw, lane);
-    if (l - 1 > T && !grid_barrier(E, nothing)) return;
+    mid_restrict_pass<typename Pol::V>(E, ms, lists[l - 1], l, want, gw, nw, lane);
+    if (l - 1 > T && !grid_sync<false>(E, gb, nothing)) return;
   }
 }
 
@@ -2160,20 +2226,24 @@ __global__ void __launch_bounds__(mid_threads<Pol>(), 1) k_mid_down(EngineDev E,
 template <class Pol>
 __global__ void __launch_bounds__(mid_threads<Pol>(), 1) k_mid_up(EngineDev E, const TileList* lists,
                                                                   int M, int T, int want) {
+  __shared__ MidSolo ms;
   pdl_wait();
+  GridBar gb;
+  grid_bar_init(gb, E.gbar + 1, E.gbar + 2);
+  mid_solo_load(E, lists, M, T, want, ms);
+  if (ms.on && !ms.in_phase) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   const int pre = E.prm.pre, post = E.prm.post;
-  if (E.nprob == 1 && __ldcg(&E.S[0].phase) != want) return;
   auto nothing = [] {};
   for (int l = T + 1; l <= M; ++l) {
     const TileList& tl = lists[l];
-    mid_prolong_pass<typename Pol::V>(E, tl, l, want, pre & 1, gw, nw, lane);
-    if ((post > 0 || l < M) && !grid_barrier(E, nothing)) return;
+    mid_prolong_pass<typename Pol::V>(E, ms, tl, l, want, pre & 1, gw, nw, lane);
+    if ((post > 0 || l < M) && !grid_sync<false>(E, gb, nothing)) return;
     for (int s = 1; s <= post; ++s) {
-      mid_band_pass<Pol, M_JACOBI>(E, tl, l, want, (pre + s - 1) & 1, gw, nw, lane);
-      if ((s < post || l < M) && !grid_barrier(E, nothing)) return;
+      mid_band_pass<Pol, M_JACOBI>(E, ms, tl, l, want, (pre + s - 1) & 1, gw, nw, lane);
+      if ((s < post || l < M) && !grid_sync<false>(E, gb, nothing)) return;
     }
   }
 }

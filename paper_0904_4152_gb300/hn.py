@@ -353,7 +353,7 @@ def hn_mg_kernel_times(mg, max_entries=256):
             for i in range(n)]
 
 
-def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0, dsm=1, fuse_up=0, mid=10):
+def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0, dsm=1, fuse_up=0, mid=0):
     _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl, staged, dsm, fuse_up, mid))))
 
 

@@ -188,6 +188,36 @@ def test_batch_alone_equals_in_mix(hn, prec):
             hn.hn_mg_destroy(m)
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_batch_in_the_persistent_kernels_gives_the_same_bits(hn, prec):
+    # levels 5..9 in the two persistent kernels of each cycle (tail level 4): the work-list path,
+    # the lagged checks of up to two problems per level in the last block to reach the barrier
+    # (levels 5, 8) and of more problems spread over the blocks (levels 6, 7)
+    levels = [5, 7, 6, 8, 7, 6, 5, 8, 9, 6, 7]
+    mgs, bs = [], []
+    for j, L in enumerate(levels):
+        coef, b = I.batch_problem(80 + j, L)
+        A = hn.hn_band_create(L, coef)
+        mgs.append(hn.hn_mg_setup(A, prec=prec))
+        hn.hn_band_destroy(A)
+        bs.append(b)
+    try:
+        ref, sref, status = hn.hn_mg_solve_batch(mgs, levels, bs)
+        assert status == hn.HN_OK
+        for m in mgs:
+            hn.hn_mg_set_tuning(m, 4, 1, 2, 0, 1, 0, 10)
+        xs, stats, status = hn.hn_mg_solve_batch(mgs, levels, bs)
+        assert status == hn.HN_OK
+        for j in range(len(levels)):
+            np.testing.assert_array_equal(xs[j], ref[j])
+            assert stats[j]["cycles"] == sref[j]["cycles"]
+        xa, sa, _ = hn.hn_mg_solve(mgs[8], levels[8], bs[8])     # alone, same shape
+        np.testing.assert_array_equal(xa, ref[8])
+    finally:
+        for m in mgs:
+            hn.hn_mg_destroy(m)
+
+
 def test_fp16_large_level_alone_equals_in_batch(hn):
     # alone, an engine of one problem passes its descriptors by value (and at L = 10 its levels
     # take the bulk-sized grids); in a batch the same kernels walk the work lists: same bits
