@@ -269,11 +269,19 @@ def run_reference(args, rank, world, pg):
     print(json.dumps(line), flush=True)
 
 
-def band_kernels(hn, stream, peak, L=12, reps=20):
+# FP64 operations per node of the FP64 band and transfer kernels (the defect is one FMA chain
+# from b; Jacobi adds one FMA; the restriction does 9 per coarse node, 2.25 per fine node; the
+# prolongation 1, 2 or 4 per fine node by its position, 2.25 on average)
+FP64_OPS_PER_NODE = {"spmv": 9.0, "defect": 9.0, "jacobi": 10.0, "restrict": 2.25, "prolong": 2.25}
+
+
+def band_kernels(hn, stream, peak, L=12, reps=20, rates=None):
     """Band-SpMV, defect and Jacobi launched alone on level L (FP64, FP32, FP16-band storage):
-    mean launch time by CUDA events and algorithmic bytes -> GB/s and fraction of `peak`."""
+    mean launch time by CUDA events and algorithmic bytes -> GB/s and fraction of `peak`.  For
+    FP64 also the fraction of min(HBM, FP64 rate) (`rates`: hn_measure_fp_rates)."""
     band = {}
     A = hn.hn_band_create(L)
+    N = ((1 << L) + 1) ** 2
     for pname, prec in (("fp64", hn.HN_PREC_FP64), ("fp32", hn.HN_PREC_FP32_DC),
                         ("fp16band", hn.HN_PREC_FP16BAND_DC)):
         mg = hn.hn_mg_setup(A, prec=prec, stream=stream.cuda_stream)
@@ -282,8 +290,14 @@ def band_kernels(hn, stream, peak, L=12, reps=20):
                           ("jacobi", hn.HN_OP_JACOBI), ("restrict", hn.HN_OP_RESTRICT),
                           ("prolong", hn.HN_OP_PROLONG_ADD)):
             ms, by = hn.hn_mg_time_kernel(mg, op, L, reps=reps)
-            row[oname] = {"gb_per_s": by / (ms * 1e-3) / 1e9, "frac": by / (ms * 1e-3) / 1e9 / peak,
-                          "us": ms * 1e3, "bytes": by}
+            r = {"gb_per_s": by / (ms * 1e-3) / 1e9, "frac": by / (ms * 1e-3) / 1e9 / peak,
+                 "us": ms * 1e3, "bytes": by}
+            if pname == "fp64" and rates:
+                t_hbm = by / (peak * 1e9)
+                t_fp64 = FP64_OPS_PER_NODE[oname] * N / rates["fp64_fma_per_s"]
+                r["bound"] = "fp64" if t_fp64 > t_hbm else "hbm"
+                r["frac_of_bound"] = max(t_hbm, t_fp64) / (ms * 1e-3)
+            row[oname] = r
         band[pname] = row
         hn.hn_mg_destroy(mg)
     hn.hn_band_destroy(A)
@@ -297,9 +311,12 @@ def run_kernels(args, rank, local):
     torch.cuda.set_device(local)
     g.build()
     peak, kind = measured_peak_gbs()
-    band = band_kernels(hn, torch.cuda.current_stream(), peak, L=args.level if args.level is not None else 12)
+    rates = hn.hn_measure_fp_rates()
+    band = band_kernels(hn, torch.cuda.current_stream(), peak, L=args.level if args.level is not None else 12,
+                        rates=rates)
     if rank == 0:
         print(json.dumps({"metric": "band kernels alone, HBM GB/s", "peak": peak, "peak_kind": kind,
+                          "fp_rates": rates, "fp64_ops_per_node": FP64_OPS_PER_NODE,
                           "kernels": band}), flush=True)
 
 
@@ -762,7 +779,8 @@ def run_ours(args, rank, world, local, pg):
     # lognormal solves, the 256-problem batch
     band = l12 = batch = None
     if rank == 0:
-        band = band_kernels(hn, stream, peak)
+        rates = hn.hn_measure_fp_rates()
+        band = band_kernels(hn, stream, peak, rates=rates)
         k_steps, k_warm = max(1, min(args.steps, 5)), max(1, min(args.warmup, 2))
         l12 = l12_solves(hn, I, stream, flush, dev, k_steps, k_warm)
         batch = batch256_solves(hn, I, stream, flush, dev, max(1, min(args.steps, 10)), k_warm)
@@ -820,6 +838,8 @@ def run_ours(args, rank, world, local, pg):
             "kernel_share": dict(sorted(((k, v / prof_total) for k, v in by_class.items()),
                                         key=lambda kv: -kv[1])[:6]) if prof_total else {},
             "band_kernels_L12_frac": {p: {o: r["frac"] for o, r in row.items()} for p, row in band.items()},
+            "fp64_L12_frac_of_bound": {o: r.get("frac_of_bound") for o, r in band["fp64"].items()},
+            "fp64_tfma_per_s": rates["fp64_fma_per_s"] * 1e-12,
         }
         if serve is not None:
             line["serve"] = serve

@@ -37,6 +37,16 @@ int hn_mg_kernel_times(const hn_mg* mg, hn_kernel_time* out, int max);
  * one launch (N_l x bytes per node of the kernel and precision). */
 hn_status hn_mg_time_kernel(hn_mg* mg, int op, int level, int reps, double* avg_ms, double* bytes);
 
+/* Arithmetic rates of the current device, measured by kernels that keep the pipe busy with
+ * independent chains of one operation (operations per second; an FMA counts as one operation).
+ * The FP64 band and transfer kernels are bounded by min(HBM bandwidth / bytes per node, FP64
+ * rate / FP64 operations per node) on a part whose FP64 rate is low.  Allocates a small device
+ * buffer and a stream for the duration of the call; takes a few milliseconds. */
+typedef struct {
+  double fp64_fma_per_s, fp64_add_per_s, fp64_mul_per_s, fp32_fma_per_s;
+} hn_fp_rates;
+hn_status hn_measure_fp_rates(hn_fp_rates* out);
+
 /* Kernel launches of mg's last single solve (hn_mg_solve): the graph's init kernels plus the
  * kernels of every loop iteration that ran.  0 before the first solve. */
 long long hn_mg_last_launches(const hn_mg* mg);

@@ -533,7 +533,23 @@ __device__ __forceinline__ void restrict_tile(const LevelDev& f, const LevelDev&
     V v = V(0);
     if (q < Nc) {
       const int J = (int)((unsigned)q / (unsigned)nc), I = q - J * nc;
-      v = restrict_value<V>(I, J, nc, nf, c.bc, [&](long long k) { return ld1<LK>(r + k); });
+      if (I > 0 && J > 0 && I < nc - 1 && J < nc - 1) {
+        // an interior coarse node: its 3 x 3 fine neighbourhood lies on the grid and it is no
+        // Dirichlet node; restrict_value's sum without its per-tap bounds checks
+        const V* f = r + (long long)(2 * J) * nf + 2 * I;
+        const V qw = V(0.25), h = V(0.5);
+        v = qw * ld1<LK>(f - nf - 1);
+        v = fma(h, ld1<LK>(f - nf), v);
+        v = fma(qw, ld1<LK>(f - nf + 1), v);
+        v = fma(h, ld1<LK>(f - 1), v);
+        v = v + ld1<LK>(f);
+        v = fma(h, ld1<LK>(f + 1), v);
+        v = fma(qw, ld1<LK>(f + nf - 1), v);
+        v = fma(h, ld1<LK>(f + nf), v);
+        v = fma(qw, ld1<LK>(f + nf + 1), v);
+      } else {
+        v = restrict_value<V>(I, J, nc, nf, c.bc, [&](long long k) { return ld1<LK>(r + k); });
+      }
     }
     out[q] = v;
   }
@@ -582,28 +598,38 @@ __device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& 
     // (odd) are the same for all lanes of a warp that lie in one fine row, so the four cases
     // below are separate code paths: each node does its own formula's operations only (a
     // per-node choice between the formulas had the FP64 pipe evaluate several of them).
-    auto mid = [](V a, V b) { return V(0.5) * (a + b); };                    // edge midpoint
-    auto ctr = [](V a, V b, V c, V d) { return V(0.25) * (((a + b) + c) + d); };   // cell centre
-    V add[4];
+    // A node adds a coarse value (x + e), an edge midpoint (x + 0.5 (a + b)) or a cell centre
+    // (x + 0.25 (((a + b) + c) + d)).  The products by 0.5 and 0.25 are exact, so one FMA of the
+    // scale, the sum and x rounds exactly as prolong_value's product followed by the addition, with
+    // one FP64 operation fewer per midpoint and centre (the FP64 transfers are bound by the pipe).
+    auto pt = [](V x, V a) { return x + a; };
+    auto mid = [](V x, V a, V b) { return fma(V(0.5), a + b, x); };
+    auto ctr = [](V x, V a, V b, V c, V d) { return fma(V(0.25), ((a + b) + c) + d, x); };
+    V out[4];
     if (!oy) {
-      if (!odd) { add[0] = e0[0]; add[1] = mid(e0[0], e0[1]); add[2] = e0[1]; add[3] = mid(e0[1], e0[2]); }
-      else      { add[0] = mid(e0[0], e0[1]); add[1] = e0[1]; add[2] = mid(e0[1], e0[2]); add[3] = e0[2]; }
+      if (!odd) {
+        out[0] = pt(v[0], e0[0]); out[1] = mid(v[1], e0[0], e0[1]);
+        out[2] = pt(v[2], e0[1]); out[3] = mid(v[3], e0[1], e0[2]);
+      } else {
+        out[0] = mid(v[0], e0[0], e0[1]); out[1] = pt(v[1], e0[1]);
+        out[2] = mid(v[2], e0[1], e0[2]); out[3] = pt(v[3], e0[2]);
+      }
     } else {
       if (!odd) {
-        add[0] = mid(e0[0], e1[0]);
-        add[1] = ctr(e0[0], e0[1], e1[0], e1[1]);
-        add[2] = mid(e0[1], e1[1]);
-        add[3] = ctr(e0[1], e0[2], e1[1], e1[2]);
+        out[0] = mid(v[0], e0[0], e1[0]);
+        out[1] = ctr(v[1], e0[0], e0[1], e1[0], e1[1]);
+        out[2] = mid(v[2], e0[1], e1[1]);
+        out[3] = ctr(v[3], e0[1], e0[2], e1[1], e1[2]);
       } else {
-        add[0] = ctr(e0[0], e0[1], e1[0], e1[1]);
-        add[1] = mid(e0[1], e1[1]);
-        add[2] = ctr(e0[1], e0[2], e1[1], e1[2]);
-        add[3] = mid(e0[2], e1[2]);
+        out[0] = ctr(v[0], e0[0], e0[1], e1[0], e1[1]);
+        out[1] = mid(v[1], e0[1], e1[1]);
+        out[2] = ctr(v[2], e0[1], e0[2], e1[1], e1[2]);
+        out[3] = mid(v[3], e0[2], e1[2]);
       }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (!is_dirichlet(ix + j, iy, nf, f.bc)) v[j] = v[j] + add[j];
+      if (!is_dirichlet(ix + j, iy, nf, f.bc)) v[j] = out[j];
   } else {
     // the nodes wrap into the next row (or reach the padding): node by node
 #pragma unroll

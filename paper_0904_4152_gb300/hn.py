@@ -38,7 +38,7 @@ EXPORTS = [
     "hn_mg_set_profiling", "hn_mg_kernel_times", "hn_mg_last_launches",
     "hn_band_defect_norm_static", "hn_mg_set_tuning", "hn_mg_get_tuning", "hn_mg_autotune",
     "hn_mg_autotune_batch", "hn_mg_time_kernel", "hn_axpy", "hn_dot", "hn_nrm2",
-    "hn_band4_spmv", "hn_swe_predict",
+    "hn_band4_spmv", "hn_swe_predict", "hn_measure_fp_rates",
 ]
 
 
@@ -397,6 +397,18 @@ def hn_mg_time_kernel(mg, op, level, reps=20):
     ms, by = ctypes.c_double(), ctypes.c_double()
     _check(lib().hn_mg_time_kernel(mg, op, level, reps, ctypes.byref(ms), ctypes.byref(by)))
     return ms.value, by.value
+
+
+class FpRates(ctypes.Structure):
+    _fields_ = [("fp64_fma_per_s", ctypes.c_double), ("fp64_add_per_s", ctypes.c_double),
+                ("fp64_mul_per_s", ctypes.c_double), ("fp32_fma_per_s", ctypes.c_double)]
+
+
+def hn_measure_fp_rates():
+    """Measured arithmetic rates of the current device (operations per second), as a dict."""
+    r = FpRates()
+    _check(lib().hn_measure_fp_rates(ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in FpRates._fields_}
 
 
 def hn_mg_last_launches(mg):
