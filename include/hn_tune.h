@@ -58,6 +58,25 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
 hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const* b, int reps,
                                hn_tuning* best);
 
+/* Persisted launch shapes (the runtime configuration file of Sec. 3: choices measured on this
+ * machine, kept in a file that later runs read).  When the environment variable HN_TUNE_CACHE
+ * names a file, hn_mg_autotune stores its result there under the key (GPU name, level, precision,
+ * solver, coarse solver, coarse level), and hn_mg_setup applies the stored shape of its key to the
+ * new hierarchy (as hn_mg_set_tuning would).  The file is text, one entry per line:
+ *     <gpu name>|<L>|<prec>|<solver>|<coarse solver>|<coarse L> <tail_level> <cluster> <pdl> <staged> <dsm> <fuse_up> <mid>
+ * A store replaces the entry of its key (the file is rewritten through a temporary file and a
+ * rename); lines that do not parse, or hold values out of range, are ignored by lookups.
+ *
+ * The two calls below are the file operations themselves (host only, no device call):
+ * hn_tune_cache_lookup fills *out with the entry of the key and returns HN_OK, or returns
+ * HN_ERR_STATE when the file is missing or has no valid entry for the key; hn_tune_cache_store
+ * returns HN_ERR_ARG for a shape out of range and HN_ERR_STATE when the file cannot be written.
+ * prec, solver, coarse_solver take the values of hn_precision, hn_solver, hn_coarse_solver. */
+hn_status hn_tune_cache_lookup(const char* path, const char* gpu, int L, int prec, int solver,
+                               int coarse_solver, int coarse_L, hn_tuning* out);
+hn_status hn_tune_cache_store(const char* path, const char* gpu, int L, int prec, int solver,
+                              int coarse_solver, int coarse_L, const hn_tuning* t);
+
 #ifdef __cplusplus
 }
 #endif

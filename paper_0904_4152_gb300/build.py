@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libhn.so")
 SOURCES = ["k_cycle.cu", "k_setup.cu", "engine.cu", "api.cu", "serve.cu", "noalloc.cu", "blas1.cu",
-           "band4.cu", "peaks.cu"]
+           "band4.cu", "peaks.cu", "tune_cache.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -2,6 +2,8 @@
 // at the boundary (Sec. 4.1 explicit-copy containers), and dispatch to the engine.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -27,6 +29,16 @@ void exact_caps(const std::vector<hn_mg*>& mgs, std::vector<long long>& caps, lo
     for (int l = mg->coarse; l <= mg->L; ++l) caps[l] += pitch_of(l) / kTile;
     fine += pitch_of(mg->L) / kTile;
   }
+}
+
+// name of the current GPU (the key of the launch-shape cache)
+hn_status gpu_name(char* out, size_t cap) {
+  int dev = 0;
+  HN_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp p;
+  HN_CUDA(cudaGetDeviceProperties(&p, dev));
+  std::snprintf(out, cap, "%s", p.name);
+  return HN_OK;
 }
 
 // top level of the persistent kernels among the autotuner's candidates
@@ -183,6 +195,25 @@ hn_status hn_mg_setup(const hn_band* A, const hn_mg_opts* opts, hn_mg** out) {
     mg->own_stream = true;
   }
   HN_TRY(build_hierarchy(A, o, mg->stream, mg.get()));
+  // a launch shape measured earlier for this key on this GPU (HN_TUNE_CACHE)
+  if (const char* path = std::getenv("HN_TUNE_CACHE")) {
+    char gpu[256];
+    hn_tuning t;
+    if (path[0] && gpu_name(gpu, sizeof gpu) == HN_OK &&
+        hn_tune_cache_lookup(path, gpu, mg->L, (int)o.prec, (int)o.solver, (int)o.coarse_solver,
+                             o.coarse_L, &t) == HN_OK) {
+      Tuning tu;
+      tu.tail_level = std::max(t.tail_level, mg->coarse);
+      tu.cluster = t.cluster;
+      tu.pdl = t.pdl;
+      tu.staged = t.staged;
+      tu.dsm = t.dsm;
+      tu.fuse_up = t.fuse_up;
+      tu.mid = t.mid;
+      mg->tuning = tu;
+      mg->tuned = true;
+    }
+  }
   mg->setup_ns = now_ns() - t0;
   *out = mg.release();
   return HN_OK;
@@ -476,6 +507,15 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
     }
   HN_TRY(hn_mg_set_tuning(mg, &bt));
   if (best) *best = bt;
+  if (const char* path = std::getenv("HN_TUNE_CACHE")) {
+    char gpu[256];
+    if (path[0] && gpu_name(gpu, sizeof gpu) == HN_OK) {
+      const hn_mg_opts& o = mg->opts;
+      const hn_status st = hn_tune_cache_store(path, gpu, mg->L, (int)o.prec, (int)o.solver,
+                                               (int)o.coarse_solver, o.coarse_L, &bt);
+      if (st != HN_OK) return set_error(st, "cannot write the launch-shape cache %s", path);
+    }
+  }
   return HN_OK;
 }
 

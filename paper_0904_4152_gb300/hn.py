@@ -38,7 +38,8 @@ EXPORTS = [
     "hn_mg_set_profiling", "hn_mg_kernel_times", "hn_mg_last_launches",
     "hn_band_defect_norm_static", "hn_mg_set_tuning", "hn_mg_get_tuning", "hn_mg_autotune",
     "hn_mg_autotune_batch", "hn_mg_time_kernel", "hn_axpy", "hn_dot", "hn_nrm2",
-    "hn_band4_spmv", "hn_swe_predict", "hn_measure_fp_rates",
+    "hn_band4_spmv", "hn_swe_predict", "hn_measure_fp_rates", "hn_tune_cache_lookup",
+    "hn_tune_cache_store",
 ]
 
 
@@ -397,6 +398,23 @@ def hn_mg_time_kernel(mg, op, level, reps=20):
     ms, by = ctypes.c_double(), ctypes.c_double()
     _check(lib().hn_mg_time_kernel(mg, op, level, reps, ctypes.byref(ms), ctypes.byref(by)))
     return ms.value, by.value
+
+
+def hn_tune_cache_store(path, gpu, L, prec, solver, coarse_solver, coarse_L, shape):
+    """Store a launch shape (7-tuple as hn_mg_get_tuning returns) in the cache file `path`."""
+    _check(lib().hn_tune_cache_store(path.encode(), gpu.encode(), L, prec, solver, coarse_solver,
+                                     coarse_L, ctypes.byref(Tuning(*shape))))
+
+
+def hn_tune_cache_lookup(path, gpu, L, prec, solver, coarse_solver, coarse_L):
+    """The stored launch shape of the key, or None."""
+    t = Tuning()
+    st = lib().hn_tune_cache_lookup(path.encode(), gpu.encode(), L, prec, solver, coarse_solver,
+                                    coarse_L, ctypes.byref(t))
+    if st == HN_ERR_STATE:
+        return None
+    _check(st)
+    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm, t.fuse_up, t.mid
 
 
 class FpRates(ctypes.Structure):

@@ -456,3 +456,36 @@ def test_grouped_norm_sums_do_not_depend_on_the_schedule(hn):
     finally:
         hn.hn_mg_destroy(mg)
         hn.hn_mg_destroy(mg2)
+
+
+def test_autotuned_shape_persists_through_the_cache_file(hn, tmp_path, monkeypatch):
+    # HN_TUNE_CACHE: the autotuner stores its choice under (GPU, level, precision, solver, coarse
+    # solver, coarse level); a later hierarchy of the same key starts with it, others do not
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("HN_TUNE_CACHE", str(path))
+    L = 6
+    b = I.rhs_uniform(L, 31)
+    A = hn.hn_band_create(L)
+    mgs = []
+    try:
+        mgs.append(hn.hn_mg_setup(A, prec=1))
+        default = hn.hn_mg_get_tuning(mgs[0])
+        mgs.append(hn.hn_mg_setup(A, prec=0))
+        default64 = hn.hn_mg_get_tuning(mgs[1])
+        best, table = hn.hn_mg_autotune(mgs[0], b, reps=1)
+        tuned = hn.hn_mg_get_tuning(mgs[0])
+        assert best == (tuned[0], tuned[1], tuned[6]) and len(open(path).read().splitlines()) == 1
+        mgs.append(hn.hn_mg_setup(A, prec=1))
+        assert hn.hn_mg_get_tuning(mgs[2]) == tuned
+        mgs.append(hn.hn_mg_setup(A, prec=0))                    # another key: untouched
+        assert hn.hn_mg_get_tuning(mgs[3]) == default64
+        x1, _, _ = hn.hn_mg_solve(mgs[0], L, b)
+        x2, _, _ = hn.hn_mg_solve(mgs[2], L, b)
+        np.testing.assert_array_equal(x1, x2)
+        monkeypatch.delenv("HN_TUNE_CACHE")
+        mgs.append(hn.hn_mg_setup(A, prec=1))
+        assert hn.hn_mg_get_tuning(mgs[4]) == default
+    finally:
+        for m in mgs:
+            hn.hn_mg_destroy(m)
+        hn.hn_band_destroy(A)
