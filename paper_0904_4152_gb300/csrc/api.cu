@@ -11,6 +11,7 @@
 #include "engine.h"
 #include "../../include/hn_profile.h"
 #include "../../include/hn_tune.h"
+#include "../../include/hn_debug.h"
 
 using namespace hn;
 
@@ -28,6 +29,19 @@ void exact_caps(const std::vector<hn_mg*>& mgs, std::vector<long long>& caps, lo
   for (hn_mg* mg : mgs) {
     for (int l = mg->coarse; l <= mg->L; ++l) caps[l] += pitch_of(l) / kTile;
     fine += pitch_of(mg->L) / kTile;
+  }
+}
+
+// the engine's device error words after a solve: a bounded wait that gave up, or (debug builds) a
+// failed index check
+hn_status device_error(Engine& e) {
+  int d[4] = {0, 0, 0, 0};
+  HN_TRY(e.read_error_detail(d));
+  switch (d[0]) {
+    case 0: return HN_OK;
+    case 3: return set_error(HN_ERR_CUDA, "a grid barrier of the persistent kernels timed out");
+    case 5: return set_error(HN_ERR_STATE, "debug check failed (k_cycle.cu line %d, indices %d, %d)", d[1], d[2], d[3]);
+    default: return set_error(HN_ERR_CUDA, "a bounded device wait for a bulk copy gave up");
   }
 }
 
@@ -131,7 +145,36 @@ void fill_stats(const hn_mg* mg, const ProbState& st, long long t0, hn_mg_stats*
 extern "C" {
 
 const char* hn_last_error(void) { return hn::last_error(); }
-const char* hn_version(void) { return "hn 0.1 (sm_103a)"; }
+const char* hn_version(void) { return HN_DEBUG_CHECKS ? "hn 0.2 (sm_103a, debug checks)" : "hn 0.2 (sm_103a)"; }
+
+int hn_debug_build(void) { return HN_DEBUG_CHECKS; }
+
+hn_status hn_debug_check_mg(const hn_mg* mg) {
+  clear_error();
+  if (!mg) return set_error(HN_ERR_ARG, "null hierarchy");
+  if (!HN_DEBUG_CHECKS) return set_error(HN_ERR_STATE, "library built without HN_DEBUG_CHECKS");
+  if (mg->stream) HN_CUDA(cudaStreamSynchronize(mg->stream));
+  HN_TRY(guards_intact(mg->mem_base, mg->bytes, "hierarchy block"));
+  if (mg->solo) HN_TRY(mg->solo->check_guards());
+  return HN_OK;
+}
+
+hn_status hn_debug_check_band(const hn_band* A) {
+  clear_error();
+  if (!A) return set_error(HN_ERR_ARG, "null operator");
+  if (!HN_DEBUG_CHECKS) return set_error(HN_ERR_STATE, "library built without HN_DEBUG_CHECKS");
+  return guards_intact(A->mem_base, A->mem_bytes, "operator block");
+}
+
+hn_status hn_debug_overwrite_guard(hn_mg* mg) {
+  clear_error();
+  if (!mg) return set_error(HN_ERR_ARG, "null hierarchy");
+  if (!HN_DEBUG_CHECKS || !mg->mem_base)
+    return set_error(HN_ERR_STATE, "no guarded hierarchy block (debug builds, library-allocated blocks)");
+  if (mg->stream) HN_CUDA(cudaStreamSynchronize(mg->stream));
+  HN_CUDA(cudaMemset(static_cast<char*>(mg->mem_base) + kGuardBytes + mg->bytes, 0, 1));
+  return HN_OK;
+}
 
 hn_status hn_band_create(int L, const double* cell_coef, hn_band** out) {
   return hn_band_create_bc(L, cell_coef, HN_DIRICHLET_ALL, out);
@@ -247,10 +290,7 @@ hn_status hn_mg_solve(hn_mg* mg, const double* b, double* x, int x_is_guess, int
   HN_TRY(e.run_to_completion());
   std::vector<ProbState> st;
   HN_TRY(e.read_states(st));
-  int derr = 0;
-  HN_TRY(e.read_error(&derr));
-  if (derr) return set_error(HN_ERR_CUDA, derr == 3 ? "a grid barrier of the persistent kernels timed out"
-                                                  : "a bounded device wait for a bulk copy gave up");
+  HN_TRY(device_error(e));
   if (st[0].status != HN_ERR_ARG) {
     if (st[0].status == HN_OK && st[0].bnorm == 0.0) HN_CUDA(cudaMemsetAsync(P.x64, 0, (size_t)N * 8, s));
     HN_TRY(copy_out(x, P.x64, N, device_ptrs, s));
@@ -310,7 +350,7 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
     const Tuning t = batch_tuning(list);
     const Tuning& c = e.tuning();
     if (t.tail_level != c.tail_level || t.cluster != c.cluster || t.pdl != c.pdl || t.staged != c.staged ||
-        t.dsm != c.dsm || t.fuse_up != c.fuse_up)
+        t.dsm != c.dsm || t.fuse_up != c.fuse_up || t.mid != c.mid)
       e.set_tuning(t);
   }
   cudaStream_t s = e.stream();
@@ -326,10 +366,7 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
   HN_TRY(e.run_to_completion());
   std::vector<ProbState> st;
   HN_TRY(e.read_states(st));
-  int derr = 0;
-  HN_TRY(e.read_error(&derr));
-  if (derr) return set_error(HN_ERR_CUDA, derr == 3 ? "a grid barrier of the persistent kernels timed out"
-                                                  : "a bounded device wait for a bulk copy gave up");
+  HN_TRY(device_error(e));
   hn_status first_bad = HN_OK;
   for (int j = 0; j < count; ++j) {
     ProblemDev& P = list[j]->host;

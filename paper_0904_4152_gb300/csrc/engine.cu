@@ -38,6 +38,37 @@ hn_status set_error(hn_status st, const char* fmt, ...) {
 void clear_error() { t_err.clear(); }
 const char* last_error() { return t_err.c_str(); }
 
+hn_status guarded_alloc(size_t bytes, void** base, void** mem) {
+  *base = *mem = nullptr;
+  char* p = nullptr;
+  HN_CUDA(cudaMalloc(reinterpret_cast<void**>(&p), bytes + 2 * kGuardBytes));
+  if (kGuardBytes) {
+    const cudaError_t e1 = cudaMemset(p, kGuardByte, kGuardBytes);
+    const cudaError_t e2 = cudaMemset(p + kGuardBytes + bytes, kGuardByte, kGuardBytes);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      cudaFree(p);
+      return set_error(HN_ERR_CUDA, "guard initialisation failed");
+    }
+  }
+  *base = p;
+  *mem = p + kGuardBytes;
+  return HN_OK;
+}
+
+hn_status guards_intact(const void* base, size_t bytes, const char* what) {
+  if (!kGuardBytes || !base) return HN_OK;
+  std::vector<unsigned char> g(2 * kGuardBytes);
+  const char* p = static_cast<const char*>(base);
+  HN_CUDA(cudaMemcpy(g.data(), p, kGuardBytes, cudaMemcpyDeviceToHost));
+  HN_CUDA(cudaMemcpy(g.data() + kGuardBytes, p + kGuardBytes + bytes, kGuardBytes, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < g.size(); ++i)
+    if (g[i] != kGuardByte)
+      return set_error(HN_ERR_STATE, "%s: guard byte %s the block overwritten (offset %lld)", what,
+                       i < kGuardBytes ? "before" : "after",
+                       i < kGuardBytes ? (long long)i - (long long)kGuardBytes : (long long)(i - kGuardBytes));
+  return HN_OK;
+}
+
 int sm_count() {
   static int cached = 0;
   static std::once_flag once;
@@ -238,7 +269,10 @@ hn_status build_band(int L, const double* cell_coef, unsigned bc, cudaStream_t s
   A->pitch = pitch_of(L);
   const long long cells = (1LL << L) * (1LL << L);
   if (mem) A->mem = mem;
-  else HN_CUDA(cudaMalloc(&A->mem, band_bytes(L, cell_coef != nullptr)));
+  else {
+    A->mem_bytes = band_bytes(L, cell_coef != nullptr);
+    HN_TRY(guarded_alloc(A->mem_bytes, &A->mem_base, &A->mem));
+  }
   Bump b{static_cast<char*>(A->mem), 0};
   BandPtrs64 bp{};
   for (int k = 0; k < 9; ++k) bp.p[k] = A->band[k] = b.take<double>(A->pitch);
@@ -272,7 +306,7 @@ hn_status build_hierarchy(const hn_band* A, const hn_mg_opts& o, cudaStream_t s,
   mg->m = ur.nx * ur.ny;
   mg->bytes = hierarchy_bytes(L, c, prec, prm.solver);
   if (mem) mg->mem = mem;                       // a block of exactly mg->bytes from the caller
-  else HN_CUDA(cudaMalloc(&mg->mem, mg->bytes));
+  else HN_TRY(guarded_alloc(mg->bytes, &mg->mem_base, &mg->mem));
   HN_CUDA(cudaMemsetAsync(mg->mem, 0, mg->bytes, s));
 
   ProblemDev& P = mg->host;
@@ -441,7 +475,7 @@ Engine::~Engine() {
   destroy_graphs();
   for (auto& m : marks_) { cudaEventDestroy(m.b); cudaEventDestroy(m.e); }
   if (upEv_) cudaEventSynchronize(upEv_);
-  if (mem_) cudaFree(mem_);
+  if (memBase_) cudaFree(memBase_);
   if (hActive_) cudaFreeHost(hActive_);
   if (hStage_) cudaFreeHost(hStage_);
   if (hLists_) cudaFreeHost(hLists_);
@@ -490,7 +524,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
     take(sizeof(int4) * (size_t)std::max<long long>(chunkCap_[l], 1));
   }
   take(sizeof(int) * (kMaxLevel + 1));
-  take(sizeof(int));
+  take(sizeof(int) * 4);
   fineCap_ = fine_cap;
   take(sizeof(int2) * (size_t)std::max<long long>(fine_cap, 1));
   take(sizeof(double) * (size_t)std::max<long long>(fine_cap, 1));
@@ -506,7 +540,8 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   take(sizeof(TileList) * (kMaxLevel + 1));
   take(sizeof(unsigned long long) * 3);
   bytes += 256;
-  HN_CUDA(cudaMalloc(&mem_, bytes));
+  memBytes_ = bytes;
+  HN_TRY(guarded_alloc(bytes, &memBase_, &mem_));
   HN_CUDA(cudaMemsetAsync(mem_, 0, bytes, s_));
   Bump b{static_cast<char*>(mem_), 0};
   dP_ = b.take<ProblemDev>(cap);
@@ -518,7 +553,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
     dChunks_[l] = b.take<int4>((size_t)std::max<long long>(chunkCap_[l], 1));
   }
   dChunkCounts_ = b.take<int>(kMaxLevel + 1);
-  dErr_ = b.take<int>(1);
+  dErr_ = b.take<int>(4);
   dFine_ = b.take<int2>((size_t)std::max<long long>(fine_cap, 1));
   double* part = b.take<double>((size_t)std::max<long long>(fine_cap, 1));
   double* part2 = b.take<double>((size_t)std::max<long long>(fine_cap, 1));
@@ -677,7 +712,7 @@ hn_status Engine::start(const std::vector<int>& slots, const std::vector<int>& h
   // the iteration counter restarts with every closed-world solve (serving keeps counting and
   // relies on per-problem caps; its limit is set out of reach)
   HN_CUDA(cudaMemsetAsync(E_.iter, 0, sizeof(unsigned), s_));
-  HN_CUDA(cudaMemsetAsync(dErr_, 0, sizeof(int), s_));
+  HN_CUDA(cudaMemsetAsync(dErr_, 0, sizeof(int) * 4, s_));
   HN_CUDA(cudaMemsetAsync(dBar_, 0, sizeof(unsigned long long) * 3, s_));
   // mirrors of the IF values as the closed-world graph sets them at its launch
   static const unsigned taken0[4] = {0u, 1u, 0u, 0u};
@@ -1210,6 +1245,14 @@ hn_status Engine::read_states(std::vector<ProbState>& out) {
   return HN_OK;
 }
 
+hn_status Engine::read_error_detail(int (&err)[4]) {
+  HN_CUDA(cudaMemcpyAsync(err, dErr_, sizeof(int) * 4, cudaMemcpyDeviceToHost, s_));
+  HN_CUDA(cudaStreamSynchronize(s_));
+  return HN_OK;
+}
+
+hn_status Engine::check_guards() const { return guards_intact(memBase_, memBytes_, "engine block"); }
+
 hn_status Engine::read_error(int* err) {
   HN_CUDA(cudaMemcpyAsync(err, dErr_, sizeof(int), cudaMemcpyDeviceToHost, s_));
   HN_CUDA(cudaStreamSynchronize(s_));
@@ -1244,11 +1287,13 @@ hn_status Engine::apply(int op, int level, int want, cudaStream_t s) {
 }  // namespace hn
 
 hn_band::~hn_band() {
-  if (mem) cudaFree(mem);
+  if (mem_base) cudaFree(mem_base);
+  else if (mem) cudaFree(mem);
 }
 
 hn_mg::~hn_mg() {
   delete solo;
-  if (mem) cudaFree(mem);
+  if (mem_base) cudaFree(mem_base);
+  else if (mem) cudaFree(mem);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }

@@ -50,6 +50,19 @@ struct Bump {
   }
 };
 
+// Debug builds (HN_DEBUG_CHECKS=1): every device block the library allocates for an operator, a
+// hierarchy or an engine carries kGuardBytes of a fixed pattern before and after it, checked by
+// hn_debug_check_mg / hn_debug_check_band; release builds allocate the block alone.
+#ifndef HN_DEBUG_CHECKS
+#define HN_DEBUG_CHECKS 0
+#endif
+constexpr size_t kGuardBytes = HN_DEBUG_CHECKS ? 4096 : 0;
+constexpr unsigned char kGuardByte = 0xC3;
+// allocate bytes (+ guards) on the device: *base is what to free, *mem the usable block
+hn_status guarded_alloc(size_t bytes, void** base, void** mem);
+// the guards of a block from guarded_alloc are intact (always HN_OK in release builds)
+hn_status guards_intact(const void* base, size_t bytes, const char* what);
+
 // device bytes a hierarchy of fine level L needs (same arithmetic as its construction)
 size_t hierarchy_bytes(int L, int coarse, int prec, int solver);
 
@@ -102,6 +115,8 @@ struct hn_band {
   double* coef = nullptr;   // device cell coefficients, nullptr for a = 1
   unsigned bc = 15u;        // Dirichlet sides (HN_DIRICHLET_*); the others are free Neumann
   int device = 0;           // CUDA device the bands live on (current at creation)
+  void* mem_base = nullptr; // the allocation of mem with its guards (nullptr: mem came from a caller)
+  size_t mem_bytes = 0;
   ~hn_band();
 };
 
@@ -118,6 +133,7 @@ struct hn_mg {
   hn::Engine* solo = nullptr;
   hn::Tuning tuning{};        // launch shape chosen for this hierarchy (hn_mg_set_tuning)
   bool tuned = false;
+  void* mem_base = nullptr;   // the allocation of mem with its guards (nullptr: mem came from a caller)
   ~hn_mg();
 };
 
@@ -163,6 +179,10 @@ class Engine {
   hn_status read_states(std::vector<ProbState>& out);
   // the device error word (a bounded wait gave up); reset by start()
   hn_status read_error(int* err);
+  // the device error word and the details a failed debug check recorded (source line, two indices)
+  hn_status read_error_detail(int (&err)[4]);
+  // the guards of the engine's device block (debug builds)
+  hn_status check_guards() const;
   hn_status read_states_async(ProbState* host_dst);
   // single-kernel execution on slot 0 (hn_mg_apply)
   hn_status apply(int op, int level, int want, cudaStream_t s);
@@ -204,6 +224,8 @@ class Engine {
   int cap_ = 0, Lmax_ = 0;
   cudaStream_t s_ = nullptr;
   void* mem_ = nullptr;
+  void* memBase_ = nullptr;      // mem_ with its guards
+  size_t memBytes_ = 0;
   unsigned* hActive_ = nullptr;  // mapped pinned
   EngineDev E_{};
   ProblemDev* dP_ = nullptr;

@@ -40,6 +40,52 @@ __device__ __forceinline__ void pdl_start() {
   pdl_wait();
 }
 
+// ------------------------------------------------------------ debug-build index checks
+// With HN_DEBUG_CHECKS the kernels check every work-list item (problem slot, level, tile) and
+// every one-problem level descriptor against the hierarchy's layout before touching memory; a
+// failed check records the source line and the indices in the engine's error words (the first
+// failure wins), skips the access and lets the launch finish.  Release builds compile the checks
+// to nothing.
+#ifndef HN_DEBUG_CHECKS
+#define HN_DEBUG_CHECKS 0
+#endif
+__device__ __forceinline__ void dbg_fail(const EngineDev& E, int line, int a, int b) {
+  if (atomicCAS(E.err, 0, 5) == 0) {
+    E.err[1] = line;
+    E.err[2] = a;
+    E.err[3] = b;
+  }
+}
+// problem p's tile `tile` of level lv (lv < 0: its finest level)
+__device__ __forceinline__ bool dbg_item(const EngineDev& E, int p, int tile, int lv, int line) {
+#if HN_DEBUG_CHECKS
+  bool ok = p >= 0 && p < E.nprob;
+  if (ok) {
+    const ProblemDev& P = E.P[p];
+    const int l = lv < 0 ? P.L : lv;
+    ok = l >= P.coarse && l <= P.L && P.lev[l].n == (1 << l) + 1 && tile >= 0 &&
+         (long long)(tile + 1) * kTile <= (long long)P.lev[l].pitch;
+  }
+  if (!ok) dbg_fail(E, line, p, tile);
+  return ok;
+#else
+  (void)E; (void)p; (void)tile; (void)lv; (void)line;
+  return true;
+#endif
+}
+// a one-problem descriptor of level l serving `tiles` tiles
+__device__ __forceinline__ bool dbg_level(const EngineDev& E, const LevelDev& d, int l, int tiles, int line) {
+#if HN_DEBUG_CHECKS
+  const bool ok = l >= HN_MIN_LEVEL && l <= kMaxLevel && d.n == (1 << l) + 1 && tiles >= 0 &&
+                  (long long)tiles * kTile <= (long long)d.pitch;
+  if (!ok) dbg_fail(E, line, l, tiles);
+  return ok;
+#else
+  (void)E; (void)d; (void)l; (void)tiles; (void)line;
+  return true;
+#endif
+}
+
 // An engine of one problem skips a whole fine-level launch when its problem is not in the phase
 // the kernel serves (otherwise every warp would walk its share of the work list to find that out:
 // ~20 us per empty launch at L = 12)
@@ -961,6 +1007,7 @@ __global__ void __launch_bounds__(256, band_min_blocks<Pol, MODE>()) k_band(Engi
   if (tl.solo_tiles > 0 && level >= 0) {          // one problem: descriptors by value
     const ProbState& st = E.S[0];
     if (st.phase != want) return;
+    if (!dbg_level(E, tl.solo_d, level, tl.solo_tiles, __LINE__)) return;
     if constexpr (MODE == M_PJ) {
       if (tl.solo_c.n == 0) return;               // (no coarser level: nothing to prolong)
       for (int t = gw; t < tl.solo_tiles; t += nw)
@@ -984,6 +1031,7 @@ __global__ void __launch_bounds__(256, band_min_blocks<Pol, MODE>()) k_band(Engi
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
     const int p = it.x;
+    if (!dbg_item(E, p, it.y, level, __LINE__)) continue;
     const ProbState& st = E.S[p];
     if (st.phase != want) continue;
     const ProblemDev& P = E.P[p];
@@ -1113,6 +1161,8 @@ __global__ void __launch_bounds__(256) k_restrict(EngineDev E, TileList tl, int 
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   if (tl.solo_tiles > 0) {                        // one problem: tl is the coarse level's list
     if (tl.solo_L < fine_level || E.S[0].phase != want) return;   // (no finer level: no descriptor)
+    if (!dbg_level(E, tl.solo_d, fine_level - 1, tl.solo_tiles, __LINE__) ||
+        !dbg_level(E, tl.solo_f, fine_level, 0, __LINE__)) return;
     for (int t = gw; t < tl.solo_tiles; t += nw)
       restrict_tile<V, LD_NC>(tl.solo_f, tl.solo_d, (long long)t * kTile, lane);
     return;
@@ -1121,6 +1171,7 @@ __global__ void __launch_bounds__(256) k_restrict(EngineDev E, TileList tl, int 
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
     const int p = it.x;
+    if (!dbg_item(E, p, it.y, fine_level - 1, __LINE__)) continue;
     const ProblemDev& P = E.P[p];
     if (P.L < fine_level || E.S[p].phase != want) continue;
     restrict_tile<V, LD_NC>(P.lev[fine_level], P.lev[fine_level - 1], (long long)it.y * kTile, lane);
@@ -1136,6 +1187,8 @@ __global__ void __launch_bounds__(256) k_prolong(EngineDev E, TileList tl, int l
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   if (tl.solo_tiles > 0) {                        // one problem: descriptors by value
     if (tl.solo_c.n == 0 || E.S[0].phase != want) return;   // (no coarser level: nothing to add)
+    if (!dbg_level(E, tl.solo_d, level, tl.solo_tiles, __LINE__) ||
+        !dbg_level(E, tl.solo_c, level - 1, 0, __LINE__)) return;
     for (int t = gw; t < tl.solo_tiles; t += nw)
       prolong_tile<V, LD_NC>(tl.solo_d, tl.solo_c, x_sel, (long long)t * kTile + lane * kLaneNodes);
     return;
@@ -1144,6 +1197,7 @@ __global__ void __launch_bounds__(256) k_prolong(EngineDev E, TileList tl, int l
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
     const int p = it.x;
+    if (!dbg_item(E, p, it.y, level, __LINE__) || !dbg_item(E, p, 0, level - 1, __LINE__)) continue;
     if (E.S[p].phase != want) continue;
     const ProblemDev& P = E.P[p];
     prolong_tile<V, LD_NC>(P.lev[level], P.lev[level - 1], x_sel,
@@ -2067,6 +2121,10 @@ __device__ void mid_solo_load(const EngineDev& E, const TileList* lists, int M, 
     reinterpret_cast<unsigned*>(&ms.lev[l])[w] = reinterpret_cast<const unsigned*>(&lists[l].solo_d)[w];
   }
   __syncthreads();
+  if (threadIdx.x == 0 && ms.on)
+    for (int l = T; l <= M; ++l)
+      if (!dbg_level(E, ms.lev[l], l, (int)(ms.lev[l].pitch / kTile), __LINE__)) ms.in_phase = 0;
+  __syncthreads();
 }
 
 // One pass of band-kernel mode MODE over level l of every problem in phase `want`, spread over all
@@ -2091,6 +2149,7 @@ __device__ __forceinline__ void mid_band_pass(const EngineDev& E, const MidSolo&
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
     const int p = it.x;
+    if (!dbg_item(E, p, it.y, l, __LINE__)) continue;
     const ProbState& st = E.S[p];
     if (__ldcg(&st.phase) != want) continue;
     const ProblemDev& P = E.P[p];
@@ -2118,6 +2177,7 @@ __device__ __forceinline__ void mid_restrict_pass(const EngineDev& E, const MidS
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
     const int p = it.x;
+    if (!dbg_item(E, p, it.y, l - 1, __LINE__)) continue;
     const ProblemDev& P = E.P[p];
     if (P.L < l || __ldcg(&E.S[p].phase) != want) continue;
     restrict_tile<V, LD_CG>(P.lev[l], P.lev[l - 1], (long long)it.y * kTile, lane);
@@ -2139,6 +2199,7 @@ __device__ __forceinline__ void mid_prolong_pass(const EngineDev& E, const MidSo
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
     const int p = it.x;
+    if (!dbg_item(E, p, it.y, l, __LINE__) || !dbg_item(E, p, 0, l - 1, __LINE__)) continue;
     if (__ldcg(&E.S[p].phase) != want) continue;
     const ProblemDev& P = E.P[p];
     prolong_tile<V, LD_CG>(P.lev[l], P.lev[l - 1], x_sel, (long long)it.y * kTile + lane * kLaneNodes);
@@ -2287,6 +2348,7 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
+    if (!dbg_item(E, it.x, it.y, -1, __LINE__)) continue;   // a tile of the finest level
     const int p = it.x;
     const ProbState& st = E.S[p];
     if (st.phase != PH_OUTER) continue;
@@ -2337,6 +2399,7 @@ __global__ void __launch_bounds__(256) k_pcg_q(EngineDev E, TileList tl) {
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
+    if (!dbg_item(E, it.x, it.y, -1, __LINE__)) continue;   // a tile of the finest level
     const ProbState& st = E.S[it.x];
     if (st.phase != PH_OUTER || st.cycles == 0) continue;
     const ProblemDev& P = E.P[it.x];
@@ -2365,6 +2428,7 @@ __global__ void __launch_bounds__(256) k_pcg_x(EngineDev E, TileList tl) {
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
+    if (!dbg_item(E, it.x, it.y, -1, __LINE__)) continue;   // a tile of the finest level
     const ProbState& st = E.S[it.x];
     if (st.phase != PH_OUTER || st.cycles == 0) continue;
     const ProblemDev& P = E.P[it.x];
@@ -2403,6 +2467,7 @@ __global__ void __launch_bounds__(256) k_pcg_dot(EngineDev E, TileList tl) {
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
+    if (!dbg_item(E, it.x, it.y, -1, __LINE__)) continue;   // a tile of the finest level
     if (E.S[it.x].phase != PH_PRECOND) continue;
     const ProblemDev& P = E.P[it.x];
     const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
@@ -2429,6 +2494,7 @@ __global__ void __launch_bounds__(256) k_pcg_p(EngineDev E, TileList tl) {
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
+    if (!dbg_item(E, it.x, it.y, -1, __LINE__)) continue;   // a tile of the finest level
     const ProbState& st = E.S[it.x];
     if (st.phase != PH_UPDATE) continue;
     const ProblemDev& P = E.P[it.x];
@@ -2454,6 +2520,7 @@ __global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl) {
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
+    if (!dbg_item(E, it.x, it.y, -1, __LINE__)) continue;   // a tile of the finest level
     const int p = it.x;
     const ProbState& st = E.S[p];
     if (st.phase != PH_UPDATE) continue;
@@ -2480,6 +2547,7 @@ __global__ void __launch_bounds__(256) k_norm_b(EngineDev E, TileList tl) {
   const int count = *tl.count;
   for (int g = gw; g < count; g += nw) {
     const int2 it = tl.items[g];
+    if (!dbg_item(E, it.x, it.y, -1, __LINE__)) continue;   // a tile of the finest level
     const int p = it.x;
     if (E.S[p].phase != PH_INIT) continue;
     const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;

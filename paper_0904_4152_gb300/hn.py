@@ -11,7 +11,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhn.so")
+# HN_DEBUG_CHECKS=1 in the environment loads the checked build (include/hn_debug.h)
+LIB_PATH = os.path.join(HERE, "libhn_debug.so" if os.environ.get("HN_DEBUG_CHECKS") == "1" else "libhn.so")
 
 HN_OK, HN_ERR_ARG, HN_ERR_OOM, HN_ERR_BUDGET, HN_ERR_CUDA = 0, 1, 2, 3, 4
 HN_ERR_NOT_CONVERGED, HN_ERR_NONFINITE, HN_PENDING, HN_ERR_TIMEOUT, HN_ERR_STATE = 5, 6, 7, 8, 9
@@ -39,7 +40,8 @@ EXPORTS = [
     "hn_band_defect_norm_static", "hn_mg_set_tuning", "hn_mg_get_tuning", "hn_mg_autotune",
     "hn_mg_autotune_batch", "hn_mg_time_kernel", "hn_axpy", "hn_dot", "hn_nrm2",
     "hn_band4_spmv", "hn_swe_predict", "hn_measure_fp_rates", "hn_tune_cache_lookup",
-    "hn_tune_cache_store",
+    "hn_tune_cache_store", "hn_debug_build", "hn_debug_check_mg", "hn_debug_check_band",
+    "hn_debug_overwrite_guard",
 ]
 
 
@@ -118,6 +120,9 @@ def lib():
         L.hn_mg_device_bytes.argtypes = [vp]
         L.hn_mg_device_bytes.restype = ctypes.c_size_t
         L.hn_mg_destroy.argtypes = [vp]
+        L.hn_debug_check_mg.argtypes = [vp]
+        L.hn_debug_check_band.argtypes = [vp]
+        L.hn_debug_overwrite_guard.argtypes = [vp]
         L.hn_mg_destroy.restype = None
         L.hn_mg_apply.argtypes = [vp, ip, ip, ip, vp, vp, vp, dp]
         L.hn_mg_get_inner_bands.argtypes = [vp, ip, vp, ctypes.POINTER(ctypes.c_float)]
@@ -228,7 +233,13 @@ def hn_band_nodes(A):
 
 
 def hn_band_destroy(A):
+    """Free the operator; the checked build first verifies the guards around its device block and
+    raises HnError if they were overwritten."""
+    st = lib().hn_debug_check_band(A) if A and lib().hn_debug_build() else HN_OK
+    msg = hn_last_error()
     lib().hn_band_destroy(A)
+    if st != HN_OK:
+        raise HnError(st, msg)
 
 
 def hn_mg_opts_default(**overrides):
@@ -295,7 +306,25 @@ def hn_mg_device_bytes(mg):
 
 
 def hn_mg_destroy(mg):
+    """Free the hierarchy; the checked build first verifies the guards around its device blocks and
+    raises HnError if they were overwritten."""
+    st = lib().hn_debug_check_mg(mg) if mg and lib().hn_debug_build() else HN_OK
+    msg = hn_last_error()
     lib().hn_mg_destroy(mg)
+    if st != HN_OK:
+        raise HnError(st, msg)
+
+
+def hn_debug_build():
+    return bool(lib().hn_debug_build())
+
+
+def hn_debug_check_mg(mg):
+    _check(lib().hn_debug_check_mg(mg))
+
+
+def hn_debug_overwrite_guard(mg):
+    _check(lib().hn_debug_overwrite_guard(mg))
 
 
 def hn_mg_apply(mg, op, level, inner, in1=None, in2=None, want_norm=False):
