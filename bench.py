@@ -1048,14 +1048,14 @@ class RequestInputs:
                 self.take(k)
             except Exception:
                 pass
-        for shm, c, b in self.ready.values():
+        for key in list(self.ready):
+            shm, c, b = self.ready.pop(key)
             del c, b
             try:
                 shm.close()
-            except BufferError:
+            except BufferError:                        # a caller still holds a view of it
                 pass
             shm.unlink()
-        self.ready.clear()
         self.pool.terminate()
         if self.saved is not None:
             try:

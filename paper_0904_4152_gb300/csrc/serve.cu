@@ -179,6 +179,18 @@ struct hn_server {
 
 namespace {
 
+// Detach a device block from its owner for the block cache.  A block the server supplied (no
+// base) or one the library allocated without guards (base == block) moves to the cache and its
+// owner forgets it; a guarded block of the checked build (base != block) stays with its owner,
+// which frees it.  Returns the block for the cache, or nullptr.
+void* detach_block(void*& mem, void*& base) {
+  if (!mem || (base && base != mem)) return nullptr;
+  void* b = mem;
+  mem = nullptr;
+  base = nullptr;
+  return b;
+}
+
 size_t request_bytes(int L, const hn_mg_opts& o) {
   const Params p = params_from(o);
   // resident hierarchy + the transient fine operator built during admission
@@ -288,8 +300,7 @@ void hn_server::run() {
         mg = h.release();
       }
       if (A) {                                      // (later users of the block run on stream s2)
-        cache.give(A->mem, bb);
-        A->mem = nullptr;
+        if (void* blk = detach_block(A->mem, A->mem_base)) cache.give(blk, bb);
         hn_band_destroy(A);
       }
       if (st == HN_OK) {
@@ -349,11 +360,10 @@ void hn_server::run() {
     for (auto& [q, r] : done_now) {
       r->b.release();                               // the inputs were consumed at admission
       r->coef.release();
-      void* hmem = r->mg->mem;                      // kept for the next request of its size
-      const size_t hbytes = r->mg->bytes;
-      r->mg->mem = nullptr;
+      const size_t hbytes = r->mg->bytes;           // kept for the next request of its size
+      void* hmem = detach_block(r->mg->mem, r->mg->mem_base);
       hn_mg_destroy(r->mg);
-      cache.give(hmem, hbytes);
+      if (hmem) cache.give(hmem, hbytes);
       running[q] = nullptr;
       std::lock_guard<std::mutex> lk(mu);
       r->mg = nullptr;
