@@ -1284,6 +1284,16 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+// Block-wide copy of `bytes` (a multiple of 16; both ends 16-byte aligned) from global to shared
+// memory by cp.async, each thread taking every blockDim.x-th 16-byte chunk; a thread waits for its
+// own chunks with cp_async_wait(), then the block synchronizes.  (Issued by all threads at once,
+// the fused tail's many small constant arrays land within a microsecond or two; one thread issuing
+// one bulk copy per array took ~1.5 us per level.)
+__device__ __forceinline__ void block_copy16(void* dst, const void* src, long long bytes) {
+  const int chunks = (int)(bytes / 16);
+  for (int q = threadIdx.x; q < chunks; q += blockDim.x)
+    cp_async16(static_cast<uint4*>(dst) + q, static_cast<const uint4*>(src) + q);
+}
 
 // shared-memory bytes of levels coarse..S for a precision (16-byte aligned pieces)
 __host__ __device__ inline long long smem_level_bytes(int l, int prec) {
@@ -1297,13 +1307,14 @@ __host__ __device__ inline long long smem_level_bytes(int l, int prec) {
   return 9 * al(e * bs) + 4 * al(e * vs) + al(e * (prec == P64 ? 8 : 4));
 }
 
-// carve level l of the shared-memory hierarchy starting at *off; with `fill`, start the bulk
-// copies of its bands (and omega/D, thread 0, accounted on bar) and zero its vectors.  The caller
-// arrives on bar, waits for its phase and synchronizes the block before use.  Every block of a cluster carves
+// carve level l of the shared-memory hierarchy starting at *off; with `fill`, start the copies of
+// its bands and omega/D (block_copy16) and zero its vectors.  The caller waits for its copies
+// (cp_async_wait) and synchronizes the block before use.  Every block of a cluster carves
 // the same layout, so a block can address block 0's copy through distributed shared memory.
 template <class Pol>
 __device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* base, long long* off,
                                  int l, bool fill, unsigned long long* bar) {
+  (void)bar;
   using V = typename Pol::V;
   using B = typename Pol::B;
   const long long halo = (((1LL << l) + 1 + 8) + 31) / 32 * 32;
@@ -1314,16 +1325,16 @@ __device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* 
   for (int k = 0; k < 9; ++k) {
     B* dst = reinterpret_cast<B*>(take(e * sizeof(B)));
     const B* src = static_cast<const B*>(g.band[k]) - halo;
-    if (fill && threadIdx.x == 0) bulk_copy(dst, src, (unsigned)(e * sizeof(B)), bar);
+    if (fill) block_copy16(dst, src, e * (long long)sizeof(B));
     t.band[k] = dst + halo;
   }
   if constexpr (Pol::prec == P64) {
     double* dst = reinterpret_cast<double*>(take(e * 8));
-    if (fill && threadIdx.x == 0) bulk_copy(dst, g.wdinv - halo, (unsigned)(e * 8), bar);
+    if (fill) block_copy16(dst, g.wdinv - halo, e * 8);
     t.wdinv = dst + halo;
   } else {
     float* dst = reinterpret_cast<float*>(take(e * 4));
-    if (fill && threadIdx.x == 0) bulk_copy(dst, g.wdf - halo, (unsigned)(e * 4), bar);
+    if (fill) block_copy16(dst, g.wdf - halo, e * 4);
     t.wdf = dst + halo;
   }
   V* vec[4];
@@ -1604,7 +1615,7 @@ __device__ void dsm_level_setup(const LevelDev& g, LevelDev& v, unsigned char* b
   for (int k = 0; k < 9; ++k) {
     B* dst = reinterpret_cast<B*>(take(nb * sizeof(B)));
     const B* src = static_cast<const B*>(g.band[k]) + g0b;
-    if (threadIdx.x == 0) bulk_copy(dst, src, (unsigned)bchunks * 16u, bar);
+    block_copy16(dst, src, (long long)bchunks * 16);
     t.band[k] = dst - g0b;
   }
   const int vchunks = (int)((R1n + n + 1 - g0v + av - 1) / av);
@@ -1613,7 +1624,7 @@ __device__ void dsm_level_setup(const LevelDev& g, LevelDev& v, unsigned char* b
     const V* src;
     if constexpr (Pol::prec == P64) src = g.wdinv + g0v;
     else src = g.wdf + g0v;
-    if (threadIdx.x == 0) bulk_copy(dst, src, (unsigned)vchunks * 16u, bar);
+    block_copy16(dst, src, (long long)vchunks * 16);
     if constexpr (Pol::prec == P64) t.wdinv = dst - g0v;
     else t.wdf = dst - g0v;
   }
@@ -1855,12 +1866,12 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
       cg_pq = reinterpret_cast<double*>(smem + off);
       off += ((long long)2 * Nc * 8 + 15) / 16 * 16;
     }
-    if (rank == 0 && threadIdx.x == 0) {
-      if (staged) {
-        bulk_copy(dst, P.cinv, (unsigned)(words / 2) * 16u, &s_bar);
-        if (words & 1) dst[words - 1] = __ldg(P.cinv + words - 1);
+    if (rank == 0) {
+      if (staged) block_copy16(dst, P.cinv, (words / 2) * 16);
+      if (threadIdx.x == 0) {
+        if (staged && (words & 1)) dst[words - 1] = __ldg(P.cinv + words - 1);
+        s_cinv = staged ? dst : P.cinv;
       }
-      s_cinv = staged ? dst : P.cinv;
     }
   }
   if (use_dsm)
@@ -1880,6 +1891,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
   const ProbState& st = E.S[p];
   if (st.phase != want) {
     wait_copies(0);                             // no copy outlives the block
+    cp_async_wait();
     return;
   }
   const int pre = E.prm.pre, post = E.prm.post;
@@ -1897,6 +1909,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
   const int w0 = rank * wpb + (threadIdx.x >> 5), nw = csize * wpb;
   if (dsm_ok) {
     wait_copies(0);                             // the next phase of bar may start only now
+    cp_async_wait();                            // the constant data of this block's levels
+    __syncthreads();
     {   // right-hand side of the top level: own and ghost rows
       const LevelDev& g = gd[top];
       const long long n = (1LL << top) + 1;
@@ -1917,6 +1931,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
     for (int l = top; l > Ss; --l) dsm_down<Pol>(cv, c0, l, rank, csize, Ss, true, pre, omega);
   } else {
     wait_copies(0);
+    cp_async_wait();                            // the constant data of this block's levels
+    __syncthreads();
     // cluster part over L2, down
     for (int l = top; l > Ss; --l) {
       const bool chk = (l == P.L) && !zero_top;
