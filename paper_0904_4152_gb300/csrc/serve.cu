@@ -202,26 +202,75 @@ size_t request_bytes(int L, const hn_mg_opts& o) {
 
 void hn_server::run() {
   cudaSetDevice(device);
-  // s: the schedule's iterations and the results; s2: building admitted requests' hierarchies
-  // while an iteration of the running requests is on the device
-  cudaStream_t s = nullptr, s2 = nullptr;
+  // s: the schedule's iterations; s2: building admitted requests' hierarchies while an iteration
+  // of the running requests is on the device; s3: copying finished requests' results back while
+  // the next iteration runs
+  cudaStream_t s = nullptr, s2 = nullptr, s3 = nullptr;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking) != cudaSuccess) {
     std::lock_guard<std::mutex> lk(mu);
     worker_error = "stream creation failed";
     stop = true;
     cv_done.notify_all();
     if (s) cudaStreamDestroy(s);
+    if (s2) cudaStreamDestroy(s2);
     return;
   }
+  // Finished requests whose results are being copied back on s3: their slot is free for the
+  // schedule already, their hierarchy and budget share are released once the copy has landed.
+  struct Retiring {
+    Request* r;
+    ProbState st;
+    cudaEvent_t ev;            // recorded on s3 after the request's copy
+  };
+  std::vector<Retiring> retiring;
   std::unique_ptr<Engine> engine;
   int engine_lmax = 0;
   bool members_dirty = false;
   std::vector<int> fresh;
   std::vector<hn_mg*> running(max_active, nullptr);   // members of the schedule the engine runs
+  // release the requests whose copies have landed (all of them, waiting, with `wait`)
+  auto finish_retiring = [&](bool wait) {
+    size_t k = 0;
+    for (; k < retiring.size(); ++k) {
+      Retiring& e = retiring[k];
+      if (wait) cudaEventSynchronize(e.ev);
+      else if (cudaEventQuery(e.ev) != cudaSuccess) break;      // in order of recording
+    }
+    for (size_t i = 0; i < k; ++i) {
+      Retiring& e = retiring[i];
+      Request* r = e.r;
+      cudaEventDestroy(e.ev);
+      r->b.release();                               // the inputs were consumed at admission
+      r->coef.release();
+      const size_t hbytes = r->mg->bytes;           // kept for the next request of its size
+      void* hmem = detach_block(r->mg->mem, r->mg->mem_base);
+      hn_mg_destroy(r->mg);
+      if (hmem) cache.give(hmem, hbytes);
+      std::lock_guard<std::mutex> lk(mu);
+      r->mg = nullptr;
+      r->status = e.st.status;
+      r->stats.cycles = e.st.cycles;
+      r->stats.outer_iters = e.st.outer_iters;
+      r->stats.inner_cycles = e.st.inner_cycles;
+      r->stats.status = e.st.status;
+      r->stats.relres = e.st.relres;
+      r->t_done = now_ns();
+      r->stats.solve_ns = r->t_done - r->t_submit;
+      r->done = true;
+      in_use -= r->bytes;
+      ++completed;
+      cv_done.notify_all();
+    }
+    retiring.erase(retiring.begin(), retiring.begin() + k);
+  };
   auto fail_all = [&](const char* why) {
+    cudaStreamSynchronize(s3);
     std::lock_guard<std::mutex> lk(mu);
     worker_error = why;
+    for (Retiring& e : retiring) { e.r->status = HN_ERR_CUDA; e.r->done = true; cudaEventDestroy(e.ev); }
+    retiring.clear();
     for (Request*& r : slots)
       if (r) { r->status = HN_ERR_CUDA; r->done = true; r = nullptr; }
     for (Request* r : queue) { r->status = HN_ERR_CUDA; r->done = true; }
@@ -234,7 +283,7 @@ void hn_server::run() {
     {
       std::unique_lock<std::mutex> lk(mu);
       auto active = [&] { return std::count_if(slots.begin(), slots.end(), [](Request* r) { return r != nullptr; }); };
-      cv_work.wait(lk, [&] { return stop || !queue.empty() || active() > 0; });
+      cv_work.wait(lk, [&] { return stop || !queue.empty() || active() > 0 || !retiring.empty(); });
       if (stop && active() == 0) break;
       if (!stop) {
         while (!queue.empty()) {
@@ -265,6 +314,17 @@ void hn_server::run() {
           admitted.push_back(r);
         }
       }
+    }
+    if (admitted.empty() && std::none_of(slots.begin(), slots.end(), [](Request* r) { return r != nullptr; })) {
+      // nothing runs and nothing could be admitted: only result copies are in flight (their
+      // memory may be what the head of the queue waits for)
+      if (!retiring.empty()) {
+        finish_retiring(true);
+      } else {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_work.wait_for(lk, std::chrono::milliseconds(1));
+      }
+      continue;
     }
     // the next iteration of the running requests ...
     const bool launched = engine && std::any_of(running.begin(), running.end(), [](hn_mg* m) { return m != nullptr; });
@@ -347,41 +407,38 @@ void hn_server::run() {
       for (int q = 0; q < max_active; ++q)
         if (running[q] && st[q].phase == PH_DONE) done_now.emplace_back(q, slots[q]);
     }
+    // results back on s3 (the iteration that finished them is complete); the requests leave the
+    // schedule now and are released once their copies have landed
     bool copy_failed = false;
-    for (auto& [q, r] : done_now) {
-      const long long N = N_of(r->L);
-      if (!r->x.alloc(&host, (size_t)N)) { copy_failed = true; break; }
-      if (st[q].status == HN_OK && st[q].bnorm == 0.0) std::fill(r->x.p, r->x.p + N, 0.0);
-      else if (cudaMemcpyAsync(r->x.p, r->mg->host.x64, (size_t)N * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        copy_failed = true;
+    if (!done_now.empty()) {
+      for (auto& [q, r] : done_now) {
+        const long long N = N_of(r->L);
+        if (!r->x.alloc(&host, (size_t)N)) { copy_failed = true; break; }
+        if (st[q].status == HN_OK && st[q].bnorm == 0.0) std::fill(r->x.p, r->x.p + N, 0.0);
+        else if (cudaMemcpyAsync(r->x.p, r->mg->host.x64, (size_t)N * 8, cudaMemcpyDeviceToHost, s3) != cudaSuccess)
+          copy_failed = true;
+      }
+      if (copy_failed) {
+        fail_all("result copy failed");
+        break;
+      }
+      for (auto& [q, r] : done_now) {
+        Retiring e{r, st[q], nullptr};              // an event per request, after all the copies
+        if (cudaEventCreateWithFlags(&e.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(e.ev, s3) != cudaSuccess) {
+          if (e.ev) cudaEventDestroy(e.ev);
+          copy_failed = true;
+          break;
+        }
+        running[q] = nullptr;
+        retiring.push_back(e);
+        std::lock_guard<std::mutex> lk(mu);
+        slots[q] = nullptr;
+        members_dirty = true;
+      }
+      if (copy_failed) { fail_all("result copy failed"); break; }
     }
-    if (!done_now.empty() && cudaStreamSynchronize(s) != cudaSuccess) copy_failed = true;
-    if (copy_failed) { fail_all("result copy failed"); break; }
-    for (auto& [q, r] : done_now) {
-      r->b.release();                               // the inputs were consumed at admission
-      r->coef.release();
-      const size_t hbytes = r->mg->bytes;           // kept for the next request of its size
-      void* hmem = detach_block(r->mg->mem, r->mg->mem_base);
-      hn_mg_destroy(r->mg);
-      if (hmem) cache.give(hmem, hbytes);
-      running[q] = nullptr;
-      std::lock_guard<std::mutex> lk(mu);
-      r->mg = nullptr;
-      r->status = st[q].status;
-      r->stats.cycles = st[q].cycles;
-      r->stats.outer_iters = st[q].outer_iters;
-      r->stats.inner_cycles = st[q].inner_cycles;
-      r->stats.status = st[q].status;
-      r->stats.relres = st[q].relres;
-      r->t_done = now_ns();
-      r->stats.solve_ns = r->t_done - r->t_submit;
-      r->done = true;
-      in_use -= r->bytes;
-      slots[q] = nullptr;
-      ++completed;
-      members_dirty = true;
-      cv_done.notify_all();
-    }
+    finish_retiring(false);
     const long long t_sched0 = now_ns();
     {
       std::lock_guard<std::mutex> lk(mu);
@@ -455,6 +512,8 @@ void hn_server::run() {
   engine.reset();
   cudaStreamSynchronize(s);
   cudaStreamSynchronize(s2);
+  finish_retiring(true);
+  cudaStreamDestroy(s3);
   cache.clear();
   if (scratch) cudaFree(scratch);
   scratch = nullptr;
