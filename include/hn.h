@@ -220,7 +220,7 @@ hn_status hn_band_defect_norm_static(const hn_band* A, const double* x, const do
 hn_status hn_mg_get_inner_bands(const hn_mg* mg, int level, void* bands_out, float* scales_out);
 
 /* -------------------------------------------------------------------------------- serving
- * A server owns a worker thread and a device-memory budget.  Submitted requests wait in a FIFO
+ * A server owns a worker thread, a builder thread and a device-memory budget.  Submitted requests wait in a FIFO
  * queue; a request is admitted once a slot (max_active) and budget room for its hierarchy are
  * free.  Admitted requests are solved together: every scheduler iteration runs one V-cycle phase
  * sequence over all active requests (continuous batching); finished requests leave, free their
@@ -247,9 +247,10 @@ typedef struct {
   long long submitted, completed, active, queued;
   long long iterations;        /* scheduler iterations run */
   size_t bytes_in_use, budget;
-  /* worker time (ns) spent building the hierarchies of admitted requests (while the running
-   * requests' iteration is on the device), waiting for iterations to finish, retiring requests,
-   * and (re)building the schedule and starting requests */
+  /* time (ns) the builder thread spent building the hierarchies of admitted requests (on its own
+   * stream, while the worker iterates the running requests), and worker time spent waiting for
+   * iterations to finish, retiring requests (their results come back on a copy stream while the
+   * next iteration runs), and (re)building the schedule and starting requests */
   long long admit_ns, schedule_ns, iterate_ns, retire_ns;
 } hn_server_info;
 hn_status hn_server_query(hn_server* srv, hn_server_info* info);

@@ -169,12 +169,22 @@ struct hn_server {
   long long submitted = 0, completed = 0, iterations = 0;
   long long admit_ns = 0, schedule_ns = 0, iterate_ns = 0, retire_ns = 0;   // worker time
   std::vector<Request*> slots;
-  BlockCache cache;                  // worker only
-  void* scratch = nullptr;           // worker only: setup temporaries, grown on demand
+  // Admitted requests go to the builder thread, which assembles their operators and hierarchies
+  // on its own stream while the worker keeps iterating the running requests; built requests join
+  // the schedule at the worker's next pass.
+  std::deque<Request*> to_build;     // admitted, waiting for the builder (under mu)
+  std::vector<Request*> built;       // built (or failed), not yet in the schedule (under mu)
+  int building = 0;                  // requests the builder holds (under mu)
+  bool builder_stop = false;         // (under mu)
+  std::condition_variable cv_build;
+  std::mutex cache_mu;               // the block cache and the scratch block
+  BlockCache cache;
+  void* scratch = nullptr;           // the builder's setup temporaries, grown on demand
   size_t scratch_bytes = 0;
-  std::thread worker;
+  std::thread worker, builder;
   std::string worker_error;
   void run();
+  void build_loop();
 };
 
 namespace {
@@ -200,21 +210,111 @@ size_t request_bytes(int L, const hn_mg_opts& o) {
 
 }  // namespace
 
+void hn_server::build_loop() {
+  cudaSetDevice(device);
+  cudaStream_t sb = nullptr;
+  const bool stream_ok = cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking) == cudaSuccess;
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_build.wait(lk, [&] { return builder_stop || !to_build.empty(); });
+      if (to_build.empty()) break;
+      r = to_build.front();
+      to_build.pop_front();
+      ++building;
+    }
+    // the operator and hierarchy (explicit copies of the inputs, checked at submit; device blocks
+    // from the cache when it has one), the right-hand side and a zero iterate
+    const long long t0 = now_ns();
+    const bool has_coef = r->coef.p != nullptr;
+    const size_t bb = band_bytes(r->L, has_coef);
+    hn_mg_opts o = opts;
+    o.stream = sb;
+    const Params prm = params_from(o);
+    const size_t hb = hierarchy_bytes(r->L, o.coarse_L, prm.prec, prm.solver);
+    void* band_blk = nullptr;
+    void* hier_blk = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(cache_mu);
+      band_blk = cache.take(bb);
+      hier_blk = cache.take(hb);
+      const size_t tmp = hierarchy_tmp_bytes(r->L, o.coarse_L, prm.prec, has_coef);
+      if (tmp > scratch_bytes) {
+        if (scratch) cudaFree(scratch);
+        scratch = nullptr;
+        scratch_bytes = 0;
+        if (cudaMalloc(&scratch, tmp) == cudaSuccess) scratch_bytes = tmp;
+        else cudaGetLastError();                    // build_hierarchy allocates its own then
+      }
+    }
+    hn_status st = stream_ok ? HN_OK : HN_ERR_CUDA;
+    hn_band* A = nullptr;
+    if (st == HN_OK) st = build_band(r->L, has_coef ? r->coef.p : nullptr, r->bc, sb, band_blk, &A);
+    else if (band_blk) { std::lock_guard<std::mutex> lk(cache_mu); cache.give(band_blk, bb); }
+    std::unique_ptr<hn_mg> h;
+    if (st == HN_OK) {
+      h.reset(new hn_mg());
+      h->stream = sb;
+      st = build_hierarchy(A, o, sb, h.get(), hier_blk, scratch, scratch_bytes);
+      hier_blk = nullptr;
+    }
+    if (hier_blk) { std::lock_guard<std::mutex> lk(cache_mu); cache.give(hier_blk, hb); }
+    if (st == HN_OK) {
+      const long long N = N_of(r->L);
+      if (cudaMemcpyAsync(h->host.b64, r->b.p, (size_t)N * 8, cudaMemcpyHostToDevice, sb) != cudaSuccess ||
+          cudaMemsetAsync(h->host.x64, 0, (size_t)N * 8, sb) != cudaSuccess ||
+          cudaStreamSynchronize(sb) != cudaSuccess)
+        st = HN_ERR_CUDA;
+    }
+    if (A) {                                        // its block: free again once sb got here
+      cudaStreamSynchronize(sb);
+      void* blk = detach_block(A->mem, A->mem_base);
+      hn_band_destroy(A);
+      if (blk) { std::lock_guard<std::mutex> lk(cache_mu); cache.give(blk, bb); }
+    }
+    hn_mg* mg = nullptr;
+    if (h) {
+      h->stream = nullptr;                          // built: later users run on the worker's streams
+      h->setup_ns = now_ns() - t0;
+      mg = h.release();
+    }
+    if (st != HN_OK && mg) {
+      hn_mg_destroy(mg);
+      mg = nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    r->mg = mg;
+    if (st != HN_OK) r->status = st;
+    else r->stats.setup_ns = mg->setup_ns;
+    admit_ns += now_ns() - t0;
+    built.push_back(r);
+    --building;
+    cv_work.notify_all();
+  }
+  {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    if (scratch) cudaFree(scratch);
+    scratch = nullptr;
+    scratch_bytes = 0;
+  }
+  if (sb) cudaStreamDestroy(sb);
+}
+
 void hn_server::run() {
   cudaSetDevice(device);
-  // s: the schedule's iterations; s2: building admitted requests' hierarchies while an iteration
-  // of the running requests is on the device; s3: copying finished requests' results back while
-  // the next iteration runs
-  cudaStream_t s = nullptr, s2 = nullptr, s3 = nullptr;
+  // s: the schedule's iterations; s3: copying finished requests' results back while the next
+  // iteration runs (the builder thread has its own stream)
+  cudaStream_t s = nullptr, s3 = nullptr;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking) != cudaSuccess) {
     std::lock_guard<std::mutex> lk(mu);
     worker_error = "stream creation failed";
     stop = true;
+    builder_stop = true;
+    cv_build.notify_all();
     cv_done.notify_all();
     if (s) cudaStreamDestroy(s);
-    if (s2) cudaStreamDestroy(s2);
     return;
   }
   // Finished requests whose results are being copied back on s3: their slot is free for the
@@ -230,6 +330,7 @@ void hn_server::run() {
   bool members_dirty = false;
   std::vector<int> fresh;
   std::vector<hn_mg*> running(max_active, nullptr);   // members of the schedule the engine runs
+  auto any_running = [&] { return std::any_of(running.begin(), running.end(), [](hn_mg* m) { return m != nullptr; }); };
   // release the requests whose copies have landed (all of them, waiting, with `wait`)
   auto finish_retiring = [&](bool wait) {
     size_t k = 0;
@@ -247,7 +348,7 @@ void hn_server::run() {
       const size_t hbytes = r->mg->bytes;           // kept for the next request of its size
       void* hmem = detach_block(r->mg->mem, r->mg->mem_base);
       hn_mg_destroy(r->mg);
-      if (hmem) cache.give(hmem, hbytes);
+      if (hmem) { std::lock_guard<std::mutex> lk(cache_mu); cache.give(hmem, hbytes); }
       std::lock_guard<std::mutex> lk(mu);
       r->mg = nullptr;
       r->status = e.st.status;
@@ -267,42 +368,61 @@ void hn_server::run() {
   };
   auto fail_all = [&](const char* why) {
     cudaStreamSynchronize(s3);
-    std::lock_guard<std::mutex> lk(mu);
+    std::unique_lock<std::mutex> lk(mu);
+    // the builder first finishes the request it holds (a failed request may be forgotten by
+    // hn_mg_poll at once)
+    builder_stop = true;
+    to_build.clear();
+    cv_build.notify_all();
+    cv_work.wait(lk, [&] { return building == 0; });
     worker_error = why;
     for (Retiring& e : retiring) { e.r->status = HN_ERR_CUDA; e.r->done = true; cudaEventDestroy(e.ev); }
     retiring.clear();
+    for (Request* r : built) {
+      if (r->mg) hn_mg_destroy(r->mg);
+      r->mg = nullptr;
+    }
+    built.clear();
     for (Request*& r : slots)
       if (r) { r->status = HN_ERR_CUDA; r->done = true; r = nullptr; }
     for (Request* r : queue) { r->status = HN_ERR_CUDA; r->done = true; }
     queue.clear();
+    to_build.clear();
     stop = true;
     cv_done.notify_all();
   };
   for (;;) {
-    std::vector<Request*> admitted;
+    bool admitted_any = false;
     {
       std::unique_lock<std::mutex> lk(mu);
-      auto active = [&] { return std::count_if(slots.begin(), slots.end(), [](Request* r) { return r != nullptr; }); };
-      cv_work.wait(lk, [&] { return stop || !queue.empty() || active() > 0 || !retiring.empty(); });
-      if (stop && active() == 0) break;
+      auto occupied = [&] { return std::any_of(slots.begin(), slots.end(), [](Request* r) { return r != nullptr; }); };
+      // wake for: the end, an admission that can happen now (a free slot and budget room for the
+      // head of the queue), built requests, copies in flight, or running requests
+      auto admissible = [&] {
+        return !stop && !queue.empty() && std::find(slots.begin(), slots.end(), nullptr) != slots.end() &&
+               in_use + queue.front()->bytes <= budget;
+      };
+      cv_work.wait(lk, [&] {
+        return (stop && !occupied() && retiring.empty()) || admissible() || !built.empty() ||
+               !retiring.empty() || any_running();
+      });
+      if (stop && !occupied() && retiring.empty()) break;
       if (!stop) {
         while (!queue.empty()) {
           auto free_slot = std::find(slots.begin(), slots.end(), nullptr);
           if (free_slot == slots.end()) break;
           Request* r = queue.front();
-          if (in_use + r->bytes + cache.bytes + scratch_bytes > budget) {
-            // cached blocks count against the budget: give back only as many as the head of the
-            // queue needs (largest first, the blocks it will reuse last), then the scratch block;
-            // freeing every cached block would make the next requests of each size allocate anew
-            const Params hp = params_from(opts);
-            const size_t hb = hierarchy_bytes(r->L, opts.coarse_L, hp.prec, hp.solver);
-            const size_t bb = band_bytes(r->L, r->coef.p != nullptr);
-            const size_t need = in_use + r->bytes + scratch_bytes;
-            cache.release_to(need < budget ? budget - need : 0, hb, bb);
+          {
+            std::lock_guard<std::mutex> ck(cache_mu);
             if (in_use + r->bytes + cache.bytes + scratch_bytes > budget) {
-              if (scratch) cudaFree(scratch);
-              scratch = nullptr;
-              scratch_bytes = 0;
+              // cached blocks count against the budget: give back only as many as the head of
+              // the queue needs (largest first, the blocks it will reuse last); freeing every
+              // cached block would make the next requests of each size allocate anew
+              const Params hp = params_from(opts);
+              const size_t hb = hierarchy_bytes(r->L, opts.coarse_L, hp.prec, hp.solver);
+              const size_t bb = band_bytes(r->L, r->coef.p != nullptr);
+              const size_t need = in_use + r->bytes + scratch_bytes;
+              cache.release_to(need < budget ? budget - need : 0, hb, bb);
             }
           }
           if (in_use + r->bytes > budget) break;    // FIFO: the head waits for memory
@@ -311,83 +431,16 @@ void hn_server::run() {
           r->slot = (int)(free_slot - slots.begin());
           *free_slot = r;
           r->t_admit = now_ns();
-          admitted.push_back(r);
+          to_build.push_back(r);
+          admitted_any = true;
         }
+        if (admitted_any) cv_build.notify_one();
       }
     }
-    if (admitted.empty() && std::none_of(slots.begin(), slots.end(), [](Request* r) { return r != nullptr; })) {
-      // nothing runs and nothing could be admitted: only result copies are in flight (their
-      // memory may be what the head of the queue waits for)
-      if (!retiring.empty()) {
-        finish_retiring(true);
-      } else {
-        std::unique_lock<std::mutex> lk(mu);
-        cv_work.wait_for(lk, std::chrono::milliseconds(1));
-      }
-      continue;
-    }
-    // the next iteration of the running requests ...
-    const bool launched = engine && std::any_of(running.begin(), running.end(), [](hn_mg* m) { return m != nullptr; });
+    // the next iteration of the running requests (the builder assembles admitted requests
+    // meanwhile)
+    const bool launched = engine && any_running();
     if (launched && engine->launch_iteration() != HN_OK) { fail_all(hn_last_error()); break; }
-    // ... while the hierarchies of the admitted requests are built (explicit copies of their
-    // inputs, checked at submit; device blocks from the cache when it has one)
-    const long long t_admit0 = now_ns();
-    bool setup_failed = false;
-    for (Request* r : admitted) {
-      const long long t0 = now_ns();
-      const bool has_coef = r->coef.p != nullptr;
-      const size_t bb = band_bytes(r->L, has_coef);
-      hn_band* A = nullptr;
-      hn_status st = build_band(r->L, has_coef ? r->coef.p : nullptr, r->bc, s2, cache.take(bb), &A);
-      hn_mg* mg = nullptr;
-      if (st == HN_OK) {
-        hn_mg_opts o = opts;
-        o.stream = s2;
-        const Params prm = params_from(o);
-        const size_t tmp = hierarchy_tmp_bytes(r->L, o.coarse_L, prm.prec, has_coef);
-        if (tmp > scratch_bytes) {
-          if (scratch) cudaFree(scratch);
-          scratch = nullptr;
-          scratch_bytes = 0;
-          if (cudaMalloc(&scratch, tmp) == cudaSuccess) scratch_bytes = tmp;
-          else cudaGetLastError();                  // build_hierarchy allocates its own then
-        }
-        std::unique_ptr<hn_mg> h(new hn_mg());
-        h->stream = s2;
-        st = build_hierarchy(A, o, s2, h.get(), cache.take(hierarchy_bytes(r->L, o.coarse_L, prm.prec, prm.solver)),
-                             scratch, scratch_bytes);
-        h->setup_ns = now_ns() - t0;
-        mg = h.release();
-      }
-      if (A) {                                      // (later users of the block run on stream s2)
-        if (void* blk = detach_block(A->mem, A->mem_base)) cache.give(blk, bb);
-        hn_band_destroy(A);
-      }
-      if (st == HN_OK) {
-        const long long N = N_of(r->L);
-        if (cudaMemcpyAsync(mg->host.b64, r->b.p, (size_t)N * 8, cudaMemcpyHostToDevice, s2) != cudaSuccess ||
-            cudaMemsetAsync(mg->host.x64, 0, (size_t)N * 8, s2) != cudaSuccess)
-          st = HN_ERR_CUDA;
-      }
-      std::lock_guard<std::mutex> lk(mu);
-      if (st != HN_OK) {
-        hn_mg_destroy(mg);
-        r->status = st;
-        r->done = true;
-        r->t_done = now_ns();
-        in_use -= r->bytes;
-        slots[r->slot] = nullptr;
-        cv_done.notify_all();
-        continue;
-      }
-      r->mg = mg;
-      r->stats.setup_ns = mg->setup_ns;
-      fresh.push_back(r->slot);
-      members_dirty = true;
-    }
-    if (!admitted.empty() && cudaStreamSynchronize(s2) != cudaSuccess) setup_failed = true;
-    if (setup_failed) { fail_all("hierarchy setup failed"); break; }
-    // the iteration's result; retire the requests it finished (their results in one batch of copies)
     const long long t_wait0 = now_ns();
     std::vector<ProbState> st;
     if (launched && (engine->finish_iteration(nullptr) != HN_OK || engine->read_states(st) != HN_OK)) {
@@ -398,17 +451,16 @@ void hn_server::run() {
     {
       std::lock_guard<std::mutex> lk(mu);
       if (launched) ++iterations;
-      admit_ns += t_wait0 - t_admit0;
       iterate_ns += t_ret0 - t_wait0;
     }
+    // the requests the iteration finished: results back on s3 (the iteration is complete); they
+    // leave the schedule now and are released once their copies have landed
     std::vector<std::pair<int, Request*>> done_now;
     if (launched) {
       std::lock_guard<std::mutex> lk(mu);
       for (int q = 0; q < max_active; ++q)
         if (running[q] && st[q].phase == PH_DONE) done_now.emplace_back(q, slots[q]);
     }
-    // results back on s3 (the iteration that finished them is complete); the requests leave the
-    // schedule now and are released once their copies have landed
     bool copy_failed = false;
     if (!done_now.empty()) {
       for (auto& [q, r] : done_now) {
@@ -418,10 +470,7 @@ void hn_server::run() {
         else if (cudaMemcpyAsync(r->x.p, r->mg->host.x64, (size_t)N * 8, cudaMemcpyDeviceToHost, s3) != cudaSuccess)
           copy_failed = true;
       }
-      if (copy_failed) {
-        fail_all("result copy failed");
-        break;
-      }
+      if (copy_failed) { fail_all("result copy failed"); break; }
       for (auto& [q, r] : done_now) {
         Retiring e{r, st[q], nullptr};              // an event per request, after all the copies
         if (cudaEventCreateWithFlags(&e.ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -438,11 +487,30 @@ void hn_server::run() {
       }
       if (copy_failed) { fail_all("result copy failed"); break; }
     }
-    finish_retiring(false);
+    // with nothing iterating, wait for the copies in flight (their memory may be what the head
+    // of the queue waits for)
+    finish_retiring(!launched && !retiring.empty());
     const long long t_sched0 = now_ns();
     {
       std::lock_guard<std::mutex> lk(mu);
       retire_ns += t_sched0 - t_ret0;
+    }
+    // built requests join the schedule (or leave, if their setup failed)
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (Request* r : built) {
+        if (!r->mg) {
+          r->done = true;
+          r->t_done = now_ns();
+          in_use -= r->bytes;
+          slots[r->slot] = nullptr;
+          cv_done.notify_all();
+          continue;
+        }
+        fresh.push_back(r->slot);
+        members_dirty = true;
+      }
+      built.clear();
     }
     // the schedule of the next iteration: (re)build the engine for the current highest level,
     // refresh its work lists, start the new requests
@@ -451,7 +519,10 @@ void hn_server::run() {
     {
       std::lock_guard<std::mutex> lk(mu);
       for (int q = 0; q < max_active; ++q)
-        if (slots[q] && slots[q]->mg) { members[q] = slots[q]->mg; lmax = std::max(lmax, slots[q]->L); }
+        if (slots[q] && slots[q]->mg && (running[q] || std::find(fresh.begin(), fresh.end(), q) != fresh.end())) {
+          members[q] = slots[q]->mg;
+          lmax = std::max(lmax, slots[q]->L);
+        }
     }
     if (lmax == 0) {
       running = members;
@@ -460,12 +531,9 @@ void hn_server::run() {
     if (!engine || lmax > engine_lmax) {
       // a larger level than the schedule covers: wait until the running requests drain
       bool running_old = false;
-      if (engine) {
-        std::lock_guard<std::mutex> lk(mu);
+      if (engine)
         for (int q = 0; q < max_active; ++q)
-          if (slots[q] && slots[q]->mg && std::find(fresh.begin(), fresh.end(), q) == fresh.end())
-            running_old = true;
-      }
+          if (members[q] && std::find(fresh.begin(), fresh.end(), q) == fresh.end()) running_old = true;
       if (!engine || !running_old) {
         const int Lcap = std::max(lmax, 8);
         std::vector<long long> caps(kMaxLevel + 1, 0);
@@ -511,14 +579,18 @@ void hn_server::run() {
   }
   engine.reset();
   cudaStreamSynchronize(s);
-  cudaStreamSynchronize(s2);
   finish_retiring(true);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    builder_stop = true;
+    cv_build.notify_all();
+  }
+  if (builder.joinable()) builder.join();
+  {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    cache.clear();
+  }
   cudaStreamDestroy(s3);
-  cache.clear();
-  if (scratch) cudaFree(scratch);
-  scratch = nullptr;
-  scratch_bytes = 0;
-  cudaStreamDestroy(s2);
   cudaStreamDestroy(s);
 }
 
@@ -534,6 +606,7 @@ hn_status hn_server_create(size_t budget_bytes, int max_active, hn_server** out)
   srv->slots.assign(max_active, nullptr);
   HN_CUDA(cudaGetDevice(&srv->device));
   hn_server* raw = srv.get();
+  srv->builder = std::thread([raw] { raw->build_loop(); });
   srv->worker = std::thread([raw] { raw->run(); });
   *out = srv.release();
   return HN_OK;
@@ -637,6 +710,12 @@ void hn_server_destroy(hn_server* srv) {
     srv->cv_work.notify_all();
   }
   if (srv->worker.joinable()) srv->worker.join();
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->builder_stop = true;
+    srv->cv_build.notify_all();
+  }
+  if (srv->builder.joinable()) srv->builder.join();
   delete srv;
 }
 
