@@ -932,7 +932,7 @@ def run_batch(args, rank, world, local, pg):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": "batch-256-L5to9-lognormal", "problems": count, "dof": dofs,
                        "levels": {str(L): levels.count(L) for L in sorted(set(levels))},
-                       "tuning": {"tail_level": best[0], "cluster": best[1]},
+                       "tuning": {"tail_level": best[0], "cluster": best[1], "mid": best[3]},
                        "l2_between_steps": "flushed (512 MiB write)"},
             "per_problem_loop_dof_per_s": loop_value, "batched_over_loop": value / loop_value,
             "inner_cycles": {"min": min(cyc), "max": max(cyc)},
