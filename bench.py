@@ -1155,6 +1155,8 @@ def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                            "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
                            "argmax": int(ok[int(lat.argmax())]), "p99_by_tenth": tenth},
+            "p99_ms_by_level": {str(L): float(np.percentile([res[i][1] for i in ok if int(levels[i]) == L], 99))
+                                for L in sorted({int(levels[i]) for i in ok})},
             "submit_late_ms_p99": float(np.percentile(late, 99) * 1e3),
             "inputs": {"distinct": unique, "host_generation_s": gen_s},
             "worker_s": {k: info[k + "_ns"] * 1e-9 for k in ("admit", "schedule", "iterate", "retire")},
@@ -1182,7 +1184,8 @@ def run_serve(args, rank, world, local, pg):
                        "arrival_rate_per_s": r["arrival_rate_per_s"], "capacity_per_s": r["capacity_per_s"],
                        "budget_gb": args.budget_gb, "slots": args.slots},
             "latency_ms": r["latency_ms"], "dof_per_s": r["dof_per_s"],
-            "submit_late_ms_p99": r["submit_late_ms_p99"], "worker_s": r["worker_s"],
+            "submit_late_ms_p99": r["submit_late_ms_p99"], "p99_ms_by_level": r["p99_ms_by_level"],
+            "worker_s": r["worker_s"],
             "relres_max": r["relres_max"]}), flush=True)
 
 
