@@ -539,6 +539,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   take(sizeof(int) * plan_ints());
   take(sizeof(TileList) * (kMaxLevel + 1));
   take(sizeof(unsigned long long) * 3);
+  take(sizeof(unsigned));
   bytes += 256;
   memBytes_ = bytes;
   HN_TRY(guarded_alloc(bytes, &memBase_, &mem_));
@@ -565,6 +566,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   dPlan_ = b.take<int>(plan_ints());
   dLists_ = b.take<TileList>(kMaxLevel + 1);
   dBar_ = b.take<unsigned long long>(3);
+  unsigned* ticket = b.take<unsigned>(1);
   HN_CUDA(cudaHostAlloc(&hStage_, stage_bytes(), cudaHostAllocDefault));
   HN_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&hLists_), sizeof(TileList) * (kMaxLevel + 1),
                         cudaHostAllocDefault));
@@ -590,6 +592,7 @@ hn_status Engine::create(const Params& prm, int cap, int Lmax, const std::vector
   E_.gsum = gsum;
   E_.gticket = gticket;
   E_.gbar = dBar_;
+  E_.ticket = ticket;
   E_.iter_limit = (unsigned)(prm.max_cycles + prm.max_outer + 8);
   for (int l = 0; l <= kMaxLevel; ++l) {
     lists_[l] = TileList{dItems_[l], dCounts_ + l, dChunks_[l], dChunkCounts_ + l, (int)chunkCap_[l]};
@@ -714,6 +717,7 @@ hn_status Engine::start(const std::vector<int>& slots, const std::vector<int>& h
   HN_CUDA(cudaMemsetAsync(E_.iter, 0, sizeof(unsigned), s_));
   HN_CUDA(cudaMemsetAsync(dErr_, 0, sizeof(int) * 4, s_));
   HN_CUDA(cudaMemsetAsync(dBar_, 0, sizeof(unsigned long long) * 3, s_));
+  HN_CUDA(cudaMemsetAsync(E_.ticket, 0, sizeof(unsigned), s_));
   // mirrors of the IF values as the closed-world graph sets them at its launch
   static const unsigned taken0[4] = {0u, 1u, 0u, 0u};
   HN_CUDA(cudaMemcpyAsync(dTaken_, taken0, sizeof taken0, cudaMemcpyHostToDevice, s_));
@@ -884,10 +888,13 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
   for (int l = Lmax_; l > std::max(T, M); --l) {
     // a finest level: lagged check (the PCG preconditioner's cycle has none)
     const bool top = prm_.solver != SOLVER_PCG && (topMaskAll_ || ((topMask_ >> l) & 1u));
+    // an engine of one problem takes the check inside the first smoothing step when the norm is
+    // one group of partials (the register-path kernel; saves the control launch)
+    const bool fuse = top && cap_ == 1 && !tune_.staged && pitch_of(l) / kTile <= kSumGroup;
     if (pre >= 2) {
-      HN_LAUNCH(KC_JACOBI_FIRST, l, launch_pre12(E_, lists_[l], l, want, grid_[l], s));
+      HN_LAUNCH(KC_JACOBI_FIRST, l, launch_pre12(E_, lists_[l], l, want, grid_[l], s, fuse ? 1 : 0));
       if (top) {
-        HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
+        if (!fuse) HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
         HN_TRY(after_check());
       }
       if (!pre_fuses(prm_.prec) || top)
@@ -895,9 +902,9 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
       for (int sw = 3; sw <= pre; ++sw)
         HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (sw - 1) & 1, 0, grid_[l], s));
     } else {
-      HN_LAUNCH(KC_JACOBI_FIRST, l, launch_jacobi(E_, lists_[l], l, want, 0, 1, grid_[l], s));
+      HN_LAUNCH(KC_JACOBI_FIRST, l, launch_jacobi(E_, lists_[l], l, want, 0, 1, grid_[l], s, fuse ? 1 : 0));
       if (top) {
-        HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
+        if (!fuse) HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
         HN_TRY(after_check());
       }
     }

@@ -203,14 +203,17 @@ struct EngineDev {
                                // problem's norm partial sum)
   double* gsum;                // [nprob * ctl_groups] group sums of the control kernel
   unsigned* gticket;           // [nprob] blocks of a problem's control launch that finished
+  unsigned* ticket;            // blocks of a first smoothing step with a fused check that finished
   unsigned long long* gbar;    // [3] grid barriers of the persistent kernels: arrivals of the
                                // down kernel, of the up kernel, barrier actions completed
 };
 
 // Launch wrappers for one step of the schedule; grid = CTAs of 256 threads.  level < 0 means
 // "each problem's own finest level" (used with the fine work list).
+// fuse_check (an engine of one problem whose norm is one group of partials, the first step of its
+// finest level): the step also takes the lagged check, in place of a control launch
 cudaError_t launch_jacobi(const EngineDev& E, TileList tl, int level, int want, int in_sel,
-                          int first, int grid, cudaStream_t s);
+                          int first, int grid, cudaStream_t s, int fuse_check = 0);
 cudaError_t launch_defect(const EngineDev& E, TileList tl, int level, int want, int in_sel,
                           int grid, cudaStream_t s);
 cudaError_t launch_spmv(const EngineDev& E, TileList tl, int level, int want, int in_sel, int grid,
@@ -220,7 +223,7 @@ cudaError_t launch_check(const EngineDev& E, TileList fine, int want, int x_sel,
 // first two smoothing steps: fused from a zero iterate (PRE12 alone), else step 1 (PRE12) and
 // step 2 (PRE2B); pre_fuses(prec) tells whether the zero-iterate fusion exists for a precision
 cudaError_t launch_pre12(const EngineDev& E, TileList tl, int level, int want, int grid,
-                         cudaStream_t s);
+                         cudaStream_t s, int fuse_check = 0);
 cudaError_t launch_pre2b(const EngineDev& E, TileList tl, int level, int want, int grid,
                          cudaStream_t s);
 bool pre_fuses(int prec);

@@ -999,6 +999,32 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // (40 warps) of FP32 / FP16 loads in flight, enough to saturate HBM (the FP16 Jacobi step spills
 // a few bytes at 5 blocks and is still faster than at 4: 89.8 vs 96.3 us at L = 12); the fused
 // pre-smoothing (4 blocks) and check modes run once per cycle and get more registers per thread.
+// The lagged check of an engine of one problem taken inside its first smoothing step (in place of
+// a separate control launch, for problems whose norm is one group of partials): the last block to
+// finish sums the tile partials in the fixed order and updates the state, and the cycle's IF value
+// is set as the control kernel sets it (the problem is still in the cycle).  A uniform early
+// return of every block (problem not in the phase) leaves the ticket at zero.
+__device__ void solo_fused_check(const EngineDev& E, int level, bool checked, int want) {
+  __shared__ double sh[32];
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();                              // this block's partials before its ticket
+    s_last = atomicAdd(E.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  ProbState& st = E.S[0];
+  double sum = 0.0;
+  if (checked) sum = problem_norm_sum(E.partial, fine_tiles(level), sh);
+  if (threadIdx.x == 0) {
+    if (checked) pre_check(st, E.prm, sqrt(sum));
+    if (st.phase == want && (st.phase == PH_INNER || st.phase == PH_CYCLE)) cond_set(E.prm.cond, 0, 1u);
+    *E.ticket = 0u;                                 // ready for the next launch
+  }
+}
+
 template <class Pol, int MODE> constexpr int band_min_blocks() {
   if (MODE == M_CHECK) return Pol::prec == P64 ? 2 : 3;
   if (MODE == M_PRE12) return Pol::prec == P64 ? 2 : 4;
@@ -1038,8 +1064,10 @@ __global__ void __launch_bounds__(256, band_min_blocks<Pol, MODE>()) k_band(Engi
       if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST)
         if (level == tl.solo_L && !zg) slot = E.partial + t;
       band_tile<Pol, MODE, LD_NC>(tl.solo_d, 1LL << level, zg, (long long)t * kTile + lane * kLaneNodes,
-                                  lane, in_sel, omega, slot);
+                                  lane, in_sel & 1, omega, slot);
     }
+    if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST)
+      if (in_sel & 2) solo_fused_check(E, level, level == tl.solo_L && !zg, want);
     return;
   }
   if (solo_idle(E, want)) return;
@@ -1063,7 +1091,7 @@ __global__ void __launch_bounds__(256, band_min_blocks<Pol, MODE>()) k_band(Engi
     if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST)
       if (lv == P.L && !zg) slot = E.partial + E.fine_off[p] + it.y;
     band_tile<Pol, MODE, LD_NC>(P.lev[lv], 1LL << lv, zg, (long long)it.y * kTile + lane * kLaneNodes,
-                                lane, in_sel, omega, slot);
+                                lane, in_sel & 1, omega, slot);
   }
 }
 
@@ -2937,12 +2965,13 @@ cudaError_t launch_band(int mode, const EngineDev& E, TileList tl, int level, in
 }  // namespace
 
 cudaError_t launch_jacobi(const EngineDev& E, TileList tl, int level, int want, int in_sel,
-                          int first, int grid, cudaStream_t s) {
-  return launch_band(first ? M_JACOBI_FIRST : M_JACOBI, E, tl, level, want, in_sel, grid, s);
+                          int first, int grid, cudaStream_t s, int fuse_check) {
+  return launch_band(first ? M_JACOBI_FIRST : M_JACOBI, E, tl, level, want,
+                     in_sel | (first && fuse_check ? 2 : 0), grid, s);
 }
 cudaError_t launch_pre12(const EngineDev& E, TileList tl, int level, int want, int grid,
-                         cudaStream_t s) {
-  return launch_band(M_PRE12, E, tl, level, want, 0, grid, s);
+                         cudaStream_t s, int fuse_check) {
+  return launch_band(M_PRE12, E, tl, level, want, fuse_check ? 2 : 0, grid, s);
 }
 cudaError_t launch_pre2b(const EngineDev& E, TileList tl, int level, int want, int grid,
                          cudaStream_t s) {
