@@ -169,19 +169,19 @@ struct hn_server {
   long long submitted = 0, completed = 0, iterations = 0;
   long long admit_ns = 0, schedule_ns = 0, iterate_ns = 0, retire_ns = 0;   // worker time
   std::vector<Request*> slots;
-  // Admitted requests go to the builder thread, which assembles their operators and hierarchies
-  // on its own stream while the worker keeps iterating the running requests; built requests join
-  // the schedule at the worker's next pass.
+  // Admitted requests go to the builder threads, which assemble their operators and hierarchies
+  // on their own streams while the worker keeps iterating the running requests; built requests
+  // join the schedule at the worker's next pass.
   std::deque<Request*> to_build;     // admitted, waiting for the builder (under mu)
   std::vector<Request*> built;       // built (or failed), not yet in the schedule (under mu)
-  int building = 0;                  // requests the builder holds (under mu)
+  int building = 0;                  // requests the builders hold (under mu)
   bool builder_stop = false;         // (under mu)
   std::condition_variable cv_build;
-  std::mutex cache_mu;               // the block cache and the scratch block
+  std::mutex cache_mu;               // the block cache and the builders' scratch bytes
   BlockCache cache;
-  void* scratch = nullptr;           // the builder's setup temporaries, grown on demand
-  size_t scratch_bytes = 0;
-  std::thread worker, builder;
+  size_t scratch_bytes = 0;          // the builders' setup temporaries, together
+  static constexpr int kBuilders = 2;  // a small request need not wait for a large one's setup
+  std::thread worker, builders[kBuilders];
   std::string worker_error;
   void run();
   void build_loop();
@@ -212,6 +212,8 @@ size_t request_bytes(int L, const hn_mg_opts& o) {
 
 void hn_server::build_loop() {
   cudaSetDevice(device);
+  void* scratch = nullptr;           // this builder's setup temporaries, grown on demand
+  size_t my_scratch = 0;
   cudaStream_t sb = nullptr;
   const bool stream_ok = cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking) == cudaSuccess;
   for (;;) {
@@ -240,12 +242,14 @@ void hn_server::build_loop() {
       band_blk = cache.take(bb);
       hier_blk = cache.take(hb);
       const size_t tmp = hierarchy_tmp_bytes(r->L, o.coarse_L, prm.prec, has_coef);
-      if (tmp > scratch_bytes) {
+      if (tmp > my_scratch) {
         if (scratch) cudaFree(scratch);
         scratch = nullptr;
-        scratch_bytes = 0;
-        if (cudaMalloc(&scratch, tmp) == cudaSuccess) scratch_bytes = tmp;
+        scratch_bytes -= my_scratch;
+        my_scratch = 0;
+        if (cudaMalloc(&scratch, tmp) == cudaSuccess) my_scratch = tmp;
         else cudaGetLastError();                    // build_hierarchy allocates its own then
+        scratch_bytes += my_scratch;
       }
     }
     hn_status st = stream_ok ? HN_OK : HN_ERR_CUDA;
@@ -256,7 +260,7 @@ void hn_server::build_loop() {
     if (st == HN_OK) {
       h.reset(new hn_mg());
       h->stream = sb;
-      st = build_hierarchy(A, o, sb, h.get(), hier_blk, scratch, scratch_bytes);
+      st = build_hierarchy(A, o, sb, h.get(), hier_blk, scratch, my_scratch);
       hier_blk = nullptr;
     }
     if (hier_blk) { std::lock_guard<std::mutex> lk(cache_mu); cache.give(hier_blk, hb); }
@@ -295,8 +299,7 @@ void hn_server::build_loop() {
   {
     std::lock_guard<std::mutex> lk(cache_mu);
     if (scratch) cudaFree(scratch);
-    scratch = nullptr;
-    scratch_bytes = 0;
+    scratch_bytes -= my_scratch;
   }
   if (sb) cudaStreamDestroy(sb);
 }
@@ -434,7 +437,7 @@ void hn_server::run() {
           to_build.push_back(r);
           admitted_any = true;
         }
-        if (admitted_any) cv_build.notify_one();
+        if (admitted_any) cv_build.notify_all();
       }
     }
     // the next iteration of the running requests (the builder assembles admitted requests
@@ -585,7 +588,8 @@ void hn_server::run() {
     builder_stop = true;
     cv_build.notify_all();
   }
-  if (builder.joinable()) builder.join();
+  for (std::thread& t : builders)
+    if (t.joinable()) t.join();
   {
     std::lock_guard<std::mutex> lk(cache_mu);
     cache.clear();
@@ -606,7 +610,7 @@ hn_status hn_server_create(size_t budget_bytes, int max_active, hn_server** out)
   srv->slots.assign(max_active, nullptr);
   HN_CUDA(cudaGetDevice(&srv->device));
   hn_server* raw = srv.get();
-  srv->builder = std::thread([raw] { raw->build_loop(); });
+  for (std::thread& t : srv->builders) t = std::thread([raw] { raw->build_loop(); });
   srv->worker = std::thread([raw] { raw->run(); });
   *out = srv.release();
   return HN_OK;
@@ -715,7 +719,8 @@ void hn_server_destroy(hn_server* srv) {
     srv->builder_stop = true;
     srv->cv_build.notify_all();
   }
-  if (srv->builder.joinable()) srv->builder.join();
+  for (std::thread& t : srv->builders)
+    if (t.joinable()) t.join();
   delete srv;
 }
 
