@@ -4,7 +4,7 @@
  * of one thread-block cluster (`cluster` blocks of 512 threads) per problem, levels
  * tail_level+1..mid in two persistent cooperative launches per cycle (one down, one up; their
  * steps separated by grid-wide barriers), and levels above mid as one launch per step over the
- * device work list.  Inside that launch the
+ * device work list, or (sweep) as one launch per level and direction over 2-D tiles.  Inside that launch the
  * smallest levels live in the shared memory of the cluster's first block; the levels between
  * them and tail_level either live in the distributed shared memory of the whole cluster (`dsm`,
  * when they fit) or are read through L2.  The best split depends on the levels and the batch;
@@ -37,17 +37,26 @@ typedef struct {
                        <= tail_level: none); not combined with staged or fuse_up, which are forms
                        of the per-step launches (default 0: on this part a grid barrier plus the
                        memory latency of a step costs as much as a kernel boundary) */
+  int sweep;        /* 1: a hierarchy solved alone with V(2,2) cycles runs the down part of each
+                       level above tail_level (both pre-smoothing steps, the defect and the
+                       restriction; on the finest level the steps after the first) and the up part
+                       of each level between tail_level and the finest (the prolongation and both
+                       post-smoothing steps) as one launch each, over 2-D tiles whose blocks
+                       recompute the halos they need instead of waiting for one another; 0: one
+                       launch per step.  Not combined with staged or mid; without effect in
+                       batches and in the server */
 } hn_tuning;
 
 /* Set / read the launch shape used by mg's later solves.  HN_ERR_ARG on values out of range. */
 hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t);
 hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t);
 
-/* Time `reps` solves of b (host vector, N doubles) for every candidate shape (persistent kernels
- * off and on (mid 0 and 10), tail_level from coarse_L to min(L, 9), cluster 1..16) and keep the
- * fastest; the candidate timings are returned in `times_ms` (may be NULL, capacity `cap` entries,
- * row-major 2 mid settings x tail_level x 5 cluster sizes) and the chosen shape in *best.  The
- * solution is unchanged by the shape. */
+/* Time `reps` solves of b (host vector, N doubles) for every candidate shape (three forms of the
+ * levels above the tail: one launch per step (mid 0, sweep 0), persistent kernels (mid 10), fused
+ * sweeps (sweep 1); tail_level from coarse_L to min(L, 9); cluster 1..16) and keep the fastest; the
+ * candidate timings are returned in `times_ms` (may be NULL, capacity `cap` entries, row-major
+ * 3 forms x tail_level x 5 cluster sizes) and the chosen shape in *best.  The solution is unchanged
+ * by the shape. */
 hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, double* times_ms,
                          int cap);
 
@@ -63,8 +72,8 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
  * names a file, hn_mg_autotune stores its result there under the key (GPU name, level, precision,
  * solver, coarse solver, coarse level), and hn_mg_setup applies the stored shape of its key to the
  * new hierarchy (as hn_mg_set_tuning would).  The file is text, one entry per line:
- *     <gpu name>|<L>|<prec>|<solver>|<coarse solver>|<coarse L> <tail_level> <cluster> <pdl> <staged> <dsm> <fuse_up> <mid>
- * A store replaces the entry of its key (the file is rewritten through a temporary file and a
+ *     <gpu name>|<L>|<prec>|<solver>|<coarse solver>|<coarse L> <tail_level> <cluster> <pdl> <staged> <dsm> <fuse_up> <mid> <sweep>
+ * (an entry without the last field has sweep 0).  A store replaces the entry of its key (the file is rewritten through a temporary file and a
  * rename); lines that do not parse, or hold values out of range, are ignored by lookups.
  *
  * The two calls below are the file operations themselves (host only, no device call):

@@ -101,7 +101,8 @@ Tuning batch_tuning(const std::vector<hn_mg*>& list) {
     same = same && mg->tuned && mg->tuning.tail_level == list[0]->tuning.tail_level &&
            mg->tuning.cluster == list[0]->tuning.cluster && mg->tuning.pdl == list[0]->tuning.pdl &&
            mg->tuning.staged == list[0]->tuning.staged && mg->tuning.dsm == list[0]->tuning.dsm &&
-           mg->tuning.fuse_up == list[0]->tuning.fuse_up && mg->tuning.mid == list[0]->tuning.mid;
+           mg->tuning.fuse_up == list[0]->tuning.fuse_up && mg->tuning.mid == list[0]->tuning.mid &&
+           mg->tuning.sweep == list[0]->tuning.sweep;
   if (same) return list[0]->tuning;
   Tuning t;
   const int n = (int)list.size();
@@ -253,6 +254,7 @@ hn_status hn_mg_setup(const hn_band* A, const hn_mg_opts* opts, hn_mg** out) {
       tu.dsm = t.dsm;
       tu.fuse_up = t.fuse_up;
       tu.mid = t.mid;
+      tu.sweep = t.sweep;
       mg->tuning = tu;
       mg->tuned = true;
     }
@@ -350,7 +352,7 @@ hn_status hn_mg_solve_batch(hn_mg* const* mgs, int count, const double* const* b
     const Tuning t = batch_tuning(list);
     const Tuning& c = e.tuning();
     if (t.tail_level != c.tail_level || t.cluster != c.cluster || t.pdl != c.pdl || t.staged != c.staged ||
-        t.dsm != c.dsm || t.fuse_up != c.fuse_up || t.mid != c.mid)
+        t.dsm != c.dsm || t.fuse_up != c.fuse_up || t.mid != c.mid || t.sweep != c.sweep)
       e.set_tuning(t);
   }
   cudaStream_t s = e.stream();
@@ -476,6 +478,7 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
   if (t->dsm != 0 && t->dsm != 1) return set_error(HN_ERR_ARG, "dsm must be 0 or 1");
   if (t->fuse_up != 0 && t->fuse_up != 1) return set_error(HN_ERR_ARG, "fuse_up must be 0 or 1");
   if (t->mid < 0 || t->mid > HN_MAX_LEVEL) return set_error(HN_ERR_ARG, "mid must be in [0, %d]", HN_MAX_LEVEL);
+  if (t->sweep != 0 && t->sweep != 1) return set_error(HN_ERR_ARG, "sweep must be 0 or 1");
   Tuning tu;
   tu.tail_level = t->tail_level;
   tu.cluster = c;
@@ -484,6 +487,7 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
   tu.dsm = t->dsm;
   tu.fuse_up = t->fuse_up;
   tu.mid = t->mid;
+  tu.sweep = t->sweep;
   mg->solo->set_tuning(tu);
   mg->tuning = tu;
   mg->tuned = true;
@@ -501,6 +505,7 @@ hn_status hn_mg_get_tuning(const hn_mg* mg, hn_tuning* t) {
   t->dsm = tu.dsm;
   t->fuse_up = tu.fuse_up;
   t->mid = tu.mid;
+  t->sweep = tu.sweep;
   return HN_OK;
 }
 
@@ -514,18 +519,20 @@ hn_status hn_mg_autotune(hn_mg* mg, const double* b, int reps, hn_tuning* best, 
   HN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&x), (size_t)N * 8));
   struct Free { double* p; ~Free() { cudaFreeHost(p); } } fr{x};
   const int clusters[5] = {1, 2, 4, 8, 16};
-  const int mids[2] = {0, kMidCandidate};
+  // the per-level forms: per-step launches, persistent kernels of the middle levels, fused sweeps
+  const int mids[3] = {0, kMidCandidate, 0}, sweeps[3] = {0, 0, 1};
   double best_ms = 1e300;
-  hn_tuning bt{mg->solo->tuning().tail_level, mg->solo->tuning().cluster, 2, 0, 1, 0, mg->solo->tuning().mid};
+  const Tuning cur = mg->solo->tuning();
+  hn_tuning bt{cur.tail_level, cur.cluster, 2, 0, 1, 0, cur.mid, cur.sweep};
   cudaEvent_t e0, e1;
   HN_CUDA(cudaEventCreate(&e0));
   HN_CUDA(cudaEventCreate(&e1));
   struct Ev { cudaEvent_t a, b; ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); } } ev{e0, e1};
   const int tmax = std::min(mg->L, 9);
-  for (int mi = 0; mi < 2; ++mi)
+  for (int mi = 0; mi < 3; ++mi)
   for (int T = mg->coarse; T <= tmax; ++T)
     for (int ci = 0; ci < 5; ++ci) {
-      hn_tuning t{T, clusters[ci], 2, 0, 1, 0, mids[mi]};
+      hn_tuning t{T, clusters[ci], 2, 0, 1, 0, mids[mi], sweeps[mi]};
       HN_TRY(hn_mg_set_tuning(mg, &t));
       HN_TRY(hn_mg_solve(mg, b, x, 0, 0, nullptr));            // capture + warm-up
       HN_CUDA(cudaEventRecord(e0, mg->solo->stream()));
@@ -569,11 +576,11 @@ hn_status hn_mg_autotune_batch(hn_mg* const* mgs, int count, const double* const
   for (int j = 0; j < count; ++j) Lmax = std::max(Lmax, mgs[j]->L);
   double best_ms = 1e300;
   const int mids[2] = {0, kMidCandidate};
-  hn_tuning bt{5, 1, 2, 0, 1, 0, mids[1]};
+  hn_tuning bt{5, 1, 2, 0, 1, 0, mids[1], 0};
   for (int mi = 0; mi < 2; ++mi)
   for (int T = mgs[0]->coarse; T <= std::min(Lmax, 8); ++T)
     for (int ci = 0; ci < 3; ++ci) {
-      hn_tuning t{T, clusters[ci], 2, 0, 1, 0, mids[mi]};
+      hn_tuning t{T, clusters[ci], 2, 0, 1, 0, mids[mi], 0};
       for (int j = 0; j < count; ++j) {
         Tuning tu; tu.tail_level = T; tu.cluster = clusters[ci]; tu.pdl = 2; tu.mid = mids[mi];
         mgs[j]->tuning = tu;

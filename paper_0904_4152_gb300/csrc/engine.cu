@@ -766,6 +766,19 @@ long long Engine::launch_bytes(int cls, int level) const {
     case KC_PCG_X: per = 4 * 8 + 2 * 8 + vb; break;            // x, r, p, q; write x, r, rhs
     case KC_PCG_DOT: per = 8 + vb; break;                       // r, z
     case KC_PCG_P: per = vb + 8 + 8; break;                     // z, p; write p
+    case KC_SWEEP_DOWN: {
+      // the fused down sweep: bands, rhs and either omega / D (from a zero iterate) or the first
+      // iterate (the problem's own finest level), the second iterate written, the coarse rhs
+      long long sum = 0;
+      for (hn_mg* mg : members_) {
+        if (!mg || level > mg->L || level <= mg->coarse) continue;
+        const bool own = level == mg->L && prm_.solver != SOLVER_PCG;
+        const double pn = 9 * bb + vb + (own ? vb + wd : (prec == P64 ? 8 : 4)) + vb + 0.25 * vb;
+        sum += (long long)(pn * (double)N_of(level));
+      }
+      return sum;
+    }
+    case KC_SWEEP_UP: per = 9 * bb + vb + 0.25 * vb + vb + wd + vb; break;   // bands, x, e_c, rhs; write
     case KC_MID_DOWN:
     case KC_MID_UP: {
       // the persistent kernels: the sum of their steps' bytes over levels T+1..level (the top
@@ -870,6 +883,11 @@ int Engine::mid_top() const {
   return std::min(Lmax_, tune_.mid);
 }
 
+bool Engine::sweep_on() const {
+  const int T = std::max(tune_.tail_level, prm_.coarse);
+  return tune_.sweep && cap_ == 1 && prm_.pre == 2 && prm_.post == 2 && !tune_.staged && mid_top() <= T;
+}
+
 hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
   const int c = prm_.coarse, pre = prm_.pre, post = prm_.post;
   const int T = std::max(tune_.tail_level, c);
@@ -885,9 +903,15 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
     return HN_OK;
   };
   const int M = mid_top();                 // levels T+1..M: the persistent kernels
+  const bool sweep = sweep_on();
   for (int l = Lmax_; l > std::max(T, M); --l) {
     // a finest level: lagged check (the PCG preconditioner's cycle has none)
     const bool top = prm_.solver != SOLVER_PCG && (topMaskAll_ || ((topMask_ >> l) & 1u));
+    if (sweep && !top) {
+      // a zero iterate: both smoothing steps, the defect and the restriction in one launch
+      HN_LAUNCH(KC_SWEEP_DOWN, l, launch_sweep_down(E_, lists_[l], l, want, 0, s));
+      continue;
+    }
     // an engine of one problem takes the check inside the first smoothing step when the norm is
     // one group of partials (the register-path kernel; saves the control launch)
     const bool fuse = top && cap_ == 1 && !tune_.staged && pitch_of(l) / kTile <= kSumGroup;
@@ -896,6 +920,11 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
       if (top) {
         if (!fuse) HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
         HN_TRY(after_check());
+      }
+      if (sweep) {
+        // the second step, the defect and the restriction in one launch
+        HN_LAUNCH(KC_SWEEP_DOWN, l, launch_sweep_down(E_, lists_[l], l, want, 1, s));
+        continue;
       }
       if (!pre_fuses(prm_.prec) || top)
         HN_LAUNCH(KC_JACOBI, l, launch_pre2b(E_, lists_[l], l, want, grid_[l], s));
@@ -914,15 +943,23 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
   if (M > T) HN_LAUNCH(KC_MID_DOWN, M, launch_mid(E_, dLists_, M, T, want, 0, s));
   HN_LAUNCH(KC_TAIL, T, launch_tail(E_, T, want, tune_.cluster, s));
   if (M > T) HN_LAUNCH(KC_MID_UP, M, launch_mid(E_, dLists_, M, T, want, 1, s));
+  int e_sel = 0;                           // buffer of the coarse iterate (the tail's: 0)
   for (int l = std::max(T, M) + 1; l <= Lmax_; ++l) {
+    if (sweep && l < Lmax_) {
+      // prolongation and both post-smoothing steps in one launch; the result in buffer 1
+      HN_LAUNCH(KC_SWEEP_UP, l, launch_sweep_up(E_, lists_[l], l, want, e_sel, s));
+      e_sel = 1;
+      continue;
+    }
     int sw = 1;
     if (tune_.fuse_up && post >= 1) {
       // prolongation and the first post-smoothing step in one pass
-      HN_LAUNCH(KC_PROLONG_JACOBI, l, launch_prolong_jacobi(E_, lists_[l], l, want, pre & 1, grid_[l], s));
+      HN_LAUNCH(KC_PROLONG_JACOBI, l, launch_prolong_jacobi(E_, lists_[l], l, want, (pre & 1) | (e_sel << 1), grid_[l], s));
       sw = 2;
     } else {
-      HN_LAUNCH(KC_PROLONG, l, launch_prolong(E_, lists_[l], l, want, pre & 1, grid_[l], s));
+      HN_LAUNCH(KC_PROLONG, l, launch_prolong(E_, lists_[l], l, want, (pre & 1) | (e_sel << 1), grid_[l], s));
     }
+    e_sel = 0;
     for (; sw <= post; ++sw)
       HN_LAUNCH(KC_JACOBI, l, launch_jacobi(E_, lists_[l], l, want, (pre + sw - 1) & 1, 0, grid_[l], s));
   }
@@ -1224,7 +1261,8 @@ int Engine::kernel_times(hn_kernel_time* out, int max) const {
   static const char* names[KC_COUNT] = {"jacobi", "jacobi_first", "defect", "restrict", "prolong",
                                         "coarse", "check", "outer_defect", "update", "control",
                                         "tail", "pcg_q", "pcg_x", "pcg_dot", "pcg_p",
-                                        "prolong_jacobi", "mid_down", "mid_up"};
+                                        "prolong_jacobi", "mid_down", "mid_up", "sweep_down",
+                                        "sweep_up"};
   int n = 0;
   for (int c = 0; c < KC_COUNT; ++c)
     for (int l = 0; l <= kMaxLevel; ++l) {

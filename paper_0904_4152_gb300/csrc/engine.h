@@ -70,7 +70,7 @@ size_t hierarchy_bytes(int L, int coarse, int prec, int solver);
 enum KClass {
   KC_JACOBI = 0, KC_JACOBI_FIRST, KC_DEFECT, KC_RESTRICT, KC_PROLONG, KC_COARSE, KC_CHECK,
   KC_OUTER_DEFECT, KC_UPDATE, KC_CONTROL, KC_TAIL, KC_PCG_Q, KC_PCG_X, KC_PCG_DOT, KC_PCG_P,
-  KC_PROLONG_JACOBI, KC_MID_DOWN, KC_MID_UP, KC_COUNT
+  KC_PROLONG_JACOBI, KC_MID_DOWN, KC_MID_UP, KC_SWEEP_DOWN, KC_SWEEP_UP, KC_COUNT
 };
 
 // launch shape of the schedule: levels <= tail_level run fused in one cluster launch of
@@ -89,6 +89,10 @@ struct Tuning {
                     // kernels (default: a grid barrier plus the memory latency of a step measured
                     // as long as a kernel boundary, ~3.5 us at L = 10, so they did not pay).
                     // Not combined with staged or fuse_up, which are per-step forms.
+  int sweep = 0;    // an engine of one problem with V(2,2) cycles: the down part of each level
+                    // above the tail (smoothing, defect, restriction) and the up part of each
+                    // level below the finest (prolongation, smoothing) as one launch each over
+                    // 2-D tiles with recomputed halos (k_sweep_down / k_sweep_up)
 };
 
 class Engine;
@@ -247,6 +251,7 @@ class Engine {
   TileList* hLists_ = nullptr;      // its pinned staging copy
   unsigned long long* dBar_ = nullptr;   // grid barriers of the persistent kernels
   int mid_top() const;              // top level of the persistent kernels (<= tail level: none)
+  bool sweep_on() const;            // the fused level sweeps run (tuning sweep, and they apply)
   int fineGrid_ = 1;
   int maxGrid_ = 1;
   std::vector<hn_mg*> members_;

@@ -241,9 +241,22 @@ cudaError_t launch_mid(const EngineDev& E, const TileList* lists, int M, int T, 
 
 cudaError_t launch_restrict(const EngineDev& E, TileList tl_coarse, int fine_level, int want,
                             int grid, cudaStream_t s);
+// Fused level sweeps of an engine of one problem (V(2,2) cycles): tiles of cx x cy coarse nodes,
+// tx x ty of them over the coarse grid of the level, tile-local pitch P = 2 cx + 7 and R = 2 cy + 7
+// rows in shared memory.  sweep_geom gives the tiles of level `level`, sweep_smem_bytes their
+// shared memory.  launch_sweep_down: top = 1 on the problem's own finest level (after its first
+// smoothing step), 0 on a level whose iterate starts at zero; launch_sweep_up: e_sel = the buffer
+// of the coarse iterate (its result goes to buffer 1).
+struct SweepGeom { int cx, cy, tx, ty, P, R; };
+SweepGeom sweep_geom(int level);
+size_t sweep_smem_bytes(int prec, const SweepGeom& g);
+cudaError_t launch_sweep_down(const EngineDev& E, TileList tl, int level, int want, int top, cudaStream_t s);
+cudaError_t launch_sweep_up(const EngineDev& E, TileList tl, int level, int want, int e_sel, cudaStream_t s);
+// x_sel: bit 0 the fine buffer corrected in place, bit 1 the buffer of the coarse iterate
 cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want, int x_sel,
                            int grid, cudaStream_t s);
-// the prolongation into x[x_sel] fused into the first post-smoothing step (result in x[1 - x_sel])
+// the prolongation into x[s] fused into the first post-smoothing step (result in x[1 - s]); s = bit 0
+// of x_sel, bit 1 the buffer of the coarse iterate
 cudaError_t launch_prolong_jacobi(const EngineDev& E, TileList tl, int level, int want, int x_sel,
                                   int grid, cudaStream_t s);
 cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, cudaStream_t s);

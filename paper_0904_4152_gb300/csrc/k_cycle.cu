@@ -13,6 +13,7 @@
 // one- or two-column overhang at each side comes from the neighbouring lanes by warp shuffles.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 #include <cooperative_groups.h>
 
@@ -114,12 +115,33 @@ struct F16 { using B = __half; using V = float; using A = float; static constexp
 // earlier launch); LD_CG reads global memory from L2 (data written earlier in the same launch by
 // other SMs of the cluster); LD_GEN is a plain generic load (data in shared memory).  Bands are
 // never written by the solver: NC from global memory, GEN from shared memory.
-enum { LD_NC = 0, LD_CG = 1, LD_GEN = 2 };
+// LD_EF: non-coherent, marked first to be evicted from L2 (data read once per outer step, such as
+// the FP64 operator of the outer defect, which would otherwise push the inner cycles' working set
+// out of L2).
+enum { LD_NC = 0, LD_CG = 1, LD_GEN = 2, LD_EF = 3 };
 template <int LK> __device__ __forceinline__ constexpr int band_kind() { return LK == LD_GEN ? LD_GEN : LD_NC; }
+
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ double2 ld_ef(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+               : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+}
+__device__ __forceinline__ double ld_ef(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+}
 
 template <int LK, class T> __device__ __forceinline__ T ldk(const T* p) {
   if constexpr (LK == LD_NC) return __ldg(p);
   else if constexpr (LK == LD_CG) return __ldcg(p);
+  else if constexpr (LK == LD_EF) return ld_ef(p);
   else return *p;
 }
 template <int LK> __device__ __forceinline__ double ld1(const double* p) { return ldk<LK>(p); }
@@ -282,6 +304,42 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
+}
+
+// Tile partial of a residual norm: the sum over the warp of the squares of each lane's 4 values.
+// FP64 values: squares and sums in FP64.  FP32 values: on the FP32 pipe in double-float
+// arithmetic (each square exactly as p + e by an FMA, sums by TwoSum), within ~2^-46 of the exact
+// sum of the non-negative terms; FP64 operations run at 1/74 of the FP32 rate on this part, and
+// per node four of them (two conversions, a product, a sum) cost as much as the band kernel's
+// memory traffic at L = 10.  Every lane gets the same value (each butterfly step is symmetric in
+// its two operands).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (bh - bb);  // TwoSum: hi + bh = s + err exactly
+  const float t = err + (lo + bl);
+  hi = s + t;                                      // FastTwoSum (|s| >= |t|)
+  lo = t - (hi - s);
+}
+__device__ __forceinline__ double tile_sumsq(const double (&r)[4]) {
+  double q = 0.0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) q += r[j] * r[j];
+  return warp_sum(q);
+}
+__device__ __forceinline__ double tile_sumsq(const float (&r)[4]) {
+  float hi = __fmul_rn(r[0], r[0]), lo = fmaf(r[0], r[0], -hi);
+#pragma unroll
+  for (int j = 1; j < 4; ++j) {
+    const float p = __fmul_rn(r[j], r[j]);
+    df_add(hi, lo, p, fmaf(r[j], r[j], -p));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(kFull, hi, o), bl = __shfl_xor_sync(kFull, lo, o);
+    df_add(hi, lo, bh, bl);
+  }
+  return double(hi) + double(lo);                  // exact (lo is below half an ulp of hi)
 }
 
 // deterministic block sum of a per-thread value (256 threads)
@@ -528,10 +586,7 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
       for (int j = 0; j < 4; ++j) out[j] = V(r[j]);
       st4(static_cast<V*>(d.r) + i0, out);
     } else if constexpr (MODE == M_CHECK) {
-      double q = 0.0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) q += double(r[j]) * double(r[j]);
-      q = warp_sum(q);
+      const double q = tile_sumsq(r);
       if (lane == 0) *partial_slot = q;
     } else {                                      // a Jacobi step src -> dst
       A wd[4];
@@ -542,10 +597,7 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
       st4(static_cast<V*>(d.x[dst]) + i0, out);
       if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST) {
         if (partial_slot) {                       // residual norm of the iterate (lagged check)
-          double q = 0.0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) q += double(r[j]) * double(r[j]);
-          q = warp_sum(q);
+          const double q = tile_sumsq(r);
           if (lane == 0) *partial_slot = q;
         }
       }
@@ -556,14 +608,14 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
 // Full-weighting restriction of the fine defect onto coarse node (I, J) (Dirichlet and padding
 // nodes get 0).  Summation order: fine rows 2J-1, 2J, 2J+1, columns 2I-1, 2I, 2I+1, weights 1/4,
 // 1/2, 1/4 x 1/4, 1/2, 1/4 (products by powers of two are exact); a fine node off the grid (next
-// to a free Neumann side) contributes 0.  rd(i) reads fine node i.
+// to a free Neumann side) contributes 0.  rd(y, x) reads fine node (x, y).
 template <class V, class F>
-__device__ __forceinline__ V restrict_value(int I, int J, int nc, int nf, int bc, F rd) {
+__device__ __forceinline__ V restrict_value_xy(int I, int J, int nc, int nf, int bc, F rd) {
   if (I < 0 || J >= nc || is_dirichlet(I, J, nc, bc)) return V(0);
   const int fx = 2 * I, fy = 2 * J;
   auto R = [&](int dy, int dx) -> V {
     const int x = fx + dx, y = fy + dy;
-    return (x >= 0 && y >= 0 && x < nf && y < nf) ? rd((long long)y * nf + x) : V(0);
+    return (x >= 0 && y >= 0 && x < nf && y < nf) ? rd(y, x) : V(0);
   };
   const V q = V(0.25), h = V(0.5);
   V v = q * R(-1, -1);
@@ -576,6 +628,11 @@ __device__ __forceinline__ V restrict_value(int I, int J, int nc, int nf, int bc
   v = fma(h, R(1, 0), v);
   v = fma(q, R(1, 1), v);
   return v;
+}
+// the same with rd(i) reading fine node i = y nf + x
+template <class V, class F>
+__device__ __forceinline__ V restrict_value(int I, int J, int nc, int nf, int bc, F rd) {
+  return restrict_value_xy<V>(I, J, nc, nf, bc, [&](int y, int x) { return rd((long long)y * nf + x); });
 }
 
 // Restriction of the coarse warp-tile starting at t0 (128 nodes): lane l takes the coarse nodes
@@ -615,28 +672,34 @@ __device__ __forceinline__ void restrict_tile(const LevelDev& f, const LevelDev&
   }
 }
 
-// x_f[x_sel] += P e_c at fine node (ix, iy): bilinear interpolation of the coarse iterate
-// (buffer 0); Dirichlet fine nodes are left unchanged (their coarse neighbours on the same side
-// are Dirichlet too and hold 0).  Returns the value added (0 for Dirichlet nodes).
+// x_f[x_sel] += P e_c at fine node (ix, iy): bilinear interpolation of the coarse iterate, ec(cy, cx)
+// reading coarse node (cx, cy); Dirichlet fine nodes are left unchanged (their coarse neighbours on
+// the same side are Dirichlet too and hold 0).  Returns false for them, else the value added.
 template <class V, class F>
-__device__ __forceinline__ bool prolong_value(int ix, int iy, int nf, int nc, int bc, F ec, V* add) {
+__device__ __forceinline__ bool prolong_value_xy(int ix, int iy, int nf, int bc, F ec, V* add) {
   if (is_dirichlet(ix, iy, nf, bc)) return false;
   const int cx0 = ix >> 1, cx1 = (ix + 1) >> 1, cy0 = iy >> 1, cy1 = (iy + 1) >> 1;
   const bool ox = ix & 1, oy = iy & 1;
-  if (!ox && !oy) *add = ec(cy0 * nc + cx0);
-  else if (ox && !oy) *add = V(0.5) * (ec(cy0 * nc + cx0) + ec(cy0 * nc + cx1));
-  else if (!ox && oy) *add = V(0.5) * (ec(cy0 * nc + cx0) + ec(cy1 * nc + cx0));
-  else *add = V(0.25) * (((ec(cy0 * nc + cx0) + ec(cy0 * nc + cx1)) + ec(cy1 * nc + cx0)) + ec(cy1 * nc + cx1));
+  if (!ox && !oy) *add = ec(cy0, cx0);
+  else if (ox && !oy) *add = V(0.5) * (ec(cy0, cx0) + ec(cy0, cx1));
+  else if (!ox && oy) *add = V(0.5) * (ec(cy0, cx0) + ec(cy1, cx0));
+  else *add = V(0.25) * (((ec(cy0, cx0) + ec(cy0, cx1)) + ec(cy1, cx0)) + ec(cy1, cx1));
   return true;
 }
+// the same with ec(k) reading coarse node k = cy nc + cx
+template <class V, class F>
+__device__ __forceinline__ bool prolong_value(int ix, int iy, int nf, int nc, int bc, F ec, V* add) {
+  return prolong_value_xy<V>(ix, iy, nf, bc, [&](int cy, int cx) { return ec(cy * nc + cx); }, add);
+}
 
-// x_f[x_sel] += P e_c on fine tile i0
+// x_f[x_sel & 1] += P e_c on fine tile i0; e_c is the coarse iterate in buffer (x_sel >> 1) & 1
+// (buffer 1 after a fused up sweep of the coarse level, else buffer 0)
 template <class V, int LK>
 __device__ __forceinline__ void prolong_tile(const LevelDev& f, const LevelDev& c, int x_sel,
                                              long long i0) {
   const int nf = f.n, nc = c.n, Nf = nf * nf;
-  const V* e = static_cast<const V*>(c.x[0]);
-  V* x = static_cast<V*>(f.x[x_sel]);
+  const V* e = static_cast<const V*>(c.x[(x_sel >> 1) & 1]);
+  V* x = static_cast<V*>(f.x[x_sel & 1]);
   V v[4];
   if constexpr (LK == LD_NC) ld4c(x + i0, v);   // read and rewritten by this thread only
   else ld4<LK>(x + i0, v);                      // written earlier in this launch
@@ -785,10 +848,11 @@ __device__ __forceinline__ void load_row_prolonged(const V* x, const V* e, long 
   w[0] = l2; w[1] = l1; w[2] = c[0]; w[3] = c[1]; w[4] = c[2]; w[5] = c[3]; w[6] = r0; w[7] = r1;
 }
 
-// The prolongation x_f[in_sel] += P e_c and the first post-smoothing Jacobi step in one pass:
-// the step's windows are formed from x and e_c on the fly, the corrected iterate is not stored
-// (the second step overwrites it), the step's result goes to buffer 1 - in_sel.  Identical values
-// to the separate prolongation and Jacobi kernels.
+// The prolongation x_f[s] += P e_c and the first post-smoothing Jacobi step in one pass (s =
+// in_sel & 1; e_c in coarse buffer (in_sel >> 1) & 1, as for prolong_tile): the step's windows are
+// formed from x and e_c on the fly, the corrected iterate is not stored (the second step
+// overwrites it), the step's result goes to buffer 1 - s.  Identical values to the separate
+// prolongation and Jacobi kernels.
 template <class Pol, int LK>
 __device__ __forceinline__ void prolong_jacobi_tile(const LevelDev& d, const LevelDev& c, long long shift,
                                                     long long i0, int lane, int in_sel,
@@ -797,8 +861,9 @@ __device__ __forceinline__ void prolong_jacobi_tile(const LevelDev& d, const Lev
   using V = typename Pol::V;
   const int nf = d.n, nc = c.n;
   const long long Nf = (long long)nf * nf;
+  const V* e = static_cast<const V*>(c.x[(in_sel >> 1) & 1]);
+  in_sel &= 1;
   const V* x = static_cast<const V*>(d.x[in_sel]);
-  const V* e = static_cast<const V*>(c.x[0]);
   const int iy0 = (int)((unsigned long long)i0 / (unsigned)nf), ix0 = (int)(i0 - (long long)iy0 * nf);
   V w[3][8];
 #pragma unroll
@@ -2061,6 +2126,292 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
   }
 }
 
+// ------------------------------------------------------ fused level sweeps over 2-D tiles
+// An engine of one problem running V(2,2) cycles may take the down part of a level above the fused
+// tail (the two pre-smoothing steps, the defect and the restriction) and the up part (the
+// prolongation and the two post-smoothing steps) as one launch each, in place of three.  A block
+// takes a tile of the coarse grid, coarse columns I0..I1-1 and rows J0..J1-1 (cx x cy coarse
+// nodes; the last tile of a row or column also takes the leftover boundary node), and owns the
+// fine nodes 2 I0 .. 2 I1 - 1 (clipped to the grid) in each direction.  Each step is recomputed on
+// a halo as wide as the steps after it read, so blocks exchange nothing: the restriction reads
+// the defect on fine columns 2 I0 - 1 .. 2 I1 - 1, the defect reads the second iterate one node
+// further out, the second iterate reads the first one a node further still.  The tile-local copy
+// of the level (bands, right-hand side, omega / D, both iterates, the defect) sits in shared
+// memory with row pitch P = 2 cx + 7 and origin at fine node (2 I0 - 3, 2 J0 - 3), zero off the
+// grid (where every coupling of a grid node is zero), and every value is computed by the node-wise
+// steps of the fused tail's shared-memory levels (band_node: the tile steps' operands and order),
+// so a fused sweep stores the bits the separate launches store.  A tile's inputs arrive by
+// asynchronous copies (cp.async, zero-filled off the grid) that all its threads issue before one
+// wait: one memory latency per tile.  The up sweep writes its result to buffer 1 (the halos of
+// other blocks still read buffer 0); the next finer level's prolongation reads it there.
+constexpr int kSweepCX = 16, kSweepCY = 8;       // coarse nodes per tile (largest)
+// threads per tile: about one node of the widest region each, so that a tile's chain of dependent
+// steps is short (a tile is latency-bound: 256 threads took ~10 us per tile at L = 8)
+constexpr int kSweepThreads = 1024;
+struct SweepTile { int I0, I1, J0, J1, ox, oy; };
+
+__device__ __forceinline__ SweepTile sweep_tile(const SweepGeom& g, int nc, int tile) {
+  SweepTile t;
+  const int by = tile / g.tx, bx = tile - by * g.tx;
+  t.I0 = bx * g.cx;
+  t.I1 = bx == g.tx - 1 ? nc : t.I0 + g.cx;
+  t.J0 = by * g.cy;
+  t.J1 = by == g.ty - 1 ? nc : t.J0 + g.cy;
+  t.ox = 2 * t.I0 - 3;
+  t.oy = 2 * t.J0 - 3;
+  return t;
+}
+
+// f(tile-local index, x, y, on the grid) for every fine node (x, y) of [x0, x1) x [y0, y1),
+// strided over the block
+template <class F>
+__device__ __forceinline__ void sweep_region(const SweepTile& t, int P, int n, int x0, int x1, int y0,
+                                             int y1, F&& f) {
+  const int w = x1 - x0, cnt = w * (y1 - y0);
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const int v = q / w, u = q - v * w;
+    const int gx = x0 + u, gy = y0 + v;
+    f((gx - t.ox) + (gy - t.oy) * P, gx, gy, gx >= 0 && gy >= 0 && gx < n && gy < n);
+  }
+}
+
+// an asynchronous copy of one 4- or 8-byte element to shared memory; with on == false nothing is
+// read and the element is zero-filled (a source size of 0)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* smem_dst, const void* gmem_src, bool on) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const unsigned sz = on ? (unsigned)BYTES : 0u;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES), "r"(sz)
+               : "memory");
+}
+// element li of a tile-local array from element gi of a level array (zero if !on)
+template <class T>
+__device__ __forceinline__ void cp_elem(const void* dst, int li, const void* src, long long gi, bool on) {
+  cp_async_elem<(int)sizeof(T)>(const_cast<T*>(static_cast<const T*>(dst)) + li,
+                                static_cast<const T*>(src) + (on ? gi : 0), on);
+}
+// the 9 bands of grid node gi into tile-local element li.  Halves go in 4-byte pairs: the tile-local
+// and global indices of a node have the same parity (P and n are odd, the origin's coordinates
+// odd), so a node of even index copies itself and its right neighbour, a node of odd index whose
+// left neighbour is not copied (left_in false) copies the pair ending at itself.
+template <class Pol>
+__device__ __forceinline__ void cp_bands(const LevelDev& t, const LevelDev& g, int li, long long gi,
+                                         bool left_in) {
+  using B = typename Pol::B;
+  if constexpr (Pol::prec == P16) {
+    int l2;
+    long long g2;
+    if ((gi & 1) == 0) { l2 = li; g2 = gi; }
+    else if (!left_in) { l2 = li - 1; g2 = gi - 1; }
+    else return;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      cp_async_elem<4>(const_cast<B*>(static_cast<const B*>(t.band[k])) + l2, static_cast<const B*>(g.band[k]) + g2,
+                       true);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) cp_elem<B>(t.band[k], li, g.band[k], gi, true);
+  }
+}
+
+// the tile-local level in dynamic shared memory (the host sizes it by sweep_smem_bytes); e: the
+// coarse iterate around the tile (up sweep), pitch cx + 4.  Every thread forms the descriptor in its
+// own registers (the node-wise steps read its pointers for every node).
+template <class Pol>
+__device__ __forceinline__ void sweep_carve(LevelDev& t, const LevelDev& g, unsigned char* base,
+                                            const SweepGeom& sg, typename Pol::V** e) {
+  using B = typename Pol::B;
+  using V = typename Pol::V;
+  const long long cnt = (long long)sg.P * sg.R;
+  long long off = 0;
+  auto take = [&](long long bytes) { unsigned char* r = base + off; off += (bytes + 15) / 16 * 16; return r; };
+  t = g;                                          // scales, boundary mask
+  for (int k = 0; k < 9; ++k) t.band[k] = take(cnt * (long long)sizeof(B));
+  if constexpr (Pol::prec == P64) t.wdinv = reinterpret_cast<const double*>(take(cnt * 8));
+  else t.wdf = reinterpret_cast<const float*>(take(cnt * 4));
+  t.x[0] = take(cnt * (long long)sizeof(V));
+  t.x[1] = take(cnt * (long long)sizeof(V));
+  t.rhs = take(cnt * (long long)sizeof(V));
+  t.r = take(cnt * (long long)sizeof(V));
+  *e = reinterpret_cast<V*>(take((long long)(sg.cx + 4) * (sg.cy + 4) * (long long)sizeof(V)));
+  t.n = sg.P;
+  t.pitch = (int)cnt;
+}
+
+__device__ __forceinline__ bool sweep_geom_ok(const EngineDev& E, const SweepGeom& sg, int nc, int line) {
+#if HN_DEBUG_CHECKS
+  const bool ok = sg.cx >= 1 && sg.cy >= 1 && sg.tx * sg.cx == nc - 1 && sg.ty * sg.cy == nc - 1 &&
+                  sg.P == 2 * sg.cx + 7 && sg.R == 2 * sg.cy + 7;
+  if (!ok) dbg_fail(E, line, sg.cx, sg.cy);
+  return ok;
+#else
+  (void)E; (void)sg; (void)nc; (void)line;
+  return true;
+#endif
+}
+
+// Down sweep of level `level`.  top = 0: the iterate of the level is zero (a level below the
+// problem's own finest, or the preconditioner's cycle of CG): both smoothing steps from b, as
+// M_PRE12 forms them.  top = 1: the problem's own finest level, whose first smoothing step (with
+// the lagged check) ran before: the second step from buffer 1 (M_PRE2B), or, in the first cycle
+// from a zero iterate, where the first launch took both steps, the defect of buffer 0 alone.
+template <class Pol>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_down(EngineDev E, TileList tl, int level, int want,
+                                                              int top, SweepGeom sg) {
+  using A = typename Pol::A;
+  using V = typename Pol::V;
+  using W = typename std::conditional<Pol::prec == P64, double, float>::type;   // omega / D
+  extern __shared__ __align__(16) unsigned char smem[];
+  pdl_start();
+  const ProbState& st = E.S[0];
+  if (st.phase != want) return;
+  const LevelDev& g = tl.solo_d;
+  const LevelDev& gc = tl.solo_c;
+  if (gc.n == 0) return;                          // (no coarser level)
+  if (!dbg_level(E, g, level, tl.solo_tiles, __LINE__) || !dbg_level(E, gc, level - 1, 0, __LINE__) ||
+      !sweep_geom_ok(E, sg, gc.n, __LINE__))
+    return;
+  const int mode = !top ? 0 : (st.zero_top ? 2 : 1);
+  LevelDev t;
+  V* es;
+  sweep_carve<Pol>(t, g, smem, sg, &es);
+  (void)es;
+  const int n = g.n, nc = gc.n, P = sg.P;
+  const A omega = A(E.prm.omega);
+  V* x0s = static_cast<V*>(t.x[0]);
+  const V* rs = static_cast<const V*>(t.r);
+  V* xg = static_cast<V*>(g.x[0]);
+  V* rc = static_cast<V*>(gc.rhs);
+  const void* wds = Pol::prec == P64 ? static_cast<const void*>(t.wdinv) : static_cast<const void*>(t.wdf);
+  const void* wdg = Pol::prec == P64 ? static_cast<const void*>(g.wdinv) : static_cast<const void*>(g.wdf);
+  for (int tile = blockIdx.x; tile < sg.tx * sg.ty; tile += gridDim.x) {
+    const SweepTile w = sweep_tile(sg, nc, tile);
+    // the defect's region; the second iterate's is one node wider, the first iterate's two
+    const int ax = 2 * w.I0 - 1, bx = 2 * w.I1, ay = 2 * w.J0 - 1, by = 2 * w.J1;
+    // the bands on the region of the first step computed here (mode 2: the defect's)
+    const int bx0 = mode == 2 ? ax : ax - 1;
+    sweep_region(w, P, n, ax - 2, bx + 2, ay - 2, by + 2, [&](int li, int gx, int gy, bool on) {
+      const long long gi = (long long)gy * n + gx;
+      const bool in2 = gx >= ax - 1 && gx < bx + 1 && gy >= ay - 1 && gy < by + 1;
+      const bool inr = gx >= ax && gx < bx && gy >= ay && gy < by;
+      const bool inb = mode == 2 ? inr : in2;
+      if (mode == 0) {
+        cp_elem<V>(t.rhs, li, g.rhs, gi, on);
+        cp_elem<W>(wds, li, wdg, gi, on);
+      } else if (mode == 1) {
+        cp_elem<V>(t.x[1], li, g.x[1], gi, on);
+        if (in2) {
+          cp_elem<V>(t.rhs, li, g.rhs, gi, on);
+          if constexpr (Pol::prec == P64) cp_elem<W>(wds, li, wdg, gi, on);
+        }
+      } else {
+        if (in2) cp_elem<V>(t.x[0], li, g.x[0], gi, on);
+        if (inr) cp_elem<V>(t.rhs, li, g.rhs, gi, on);
+      }
+      if (inb && on) cp_bands<Pol>(t, g, li, gi, gx - 1 >= bx0 && gx >= 1);
+    });
+    cp_async_wait();
+    __syncthreads();
+    if (mode != 2) {
+      // the second iterate; the block's own nodes also go to buffer 0 of the level
+      sweep_region(w, P, n, ax - 1, bx + 1, ay - 1, by + 1, [&](int li, int gx, int gy, bool on) {
+        if (!on) { x0s[li] = V(0); return; }
+        if (mode == 0) band_node<Pol, M_PRE12>(t, li, true, 0, omega);
+        else band_node<Pol, M_PRE2B>(t, li, false, 0, omega);
+        if (gx >= 2 * w.I0 && gx < 2 * w.I1 && gy >= 2 * w.J0 && gy < 2 * w.J1)
+          xg[(long long)gy * n + gx] = x0s[li];
+      });
+      __syncthreads();
+    }
+    sweep_region(w, P, n, ax, bx, ay, by, [&](int li, int, int, bool on) {
+      if (on) band_node<Pol, M_DEFECT>(t, li, false, 0, omega);
+    });
+    __syncthreads();
+    // the restriction onto the block's own coarse nodes
+    const int cw = w.I1 - w.I0, cnt = cw * (w.J1 - w.J0);
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      const int jj = q / cw, J = w.J0 + jj, I = w.I0 + (q - jj * cw);
+      rc[(long long)J * nc + I] = restrict_value_xy<V>(I, J, nc, n, gc.bc, [&](int y, int x) {
+        return rs[(x - w.ox) + (y - w.oy) * P];
+      });
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0)                            // the coarse padding nodes, as the restriction kernel
+    for (int q = nc * nc + threadIdx.x; q < gc.pitch; q += blockDim.x) rc[q] = V(0);
+}
+
+// Up sweep of level `level` (below the problem's own finest level): x + P e_c from buffer 0 and
+// the coarse iterate in buffer e_sel, then the two post-smoothing steps; the result to buffer 1.
+template <class Pol>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_up(EngineDev E, TileList tl, int level, int want,
+                                                            int e_sel, SweepGeom sg) {
+  using A = typename Pol::A;
+  using V = typename Pol::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  pdl_start();
+  const ProbState& st = E.S[0];
+  if (st.phase != want) return;
+  const LevelDev& g = tl.solo_d;
+  const LevelDev& gc = tl.solo_c;
+  if (gc.n == 0) return;
+  if (!dbg_level(E, g, level, tl.solo_tiles, __LINE__) || !dbg_level(E, gc, level - 1, 0, __LINE__) ||
+      !sweep_geom_ok(E, sg, gc.n, __LINE__))
+    return;
+  LevelDev t;
+  V* es;
+  sweep_carve<Pol>(t, g, smem, sg, &es);
+  const int n = g.n, nc = gc.n, P = sg.P, Pe = sg.cx + 4;
+  const A omega = A(E.prm.omega);
+  V* x0s = static_cast<V*>(t.x[0]);
+  V* x1s = static_cast<V*>(t.x[1]);
+  const V* e = static_cast<const V*>(gc.x[e_sel & 1]);
+  V* out = static_cast<V*>(g.x[1]);
+  for (int tile = blockIdx.x; tile < sg.tx * sg.ty; tile += gridDim.x) {
+    const SweepTile w = sweep_tile(sg, nc, tile);
+    const int ax = 2 * w.I0, bx = min(2 * w.I1, n), ay = 2 * w.J0, by = min(2 * w.J1, n);   // own
+    // the iterate two nodes around the own ones; bands, rhs (and omega / D) one node around
+    sweep_region(w, P, n, ax - 2, bx + 2, ay - 2, by + 2, [&](int li, int gx, int gy, bool on) {
+      const long long gi = (long long)gy * n + gx;
+      cp_elem<V>(t.x[0], li, g.x[0], gi, on);
+      if (gx >= ax - 1 && gx < bx + 1 && gy >= ay - 1 && gy < by + 1) {
+        cp_elem<V>(t.rhs, li, g.rhs, gi, on);
+        if constexpr (Pol::prec == P64) cp_elem<double>(t.wdinv, li, g.wdinv, gi, on);
+        if (on) cp_bands<Pol>(t, g, li, gi, gx - 1 >= ax - 1 && gx >= 1);
+      }
+    });
+    // the coarse iterate on coarse columns I0-1 .. I1+1 and rows J0-1 .. J1+1
+    const int ew = w.I1 - w.I0 + 3, ecnt = ew * (w.J1 - w.J0 + 3);
+    for (int q = threadIdx.x; q < ecnt; q += blockDim.x) {
+      const int v = q / ew, u = q - v * ew;
+      const int cxg = w.I0 - 1 + u, cyg = w.J0 - 1 + v;
+      cp_elem<V>(es, u + v * Pe, e, (long long)cyg * nc + cxg, cxg >= 0 && cyg >= 0 && cxg < nc && cyg < nc);
+    }
+    cp_async_wait();
+    __syncthreads();
+    // y = x + P e_c (prolong_node's values; off the grid and at Dirichlet nodes x itself)
+    sweep_region(w, P, n, ax - 2, bx + 2, ay - 2, by + 2, [&](int li, int gx, int gy, bool on) {
+      if (!on) return;
+      V add;
+      if (prolong_value_xy<V>(gx, gy, n, g.bc, [&](int cy, int cx) {
+            return es[(cx - (w.I0 - 1)) + (cy - (w.J0 - 1)) * Pe];
+          }, &add))
+        x0s[li] = x0s[li] + add;
+    });
+    __syncthreads();
+    sweep_region(w, P, n, ax - 1, bx + 1, ay - 1, by + 1, [&](int li, int, int, bool on) {
+      if (on) band_node<Pol, M_JACOBI>(t, li, false, 0, omega);
+      else x1s[li] = V(0);
+    });
+    __syncthreads();
+    sweep_region(w, P, n, ax, bx, ay, by, [&](int li, int gx, int gy, bool) {
+      band_node<Pol, M_JACOBI>(t, li, false, 1, omega);
+      out[(long long)gy * n + gx] = x0s[li];
+    });
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------- persistent kernels of the middle levels
 // The levels between the fused coarse-level kernel (k_tail, levels coarse..T) and a top level M
 // run in two cooperative launches per V cycle: k_mid_down does pre-smoothing, defect and
@@ -2418,7 +2769,7 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
     const LevelDev& top = P.lev[P.L];
     const long long i0 = (long long)it.y * kTile + lane * kLaneNodes;
     double b[4], r[4];
-    ld4<LD_NC>(P.b64 + i0, b);
+    ld4<LD_EF>(P.b64 + i0, b);
     if (st.x_zero) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) r[j] = b[j];
@@ -2428,7 +2779,7 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
       for (int dy = -1; dy <= 1; ++dy) load_row<double, LD_NC>(P.x64, i0 + dy * (1LL << P.L), lane, w[dy + 1]);
 #pragma unroll
       for (int j = 0; j < 4; ++j) r[j] = b[j];       // r = b - A x as one chain from b
-      stencil_windows<F64, LD_NC, true>(reinterpret_cast<const void* const*>(P.band64), nullptr, w, i0, r, dg);
+      stencil_windows<F64, LD_EF, true>(reinterpret_cast<const void* const*>(P.band64), nullptr, w, i0, r, dg);
     }
     const double s = st.s;
     V out[4];
@@ -3047,6 +3398,15 @@ cudaError_t prepare_kernels() {
   staged((const void*)k_band_staged<F16, M_JACOBI_FIRST>, staged_smem<F16>());
   staged((const void*)k_band_staged<F16, M_PRE12>, staged_smem<F16>());
   staged((const void*)k_band_staged<F16, M_PRE2B>, staged_smem<F16>());
+  // the fused sweeps: their largest tiles
+  SweepGeom g;
+  g.cx = kSweepCX; g.cy = kSweepCY; g.P = 2 * g.cx + 7; g.R = 2 * g.cy + 7; g.tx = g.ty = 1;
+  staged((const void*)k_sweep_down<F64>, sweep_smem_bytes(P64, g));
+  staged((const void*)k_sweep_down<F32>, sweep_smem_bytes(P32, g));
+  staged((const void*)k_sweep_down<F16>, sweep_smem_bytes(P16, g));
+  staged((const void*)k_sweep_up<F64>, sweep_smem_bytes(P64, g));
+  staged((const void*)k_sweep_up<F32>, sweep_smem_bytes(P32, g));
+  staged((const void*)k_sweep_up<F16>, sweep_smem_bytes(P16, g));
   return e;
 }
 
@@ -3106,6 +3466,53 @@ cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want,
   grid = grid_or_one(grid);
   if (E.prm.prec == P64) return launch_k(k_prolong<double>, grid, 0, s, E.pdl, 0, E, tl, level, want, x_sel);
   return launch_k(k_prolong<float>, grid, 0, s, E.pdl, 0, E, tl, level, want, x_sel);
+}
+
+SweepGeom sweep_geom(int level) {
+  const int h = 1 << (level - 1);                 // coarse intervals per side
+  SweepGeom g;
+  g.cx = std::min(kSweepCX, h);
+  g.cy = std::min(kSweepCY, h);
+  g.tx = h / g.cx;
+  g.ty = h / g.cy;
+  g.P = 2 * g.cx + 7;
+  g.R = 2 * g.cy + 7;
+  return g;
+}
+
+size_t sweep_smem_bytes(int prec, const SweepGeom& g) {
+  const size_t cnt = (size_t)g.P * g.R;
+  const size_t bb = prec == P64 ? 8 : (prec == P32 ? 4 : 2), vb = prec == P64 ? 8 : 4;
+  auto al = [](size_t b) { return (b + 15) / 16 * 16; };
+  // bands, omega / D, x0, x1, rhs, r; the coarse iterate around the tile
+  return 9 * al(cnt * bb) + al(cnt * vb) + 4 * al(cnt * vb) + al((size_t)(g.cx + 4) * (g.cy + 4) * vb);
+}
+
+template <class Pol>
+cudaError_t launch_sweep_t(const EngineDev& E, TileList tl, int level, int want, int arg, int up,
+                           cudaStream_t s) {
+  const SweepGeom g = sweep_geom(level);
+  const size_t smem = sweep_smem_bytes(Pol::prec, g);
+  if (up) return launch_kt(k_sweep_up<Pol>, g.tx * g.ty, kSweepThreads, smem, s, E.pdl, 0, E, tl, level, want, arg, g);
+  return launch_kt(k_sweep_down<Pol>, g.tx * g.ty, kSweepThreads, smem, s, E.pdl, 0, E, tl, level, want, arg, g);
+}
+
+cudaError_t launch_sweep_down(const EngineDev& E, TileList tl, int level, int want, int top, cudaStream_t s) {
+  switch (E.prm.prec) {
+    case P64: return launch_sweep_t<F64>(E, tl, level, want, top, 0, s);
+    case P32: return launch_sweep_t<F32>(E, tl, level, want, top, 0, s);
+    case P16: return launch_sweep_t<F16>(E, tl, level, want, top, 0, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep_up(const EngineDev& E, TileList tl, int level, int want, int e_sel, cudaStream_t s) {
+  switch (E.prm.prec) {
+    case P64: return launch_sweep_t<F64>(E, tl, level, want, e_sel, 1, s);
+    case P32: return launch_sweep_t<F32>(E, tl, level, want, e_sel, 1, s);
+    case P16: return launch_sweep_t<F16>(E, tl, level, want, e_sel, 1, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, cudaStream_t s) {

@@ -2,8 +2,9 @@
 // kept in a file that later runs read).  A text file named by HN_TUNE_CACHE holds one line per
 // (GPU name, level, precision, solver, coarse solver, coarse level):
 //
-//   <gpu name>|<L>|<prec>|<solver>|<coarse solver>|<coarse L> <tail_level> <cluster> <pdl> <staged> <dsm> <fuse_up> <mid>
+//   <gpu name>|<L>|<prec>|<solver>|<coarse solver>|<coarse L> <tail_level> <cluster> <pdl> <staged> <dsm> <fuse_up> <mid> <sweep>
 //
+// (an entry without the last field has sweep 0)
 // hn_mg_autotune stores its result there; hn_mg_setup applies a stored shape to a new hierarchy
 // of the same key.  Host code only: no device call.
 #include <cstdio>
@@ -47,10 +48,16 @@ bool parse_shape(const std::string& rest, hn_tuning* t) {
   std::istringstream is(rest);
   hn_tuning v{};
   if (!(is >> v.tail_level >> v.cluster >> v.pdl >> v.staged >> v.dsm >> v.fuse_up >> v.mid)) return false;
+  if (!(is >> v.sweep)) {
+    if (!is.eof()) return false;                  // a seventh field that is not a number
+    v.sweep = 0;
+  }
+  std::string extra;
+  if (is >> extra) return false;
   const int c = v.cluster;
   if (v.tail_level < HN_MIN_LEVEL || v.tail_level > HN_MAX_LEVEL || !(c == 1 || c == 2 || c == 4 || c == 8 || c == 16) ||
       v.pdl < 0 || v.pdl > 3 || (v.staged != 0 && v.staged != 1) || (v.dsm != 0 && v.dsm != 1) ||
-      (v.fuse_up != 0 && v.fuse_up != 1) || v.mid < 0 || v.mid > HN_MAX_LEVEL)
+      (v.fuse_up != 0 && v.fuse_up != 1) || v.mid < 0 || v.mid > HN_MAX_LEVEL || (v.sweep != 0 && v.sweep != 1))
     return false;
   *t = v;
   return true;
@@ -86,7 +93,7 @@ hn_status hn_tune_cache_store(const char* path, const char* gpu, int L, int prec
   {
     std::ostringstream os;
     os << t->tail_level << ' ' << t->cluster << ' ' << t->pdl << ' ' << t->staged << ' ' << t->dsm << ' '
-       << t->fuse_up << ' ' << t->mid;
+       << t->fuse_up << ' ' << t->mid << ' ' << t->sweep;
     probe = os.str();
   }
   hn_tuning check;

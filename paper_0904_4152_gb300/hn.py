@@ -82,7 +82,7 @@ class ServerInfo(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("tail_level", ctypes.c_int), ("cluster", ctypes.c_int), ("pdl", ctypes.c_int),
                 ("staged", ctypes.c_int), ("dsm", ctypes.c_int), ("fuse_up", ctypes.c_int),
-                ("mid", ctypes.c_int)]
+                ("mid", ctypes.c_int), ("sweep", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -383,32 +383,35 @@ def hn_mg_kernel_times(mg, max_entries=256):
             for i in range(n)]
 
 
-def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0, dsm=1, fuse_up=0, mid=0):
-    _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl, staged, dsm, fuse_up, mid))))
+def hn_mg_set_tuning(mg, tail_level, cluster, pdl=2, staged=0, dsm=1, fuse_up=0, mid=0, sweep=0):
+    _check(lib().hn_mg_set_tuning(mg, ctypes.byref(Tuning(tail_level, cluster, pdl, staged, dsm, fuse_up, mid,
+                                                          sweep))))
 
 
 def hn_mg_get_tuning(mg):
     t = Tuning()
     _check(lib().hn_mg_get_tuning(mg, ctypes.byref(t)))
-    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm, t.fuse_up, t.mid
+    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm, t.fuse_up, t.mid, t.sweep
 
 
 def hn_mg_autotune(mg, b, reps=3, coarse_L=2):
-    """Time every launch shape on this hierarchy, keep the fastest; returns (best, {shape: ms})."""
+    """Time every launch shape on this hierarchy, keep the fastest; returns (best, {shape: ms}),
+    shapes as (tail_level, cluster, mid, sweep)."""
     b = np.ascontiguousarray(b, dtype=np.float64)
-    cap = 2 * 5 * 16
+    cap = 3 * 5 * 16
     times = np.full(cap, np.nan)
     best = Tuning()
     _check(lib().hn_mg_autotune(mg, _host_ptr(b, np.float64), reps, ctypes.byref(best),
                                 times.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cap))
     clusters = (1, 2, 4, 8, 16)
-    rows = int(np.count_nonzero(~np.isnan(times))) // 10     # tail levels per mid setting
+    modes = ((0, 0), (10, 0), (0, 1))                        # (mid, sweep) of the three forms
+    rows = int(np.count_nonzero(~np.isnan(times))) // 15     # tail levels per form
     table = {}
     for i, v in enumerate(times):
         if not np.isnan(v):
             mi, k = divmod(i, 5 * rows)
-            table[(coarse_L + k // 5, clusters[k % 5], (0, 10)[mi])] = float(v)
-    return (best.tail_level, best.cluster, best.mid), table
+            table[(coarse_L + k // 5, clusters[k % 5]) + modes[mi]] = float(v)
+    return (best.tail_level, best.cluster, best.mid, best.sweep), table
 
 
 def hn_mg_autotune_batch(mgs, bs, reps=2):
@@ -430,7 +433,8 @@ def hn_mg_time_kernel(mg, op, level, reps=20):
 
 
 def hn_tune_cache_store(path, gpu, L, prec, solver, coarse_solver, coarse_L, shape):
-    """Store a launch shape (7-tuple as hn_mg_get_tuning returns) in the cache file `path`."""
+    """Store a launch shape (as hn_mg_get_tuning returns it; a 7-tuple has sweep 0) in the cache
+    file `path`."""
     _check(lib().hn_tune_cache_store(path.encode(), gpu.encode(), L, prec, solver, coarse_solver,
                                      coarse_L, ctypes.byref(Tuning(*shape))))
 
@@ -443,7 +447,7 @@ def hn_tune_cache_lookup(path, gpu, L, prec, solver, coarse_solver, coarse_L):
     if st == HN_ERR_STATE:
         return None
     _check(st)
-    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm, t.fuse_up, t.mid
+    return t.tail_level, t.cluster, t.pdl, t.staged, t.dsm, t.fuse_up, t.mid, t.sweep
 
 
 class FpRates(ctypes.Structure):

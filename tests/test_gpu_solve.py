@@ -337,15 +337,20 @@ def test_profiling_times_kernels_without_changing_results(hn):
     try:
         x0, _, _ = hn.hn_mg_solve(mg, L, b)
         tail = hn.hn_mg_get_tuning(mg)[0]
-        # levels above the tail in the persistent kernels, then as one launch per step
-        for mid, want in ((10, {"mid_down", "mid_up", "tail", "outer_defect"}),
-                          (0, {"jacobi", "defect", "restrict", "prolong", "tail", "outer_defect"})):
-            hn.hn_mg_set_tuning(mg, tail, 16, 2, 0, 1, 0, mid)
+        # levels above the tail in the persistent kernels, as one launch per step, in fused sweeps
+        # (the finest level's first smoothing step, its prolongation and post-smoothing apart)
+        for mid, sweep, want in ((10, 0, {"mid_down", "mid_up", "tail", "outer_defect"}),
+                                 (0, 0, {"jacobi", "defect", "restrict", "prolong", "tail", "outer_defect"}),
+                                 (0, 1, {"jacobi_first", "sweep_down", "sweep_up", "prolong", "jacobi",
+                                         "tail", "outer_defect"})):
+            hn.hn_mg_set_tuning(mg, tail, 16, 2, 0, 1, 0, mid, sweep)
             hn.hn_mg_set_profiling(mg, True)
             x1, _, _ = hn.hn_mg_solve(mg, L, b)
             times = hn.hn_mg_kernel_times(mg)
             names = {t["name"] for t in times}
-            assert want <= names, (mid, names)
+            assert want <= names, (mid, sweep, names)
+            if sweep:
+                assert not {"defect", "restrict"} & names, names
             assert all(t["total_ms"] > 0 for t in times)
             np.testing.assert_array_equal(x0, x1)
             hn.hn_mg_set_profiling(mg, False)
@@ -353,10 +358,10 @@ def test_profiling_times_kernels_without_changing_results(hn):
         hn.hn_mg_destroy(mg)
 
 
-@pytest.mark.parametrize("mid", [0, 10])
+@pytest.mark.parametrize("mid,sweep", [(0, 0), (10, 0), (0, 1)])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("L", [6, 9])
-def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L, mid):
+def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L, mid, sweep):
     # the one-launch solve of the defect correction skips, through an IF node, the rest of a V
     # cycle after a lagged check that ends the inner solve (a check on a level run by one launch
     # per step; the persistent kernels take their checks inside and skip the rest themselves);
@@ -367,7 +372,7 @@ def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L, mid)
     hn.hn_band_destroy(A)
     try:
         tail = hn.hn_mg_get_tuning(mg)[0]
-        hn.hn_mg_set_tuning(mg, tail, 16, 2, 0, 1, 0, mid)
+        hn.hn_mg_set_tuning(mg, tail, 16, 2, 0, 1, 0, mid, sweep)
         x0, st0, s0 = hn.hn_mg_solve(mg, L, b)
         n_loop = hn.hn_mg_last_launches(mg)
         hn.hn_mg_set_profiling(mg, True)
@@ -400,17 +405,24 @@ def test_launch_shapes_do_not_change_results(hn, prec):
     hn.hn_band_destroy(A)
     try:
         ref, st0, _ = hn.hn_mg_solve(mg, L, b)
-        for shape in [(2, 1, 0, 0, 1, 1, 0), (4, 2, 0, 1, 1, 0, 0), (5, 16, 1, 0, 0, 1, 0), (7, 8, 2, 1, 1, 1, 0),
-                      (7, 16, 2, 0, 0, 0, 0), (7, 16, 2, 0, 1, 0, 0), (6, 4, 2, 0, 1, 1, 0), (8, 16, 1, 1, 1, 0, 0),
-                      (7, 16, 2, 0, 1, 1, 0), (7, 16, 2, 0, 1, 0, 10), (7, 16, 2, 0, 1, 0, 9), (7, 16, 2, 0, 1, 0, 8),
-                      (5, 16, 2, 0, 1, 0, 10), (2, 1, 2, 0, 1, 0, 10), (6, 4, 0, 0, 0, 0, 10), (9, 16, 2, 0, 1, 0, 10)]:
+        shapes = [(2, 1, 0, 0, 1, 1, 0), (4, 2, 0, 1, 1, 0, 0), (5, 16, 1, 0, 0, 1, 0), (7, 8, 2, 1, 1, 1, 0),
+                  (7, 16, 2, 0, 0, 0, 0), (7, 16, 2, 0, 1, 0, 0), (6, 4, 2, 0, 1, 1, 0), (8, 16, 1, 1, 1, 0, 0),
+                  (7, 16, 2, 0, 1, 1, 0), (7, 16, 2, 0, 1, 0, 10), (7, 16, 2, 0, 1, 0, 9), (7, 16, 2, 0, 1, 0, 8),
+                  (5, 16, 2, 0, 1, 0, 10), (2, 1, 2, 0, 1, 0, 10), (6, 4, 0, 0, 0, 0, 10), (9, 16, 2, 0, 1, 0, 10)]
+        shapes = [s + (0,) for s in shapes]
+        # the fused level sweeps: every level between the tail and the finest, with or without the
+        # prolongation fused into the finest level's first post-smoothing step, without PDL
+        shapes += [(7, 16, 2, 0, 1, 0, 0, 1), (2, 1, 2, 0, 1, 0, 0, 1), (5, 16, 2, 0, 1, 0, 0, 1),
+                   (6, 4, 2, 0, 1, 1, 0, 1), (8, 16, 1, 0, 1, 0, 0, 1), (9, 16, 2, 0, 1, 0, 0, 1),
+                   (7, 16, 0, 0, 0, 0, 0, 1), (4, 2, 3, 0, 1, 0, 0, 1)]
+        for shape in shapes:
             hn.hn_mg_set_tuning(mg, *shape)
             assert hn.hn_mg_get_tuning(mg) == shape
             x, st, _ = hn.hn_mg_solve(mg, L, b)
             np.testing.assert_array_equal(x, ref)
             assert st["cycles"] == st0["cycles"]
         best, table = hn.hn_mg_autotune(mg, b, reps=1)
-        assert best in table and len(table) == 2 * 5 * 8
+        assert best in table and len(table) == 3 * 5 * 8
         x, _, _ = hn.hn_mg_solve(mg, L, b)
         np.testing.assert_array_equal(x, ref)
     finally:
@@ -474,7 +486,7 @@ def test_autotuned_shape_persists_through_the_cache_file(hn, tmp_path, monkeypat
         default64 = hn.hn_mg_get_tuning(mgs[1])
         best, table = hn.hn_mg_autotune(mgs[0], b, reps=1)
         tuned = hn.hn_mg_get_tuning(mgs[0])
-        assert best == (tuned[0], tuned[1], tuned[6]) and len(open(path).read().splitlines()) == 1
+        assert best == (tuned[0], tuned[1], tuned[6], tuned[7]) and len(open(path).read().splitlines()) == 1
         mgs.append(hn.hn_mg_setup(A, prec=1))
         assert hn.hn_mg_get_tuning(mgs[2]) == tuned
         mgs.append(hn.hn_mg_setup(A, prec=0))                    # another key: untouched
