@@ -37,14 +37,15 @@ typedef struct {
                        <= tail_level: none); not combined with staged or fuse_up, which are forms
                        of the per-step launches (default 0: on this part a grid barrier plus the
                        memory latency of a step costs as much as a kernel boundary) */
-  int sweep;        /* 1: a hierarchy solved alone with V(2,2) cycles runs the down part of each
-                       level above tail_level (both pre-smoothing steps, the defect and the
-                       restriction; on the finest level the steps after the first) and the up part
-                       of each level between tail_level and the finest (the prolongation and both
-                       post-smoothing steps) as one launch each, over 2-D tiles whose blocks
-                       recompute the halos they need instead of waiting for one another; 0: one
-                       launch per step.  Not combined with staged or mid; without effect in
-                       batches and in the server */
+  int sweep;        /* 1 (default): a hierarchy solved alone with V(2,2) cycles runs the down
+                       part of each level between tail_level and the finest, up to level 9 (both
+                       pre-smoothing steps, the defect and the restriction), and the up part (the
+                       prolongation and both post-smoothing steps) as one launch each, over 2-D
+                       tiles whose blocks recompute the halos they need instead of waiting for one
+                       another; 2: every level above tail_level and, on the finest level, the steps
+                       after the first smoothing step (the second step, the defect, the
+                       restriction) in one launch; 0: one launch per step.  Not combined with
+                       staged or mid; without effect in batches and in the server */
 } hn_tuning;
 
 /* Set / read the launch shape used by mg's later solves.  HN_ERR_ARG on values out of range. */

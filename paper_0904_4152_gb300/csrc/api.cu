@@ -478,7 +478,7 @@ hn_status hn_mg_set_tuning(hn_mg* mg, const hn_tuning* t) {
   if (t->dsm != 0 && t->dsm != 1) return set_error(HN_ERR_ARG, "dsm must be 0 or 1");
   if (t->fuse_up != 0 && t->fuse_up != 1) return set_error(HN_ERR_ARG, "fuse_up must be 0 or 1");
   if (t->mid < 0 || t->mid > HN_MAX_LEVEL) return set_error(HN_ERR_ARG, "mid must be in [0, %d]", HN_MAX_LEVEL);
-  if (t->sweep != 0 && t->sweep != 1) return set_error(HN_ERR_ARG, "sweep must be 0 or 1");
+  if (t->sweep < 0 || t->sweep > 2) return set_error(HN_ERR_ARG, "sweep must be 0, 1 or 2");
   Tuning tu;
   tu.tail_level = t->tail_level;
   tu.cluster = c;

@@ -888,6 +888,16 @@ bool Engine::sweep_on() const {
   return tune_.sweep && cap_ == 1 && prm_.pre == 2 && prm_.post == 2 && !tune_.staged && mid_top() <= T;
 }
 
+// Levels in fused sweeps.  sweep 1: the levels below the finest up to kSweepMaxLevel, where a step
+// is bound by latency (a sweep's tile takes several dependent phases, each about one memory
+// latency; larger levels stream enough data that the halo re-reads cost more than the launches
+// saved: measured at L = 10..12).  sweep 2: every level above the tail, the finest one's down part
+// included.
+bool Engine::sweep_level(int l) const {
+  if (!sweep_on()) return false;
+  return tune_.sweep == 2 || (!is_top(l) && l <= kSweepMaxLevel);
+}
+
 hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
   const int c = prm_.coarse, pre = prm_.pre, post = prm_.post;
   const int T = std::max(tune_.tail_level, c);
@@ -903,11 +913,10 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
     return HN_OK;
   };
   const int M = mid_top();                 // levels T+1..M: the persistent kernels
-  const bool sweep = sweep_on();
   for (int l = Lmax_; l > std::max(T, M); --l) {
     // a finest level: lagged check (the PCG preconditioner's cycle has none)
-    const bool top = prm_.solver != SOLVER_PCG && (topMaskAll_ || ((topMask_ >> l) & 1u));
-    if (sweep && !top) {
+    const bool top = prm_.solver != SOLVER_PCG && is_top(l);
+    if (sweep_level(l) && !top) {
       // a zero iterate: both smoothing steps, the defect and the restriction in one launch
       HN_LAUNCH(KC_SWEEP_DOWN, l, launch_sweep_down(E_, lists_[l], l, want, 0, s));
       continue;
@@ -921,7 +930,7 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
         if (!fuse) HN_LAUNCH(KC_CONTROL, l, launch_control(E_, CTRL_PRE, s, l));
         HN_TRY(after_check());
       }
-      if (sweep) {
+      if (sweep_level(l)) {
         // the second step, the defect and the restriction in one launch
         HN_LAUNCH(KC_SWEEP_DOWN, l, launch_sweep_down(E_, lists_[l], l, want, 1, s));
         continue;
@@ -945,8 +954,9 @@ hn_status Engine::issue_vcycle(cudaStream_t s0, int want) {
   if (M > T) HN_LAUNCH(KC_MID_UP, M, launch_mid(E_, dLists_, M, T, want, 1, s));
   int e_sel = 0;                           // buffer of the coarse iterate (the tail's: 0)
   for (int l = std::max(T, M) + 1; l <= Lmax_; ++l) {
-    if (sweep && l < Lmax_) {
-      // prolongation and both post-smoothing steps in one launch; the result in buffer 1
+    if (sweep_level(l) && !is_top(l)) {
+      // prolongation and both post-smoothing steps in one launch; the result in buffer 1 (a
+      // problem's own finest level keeps its iterate in buffer 0)
       HN_LAUNCH(KC_SWEEP_UP, l, launch_sweep_up(E_, lists_[l], l, want, e_sel, s));
       e_sel = 1;
       continue;

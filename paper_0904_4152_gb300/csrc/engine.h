@@ -75,6 +75,8 @@ enum KClass {
 
 // launch shape of the schedule: levels <= tail_level run fused in one cluster launch of
 // `cluster` blocks per problem; levels above run as one launch per step
+constexpr int kSweepMaxLevel = 9;   // largest level in fused sweeps under tuning sweep 1
+
 struct Tuning {
   int tail_level = 7;
   int cluster = 16;
@@ -89,10 +91,13 @@ struct Tuning {
                     // kernels (default: a grid barrier plus the memory latency of a step measured
                     // as long as a kernel boundary, ~3.5 us at L = 10, so they did not pay).
                     // Not combined with staged or fuse_up, which are per-step forms.
-  int sweep = 0;    // an engine of one problem with V(2,2) cycles: the down part of each level
-                    // above the tail (smoothing, defect, restriction) and the up part of each
-                    // level below the finest (prolongation, smoothing) as one launch each over
-                    // 2-D tiles with recomputed halos (k_sweep_down / k_sweep_up)
+  int sweep = 1;    // an engine of one problem with V(2,2) cycles: the down part of each level
+                    // between the tail and the finest, up to kSweepMaxLevel (smoothing, defect,
+                    // restriction), and the up part (prolongation, smoothing) as one launch each
+                    // over 2-D tiles with recomputed halos (k_sweep_down / k_sweep_up); 2: every
+                    // level above the tail, with the finest level's steps after its first smoothing
+                    // step.  Default 1 (measured at L = 9 / 10 / 12: FP32-inner DC -3.6 / -1.0 /
+                    // -0.4 %, FP64 MG -11.5 / -2.3 / -0.3 %); 2 was slower from L = 10 up.
 };
 
 class Engine;
@@ -252,6 +257,9 @@ class Engine {
   unsigned long long* dBar_ = nullptr;   // grid barriers of the persistent kernels
   int mid_top() const;              // top level of the persistent kernels (<= tail level: none)
   bool sweep_on() const;            // the fused level sweeps run (tuning sweep, and they apply)
+  bool sweep_level(int l) const;    // level l's down / up parts run as fused sweeps
+  // level l may be a member's own finest level (the server's engines: any level)
+  bool is_top(int l) const { return topMaskAll_ || ((topMask_ >> l) & 1u); }
   int fineGrid_ = 1;
   int maxGrid_ = 1;
   std::vector<hn_mg*> members_;

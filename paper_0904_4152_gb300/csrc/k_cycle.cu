@@ -1377,15 +1377,25 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
-// Block-wide copy of `bytes` (a multiple of 16; both ends 16-byte aligned) from global to shared
-// memory by cp.async, each thread taking every blockDim.x-th 16-byte chunk; a thread waits for its
-// own chunks with cp_async_wait(), then the block synchronizes.  (Issued by all threads at once,
-// the fused tail's many small constant arrays land within a microsecond or two; one thread issuing
-// one bulk copy per array took ~1.5 us per level.)
-__device__ __forceinline__ void block_copy16(void* dst, const void* src, long long bytes) {
-  const int chunks = (int)(bytes / 16);
-  for (int q = threadIdx.x; q < chunks; q += blockDim.x)
-    cp_async16(static_cast<uint4*>(dst) + q, static_cast<const uint4*>(src) + q);
+// Copy of `bytes` (a multiple of 16; both ends 16-byte aligned) from global to this block's
+// shared memory as one bulk copy (the TMA engine) issued by thread 0 and accounted on the mbarrier
+// `bar`, whose phase completes once thread 0 has arrived and every byte has landed.  (The fused
+// tail's constant data are ~40 arrays, ~70 KB in block 0: issued as 16-byte cp.async by every
+// thread the copies took ~5 us, bound by the requests one SM keeps in flight.)  The copies ask L2
+// to keep the lines (evict-last): the tail reads the same constant data (~2 MB) once per cycle,
+// between which the finer levels stream tens of MB through L2.
+__device__ __forceinline__ void block_copy16(void* dst, const void* src, long long bytes,
+                                             unsigned long long* bar) {
+  if (threadIdx.x != 0 || bytes <= 0) return;
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(bar)), "r"((unsigned)bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
+          (unsigned)__cvta_generic_to_shared(dst)),
+      "l"(src), "r"((unsigned)bytes), "r"((unsigned)__cvta_generic_to_shared(bar)), "l"(pol)
+      : "memory");
 }
 
 // shared-memory bytes of levels coarse..S for a precision (16-byte aligned pieces)
@@ -1401,13 +1411,12 @@ __host__ __device__ inline long long smem_level_bytes(int l, int prec) {
 }
 
 // carve level l of the shared-memory hierarchy starting at *off; with `fill`, start the copies of
-// its bands and omega/D (block_copy16) and zero its vectors.  The caller waits for its copies
-// (cp_async_wait) and synchronizes the block before use.  Every block of a cluster carves
+// its bands and omega/D (block_copy16, on the mbarrier bar) and zero its vectors.  The caller
+// waits for the copies (the mbarrier phase) and synchronizes the block before use.  Every block of a cluster carves
 // the same layout, so a block can address block 0's copy through distributed shared memory.
 template <class Pol>
 __device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* base, long long* off,
                                  int l, bool fill, unsigned long long* bar) {
-  (void)bar;
   using V = typename Pol::V;
   using B = typename Pol::B;
   const long long halo = (((1LL << l) + 1 + 8) + 31) / 32 * 32;
@@ -1418,16 +1427,16 @@ __device__ void smem_level_setup(const LevelDev& g, LevelDev& s, unsigned char* 
   for (int k = 0; k < 9; ++k) {
     B* dst = reinterpret_cast<B*>(take(e * sizeof(B)));
     const B* src = static_cast<const B*>(g.band[k]) - halo;
-    if (fill) block_copy16(dst, src, e * (long long)sizeof(B));
+    if (fill) block_copy16(dst, src, e * (long long)sizeof(B), bar);
     t.band[k] = dst + halo;
   }
   if constexpr (Pol::prec == P64) {
     double* dst = reinterpret_cast<double*>(take(e * 8));
-    if (fill) block_copy16(dst, g.wdinv - halo, e * 8);
+    if (fill) block_copy16(dst, g.wdinv - halo, e * 8, bar);
     t.wdinv = dst + halo;
   } else {
     float* dst = reinterpret_cast<float*>(take(e * 4));
-    if (fill) block_copy16(dst, g.wdf - halo, e * 4);
+    if (fill) block_copy16(dst, g.wdf - halo, e * 4, bar);
     t.wdf = dst + halo;
   }
   V* vec[4];
@@ -1708,7 +1717,7 @@ __device__ void dsm_level_setup(const LevelDev& g, LevelDev& v, unsigned char* b
   for (int k = 0; k < 9; ++k) {
     B* dst = reinterpret_cast<B*>(take(nb * sizeof(B)));
     const B* src = static_cast<const B*>(g.band[k]) + g0b;
-    block_copy16(dst, src, (long long)bchunks * 16);
+    block_copy16(dst, src, (long long)bchunks * 16, bar);
     t.band[k] = dst - g0b;
   }
   const int vchunks = (int)((R1n + n + 1 - g0v + av - 1) / av);
@@ -1717,7 +1726,7 @@ __device__ void dsm_level_setup(const LevelDev& g, LevelDev& v, unsigned char* b
     const V* src;
     if constexpr (Pol::prec == P64) src = g.wdinv + g0v;
     else src = g.wdf + g0v;
-    block_copy16(dst, src, (long long)vchunks * 16);
+    block_copy16(dst, src, (long long)vchunks * 16, bar);
     if constexpr (Pol::prec == P64) t.wdinv = dst - g0v;
     else t.wdf = dst - g0v;
   }
@@ -1960,7 +1969,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
       off += ((long long)2 * Nc * 8 + 15) / 16 * 16;
     }
     if (rank == 0) {
-      if (staged) block_copy16(dst, P.cinv, (words / 2) * 16);
+      if (staged) block_copy16(dst, P.cinv, (words / 2) * 16, &s_bar);
       if (threadIdx.x == 0) {
         if (staged && (words & 1)) dst[words - 1] = __ldg(P.cinv + words - 1);
         s_cinv = staged ? dst : P.cinv;
@@ -2144,7 +2153,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
 // asynchronous copies (cp.async, zero-filled off the grid) that all its threads issue before one
 // wait: one memory latency per tile.  The up sweep writes its result to buffer 1 (the halos of
 // other blocks still read buffer 0); the next finer level's prolongation reads it there.
-constexpr int kSweepCX = 16, kSweepCY = 8;       // coarse nodes per tile (largest)
+constexpr int kSweepCX = 16, kSweepCY = 16;      // coarse nodes per tile (largest)
 // threads per tile: about one node of the widest region each, so that a tile's chain of dependent
 // steps is short (a tile is latency-bound: 256 threads took ~10 us per tile at L = 8)
 constexpr int kSweepThreads = 1024;
@@ -2267,11 +2276,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_down(EngineDev E, TileL
   if (st.phase != want) return;
   const LevelDev& g = tl.solo_d;
   const LevelDev& gc = tl.solo_c;
-  if (gc.n == 0) return;                          // (no coarser level)
+  if (tl.solo_tiles == 0 || gc.n == 0) return;    // (a level the problem does not have, or no coarser)
   if (!dbg_level(E, g, level, tl.solo_tiles, __LINE__) || !dbg_level(E, gc, level - 1, 0, __LINE__) ||
       !sweep_geom_ok(E, sg, gc.n, __LINE__))
     return;
-  const int mode = !top ? 0 : (st.zero_top ? 2 : 1);
+  // below the problem's own finest level the iterate starts at zero whatever the launch says (an
+  // engine whose graphs serve any member level launches every level as a possible top)
+  const int mode = (!top || tl.solo_L > level) ? 0 : (st.zero_top ? 2 : 1);
   LevelDev t;
   V* es;
   sweep_carve<Pol>(t, g, smem, sg, &es);
@@ -2354,7 +2365,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_up(EngineDev E, TileLis
   if (st.phase != want) return;
   const LevelDev& g = tl.solo_d;
   const LevelDev& gc = tl.solo_c;
-  if (gc.n == 0) return;
+  if (tl.solo_tiles == 0 || gc.n == 0) return;
   if (!dbg_level(E, g, level, tl.solo_tiles, __LINE__) || !dbg_level(E, gc, level - 1, 0, __LINE__) ||
       !sweep_geom_ok(E, sg, gc.n, __LINE__))
     return;
@@ -3471,8 +3482,10 @@ cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want,
 SweepGeom sweep_geom(int level) {
   const int h = 1 << (level - 1);                 // coarse intervals per side
   SweepGeom g;
+  // 16 x 16 coarse nodes from 256 coarse intervals per side up (L = 9: 256 tiles, one wave of two
+  // blocks per SM), 16 x 8 below (L = 8: 128 tiles)
   g.cx = std::min(kSweepCX, h);
-  g.cy = std::min(kSweepCY, h);
+  g.cy = std::min(h >= 256 ? kSweepCY : kSweepCY / 2, h);
   g.tx = h / g.cx;
   g.ty = h / g.cy;
   g.P = 2 * g.cx + 7;

@@ -57,7 +57,7 @@ bool parse_shape(const std::string& rest, hn_tuning* t) {
   const int c = v.cluster;
   if (v.tail_level < HN_MIN_LEVEL || v.tail_level > HN_MAX_LEVEL || !(c == 1 || c == 2 || c == 4 || c == 8 || c == 16) ||
       v.pdl < 0 || v.pdl > 3 || (v.staged != 0 && v.staged != 1) || (v.dsm != 0 && v.dsm != 1) ||
-      (v.fuse_up != 0 && v.fuse_up != 1) || v.mid < 0 || v.mid > HN_MAX_LEVEL || (v.sweep != 0 && v.sweep != 1))
+      (v.fuse_up != 0 && v.fuse_up != 1) || v.mid < 0 || v.mid > HN_MAX_LEVEL || v.sweep < 0 || v.sweep > 2)
     return false;
   *t = v;
   return true;

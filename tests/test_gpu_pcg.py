@@ -118,7 +118,8 @@ def test_pcg_launch_shapes_and_host_iterations(hn, prec):
         for shape in [(2, 1, 0, 0, 1, 1), (5, 16, 1, 0, 0, 0), (7, 8, 2, 1, 1, 1), (6, 16, 2, 0, 1, 0),
                       (8, 16, 1, 1, 1, 1),
                       (7, 16, 2, 0, 1, 0, 0), (4, 16, 2, 0, 1, 0, 10),
-                      (7, 16, 2, 0, 1, 0, 0, 1), (4, 16, 2, 0, 1, 0, 0, 1), (6, 4, 2, 0, 1, 1, 0, 1)]:
+                      (7, 16, 2, 0, 1, 0, 0, 1), (4, 16, 2, 0, 1, 0, 0, 1), (6, 4, 2, 0, 1, 1, 0, 2),
+                      (5, 16, 2, 0, 1, 0, 0, 2)]:
             hn.hn_mg_set_tuning(mg, *shape)
             x, st, _ = hn.hn_mg_solve(mg, L, b)
             np.testing.assert_array_equal(x, ref)

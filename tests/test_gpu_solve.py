@@ -341,7 +341,9 @@ def test_profiling_times_kernels_without_changing_results(hn):
         # (the finest level's first smoothing step, its prolongation and post-smoothing apart)
         for mid, sweep, want in ((10, 0, {"mid_down", "mid_up", "tail", "outer_defect"}),
                                  (0, 0, {"jacobi", "defect", "restrict", "prolong", "tail", "outer_defect"}),
-                                 (0, 1, {"jacobi_first", "sweep_down", "sweep_up", "prolong", "jacobi",
+                                 (0, 1, {"jacobi_first", "jacobi", "defect", "restrict", "sweep_down",
+                                         "sweep_up", "prolong", "tail", "outer_defect"}),
+                                 (0, 2, {"jacobi_first", "sweep_down", "sweep_up", "prolong", "jacobi",
                                          "tail", "outer_defect"})):
             hn.hn_mg_set_tuning(mg, tail, 16, 2, 0, 1, 0, mid, sweep)
             hn.hn_mg_set_profiling(mg, True)
@@ -349,7 +351,7 @@ def test_profiling_times_kernels_without_changing_results(hn):
             times = hn.hn_mg_kernel_times(mg)
             names = {t["name"] for t in times}
             assert want <= names, (mid, sweep, names)
-            if sweep:
+            if sweep == 2:
                 assert not {"defect", "restrict"} & names, names
             assert all(t["total_ms"] > 0 for t in times)
             np.testing.assert_array_equal(x0, x1)
@@ -358,7 +360,7 @@ def test_profiling_times_kernels_without_changing_results(hn):
         hn.hn_mg_destroy(mg)
 
 
-@pytest.mark.parametrize("mid,sweep", [(0, 0), (10, 0), (0, 1)])
+@pytest.mark.parametrize("mid,sweep", [(0, 0), (10, 0), (0, 1), (0, 2)])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("L", [6, 9])
 def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L, mid, sweep):
@@ -410,11 +412,14 @@ def test_launch_shapes_do_not_change_results(hn, prec):
                   (7, 16, 2, 0, 1, 1, 0), (7, 16, 2, 0, 1, 0, 10), (7, 16, 2, 0, 1, 0, 9), (7, 16, 2, 0, 1, 0, 8),
                   (5, 16, 2, 0, 1, 0, 10), (2, 1, 2, 0, 1, 0, 10), (6, 4, 0, 0, 0, 0, 10), (9, 16, 2, 0, 1, 0, 10)]
         shapes = [s + (0,) for s in shapes]
-        # the fused level sweeps: every level between the tail and the finest, with or without the
-        # prolongation fused into the finest level's first post-smoothing step, without PDL
+        # the fused level sweeps: every level between the tail and the finest (1; 2: and the
+        # finest level's down part), with or without the prolongation fused into the finest
+        # level's first post-smoothing step, without PDL
         shapes += [(7, 16, 2, 0, 1, 0, 0, 1), (2, 1, 2, 0, 1, 0, 0, 1), (5, 16, 2, 0, 1, 0, 0, 1),
                    (6, 4, 2, 0, 1, 1, 0, 1), (8, 16, 1, 0, 1, 0, 0, 1), (9, 16, 2, 0, 1, 0, 0, 1),
-                   (7, 16, 0, 0, 0, 0, 0, 1), (4, 2, 3, 0, 1, 0, 0, 1)]
+                   (7, 16, 0, 0, 0, 0, 0, 1), (4, 2, 3, 0, 1, 0, 0, 1),
+                   (7, 16, 2, 0, 1, 0, 0, 2), (5, 16, 2, 0, 1, 0, 0, 2), (6, 4, 2, 0, 1, 1, 0, 2),
+                   (9, 16, 2, 0, 1, 0, 0, 2)]
         for shape in shapes:
             hn.hn_mg_set_tuning(mg, *shape)
             assert hn.hn_mg_get_tuning(mg) == shape

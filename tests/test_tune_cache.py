@@ -47,7 +47,7 @@ def test_malformed_and_out_of_range_lines_are_ignored(hn, tmp_path):
                     "GPU|10|1|0|0|2 7 16 2 0 1 0 0 1\n"
                     "GPU|10|1|0|0|2 7 3 2 0 1 0 0 0\n"          # cluster 3: out of range
                     "GPU|11|1|0|0|2 7 16\n"                      # too few fields
-                    "GPU|12|1|0|0|2 7 16 2 0 1 0 0 2\n"          # sweep 2: out of range
+                    "GPU|12|1|0|0|2 7 16 2 0 1 0 0 3\n"          # sweep 3: out of range
                     "GPU|13|1|0|0|2 7 16 2 0 1 0 0 1 5\n"        # a field too many
                     "GPU|14|1|0|0|2 7 16 2 0 1 0 0 x\n"          # not a number
                     "GPU|15|1|0|0|2 6 8 2 0 1 0 0\n"             # no sweep field: sweep 0
