@@ -1010,6 +1010,17 @@ hn_status Engine::issue_iteration(cudaStream_t s0, cudaGraphConditionalHandle h,
     HN_LAUNCH(KC_CONTROL, -1, launch_control(E_, CTRL_OUTER, s));
   } else if (prm_.prec == P64) {
     HN_TRY(issue_vcycle(s, PH_CYCLE));
+  } else if (fuse_control()) {
+    // an engine of one problem: the outer control step inside the outer defect, the control step
+    // after the update and the iteration's summary inside the update (their last blocks)
+    HN_LAUNCH(KC_OUTER_DEFECT, -1, launch_outer_defect(E_, fine_, fineGrid_, s, 1));
+    HN_TRY(issue_vcycle(s, PH_INNER));
+    HN_LAUNCH(KC_UPDATE, -1, launch_update(E_, fine_, fineGrid_, s, 1, h, use_h));
+    if (condCapture_) {
+      const CondDev& cd = E_.prm.cond;
+      E_.prm.cond.n_base = (unsigned)(counting_ - start) - cd.n_cycle - cd.n_outer - cd.n_update;
+    }
+    return HN_OK;
   } else {
     if (cond_on(1)) HN_TRY(open_if(s, 1));
     int c0 = counting_;
@@ -1035,6 +1046,14 @@ hn_status Engine::issue_iteration(cudaStream_t s0, cudaGraphConditionalHandle h,
   }
   HN_LAUNCH0(launch_summary(E_, h, use_h, 1, s));
   return HN_OK;
+}
+
+// The defect correction of an engine of one problem folds its control steps and the iteration
+// summary into the outer defect and the update when the fine norm is one group of partials (one
+// block sums it) and neither step has an IF node of its own.
+bool Engine::fuse_control() const {
+  return cap_ == 1 && prm_.solver != SOLVER_PCG && prm_.prec != P64 && !cond_on(1) && !cond_on(2) &&
+         pitch_of(Lmax_) / kTile <= kSumGroup;
 }
 
 hn_status Engine::capture_graphs() {

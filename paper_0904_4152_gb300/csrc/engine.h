@@ -258,6 +258,7 @@ class Engine {
   int mid_top() const;              // top level of the persistent kernels (<= tail level: none)
   bool sweep_on() const;            // the fused level sweeps run (tuning sweep, and they apply)
   bool sweep_level(int l) const;    // level l's down / up parts run as fused sweeps
+  bool fuse_control() const;        // the DC control steps fold into the outer defect and update
   // level l may be a member's own finest level (the server's engines: any level)
   bool is_top(int l) const { return topMaskAll_ || ((topMask_ >> l) & 1u); }
   int fineGrid_ = 1;

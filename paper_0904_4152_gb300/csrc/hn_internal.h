@@ -260,7 +260,10 @@ cudaError_t launch_prolong(const EngineDev& E, TileList tl, int level, int want,
 cudaError_t launch_prolong_jacobi(const EngineDev& E, TileList tl, int level, int want, int x_sel,
                                   int grid, cudaStream_t s);
 cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, cudaStream_t s);
-cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+// fuse: an engine of one problem whose fine norm is one group of partials takes the outer control
+// step in the last block of the outer defect, and the control step after the update plus the
+// end-of-iteration summary (WHILE handle h if use_handle) in the last block of the update
+cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse = 0);
 // PCG vector steps on each problem's finest level (FP64): q = A p with partials (p, q); x += alpha
 // p, r -= alpha q with partials ||r||^2 and the scaled residual as the cycle's right-hand side;
 // partials (r, z); p = z / s + beta p
@@ -268,7 +271,8 @@ cudaError_t launch_pcg_q(const EngineDev& E, TileList fine, int grid, cudaStream
 cudaError_t launch_pcg_x(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
 cudaError_t launch_pcg_dot(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
 cudaError_t launch_pcg_p(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
-cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse = 0,
+                          cudaGraphConditionalHandle h = 0, int use_handle = 0);
 cudaError_t launch_norm_b(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
 // kind: ControlKind; level: for CTRL_PRE, the finest level whose problems are checked
 cudaError_t launch_control(const EngineDev& E, int kind, cudaStream_t s, int level = -1);

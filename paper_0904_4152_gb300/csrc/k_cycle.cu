@@ -1069,6 +1069,24 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // finish sums the tile partials in the fixed order and updates the state, and the cycle's IF value
 // is set as the control kernel sets it (the problem is still in the cycle).  A uniform early
 // return of every block (problem not in the phase) leaves the ticket at zero.
+__device__ void control_apply(const EngineDev& E, ProbState& st, int kind, double sum);
+__device__ void summary_apply(const EngineDev& E, cudaGraphConditionalHandle h, int use_handle,
+                              int end_of_iteration, double* sh);
+
+// true in the last block of the launch to get here (every block calls it once, after its work;
+// the block's writes are visible to that block); the last block resets the ticket when done
+__device__ bool solo_last_block(const EngineDev& E) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(E.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
 __device__ void solo_fused_check(const EngineDev& E, int level, bool checked, int want) {
   __shared__ double sh[32];
   __shared__ int s_last;
@@ -2761,7 +2779,10 @@ __global__ void __launch_bounds__(mid_threads<Pol>(), 1) k_mid_up(EngineDev E, c
 // inner top-level right-hand side as V(d * s); partial[g] = sum d^2.  x = 0 gives d = b.  PCG:
 // the initial residual (before the first cycle), also kept in FP64 (r64).
 template <class V>
-__global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) {
+// fuse (an engine of one problem whose norm is one group of partials): the last block to finish
+// sums the partials in the fixed order and takes the outer control step (in place of a control
+// launch)
+__global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl, int fuse) {
   pdl_start();
   if (solo_idle(E, PH_OUTER)) return;
   const int lane = threadIdx.x & 31;
@@ -2804,6 +2825,14 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl) 
     if (pcg) st4(P.r64 + i0, r);
     q = warp_sum(q);
     if (lane == 0) E.partial[g] = q;
+  }
+  if (fuse && solo_last_block(E)) {               // (every block was in the outer phase)
+    __shared__ double sh[32];
+    const double sum = problem_norm_sum(E.partial, fine_tiles(E.P[0].L), sh);
+    if (threadIdx.x == 0) {
+      control_apply(E, E.S[0], CTRL_OUTER, sum);
+      *E.ticket = 0u;
+    }
   }
 }
 
@@ -2933,9 +2962,14 @@ __global__ void __launch_bounds__(256) k_pcg_p(EngineDev E, TileList tl) {
 }
 
 // x64 += c / s (c = inner top-level iterate, buffer 0), for problems in PH_UPDATE
-__global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl) {
+// fuse (an engine of one problem, defect correction): the last block to finish takes the control
+// step after the update and the end-of-iteration summary (in place of two launches); then every
+// block runs to the end whatever the phase
+__global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl, int fuse,
+                                                cudaGraphConditionalHandle h, int use_handle) {
   pdl_start();
-  if (solo_idle(E, PH_UPDATE)) return;
+  const bool updating = E.nprob != 1 || E.S[0].phase == PH_UPDATE;
+  if (!fuse && !updating) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -2956,6 +2990,15 @@ __global__ void __launch_bounds__(256) k_update(EngineDev E, TileList tl) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) x[j] = fma(double(c[j]), inv_s, x[j]);
     st4(P.x64 + i0, x);
+  }
+  if (fuse && solo_last_block(E)) {
+    __shared__ double sh[32];
+    if (threadIdx.x == 0) {
+      if (updating) control_apply(E, E.S[0], CTRL_POST, 0.0);
+      *E.ticket = 0u;
+    }
+    __syncthreads();
+    summary_apply(E, h, use_handle, 1, sh);
   }
 }
 
@@ -3038,41 +3081,10 @@ __device__ bool control_sum(const EngineDev& E, int p, int j, const double* part
   return true;
 }
 
-__global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int level) {
-  pdl_start();
-  __shared__ double sh[32];
-  const int p = blockIdx.x / E.ctl_groups, j = blockIdx.x - p * E.ctl_groups;
-  if (p >= E.nprob) return;
-  ProbState& st = E.S[p];
+// The state transition of control step `kind` for problem state st, given the summed partials
+// (thread 0 of one block; the control kernel, or the last block of a kernel that folds the step in)
+__device__ void control_apply(const EngineDev& E, ProbState& st, int kind, double sum) {
   const int ph = st.phase;
-  if (kind == CTRL_PRE) {
-    bool owner = j == 0;                        // the block that sets the cycle's IF value
-    if ((ph == PH_INNER || ph == PH_CYCLE) && E.P[p].L == level && !st.zero_top) {
-      double sum = 0.0;
-      owner = control_sum(E, p, j, E.partial + E.fine_off[p], fine_tiles(level), sh, &sum);
-      if (owner && threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
-    }
-    // the rest of the V cycle runs if any problem is still in it
-    if (owner && threadIdx.x == 0 && (st.phase == PH_INNER || st.phase == PH_CYCLE))
-      cond_set(E.prm.cond, 0, 1u);
-    return;
-  }
-  const bool mine = (kind == CTRL_INIT && ph == PH_INIT) ||
-                    (kind == CTRL_CHECK0 && ph == PH_CHECK) ||
-                    (kind == CTRL_CHECK && ph == PH_CYCLE) ||
-                    (kind == CTRL_OUTER && ph == PH_OUTER) ||
-                    (kind == CTRL_POST && ph == PH_UPDATE) ||
-                    (kind == CTRL_PCG_ALPHA && ph == PH_OUTER && st.cycles > 0) ||
-                    (kind == CTRL_PCG_BETA && ph == PH_PRECOND);
-  if (!mine) return;
-  double sum = 0.0;
-  if (kind != CTRL_POST) {
-    const double* part = kind == CTRL_INIT ? E.partial2 : E.partial;
-    if (!control_sum(E, p, j, part + E.fine_off[p], fine_tiles(E.P[p].L), sh, &sum)) return;
-  } else if (j != 0) {
-    return;
-  }
-  if (threadIdx.x != 0) return;
   const Params& prm = E.prm;
   const double nrm = sqrt(sum);
   switch (kind) {
@@ -3166,13 +3178,49 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
   }
 }
 
+__global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int level) {
+  pdl_start();
+  __shared__ double sh[32];
+  const int p = blockIdx.x / E.ctl_groups, j = blockIdx.x - p * E.ctl_groups;
+  if (p >= E.nprob) return;
+  ProbState& st = E.S[p];
+  const int ph = st.phase;
+  if (kind == CTRL_PRE) {
+    bool owner = j == 0;                        // the block that sets the cycle's IF value
+    if ((ph == PH_INNER || ph == PH_CYCLE) && E.P[p].L == level && !st.zero_top) {
+      double sum = 0.0;
+      owner = control_sum(E, p, j, E.partial + E.fine_off[p], fine_tiles(level), sh, &sum);
+      if (owner && threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
+    }
+    // the rest of the V cycle runs if any problem is still in it
+    if (owner && threadIdx.x == 0 && (st.phase == PH_INNER || st.phase == PH_CYCLE))
+      cond_set(E.prm.cond, 0, 1u);
+    return;
+  }
+  const bool mine = (kind == CTRL_INIT && ph == PH_INIT) ||
+                    (kind == CTRL_CHECK0 && ph == PH_CHECK) ||
+                    (kind == CTRL_CHECK && ph == PH_CYCLE) ||
+                    (kind == CTRL_OUTER && ph == PH_OUTER) ||
+                    (kind == CTRL_POST && ph == PH_UPDATE) ||
+                    (kind == CTRL_PCG_ALPHA && ph == PH_OUTER && st.cycles > 0) ||
+                    (kind == CTRL_PCG_BETA && ph == PH_PRECOND);
+  if (!mine) return;
+  double sum = 0.0;
+  if (kind != CTRL_POST) {
+    const double* part = kind == CTRL_INIT ? E.partial2 : E.partial;
+    if (!control_sum(E, p, j, part + E.fine_off[p], fine_tiles(E.P[p].L), sh, &sum)) return;
+  } else if (j != 0) {
+    return;
+  }
+  if (threadIdx.x != 0) return;
+  control_apply(E, st, kind, sum);
+}
+
 // Count problems still running; publish to the host word and, inside a device-side loop, to the
 // graph's while-condition.  Past the iteration limit every running problem is stopped as not
 // converged, so a device-side loop always ends.
-__global__ void __launch_bounds__(256) k_summary(EngineDev E, cudaGraphConditionalHandle h,
-                                                 int use_handle, int end_of_iteration) {
-  pdl_start();
-  __shared__ double sh[32];
+__device__ void summary_apply(const EngineDev& E, cudaGraphConditionalHandle h, int use_handle,
+                              int end_of_iteration, double* sh) {
   __shared__ unsigned over;
   if (threadIdx.x == 0) {
     const unsigned it = E.iter ? (*E.iter += 1) : 0u;
@@ -3203,6 +3251,13 @@ __global__ void __launch_bounds__(256) k_summary(EngineDev E, cudaGraphCondition
       cond_set(cd, 1, o > 0.0 ? 1u : 0u);
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_summary(EngineDev E, cudaGraphConditionalHandle h,
+                                                 int use_handle, int end_of_iteration) {
+  pdl_start();
+  __shared__ double sh[32];
+  summary_apply(E, h, use_handle, end_of_iteration, sh);
 }
 
 inline int grid_or_one(int g) { return g < 1 ? 1 : g; }
@@ -3538,9 +3593,9 @@ cudaError_t launch_coarse(const EngineDev& E, TileList tl, int want, int grid, c
   return launch_k(k_coarse<float>, grid, 0, s, E.pdl, 0, E, tl, want);
 }
 
-cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  if (E.prm.prec == P64) return launch_k(k_outer_defect<double>, grid, 0, s, E.pdl, 0, E, fine);
-  return launch_k(k_outer_defect<float>, grid, 0, s, E.pdl, 0, E, fine);
+cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse) {
+  if (E.prm.prec == P64) return launch_k(k_outer_defect<double>, grid, 0, s, E.pdl, 0, E, fine, fuse);
+  return launch_k(k_outer_defect<float>, grid, 0, s, E.pdl, 0, E, fine, fuse);
 }
 
 cudaError_t launch_pcg_q(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
@@ -3559,8 +3614,9 @@ cudaError_t launch_pcg_p(const EngineDev& E, TileList fine, int grid, cudaStream
   return launch_k(k_pcg_p<float>, grid, 0, s, E.pdl, 0, E, fine);
 }
 
-cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  return launch_k(k_update, grid, 0, s, E.pdl, 0, E, fine);
+cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse,
+                          cudaGraphConditionalHandle h, int use_handle) {
+  return launch_k(k_update, grid, 0, s, E.pdl, 0, E, fine, fuse, h, use_handle);
 }
 
 cudaError_t launch_norm_b(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
