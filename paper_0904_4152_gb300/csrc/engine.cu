@@ -856,7 +856,8 @@ hn_status Engine::open_if(cudaStream_t& s, int which) {
   if (cst != cudaStreamCaptureStatusActive) return set_error(HN_ERR_STATE, "IF node outside a capture");
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = hCond_[which];
+  const CondDev& cdv = E_.prm.cond;               // the handles of the half being captured
+  cp.conditional.handle = which == 0 ? cdv.h_cycle : (which == 1 ? cdv.h_outer : cdv.h_update);
   cp.conditional.type = cudaGraphCondTypeIf;
   cp.conditional.size = 1;
   cudaGraphNode_t node;
@@ -1015,11 +1016,11 @@ hn_status Engine::issue_iteration(cudaStream_t s0, cudaGraphConditionalHandle h,
     // after the update and the iteration's summary inside the update (their last blocks)
     HN_LAUNCH(KC_OUTER_DEFECT, -1, launch_outer_defect(E_, fine_, fineGrid_, s, 1));
     HN_TRY(issue_vcycle(s, PH_INNER));
-    HN_LAUNCH(KC_UPDATE, -1, launch_update(E_, fine_, fineGrid_, s, 1, h, use_h));
-    if (condCapture_) {
+    if (condCapture_) {                            // the launches outside IF nodes, the update's too
       const CondDev& cd = E_.prm.cond;
-      E_.prm.cond.n_base = (unsigned)(counting_ - start) - cd.n_cycle - cd.n_outer - cd.n_update;
+      E_.prm.cond.n_base = (unsigned)(counting_ + 1 - start) - cd.n_cycle - cd.n_outer - cd.n_update;
     }
+    HN_LAUNCH(KC_UPDATE, -1, launch_update(E_, fine_, fineGrid_, s, 1, h, use_h));
     return HN_OK;
   } else {
     if (cond_on(1)) HN_TRY(open_if(s, 1));
@@ -1146,12 +1147,14 @@ hn_status Engine::capture_solve(bool cond) {
     const int T = std::max(std::max(tune_.tail_level, prm_.coarse), mid_top());
     if (Lmax_ > T && prm_.prec != P64 && prm_.solver != SOLVER_PCG) cd.mask |= 1u;
     const unsigned defaults[3] = {0u, 1u, 0u};
+    // two sets: the loop body holds two iterations, each with IF nodes of its own handles
     for (int w = 0; w < 3; ++w)
       if ((cd.mask >> w) & 1u)
-        HN_CUDA(cudaGraphConditionalHandleCreate(&hCond_[w], main, defaults[w], cudaGraphCondAssignDefault));
-    cd.h_cycle = hCond_[0];
-    cd.h_outer = hCond_[1];
-    cd.h_update = hCond_[2];
+        for (int half = 0; half < 2; ++half)
+          HN_CUDA(cudaGraphConditionalHandleCreate(&hCond_[half][w], main, defaults[w], cudaGraphCondAssignDefault));
+    cd.h_cycle = hCond_[0][0];
+    cd.h_outer = hCond_[0][1];
+    cd.h_update = hCond_[0][2];
     cd.taken = dTaken_;
     cd.launches = dLaunches_;
   }
@@ -1174,10 +1177,25 @@ hn_status Engine::capture_solve(bool cond) {
   HN_CUDA(cudaGraphAddNode(&nCond, main, &nInit, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   HN_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  // The loop body is two iterations: the first one's summary leaves the loop condition alone, the
+  // second one's sets it (a problem that finishes in the first runs the second as no-ops).  Each
+  // turn of a device-side loop costs several microseconds; this halves their number.
   E_.prm.cond = cd;
   condCapture_ = cd.mask != 0;
   counting_ = 0;
-  st = issue_iteration(cs, h, 1);
+  st = issue_iteration(cs, h, 0);
+  if (st == HN_OK) {
+    CondDev cd2 = cd;
+    cd2.h_cycle = hCond_[1][0];
+    cd2.h_outer = hCond_[1][1];
+    cd2.h_update = hCond_[1][2];
+    cd2.n_base = E_.prm.cond.n_base;               // the counts of the first half (same shape)
+    cd2.n_cycle = E_.prm.cond.n_cycle;
+    cd2.n_outer = E_.prm.cond.n_outer;
+    cd2.n_update = E_.prm.cond.n_update;
+    E_.prm.cond = cd2;
+    st = issue_iteration(cs, h, 1);
+  }
   condCapture_ = false;
   e = cudaStreamEndCapture(cs, &body);
   HN_TRY(st);

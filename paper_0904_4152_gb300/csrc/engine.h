@@ -284,7 +284,7 @@ class Engine {
   // IF nodes inside the closed-world loop (see CondDev)
   cudaStream_t aux_ = nullptr;
   bool condCapture_ = false, condUsed_ = false, pdlBarrier_ = false;
-  cudaGraphConditionalHandle hCond_[3] = {};
+  cudaGraphConditionalHandle hCond_[2][3] = {};   // IF handles of the two halves of the loop body
   unsigned* dTaken_ = nullptr;
   unsigned long long* dLaunches_ = nullptr;
   // profiling

@@ -327,7 +327,9 @@ __device__ __forceinline__ double tile_sumsq(const double (&r)[4]) {
   for (int j = 0; j < 4; ++j) q += r[j] * r[j];
   return warp_sum(q);
 }
-__device__ __forceinline__ double tile_sumsq(const float (&r)[4]) {
+// FP32: the pair (hi, lo) itself, stored in the partial's 8 bytes; every consumer of the partials
+// of an FP32 / FP16 cycle sums them as pairs (problem_partial_sum with df)
+__device__ __forceinline__ float2 tile_sumsq(const float (&r)[4]) {
   float hi = __fmul_rn(r[0], r[0]), lo = fmaf(r[0], r[0], -hi);
 #pragma unroll
   for (int j = 1; j < 4; ++j) {
@@ -339,7 +341,36 @@ __device__ __forceinline__ double tile_sumsq(const float (&r)[4]) {
     const float bh = __shfl_xor_sync(kFull, hi, o), bl = __shfl_xor_sync(kFull, lo, o);
     df_add(hi, lo, bh, bl);
   }
-  return double(hi) + double(lo);                  // exact (lo is below half an ulp of hi)
+  return make_float2(hi, lo);
+}
+__device__ __forceinline__ void store_partial(double* slot, double q) { *slot = q; }
+__device__ __forceinline__ void store_partial(double* slot, float2 q) { *reinterpret_cast<float2*>(slot) = q; }
+
+// the same butterfly over the block (any multiple of 32 threads up to 1024); valid in warp 0.
+// sh: 32 doubles of shared memory, used as 64 floats
+__device__ double block_sum_df(float hi, float lo, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(kFull, hi, o), bl = __shfl_xor_sync(kFull, lo, o);
+    df_add(hi, lo, bh, bl);
+  }
+  float* sf = reinterpret_cast<float*>(sh);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sf[2 * w] = hi; sf[2 * w + 1] = lo; }
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    const bool in = lane < (int)(blockDim.x >> 5);
+    float h = in ? sf[2 * lane] : 0.0f, l = in ? sf[2 * lane + 1] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float bh = __shfl_xor_sync(kFull, h, o), bl = __shfl_xor_sync(kFull, l, o);
+      df_add(h, l, bh, bl);
+    }
+    t = double(h) + double(l);                    // exact (l is below half an ulp of h)
+  }
+  __syncthreads();
+  return t;
 }
 
 // deterministic block sum of a per-thread value (256 threads)
@@ -362,7 +393,44 @@ __device__ double block_sum256(double v, double* sh) {
 // the block tree.  Every caller uses this order, so a problem's norm does not depend on which
 // kernel or batch computed it.  (Four chains: a dependent FP64 add costs ~64 cycles here.)
 // Valid in thread 0.
-__device__ double problem_partial_sum(const double* part, int ntiles, double* sh) {
+// df: the partials are double-float pairs (an FP32 / FP16 cycle's), summed in the same order in
+// double-float arithmetic on the FP32 pipe: one SM's FP64 rate (~1.7 operations per cycle) made
+// the 8,209 FP64 additions of an L = 10 norm the longest part of its lagged check (~10 us).
+__device__ double problem_partial_sum_df(const double* part, int ntiles, double* sh) {
+  const float2* pp = reinterpret_cast<const float2*>(part);
+  float h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, l[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (threadIdx.x < 256) {
+    int q = threadIdx.x;
+    for (; q + 31 * 256 < ntiles; q += 32 * 256) {
+      float2 v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = __ldcg(pp + q + k * 256);
+#pragma unroll
+      for (int k = 0; k < 32; k += 4)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) df_add(h[c], l[c], v[k + c].x, v[k + c].y);
+    }
+    for (; q + 3 * 256 < ntiles; q += 4 * 256)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float2 v = __ldcg(pp + q + c * 256);
+        df_add(h[c], l[c], v.x, v.y);
+      }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (q + c * 256 < ntiles) {
+        const float2 v = __ldcg(pp + q + c * 256);
+        df_add(h[c], l[c], v.x, v.y);
+      }
+  }
+  df_add(h[0], l[0], h[1], l[1]);
+  df_add(h[2], l[2], h[3], l[3]);
+  df_add(h[0], l[0], h[2], l[2]);
+  return block_sum_df(h[0], l[0], sh);
+}
+
+__device__ double problem_partial_sum(const double* part, int ntiles, double* sh, bool df = false) {
+  if (df) return problem_partial_sum_df(part, ntiles, sh);
   double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
   if (threadIdx.x < 256) {                    // larger blocks: the other threads add +0.0
     int q = threadIdx.x;
@@ -399,18 +467,18 @@ __device__ double problem_partial_sum(const double* part, int ntiles, double* sh
 // gives each group its own block.)  Every path that forms a problem's norm uses this order.
 __device__ __forceinline__ int sum_groups(int ntiles) { return (ntiles + kSumGroup - 1) / kSumGroup; }
 
-__device__ double group_partial_sum(const double* part, int ntiles, int j, double* sh) {
+__device__ double group_partial_sum(const double* part, int ntiles, int j, double* sh, bool df = false) {
   const int lo = j * kSumGroup;
-  return problem_partial_sum(part + lo, min(kSumGroup, ntiles - lo), sh);
+  return problem_partial_sum(part + lo, min(kSumGroup, ntiles - lo), sh, df);
 }
 
 // the same order in one block (valid in thread 0)
-__device__ double problem_norm_sum(const double* part, int ntiles, double* sh) {
+__device__ double problem_norm_sum(const double* part, int ntiles, double* sh, bool df = false) {
   const int ng = sum_groups(ntiles);
-  if (ng == 1) return problem_partial_sum(part, ntiles, sh);
+  if (ng == 1) return problem_partial_sum(part, ntiles, sh, df);
   double t = 0.0;
   for (int j = 0; j < ng; ++j) {
-    const double g = group_partial_sum(part, ntiles, j, sh);
+    const double g = group_partial_sum(part, ntiles, j, sh, df);
     if (threadIdx.x == 0) t += g;
   }
   return t;
@@ -586,8 +654,8 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
       for (int j = 0; j < 4; ++j) out[j] = V(r[j]);
       st4(static_cast<V*>(d.r) + i0, out);
     } else if constexpr (MODE == M_CHECK) {
-      const double q = tile_sumsq(r);
-      if (lane == 0) *partial_slot = q;
+      const auto q = tile_sumsq(r);
+      if (lane == 0) store_partial(partial_slot, q);
     } else {                                      // a Jacobi step src -> dst
       A wd[4];
       wd4_of<Pol, LKB>(d, i0, omega, dg, wd);
@@ -597,8 +665,8 @@ __device__ __forceinline__ void band_tile(const LevelDev& d, long long shift, bo
       st4(static_cast<V*>(d.x[dst]) + i0, out);
       if constexpr (MODE == M_PRE12 || MODE == M_JACOBI_FIRST) {
         if (partial_slot) {                       // residual norm of the iterate (lagged check)
-          const double q = tile_sumsq(r);
-          if (lane == 0) *partial_slot = q;
+          const auto q = tile_sumsq(r);
+          if (lane == 0) store_partial(partial_slot, q);
         }
       }
     }
@@ -1100,7 +1168,7 @@ __device__ void solo_fused_check(const EngineDev& E, int level, bool checked, in
   __threadfence();
   ProbState& st = E.S[0];
   double sum = 0.0;
-  if (checked) sum = problem_norm_sum(E.partial, fine_tiles(level), sh);
+  if (checked) sum = problem_norm_sum(E.partial, fine_tiles(level), sh, E.prm.prec != P64);
   if (threadIdx.x == 0) {
     if (checked) pre_check(st, E.prm, sqrt(sum));
     if (st.phase == want && (st.phase == PH_INNER || st.phase == PH_CYCLE)) cond_set(E.prm.cond, 0, 1u);
@@ -1628,7 +1696,7 @@ __device__ bool vcycle_down_smem(const LevelDev& d, const LevelDev& dc, int l, b
                                                lane, 0, omega, check_part + t);
     }
     __syncthreads();
-    const double sum = problem_norm_sum(check_part, fine_tiles(l), sh);
+    const double sum = problem_norm_sum(check_part, fine_tiles(l), sh, Pol::prec != P64);
     if (tid == 0) pre_check(*st, prm, sqrt(sum));
     __syncthreads();
     if (__ldcg(&st->phase) != want) return false;
@@ -1881,7 +1949,7 @@ __device__ __forceinline__ bool vcycle_down_level(const LevelDev& d, const Level
   sync();
   if (check_part) {
     if (rank == 0) {
-      const double sum = problem_norm_sum(check_part, fine_tiles(l), sh);
+      const double sum = problem_norm_sum(check_part, fine_tiles(l), sh, Pol::prec != P64);
       if (threadIdx.x == 0) pre_check(*st, prm, sqrt(sum));
     }
     sync();
@@ -2090,7 +2158,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(EngineDev E, int T, in
         band_tile<Pol, M_CHECK, LD_GEN>(d, 1LL << c, false, (long long)t * kTile + lane * kLaneNodes, lane, 0,
                                         omega, check_part + t);
       __syncthreads();
-      const double sum = problem_norm_sum(check_part, fine_tiles(c), sh);
+      const double sum = problem_norm_sum(check_part, fine_tiles(c), sh, Pol::prec != P64);
       if (threadIdx.x == 0) pre_check(*stw, E.prm, sqrt(sum));
       __syncthreads();
       go = __ldcg(&stw->phase) == want;
@@ -2654,7 +2722,7 @@ __device__ void mid_check(const EngineDev& E, int l, int want, int first, int st
   for (int p = first; p < E.nprob; p += stride) {
     ProbState& st = E.S[p];
     if (E.P[p].L != l || __ldcg(&st.phase) != want || __ldcg(&st.zero_top)) continue;
-    const double sum = problem_norm_sum(E.partial + E.fine_off[p], fine_tiles(l), sh);
+    const double sum = problem_norm_sum(E.partial + E.fine_off[p], fine_tiles(l), sh, E.prm.prec != P64);
     if (threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
     __syncthreads();
   }
@@ -3053,17 +3121,18 @@ __global__ void __launch_bounds__(256) k_boundary_check(EngineDev E) {
 // The norm of problem p from its tile partials, by the ctl_groups blocks of p in this launch
 // (block j adds group j; the block that finishes last adds the group sums in order).  Returns
 // true in the one block that holds the result (in thread 0); the others return false.
+// df: double-float partials (the checks of an FP32 / FP16 cycle)
 __device__ bool control_sum(const EngineDev& E, int p, int j, const double* part, int ntiles,
-                            double* sh, double* sum) {
+                            double* sh, double* sum, bool df) {
   const int ng = sum_groups(ntiles);
   if (ng == 1) {
     if (j != 0) return false;
-    *sum = problem_partial_sum(part, ntiles, sh);
+    *sum = problem_partial_sum(part, ntiles, sh, df);
     return true;
   }
   if (j >= ng) return false;
   __shared__ int last;
-  const double g = group_partial_sum(part, ntiles, j, sh);
+  const double g = group_partial_sum(part, ntiles, j, sh, df);
   if (threadIdx.x == 0) {
     E.gsum[(long long)p * E.ctl_groups + j] = g;
     __threadfence();
@@ -3189,7 +3258,7 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
     bool owner = j == 0;                        // the block that sets the cycle's IF value
     if ((ph == PH_INNER || ph == PH_CYCLE) && E.P[p].L == level && !st.zero_top) {
       double sum = 0.0;
-      owner = control_sum(E, p, j, E.partial + E.fine_off[p], fine_tiles(level), sh, &sum);
+      owner = control_sum(E, p, j, E.partial + E.fine_off[p], fine_tiles(level), sh, &sum, E.prm.prec != P64);
       if (owner && threadIdx.x == 0) pre_check(st, E.prm, sqrt(sum));
     }
     // the rest of the V cycle runs if any problem is still in it
@@ -3208,7 +3277,9 @@ __global__ void __launch_bounds__(256) k_control(EngineDev E, int kind, int leve
   double sum = 0.0;
   if (kind != CTRL_POST) {
     const double* part = kind == CTRL_INIT ? E.partial2 : E.partial;
-    if (!control_sum(E, p, j, part + E.fine_off[p], fine_tiles(E.P[p].L), sh, &sum)) return;
+    // the checks of the cycle's own precision: double-float partials in FP32 / FP16 cycles
+    const bool df = (kind == CTRL_CHECK || kind == CTRL_CHECK0) && E.prm.prec != P64;
+    if (!control_sum(E, p, j, part + E.fine_off[p], fine_tiles(E.P[p].L), sh, &sum, df)) return;
   } else if (j != 0) {
     return;
   }

@@ -367,7 +367,9 @@ def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L, mid,
     # the one-launch solve of the defect correction skips, through an IF node, the rest of a V
     # cycle after a lagged check that ends the inner solve (a check on a level run by one launch
     # per step; the persistent kernels take their checks inside and skip the rest themselves);
-    # the host-driven iterations (profiling) run every kernel of every iteration
+    # the host-driven iterations (profiling) run every kernel of every iteration.  A turn of the
+    # device-side loop holds two iterations, so a solve that ends in the first may launch the
+    # second's kernels as no-ops: at most one iteration's launches more than the host-driven solve.
     coef, b = I.batch_problem(5, L)
     A = hn.hn_band_create(L, coef)
     mg = hn.hn_mg_setup(A, prec=prec)
@@ -385,7 +387,7 @@ def test_device_loop_skips_idle_parts_without_changing_results(hn, prec, L, mid,
         np.testing.assert_array_equal(x0, x1)
         for k in ("cycles", "outer_iters", "inner_cycles", "relres"):
             assert st0[k] == st1[k], k
-        assert 0 < n_loop <= n_host
+        assert 0 < n_loop <= n_host + n_host // max(1, st0["cycles"])
         if prec != 0 and L > max(tail, mid):
             assert n_loop < n_host
         # a second solve counts its own launches again
