@@ -60,10 +60,12 @@ constexpr int kMidCandidate = 10;
 
 // default launch shape of one problem: FP64 arithmetic is slow enough on this part that the
 // fused tail pays from level 6 down (its levels then fit in distributed shared memory); the
-// FP32/FP16 inner cycles fuse from level 7 down (measured at L=10)
+// FP32/FP16 inner cycles fuse from level 5 down (block 0's shared memory alone), the levels
+// above it up to 9 running as fused sweeps (autotuned at L = 10: 1.537 ms against >= 1.576 ms
+// with the tail from level 7)
 Tuning default_tuning(const Params& prm) {
   Tuning t;
-  t.tail_level = prm.prec == P64 ? 6 : 7;
+  t.tail_level = prm.prec == P64 ? 6 : 5;
   return t;
 }
 
