@@ -997,7 +997,20 @@ hn_status Engine::issue_init(cudaStream_t s, cudaGraphConditionalHandle h, int u
 hn_status Engine::issue_iteration(cudaStream_t s0, cudaGraphConditionalHandle h, int use_h) {
   cudaStream_t s = s0;
   const int start = counting_;
-  if (prm_.solver == SOLVER_PCG) {
+  if (prm_.solver == SOLVER_PCG && fuse_control()) {
+    // the same steps with each control step in the last block of the kernel before it, and the
+    // summary in the last one's
+    HN_TRY(issue_vcycle(s, PH_PRECOND));
+    HN_LAUNCH(KC_PCG_DOT, -1, launch_pcg_dot(E_, fine_, fineGrid_, s, 1));
+    HN_LAUNCH(KC_PCG_P, -1, launch_pcg_p(E_, fine_, fineGrid_, s, 1));
+    HN_LAUNCH(KC_PCG_Q, -1, launch_pcg_q(E_, fine_, fineGrid_, s, 1));
+    if (condCapture_) {
+      const CondDev& cd = E_.prm.cond;
+      E_.prm.cond.n_base = (unsigned)(counting_ + 1 - start) - cd.n_cycle - cd.n_outer - cd.n_update;
+    }
+    HN_LAUNCH(KC_PCG_X, -1, launch_pcg_x(E_, fine_, fineGrid_, s, 1, h, use_h));
+    return HN_OK;
+  } else if (prm_.solver == SOLVER_PCG) {
     // z = M r (one cycle from zero), rho' = (r, z), beta, p = z + beta p, then the CG step
     // q = A p, alpha, x += alpha p, r -= alpha q, and its check
     HN_TRY(issue_vcycle(s, PH_PRECOND));
@@ -1049,11 +1062,12 @@ hn_status Engine::issue_iteration(cudaStream_t s0, cudaGraphConditionalHandle h,
   return HN_OK;
 }
 
-// The defect correction of an engine of one problem folds its control steps and the iteration
-// summary into the outer defect and the update when the fine norm is one group of partials (one
-// block sums it) and neither step has an IF node of its own.
+// The defect correction and CG of an engine of one problem fold their control steps and the
+// iteration summary into the kernels before them when the fine norm is one group of partials (one
+// block sums it) and no step has an IF node of its own.
 bool Engine::fuse_control() const {
-  return cap_ == 1 && prm_.solver != SOLVER_PCG && prm_.prec != P64 && !cond_on(1) && !cond_on(2) &&
+  const bool dc = prm_.solver != SOLVER_PCG && prm_.prec != P64;
+  return cap_ == 1 && (dc || prm_.solver == SOLVER_PCG) && !cond_on(1) && !cond_on(2) &&
          pitch_of(Lmax_) / kTile <= kSumGroup;
 }
 

@@ -267,10 +267,12 @@ cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cud
 // PCG vector steps on each problem's finest level (FP64): q = A p with partials (p, q); x += alpha
 // p, r -= alpha q with partials ||r||^2 and the scaled residual as the cycle's right-hand side;
 // partials (r, z); p = z / s + beta p
-cudaError_t launch_pcg_q(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
-cudaError_t launch_pcg_x(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
-cudaError_t launch_pcg_dot(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
-cudaError_t launch_pcg_p(const EngineDev& E, TileList fine, int grid, cudaStream_t s);
+cudaError_t launch_pcg_q(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse = 0);
+// fuse (one problem): the kernels' last blocks take the control steps (pcg_x also the summary)
+cudaError_t launch_pcg_x(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse = 0,
+                         cudaGraphConditionalHandle h = 0, int use_handle = 0);
+cudaError_t launch_pcg_dot(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse = 0);
+cudaError_t launch_pcg_p(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse = 0);
 cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse = 0,
                           cudaGraphConditionalHandle h = 0, int use_handle = 0);
 cudaError_t launch_norm_b(const EngineDev& E, TileList fine, int grid, cudaStream_t s);

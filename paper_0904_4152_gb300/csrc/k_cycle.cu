@@ -1155,6 +1155,20 @@ __device__ bool solo_last_block(const EngineDev& E) {
   return s_last != 0;
 }
 
+// The last block of a launch of an engine of one problem takes control step `kind` in place of a
+// control launch: with the launch's FP64 partials summed in the fixed order (sum_partials), if
+// the problem was in the phase the step serves (mine: block-uniform, read at the launch's start)
+__device__ void solo_fused_control(const EngineDev& E, int kind, bool mine, bool sum_partials) {
+  if (!solo_last_block(E)) return;
+  __shared__ double sh[32];
+  double sum = 0.0;
+  if (mine && sum_partials) sum = problem_norm_sum(E.partial, fine_tiles(E.P[0].L), sh);
+  if (threadIdx.x == 0) {
+    if (mine) control_apply(E, E.S[0], kind, sum);
+    *E.ticket = 0u;
+  }
+}
+
 __device__ void solo_fused_check(const EngineDev& E, int level, bool checked, int want) {
   __shared__ double sh[32];
   __shared__ int s_last;
@@ -2909,9 +2923,10 @@ __global__ void __launch_bounds__(256) k_outer_defect(EngineDev E, TileList tl, 
 // solver plugged into another, Sec. 4.1): every step below is one pass over the fine work list.
 
 // q = A p (FP64 bands, p with zero halos), partial[g] = sum p q, for problems in their CG step
-__global__ void __launch_bounds__(256) k_pcg_q(EngineDev E, TileList tl) {
+__global__ void __launch_bounds__(256) k_pcg_q(EngineDev E, TileList tl, int fuse) {
   pdl_start();
   if (solo_idle(E, PH_OUTER)) return;
+  const bool mine = E.S[0].cycles > 0;            // (fuse: one problem, in the outer phase)
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -2934,13 +2949,18 @@ __global__ void __launch_bounds__(256) k_pcg_q(EngineDev E, TileList tl) {
     t = warp_sum(t);
     if (lane == 0) E.partial[g] = t;
   }
+  if (fuse) solo_fused_control(E, CTRL_PCG_ALPHA, mine, true);
 }
 
 // x += alpha p, r -= alpha q; partial[g] = sum r^2; the cycle's right-hand side V(s r)
+// fuse (one problem): the last block takes the check after the step and the iteration's summary;
+// every block then runs to the end whatever the phase
 template <class V>
-__global__ void __launch_bounds__(256) k_pcg_x(EngineDev E, TileList tl) {
+__global__ void __launch_bounds__(256) k_pcg_x(EngineDev E, TileList tl, int fuse,
+                                               cudaGraphConditionalHandle h, int use_handle) {
   pdl_start();
-  if (solo_idle(E, PH_OUTER)) return;
+  const bool outer = E.nprob != 1 || E.S[0].phase == PH_OUTER;
+  if (!fuse && !outer) return;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -2973,11 +2993,22 @@ __global__ void __launch_bounds__(256) k_pcg_x(EngineDev E, TileList tl) {
     t = warp_sum(t);
     if (lane == 0) E.partial[g] = t;
   }
+  if (fuse && solo_last_block(E)) {
+    __shared__ double sh[32];
+    double sum = 0.0;
+    if (outer) sum = problem_norm_sum(E.partial, fine_tiles(E.P[0].L), sh);
+    if (threadIdx.x == 0) {
+      if (outer) control_apply(E, E.S[0], CTRL_OUTER, sum);
+      *E.ticket = 0u;
+    }
+    __syncthreads();
+    summary_apply(E, h, use_handle, 1, sh);
+  }
 }
 
 // partial[g] = sum r c, c = the cycle's result (top-level buffer 0, z = c / s)
 template <class V>
-__global__ void __launch_bounds__(256) k_pcg_dot(EngineDev E, TileList tl) {
+__global__ void __launch_bounds__(256) k_pcg_dot(EngineDev E, TileList tl, int fuse) {
   pdl_start();
   if (solo_idle(E, PH_PRECOND)) return;
   const int lane = threadIdx.x & 31;
@@ -3000,11 +3031,12 @@ __global__ void __launch_bounds__(256) k_pcg_dot(EngineDev E, TileList tl) {
     t = warp_sum(t);
     if (lane == 0) E.partial[g] = t;
   }
+  if (fuse) solo_fused_control(E, CTRL_PCG_BETA, true, true);
 }
 
 // p = c / s + beta p (the new search direction), for problems in PH_UPDATE
 template <class V>
-__global__ void __launch_bounds__(256) k_pcg_p(EngineDev E, TileList tl) {
+__global__ void __launch_bounds__(256) k_pcg_p(EngineDev E, TileList tl, int fuse) {
   pdl_start();
   if (solo_idle(E, PH_UPDATE)) return;
   const int lane = threadIdx.x & 31;
@@ -3027,6 +3059,7 @@ __global__ void __launch_bounds__(256) k_pcg_p(EngineDev E, TileList tl) {
     for (int j = 0; j < 4; ++j) pv[j] = fma(beta, pv[j], double(c[j]) * inv_s);
     st4(P.p64 + i0, pv);
   }
+  if (fuse) solo_fused_control(E, CTRL_POST, true, false);
 }
 
 // x64 += c / s (c = inner top-level iterate, buffer 0), for problems in PH_UPDATE
@@ -3669,20 +3702,21 @@ cudaError_t launch_outer_defect(const EngineDev& E, TileList fine, int grid, cud
   return launch_k(k_outer_defect<float>, grid, 0, s, E.pdl, 0, E, fine, fuse);
 }
 
-cudaError_t launch_pcg_q(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  return launch_k(k_pcg_q, grid, 0, s, E.pdl, 0, E, fine);
+cudaError_t launch_pcg_q(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse) {
+  return launch_k(k_pcg_q, grid, 0, s, E.pdl, 0, E, fine, fuse);
 }
-cudaError_t launch_pcg_x(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  if (E.prm.prec == P64) return launch_k(k_pcg_x<double>, grid, 0, s, E.pdl, 0, E, fine);
-  return launch_k(k_pcg_x<float>, grid, 0, s, E.pdl, 0, E, fine);
+cudaError_t launch_pcg_x(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse,
+                         cudaGraphConditionalHandle h, int use_handle) {
+  if (E.prm.prec == P64) return launch_k(k_pcg_x<double>, grid, 0, s, E.pdl, 0, E, fine, fuse, h, use_handle);
+  return launch_k(k_pcg_x<float>, grid, 0, s, E.pdl, 0, E, fine, fuse, h, use_handle);
 }
-cudaError_t launch_pcg_dot(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  if (E.prm.prec == P64) return launch_k(k_pcg_dot<double>, grid, 0, s, E.pdl, 0, E, fine);
-  return launch_k(k_pcg_dot<float>, grid, 0, s, E.pdl, 0, E, fine);
+cudaError_t launch_pcg_dot(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse) {
+  if (E.prm.prec == P64) return launch_k(k_pcg_dot<double>, grid, 0, s, E.pdl, 0, E, fine, fuse);
+  return launch_k(k_pcg_dot<float>, grid, 0, s, E.pdl, 0, E, fine, fuse);
 }
-cudaError_t launch_pcg_p(const EngineDev& E, TileList fine, int grid, cudaStream_t s) {
-  if (E.prm.prec == P64) return launch_k(k_pcg_p<double>, grid, 0, s, E.pdl, 0, E, fine);
-  return launch_k(k_pcg_p<float>, grid, 0, s, E.pdl, 0, E, fine);
+cudaError_t launch_pcg_p(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse) {
+  if (E.prm.prec == P64) return launch_k(k_pcg_p<double>, grid, 0, s, E.pdl, 0, E, fine, fuse);
+  return launch_k(k_pcg_p<float>, grid, 0, s, E.pdl, 0, E, fine, fuse);
 }
 
 cudaError_t launch_update(const EngineDev& E, TileList fine, int grid, cudaStream_t s, int fuse,
