@@ -246,12 +246,26 @@ __device__ __forceinline__ void stencil_windows(const void* const* band, const f
 
 // FP16-band operator in row-sum form (array 4 holds the row sum rho):
 // acc[j] = rho x_i + sum_{k != 4} a_k (x_{i+off_k} - x_i) in band order; dg[j] = rho - sum a_k.
+// The nine 8-byte band loads of the lane are issued before any arithmetic (the FP16 kernels move
+// half an FP32 lane's bytes per load, so more of them must be in flight: L = 12 Jacobi 0.88 ->
+// 0.90 of HBM); each value is then scaled and used in band order as before.
 template <int LKB>
 __device__ __forceinline__ void stencil_windows_rowsum(const void* const* band, const float* scale,
                                                        const float (&w)[3][8], long long i0,
                                                        float (&acc)[4], float (&dg)[4]) {
+  uint2 raw[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) raw[k] = ldk<LKB>(reinterpret_cast<const uint2*>(static_cast<const __half*>(band[k]) + i0));
+  // 4 consecutive values of band k, each rounded on its own (never contracted into a following add)
+  auto unpack = [&](int k, float (&o)[4]) {
+    const __half2 h0 = *reinterpret_cast<const __half2*>(&raw[k].x);
+    const __half2 h1 = *reinterpret_cast<const __half2*>(&raw[k].y);
+    const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+    o[0] = __fmul_rn(scale[k], f0.x); o[1] = __fmul_rn(scale[k], f0.y);
+    o[2] = __fmul_rn(scale[k], f1.x); o[3] = __fmul_rn(scale[k], f1.y);
+  };
   float rho[4];
-  load_band<F16, LKB>(band[4], scale[4], i0, rho);
+  unpack(4, rho);
 #pragma unroll
   for (int j = 0; j < 4; ++j) { acc[j] = rho[j] * w[1][j + 2]; dg[j] = rho[j]; }
 #pragma unroll
@@ -259,7 +273,7 @@ __device__ __forceinline__ void stencil_windows_rowsum(const void* const* band, 
     if (k == 4) continue;
     const int dy = k / 3 - 1, dx = k % 3 - 1;
     float b[4];
-    load_band<F16, LKB>(band[k], scale[k], i0, b);
+    unpack(k, b);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       acc[j] = fmaf(b[j], w[dy + 1][j + dy + dx + 2] - w[1][j + 2], acc[j]);
@@ -1130,8 +1144,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // One warp-tile per loop trip over the work list.  level < 0: each problem's own finest level.
 // Resident blocks per SM asked of the register allocator.  The streaming modes keep 5 blocks
 // (40 warps) of FP32 / FP16 loads in flight, enough to saturate HBM (the FP16 Jacobi step spills
-// a few bytes at 5 blocks and is still faster than at 4: 89.8 vs 96.3 us at L = 12); the fused
-// pre-smoothing (4 blocks) and check modes run once per cycle and get more registers per thread.
+// a few bytes at 5 blocks and is still faster than at 4: 89.8 vs 96.3 us at L = 12), except the
+// FP16 defect, faster at 4 with its band loads hoisted; the fused pre-smoothing (4 blocks) and
+// check modes run once per cycle and get more registers per thread.
 // The lagged check of an engine of one problem taken inside its first smoothing step (in place of
 // a separate control launch, for problems whose norm is one group of partials): the last block to
 // finish sums the tile partials in the fixed order and updates the state, and the cycle's IF value
@@ -1195,7 +1210,7 @@ template <class Pol, int MODE> constexpr int band_min_blocks() {
   if (MODE == M_PRE12) return Pol::prec == P64 ? 2 : 4;
   if (MODE == M_PJ) return Pol::prec == P64 ? 2 : (Pol::prec == P32 ? 4 : 3);
   if (Pol::prec == P32) return 5;
-  if (Pol::prec == P16) return (MODE == M_SPMV || MODE == M_DEFECT || MODE == M_JACOBI) ? 5 : 4;
+  if (Pol::prec == P16) return (MODE == M_SPMV || MODE == M_JACOBI) ? 5 : 4;   // defect: 0.90 -> 0.92 at 4
   return MODE == M_SPMV ? 4 : 3;
 }
 
