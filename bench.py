@@ -1141,7 +1141,9 @@ def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
             if sub[i] is None:
                 break
             status, x, st = hn.hn_mg_poll(srv, sub[i], int(levels[i]))
-            res[i] = (status, st["solve_ns"] * 1e-6 if st else None, st["relres"] if st else None)
+            res[i] = (status, st["solve_ns"] * 1e-6 if st else None, st["relres"] if st else None,
+                      st["setup_ns"] * 1e-6 if st else None,
+                      st["outer_iters"] + st["inner_cycles"] if st else None)
         th.join()
         t_end = time.perf_counter()
         info = hn.hn_server_query(srv)
@@ -1151,6 +1153,8 @@ def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
         gen.close()
     ok = [i for i, r in enumerate(res) if r is not None and r[0] == hn.HN_OK]
     lat = np.array([res[i][1] for i in ok])
+    setup = np.array([res[i][3] for i in ok])
+    steps = np.array([res[i][4] for i in ok])
     wall = t_end - t_start
     dofs = sum(((1 << int(levels[i])) + 1) ** 2 for i in ok)
     tenth = [float(np.percentile(lat[k * len(lat) // 10:(k + 1) * len(lat) // 10], 99))
@@ -1164,6 +1168,16 @@ def serve_sample(hn, I, requests, load, budget_gb, slots, seed):
             "p99_ms_by_level": {str(L): float(np.percentile([res[i][1] for i in ok if int(levels[i]) == L], 99))
                                 for L in sorted({int(levels[i]) for i in ok})},
             "submit_late_ms_p99": float(np.percentile(late, 99) * 1e3),
+            # where a request's time goes: the build of its operator and hierarchy (inside the
+            # latency), the solver steps it needs (each one scheduler pass shared with the other
+            # running requests), the passes of the whole run and the mean number of requests in
+            # the server (sum of latencies / wall time)
+            "breakdown": {"build_ms_p50": float(np.percentile(setup, 50)),
+                          "build_ms_p99": float(np.percentile(setup, 99)),
+                          "steps_p50": float(np.percentile(steps, 50)), "steps_max": int(steps.max()),
+                          "passes": int(info["iterations"]),
+                          "ms_per_pass": float(info["iterate_ns"] * 1e-6 / max(1, info["iterations"])),
+                          "mean_in_server": float(lat.sum() * 1e-3 / wall)},
             "inputs": {"distinct": unique, "host_generation_s": gen_s},
             "worker_s": {k: info[k + "_ns"] * 1e-9 for k in ("admit", "schedule", "iterate", "retire")},
             "relres_max": max(res[i][2] for i in ok)}
@@ -1191,7 +1205,7 @@ def run_serve(args, rank, world, local, pg):
                        "budget_gb": args.budget_gb, "slots": args.slots},
             "latency_ms": r["latency_ms"], "dof_per_s": r["dof_per_s"],
             "submit_late_ms_p99": r["submit_late_ms_p99"], "p99_ms_by_level": r["p99_ms_by_level"],
-            "worker_s": r["worker_s"],
+            "breakdown": r["breakdown"], "worker_s": r["worker_s"],
             "relres_max": r["relres_max"]}), flush=True)
 
 
