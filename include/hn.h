@@ -220,11 +220,13 @@ hn_status hn_band_defect_norm_static(const hn_band* A, const double* x, const do
 hn_status hn_mg_get_inner_bands(const hn_mg* mg, int level, void* bands_out, float* scales_out);
 
 /* -------------------------------------------------------------------------------- serving
- * A server owns a worker thread, a builder thread and a device-memory budget.  Submitted requests wait in a FIFO
- * queue; a request is admitted once a slot (max_active) and budget room for its hierarchy are
- * free.  Admitted requests are solved together: every scheduler iteration runs one V-cycle phase
- * sequence over all active requests (continuous batching); finished requests leave, free their
- * memory and let queued requests in.  All requests of a server share precision, pre, post, omega,
+ * A server owns two lanes (requests of levels below 10, and of levels 10 and up), each with a
+ * worker thread, a FIFO queue and its own stream (the small requests' lane at the greatest stream
+ * priority), two builder threads and a device-memory budget.  A request is admitted once a slot
+ * (max_active, shared by the lanes) and budget room for its hierarchy are free.  Admitted requests
+ * of a lane are solved together: every scheduler iteration of a lane runs one V-cycle phase
+ * sequence over its active requests (continuous batching), beside the other lane's iterations;
+ * finished requests leave, free their memory and let queued requests in.  All requests of a server share precision, pre, post, omega,
  * coarse_L, solver and coarse solver (taken from the first submit; HN_ERR_ARG for a request that
  * differs). */
 hn_status hn_server_create(size_t budget_bytes, int max_active, hn_server** out);
@@ -245,17 +247,18 @@ hn_status hn_mg_poll(hn_server* srv, unsigned long long ticket, long long timeou
 
 typedef struct {
   long long submitted, completed, active, queued;
-  long long iterations;        /* scheduler iterations run */
+  long long iterations;        /* scheduler iterations run (both lanes) */
   size_t bytes_in_use, budget;
-  /* time (ns) the builder thread spent building the hierarchies of admitted requests (on its own
-   * stream, while the worker iterates the running requests), and worker time spent waiting for
-   * iterations to finish, retiring requests (their results come back on a copy stream while the
-   * next iteration runs), and (re)building the schedule and starting requests */
+  /* time (ns) the builder threads spent building the hierarchies of admitted requests (on their
+   * own streams, while the workers iterate the running requests), and the workers' time (summed
+   * over the lanes, which run at the same time) spent waiting for iterations to finish, retiring
+   * requests (their results come back on a copy stream while the next iteration runs), and
+   * (re)building the schedule and starting requests */
   long long admit_ns, schedule_ns, iterate_ns, retire_ns;
 } hn_server_info;
 hn_status hn_server_query(hn_server* srv, hn_server_info* info);
 
-/* Stop the worker after finishing active requests; queued requests are dropped. */
+/* Stop the workers after finishing active requests; queued requests are dropped. */
 void hn_server_destroy(hn_server* srv);
 
 /* Message describing the calling thread's last error ("" if none). */

@@ -1,8 +1,12 @@
-// Continuous-batching solve server.  Requests queue FIFO; a request is admitted when a slot is free
-// and its hierarchy fits the device-memory budget.  Every scheduler iteration runs one launch
-// sequence of the V-cycle schedule (engine.cu) over all active requests at once; requests that
-// finish leave between iterations, free their memory and let queued requests in.  The hierarchy
-// of a request stays resident on the device from admission to completion.
+// Continuous-batching solve server.  Requests go to one of two lanes by size (levels below
+// kLargeLevel, and the rest); each lane has its own FIFO queue, worker thread, engine and streams,
+// so that small requests' iterations run at their own cadence beside the large requests' ones
+// instead of waiting for their finest-level steps.  A request is admitted when a slot is free and
+// its hierarchy fits the device-memory budget (slots and budget shared by the lanes).  Every pass
+// of a lane's worker runs one launch sequence of the V-cycle schedule (engine.cu) over the lane's
+// active requests at once; requests that finish leave between passes, free their memory and let
+// queued requests in.  The hierarchy of a request stays resident on the device from admission to
+// completion.
 #include <algorithm>
 #include <climits>
 #include <condition_variable>
@@ -91,6 +95,7 @@ struct Request {
   HostBuf coef, b, x;                // coef empty for a = 1
   hn_mg* mg = nullptr;
   int slot = -1;
+  int lane = 0;                      // 0: levels below kLargeLevel, 1: the others
   size_t bytes = 0;
   bool done = false;
   int status = HN_PENDING;
@@ -159,7 +164,9 @@ struct hn_server {
   int device = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<Request*> queue;
+  static constexpr int kLanes = 2;
+  static constexpr int kLargeLevel = 10;
+  std::deque<Request*> queue[kLanes];   // FIFO per lane
   std::map<unsigned long long, std::unique_ptr<Request>> all;
   unsigned long long next_ticket = 1;
   bool stop = false;
@@ -170,10 +177,10 @@ struct hn_server {
   long long admit_ns = 0, schedule_ns = 0, iterate_ns = 0, retire_ns = 0;   // worker time
   std::vector<Request*> slots;
   // Admitted requests go to the builder threads, which assemble their operators and hierarchies
-  // on their own streams while the worker keeps iterating the running requests; built requests
-  // join the schedule at the worker's next pass.
+  // on their own streams while the workers keep iterating the running requests; built requests
+  // join their lane's schedule at its worker's next pass.
   std::deque<Request*> to_build;     // admitted, waiting for the builder (under mu)
-  std::vector<Request*> built;       // built (or failed), not yet in the schedule (under mu)
+  std::vector<Request*> built[kLanes];   // built (or failed), not yet in the schedule (under mu)
   int building = 0;                  // requests the builders hold (under mu)
   bool builder_stop = false;         // (under mu)
   std::condition_variable cv_build;
@@ -181,9 +188,9 @@ struct hn_server {
   BlockCache cache;
   size_t scratch_bytes = 0;          // the builders' setup temporaries, together
   static constexpr int kBuilders = 2;  // a small request need not wait for a large one's setup
-  std::thread worker, builders[kBuilders];
-  std::string worker_error;
-  void run();
+  std::thread workers[kLanes], builders[kBuilders];
+  std::string worker_error;          // the first worker failure (under mu)
+  void run(int lane);
   void build_loop();
 };
 
@@ -292,7 +299,7 @@ void hn_server::build_loop() {
     if (st != HN_OK) r->status = st;
     else r->stats.setup_ns = mg->setup_ns;
     admit_ns += now_ns() - t0;
-    built.push_back(r);
+    built[r->lane].push_back(r);
     --building;
     cv_work.notify_all();
   }
@@ -304,18 +311,27 @@ void hn_server::build_loop() {
   if (sb) cudaStreamDestroy(sb);
 }
 
-void hn_server::run() {
+void hn_server::run(int lane) {
   cudaSetDevice(device);
-  // s: the schedule's iterations; s3: copying finished requests' results back while the next
-  // iteration runs (the builder thread has its own stream)
+  // s: the lane's iterations (the small requests' lane at the greatest stream priority, so that
+  // its short kernels are not queued behind the large requests' blocks); s3: copying finished
+  // requests' results back while the next iteration runs (the builders have their own streams)
   cudaStream_t s = nullptr, s3 = nullptr;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+    cudaGetLastError();
+    prio_least = prio_greatest = 0;
+  }
+  if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, lane == 0 ? prio_greatest : prio_least) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking) != cudaSuccess) {
     std::lock_guard<std::mutex> lk(mu);
-    worker_error = "stream creation failed";
+    if (worker_error.empty()) worker_error = "stream creation failed";
     stop = true;
-    builder_stop = true;
-    cv_build.notify_all();
+    for (std::deque<Request*>& q : queue) {
+      for (Request* r : q) { r->status = HN_ERR_CUDA; r->done = true; }
+      q.clear();
+    }
+    cv_work.notify_all();
     cv_done.notify_all();
     if (s) cudaStreamDestroy(s);
     return;
@@ -366,55 +382,68 @@ void hn_server::run() {
       in_use -= r->bytes;
       ++completed;
       cv_done.notify_all();
+      cv_work.notify_all();                         // (memory for the other lane's queue head)
     }
     retiring.erase(retiring.begin(), retiring.begin() + k);
   };
+  // A failure stops the server: this lane's requests, the queued ones and those admitted but not
+  // yet built fail; the other lane fails its own at the end of its pass.
   auto fail_all = [&](const char* why) {
     cudaStreamSynchronize(s3);
     std::unique_lock<std::mutex> lk(mu);
-    // the builder first finishes the request it holds (a failed request may be forgotten by
+    // the builders first finish the requests they hold (a failed request may be forgotten by
     // hn_mg_poll at once)
     builder_stop = true;
+    for (Request* r : to_build) {
+      slots[r->slot] = nullptr;
+      r->status = HN_ERR_CUDA;
+      r->done = true;
+    }
     to_build.clear();
     cv_build.notify_all();
     cv_work.wait(lk, [&] { return building == 0; });
-    worker_error = why;
+    if (worker_error.empty()) worker_error = why;
     for (Retiring& e : retiring) { e.r->status = HN_ERR_CUDA; e.r->done = true; cudaEventDestroy(e.ev); }
     retiring.clear();
-    for (Request* r : built) {
+    for (Request* r : built[lane]) {
       if (r->mg) hn_mg_destroy(r->mg);
       r->mg = nullptr;
     }
-    built.clear();
+    built[lane].clear();
     for (Request*& r : slots)
-      if (r) { r->status = HN_ERR_CUDA; r->done = true; r = nullptr; }
-    for (Request* r : queue) { r->status = HN_ERR_CUDA; r->done = true; }
-    queue.clear();
-    to_build.clear();
+      if (r && r->lane == lane) { r->status = HN_ERR_CUDA; r->done = true; r = nullptr; }
+    for (std::deque<Request*>& q : queue) {
+      for (Request* r : q) { r->status = HN_ERR_CUDA; r->done = true; }
+      q.clear();
+    }
     stop = true;
     cv_done.notify_all();
+    cv_work.notify_all();
   };
   for (;;) {
     bool admitted_any = false;
     {
       std::unique_lock<std::mutex> lk(mu);
-      auto occupied = [&] { return std::any_of(slots.begin(), slots.end(), [](Request* r) { return r != nullptr; }); };
+      auto occupied = [&] {
+        return std::any_of(slots.begin(), slots.end(), [&](Request* r) { return r != nullptr && r->lane == lane; });
+      };
+      std::deque<Request*>& q = queue[lane];
       // wake for: the end, an admission that can happen now (a free slot and budget room for the
-      // head of the queue), built requests, copies in flight, or running requests
+      // head of the lane's queue), built requests, copies in flight, or running requests
       auto admissible = [&] {
-        return !stop && !queue.empty() && std::find(slots.begin(), slots.end(), nullptr) != slots.end() &&
-               in_use + queue.front()->bytes <= budget;
+        return !stop && !q.empty() && std::find(slots.begin(), slots.end(), nullptr) != slots.end() &&
+               in_use + q.front()->bytes <= budget;
       };
       cv_work.wait(lk, [&] {
-        return (stop && !occupied() && retiring.empty()) || admissible() || !built.empty() ||
+        return (stop && !occupied() && retiring.empty()) || admissible() || !built[lane].empty() ||
                !retiring.empty() || any_running();
       });
       if (stop && !occupied() && retiring.empty()) break;
       if (!stop) {
-        while (!queue.empty()) {
+        while (!q.empty()) {
           auto free_slot = std::find(slots.begin(), slots.end(), nullptr);
           if (free_slot == slots.end()) break;
-          Request* r = queue.front();
+          Request* r = q.front();
           {
             std::lock_guard<std::mutex> ck(cache_mu);
             if (in_use + r->bytes + cache.bytes + scratch_bytes > budget) {
@@ -429,7 +458,7 @@ void hn_server::run() {
             }
           }
           if (in_use + r->bytes > budget) break;    // FIFO: the head waits for memory
-          queue.pop_front();
+          q.pop_front();
           in_use += r->bytes;
           r->slot = (int)(free_slot - slots.begin());
           *free_slot = r;
@@ -487,6 +516,7 @@ void hn_server::run() {
         std::lock_guard<std::mutex> lk(mu);
         slots[q] = nullptr;
         members_dirty = true;
+        cv_work.notify_all();                       // (a free slot for the other lane)
       }
       if (copy_failed) { fail_all("result copy failed"); break; }
     }
@@ -501,19 +531,20 @@ void hn_server::run() {
     // built requests join the schedule (or leave, if their setup failed)
     {
       std::lock_guard<std::mutex> lk(mu);
-      for (Request* r : built) {
+      for (Request* r : built[lane]) {
         if (!r->mg) {
           r->done = true;
           r->t_done = now_ns();
           in_use -= r->bytes;
           slots[r->slot] = nullptr;
           cv_done.notify_all();
+          cv_work.notify_all();                     // (a slot and memory for the other lane)
           continue;
         }
         fresh.push_back(r->slot);
         members_dirty = true;
       }
-      built.clear();
+      built[lane].clear();
     }
     // the schedule of the next iteration: (re)build the engine for the current highest level,
     // refresh its work lists, start the new requests
@@ -578,22 +609,20 @@ void hn_server::run() {
       std::lock_guard<std::mutex> lk(mu);
       schedule_ns += now_ns() - t_sched0;
     }
-    if (stop && worker_error.size()) break;
+    bool failed_elsewhere = false;                   // the other lane's worker failed
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      failed_elsewhere = stop && !worker_error.empty();
+    }
+    if (failed_elsewhere) {
+      cudaStreamSynchronize(s);
+      fail_all("stopped by the other lane's failure");
+      break;
+    }
   }
   engine.reset();
   cudaStreamSynchronize(s);
   finish_retiring(true);
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    builder_stop = true;
-    cv_build.notify_all();
-  }
-  for (std::thread& t : builders)
-    if (t.joinable()) t.join();
-  {
-    std::lock_guard<std::mutex> lk(cache_mu);
-    cache.clear();
-  }
   cudaStreamDestroy(s3);
   cudaStreamDestroy(s);
 }
@@ -611,7 +640,8 @@ hn_status hn_server_create(size_t budget_bytes, int max_active, hn_server** out)
   HN_CUDA(cudaGetDevice(&srv->device));
   hn_server* raw = srv.get();
   for (std::thread& t : srv->builders) t = std::thread([raw] { raw->build_loop(); });
-  srv->worker = std::thread([raw] { raw->run(); });
+  for (int lane = 0; lane < hn_server::kLanes; ++lane)
+    srv->workers[lane] = std::thread([raw, lane] { raw->run(lane); });
   *out = srv.release();
   return HN_OK;
 }
@@ -627,6 +657,7 @@ hn_status hn_mg_submit(hn_server* srv, int L, const double* cell_coef, const dou
   HN_TRY(check_band_inputs(L, cell_coef, o.dirichlet_sides));   // here, not on the worker
   std::unique_ptr<Request> r(new Request());
   r->L = L;
+  r->lane = L >= hn_server::kLargeLevel ? 1 : 0;
   r->bc = o.dirichlet_sides;
   const long long N = N_of(L), cells = (1LL << L) * (1LL << L);
   if (cell_coef) {
@@ -653,10 +684,10 @@ hn_status hn_mg_submit(hn_server* srv, int L, const double* cell_coef, const dou
   r->ticket = srv->next_ticket++;
   r->t_submit = now_ns();
   *ticket = r->ticket;
-  srv->queue.push_back(r.get());
+  srv->queue[r->lane].push_back(r.get());
   srv->all[r->ticket] = std::move(r);
   ++srv->submitted;
-  srv->cv_work.notify_one();
+  srv->cv_work.notify_all();                        // (the workers share the condition)
   return HN_OK;
 }
 
@@ -693,7 +724,7 @@ hn_status hn_server_query(hn_server* srv, hn_server_info* info) {
   info->submitted = srv->submitted;
   info->completed = srv->completed;
   info->active = std::count_if(srv->slots.begin(), srv->slots.end(), [](Request* r) { return r != nullptr; });
-  info->queued = (long long)srv->queue.size();
+  info->queued = (long long)(srv->queue[0].size() + srv->queue[1].size());
   info->iterations = srv->iterations;
   info->bytes_in_use = srv->in_use;
   info->budget = srv->budget;
@@ -709,11 +740,14 @@ void hn_server_destroy(hn_server* srv) {
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->stop = true;
-    for (Request* r : srv->queue) { r->status = HN_ERR_STATE; r->done = true; }
-    srv->queue.clear();
+    for (std::deque<Request*>& q : srv->queue) {
+      for (Request* r : q) { r->status = HN_ERR_STATE; r->done = true; }
+      q.clear();
+    }
     srv->cv_work.notify_all();
   }
-  if (srv->worker.joinable()) srv->worker.join();
+  for (std::thread& t : srv->workers)
+    if (t.joinable()) t.join();
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->builder_stop = true;
@@ -721,6 +755,15 @@ void hn_server_destroy(hn_server* srv) {
   }
   for (std::thread& t : srv->builders)
     if (t.joinable()) t.join();
+  {
+    // the retired requests' device blocks (on the server's device)
+    int prev = -1;
+    const bool switched = cudaGetDevice(&prev) == cudaSuccess && prev != srv->device &&
+                          cudaSetDevice(srv->device) == cudaSuccess;
+    std::lock_guard<std::mutex> lk(srv->cache_mu);
+    srv->cache.clear();
+    if (switched) cudaSetDevice(prev);
+  }
   delete srv;
 }
 

@@ -266,6 +266,29 @@ def test_server_results_match_alone(hn, slots):
         hn.hn_server_destroy(srv)
 
 
+@pytest.mark.parametrize("slots", [4, 1])
+def test_server_lanes_of_small_and_large_requests_match_alone(hn, slots):
+    # levels below 10 and from 10 up go to the server's two lanes (a worker, an engine and a stream
+    # each, iterating side by side); with one slot it passes from lane to lane
+    srv = hn.hn_server_create(4 << 30, slots)
+    try:
+        reqs = []
+        for j, L in enumerate([10, 6, 5, 10, 8]):
+            coef, b = I.batch_problem(70 + j, L)
+            reqs.append((hn.hn_mg_submit(srv, L, b, coef, prec=1), L, coef, b))
+        for t, L, coef, b in reqs:
+            status, x, st = hn.hn_mg_poll(srv, t, L, timeout_ns=60_000_000_000)
+            assert status == hn.HN_OK
+            xa, sa, _ = solve(hn, L, b, coef, prec=1)
+            np.testing.assert_array_equal(x, xa)
+            assert st["cycles"] == sa["cycles"]
+        info = hn.hn_server_query(srv)
+        assert info["completed"] == len(reqs) and info["active"] == 0 and info["queued"] == 0
+        assert info["bytes_in_use"] == 0
+    finally:
+        hn.hn_server_destroy(srv)
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_server_reuses_device_blocks_without_leaking_state(hn, prec):
     # one slot: every request is admitted after the previous one retired, so its operator and
