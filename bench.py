@@ -185,6 +185,23 @@ def ncu_traffic_per_node(kernel):
     return None
 
 
+def solve_roofline(n_dof, ms, peak_gbs, inner_cycles=0, outer_iters=0, fp64_cycles=0):
+    """A whole solve against its bandwidth roofline: the algorithmic (compulsory, unfused) bytes
+    per DOF of the cycles and outer steps it ran, moved at the measured copy bandwidth, as a
+    fraction of the measured time.  A V(2,2) cycle moves, on the finest level, four smoothing
+    sweeps and one defect (x, b in, x' or r out, with the bands: 48 B/DOF in FP32, 96 in FP64), the
+    restriction (5 / 10 B) and the prolongation with its correction (9 / 18 B), and 4/3 of that
+    over the hierarchy; the residual check rides in the next cycle's first sweep.  A defect
+    correction adds one FP64 defect per outer step and a last one that stops it (96 B each), and
+    one FP64 update per step (x += s c: 24 B)."""
+    fp32_cycle = (4 * 48 + 48 + 5 + 9) * 4.0 / 3.0
+    fp64_cycle = (4 * 96 + 96 + 10 + 18) * 4.0 / 3.0
+    outer = (outer_iters + 1) * 96.0 + outer_iters * 24.0 if outer_iters > 0 else 0.0
+    per_dof = inner_cycles * fp32_cycle + fp64_cycles * fp64_cycle + outer
+    roof_ms = per_dof * n_dof / (peak_gbs * 1e9) * 1e3
+    return {"bytes_per_dof": per_dof, "roofline_ms": roof_ms, "ms": ms, "frac": roof_ms / ms}
+
+
 def measured_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -854,6 +871,13 @@ def run_ours(args, rank, world, local, pg):
         line["fp64"] = solve_row(total_fp64, st_fp64, "fp64")
         line["mixed"] = solve_row(total_mixed, st_mixed, "mixed")
         line["mixed_over_fp64"] = value / fp64_value
+        try:                                           # never costs the line
+            line["solve_roofline"] = {
+                "mixed": solve_roofline(N, total_mixed / args.steps, peak, inner_cycles=st_mixed["inner_cycles"],
+                                        outer_iters=st_mixed["outer_iters"]),
+                "fp64": solve_roofline(N, total_fp64 / args.steps, peak, fp64_cycles=st_fp64["cycles"])}
+        except Exception as e:
+            line["solve_roofline"] = {"error": "%s: %s" % (type(e).__name__, e)}
         print(json.dumps(sig(line)), flush=True)
 
 

@@ -38,3 +38,16 @@ def test_reference_arm_prints_one_line_with_the_contract_keys():
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     cb = j["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == j["value"] and cb["sample"]
+
+
+def test_solve_roofline_counts_the_algorithmic_bytes_of_what_the_solve_ran():
+    # 3 FP32 cycles of (4 sweeps + 1 defect at 48 B, restriction 5 B, prolongation 9 B) x 4/3,
+    # three FP64 defects (two steps and the last check) at 96 B and two updates at 24 B
+    r = bench.solve_roofline(1_000_000, 1.0, 1000.0, inner_cycles=3, outer_iters=2)
+    per = 3 * (4 * 48 + 48 + 5 + 9) * 4 / 3 + 3 * 96 + 2 * 24
+    assert abs(r["bytes_per_dof"] - per) < 1e-9
+    assert abs(r["roofline_ms"] - per * 1e6 / 1e12 * 1e3) < 1e-12     # bytes / (GB/s), in ms
+    assert abs(r["frac"] - r["roofline_ms"]) < 1e-12                    # measured 1 ms
+    f = bench.solve_roofline(1_000_000, 2.0, 1000.0, fp64_cycles=2)     # FP64 MG: no outer steps
+    assert abs(f["bytes_per_dof"] - 2 * (4 * 96 + 96 + 10 + 18) * 4 / 3) < 1e-9
+    assert abs(f["frac"] - f["roofline_ms"] / 2.0) < 1e-12
