@@ -223,7 +223,9 @@ hn_status hn_mg_get_inner_bands(const hn_mg* mg, int level, void* bands_out, flo
  * A server owns two lanes (requests of levels below 10, and of levels 10 and up), each with a
  * worker thread, a FIFO queue and its own stream (the small requests' lane at the greatest stream
  * priority), two builder threads and a device-memory budget.  A request is admitted once a slot
- * (max_active, shared by the lanes) and budget room for its hierarchy are free.  Admitted requests
+ * (max_active, shared by the lanes) and budget room for its hierarchy are free; requests of one
+ * lane are admitted in submission order, the lanes independently (under a budget too tight for
+ * both, a large request waiting for memory can be overtaken by small ones).  Admitted requests
  * of a lane are solved together: every scheduler iteration of a lane runs one V-cycle phase
  * sequence over its active requests (continuous batching), beside the other lane's iterations;
  * finished requests leave, free their memory and let queued requests in.  All requests of a server share precision, pre, post, omega,
