@@ -73,3 +73,14 @@ def test_host_side_argument_checks(lib):
     assert lib.hn_mg_setup(None, ctypes.byref(o), ctypes.byref(h)) == hn.HN_ERR_ARG
     assert lib.hn_server_create(0, 4, ctypes.byref(h)) == hn.HN_ERR_ARG
     assert lib.hn_mg_poll(None, 1, 0, None, None) == hn.HN_ERR_ARG
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    # no CPU path stands in for the CUDA library: without it every call raises
+    from paper_0904_4152_gb300 import hn
+    monkeypatch.setattr(hn, "LIB_PATH", str(tmp_path / "libhn.so"))
+    monkeypatch.setattr(hn, "_lib", None)
+    with pytest.raises(ImportError, match="not built"):
+        hn.lib()
+    with pytest.raises(ImportError):
+        hn.hn_band_create(4)
