@@ -302,6 +302,66 @@ def test_mg_matches_dense_lu(L, lognormal):
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-11
 
 
+def bilinear_P(Lf):
+    """Dense interpolation from level Lf - 1 to Lf, written from the bilinear definition: a fine
+    node takes its coarse parent's value (even index), the mean of its two parents (odd index),
+    per axis, the weights multiplying; rows of fine boundary nodes and columns of coarse boundary
+    nodes are zero."""
+    nf, nc = O.n_of(Lf), O.n_of(Lf - 1)
+    P = np.zeros((nf * nf, nc * nc))
+
+    def parents(f):
+        return [(f // 2, 1.0)] if f % 2 == 0 else [((f - 1) // 2, 0.5), ((f + 1) // 2, 0.5)]
+
+    for fy in range(1, nf - 1):
+        for fx in range(1, nf - 1):
+            for Cy, wy in parents(fy):
+                for Cx, wx in parents(fx):
+                    if 0 < Cx < nc - 1 and 0 < Cy < nc - 1:
+                        P[fy * nf + fx, Cy * nc + Cx] += wx * wy
+    return P
+
+
+def dense_vcycle(L, Lc, coef, b, pre, post, omega):
+    """One V(pre, post) cycle from zero in dense matrices: damped Jacobi pre-smoothing, the defect
+    restricted by P^T, the same cycle on the coarser level (an exact solve on the unknowns of the
+    coarsest), prolongation of the correction, post-smoothing."""
+    cf = {L: coef}
+    for l in range(L, Lc, -1):
+        cf[l - 1] = None if cf[l] is None else O.coarsen_coef(l, cf[l])
+    A = {l: dense_from_bands(l, O.assemble(l, cf[l])) for l in range(Lc, L + 1)}
+
+    def cycle(l, rhs):
+        if l == Lc:
+            idx = interior_idx(l)
+            x = np.zeros(rhs.size)
+            x[idx] = np.linalg.solve(A[l][np.ix_(idx, idx)], rhs[idx])
+            return x
+        D = np.diag(A[l])
+        x = np.zeros(rhs.size)
+        for _ in range(pre):
+            x = x + omega * (rhs - A[l] @ x) / D
+        P = bilinear_P(l)
+        x = x + P @ cycle(l - 1, P.T @ (rhs - A[l] @ x))
+        for _ in range(post):
+            x = x + omega * (rhs - A[l] @ x) / D
+        return x
+
+    return cycle(L, b)
+
+
+@pytest.mark.parametrize("pre,post", [(1, 2), (2, 1), (0, 1), (2, 2)])
+@pytest.mark.parametrize("L,lognormal", [(3, False), (4, True)])
+def test_one_cycle_equals_its_dense_composition(L, lognormal, pre, post):
+    # the cycle's structure, with unequal smoothing counts: a swapped pre/post count, a missing
+    # restriction of the defect or a correction applied before the coarse solve all change it
+    a = I.lognormal_coef(L, 31) if lognormal else None
+    b = I.rhs_uniform(L, 32)
+    z = O.precondition(L, b, coef=a, prec=O.PREC_FP64, pre=pre, post=post, omega=0.7, coarse_L=2)
+    ref = dense_vcycle(L, 2, a, b, pre, post, 0.7)
+    assert np.linalg.norm(z - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
 def test_mg_contraction_level_independent():
     # Sec. 6.2: two V(2,2) cycles gain (at least) one digit; the rate does not grow with L
     rates = []
@@ -368,6 +428,50 @@ def test_mixed_precision_reaches_fp64_tolerance(prec):
     r = O.defect(L, O.assemble(L, a), b, x)
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-8
     assert st["outer_iters"] >= 2 and st["inner_cycles"] >= st["outer_iters"]
+
+
+@pytest.mark.parametrize("prec", [O.PREC_FP64, O.PREC_FP32_DC, O.PREC_FP16BAND_DC])
+def test_stopping_rule_is_the_first_iterate_within_tolerance(prec):
+    # the solve stops at the first cycle (FP64) or outer step (defect correction) whose FP64
+    # relative residual is at most tol, and counts one entry per cycle / step
+    L = 6
+    a = I.lognormal_coef(L, 3)
+    b = I.rhs_uniform(L, 4)
+    for tol in (1e-3, 1e-5, 1e-7, 1e-9, 1e-11):
+        x, st, hist = O.mg_solve(L, b, coef=a, prec=prec, tol=tol, history=True)
+        assert st["converged"] and hist[-1] <= tol and (hist[:-1] > tol).all()
+        steps = st["cycles"] if prec == O.PREC_FP64 else st["outer_iters"]
+        assert hist.size == steps + 1
+        r = O.defect(L, O.assemble(L, a), b, x)
+        assert abs(np.linalg.norm(r) / np.linalg.norm(b) - hist[-1]) <= 1e-6 * hist[-1]
+
+
+@pytest.mark.parametrize("inner_max", [1, 3])
+def test_inner_cycles_per_outer_step_are_capped(inner_max):
+    # with an inner tolerance no cycle meets, every outer step runs exactly inner_max cycles
+    L = 5
+    b = I.rhs_uniform(L, 5)
+    x, st = O.mg_solve(L, b, prec=O.PREC_FP32_DC, inner_tol=1e-30, inner_max=inner_max,
+                       max_outer=4, tol=1e-30)
+    assert st["outer_iters"] == 4 and st["inner_cycles"] == 4 * inner_max
+
+
+def test_inner_solve_stops_like_the_fp32_solve_of_the_scaled_defect():
+    # from x = 0 the first outer step's inner solve is FP32 multigrid on d / ||d|| = b / ||b||
+    # from zero, stopped at the first cycle whose FP32 residual is within inner_tol of that
+    # right-hand side: the same count as the FP32-only solve of it to tol = inner_tol
+    L = 6
+    a = I.lognormal_coef(L, 7)
+    b = I.rhs_uniform(L, 8)
+    dhat = (b / np.linalg.norm(b)).astype(np.float32).astype(np.float64)
+    counts = []
+    for inner_tol in (0.3, 0.1, 3e-2, 1e-2, 1e-3):
+        _, st = O.mg_solve(L, b, coef=a, prec=O.PREC_FP32_DC, inner_tol=inner_tol, inner_max=50,
+                           max_outer=1, tol=1e-30)
+        _, s32 = O.mg_solve(L, dhat, coef=a, prec=O.PREC_FP32_ONLY, tol=inner_tol, max_cycles=50)
+        assert st["inner_cycles"] == s32["cycles"]
+        counts.append(st["inner_cycles"])
+    assert counts == sorted(counts) and counts[-1] > counts[0]
 
 
 def test_fp32_only_loses_accuracy():
