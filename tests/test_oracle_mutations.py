@@ -6,7 +6,10 @@ local node order, a transposed band index, a missed Dirichlet elimination, a wro
 dropped band, flipped signs, a missing damping factor or square root, wrong transfer weights,
 rounding ties away from even, a wrong subnormal threshold, a signed maximum for the FP16 scale,
 a short row sum, swapped smoothing counts, an unscaled correction, wrong Cholesky indices, CG and
-PCG update mistakes, and stopping rules that are off by a factor or a cycle.
+PCG update mistakes, stopping rules that are off by a factor or a cycle, a swapped side bit,
+wrong load-vector quadrature or source factor, a wrong corner of the error's interpolant, a wrong
+FP16 subnormal decoding, a float accumulator for the dot product, two roundings in axpy, a dropped
+band and swapped operands or sign in the shallow-water step.
 
 Four further changes leave the oracle's results unchanged and are therefore not mistakes: the
 sign of every y-derivative of the element basis (the stiffness is quadratic in it), the weight of
@@ -94,6 +97,35 @@ MUTATIONS = [
      "    while (rr > tol && s.cycles < max_cycles) {\n      vcycle<double>(H, 0, x, b, pre, post, omega);",
      "    while (rr > 0.1 * tol && s.cycles < max_cycles) {\n      vcycle<double>(H, 0, x, b, pre, post, omega);",
      "test_stopping_rule_is_the_first_iterate_within_tolerance"),
+    ("side_mask_bit", "(ix == n - 1 && (m & 2u))", "(ix == n - 1 && (m & 4u))",
+     "test_mixed_bc_operator_symmetric_and_natural"),
+    ("load_quadrature_weights", "  const double wts[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};\n  const int lx[4]",
+     "  const double wts[3] = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0};\n  const int lx[4]",
+     "test_load_vector_matches_the_exact_integral"),
+    ("load_source_factor", "const double f = 2.0 * M_PI * M_PI * u(px, py);", "const double f = M_PI * M_PI * u(px, py);",
+     "test_load_vector_matches_the_exact_integral"),
+    ("l2_error_interpolant_corner",
+     "xi * eta * x[(ey + 1) * n + ex + 1] + (1 - xi) * eta * x[(ey + 1) * n + ex];",
+     "xi * eta * x[(ey + 1) * n + ex] + (1 - xi) * eta * x[(ey + 1) * n + ex + 1];",
+     "test_l2_error_of_zero_and_of_interpolant"),
+    ("fp16_decode_subnormal", "if (e == 0) v = std::ldexp((double)f, -24);", "if (e == 0) v = std::ldexp((double)f, -25);",
+     "test_fp16_decoding_matches_ieee"),
+    ("dot_float_accumulator", "double or_dot_f32(long n, const float* x, const float* y) {\n  long double s = 0.0L;",
+     "double or_dot_f32(long n, const float* x, const float* y) {\n  float s = 0.0f;",
+     "test_oracle_dot_closed_form_and_exact_sum"),
+    ("axpy_two_roundings", "void or_axpy_f32(long n, float a, const float* x, float* y) {\n  for (long i = 0; i < n; ++i) y[i] = std::fma(a, x[i], y[i]);",
+     "void or_axpy_f32(long n, float a, const float* x, float* y) {\n  for (long i = 0; i < n; ++i) y[i] = a * x[i] + y[i];",
+     "test_oracle_axpy_single_rounding"),
+    ("band4_first_band_dropped", "  for (int k = 0; k < 4; ++k) {\n    const long long j = (long long)i + off[k];",
+     "  for (int k = 1; k < 4; ++k) {\n    const long long j = (long long)i + off[k];", "test_band4_against_scipy_diagonals"),
+    ("swe_operands_swapped", "const T* xs[4] = {v, w, u, u};", "const T* xs[4] = {w, v, u, u};",
+     "test_swe_predict_exact_on_integers"),
+    ("swe_source_sign", "u_new[i] = s ? t + s[i] : t;", "u_new[i] = s ? t - s[i] : t;",
+     "test_swe_predict_exact_on_integers"),
+    ("coarse_cg_tolerance", "constexpr double kCgTol = 1e-13;", "constexpr double kCgTol = 1e-4;",
+     "test_coarse_cg_matches_cholesky"),
+    ("pcg_alpha_denominator", "      const double alpha = rho / dot64(N, p.data(), q.data());",
+     "      const double alpha = rho / dot64(N, r.data(), q.data());", "test_pcg_follows_scipy_cg"),
 ]
 
 

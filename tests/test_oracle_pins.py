@@ -418,6 +418,41 @@ def test_load_vector_consistent_with_point_values():
     assert np.all(b[0, :] == 0) and np.all(b[:, -1] == 0)
 
 
+@pytest.mark.parametrize("L", [4, 6])
+def test_load_vector_matches_the_exact_integral(L):
+    # f = 2 pi^2 sin(pi x) g(y) against the hat function of node (x_i, y_j) separates; per axis
+    # the integral of sin (or cos) times a hat of half-width h is sin(pi x_i) * 2 (1 - cos pi h) /
+    # (pi^2 h), and half of that (times cos(pi y_j)) for the half hat of a free side's node
+    n = O.n_of(L)
+    h = 1.0 / (n - 1)
+    c = 2.0 * (1.0 - math.cos(math.pi * h)) / (math.pi ** 2 * h)
+    x = np.arange(n) * h
+    sx = np.sin(np.pi * x) * c
+    exact = 2 * np.pi ** 2 * np.outer(sx, sx)                                  # [y, x]
+    exact[0, :] = exact[-1, :] = exact[:, 0] = exact[:, -1] = 0.0
+    b = O.load_sinsin(L).reshape(n, n)
+    assert np.abs(b - exact).max() <= 1e-8 * np.abs(exact).max()
+    cy = np.cos(np.pi * x) * c
+    cy[0] *= 0.5
+    cy[-1] *= 0.5
+    exact = 2 * np.pi ** 2 * np.outer(cy, sx)                                  # Dirichlet x = 0, 1
+    exact[:, 0] = exact[:, -1] = 0.0
+    b = O.load_sincos(L).reshape(n, n)
+    assert np.abs(b - exact).max() <= 1e-8 * np.abs(exact).max()
+
+
+def test_fp16_decoding_matches_ieee():
+    # every binary16 code decodes to the value numpy's IEEE half type gives it
+    codes = np.arange(1 << 16, dtype=np.uint16)
+    want = codes.view(np.float16).astype(np.float32)
+    f = O.lib().or_fp16_to_float
+    got = np.array([f(int(c)) for c in codes], dtype=np.float32)
+    nan = np.isnan(want)
+    assert (np.isnan(got) == nan).all()
+    np.testing.assert_array_equal(got[~nan], want[~nan])
+    assert (np.signbit(got[~nan]) == np.signbit(want[~nan])).all()
+
+
 @pytest.mark.parametrize("prec", [O.PREC_FP32_DC, O.PREC_FP16BAND_DC])
 def test_mixed_precision_reaches_fp64_tolerance(prec):
     L = 7
