@@ -124,6 +124,10 @@ MUTATIONS = [
      "test_swe_predict_exact_on_integers"),
     ("coarse_cg_tolerance", "constexpr double kCgTol = 1e-13;", "constexpr double kCgTol = 1e-4;",
      "test_coarse_cg_matches_cholesky"),
+    ("fp16_quotient_in_float", "codes[k * N + i] = fp16_rne(v[i] / (double)s);",
+     "codes[k * N + i] = fp16_rne((double)((float)v[i] / s));", "test_quantize_fp16_bands"),
+    ("hierarchy_without_coarsening", "        coarsen_coef(l, a.data(), ac.data());\n        a.swap(ac);",
+     "        coarsen_coef(l, a.data(), ac.data());", "test_mg_matches_dense_lu"),
     ("pcg_alpha_denominator", "      const double alpha = rho / dot64(N, p.data(), q.data());",
      "      const double alpha = rho / dot64(N, r.data(), q.data());", "test_pcg_follows_scipy_cg"),
 ]

@@ -538,9 +538,11 @@ def test_fp16_rne_matches_ieee():
     np.testing.assert_array_equal(O.fp16_rne(vals), ref)
 
 
-def test_quantize_fp16_bands():
-    # slot 4 holds the row sums; every array has its own max-abs scale; codes are numpy's RNE
-    L = 5
+@pytest.mark.parametrize("L", [5, 9])
+def test_quantize_fp16_bands(L):
+    # slot 4 holds the row sums; every array has its own max-abs scale; codes are numpy's RNE of
+    # the FP64 quotient (at L = 9, 2.4 million values: a quotient rounded to FP32 first would
+    # round about a hundred of them twice and differ)
     A = O.assemble(L, I.lognormal_coef(L, 3))
     s, codes = O.quantize_fp16(L, A)
     V = A.copy()
