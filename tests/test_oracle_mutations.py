@@ -7,6 +7,7 @@ dropped band, flipped signs, a missing damping factor or square root, wrong tran
 rounding ties away from even, a wrong subnormal threshold, a signed maximum for the FP16 scale,
 a short row sum, swapped smoothing counts, an unscaled correction, wrong Cholesky indices, CG and
 PCG update mistakes, stopping rules that are off by a factor or a cycle, a swapped side bit,
+transfers that skip the free sides as if they were Dirichlet, Dirichlet rows kept in the load,
 wrong load-vector quadrature or source factor, a wrong corner of the error's interpolant, a wrong
 FP16 subnormal decoding, a float accumulator for the dot product, two roundings in axpy, a dropped
 band and swapped operands or sign in the shallow-water step.
@@ -128,6 +129,14 @@ MUTATIONS = [
      "codes[k * N + i] = fp16_rne((double)((float)v[i] / s));", "test_quantize_fp16_bands"),
     ("hierarchy_without_coarsening", "        coarsen_coef(l, a.data(), ac.data());\n        a.swap(ac);",
      "        coarsen_coef(l, a.data(), ac.data());", "test_mg_matches_dense_lu"),
+    ("restriction_skips_free_sides", "      if (is_boundary(fx, fy, nf)) continue;\n      for (long Cy",
+     "      if (fx == 0 || fy == 0 || fx == nf - 1 || fy == nf - 1) continue;\n      for (long Cy",
+     "test_mixed_bc_transfers_adjoint_and_exact"),
+    ("prolongation_skips_free_sides", "      if (is_boundary(fx, fy, nf)) continue;\n      T s = 0;",
+     "      if (fx == 0 || fy == 0 || fx == nf - 1 || fy == nf - 1) continue;\n      T s = 0;",
+     "test_mixed_bc_transfers_adjoint_and_exact"),
+    ("load_dirichlet_rows_kept", "      if (is_boundary(ix, iy, n)) b[iy * n + ix] = 0.0;\n}", "      if (false) b[iy * n + ix] = 0.0;\n}",
+     "test_load_vector_matches_the_exact_integral"),
     ("pcg_alpha_denominator", "      const double alpha = rho / dot64(N, p.data(), q.data());",
      "      const double alpha = rho / dot64(N, r.data(), q.data());", "test_pcg_follows_scipy_cg"),
 ]
