@@ -34,9 +34,9 @@
 // Parity is pinned by the tests (closed-form stencil and eigenvalues, independent dense assembly,
 // dense LU, one cycle against its dense composition, the stopping rules, the load vector's exact
 // integral, O(h^2) convergence, transfer identities, numpy's float16 rounding and decoding); a
-// test plants plausible slips in copies of this file and checks that each fails a pin.  Nothing here is
-// "parity unpinned" except the absolute Table 1 values of the paper, which are not reproducible
-// because the paper does not name its test polynomial.
+// test plants plausible slips in copies of this file and checks that each fails a pin.  Nothing
+// here is "parity unpinned" except the absolute Table 1 values of the paper, which are not
+// reproducible because the paper does not name its test polynomial.
 
 #include <cmath>
 #include <cstdint>
